@@ -1,0 +1,191 @@
+"""Seeded synthetic inputs shared by the oracle and the CUDA path.
+
+This module holds grid and scene *descriptions* and seeded random draws only.
+No step of the method's arithmetic (geometry evaluation, rasterisation,
+advection, projection, adjoint) lives here, so the oracle and the CUDA path
+can both consume these inputs without sharing any solver code.
+
+Conventions of the descriptions (both consumers follow them):
+
+* Unit-spaced MAC grid of ``nx * ny * nz`` cells with spacing ``dx``. Face
+  arrays are stored per component with x fastest: ``u[0]`` has shape
+  ``(nz, ny, nx + 1)``, ``u[1]`` ``(nz, ny + 1, nx)``, ``u[2]``
+  ``(nz + 1, ny, nx)``; cell arrays have shape ``(nz, ny, nx)``. A periodic
+  grid (oracle only) stores ``(nz, ny, nx)`` for every component.
+* ``outlet`` is ``None`` or a dict ``{"axis": 0, "side": 1, "j0", "k0", "w",
+  "h"}``: the patch of boundary faces on the high-x wall whose y-cell index is
+  in ``[j0, j0 + w)`` and z-cell index in ``[k0, k0 + h)``.
+* A scene is ``{"kind": ..., "theta": [...], **constants}`` with kinds
+  ``none``, ``sphere``, ``chamber``, ``plate`` and ``spheres``; ``theta`` holds
+  the differentiable parameters (design and control).
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+SCENE_KINDS = ("none", "sphere", "chamber", "plate", "spheres", "shell")
+
+
+def make_grid(n, dt, *, ny=None, nz=None, nu=0.0, rho=1.0, outlet=None,
+              periodic=False, extent=1.0):
+    """A grid description: ``n`` cells along x over ``[0, extent]``."""
+    ny = n if ny is None else ny
+    nz = n if nz is None else nz
+    return dict(nx=int(n), ny=int(ny), nz=int(nz), dx=float(extent) / n,
+                dt=float(dt), rho=float(rho), nu=float(nu),
+                periodic=bool(periodic), outlet=outlet)
+
+
+def face_shape(grid, d):
+    """Array shape of face component ``d`` (0 = x, 1 = y, 2 = z)."""
+    nx, ny, nz = grid["nx"], grid["ny"], grid["nz"]
+    if grid.get("periodic", False):
+        return (nz, ny, nx)
+    return [(nz, ny, nx + 1), (nz, ny + 1, nx), (nz + 1, ny, nx)][d]
+
+
+def cell_shape(grid):
+    return (grid["nz"], grid["ny"], grid["nx"])
+
+
+def centred_outlet(n, width):
+    """A ``width x width`` patch of high-x boundary faces centred in (y, z)."""
+    j0 = n // 2 - width // 2
+    return dict(axis=0, side=1, j0=j0, k0=j0, w=int(width), h=int(width))
+
+
+def gaussian_faces(grid, sigma, seed):
+    """Independent N(0, sigma^2) values on every face (PCG64 with ``seed``)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return [sigma * rng.standard_normal(face_shape(grid, d)) for d in range(3)]
+
+
+def zero_faces(grid):
+    return [np.zeros(face_shape(grid, d)) for d in range(3)]
+
+
+# ---------------------------------------------------------------- scenes ----
+
+def sphere_scene(v=(0.1, 0.0, 0.0), centre=(0.5, 0.5, 0.5), radius=0.2):
+    """A solid sphere translating with constant velocity ``theta = v``."""
+    return dict(kind="sphere", theta=[float(x) for x in v],
+                centre=[float(x) for x in centre], radius=float(radius))
+
+
+def chamber_scene(theta, dx, *, centre=(0.5, 0.5, 0.5),
+                  axes=(0.35, 0.25, 0.25), period=0.5, duct_x0=0.5,
+                  duct_half_cells=8):
+    """Pulsing ellipsoidal chamber joined to an outlet duct.
+
+    ``theta = (a1..a4, b1..b4)`` are the Fourier coefficients of the radius
+    modulation. The duct is the slab ``x >= duct_x0`` with square cross
+    section of half width ``duct_half_cells * dx`` centred at (0.5, 0.5).
+    """
+    theta = [float(x) for x in theta]
+    assert len(theta) == 8
+    return dict(kind="chamber", theta=theta, centre=[float(x) for x in centre],
+                axes=[float(x) for x in axes], period=float(period),
+                duct_x0=float(duct_x0), duct_half=float(duct_half_cells * dx))
+
+
+def plate_scene(theta, dx, period, *, centre=(0.5, 0.5, 0.5),
+                half=(0.3, None, 0.3)):
+    """Flat plate hinged at ``centre`` rotating about z.
+
+    ``theta`` holds 4 angle knots at t = 0, T/3, 2T/3, T (T = ``period``); the
+    plate is 3 cells thick (half thickness 1.5 dx) unless ``half`` says
+    otherwise.
+    """
+    theta = [float(x) for x in theta]
+    assert len(theta) == 4
+    hy = 1.5 * dx if half[1] is None else half[1]
+    return dict(kind="plate", theta=theta, centre=[float(x) for x in centre],
+                half=[float(half[0]), float(hy), float(half[2])],
+                period=float(period))
+
+
+def spheres_scene(seed, count=64, rmin=0.02, rmax=0.08):
+    """``count`` static spheres, centres U[0,1]^3 and radii U[rmin, rmax]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    c = rng.uniform(0.0, 1.0, size=(count, 3))
+    r = rng.uniform(rmin, rmax, size=(count,))
+    return dict(kind="spheres", theta=[],
+                spheres=[[float(a), float(b), float(e), float(f)]
+                         for (a, b, e), f in zip(c, r)])
+
+
+def empty_scene():
+    return dict(kind="none", theta=[])
+
+
+def shell_scene(lo, hi, thickness, v):
+    """Hollow axis-aligned box shell translating with velocity ``v``.
+
+    Solid between the boxes ``[lo, hi]`` and ``[lo + thickness, hi -
+    thickness]``; used by the invariant test of the step (interior fluid
+    moving with the shell stays uniform).
+    """
+    return dict(kind="shell", theta=[float(x) for x in v],
+                lo=[float(x) for x in lo], hi=[float(x) for x in hi],
+                thickness=float(thickness))
+
+
+# --------------------------------------------------------------- configs ----
+
+def config_sphere(n=32, *, seed=0, steps=20, dt=0.01, sigma=0.1, tol=1e-10):
+    """Plain FP64 method: translating sphere in a closed box (32^3, 20 steps)."""
+    g = make_grid(n, dt)
+    return dict(name=f"sphere{n}", grid=g, scene=sphere_scene(),
+                u0=gaussian_faces(g, sigma, seed), project_initial=True,
+                steps=steps, tol=tol, loss="kinetic_energy")
+
+
+def config_chamber(n=128, *, seed=0, steps=100, dt=0.005, tol=1e-6,
+                   duct_half_cells=8):
+    """Pulsing chamber with one outlet patch (128^3, 100 steps)."""
+    g = make_grid(n, dt, outlet=centred_outlet(n, 2 * duct_half_cells))
+    rng = np.random.Generator(np.random.PCG64(seed))
+    theta = rng.uniform(-0.05, 0.05, size=8)
+    sc = chamber_scene(theta, g["dx"], duct_half_cells=duct_half_cells)
+    return dict(name=f"chamber{n}", grid=g, scene=sc, u0=zero_faces(g),
+                project_initial=False, steps=steps, tol=tol, loss="outflow")
+
+
+def config_plate(n=64, *, seed=0, steps=16, dt=0.01, sigma=0.1, tol=1e-10):
+    """Rotating plate with 4 angle knots (64^3, 16 steps)."""
+    g = make_grid(n, dt)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    theta = rng.uniform(-0.5, 0.5, size=4)
+    sc = plate_scene(theta, g["dx"], period=steps * dt)
+    return dict(name=f"plate{n}", grid=g, scene=sc,
+                u0=gaussian_faces(g, sigma, seed + 1000), project_initial=True,
+                steps=steps, tol=tol, loss="kinetic_energy")
+
+
+def config_spheres(n=256, *, seed=0, count=64, tol=1e-8):
+    """Single projection: 64 static spheres, divergent N(0, 1) velocity."""
+    g = make_grid(n, 0.01)
+    return dict(name=f"spheres{n}", grid=g, scene=spheres_scene(seed, count),
+                u0=gaussian_faces(g, 1.0, seed + 2000), project_initial=True,
+                steps=0, tol=tol, loss="kinetic_energy")
+
+
+def serving_mix(seed=0, count=512, rate_per_ms=0.5,
+                sizes=(32, 64, 96, 128, 192), adjoint_frac=0.3):
+    """Seeded serving workload: Poisson arrivals of episode requests.
+
+    Returns a list of dicts ``{arrival_ms, n, scene_kind, adjoint, seed}``.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gaps = rng.exponential(1.0 / rate_per_ms, size=count)
+    t = np.cumsum(gaps)
+    out = []
+    kinds = ("sphere", "chamber", "plate")
+    for i in range(count):
+        out.append(dict(arrival_ms=float(t[i]),
+                        n=int(sizes[rng.integers(len(sizes))]),
+                        scene_kind=kinds[rng.integers(3)],
+                        adjoint=bool(rng.uniform() < adjoint_frac),
+                        seed=int(rng.integers(1 << 31))))
+    return out

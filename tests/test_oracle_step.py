@@ -1,0 +1,152 @@
+"""Pins of the oracle's full step, rollout and adjoint (no GPU)."""
+
+import numpy as np
+import pytest
+
+import nf_inputs as I
+from oracle import Grid, mac, project, rasterize
+from oracle import step as S
+
+
+# ------------------------------------------------------ Taylor-Green ----
+
+def _taylor_green_ratio(n, nu=0.01, amp=1e-3, t_end=0.4):
+    dt0 = 0.1 * (1.0 / n) ** 2 / nu
+    steps = int(np.ceil(t_end / dt0))
+    dt = t_end / steps
+    g = Grid(I.make_grid(n, dt, nz=4, periodic=True, nu=nu))
+    U = g.zeros_faces()
+    X0 = mac.face_positions(g, 0) * g.dx
+    X1 = mac.face_positions(g, 1) * g.dx
+    tp = 2 * np.pi
+    U[0] = amp * np.sin(tp * X0[..., 0]) * np.cos(tp * X0[..., 1])
+    U[1] = -amp * np.cos(tp * X1[..., 0]) * np.sin(tp * X1[..., 1])
+    U0 = [u.copy() for u in U]
+    for k in range(steps):
+        U, _ = S.step(g, I.empty_scene(), U, k, 1e-12)
+    num = sum(np.sum(a * b) for a, b in zip(U, U0)) / sum(np.sum(b * b) for b in U0)
+    return num, np.exp(-8 * np.pi ** 2 * nu * t_end)
+
+
+def test_taylor_green_decay_converges_to_analytic():
+    r16, ex = _taylor_green_ratio(16)
+    r32, _ = _taylor_green_ratio(32)
+    e16, e32 = abs(r16 - ex) / ex, abs(r32 - ex) / ex
+    assert e32 < 0.02
+    assert e32 < e16
+
+
+# ----------------------------------------------------------- shell -----
+
+def test_fluid_inside_a_translating_shell_moves_rigidly():
+    n = 16
+    g = Grid(I.make_grid(n, 0.02))
+    V = np.array([0.3, -0.2, 0.1])
+    sc = I.shell_scene((0.2, 0.2, 0.2), (0.8, 0.8, 0.8), 3.0 / n, V)
+    U = g.zeros_faces()
+    for d in range(3):
+        X = mac.face_positions(g, d) * g.dx
+        inside = np.all((X > 0.2) & (X < 0.8), axis=-1)
+        U[d][inside] = V[d]
+    for k in range(3):
+        U, tape = S.step(g, sc, U, k, 1e-13)
+    t = tape["t"]
+    for d in range(3):
+        X = mac.face_positions(g, d) * g.dx
+        deep = np.all((X > 0.2 + V * t + 3.0 / n) & (X < 0.8 + V * t - 3.0 / n), axis=-1)
+        assert deep.sum() > 20
+        np.testing.assert_allclose(U[d][deep], V[d], rtol=0, atol=1e-12)
+
+
+# --------------------------------------------------- projection adjoint ----
+
+def _proj_case(seed=0):
+    cfg = I.config_plate(10)
+    g = Grid(cfg["grid"])
+    alpha = rasterize.fractions(g, cfg["scene"], 0.05)
+    us = rasterize.face_solid_velocity(g, cfg["scene"], 0.05)
+    rng = np.random.default_rng(seed)
+    Uh = [rng.standard_normal(g.face_shape(d)) for d in range(3)]
+    W = [rng.standard_normal(g.face_shape(d)) for d in range(3)]
+    return g, alpha, us, Uh, W, rng
+
+
+def _dot(a, b):
+    return sum(float(np.sum(x * y)) for x, y in zip(a, b))
+
+
+def test_projection_adjoint_in_velocity_and_solid_velocity():
+    g, alpha, us, Uh, W, rng = _proj_case(1)
+    tol = 1e-14
+    U0, P0, _ = project.project(g, alpha, us, Uh, tol)
+    gUh, gS, gUs, y, _ = project.project_adjoint(g, alpha, us, Uh, P0, W, tol)
+    dU = [rng.standard_normal(u.shape) for u in Uh]
+    dUs = [rng.standard_normal(u.shape) * (~mac.boundary_face_mask(g, d)) for d, u in enumerate(us)]
+    U1, _, _ = project.project(g, alpha, us, [a + b for a, b in zip(Uh, dU)], tol)
+    lhs = _dot(W, [a - b for a, b in zip(U1, U0)])
+    assert abs(lhs - _dot(gUh, dU)) <= 1e-9 * abs(lhs)
+    U2, _, _ = project.project(g, alpha, [a + b for a, b in zip(us, dUs)], Uh, tol)
+    lhs = _dot(W, [a - b for a, b in zip(U2, U0)])
+    assert abs(lhs - _dot(gUs, dUs)) <= 1e-9 * abs(lhs)
+
+
+def test_projection_adjoint_in_fractions():
+    g, alpha, us, Uh, W, rng = _proj_case(2)
+    tol = 1e-14
+    U0, P0, _ = project.project(g, alpha, us, Uh, tol)
+    _, gS, _, _, _ = project.project_adjoint(g, alpha, us, Uh, P0, W, tol)
+    # perturb only cut faces, keeping the active set fixed
+    dA = [rng.standard_normal(a.shape) * ((a > 0.05) & (a < 0.95)) for a in alpha]
+    h = 1e-6
+    Up, _, _ = project.project(g, [a + h * b for a, b in zip(alpha, dA)], us, Uh, tol)
+    Um, _, _ = project.project(g, [a - h * b for a, b in zip(alpha, dA)], us, Uh, tol)
+    fd = _dot(W, [a - b for a, b in zip(Up, Um)]) / (2 * h)
+    assert abs(fd - _dot(gS, dA)) <= 1e-6 * abs(fd)
+
+
+# ------------------------------------------------- rollout gradients ----
+
+@pytest.mark.parametrize("name", ["sphere", "plate", "chamber"])
+def test_rollout_gradient_matches_central_differences(name):
+    cfg = {"sphere": lambda: I.config_sphere(12, steps=3),
+           "plate": lambda: I.config_plate(12, steps=4),
+           "chamber": lambda: I.config_chamber(16, steps=4, duct_half_cells=2)}[name]()
+    J, g_adj, _ = S.loss_and_grad(cfg, tol=1e-12)
+    g_fd = S.fd_gradient(cfg, h=1e-4, tol=1e-12)
+    err = np.linalg.norm(g_adj - g_fd) / np.linalg.norm(g_fd)
+    assert err < 1e-3, (g_adj, g_fd)
+
+
+def _active_boundary_flux(g, alpha, us):
+    """sum over faces with exactly one active neighbour (outlet excluded) of
+    (a_high - a_low) u_s: by incompressibility this equals the outflow."""
+    act = project.active_cells(g, alpha)
+    tot = 0.0
+    for d in range(3):
+        ax = mac.axis_of(d)
+        pad = [(0, 0)] * 3
+        pad[ax] = (1, 1)
+        a = np.pad(act, pad).astype(np.float64)
+        lo = [slice(None)] * 3
+        hi = [slice(None)] * 3
+        lo[ax] = slice(0, -1)
+        hi[ax] = slice(1, None)
+        sgn = a[tuple(hi)] - a[tuple(lo)]
+        sgn[mac.outlet_face_mask(g, d)] = 0.0
+        tot += float(np.sum(sgn * us[d]))
+    return tot
+
+
+def test_chamber_outflow_equals_geometric_volume_rate_and_its_gradient():
+    cfg = I.config_chamber(16, steps=4, duct_half_cells=2)
+    J, g_adj, info = S.loss_and_grad(cfg, tol=1e-13)
+    g = Grid(cfg["grid"])
+    t = cfg["steps"] * g.dt
+    alpha = rasterize.fractions(g, cfg["scene"], t)
+    us, dus = rasterize.face_solid_velocity(g, cfg["scene"], t, with_grad=True)
+    geo = g.dx ** 2 * _active_boundary_flux(g, alpha, us)
+    assert abs(J - geo) <= 1e-9 * abs(J)
+    K = len(cfg["scene"]["theta"])
+    g_geo = np.array([g.dx ** 2 * _active_boundary_flux(g, alpha, [dus[d][..., k] for d in range(3)])
+                      for k in range(K)])
+    np.testing.assert_allclose(g_adj, g_geo, rtol=1e-7, atol=1e-9 * np.abs(g_geo).max())
