@@ -1,0 +1,261 @@
+/*
+ * nf.h — C ABI of the B300 differentiable cut-cell fluid step library (libnf).
+ *
+ * One time step on a 3D MAC grid (Sec. 2.3.1 of arXiv 2405.14903): RK2
+ * semi-Lagrangian advection (Eq. advection_matrix; Appendix B, Eqs.
+ * advection_1/advection_2), rasterisation of a parametric solid into per-face
+ * fluid fractions alpha (Sec. 2.3.1, Projection), and the cut-cell pressure
+ * projection (Eq. projection_matrix, Eq. u_next_matrix) solved by a
+ * matrix-free multigrid-preconditioned conjugate gradient; plus the adjoint
+ * of the step (Sec. 2.3.2 and 2.3.3) for back-propagation through a rollout.
+ *
+ * Conventions shared by every call:
+ *  - Status: every call returns an int status (NF_OK = 0 or an NF_E_* code);
+ *    nothing throws across the ABI and no kernel traps. nf_status_string()
+ *    names a code; nf_last_error() gives the calling thread's last message.
+ *  - Layout: a grid has nx*ny*nz cells of edge dx. Face arrays are separate
+ *    per component, x fastest: ux is [nz][ny][nx+1], uy [nz][ny+1][nx],
+ *    uz [nz+1][ny][nx]; cell arrays are [nz][ny][nx]. Pointers given in a
+ *    3-array are (x, y, z) components.
+ *  - Memory: `mem` selects NF_MEM_DEVICE (device pointers on the context's
+ *    device, e.g. torch data_ptr()) or NF_MEM_HOST (host pointers; the
+ *    library copies them, pinned memory is faster). Caller buffers are
+ *    borrowed for the duration of the call only; nothing is retained.
+ *  - Ownership: the library owns all episode state (velocity, pressure,
+ *    fractions, the multigrid hierarchy, the checkpoint tape) in device
+ *    memory, freed by nf_episode_destroy / nf_destroy.
+ *  - Streams: all device work of a context is ordered on its stream. Calls
+ *    return once their results are in the destination (they synchronise the
+ *    stream when they must read solver status on the host).
+ *  - Threads: a context is not thread safe; use one context per host thread.
+ */
+#ifndef NF_H
+#define NF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define NF_OK 0
+#define NF_E_INVALID 1       /* bad argument, unknown episode id, bad size  */
+#define NF_E_OOM 2           /* HBM budget exceeded or device alloc failed */
+#define NF_E_NOT_CONVERGED 3 /* iteration cap hit; stats hold iters, resid */
+#define NF_E_DIVERGED 4      /* NaN or Inf met in a residual               */
+#define NF_E_TIMEOUT 5       /* a bounded device wait expired              */
+#define NF_E_CUDA 6          /* a CUDA runtime call failed                 */
+#define NF_E_STATE 7         /* call invalid in the episode's state        */
+
+/* ----------------------------------------------------------------- enums */
+#define NF_PREC_FP64 0   /* FP64 fields, vectors and multigrid            */
+#define NF_PREC_FP32 1   /* FP32 fields, vectors and multigrid            */
+#define NF_PREC_MIXED 2  /* FP32 fields; FP32 PCG with BF16 coarse-level
+                            coefficients; FP64 dots and FP64 iterative
+                            refinement of r = b - A x                     */
+#define NF_SOLVER_CG 0    /* unpreconditioned conjugate gradient           */
+#define NF_SOLVER_MGPCG 1 /* geometric multigrid V-cycle preconditioned CG */
+
+#define NF_F32 0
+#define NF_F64 1
+#define NF_MEM_DEVICE 0
+#define NF_MEM_HOST 1
+
+#define NF_SCENE_NONE 0    /* no solid                                      */
+#define NF_SCENE_SPHERE 1  /* sphere translating with velocity theta[0..2]  */
+#define NF_SCENE_CHAMBER 2 /* ellipsoid chamber, radius modulated by 8
+                              Fourier coefficients theta, union a duct    */
+#define NF_SCENE_PLATE 3   /* plate rotating about z, 4 angle knots theta   */
+#define NF_SCENE_SPHERES 4 /* static spheres, no parameters                */
+
+#define NF_LOSS_KINETIC 0 /* J = 1/2 sum_faces u^2 dx^3                     */
+#define NF_LOSS_OUTFLOW 1 /* J = sum over outlet faces of u_x dx^2         */
+
+#define NF_MAX_PARAMS 8
+
+/* ------------------------------------------------------------- structures */
+typedef struct nf_ctx nf_ctx;
+
+typedef struct nf_config {
+  int device;             /* CUDA device ordinal                              */
+  void *stream;           /* cudaStream_t to order work on; NULL: the library
+                             creates its own stream. Pass cudaStreamLegacy
+                             ((void *)1) for the legacy default stream.       */
+  int precision;          /* NF_PREC_*                                        */
+  int solver;             /* NF_SOLVER_*                                      */
+  double tol;             /* stop when ||b - A P||_2 / ||b||_2 <= tol (FP64) */
+  int max_iters;          /* cap on preconditioned iterations per solve       */
+  double inner_tol;       /* MIXED: residual reduction per FP32 inner solve   */
+  int mg_smooth;          /* red-black Gauss-Seidel sweeps before and after   */
+  int mg_coarsest;        /* stop coarsening at this many cells per edge      */
+  int advect_order;       /* 2 = RK2 midpoint backtrace, 1 = forward Euler    */
+  int checkpoint_every;   /* rollout checkpoint interval C (steps)            */
+  size_t hbm_budget;      /* admission budget for episode state; 0 = none     */
+} nf_config;
+
+typedef struct nf_grid {
+  int nx, ny, nz;         /* cells per axis (each >= 4)                       */
+  double dx;              /* cell edge                                        */
+  double dt;              /* time step                                        */
+  double rho;             /* density (1 in every shipped scene)               */
+  int outlet;             /* 0: closed box; 1: open patch on the high-x wall  */
+  int outlet_j0, outlet_k0, outlet_w, outlet_h; /* patch cells in y and z   */
+} nf_grid;
+
+typedef struct nf_scene {
+  int kind;               /* NF_SCENE_*                                       */
+  int K;                  /* parameters in theta (0..NF_MAX_PARAMS)           */
+  double theta[NF_MAX_PARAMS];
+  /* kind constants: SPHERE: centre[0..2], radius[3]. CHAMBER: centre[0..2],
+     axes[3..5], period[6], duct_x0[7], duct_half[8]. PLATE: centre[0..2],
+     half extents[3..5], period[6] (knots at 0, T/3, 2T/3, T).             */
+  double consts[16];
+  const double *spheres;  /* SPHERES: nspheres x (cx, cy, cz, r), host memory */
+  int nspheres;
+} nf_scene;
+
+typedef struct nf_step_stats {
+  int steps;              /* time steps performed by the call                 */
+  int solves;             /* linear solves performed                          */
+  int iters;              /* preconditioned iterations, summed over solves    */
+  int max_iters;          /* most iterations of a single solve                */
+  int outer;              /* FP64 refinement passes, summed over solves       */
+  double rel_residual;    /* worst final FP64 relative residual of the call   */
+} nf_step_stats;
+
+/* ------------------------------------------------------------- lifecycle */
+
+/* Fill *cfg with defaults: device 0, own stream, MIXED, MGPCG, tol 1e-6,
+   max_iters 500, inner_tol 1e-3, mg_smooth 2, mg_coarsest 4, RK2,
+   checkpoint_every 10, no budget. */
+int nf_config_default(nf_config *cfg);
+
+/* Create a context on cfg->device. *out receives the handle. */
+int nf_create(nf_ctx **out, const nf_config *cfg);
+
+/* Free every episode and the context. */
+int nf_destroy(nf_ctx *ctx);
+
+/* The calling thread's last error message (valid until its next call). */
+const char *nf_last_error(nf_ctx *ctx);
+const char *nf_status_string(int status);
+
+/* Wait for all work of the context's stream. */
+int nf_synchronize(nf_ctx *ctx);
+
+/* ---------------------------------------------------------------- episode */
+
+/* Create an episode: a grid, a scene with parameters theta, zero velocity,
+   step counter 0. Admission: NF_E_OOM when its device state would exceed the
+   context's HBM budget. Geometry is evaluated analytically at
+   t_{n+1} = (n + 1) dt in every step (Sec. 2.3.1, Projection). */
+int nf_episode_create(nf_ctx *ctx, const nf_grid *g, const nf_scene *s,
+                      int64_t *id);
+int nf_episode_destroy(nf_ctx *ctx, int64_t id);
+
+/* Device bytes held by the episode (fields, hierarchy, tape so far). */
+int nf_episode_bytes(nf_ctx *ctx, int64_t id, size_t *bytes);
+
+/* Replace the scene parameters theta (K values, host memory). Clears the tape. */
+int nf_set_params(nf_ctx *ctx, int64_t id, const double *theta, int K);
+
+/* Set the velocity u (3 face arrays of dtype NF_F32/NF_F64 in `mem`), reset
+   the step counter to 0 and clear the tape. With project != 0 the field is
+   first made divergence free with the t = 0 cut-cell system (projection
+   only, no advection); that projection is recorded and is part of the
+   adjoint computed by nf_backward. */
+int nf_set_velocity(nf_ctx *ctx, int64_t id, const void *const u[3],
+                    int dtype, int mem, int project, nf_step_stats *st);
+
+/* Advance nsteps time steps: rasterise alpha and u_s at t_{n+1}, advect
+   (Eq. advection_matrix), solve Eq. projection_matrix, apply the blended
+   update U = S (U^ - c G P) + (I - S) U_s (c = dt / (rho dx)). In a closed
+   box (no outlet) the right-hand side is projected to zero mean over the
+   active cells and the pressure is returned with zero mean there. Records
+   checkpoints every checkpoint_every steps for nf_backward. Returns
+   NF_E_NOT_CONVERGED if a solve hit max_iters (the step is still applied). */
+int nf_step(nf_ctx *ctx, int64_t id, int nsteps, nf_step_stats *st);
+
+/* Loss of the current velocity: J (host double) and optionally dJ/dU into
+   gU (device or host arrays, may be NULL). */
+int nf_loss(nf_ctx *ctx, int64_t id, int loss_kind, double *J,
+            void *const gU[3], int dtype, int mem);
+
+/* Back-propagate through the most recent unreverted step (Sec. 2.3.2,
+   2.3.3): from dJ/dU^{n+1} (gU_next) compute dJ/dU^n (gU_prev, may alias
+   gU_next) and add that step's dJ/dtheta into g_theta (K host doubles).
+   Recomputes the step's segment from its checkpoint when needed. After the
+   last time step it reverts the initial projection, if one was recorded.
+   NF_E_STATE when nothing is left to revert. */
+int nf_backward_step(nf_ctx *ctx, int64_t id, const void *const gU_next[3],
+                     void *const gU_prev[3], int dtype, int mem,
+                     double *g_theta, nf_step_stats *st);
+
+/* Back-propagate through the whole recorded rollout: gU_final = dJ/dU^T,
+   gU0 (may be NULL) receives dJ/dU^0 of the velocity given to
+   nf_set_velocity, g_theta (K host doubles) is overwritten with dJ/dtheta.
+   Uses checkpoints and per-segment recomputation. */
+int nf_backward(nf_ctx *ctx, int64_t id, const void *const gU_final[3],
+                void *const gU0[3], int dtype, int mem, double *g_theta,
+                nf_step_stats *st);
+
+/* ---------------------------------------------------------------- queries */
+int nf_get_velocity(nf_ctx *ctx, int64_t id, void *const u[3], int dtype,
+                    int mem);
+/* Pressure of the last solve (cell array). */
+int nf_get_pressure(nf_ctx *ctx, int64_t id, void *p, int dtype, int mem);
+/* Face fractions alpha of the last step (3 face arrays). */
+int nf_get_fractions(nf_ctx *ctx, int64_t id, void *const a[3], int dtype,
+                     int mem);
+/* Advected velocity U^ of the last step (3 face arrays). */
+int nf_get_advected(nf_ctx *ctx, int64_t id, void *const u[3], int dtype,
+                    int mem);
+/* Step counter n (the velocity is U^n). */
+int nf_get_step(nf_ctx *ctx, int64_t id, int *n);
+
+/* Kernel launches issued by this context since creation (a counter of the
+   library's own kernels, used to report launches per timed region). */
+int nf_launch_count(nf_ctx *ctx, int64_t *count);
+
+/* ------------------------------------------------------------- profiling */
+/* Kernel classes that nf_profile can time (CUDA events on the context's
+   stream bracketing every launch of the class). */
+#define NF_K_RASTERIZE 0
+#define NF_K_ADVECT 1
+#define NF_K_RHS 2
+#define NF_K_UPDATE 3
+#define NF_K_LOSS 4
+#define NF_K_ADJ_GP 5
+#define NF_K_ADJ_FACE 6
+#define NF_K_ADJ_ADVECT 7
+#define NF_K_RESIDUAL64 8
+#define NF_K_AXPY64 9
+#define NF_K_CG_INIT 10
+#define NF_K_APPLY_DOT 11
+#define NF_K_CG_XR 12
+#define NF_K_CG_RZ 13
+#define NF_K_CG_D 14
+#define NF_K_MG_COARSEN 15
+#define NF_K_MG_SMOOTH 16     /* coarse levels */
+#define NF_K_MG_RESIDUAL 17
+#define NF_K_MG_RESTRICT 18
+#define NF_K_MG_PROLONG 19
+#define NF_K_MG_CHAIN 20
+#define NF_K_CAST 21
+#define NF_K_MG_SMOOTH0 22    /* finest level  */
+#define NF_K_GAUGE 23
+#define NF_K_COUNT 24
+
+/* Start timing launches of kernel class `kclass` (NF_K_*), or of every class
+   with kclass = -1; kclass = -2 stops. Resets the accumulated totals. */
+int nf_profile(nf_ctx *ctx, int kclass);
+/* Accumulated launches and device milliseconds of one class since
+   nf_profile (synchronises the stream). */
+int nf_profile_read(nf_ctx *ctx, int kclass, int64_t *launches, double *ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NF_H */

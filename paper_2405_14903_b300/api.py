@@ -1,0 +1,307 @@
+"""Python binding of libnf: argument marshalling over the C ABI.
+
+``Context`` wraps ``nf_ctx`` (device, stream, precision and solver
+settings); ``Episode`` wraps one simulated grid. Device arrays are torch
+tensors (their ``data_ptr`` is passed through); host arrays are NumPy arrays
+or CPU tensors. Grid and scene descriptions are the plain dictionaries of
+``nf_inputs``. Every call checks the returned status and raises
+:class:`NFError` on failure.
+
+Stream ordering: by default a context runs on torch's current stream of its
+device, so library work and torch work on the same stream are ordered. The
+legacy default stream (handle 0 in torch) is passed as ``cudaStreamLegacy``
+because the C ABI reads a null stream as "create a private stream".
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import warnings
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+lib = L.lib
+
+
+class NFError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libnf status {status} ({lib.nf_status_string(status).decode()}): {msg}")
+        self.status = status
+
+
+class NotConvergedWarning(RuntimeWarning):
+    pass
+
+
+def _check(status, ctx=None, allow_not_converged=True):
+    if status == L.NF_OK:
+        return status
+    msg = lib.nf_last_error(ctx).decode() if ctx is not None else ""
+    if status == L.NF_E_NOT_CONVERGED and allow_not_converged:
+        warnings.warn(f"solver did not reach its tolerance: {msg}", NotConvergedWarning)
+        return status
+    raise NFError(status, msg)
+
+
+def grid_struct(desc):
+    g = L.Grid()
+    g.nx, g.ny, g.nz = desc["nx"], desc["ny"], desc["nz"]
+    g.dx, g.dt, g.rho = desc["dx"], desc["dt"], desc.get("rho", 1.0)
+    if desc.get("periodic", False):
+        raise ValueError("the CUDA path implements closed boxes (walls and an outlet patch)")
+    if desc.get("nu", 0.0):
+        raise ValueError("the CUDA path implements the inviscid step (nu = 0)")
+    o = desc.get("outlet")
+    if o:
+        if o["axis"] != 0 or o["side"] != 1:
+            raise ValueError("outlet patches are on the high-x wall")
+        g.outlet, g.outlet_j0, g.outlet_k0, g.outlet_w, g.outlet_h = 1, o["j0"], o["k0"], o["w"], o["h"]
+    return g
+
+
+def scene_struct(sc):
+    s = L.Scene()
+    kind = sc["kind"]
+    if kind not in L.SCENE:
+        raise ValueError(f"scene kind {kind!r} is not implemented on the GPU")
+    s.kind = L.SCENE[kind]
+    th = list(sc.get("theta", []))
+    s.K = len(th)
+    for k, v in enumerate(th):
+        s.theta[k] = v
+    consts = []
+    keep = None
+    if kind == "sphere":
+        consts = list(sc["centre"]) + [sc["radius"]]
+    elif kind == "chamber":
+        consts = list(sc["centre"]) + list(sc["axes"]) + [sc["period"], sc["duct_x0"], sc["duct_half"]]
+    elif kind == "plate":
+        consts = list(sc["centre"]) + list(sc["half"]) + [sc["period"]]
+    elif kind == "spheres":
+        keep = np.ascontiguousarray(np.asarray(sc["spheres"], dtype=np.float64).reshape(-1, 4))
+        s.spheres = keep.ctypes.data_as(C.POINTER(C.c_double))
+        s.nspheres = keep.shape[0]
+    for k, v in enumerate(consts):
+        s.consts[k] = v
+    return s, keep
+
+
+def _ptrs(arrs):
+    """(pointer triple, dtype code, memory kind, keep-alive list)."""
+    arrs = list(arrs)
+    if isinstance(arrs[0], torch.Tensor):
+        dt = arrs[0].dtype
+        if dt not in (torch.float32, torch.float64):
+            raise TypeError("arrays must be float32 or float64")
+        ts = [a.contiguous() for a in arrs]
+        if not all(t.dtype == dt for t in ts):
+            raise TypeError("all components must share a dtype")
+        code = L.NF_F64 if dt == torch.float64 else L.NF_F32
+        mem = L.NF_MEM_DEVICE if ts[0].is_cuda else L.NF_MEM_HOST
+        return L.P3(*[t.data_ptr() for t in ts]), code, mem, ts
+    nps = [np.ascontiguousarray(a) for a in arrs]
+    dt = nps[0].dtype
+    if dt not in (np.float32, np.float64) or not all(a.dtype == dt for a in nps):
+        raise TypeError("host arrays must all be float32 or all float64")
+    code = L.NF_F64 if dt == np.float64 else L.NF_F32
+    return L.P3(*[a.ctypes.data for a in nps]), code, L.NF_MEM_HOST, nps
+
+
+class Context:
+    """An ``nf_ctx``: one device, one stream, one precision/solver setting."""
+
+    def __init__(self, precision="mixed", solver="mgpcg", tol=1e-6, max_iters=500,
+                 inner_tol=1e-3, mg_smooth=2, mg_coarsest=4, advect_order=2,
+                 checkpoint_every=10, hbm_budget=0, device=0, stream=None):
+        cfg = L.Config()
+        _check(lib.nf_config_default(C.byref(cfg)))
+        cfg.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device).cuda_stream
+            if not stream:
+                stream = L.CUDA_STREAM_LEGACY
+        cfg.stream = stream
+        cfg.precision = L.PREC[precision]
+        cfg.solver = L.SOLVER[solver]
+        cfg.tol = tol
+        cfg.max_iters = max_iters
+        cfg.inner_tol = inner_tol
+        cfg.mg_smooth = mg_smooth
+        cfg.mg_coarsest = mg_coarsest
+        cfg.advect_order = advect_order
+        cfg.checkpoint_every = checkpoint_every
+        cfg.hbm_budget = int(hbm_budget)
+        self.precision = precision
+        self.device = device
+        self._h = C.c_void_p()
+        _check(lib.nf_create(C.byref(self._h), C.byref(cfg)))
+        self.field_dtype = torch.float64 if precision == "fp64" else torch.float32
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib.nf_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def synchronize(self):
+        _check(lib.nf_synchronize(self._h), self._h)
+
+    def launches(self):
+        n = C.c_int64()
+        _check(lib.nf_launch_count(self._h, C.byref(n)), self._h)
+        return n.value
+
+    def profile(self, kclass):
+        """Time launches of one kernel class (name), 'all', or None to stop."""
+        code = -2 if kclass is None else (-1 if kclass == "all" else L.KCLASS.index(kclass))
+        _check(lib.nf_profile(self._h, code), self._h)
+
+    def profile_read(self, kclass):
+        """(launches, device ms) of a kernel class since :meth:`profile`."""
+        n, ms = C.c_int64(), C.c_double()
+        _check(lib.nf_profile_read(self._h, L.KCLASS.index(kclass), C.byref(n), C.byref(ms)), self._h)
+        return n.value, ms.value
+
+    def episode(self, grid_desc, scene):
+        return Episode(self, grid_desc, scene)
+
+
+class Episode:
+    """One simulated grid (``nf_episode_*``)."""
+
+    def __init__(self, ctx: Context, grid_desc, scene):
+        self.ctx = ctx
+        self.id = None
+        self.grid = dict(grid_desc)
+        self.scene = dict(scene)
+        g = grid_struct(grid_desc)
+        s, keep = scene_struct(scene)
+        self.K = s.K
+        eid = C.c_int64()
+        _check(lib.nf_episode_create(ctx.handle, C.byref(g), C.byref(s), C.byref(eid)), ctx.handle)
+        self.id = eid.value
+        nx, ny, nz = g.nx, g.ny, g.nz
+        self.face_shapes = [(nz, ny, nx + 1), (nz, ny + 1, nx), (nz + 1, ny, nx)]
+        self.cell_shape = (nz, ny, nx)
+
+    def close(self):
+        if self.id is not None and self.ctx.handle:
+            lib.nf_episode_destroy(self.ctx.handle, self.id)
+        self.id = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def _c(self):
+        return self.ctx.handle
+
+    def bytes(self):
+        b = C.c_size_t()
+        _check(lib.nf_episode_bytes(self._c, self.id, C.byref(b)), self._c)
+        return b.value
+
+    def set_params(self, theta):
+        th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+        _check(lib.nf_set_params(self._c, self.id, th.ctypes.data_as(C.POINTER(C.c_double)), len(th)), self._c)
+        self.scene["theta"] = list(th)
+
+    def set_velocity(self, u, project=False):
+        p, code, mem, keep = _ptrs(u)
+        st = L.StepStats()
+        _check(lib.nf_set_velocity(self._c, self.id, p, code, mem, int(bool(project)), C.byref(st)), self._c)
+        return st.as_dict()
+
+    def step(self, n=1):
+        st = L.StepStats()
+        _check(lib.nf_step(self._c, self.id, int(n), C.byref(st)), self._c)
+        return st.as_dict()
+
+    def _faces_out(self, dtype, host):
+        if host:
+            npdt = np.float64 if dtype == torch.float64 else np.float32
+            return [np.empty(s, dtype=npdt) for s in self.face_shapes]
+        return [torch.empty(s, dtype=dtype, device=f"cuda:{self.ctx.device}") for s in self.face_shapes]
+
+    def loss(self, kind, want_grad=False, dtype=None):
+        J = C.c_double()
+        if want_grad:
+            gU = self._faces_out(dtype or self.ctx.field_dtype, host=False)
+            p, code, mem, _ = _ptrs(gU)
+            _check(lib.nf_loss(self._c, self.id, L.LOSS[kind], C.byref(J), p, code, mem), self._c)
+            return J.value, gU
+        _check(lib.nf_loss(self._c, self.id, L.LOSS[kind], C.byref(J), None, L.NF_F32,
+                           L.NF_MEM_DEVICE), self._c)
+        return J.value
+
+    def backward(self, gU_final, want_gU0=True, host=False):
+        """BPTT through the recorded rollout: (dJ/dtheta, dJ/dU^0, stats)."""
+        p, code, mem, keep = _ptrs(gU_final)
+        dtype = torch.float64 if code == L.NF_F64 else torch.float32
+        out, po = None, None
+        if want_gU0:
+            out = self._faces_out(dtype, host or mem == L.NF_MEM_HOST)
+            po, ocode, omem, okeep = _ptrs(out)
+            if ocode != code or omem != mem:
+                raise ValueError("gradient input and output must share dtype and memory kind")
+        gth = (C.c_double * max(1, self.K))()
+        st = L.StepStats()
+        _check(lib.nf_backward(self._c, self.id, p, po, code, mem, gth, C.byref(st)), self._c)
+        return np.array(gth[:self.K]), out, st.as_dict()
+
+    def backward_step(self, gU_next):
+        """Revert one step: (dJ/dU^n, this step's dJ/dtheta, stats)."""
+        p, code, mem, keep = _ptrs(gU_next)
+        dtype = torch.float64 if code == L.NF_F64 else torch.float32
+        out = self._faces_out(dtype, mem == L.NF_MEM_HOST)
+        po, *_ = _ptrs(out)
+        gth = (C.c_double * max(1, self.K))()
+        st = L.StepStats()
+        _check(lib.nf_backward_step(self._c, self.id, p, po, code, mem, gth, C.byref(st)), self._c)
+        return out, np.array(gth[:self.K]), st.as_dict()
+
+    def _get_faces(self, fn, dtype, host):
+        out = self._faces_out(dtype, host)
+        p, code, mem, _ = _ptrs(out)
+        _check(fn(self._c, self.id, p, code, mem), self._c)
+        return out
+
+    def velocity(self, dtype=torch.float64, host=False):
+        return self._get_faces(lib.nf_get_velocity, dtype, host)
+
+    def advected(self, dtype=torch.float64, host=False):
+        return self._get_faces(lib.nf_get_advected, dtype, host)
+
+    def fractions(self, dtype=torch.float64, host=False):
+        return self._get_faces(lib.nf_get_fractions, dtype, host)
+
+    def pressure(self, dtype=torch.float64, host=False):
+        code = L.NF_F64 if dtype == torch.float64 else L.NF_F32
+        if host:
+            out = np.empty(self.cell_shape, dtype=np.float64 if dtype == torch.float64 else np.float32)
+            ptr, mem = out.ctypes.data, L.NF_MEM_HOST
+        else:
+            out = torch.empty(self.cell_shape, dtype=dtype, device=f"cuda:{self.ctx.device}")
+            ptr, mem = out.data_ptr(), L.NF_MEM_DEVICE
+        _check(lib.nf_get_pressure(self._c, self.id, ptr, code, mem), self._c)
+        return out
+
+    def step_index(self):
+        n = C.c_int()
+        _check(lib.nf_get_step(self._c, self.id, C.byref(n)), self._c)
+        return n.value

@@ -1,0 +1,407 @@
+// The C ABI of libnf (declared in include/nf.h): argument checking, context
+// and episode bookkeeping, HBM admission, kernel-class profiling and error
+// plumbing. No exception crosses the ABI; every entry point returns a status.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <new>
+#include <string>
+
+#include "episode.h"
+#include "util.h"
+
+namespace nf {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+const std::string &get_error() { return g_err; }
+int cuda_fail(cudaError_t e, const char *what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? NF_E_OOM : NF_E_CUDA;
+}
+
+int Alloc::get(void **p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 16;
+  const cudaError_t e = cudaMalloc(p, n);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return cuda_fail(e, "cudaMalloc");
+  }
+  ptrs.push_back(*p);
+  bytes += n;
+  return NF_OK;
+}
+
+void Alloc::free_all() {
+  for (void *p : ptrs) cudaFree(p);
+  ptrs.clear();
+  bytes = 0;
+}
+
+// ------------------------------------------------------------ profiling ---
+static constexpr size_t kProfSlots = 4096;
+
+void prof_begin(Prof *p, int kclass, cudaStream_t s, int *slot) {
+  *slot = -1;
+  if (p->kclass != -1 && p->kclass != kclass) return;
+  if (p->ev.empty()) {
+    p->ev.resize(2 * kProfSlots);
+    p->cls.resize(kProfSlots);
+    for (auto &e : p->ev) cudaEventCreate(&e);
+  }
+  if (p->used == kProfSlots) p->drain(s);
+  *slot = (int)p->used++;
+  p->cls[*slot] = kclass;
+  cudaEventRecord(p->ev[2 * *slot], s);
+}
+
+void prof_end(Prof *p, int slot, cudaStream_t s) {
+  cudaEventRecord(p->ev[2 * slot + 1], s);
+}
+
+void Prof::drain(cudaStream_t s) {
+  cudaStreamSynchronize(s);
+  for (size_t i = 0; i < used; ++i) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]) == cudaSuccess) {
+      launches[cls[i]] += 1;
+      ms[cls[i]] += t;
+    } else {
+      cudaGetLastError();
+    }
+  }
+  used = 0;
+}
+
+void Prof::reset() {
+  used = 0;
+  for (int k = 0; k < NF_K_COUNT; ++k) {
+    launches[k] = 0;
+    ms[k] = 0.0;
+  }
+}
+
+Prof::~Prof() {
+  for (auto &e : ev) cudaEventDestroy(e);
+}
+
+double Ctx::read_double(const double *dptr) {
+  double *h = (double *)pinned;
+  cudaMemcpyAsync(h, dptr, sizeof(double), cudaMemcpyDeviceToHost, stream);
+  cudaStreamSynchronize(stream);
+  return *h;
+}
+
+void Ctx::read_bytes(void *host, const void *dev, size_t n) {
+  cudaMemcpyAsync(pinned, dev, n, cudaMemcpyDeviceToHost, stream);
+  cudaStreamSynchronize(stream);
+  memcpy(host, pinned, n);
+}
+
+}  // namespace nf
+
+struct nf_ctx {
+  nf::Ctx c;
+  std::map<int64_t, std::unique_ptr<nf::EpisodeBase>> eps;
+  int64_t next_id = 1;
+};
+
+using nf::set_error;
+
+#define GUARD(ctx)                                                    \
+  do {                                                                \
+    if (!(ctx)) {                                                     \
+      set_error("null context");                                      \
+      return NF_E_INVALID;                                            \
+    }                                                                 \
+    cudaError_t _e = cudaSetDevice((ctx)->c.device);                  \
+    if (_e != cudaSuccess) return nf::cuda_fail(_e, "cudaSetDevice"); \
+  } while (0)
+
+static nf::EpisodeBase *find(nf_ctx *ctx, int64_t id) {
+  auto it = ctx->eps.find(id);
+  if (it == ctx->eps.end()) {
+    set_error("unknown episode id " + std::to_string(id));
+    return nullptr;
+  }
+  return it->second.get();
+}
+
+#define EPISODE(ctx, id, e)           \
+  GUARD(ctx);                         \
+  nf::EpisodeBase *e = find(ctx, id); \
+  if (!e) return NF_E_INVALID;
+
+static bool valid_dtype(int dt) { return dt == NF_F32 || dt == NF_F64; }
+static bool valid_mem(int m) { return m == NF_MEM_DEVICE || m == NF_MEM_HOST; }
+
+extern "C" {
+
+int nf_config_default(nf_config *cfg) {
+  if (!cfg) return NF_E_INVALID;
+  cfg->device = 0;
+  cfg->stream = nullptr;
+  cfg->precision = NF_PREC_MIXED;
+  cfg->solver = NF_SOLVER_MGPCG;
+  cfg->tol = 1e-6;
+  cfg->max_iters = 500;
+  cfg->inner_tol = 1e-3;
+  cfg->mg_smooth = 2;
+  cfg->mg_coarsest = 4;
+  cfg->advect_order = 2;
+  cfg->checkpoint_every = 10;
+  cfg->hbm_budget = 0;
+  return NF_OK;
+}
+
+const char *nf_status_string(int s) {
+  switch (s) {
+    case NF_OK: return "ok";
+    case NF_E_INVALID: return "invalid argument";
+    case NF_E_OOM: return "out of device memory or over the HBM budget";
+    case NF_E_NOT_CONVERGED: return "solver did not converge";
+    case NF_E_DIVERGED: return "non-finite value in a residual";
+    case NF_E_TIMEOUT: return "bounded device wait expired";
+    case NF_E_CUDA: return "CUDA runtime error";
+    case NF_E_STATE: return "call invalid in the current state";
+    default: return "unknown status";
+  }
+}
+
+const char *nf_last_error(nf_ctx *) { return nf::get_error().c_str(); }
+
+int nf_create(nf_ctx **out, const nf_config *cfg) {
+  if (!out || !cfg) {
+    set_error("nf_create: null argument");
+    return NF_E_INVALID;
+  }
+  *out = nullptr;
+  if (cfg->precision < NF_PREC_FP64 || cfg->precision > NF_PREC_MIXED ||
+      (cfg->solver != NF_SOLVER_CG && cfg->solver != NF_SOLVER_MGPCG) ||
+      !(cfg->tol > 0) || cfg->max_iters <= 0 ||
+      (cfg->advect_order != 1 && cfg->advect_order != 2) ||
+      cfg->checkpoint_every <= 0 || cfg->mg_smooth < 0) {
+    set_error("nf_create: invalid configuration");
+    return NF_E_INVALID;
+  }
+  nf_ctx *ctx = new (std::nothrow) nf_ctx();
+  if (!ctx) return NF_E_OOM;
+  ctx->c.cfg = *cfg;
+  if (!(ctx->c.cfg.inner_tol > 0 && ctx->c.cfg.inner_tol < 1)) ctx->c.cfg.inner_tol = 1e-3;
+  ctx->c.device = cfg->device;
+  cudaError_t e = cudaSetDevice(cfg->device);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return nf::cuda_fail(e, "cudaSetDevice");
+  }
+  if (cfg->stream) {
+    ctx->c.stream = (cudaStream_t)cfg->stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&ctx->c.stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete ctx;
+      return nf::cuda_fail(e, "cudaStreamCreate");
+    }
+    ctx->c.own_stream = true;
+  }
+  e = cudaMalloc(&ctx->c.rs.partials, sizeof(double) * nf::kRedBlocks * nf::kMaxWidth);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->c.rs.ticket, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(ctx->c.rs.ticket, 0, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMallocHost(&ctx->c.pinned, 4096);
+  if (e != cudaSuccess) {
+    const int rc = nf::cuda_fail(e, "nf_create allocation");
+    nf_destroy(ctx);
+    return rc;
+  }
+  *out = ctx;
+  return NF_OK;
+}
+
+int nf_destroy(nf_ctx *ctx) {
+  if (!ctx) return NF_E_INVALID;
+  cudaSetDevice(ctx->c.device);
+  if (ctx->c.stream) cudaStreamSynchronize(ctx->c.stream);
+  ctx->eps.clear();
+  if (ctx->c.rs.partials) cudaFree(ctx->c.rs.partials);
+  if (ctx->c.rs.ticket) cudaFree(ctx->c.rs.ticket);
+  if (ctx->c.pinned) cudaFreeHost(ctx->c.pinned);
+  if (ctx->c.own_stream && ctx->c.stream) cudaStreamDestroy(ctx->c.stream);
+  delete ctx;
+  return NF_OK;
+}
+
+int nf_synchronize(nf_ctx *ctx) {
+  GUARD(ctx);
+  const cudaError_t e = cudaStreamSynchronize(ctx->c.stream);
+  if (e != cudaSuccess) return nf::cuda_fail(e, "cudaStreamSynchronize");
+  return NF_OK;
+}
+
+int nf_episode_create(nf_ctx *ctx, const nf_grid *g, const nf_scene *s,
+                      int64_t *id) {
+  GUARD(ctx);
+  if (!g || !s || !id) {
+    set_error("nf_episode_create: null argument");
+    return NF_E_INVALID;
+  }
+  if (g->nx < 4 || g->ny < 4 || g->nz < 4 || !(g->dx > 0) || !(g->dt > 0) ||
+      (int64_t)g->nx * g->ny * g->nz > ((int64_t)1 << 31)) {
+    set_error("nf_episode_create: grid must have >= 4 cells per axis, dx > 0, dt > 0");
+    return NF_E_INVALID;
+  }
+  if (g->outlet && (g->outlet_j0 < 0 || g->outlet_k0 < 0 || g->outlet_w <= 0 ||
+                    g->outlet_h <= 0 || g->outlet_j0 + g->outlet_w > g->ny ||
+                    g->outlet_k0 + g->outlet_h > g->nz)) {
+    set_error("nf_episode_create: outlet patch outside the high-x wall");
+    return NF_E_INVALID;
+  }
+  if (s->kind < NF_SCENE_NONE || s->kind > NF_SCENE_SPHERES) {
+    set_error("nf_episode_create: unknown scene kind");
+    return NF_E_INVALID;
+  }
+  const int want = s->kind == NF_SCENE_SPHERE ? 3 : s->kind == NF_SCENE_CHAMBER ? 8
+                   : s->kind == NF_SCENE_PLATE ? 4 : 0;
+  if (s->K != want) {
+    set_error("nf_episode_create: scene expects " + std::to_string(want) + " parameters");
+    return NF_E_INVALID;
+  }
+  if (s->kind == NF_SCENE_SPHERES && (s->nspheres < 0 || (s->nspheres > 0 && !s->spheres))) {
+    set_error("nf_episode_create: spheres array missing");
+    return NF_E_INVALID;
+  }
+  const size_t need = nf::episode_base_bytes(ctx->c.cfg, *g);
+  if (ctx->c.cfg.hbm_budget && ctx->c.bytes_in_use + need > ctx->c.cfg.hbm_budget) {
+    set_error("nf_episode_create: HBM budget exceeded (admission refused)");
+    return NF_E_OOM;
+  }
+  nf::EpisodeBase *e = nullptr;
+  const int rc = nf::create_episode(&ctx->c, g, s, &e);
+  if (rc != NF_OK) return rc;
+  const int64_t eid = ctx->next_id++;
+  ctx->c.bytes_in_use += e->bytes();
+  ctx->eps[eid].reset(e);
+  *id = eid;
+  return NF_OK;
+}
+
+int nf_episode_destroy(nf_ctx *ctx, int64_t id) {
+  EPISODE(ctx, id, e);
+  cudaStreamSynchronize(ctx->c.stream);
+  const size_t b = e->bytes();
+  ctx->c.bytes_in_use -= std::min(b, ctx->c.bytes_in_use);
+  ctx->eps.erase(id);
+  return NF_OK;
+}
+
+int nf_episode_bytes(nf_ctx *ctx, int64_t id, size_t *bytes) {
+  EPISODE(ctx, id, e);
+  if (!bytes) return NF_E_INVALID;
+  *bytes = e->bytes();
+  return NF_OK;
+}
+
+int nf_set_params(nf_ctx *ctx, int64_t id, const double *theta, int K) {
+  EPISODE(ctx, id, e);
+  if (K > 0 && !theta) return NF_E_INVALID;
+  return e->set_params(theta, K);
+}
+
+int nf_set_velocity(nf_ctx *ctx, int64_t id, const void *const u[3], int dtype,
+                    int mem, int project, nf_step_stats *st) {
+  EPISODE(ctx, id, e);
+  if (!u || !valid_dtype(dtype) || !valid_mem(mem)) {
+    set_error("nf_set_velocity: bad arguments");
+    return NF_E_INVALID;
+  }
+  return e->set_velocity(u, dtype, mem, project, st);
+}
+
+int nf_step(nf_ctx *ctx, int64_t id, int nsteps, nf_step_stats *st) {
+  EPISODE(ctx, id, e);
+  return e->step(nsteps, st);
+}
+
+int nf_loss(nf_ctx *ctx, int64_t id, int loss_kind, double *J,
+            void *const gU[3], int dtype, int mem) {
+  EPISODE(ctx, id, e);
+  if (!valid_dtype(dtype) || !valid_mem(mem)) return NF_E_INVALID;
+  return e->loss(loss_kind, J, gU, dtype, mem);
+}
+
+int nf_backward_step(nf_ctx *ctx, int64_t id, const void *const gU_next[3],
+                     void *const gU_prev[3], int dtype, int mem,
+                     double *g_theta, nf_step_stats *st) {
+  EPISODE(ctx, id, e);
+  if (!gU_next || !valid_dtype(dtype) || !valid_mem(mem)) return NF_E_INVALID;
+  return e->backward_step(gU_next, gU_prev, dtype, mem, g_theta, st);
+}
+
+int nf_backward(nf_ctx *ctx, int64_t id, const void *const gU_final[3],
+                void *const gU0[3], int dtype, int mem, double *g_theta,
+                nf_step_stats *st) {
+  EPISODE(ctx, id, e);
+  if (!gU_final || !valid_dtype(dtype) || !valid_mem(mem)) return NF_E_INVALID;
+  return e->backward(gU_final, gU0, dtype, mem, g_theta, st);
+}
+
+int nf_get_velocity(nf_ctx *ctx, int64_t id, void *const u[3], int dtype, int mem) {
+  EPISODE(ctx, id, e);
+  if (!u || !valid_dtype(dtype) || !valid_mem(mem)) return NF_E_INVALID;
+  return e->get_faces(0, u, dtype, mem);
+}
+
+int nf_get_advected(nf_ctx *ctx, int64_t id, void *const u[3], int dtype, int mem) {
+  EPISODE(ctx, id, e);
+  if (!u || !valid_dtype(dtype) || !valid_mem(mem)) return NF_E_INVALID;
+  return e->get_faces(1, u, dtype, mem);
+}
+
+int nf_get_fractions(nf_ctx *ctx, int64_t id, void *const a[3], int dtype, int mem) {
+  EPISODE(ctx, id, e);
+  if (!a || !valid_dtype(dtype) || !valid_mem(mem)) return NF_E_INVALID;
+  return e->get_faces(2, a, dtype, mem);
+}
+
+int nf_get_pressure(nf_ctx *ctx, int64_t id, void *p, int dtype, int mem) {
+  EPISODE(ctx, id, e);
+  if (!p || !valid_dtype(dtype) || !valid_mem(mem)) return NF_E_INVALID;
+  return e->get_pressure(p, dtype, mem);
+}
+
+int nf_get_step(nf_ctx *ctx, int64_t id, int *n) {
+  EPISODE(ctx, id, e);
+  if (!n) return NF_E_INVALID;
+  *n = e->step_index();
+  return NF_OK;
+}
+
+int nf_launch_count(nf_ctx *ctx, int64_t *count) {
+  if (!ctx || !count) return NF_E_INVALID;
+  *count = ctx->c.launches;
+  return NF_OK;
+}
+
+int nf_profile(nf_ctx *ctx, int kclass) {
+  GUARD(ctx);
+  if (kclass < -2 || kclass >= NF_K_COUNT) return NF_E_INVALID;
+  if (ctx->c.prof.used) ctx->c.prof.drain(ctx->c.stream);
+  ctx->c.prof.reset();
+  ctx->c.prof.kclass = kclass;
+  return NF_OK;
+}
+
+int nf_profile_read(nf_ctx *ctx, int kclass, int64_t *launches, double *ms) {
+  GUARD(ctx);
+  if (kclass < 0 || kclass >= NF_K_COUNT || !launches || !ms) return NF_E_INVALID;
+  if (ctx->c.prof.used) ctx->c.prof.drain(ctx->c.stream);
+  *launches = ctx->c.prof.launches[kclass];
+  *ms = ctx->c.prof.ms[kclass];
+  return NF_OK;
+}
+
+}  // extern "C"

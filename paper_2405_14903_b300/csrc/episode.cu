@@ -1,0 +1,623 @@
+// Episode implementation: the forward step (Sec. 2.3.1), the checkpointed
+// rollout tape, and the adjoint step (Sec. 2.3.2 / 2.3.3).
+//
+// Rollout tape: the velocity U^{mC} is saved before every C-th step. To
+// revert step m the library restores U^{sC} (s = m / C), recomputes the
+// segment's steps storing (U^k, U^k hat, P^k) for each, then runs the
+// adjoint of the segment's steps in reverse. The forward kernels are
+// deterministic (no float atomics, fixed-order reductions), so the recomputed
+// segment reproduces the recorded rollout bit for bit.
+//
+// Gauge: in a closed box (no outlet) A is singular with the constants on the
+// active cells as null space. The right-hand side is projected to zero mean
+// there (a no-op for consistent data, the least-squares reading otherwise)
+// and the pressure is returned with zero mean; the adjoint does the same for
+// dJ/dP and the adjoint variable y, so the parameter gradient matches the
+// derivative of that reading.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <vector>
+
+#include "episode.h"
+#include "kernels.h"
+#include "solver.cuh"
+
+namespace nf {
+
+// ------------------------------------------------------------- scenes -----
+
+static int scene_K(int kind) {
+  switch (kind) {
+    case NF_SCENE_SPHERE:
+      return 3;
+    case NF_SCENE_CHAMBER:
+      return 8;
+    case NF_SCENE_PLATE:
+      return 4;
+    default:
+      return 0;
+  }
+}
+
+// Scene state at time t (host, double precision).
+static SceneDev scene_at(const nf_scene &sc, double t, const double *d_spheres) {
+  SceneDev s;
+  std::memset(&s, 0, sizeof(s));
+  s.kind = sc.kind;
+  s.K = scene_K(sc.kind);
+  s.t = t;
+  const double *c = sc.consts;
+  const double *th = sc.theta;
+  switch (sc.kind) {
+    case NF_SCENE_SPHERE:
+      for (int a = 0; a < 3; ++a) {
+        s.sv[a] = th[a];
+        s.sc[a] = c[a] + th[a] * t;
+      }
+      s.sr = c[3];
+      break;
+    case NF_SCENE_CHAMBER: {
+      for (int a = 0; a < 3; ++a) {
+        s.cc[a] = c[a];
+        s.ca[a] = c[3 + a];
+      }
+      s.camin = std::min(s.ca[0], std::min(s.ca[1], s.ca[2]));
+      const double T = c[6];
+      double r = 1.0, rd = 0.0;
+      for (int k = 1; k <= 4; ++k) {
+        const double w = 2.0 * M_PI * k / T;
+        const double cs = std::cos(w * t), sn = std::sin(w * t);
+        const double a = th[k - 1], b = th[3 + k];
+        r += a * cs + b * sn;
+        rd += w * (-a * sn + b * cs);
+        s.cds[k - 1] = cs;
+        s.cds[3 + k] = sn;
+        s.cdsdot[k - 1] = -w * sn;
+        s.cdsdot[3 + k] = w * cs;
+      }
+      s.cs = r;
+      s.csdot = rd;
+      const double x0 = c[7], hw = c[8];
+      s.dc[0] = 0.5 * (x0 + 2.0);
+      s.dc[1] = c[1];
+      s.dc[2] = c[2];
+      s.dh[0] = 0.5 * (2.0 - x0);
+      s.dh[1] = hw;
+      s.dh[2] = hw;
+      break;
+    }
+    case NF_SCENE_PLATE: {
+      for (int a = 0; a < 3; ++a) {
+        s.pc[a] = c[a];
+        s.ph[a] = c[3 + a];
+      }
+      const double L = c[6] / 3.0;
+      int seg = (int)std::floor(t / L);
+      seg = std::max(0, std::min(2, seg));
+      const double tau = (t - seg * L) / L;
+      s.pang = th[seg] * (1.0 - tau) + th[seg + 1] * tau;
+      s.pomega = (th[seg + 1] - th[seg]) / L;
+      s.pcos = std::cos(s.pang);
+      s.psin = std::sin(s.pang);
+      for (int k = 0; k < 4; ++k) s.pdang[k] = s.pdomega[k] = 0.0;
+      s.pdang[seg] = 1.0 - tau;
+      s.pdang[seg + 1] = tau;
+      s.pdomega[seg] = -1.0 / L;
+      s.pdomega[seg + 1] = 1.0 / L;
+      break;
+    }
+    case NF_SCENE_SPHERES:
+      s.spheres = d_spheres;
+      s.nspheres = sc.nspheres;
+      break;
+    default:
+      break;
+  }
+  return s;
+}
+
+// -------------------------------------------------------- conversions -----
+template <class A, class B>
+__global__ void k_cast(int64_t n, const A *in, B *out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (B)in[i];
+}
+
+template <class A, class B>
+static void cast(const Launch &L, int64_t n, const A *in, B *out) {
+  unsigned nb = nblocks(n);
+  if (nb > 148u * 32u) nb = 148u * 32u;
+  ProfScope _ps(L, NF_K_CAST);
+  k_cast<A, B><<<nb, kBlock, 0, L.s>>>(n, in, out);
+  ++*L.counter;
+}
+
+static size_t dtype_size(int dtype) { return dtype == NF_F64 ? 8 : 4; }
+
+// --------------------------------------------------------------- impl -----
+template <class T, class S, class V, class TA>
+class EpisodeImpl : public EpisodeBase {
+ public:
+  EpisodeImpl(Ctx *ctx, const nf_grid &gr, const nf_scene &sc)
+      : ctx_(ctx), g_(make_grid(gr)), sc_(sc), solver_(ctx, make_grid(gr), ctx->cfg) {
+    sc_.K = scene_K(sc.kind);
+    sc_.spheres = nullptr;
+  }
+
+  static GridDev make_grid(const nf_grid &gr) {
+    GridDev g;
+    g.nx = gr.nx;
+    g.ny = gr.ny;
+    g.nz = gr.nz;
+    g.dx = gr.dx;
+    g.dt = gr.dt;
+    g.rho = gr.rho > 0 ? gr.rho : 1.0;
+    g.c = g.dt / (g.rho * g.dx);
+    g.outlet = gr.outlet;
+    g.oj0 = gr.outlet_j0;
+    g.ok0 = gr.outlet_k0;
+    g.ow = gr.outlet_w;
+    g.oh = gr.outlet_h;
+    return g;
+  }
+
+  int init(const nf_scene &sc) {
+    nfaces_ = g_.nface(0) + g_.nface(1) + g_.nface(2);
+    ncell_ = g_.ncell();
+    CKS(faces(&U_));
+    CKS(faces(&Uh_));
+    CKS(faces(&alpha_));
+    CKS(faces(&gU_));
+    CKS(faces(&gUb_));
+    CKS(faces(&gUh_));
+    CKS(A_.get(&P_, ncell_ * sizeof(S)));
+    CKS(A_.get(&b_, ncell_ * sizeof(S)));
+    CKS(A_.get(&gP_, ncell_ * sizeof(S)));
+    CKS(A_.get(&y_, ncell_ * sizeof(S)));
+    const int64_t mf = std::max(g_.nface(0), std::max(g_.nface(1), g_.nface(2)));
+    CKS(A_.get(&stage_, std::max(mf, ncell_) * sizeof(double)));
+    CKS(A_.get(&dscal_, 64 * sizeof(double)));
+    if (sc.kind == NF_SCENE_SPHERES && sc.nspheres > 0) {
+      CKS(A_.get(&dsph_, (size_t)sc.nspheres * 4 * sizeof(double)));
+      CKC(cudaMemcpy(dsph_, sc.spheres, (size_t)sc.nspheres * 4 * sizeof(double),
+                     cudaMemcpyHostToDevice));
+    }
+    CKS(solver_.init(A_));
+    Launch L = ctx_->launch();
+    CKC(cudaMemsetAsync(U_, 0, nfaces_ * sizeof(T), L.s));
+    CKC(cudaMemsetAsync(P_, 0, ncell_ * sizeof(S), L.s));
+    CKC(cudaMemsetAsync(Uh_, 0, nfaces_ * sizeof(T), L.s));
+    // fractions of the initial geometry (t = 0) so queries are meaningful
+    launch_rasterize<T>(L, g_, scene_at(sc_, 0.0, dsph_), mut(alpha_));
+    return check_launch();
+  }
+
+  size_t bytes() const override { return A_.bytes; }
+  int step_index() const override { return n_; }
+
+  int set_params(const double *theta, int K) override {
+    if (K != sc_.K) return invalid("set_params: expected %d parameters", sc_.K);
+    for (int k = 0; k < K; ++k) sc_.theta[k] = theta[k];
+    clear_tape();
+    return NF_OK;
+  }
+
+  int set_velocity(const void *const u[3], int dtype, int mem, int project,
+                   nf_step_stats *st) override {
+    for (int d = 0; d < 3; ++d)
+      CKS(copy_in(comp(U_, d), u[d], g_.nface(d), dtype, mem));
+    clear_tape();
+    nf_step_stats s{};
+    int rc = NF_OK;
+    if (project) {
+      if (!Uinit_) {
+        CKS(faces(&Uinit_));
+        CKS(A_.get(&Pinit_, ncell_ * sizeof(S)));
+      }
+      Launch L = ctx_->launch();
+      CKC(cudaMemcpyAsync(Uinit_, U_, nfaces_ * sizeof(T), cudaMemcpyDeviceToDevice, L.s));
+      const SceneDev sd = scene_at(sc_, 0.0, dsph_);
+      launch_rasterize<T>(L, g_, sd, mut(alpha_));
+      SolveStats ss;
+      CKS(project_faces(sd, Uinit_, Pinit_, U_, &ss));
+      CKC(cudaMemcpyAsync(Uh_, Uinit_, nfaces_ * sizeof(T), cudaMemcpyDeviceToDevice, L.s));
+      CKC(cudaMemcpyAsync(P_, Pinit_, ncell_ * sizeof(S), cudaMemcpyDeviceToDevice, L.s));
+      acc_stats(&s, ss);
+      init_proj_ = true;
+      rc = ss.status;
+    }
+    if (st) *st = s;
+    CKS(check_launch());
+    return rc;
+  }
+
+  int step(int nsteps, nf_step_stats *st) override {
+    if (nsteps < 0) return invalid("step: nsteps < 0%s", "");
+    nf_step_stats s{};
+    int worst = NF_OK;
+    for (int i = 0; i < nsteps; ++i) {
+      const int C = std::max(1, ctx_->cfg.checkpoint_every);
+      if (n_ % C == 0) {
+        const int idx = n_ / C;
+        while ((int)ckpt_.size() <= idx) {
+          T *p = nullptr;
+          CKS(faces(&p));
+          ckpt_.push_back(p);
+        }
+        CKC(cudaMemcpyAsync(ckpt_[idx], U_, nfaces_ * sizeof(T),
+                            cudaMemcpyDeviceToDevice, ctx_->stream));
+      }
+      SolveStats ss;
+      CKS(forward_step(n_, U_, U_, Uh_, P_, &ss));
+      acc_stats(&s, ss);
+      s.steps += 1;
+      if (ss.status != NF_OK && worst == NF_OK) worst = ss.status;
+      if (ss.status == NF_E_DIVERGED) break;
+      ++n_;
+      n_rev_ = n_;
+      seg_start_ = -1;  // a new step invalidates the cached segment
+    }
+    if (st) *st = s;
+    CKS(check_launch());
+    return worst;
+  }
+
+  int loss(int kind, double *J, void *const gU[3], int dtype, int mem) override {
+    if (kind != NF_LOSS_KINETIC && kind != NF_LOSS_OUTFLOW)
+      return invalid("loss: unknown kind %d", kind);
+    if (kind == NF_LOSS_OUTFLOW && !g_.outlet)
+      return invalid("loss: outflow needs an outlet%s", "");
+    Launch L = ctx_->launch();
+    const bool want = gU != nullptr;
+    launch_loss<T>(L, g_, kind, cview(U_), mut(gUh_), want, ctx_->rs, dscal_ + 1);
+    if (J) *J = ctx_->read_double(dscal_ + 1);
+    if (want)
+      for (int d = 0; d < 3; ++d)
+        CKS(copy_out(gU[d], comp(gUh_, d), g_.nface(d), dtype, mem));
+    return check_launch();
+  }
+
+  int backward_step(const void *const gU_next[3], void *const gU_prev[3],
+                    int dtype, int mem, double *g_theta,
+                    nf_step_stats *st) override {
+    if (n_rev_ == 0 && !(init_proj_ && !init_reverted_))
+      return state_err("backward_step: nothing left to revert");
+    for (int d = 0; d < 3; ++d)
+      CKS(copy_in(comp(gU_, d), gU_next[d], g_.nface(d), dtype, mem));
+    nf_step_stats s{};
+    double gth[kMaxParams] = {0};
+    const int rc = revert_one(gth, &s);
+    if (rc != NF_OK && rc != NF_E_NOT_CONVERGED) return rc;
+    if (g_theta)
+      for (int k = 0; k < sc_.K; ++k) g_theta[k] += gth[k];
+    if (gU_prev)
+      for (int d = 0; d < 3; ++d)
+        if (gU_prev[d]) CKS(copy_out(gU_prev[d], comp(gU_, d), g_.nface(d), dtype, mem));
+    if (st) *st = s;
+    CKS(check_launch());
+    return rc;
+  }
+
+  int backward(const void *const gU_final[3], void *const gU0[3], int dtype,
+               int mem, double *g_theta, nf_step_stats *st) override {
+    if (n_rev_ == 0 && !(init_proj_ && !init_reverted_))
+      return state_err("backward: no recorded step to revert");
+    for (int d = 0; d < 3; ++d)
+      CKS(copy_in(comp(gU_, d), gU_final[d], g_.nface(d), dtype, mem));
+    nf_step_stats s{};
+    double gth[kMaxParams] = {0};
+    int worst = NF_OK;
+    while (n_rev_ > 0 || (init_proj_ && !init_reverted_)) {
+      const int rc = revert_one(gth, &s);
+      if (rc != NF_OK && rc != NF_E_NOT_CONVERGED) return rc;
+      if (rc != NF_OK && worst == NF_OK) worst = rc;
+    }
+    if (g_theta)
+      for (int k = 0; k < sc_.K; ++k) g_theta[k] = gth[k];
+    if (gU0)
+      for (int d = 0; d < 3; ++d)
+        if (gU0[d]) CKS(copy_out(gU0[d], comp(gU_, d), g_.nface(d), dtype, mem));
+    if (st) *st = s;
+    CKS(check_launch());
+    return worst;
+  }
+
+  int get_faces(int which, void *const dst[3], int dtype, int mem) override {
+    const T *src = which == 0 ? U_ : (which == 1 ? Uh_ : alpha_);
+    for (int d = 0; d < 3; ++d)
+      CKS(copy_out(dst[d], comp(src, d), g_.nface(d), dtype, mem));
+    return check_launch();
+  }
+
+  int get_pressure(void *dst, int dtype, int mem) override {
+    return copy_out_t<S>(dst, P_, ncell_, dtype, mem);
+  }
+
+ private:
+  // ---------------------------------------------------------- helpers ----
+  int faces(T **p) { return A_.get(p, nfaces_ * sizeof(T)); }
+  T *comp(T *base, int d) const {
+    return base + (d == 0 ? 0 : (d == 1 ? g_.nface(0) : g_.nface(0) + g_.nface(1)));
+  }
+  const T *comp(const T *base, int d) const {
+    return base + (d == 0 ? 0 : (d == 1 ? g_.nface(0) : g_.nface(0) + g_.nface(1)));
+  }
+  FieldsMut<T> mut(T *base) const {
+    return FieldsMut<T>{comp(base, 0), comp(base, 1), comp(base, 2)};
+  }
+  Fields<T> cview(const T *base) const {
+    return Fields<T>{comp(base, 0), comp(base, 1), comp(base, 2)};
+  }
+  int invalid(const char *fmt, int v) {
+    char buf[256];
+    snprintf(buf, sizeof buf, fmt, v);
+    set_error(buf);
+    return NF_E_INVALID;
+  }
+  int invalid(const char *fmt, const char *v) {
+    char buf[256];
+    snprintf(buf, sizeof buf, fmt, v);
+    set_error(buf);
+    return NF_E_INVALID;
+  }
+  int state_err(const char *msg) {
+    set_error(msg);
+    return NF_E_STATE;
+  }
+  int check_launch() {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return NF_OK;
+  }
+  void acc_stats(nf_step_stats *s, const SolveStats &ss) {
+    s->solves += 1;
+    s->iters += ss.iters;
+    s->max_iters = std::max(s->max_iters, ss.iters);
+    s->outer += ss.outer;
+    s->rel_residual = std::max(s->rel_residual, ss.rel);
+  }
+
+  template <class D>
+  int copy_in_t(D *dst, const void *src, int64_t n, int dtype, int mem) {
+    if (!src) return invalid("null input array%s", "");
+    Launch L = ctx_->launch();
+    const size_t es = dtype_size(dtype);
+    const bool same = es == sizeof(D);
+    if (mem == NF_MEM_DEVICE && same) {
+      CKC(cudaMemcpyAsync(dst, src, n * es, cudaMemcpyDeviceToDevice, L.s));
+      return NF_OK;
+    }
+    const void *dsrc = src;
+    if (mem == NF_MEM_HOST) {
+      void *target = same ? (void *)dst : stage_;
+      CKC(cudaMemcpyAsync(target, src, n * es, cudaMemcpyHostToDevice, L.s));
+      if (same) return NF_OK;
+      dsrc = stage_;
+    }
+    if (dtype == NF_F64)
+      cast<double, D>(L, n, (const double *)dsrc, dst);
+    else
+      cast<float, D>(L, n, (const float *)dsrc, dst);
+    return NF_OK;
+  }
+  int copy_in(T *dst, const void *src, int64_t n, int dtype, int mem) {
+    return copy_in_t<T>(dst, src, n, dtype, mem);
+  }
+
+  template <class D>
+  int copy_out_t(void *dst, const D *src, int64_t n, int dtype, int mem) {
+    if (!dst) return invalid("null output array%s", "");
+    Launch L = ctx_->launch();
+    const size_t es = dtype_size(dtype);
+    const bool same = es == sizeof(D);
+    const void *from = src;
+    if (!same) {
+      void *target = mem == NF_MEM_DEVICE ? dst : stage_;
+      if (dtype == NF_F64)
+        cast<D, double>(L, n, src, (double *)target);
+      else
+        cast<D, float>(L, n, src, (float *)target);
+      if (mem == NF_MEM_DEVICE) return NF_OK;
+      from = stage_;
+    }
+    CKC(cudaMemcpyAsync(dst, from, n * es,
+                        mem == NF_MEM_DEVICE ? cudaMemcpyDeviceToDevice
+                                             : cudaMemcpyDeviceToHost,
+                        L.s));
+    if (mem == NF_MEM_HOST) CKC(cudaStreamSynchronize(L.s));
+    return NF_OK;
+  }
+  int copy_out(void *dst, const T *src, int64_t n, int dtype, int mem) {
+    return copy_out_t<T>(dst, src, n, dtype, mem);
+  }
+
+  void clear_tape() {
+    n_ = 0;
+    n_rev_ = 0;
+    init_proj_ = false;
+    init_reverted_ = false;
+    seg_start_ = -1;
+  }
+
+  // Zero mean over the active cells (closed boxes only); returns ||v||^2
+  // after the projection, or `n2` unchanged when the box has an outlet.
+  double gauge(S *v, double n2) {
+    if (g_.outlet) return n2;
+    Launch L = ctx_->launch();
+    launch_remove_mean<T, S>(L, g_, cview(alpha_), v, ctx_->rs, dscal_ + 4);
+    return ctx_->read_double(dscal_ + 6);
+  }
+
+  // ----------------------------------------------------------- forward ----
+  // Right-hand side, solve and blended update for fractions alpha_ (already
+  // rasterised for scene state sd): uh -> P, u_out.
+  int project_faces(const SceneDev &sd, const T *uh, S *P, T *u_out,
+                    SolveStats *ss) {
+    Launch L = ctx_->launch();
+    launch_rhs<T, S>(L, g_, sd, cview(alpha_), cview(uh), b_, ctx_->rs, dscal_);
+    solver_.set_fractions(comp(alpha_, 0), comp(alpha_, 1), comp(alpha_, 2));
+    const double bn2 = gauge(b_, ctx_->read_double(dscal_));
+    *ss = solver_.solve(b_, P, bn2);
+    gauge(P, 0.0);
+    launch_update<T, S>(L, g_, sd, cview(alpha_), cview(uh), P, mut(u_out));
+    return NF_OK;
+  }
+
+  // Step m (t_{m+1} = (m + 1) dt): u_in -> uh, P, u_out (u_out may alias u_in).
+  int forward_step(int m, const T *u_in, T *u_out, T *uh, S *P, SolveStats *ss) {
+    Launch L = ctx_->launch();
+    const SceneDev sd = scene_at(sc_, (m + 1) * g_.dt, dsph_);
+    launch_rasterize<T>(L, g_, sd, mut(alpha_));
+    launch_advect<T>(L, g_, cview(u_in), mut(uh), ctx_->cfg.advect_order);
+    return project_faces(sd, uh, P, u_out, ss);
+  }
+
+  // ---------------------------------------------------------- backward ----
+  int ensure_segment_buffers(int C) {
+    while ((int)segU_.size() < C) {
+      T *a = nullptr, *b = nullptr;
+      S *p = nullptr;
+      CKS(faces(&a));
+      CKS(faces(&b));
+      CKS(A_.get(&p, ncell_ * sizeof(S)));
+      segU_.push_back(a);
+      segUh_.push_back(b);
+      segP_.push_back(p);
+    }
+    if (!tmpU_) CKS(faces(&tmpU_));
+    return NF_OK;
+  }
+
+  // Recompute segment s from its checkpoint, recording the per-step tape.
+  int recompute_segment(int s, nf_step_stats *st) {
+    const int C = std::max(1, ctx_->cfg.checkpoint_every);
+    CKS(ensure_segment_buffers(C));
+    const int start = s * C, end = std::min(start + C, n_);
+    CKC(cudaMemcpyAsync(segU_[0], ckpt_[s], nfaces_ * sizeof(T),
+                        cudaMemcpyDeviceToDevice, ctx_->stream));
+    for (int m = start; m < end; ++m) {
+      const int k = m - start;
+      T *out = (k + 1 < end - start) ? segU_[k + 1] : tmpU_;
+      SolveStats ss;
+      CKS(forward_step(m, segU_[k], out, segUh_[k], segP_[k], &ss));
+      acc_stats(st, ss);
+    }
+    seg_start_ = start;
+    return NF_OK;
+  }
+
+  // Adjoint of one projection (fractions alpha_ for scene state sd) with
+  // the forward's U^ = uh and pressure P: gU_ -> gUh_, theta gradient.
+  int adjoint_projection(const SceneDev &sd, const T *uh, const S *P,
+                         double *gth, nf_step_stats *st) {
+    Launch L = ctx_->launch();
+    solver_.set_fractions(comp(alpha_, 0), comp(alpha_, 1), comp(alpha_, 2));
+    launch_adj_gp<T, S>(L, g_, cview(alpha_), cview(gU_), gP_, ctx_->rs, dscal_);
+    const double n2 = gauge(gP_, ctx_->read_double(dscal_));
+    const SolveStats ss = solver_.solve(gP_, y_, n2);
+    gauge(y_, 0.0);
+    acc_stats(st, ss);
+    launch_adj_face<T, S>(L, g_, sd, cview(alpha_), cview(uh), P, y_, cview(gU_),
+                          mut(gUh_), ctx_->rs, dscal_ + 8);
+    if (sd.K > 0) {
+      double h[kMaxParams];
+      ctx_->read_bytes(h, dscal_ + 8, sizeof(h));
+      for (int k = 0; k < sd.K; ++k) gth[k] += h[k];
+    }
+    return ss.status;
+  }
+
+  // Revert the most recent unreverted step (or the initial projection).
+  int revert_one(double *gth, nf_step_stats *st) {
+    Launch L = ctx_->launch();
+    if (n_rev_ == 0) {
+      if (!init_proj_ || init_reverted_)
+        return state_err("backward_step: nothing left to revert");
+      const SceneDev sd = scene_at(sc_, 0.0, dsph_);
+      launch_rasterize<T>(L, g_, sd, mut(alpha_));
+      const int rc = adjoint_projection(sd, Uinit_, Pinit_, gth, st);
+      CKC(cudaMemcpyAsync(gU_, gUh_, nfaces_ * sizeof(T), cudaMemcpyDeviceToDevice, L.s));
+      init_reverted_ = true;
+      return rc;
+    }
+    const int m = n_rev_ - 1;
+    const int C = std::max(1, ctx_->cfg.checkpoint_every);
+    const int s = m / C;
+    if (seg_start_ != s * C) CKS(recompute_segment(s, st));
+    const int k = m - seg_start_;
+    const SceneDev sd = scene_at(sc_, (m + 1) * g_.dt, dsph_);
+    launch_rasterize<T>(L, g_, sd, mut(alpha_));
+    const int rc = adjoint_projection(sd, segUh_[k], segP_[k], gth, st);
+    launch_advect_adjoint<T>(L, g_, cview(segU_[k]), cview(gUh_), mut(gUb_),
+                             ctx_->cfg.advect_order);
+    std::swap(gU_, gUb_);
+    n_rev_ = m;
+    st->steps += 1;
+    return rc;
+  }
+
+  Ctx *ctx_;
+  GridDev g_;
+  nf_scene sc_;
+  Solver<T, S, V, TA> solver_;
+  Alloc A_;
+  int64_t nfaces_ = 0, ncell_ = 0;
+  T *U_ = nullptr, *Uh_ = nullptr, *alpha_ = nullptr;
+  T *gU_ = nullptr, *gUb_ = nullptr, *gUh_ = nullptr, *tmpU_ = nullptr;
+  S *P_ = nullptr, *b_ = nullptr, *gP_ = nullptr, *y_ = nullptr;
+  void *stage_ = nullptr;
+  double *dscal_ = nullptr;  // [0] norms, [1] loss, [4..7) gauge, [8..16) dJ/dtheta
+  double *dsph_ = nullptr;
+  // tape
+  int n_ = 0, n_rev_ = 0;
+  bool init_proj_ = false, init_reverted_ = false;
+  T *Uinit_ = nullptr;
+  S *Pinit_ = nullptr;
+  std::vector<T *> ckpt_;
+  int seg_start_ = -1;
+  std::vector<T *> segU_, segUh_;
+  std::vector<S *> segP_;
+};
+
+size_t episode_base_bytes(const nf_config &cfg, const nf_grid &g) {
+  const size_t nf = (size_t)(g.nx + 1) * g.ny * g.nz + (size_t)g.nx * (g.ny + 1) * g.nz +
+                    (size_t)g.nx * g.ny * (g.nz + 1);
+  const size_t nc = (size_t)g.nx * g.ny * g.nz;
+  const size_t t = cfg.precision == NF_PREC_FP64 ? 8 : 4;
+  const size_t s = cfg.precision == NF_PREC_FP32 ? 4 : 8;
+  const size_t v = cfg.precision == NF_PREC_FP64 ? 8 : 4;
+  size_t b = 6 * nf * t + 4 * nc * s + nc * 8;  // fields, scalars, staging
+  b += nc * s + 5 * nc * v;                      // solver vectors
+  b += (nc * (2 * v + 3 * t)) * 2 / 7 + nc * v;  // hierarchy (approx.)
+  return b;
+}
+
+template <class T, class S, class V, class TA>
+static int make(Ctx *ctx, const nf_grid *g, const nf_scene *s, EpisodeBase **out) {
+  auto *e = new EpisodeImpl<T, S, V, TA>(ctx, *g, *s);
+  const int rc = e->init(*s);
+  if (rc != NF_OK) {
+    delete e;
+    return rc;
+  }
+  *out = e;
+  return NF_OK;
+}
+
+int create_episode(Ctx *ctx, const nf_grid *g, const nf_scene *s,
+                   EpisodeBase **out) {
+  *out = nullptr;
+  switch (ctx->cfg.precision) {
+    case NF_PREC_FP64:
+      return make<double, double, double, double>(ctx, g, s, out);
+    case NF_PREC_FP32:
+      return make<float, float, float, float>(ctx, g, s, out);
+    default:
+      return make<float, double, float, __nv_bfloat16>(ctx, g, s, out);
+  }
+}
+
+}  // namespace nf

@@ -1,0 +1,641 @@
+// Solver kernels for A P = b, A = c G^T S G (Sec. 2.3.1, Eq.
+// projection_matrix): the matrix-free 7-point alpha-weighted apply, fused CG
+// vector updates with deterministic FP64 reductions, and the geometric
+// multigrid V-cycle used as the CG preconditioner (red-black Gauss-Seidel
+// smoothing, trilinear prolongation, restriction R = P^T / 4, coarse
+// fractions = mean of the four fine sub-faces, operator rediscretised with
+// c_l = dt / (rho dx_l)).
+#include "kernels.h"
+
+namespace nf {
+
+// ---------------------------------------------------- level indexing -----
+struct Lv {
+  int nx, ny, nz;
+  __device__ __forceinline__ int64_t fx(int i, int j, int k) const {
+    return ((int64_t)k * ny + j) * (nx + 1) + i;
+  }
+  __device__ __forceinline__ int64_t fy(int i, int j, int k) const {
+    return ((int64_t)k * (ny + 1) + j) * nx + i;
+  }
+  __device__ __forceinline__ int64_t fz(int i, int j, int k) const {
+    return ((int64_t)k * ny + j) * nx + i;
+  }
+};
+
+// Fractions of the six faces of a cell, in arithmetic type R.
+template <class R>
+struct Six {
+  R xm, xp, ym, yp, zm, zp;
+  __device__ __forceinline__ R diag() const { return xm + xp + ym + yp + zm + zp; }
+};
+template <class R, class TA>
+__device__ __forceinline__ Six<R> six(const LevelView<TA> &lv, int i, int j,
+                                      int k) {
+  Lv L{lv.nx, lv.ny, lv.nz};
+  Six<R> s;
+  s.xm = (R)ld(lv.ax + L.fx(i, j, k));
+  s.xp = (R)ld(lv.ax + L.fx(i + 1, j, k));
+  s.ym = (R)ld(lv.ay + L.fy(i, j, k));
+  s.yp = (R)ld(lv.ay + L.fy(i, j + 1, k));
+  s.zm = (R)ld(lv.az + L.fz(i, j, k));
+  s.zp = (R)ld(lv.az + L.fz(i, j, k + 1));
+  return s;
+}
+
+// Weighted neighbour sum sum_f alpha_f x_nb(f) (ghost x = 0 outside).
+template <class R, class X>
+__device__ __forceinline__ R nbsum(const Six<R> &s, const X *x, int nx, int ny,
+                                   int nz, int i, int j, int k, int64_t c) {
+  const int64_t sy = nx, sz = (int64_t)nx * ny;
+  R acc = R(0);
+  if (i > 0) acc += s.xm * (R)x[c - 1];
+  if (i < nx - 1) acc += s.xp * (R)x[c + 1];
+  if (j > 0) acc += s.ym * (R)x[c - sy];
+  if (j < ny - 1) acc += s.yp * (R)x[c + sy];
+  if (k > 0) acc += s.zm * (R)x[c - sz];
+  if (k < nz - 1) acc += s.zp * (R)x[c + sz];
+  return acc;
+}
+
+// ------------------------------------------------- per-cell operations -----
+// (A x)_c = c (diag x_c - sum_f alpha_f x_nb), 0 on inactive cells. The
+// arithmetic type is the vector type V.
+template <class V, class TA>
+__device__ __forceinline__ V apply_cell(const LevelView<TA> &lv, const V *x,
+                                        int i, int j, int k, int64_t c) {
+  const Six<V> s = six<V>(lv, i, j, k);
+  const V dg = s.diag();
+  if (!(dg > V(0))) return V(0);
+  const V nb = nbsum<V>(s, x, lv.nx, lv.ny, lv.nz, i, j, k, c);
+  return V(lv.c) * (dg * x[c] - nb);
+}
+
+// Gauss-Seidel update of one cell: x = (b + c nb) / (c diag); 0 if inactive.
+template <class V, class TA>
+__device__ __forceinline__ V gs_cell(const LevelView<TA> &lv, const V *x,
+                                     const V *b, int i, int j, int k,
+                                     int64_t c) {
+  const Six<V> s = six<V>(lv, i, j, k);
+  const V dg = s.diag();
+  if (!(dg > V(0))) return V(0);
+  const V cc = V(lv.c);
+  const V nb = nbsum<V>(s, x, lv.nx, lv.ny, lv.nz, i, j, k, c);
+  return (b[c] + cc * nb) / (cc * dg);
+}
+
+// 1D restriction weights (R = P^T / 4 with clamped trilinear P) for coarse
+// index I of n coarse cells: fine offsets 2I-1 .. 2I+2.
+__device__ __forceinline__ void rweights(int I, int n, float w[4]) {
+  w[0] = 0.25f;
+  w[1] = 0.75f;
+  w[2] = 0.75f;
+  w[3] = 0.25f;
+  if (I == 0) {
+    w[0] = 0.f;
+    w[1] = 1.f;
+  }
+  if (I == n - 1) {
+    w[3] = 0.f;
+    w[2] = 1.f;
+  }
+}
+
+template <class V>
+__device__ __forceinline__ V restrict_cell(int fnx, int fny, int fnz, int cnx,
+                                           int cny, int cnz, const V *rf, int I,
+                                           int J, int K) {
+  float wx[4], wy[4], wz[4];
+  rweights(I, cnx, wx);
+  rweights(J, cny, wy);
+  rweights(K, cnz, wz);
+  V acc = V(0);
+  for (int c = 0; c < 4; ++c) {
+    const int k = 2 * K - 1 + c;
+    if (k < 0 || k >= fnz || wz[c] == 0.f) continue;
+    for (int b = 0; b < 4; ++b) {
+      const int j = 2 * J - 1 + b;
+      if (j < 0 || j >= fny || wy[b] == 0.f) continue;
+      const V wzy = V(wz[c] * wy[b]);
+      const V *row = rf + ((int64_t)k * fny + j) * fnx;
+      for (int a = 0; a < 4; ++a) {
+        const int i = 2 * I - 1 + a;
+        if (i < 0 || i >= fnx || wx[a] == 0.f) continue;
+        acc += wzy * V(wx[a]) * row[i];
+      }
+    }
+  }
+  return V(0.25) * acc;
+}
+
+// Trilinear (clamped) prolongation of the coarse correction to fine cell
+// (i, j, k).
+template <class V>
+__device__ __forceinline__ V prolong_cell(int cnx, int cny, int cnz,
+                                          const V *xc, int i, int j, int k) {
+  int I[2], J[2], K[2];
+  auto ax = [](int f, int n, int *C) {
+    const int c0 = f >> 1;
+    int c1 = (f & 1) ? c0 + 1 : c0 - 1;
+    if (c1 < 0 || c1 >= n) c1 = c0;
+    C[0] = c0;
+    C[1] = c1;
+  };
+  ax(i, cnx, I);
+  ax(j, cny, J);
+  ax(k, cnz, K);
+  const V w[2] = {V(0.75), V(0.25)};
+  V acc = V(0);
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+        acc += w[c] * w[b] * w[a] * xc[((int64_t)K[c] * cny + J[b]) * cnx + I[a]];
+  return acc;
+}
+
+__device__ __forceinline__ bool stopped(const CGState *st) {
+  return st != nullptr && *(volatile const int *)&st->done != 0;
+}
+
+// ------------------------------------------------------ outer residual -----
+template <class S, class T, class V>
+__global__ void k_residual_outer(LevelView<T> lv, const S *b, const S *x, S *r,
+                                 V *rin, RedScratch rs, double *norm2) {
+  double v[1] = {0.0};
+  const int64_t n = lv.ncell();
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % lv.nx);
+    const int64_t q = c / lv.nx;
+    const int j = (int)(q % lv.ny), k = (int)(q / lv.ny);
+    const Six<double> s = six<double>(lv, i, j, k);
+    const double dg = s.diag();
+    double rv = 0.0;
+    if (dg > 0.0) {
+      const double nb = nbsum<double>(s, x, lv.nx, lv.ny, lv.nz, i, j, k, c);
+      rv = (double)b[c] - lv.c * (dg * (double)x[c] - nb);
+    }
+    r[c] = (S)rv;
+    if (rin) rin[c] = (V)rv;
+    v[0] += rv * rv;
+  }
+  double tot[1];
+  if (grid_sum<1>(v, rs, tot) && threadIdx.x == 0) *norm2 = tot[0];
+}
+
+template <class S, class V>
+__global__ void k_axpy_outer(int64_t n, S *x, const V *e) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x)
+    x[c] = (S)((double)x[c] + (double)e[c]);
+}
+
+// ------------------------------------------------------------------ CG -----
+template <class V>
+__global__ void k_cg_init(int64_t n, const V *r, const V *z, V *d, CGState *st,
+                          RedScratch rs, double rel_tol) {
+  double v[2] = {0.0, 0.0};
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const V rc = r[c], zc = z[c];
+    d[c] = zc;
+    v[0] += (double)rc * (double)zc;
+    v[1] += (double)rc * (double)rc;
+  }
+  double tot[2];
+  if (grid_sum<2>(v, rs, tot) && threadIdx.x == 0) {
+    st->rz = tot[0];
+    st->rr = tot[1];
+    st->stop2 = rel_tol * rel_tol * tot[1];
+    st->iters = 0;
+    st->alpha = st->beta = st->dq = 0.0;
+    st->done = (tot[1] == 0.0) ? 1 : (isfinite(tot[0]) && isfinite(tot[1]) ? 0 : 3);
+    if (st->done == 0 && !(tot[0] > 0.0)) st->done = 2;
+  }
+}
+
+template <class V, class TA>
+__global__ void k_apply_dot(LevelView<TA> lv, const V *d, V *q, CGState *st,
+                            RedScratch rs) {
+  if (stopped(st)) return;
+  double v[1] = {0.0};
+  const int64_t n = lv.ncell();
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % lv.nx);
+    const int64_t t = c / lv.nx;
+    const int j = (int)(t % lv.ny), k = (int)(t / lv.ny);
+    const V qc = apply_cell<V, TA>(lv, d, i, j, k, c);
+    q[c] = qc;
+    v[0] += (double)d[c] * (double)qc;
+  }
+  double tot[1];
+  if (grid_sum<1>(v, rs, tot) && threadIdx.x == 0) {
+    st->dq = tot[0];
+    if (tot[0] > 0.0 && isfinite(tot[0]))
+      st->alpha = st->rz / tot[0];
+    else
+      st->done = isfinite(tot[0]) ? 2 : 3;
+  }
+}
+
+template <class V>
+__global__ void k_cg_xr(int64_t n, V *x, V *r, const V *d, const V *q,
+                        CGState *st, RedScratch rs, bool preconditioned) {
+  if (stopped(st)) return;
+  const V a = (V)st->alpha;
+  double v[1] = {0.0};
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    x[c] += a * d[c];
+    const V rc = r[c] - a * q[c];
+    r[c] = rc;
+    v[0] += (double)rc * (double)rc;
+  }
+  double tot[1];
+  if (grid_sum<1>(v, rs, tot) && threadIdx.x == 0) {
+    st->rr = tot[0];
+    st->iters += 1;
+    if (!isfinite(tot[0])) {
+      st->done = 3;
+    } else if (tot[0] <= st->stop2) {
+      st->done = 1;
+    } else if (!preconditioned) {
+      st->beta = tot[0] / st->rz;
+      st->rz = tot[0];
+    }
+  }
+}
+
+template <class V>
+__global__ void k_cg_rz(int64_t n, const V *r, const V *z, CGState *st,
+                        RedScratch rs) {
+  if (stopped(st)) return;
+  double v[1] = {0.0};
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x)
+    v[0] += (double)r[c] * (double)z[c];
+  double tot[1];
+  if (grid_sum<1>(v, rs, tot) && threadIdx.x == 0) {
+    if (!(tot[0] > 0.0) || !isfinite(tot[0])) {
+      st->done = isfinite(tot[0]) ? 2 : 3;
+    } else {
+      st->beta = tot[0] / st->rz;
+      st->rz = tot[0];
+    }
+  }
+}
+
+template <class V>
+__global__ void k_cg_d(int64_t n, const V *z, V *d, const CGState *st) {
+  if (stopped(st)) return;
+  const V b = (V)st->beta;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x)
+    d[c] = z[c] + b * d[c];
+}
+
+// ----------------------------------------------------------- multigrid -----
+template <class TI, class TO>
+__global__ void k_mg_coarsen(LevelView<TI> f, int cnx, int cny, int cnz, TO *ax,
+                             TO *ay, TO *az) {
+  const int64_t n0 = (int64_t)(cnx + 1) * cny * cnz;
+  const int64_t n1 = (int64_t)cnx * (cny + 1) * cnz;
+  const int64_t n2 = (int64_t)cnx * cny * (cnz + 1);
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  Lv F{f.nx, f.ny, f.nz};
+  if (t < n0) {
+    const int I = (int)(t % (cnx + 1));
+    const int64_t q = t / (cnx + 1);
+    const int J = (int)(q % cny), K = (int)(q / cny);
+    float s = 0.f;
+    for (int b = 0; b < 2; ++b)
+      for (int a = 0; a < 2; ++a) s += (float)ld(f.ax + F.fx(2 * I, 2 * J + a, 2 * K + b));
+    ax[t] = cvt<TO>(0.25 * s);
+    return;
+  }
+  t -= n0;
+  if (t < n1) {
+    const int I = (int)(t % cnx);
+    const int64_t q = t / cnx;
+    const int J = (int)(q % (cny + 1)), K = (int)(q / (cny + 1));
+    float s = 0.f;
+    for (int b = 0; b < 2; ++b)
+      for (int a = 0; a < 2; ++a) s += (float)ld(f.ay + F.fy(2 * I + a, 2 * J, 2 * K + b));
+    ay[t] = cvt<TO>(0.25 * s);
+    return;
+  }
+  t -= n1;
+  if (t < n2) {
+    const int I = (int)(t % cnx);
+    const int64_t q = t / cnx;
+    const int J = (int)(q % cny), K = (int)(q / cny);
+    float s = 0.f;
+    for (int b = 0; b < 2; ++b)
+      for (int a = 0; a < 2; ++a) s += (float)ld(f.az + F.fz(2 * I + a, 2 * J + b, 2 * K));
+    az[t] = cvt<TO>(0.25 * s);
+  }
+}
+
+// Red-black Gauss-Seidel half sweep over cells with (i + j + k) % 2 == color.
+template <class V, class TA>
+__global__ void k_mg_smooth(LevelView<TA> lv, V *x, const V *b, int color,
+                            const CGState *st) {
+  if (stopped(st)) return;
+  const int hx = (lv.nx + 1) >> 1;
+  const int64_t n = (int64_t)hx * lv.ny * lv.nz;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int ii = (int)(t % hx);
+    const int64_t q = t / hx;
+    const int j = (int)(q % lv.ny), k = (int)(q / lv.ny);
+    const int i = 2 * ii + ((j + k + color) & 1);
+    if (i >= lv.nx) continue;
+    const int64_t c = ((int64_t)k * lv.ny + j) * lv.nx + i;
+    x[c] = gs_cell<V, TA>(lv, x, b, i, j, k, c);
+  }
+}
+
+template <class V, class TA>
+__global__ void k_mg_residual(LevelView<TA> lv, const V *x, const V *b, V *r,
+                              const CGState *st) {
+  if (stopped(st)) return;
+  const int64_t n = lv.ncell();
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % lv.nx);
+    const int64_t q = c / lv.nx;
+    const int j = (int)(q % lv.ny), k = (int)(q / lv.ny);
+    r[c] = b[c] - apply_cell<V, TA>(lv, x, i, j, k, c);
+  }
+}
+
+template <class V>
+__global__ void k_mg_restrict(int fnx, int fny, int fnz, int cnx, int cny,
+                              int cnz, const V *rf, V *bc, const CGState *st) {
+  if (stopped(st)) return;
+  const int64_t n = (int64_t)cnx * cny * cnz;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int I = (int)(c % cnx);
+    const int64_t q = c / cnx;
+    const int J = (int)(q % cny), K = (int)(q / cny);
+    bc[c] = restrict_cell<V>(fnx, fny, fnz, cnx, cny, cnz, rf, I, J, K);
+  }
+}
+
+// x_f += P x_c on active fine cells.
+template <class V, class TF>
+__global__ void k_mg_prolong(LevelView<TF> f, int cnx, int cny, int cnz,
+                             const V *xc, V *xf, const CGState *st) {
+  if (stopped(st)) return;
+  const int64_t n = f.ncell();
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % f.nx);
+    const int64_t q = c / f.nx;
+    const int j = (int)(q % f.ny), k = (int)(q / f.ny);
+    if (!(six<float>(f, i, j, k).diag() > 0.f)) continue;
+    xf[c] += prolong_cell<V>(cnx, cny, cnz, xc, i, j, k);
+  }
+}
+
+// One thread block runs the V-cycle on all small levels of the chain. Global
+// memory writes are made visible to the block by __syncthreads().
+template <class V, class TA>
+__device__ void blk_smooth(const LevelView<TA> &lv, V *x, const V *b,
+                           int color) {
+  const int hx = (lv.nx + 1) >> 1;
+  const int n = hx * lv.ny * lv.nz;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const int ii = t % hx, q = t / hx;
+    const int j = q % lv.ny, k = q / lv.ny;
+    const int i = 2 * ii + ((j + k + color) & 1);
+    if (i >= lv.nx) continue;
+    const int64_t c = ((int64_t)k * lv.ny + j) * lv.nx + i;
+    x[c] = gs_cell<V, TA>(lv, x, b, i, j, k, c);
+  }
+  __syncthreads();
+}
+
+template <class V, class TA>
+__global__ void __launch_bounds__(1024, 1)
+k_mg_coarse_chain(CoarseChain<V, TA> ch, const CGState *st) {
+  if (stopped(st)) return;
+  const int last = ch.nlev - 1;
+  for (int l = ch.first; l <= last; ++l) {
+    const LevelView<TA> &lv = ch.lv[l];
+    const int n = (int)lv.ncell();
+    for (int t = threadIdx.x; t < n; t += blockDim.x) ch.x[l][t] = V(0);
+    __syncthreads();
+    if (l == last) break;
+    for (int s = 0; s < ch.smooth; ++s) {
+      blk_smooth(lv, ch.x[l], ch.b[l], 0);
+      blk_smooth(lv, ch.x[l], ch.b[l], 1);
+    }
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      const int i = t % lv.nx, q = t / lv.nx;
+      const int j = q % lv.ny, k = q / lv.ny;
+      ch.r[l][t] = ch.b[l][t] - apply_cell<V, TA>(lv, ch.x[l], i, j, k, t);
+    }
+    __syncthreads();
+    const LevelView<TA> &cv = ch.lv[l + 1];
+    const int nc = (int)cv.ncell();
+    for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+      const int I = t % cv.nx, q = t / cv.nx;
+      const int J = q % cv.ny, K = q / cv.ny;
+      ch.b[l + 1][t] = restrict_cell<V>(lv.nx, lv.ny, lv.nz, cv.nx, cv.ny,
+                                        cv.nz, ch.r[l], I, J, K);
+    }
+    __syncthreads();
+  }
+  {
+    const LevelView<TA> &lv = ch.lv[last];
+    for (int s = 0; s < ch.coarsest_sweeps; ++s) {
+      blk_smooth(lv, ch.x[last], ch.b[last], 0);
+      blk_smooth(lv, ch.x[last], ch.b[last], 1);
+    }
+    for (int s = 0; s < ch.coarsest_sweeps; ++s) {
+      blk_smooth(lv, ch.x[last], ch.b[last], 1);
+      blk_smooth(lv, ch.x[last], ch.b[last], 0);
+    }
+  }
+  for (int l = last - 1; l >= ch.first; --l) {
+    const LevelView<TA> &lv = ch.lv[l];
+    const LevelView<TA> &cv = ch.lv[l + 1];
+    const int n = (int)lv.ncell();
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      const int i = t % lv.nx, q = t / lv.nx;
+      const int j = q % lv.ny, k = q / lv.ny;
+      if (six<float>(lv, i, j, k).diag() > 0.f)
+        ch.x[l][t] += prolong_cell<V>(cv.nx, cv.ny, cv.nz, ch.x[l + 1], i, j, k);
+    }
+    __syncthreads();
+    for (int s = 0; s < ch.smooth; ++s) {
+      blk_smooth(lv, ch.x[l], ch.b[l], 1);
+      blk_smooth(lv, ch.x[l], ch.b[l], 0);
+    }
+  }
+}
+
+// ------------------------------------------------------------ launchers ---
+static inline unsigned gs_blocks(int64_t n) {
+  const unsigned b = nblocks(n);
+  return b < (unsigned)kRedBlocks * 8 ? b : (unsigned)kRedBlocks * 8;
+}
+
+template <class S, class T, class V>
+void launch_residual_outer(const Launch &L, const LevelView<T> &lv, const S *b,
+                           const S *x, S *r, V *rin, const RedScratch &rs,
+                           double *norm2) {
+  ProfScope _ps(L, NF_K_RESIDUAL64);
+  k_residual_outer<S, T, V><<<kRedBlocks, kBlock, 0, L.s>>>(lv, b, x, r, rin, rs, norm2);
+  ++*L.counter;
+}
+template <class S, class V>
+void launch_axpy_outer(const Launch &L, int64_t n, S *x, const V *e) {
+  ProfScope _ps(L, NF_K_AXPY64);
+  k_axpy_outer<S, V><<<gs_blocks(n), kBlock, 0, L.s>>>(n, x, e);
+  ++*L.counter;
+}
+template <class V>
+void launch_cg_init(const Launch &L, int64_t n, const V *r, const V *z, V *d,
+                    CGState *st, const RedScratch &rs, double rel_tol) {
+  ProfScope _ps(L, NF_K_CG_INIT);
+  k_cg_init<V><<<kRedBlocks, kBlock, 0, L.s>>>(n, r, z, d, st, rs, rel_tol);
+  ++*L.counter;
+}
+template <class V, class TA>
+void launch_apply_dot(const Launch &L, const LevelView<TA> &lv, const V *d,
+                      V *q, CGState *st, const RedScratch &rs) {
+  ProfScope _ps(L, NF_K_APPLY_DOT);
+  k_apply_dot<V, TA><<<kRedBlocks, kBlock, 0, L.s>>>(lv, d, q, st, rs);
+  ++*L.counter;
+}
+template <class V>
+void launch_cg_xr(const Launch &L, int64_t n, V *x, V *r, const V *d,
+                  const V *q, CGState *st, const RedScratch &rs,
+                  bool preconditioned) {
+  ProfScope _ps(L, NF_K_CG_XR);
+  k_cg_xr<V><<<kRedBlocks, kBlock, 0, L.s>>>(n, x, r, d, q, st, rs, preconditioned);
+  ++*L.counter;
+}
+template <class V>
+void launch_cg_rz(const Launch &L, int64_t n, const V *r, const V *z,
+                  CGState *st, const RedScratch &rs) {
+  ProfScope _ps(L, NF_K_CG_RZ);
+  k_cg_rz<V><<<kRedBlocks, kBlock, 0, L.s>>>(n, r, z, st, rs);
+  ++*L.counter;
+}
+template <class V>
+void launch_cg_d(const Launch &L, int64_t n, const V *z, V *d,
+                 const CGState *st) {
+  ProfScope _ps(L, NF_K_CG_D);
+  k_cg_d<V><<<gs_blocks(n), kBlock, 0, L.s>>>(n, z, d, st);
+  ++*L.counter;
+}
+template <class TI, class TO>
+void launch_mg_coarsen(const Launch &L, const LevelView<TI> &fine, int cnx,
+                       int cny, int cnz, TO *ax, TO *ay, TO *az) {
+  const int64_t n = (int64_t)(cnx + 1) * cny * cnz + (int64_t)cnx * (cny + 1) * cnz +
+                    (int64_t)cnx * cny * (cnz + 1);
+  ProfScope _ps(L, NF_K_MG_COARSEN);
+  k_mg_coarsen<TI, TO><<<nblocks(n), kBlock, 0, L.s>>>(fine, cnx, cny, cnz, ax, ay, az);
+  ++*L.counter;
+}
+template <class V, class TA>
+void launch_mg_smooth(const Launch &L, const LevelView<TA> &lv, V *x,
+                      const V *b, int color, const CGState *st, int kclass) {
+  const int64_t n = (int64_t)((lv.nx + 1) / 2) * lv.ny * lv.nz;
+  ProfScope _ps(L, kclass);
+  k_mg_smooth<V, TA><<<gs_blocks(n), kBlock, 0, L.s>>>(lv, x, b, color, st);
+  ++*L.counter;
+}
+template <class V, class TA>
+void launch_mg_residual(const Launch &L, const LevelView<TA> &lv, const V *x,
+                        const V *b, V *r, const CGState *st) {
+  ProfScope _ps(L, NF_K_MG_RESIDUAL);
+  k_mg_residual<V, TA><<<gs_blocks(lv.ncell()), kBlock, 0, L.s>>>(lv, x, b, r, st);
+  ++*L.counter;
+}
+template <class V, class TA>
+void launch_mg_restrict(const Launch &L, const LevelView<TA> &fine,
+                        const LevelView<TA> &coarse, const V *rf, V *bc,
+                        const CGState *st) {
+  ProfScope _ps(L, NF_K_MG_RESTRICT);
+  k_mg_restrict<V><<<gs_blocks(coarse.ncell()), kBlock, 0, L.s>>>(
+      fine.nx, fine.ny, fine.nz, coarse.nx, coarse.ny, coarse.nz, rf, bc, st);
+  ++*L.counter;
+}
+template <class V, class TF, class TC>
+void launch_mg_prolong(const Launch &L, const LevelView<TF> &fine,
+                       const LevelView<TC> &coarse, const V *xc, V *xf,
+                       const CGState *st) {
+  ProfScope _ps(L, NF_K_MG_PROLONG);
+  k_mg_prolong<V, TF><<<gs_blocks(fine.ncell()), kBlock, 0, L.s>>>(
+      fine, coarse.nx, coarse.ny, coarse.nz, xc, xf, st);
+  ++*L.counter;
+}
+template <class V, class TA>
+void launch_mg_coarse_chain(const Launch &L, const CoarseChain<V, TA> &ch,
+                            const CGState *st) {
+  ProfScope _ps(L, NF_K_MG_CHAIN);
+  k_mg_coarse_chain<V, TA><<<1, 1024, 0, L.s>>>(ch, st);
+  ++*L.counter;
+}
+
+#define NF_INST_V(V)                                                           \
+  template void launch_cg_init<V>(const Launch &, int64_t, const V *,        \
+                                  const V *, V *, CGState *,                  \
+                                  const RedScratch &, double);                \
+  template void launch_cg_xr<V>(const Launch &, int64_t, V *, V *, const V *,\
+                                const V *, CGState *, const RedScratch &,     \
+                                bool);                                        \
+  template void launch_cg_rz<V>(const Launch &, int64_t, const V *,          \
+                                const V *, CGState *, const RedScratch &);    \
+  template void launch_cg_d<V>(const Launch &, int64_t, const V *, V *,      \
+                               const CGState *);
+#define NF_INST_VA(V, TA)                                                      \
+  template void launch_apply_dot<V, TA>(const Launch &, const LevelView<TA> &,\
+                                        const V *, V *, CGState *,            \
+                                        const RedScratch &);                  \
+  template void launch_mg_smooth<V, TA>(const Launch &, const LevelView<TA> &,\
+                                        V *, const V *, int, const CGState *, \
+                                        int);                                 \
+  template void launch_mg_residual<V, TA>(const Launch &,                    \
+                                          const LevelView<TA> &, const V *,   \
+                                          const V *, V *, const CGState *);   \
+  template void launch_mg_restrict<V, TA>(const Launch &,                    \
+                                          const LevelView<TA> &,              \
+                                          const LevelView<TA> &, const V *,   \
+                                          V *, const CGState *);              \
+  template void launch_mg_coarse_chain<V, TA>(const Launch &,                \
+                                              const CoarseChain<V, TA> &,     \
+                                              const CGState *);
+NF_INST_V(float)
+NF_INST_V(double)
+NF_INST_VA(float, float)
+NF_INST_VA(float, __nv_bfloat16)
+NF_INST_VA(double, double)
+
+template void launch_mg_prolong<float, float, float>(const Launch &, const LevelView<float> &, const LevelView<float> &, const float *, float *, const CGState *);
+template void launch_mg_prolong<float, float, __nv_bfloat16>(const Launch &, const LevelView<float> &, const LevelView<__nv_bfloat16> &, const float *, float *, const CGState *);
+template void launch_mg_prolong<float, __nv_bfloat16, __nv_bfloat16>(const Launch &, const LevelView<__nv_bfloat16> &, const LevelView<__nv_bfloat16> &, const float *, float *, const CGState *);
+template void launch_mg_prolong<double, double, double>(const Launch &, const LevelView<double> &, const LevelView<double> &, const double *, double *, const CGState *);
+
+template void launch_mg_coarsen<float, float>(const Launch &, const LevelView<float> &, int, int, int, float *, float *, float *);
+template void launch_mg_coarsen<float, __nv_bfloat16>(const Launch &, const LevelView<float> &, int, int, int, __nv_bfloat16 *, __nv_bfloat16 *, __nv_bfloat16 *);
+template void launch_mg_coarsen<__nv_bfloat16, __nv_bfloat16>(const Launch &, const LevelView<__nv_bfloat16> &, int, int, int, __nv_bfloat16 *, __nv_bfloat16 *, __nv_bfloat16 *);
+template void launch_mg_coarsen<double, double>(const Launch &, const LevelView<double> &, int, int, int, double *, double *, double *);
+
+template void launch_residual_outer<double, float, float>(const Launch &, const LevelView<float> &, const double *, const double *, double *, float *, const RedScratch &, double *);
+template void launch_residual_outer<float, float, float>(const Launch &, const LevelView<float> &, const float *, const float *, float *, float *, const RedScratch &, double *);
+template void launch_residual_outer<double, double, double>(const Launch &, const LevelView<double> &, const double *, const double *, double *, double *, const RedScratch &, double *);
+template void launch_axpy_outer<double, float>(const Launch &, int64_t, double *, const float *);
+template void launch_axpy_outer<float, float>(const Launch &, int64_t, float *, const float *);
+template void launch_axpy_outer<double, double>(const Launch &, int64_t, double *, const double *);
+
+}  // namespace nf

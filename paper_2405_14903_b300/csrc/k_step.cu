@@ -1,0 +1,704 @@
+// Step kernels: rasterisation (Sec. 2.3.1, Projection), RK2 semi-Lagrangian
+// advection (Eq. advection_matrix; Appendix B, Eqs. advection_1/2), the
+// right-hand side of Eq. projection_matrix, the blended velocity update
+// (Eq. u_next_matrix, read as U = S (U^ - c G P) + (I - S) U_s), the losses,
+// and the adjoint kernels of Sec. 2.3.2 / 2.3.3.
+//
+// All kernels are HBM-bound stencils or gathers (no dense contraction), so
+// they are plain CUDA-core code: one thread per face or cell, x fastest so
+// that warps read contiguous rows.
+#include "kernels.h"
+#include "scene.cuh"
+
+namespace nf {
+
+// ------------------------------------------------------------ helpers -----
+
+// Split a flat index over the three face arrays into (component, face).
+__device__ __forceinline__ bool split_face(const GridDev &g, int64_t t, int &d,
+                                           int64_t &f) {
+  const int64_t n0 = g.nface(0), n1 = g.nface(1), n2 = g.nface(2);
+  if (t < n0) {
+    d = 0;
+    f = t;
+    return true;
+  }
+  t -= n0;
+  if (t < n1) {
+    d = 1;
+    f = t;
+    return true;
+  }
+  t -= n1;
+  if (t < n2) {
+    d = 2;
+    f = t;
+    return true;
+  }
+  return false;
+}
+
+// Grid-unit position of face (d; i, j, k): integer part plus 1/2 off-axis.
+__device__ __forceinline__ void face_pos(int d, int i, int j, int k, double &X,
+                                         double &Y, double &Z) {
+  X = i + (d == 0 ? 0.0 : 0.5);
+  Y = j + (d == 1 ? 0.0 : 0.5);
+  Z = k + (d == 2 ? 0.0 : 0.5);
+}
+
+// One axis of a clamped linear interpolation on a lattice of n points, at
+// position base + o (o small). Returns the left index, fraction, and the
+// clamp slope (1 inside [0, n-1], 0 outside).
+template <class R>
+__device__ __forceinline__ void axis_w(int base, R o, int n, int &i0, R &fr,
+                                       R &slope) {
+  const R fl = floor(o);
+  const int i = base + (int)fl;
+  const R f = o - fl;
+  if (i < 0) {
+    i0 = 0;
+    fr = R(0);
+    slope = R(0);
+  } else if (i > n - 1 || (i == n - 1 && f > R(0))) {
+    i0 = n - 2;
+    fr = R(1);
+    slope = R(0);
+  } else if (i == n - 1) {  // exactly on the last point
+    i0 = n - 2;
+    fr = R(1);
+    slope = R(1);
+  } else {
+    i0 = i;
+    fr = f;
+    slope = R(1);
+  }
+}
+
+// Lattice offsets (h_d - s_e) of a component-d face in component e's lattice.
+__device__ __forceinline__ float lat_off(int d, int e, int a) {
+  if (a == d && a != e) return -0.5f;
+  if (a == e && a != d) return 0.5f;
+  return 0.0f;
+}
+
+template <class R>
+struct Interp {
+  int64_t idx[8];
+  R w[8];
+  R dw[3][8];
+};
+
+// Trilinear interpolation of component e at base + o (grid units, e's
+// lattice coordinates). Optionally records corners and weight derivatives.
+template <class T, class R, bool kStencil>
+__device__ __forceinline__ R trilerp(const GridDev &g, const T *U, int e,
+                                     int bi, int bj, int bk, R ox, R oy, R oz,
+                                     Interp<R> *st = nullptr) {
+  const int nx = g.nx + (e == 0), ny = g.ny + (e == 1), nz = g.nz + (e == 2);
+  int i0, j0, k0;
+  R fx, fy, fz, sx, sy, sz;
+  axis_w<R>(bi, ox, nx, i0, fx, sx);
+  axis_w<R>(bj, oy, ny, j0, fy, sy);
+  axis_w<R>(bk, oz, nz, k0, fz, sz);
+  const int64_t base = ((int64_t)k0 * ny + j0) * nx + i0;
+  const int64_t sy1 = nx, sz1 = (int64_t)nx * ny;
+  const R c000 = (R)U[base], c100 = (R)U[base + 1];
+  const R c010 = (R)U[base + sy1], c110 = (R)U[base + sy1 + 1];
+  const R c001 = (R)U[base + sz1], c101 = (R)U[base + sz1 + 1];
+  const R c011 = (R)U[base + sz1 + sy1], c111 = (R)U[base + sz1 + sy1 + 1];
+  const R gx = R(1) - fx, gy = R(1) - fy, gz = R(1) - fz;
+  const R v = gz * (gy * (gx * c000 + fx * c100) + fy * (gx * c010 + fx * c110)) +
+              fz * (gy * (gx * c001 + fx * c101) + fy * (gx * c011 + fx * c111));
+  if (kStencil) {
+    const int64_t id[8] = {base,           base + 1,       base + sy1,
+                           base + sy1 + 1, base + sz1,     base + sz1 + 1,
+                           base + sz1 + sy1, base + sz1 + sy1 + 1};
+    const R wx[2] = {gx, fx}, wy[2] = {gy, fy}, wz[2] = {gz, fz};
+    const R ddx[2] = {-sx, sx}, ddy[2] = {-sy, sy}, ddz[2] = {-sz, sz};
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+      st->idx[c] = id[c];
+      st->w[c] = wx[cx] * wy[cy] * wz[cz];
+      st->dw[0][c] = ddx[cx] * wy[cy] * wz[cz];
+      st->dw[1][c] = wx[cx] * ddy[cy] * wz[cz];
+      st->dw[2][c] = wx[cx] * wy[cy] * ddz[cz];
+    }
+  }
+  return v;
+}
+
+template <class T>
+__device__ __forceinline__ const T *comp(const Fields<T> &u, int e) {
+  return e == 0 ? u.x : (e == 1 ? u.y : u.z);
+}
+template <class T>
+__device__ __forceinline__ T *comp(FieldsMut<T> &u, int e) {
+  return e == 0 ? u.x : (e == 1 ? u.y : u.z);
+}
+
+// ---------------------------------------------------------- rasterise -----
+// alpha_f = (1/64) sum over 4x4x4 cell-centred subsamples of the face's
+// dx^3 control volume of H(phi), H = clamp(1/2 + phi / (dx/4), 0, 1).
+// Faces whose centre is farther than 0.8 dx from the interface are saturated
+// (subsamples lie within 0.65 dx of the centre and phi is 1-Lipschitz), so
+// only the narrow band evaluates the 64 samples, in FP64.
+template <class T>
+__global__ void k_rasterize(GridDev g, SceneDev s, FieldsMut<T> alpha) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int d;
+  int64_t f;
+  if (!split_face(g, t, d, f)) return;
+  int i, j, k;
+  g.face_ijk(d, f, i, j, k);
+  T *a = comp(alpha, d);
+  if (g.boundary(d, i, j, k)) {
+    a[f] = g.outlet_face(d, i, j, k) ? T(1) : T(0);
+    return;
+  }
+  double X, Y, Z;
+  face_pos(d, i, j, k, X, Y, Z);
+  const float pc = scene_phi<float>(s, (float)(X * g.dx), (float)(Y * g.dx),
+                                    (float)(Z * g.dx));
+  const float margin = 0.8f * (float)g.dx;
+  if (pc > margin) {
+    a[f] = T(1);
+    return;
+  }
+  if (pc < -margin) {
+    a[f] = T(0);
+    return;
+  }
+  const double inv_w = 4.0 / g.dx;
+  double acc = 0.0;
+  for (int c = 0; c < 4; ++c) {
+    const double z = (Z + (c + 0.5) * 0.25 - 0.5) * g.dx;
+    for (int b = 0; b < 4; ++b) {
+      const double y = (Y + (b + 0.5) * 0.25 - 0.5) * g.dx;
+      for (int q = 0; q < 4; ++q) {
+        const double x = (X + (q + 0.5) * 0.25 - 0.5) * g.dx;
+        const double h = 0.5 + scene_phi<double>(s, x, y, z) * inv_w;
+        acc += fmin(fmax(h, 0.0), 1.0);
+      }
+    }
+  }
+  a[f] = T(acc * (1.0 / 64.0));
+}
+
+// ------------------------------------------------------------- advect -----
+// Positions are carried as (integer lattice base, small fractional offset)
+// so that the interpolation weights keep full precision at every grid size.
+template <class T>
+__global__ void k_advect(GridDev g, Fields<T> u, FieldsMut<T> out, int order) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int d;
+  int64_t f;
+  if (!split_face(g, t, d, f)) return;
+  int i, j, k;
+  g.face_ijk(d, f, i, j, k);
+  typedef T R;
+  const R r = R(g.dt / g.dx);
+  R v0[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e)
+    v0[e] = trilerp<T, R, false>(g, comp(u, e), e, i, j, k, R(lat_off(d, e, 0)),
+                                 R(lat_off(d, e, 1)), R(lat_off(d, e, 2)));
+  R db[3];
+  if (order == 1) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) db[a] = -r * v0[a];
+  } else {
+    R dm[3], v1[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dm[a] = R(-0.5) * r * v0[a];
+#pragma unroll
+    for (int e = 0; e < 3; ++e)
+      v1[e] = trilerp<T, R, false>(g, comp(u, e), e, i, j, k,
+                                   R(lat_off(d, e, 0)) + dm[0],
+                                   R(lat_off(d, e, 1)) + dm[1],
+                                   R(lat_off(d, e, 2)) + dm[2]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) db[a] = -r * v1[a];
+  }
+  comp(out, d)[f] =
+      trilerp<T, R, false>(g, comp(u, d), d, i, j, k, db[0], db[1], db[2]);
+}
+
+// Adjoint of k_advect: scatter dJ/dU~ back to dJ/dU^n through the
+// interpolation weights at x_b, x_m, x_f and through the positions
+// (Sec. 2.3.2, the dB/dU U term). gu must be zeroed; float atomics make the
+// summation order (not the set of terms) scheduling dependent.
+template <class T>
+__global__ void k_advect_adjoint(GridDev g, Fields<T> u, Fields<T> gut,
+                                 FieldsMut<T> gu, int order) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int d;
+  int64_t f;
+  if (!split_face(g, t, d, f)) return;
+  const T gval = comp(gut, d)[f];
+  if (gval == T(0)) return;
+  int i, j, k;
+  g.face_ijk(d, f, i, j, k);
+  typedef T R;
+  const R r = R(g.dt / g.dx);
+  Interp<R> st;
+  R v0[3], v1[3], dm[3], db[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e)
+    v0[e] = trilerp<T, R, false>(g, comp(u, e), e, i, j, k, R(lat_off(d, e, 0)),
+                                 R(lat_off(d, e, 1)), R(lat_off(d, e, 2)));
+  if (order == 1) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) db[a] = -r * v0[a];
+  } else {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dm[a] = R(-0.5) * r * v0[a];
+#pragma unroll
+    for (int e = 0; e < 3; ++e)
+      v1[e] = trilerp<T, R, false>(g, comp(u, e), e, i, j, k,
+                                   R(lat_off(d, e, 0)) + dm[0],
+                                   R(lat_off(d, e, 1)) + dm[1],
+                                   R(lat_off(d, e, 2)) + dm[2]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) db[a] = -r * v1[a];
+  }
+  // u~_d = I_d(u_d; x_b)
+  trilerp<T, R, true>(g, comp(u, d), d, i, j, k, db[0], db[1], db[2], &st);
+  T *gd = comp(gu, d);
+  const T *ud = comp(u, d);
+  R gxb[3] = {0, 0, 0};
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    atomicAdd(gd + st.idx[c], (T)(gval * st.w[c]));
+    const R uc = (R)ud[st.idx[c]];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) gxb[a] += st.dw[a][c] * uc;
+  }
+  R gv0[3];
+  if (order == 1) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) gv0[a] = -r * gval * gxb[a];
+  } else {
+    R gxm[3] = {0, 0, 0};
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      const R gv1 = -r * gval * gxb[e];
+      trilerp<T, R, true>(g, comp(u, e), e, i, j, k, R(lat_off(d, e, 0)) + dm[0],
+                          R(lat_off(d, e, 1)) + dm[1],
+                          R(lat_off(d, e, 2)) + dm[2], &st);
+      T *ge = comp(gu, e);
+      const T *ue = comp(u, e);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        atomicAdd(ge + st.idx[c], (T)(gv1 * st.w[c]));
+        const R uc = (R)ue[st.idx[c]];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) gxm[a] += gv1 * st.dw[a][c] * uc;
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) gv0[a] = R(-0.5) * r * gxm[a];
+  }
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    trilerp<T, R, true>(g, comp(u, e), e, i, j, k, R(lat_off(d, e, 0)),
+                        R(lat_off(d, e, 1)), R(lat_off(d, e, 2)), &st);
+    T *ge = comp(gu, e);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) atomicAdd(ge + st.idx[c], (T)(gv0[e] * st.w[c]));
+  }
+}
+
+// ----------------------------------------------------- face helpers -------
+// Solid velocity of a component-d face (0 on the box boundary), evaluated in
+// the field precision T.
+template <class T>
+__device__ __forceinline__ T face_us(const GridDev &g, const SceneDev &s,
+                                     int d, int i, int j, int k) {
+  if (s.kind == NF_SCENE_NONE || s.kind == NF_SCENE_SPHERES) return T(0);
+  if (g.boundary(d, i, j, k)) return T(0);
+  double X, Y, Z;
+  face_pos(d, i, j, k, X, Y, Z);
+  return scene_us<T>(s, d, T(X * g.dx), T(Y * g.dx), T(Z * g.dx));
+}
+
+// Sum of the six face fractions of cell (i, j, k).
+template <class T>
+__device__ __forceinline__ T cell_diag(const GridDev &g, const Fields<T> &a,
+                                       int i, int j, int k) {
+  return a.x[g.face(0, i, j, k)] + a.x[g.face(0, i + 1, j, k)] +
+         a.y[g.face(1, i, j, k)] + a.y[g.face(1, i, j + 1, k)] +
+         a.z[g.face(2, i, j, k)] + a.z[g.face(2, i, j, k + 1)];
+}
+
+// Cells on the two sides of face (d; i, j, k); -1 outside the box.
+__device__ __forceinline__ void face_cells(const GridDev &g, int d, int i,
+                                           int j, int k, int64_t &cL,
+                                           int64_t &cR) {
+  const int n = d == 0 ? g.nx : (d == 1 ? g.ny : g.nz);
+  const int o = d == 0 ? i : (d == 1 ? j : k);
+  cR = o < n ? g.cell(i, j, k) : -1;
+  cL = o > 0 ? g.cell(i - (d == 0), j - (d == 1), k - (d == 2)) : -1;
+}
+
+// --------------------------------------------------------------- rhs ------
+// b = G^T (S U^ + (I - S) U_s) on active cells (sum alpha > 0), else 0.
+// G^T v at a cell is v(low face) - v(high face), summed over the axes.
+template <class T, class S>
+__global__ void k_rhs(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
+                      S *b, RedScratch rs, double *bnorm2) {
+  double v[1] = {0.0};
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+       c < g.ncell(); c += (int64_t)gridDim.x * blockDim.x) {
+    int i, j, k;
+    g.cell_ijk(c, i, j, k);
+    const T dg = cell_diag(g, alpha, i, j, k);
+    double acc = 0.0;
+    if (dg > T(0)) {
+      const int I[2] = {i, i + 1}, J[2] = {j, j + 1}, K[2] = {k, k + 1};
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const double sg = side == 0 ? 1.0 : -1.0;
+        const int64_t fx = g.face(0, I[side], j, k), fy = g.face(1, i, J[side], k),
+                      fz = g.face(2, i, j, K[side]);
+        const T ax = alpha.x[fx], ay = alpha.y[fy], az = alpha.z[fz];
+        acc += sg * (double)(ax * uh.x[fx] +
+                             (T(1) - ax) * face_us<T>(g, s, 0, I[side], j, k));
+        acc += sg * (double)(ay * uh.y[fy] +
+                             (T(1) - ay) * face_us<T>(g, s, 1, i, J[side], k));
+        acc += sg * (double)(az * uh.z[fz] +
+                             (T(1) - az) * face_us<T>(g, s, 2, i, j, K[side]));
+      }
+    }
+    b[c] = (S)acc;
+    v[0] += acc * acc;
+  }
+  double tot[1];
+  if (grid_sum<1>(v, rs, tot) && threadIdx.x == 0) *bnorm2 = tot[0];
+}
+
+// ------------------------------------------------------------- gauge ------
+// Sum and count of v over active cells.
+template <class T, class S>
+__global__ void k_active_sum(GridDev g, Fields<T> alpha, const S *v,
+                             RedScratch rs, double *out) {
+  double acc[2] = {0.0, 0.0};
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+       c < g.ncell(); c += (int64_t)gridDim.x * blockDim.x) {
+    int i, j, k;
+    g.cell_ijk(c, i, j, k);
+    if (cell_diag(g, alpha, i, j, k) > T(0)) {
+      acc[0] += (double)v[c];
+      acc[1] += 1.0;
+    }
+  }
+  double tot[2];
+  if (grid_sum<2>(acc, rs, tot) && threadIdx.x == 0) {
+    out[0] = tot[0];
+    out[1] = tot[1];
+  }
+}
+
+// v -= mean on active cells; ||v||^2 of the result into out[2].
+template <class T, class S>
+__global__ void k_sub_mean(GridDev g, Fields<T> alpha, S *v, RedScratch rs,
+                           double *out) {
+  const double mean = out[1] > 0.0 ? out[0] / out[1] : 0.0;
+  double acc[1] = {0.0};
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+       c < g.ncell(); c += (int64_t)gridDim.x * blockDim.x) {
+    int i, j, k;
+    g.cell_ijk(c, i, j, k);
+    if (cell_diag(g, alpha, i, j, k) > T(0)) {
+      const double x = (double)v[c] - mean;
+      v[c] = (S)x;
+      acc[0] += x * x;
+    }
+  }
+  double tot[1];
+  if (grid_sum<1>(acc, rs, tot) && threadIdx.x == 0) out[2] = tot[0];
+}
+
+// ------------------------------------------------------------- update -----
+// U = alpha (U^ - c G P) + (1 - alpha) U_s, with ghost P = 0 outside.
+template <class T, class S>
+__global__ void k_update(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
+                         const S *P, FieldsMut<T> u) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int d;
+  int64_t f;
+  if (!split_face(g, t, d, f)) return;
+  int i, j, k;
+  g.face_ijk(d, f, i, j, k);
+  int64_t cL, cR;
+  face_cells(g, d, i, j, k, cL, cR);
+  const double pR = cR >= 0 ? (double)P[cR] : 0.0;
+  const double pL = cL >= 0 ? (double)P[cL] : 0.0;
+  const T gp = (T)(g.c * (pR - pL));
+  const T a = comp(alpha, d)[f];
+  comp(u, d)[f] = a * (comp(uh, d)[f] - gp) + (T(1) - a) * face_us<T>(g, s, d, i, j, k);
+}
+
+// -------------------------------------------------------------- losses ----
+template <class T>
+__global__ void k_loss_kinetic(GridDev g, Fields<T> u, FieldsMut<T> gu,
+                               bool want_grad, RedScratch rs, double *J) {
+  const double vol = g.dx * g.dx * g.dx;
+  double v[1] = {0.0};
+  const int64_t n = g.nface(0) + g.nface(1) + g.nface(2);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int d;
+    int64_t f;
+    split_face(g, t, d, f);
+    const T x = comp(u, d)[f];
+    v[0] += (double)x * (double)x;
+    if (want_grad) comp(gu, d)[f] = (T)(vol * (double)x);
+  }
+  double tot[1];
+  if (grid_sum<1>(v, rs, tot) && threadIdx.x == 0) *J = 0.5 * vol * tot[0];
+}
+
+template <class T>
+__global__ void k_loss_outflow(GridDev g, Fields<T> u, FieldsMut<T> gu,
+                               bool want_grad, RedScratch rs, double *J) {
+  const double area = g.dx * g.dx;
+  double v[1] = {0.0};
+  const int64_t n = g.nface(0) + g.nface(1) + g.nface(2);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int d;
+    int64_t f;
+    split_face(g, t, d, f);
+    int i, j, k;
+    g.face_ijk(d, f, i, j, k);
+    const bool o = g.outlet_face(d, i, j, k);
+    if (o) v[0] += (double)comp(u, d)[f];
+    if (want_grad) comp(gu, d)[f] = o ? (T)area : T(0);
+  }
+  double tot[1];
+  if (grid_sum<1>(v, rs, tot) && threadIdx.x == 0) *J = area * tot[0];
+}
+
+// ------------------------------------------------------------ adjoint -----
+// gP = -c G^T (S gU) on active cells.
+template <class T, class S>
+__global__ void k_adj_gp(GridDev g, Fields<T> alpha, Fields<T> gu, S *gp,
+                         RedScratch rs, double *norm2) {
+  double v[1] = {0.0};
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+       c < g.ncell(); c += (int64_t)gridDim.x * blockDim.x) {
+    int i, j, k;
+    g.cell_ijk(c, i, j, k);
+    double acc = 0.0;
+    if (cell_diag(g, alpha, i, j, k) > T(0)) {
+      const int64_t f0 = g.face(0, i, j, k), f1 = g.face(1, i, j, k),
+                    f2 = g.face(2, i, j, k);
+      const int64_t f0p = f0 + 1, f1p = g.face(1, i, j + 1, k),
+                    f2p = g.face(2, i, j, k + 1);
+      acc = (double)(alpha.x[f0] * gu.x[f0]) - (double)(alpha.x[f0p] * gu.x[f0p]) +
+            (double)(alpha.y[f1] * gu.y[f1]) - (double)(alpha.y[f1p] * gu.y[f1p]) +
+            (double)(alpha.z[f2] * gu.z[f2]) - (double)(alpha.z[f2p] * gu.z[f2p]);
+      acc *= -g.c;
+    }
+    gp[c] = (S)acc;
+    v[0] += acc * acc;
+  }
+  double tot[1];
+  if (grid_sum<1>(v, rs, tot) && threadIdx.x == 0) *norm2 = tot[0];
+}
+
+// Per face, with GP and Gy from the pressure and the adjoint variable:
+//   gS   = gU (U^ - c GP - U_s) + Gy (U^ - U_s) - c Gy GP
+//   gU^  = alpha (gU + Gy),   gU_s = (1 - alpha)(gU + Gy)
+// and the parameter gradient  sum_f gS_f dalpha_f/dtheta + gU_s,f du_s,f/dtheta
+// (Sec. 2.3.3), with dalpha/dtheta from the subsample ramps (narrow band).
+template <class T, class S>
+__global__ void k_adj_face(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
+                           const S *P, const S *y, Fields<T> gu,
+                           FieldsMut<T> guh, RedScratch rs, double *gtheta) {
+  double acc[kMaxParams];
+#pragma unroll
+  for (int q = 0; q < kMaxParams; ++q) acc[q] = 0.0;
+  const int64_t n = g.nface(0) + g.nface(1) + g.nface(2);
+  const double c = g.c;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int d;
+    int64_t f;
+    split_face(g, t, d, f);
+    int i, j, k;
+    g.face_ijk(d, f, i, j, k);
+    int64_t cL, cR;
+    face_cells(g, d, i, j, k, cL, cR);
+    const double GP = (cR >= 0 ? (double)P[cR] : 0.0) - (cL >= 0 ? (double)P[cL] : 0.0);
+    const double Gy = (cR >= 0 ? (double)y[cR] : 0.0) - (cL >= 0 ? (double)y[cL] : 0.0);
+    const double a = (double)comp(alpha, d)[f];
+    const double gU = (double)comp(gu, d)[f];
+    comp(guh, d)[f] = (T)(a * (gU + Gy));
+    if (s.K == 0 || g.boundary(d, i, j, k)) continue;
+    const double Uh = (double)comp(uh, d)[f];
+    const double us = (double)face_us<T>(g, s, d, i, j, k);
+    const double gUs = (1.0 - a) * (gU + Gy);
+    const double gS = gU * (Uh - c * GP - us) + Gy * (Uh - us) - c * Gy * GP;
+    double X, Y, Z;
+    face_pos(d, i, j, k, X, Y, Z);
+    double tmp[kMaxParams];
+    if (gUs != 0.0 && s.kind != NF_SCENE_SPHERES) {
+      scene_dus(s, d, X * g.dx, Y * g.dx, Z * g.dx, tmp);
+      for (int q = 0; q < s.K; ++q) acc[q] += gUs * tmp[q];
+    }
+    if (gS == 0.0) continue;
+    const float pc = scene_phi<float>(s, (float)(X * g.dx), (float)(Y * g.dx),
+                                      (float)(Z * g.dx));
+    const float margin = 0.8f * (float)g.dx;
+    if (pc > margin || pc < -margin) continue;
+    const double inv_w = 4.0 / g.dx;
+    double da[kMaxParams];
+    for (int q = 0; q < s.K; ++q) da[q] = 0.0;
+    for (int cz = 0; cz < 4; ++cz) {
+      const double z = (Z + (cz + 0.5) * 0.25 - 0.5) * g.dx;
+      for (int cy = 0; cy < 4; ++cy) {
+        const double yy = (Y + (cy + 0.5) * 0.25 - 0.5) * g.dx;
+        for (int cx = 0; cx < 4; ++cx) {
+          const double x = (X + (cx + 0.5) * 0.25 - 0.5) * g.dx;
+          const double h = 0.5 + scene_phi<double>(s, x, yy, z) * inv_w;
+          if (h > 0.0 && h < 1.0) {
+            scene_dphi(s, x, yy, z, tmp);
+            for (int q = 0; q < s.K; ++q) da[q] += inv_w * tmp[q];
+          }
+        }
+      }
+    }
+    for (int q = 0; q < s.K; ++q) acc[q] += gS * da[q] * (1.0 / 64.0);
+  }
+  double tot[kMaxParams];
+  if (grid_sum<kMaxParams>(acc, rs, tot) && threadIdx.x == 0)
+    for (int q = 0; q < kMaxParams; ++q) gtheta[q] = tot[q];
+}
+
+// ------------------------------------------------------------ launchers ---
+template <class T>
+void launch_rasterize(const Launch &L, const GridDev &g, const SceneDev &s,
+                      FieldsMut<T> alpha) {
+  const int64_t n = g.nface(0) + g.nface(1) + g.nface(2);
+  ProfScope _ps(L, NF_K_RASTERIZE);
+  k_rasterize<T><<<nblocks(n), kBlock, 0, L.s>>>(g, s, alpha);
+  ++*L.counter;
+}
+
+template <class T>
+void launch_advect(const Launch &L, const GridDev &g, Fields<T> u,
+                   FieldsMut<T> out, int order) {
+  const int64_t n = g.nface(0) + g.nface(1) + g.nface(2);
+  ProfScope _ps(L, NF_K_ADVECT);
+  k_advect<T><<<nblocks(n), kBlock, 0, L.s>>>(g, u, out, order);
+  ++*L.counter;
+}
+
+template <class T>
+void launch_advect_adjoint(const Launch &L, const GridDev &g, Fields<T> u,
+                           Fields<T> gut, FieldsMut<T> gu, int order) {
+  const int64_t n = g.nface(0) + g.nface(1) + g.nface(2);
+  cudaMemsetAsync(gu.x, 0, g.nface(0) * sizeof(T), L.s);
+  cudaMemsetAsync(gu.y, 0, g.nface(1) * sizeof(T), L.s);
+  cudaMemsetAsync(gu.z, 0, g.nface(2) * sizeof(T), L.s);
+  ProfScope _ps(L, NF_K_ADJ_ADVECT);
+  k_advect_adjoint<T><<<nblocks(n), kBlock, 0, L.s>>>(g, u, gut, gu, order);
+  ++*L.counter;
+}
+
+template <class T, class S>
+void launch_rhs(const Launch &L, const GridDev &g, const SceneDev &s,
+                Fields<T> alpha, Fields<T> uh, S *b, const RedScratch &rs,
+                double *bnorm2) {
+  ProfScope _ps(L, NF_K_RHS);
+  k_rhs<T, S><<<kRedBlocks, kBlock, 0, L.s>>>(g, s, alpha, uh, b, rs, bnorm2);
+  ++*L.counter;
+}
+
+template <class T, class S>
+void launch_remove_mean(const Launch &L, const GridDev &g, Fields<T> alpha,
+                        S *v, const RedScratch &rs, double *scratch) {
+  ProfScope _ps(L, NF_K_GAUGE);
+  k_active_sum<T, S><<<kRedBlocks, kBlock, 0, L.s>>>(g, alpha, v, rs, scratch);
+  k_sub_mean<T, S><<<kRedBlocks, kBlock, 0, L.s>>>(g, alpha, v, rs, scratch);
+  *L.counter += 2;
+}
+
+template <class T, class S>
+void launch_update(const Launch &L, const GridDev &g, const SceneDev &s,
+                   Fields<T> alpha, Fields<T> uh, const S *P, FieldsMut<T> u) {
+  const int64_t n = g.nface(0) + g.nface(1) + g.nface(2);
+  ProfScope _ps(L, NF_K_UPDATE);
+  k_update<T, S><<<nblocks(n), kBlock, 0, L.s>>>(g, s, alpha, uh, P, u);
+  ++*L.counter;
+}
+
+template <class T>
+void launch_loss(const Launch &L, const GridDev &g, int kind, Fields<T> u,
+                 FieldsMut<T> gu, bool want_grad, const RedScratch &rs,
+                 double *J) {
+  ProfScope _ps(L, NF_K_LOSS);
+  if (kind == NF_LOSS_KINETIC)
+    k_loss_kinetic<T><<<kRedBlocks, kBlock, 0, L.s>>>(g, u, gu, want_grad, rs, J);
+  else
+    k_loss_outflow<T><<<kRedBlocks, kBlock, 0, L.s>>>(g, u, gu, want_grad, rs, J);
+  ++*L.counter;
+}
+
+template <class T, class S>
+void launch_adj_gp(const Launch &L, const GridDev &g, Fields<T> alpha,
+                   Fields<T> gu, S *gp, const RedScratch &rs, double *norm2) {
+  ProfScope _ps(L, NF_K_ADJ_GP);
+  k_adj_gp<T, S><<<kRedBlocks, kBlock, 0, L.s>>>(g, alpha, gu, gp, rs, norm2);
+  ++*L.counter;
+}
+
+template <class T, class S>
+void launch_adj_face(const Launch &L, const GridDev &g, const SceneDev &s,
+                     Fields<T> alpha, Fields<T> uh, const S *P, const S *y,
+                     Fields<T> gu, FieldsMut<T> guh, const RedScratch &rs,
+                     double *gtheta) {
+  ProfScope _ps(L, NF_K_ADJ_FACE);
+  k_adj_face<T, S><<<kRedBlocks, kBlock, 0, L.s>>>(g, s, alpha, uh, P, y, gu, guh,
+                                                   rs, gtheta);
+  ++*L.counter;
+}
+
+#define NF_INST_T(T)                                                          \
+  template void launch_rasterize<T>(const Launch &, const GridDev &,        \
+                                    const SceneDev &, FieldsMut<T>);         \
+  template void launch_advect<T>(const Launch &, const GridDev &, Fields<T>,\
+                                 FieldsMut<T>, int);                         \
+  template void launch_advect_adjoint<T>(const Launch &, const GridDev &,   \
+                                         Fields<T>, Fields<T>, FieldsMut<T>, \
+                                         int);                               \
+  template void launch_loss<T>(const Launch &, const GridDev &, int,        \
+                               Fields<T>, FieldsMut<T>, bool,                \
+                               const RedScratch &, double *);
+#define NF_INST_TS(T, S)                                                      \
+  template void launch_rhs<T, S>(const Launch &, const GridDev &,           \
+                                 const SceneDev &, Fields<T>, Fields<T>, S *,\
+                                 const RedScratch &, double *);              \
+  template void launch_update<T, S>(const Launch &, const GridDev &,        \
+                                    const SceneDev &, Fields<T>, Fields<T>,  \
+                                    const S *, FieldsMut<T>);                \
+  template void launch_adj_gp<T, S>(const Launch &, const GridDev &,        \
+                                    Fields<T>, Fields<T>, S *,               \
+                                    const RedScratch &, double *);           \
+  template void launch_adj_face<T, S>(const Launch &, const GridDev &,      \
+                                      const SceneDev &, Fields<T>, Fields<T>,\
+                                      const S *, const S *, Fields<T>,       \
+                                      FieldsMut<T>, const RedScratch &,      \
+                                      double *);                             \
+  template void launch_remove_mean<T, S>(const Launch &, const GridDev &,   \
+                                         Fields<T>, S *, const RedScratch &, \
+                                         double *);
+NF_INST_T(float)
+NF_INST_T(double)
+NF_INST_TS(float, float)
+NF_INST_TS(float, double)
+NF_INST_TS(double, double)
+
+}  // namespace nf

@@ -1,0 +1,143 @@
+// Host-side launchers of the libnf kernels (explicitly instantiated in the
+// .cu files for the precisions the library uses).
+#pragma once
+
+#include "nf_internal.cuh"
+
+namespace nf {
+
+constexpr int kMaxParams = NF_MAX_PARAMS;
+
+template <class T>
+struct Fields {
+  const T *x, *y, *z;
+};
+template <class T>
+struct FieldsMut {
+  T *x, *y, *z;
+  operator Fields<T>() const { return Fields<T>{x, y, z}; }
+};
+
+// Device-resident state of one conjugate-gradient solve. Every iteration
+// kernel returns immediately once `done` is set, so the host may enqueue
+// iterations in batches and poll rarely without changing the result.
+struct CGState {
+  double rz;     // <r, z>
+  double dq;     // <d, A d>
+  double rr;     // <r, r>
+  double alpha, beta;
+  double stop2;  // stop when <r, r> <= stop2
+  int iters;
+  int done;      // 0 running, 1 converged, 2 breakdown, 3 non-finite
+};
+
+// One multigrid level: dimensions, operator scale c = dt / (rho dx_l) and
+// face fractions (component arrays) of type TA.
+template <class TA>
+struct LevelView {
+  int nx, ny, nz;
+  double c;
+  const TA *ax, *ay, *az;
+  __host__ __device__ int64_t ncell() const { return (int64_t)nx * ny * nz; }
+};
+
+// ------------------------------------------------------------- step ops ---
+template <class T>
+void launch_rasterize(const Launch &L, const GridDev &g, const SceneDev &s,
+                      FieldsMut<T> alpha);
+template <class T>
+void launch_advect(const Launch &L, const GridDev &g, Fields<T> u,
+                   FieldsMut<T> out, int order);
+template <class T>
+void launch_advect_adjoint(const Launch &L, const GridDev &g, Fields<T> u,
+                           Fields<T> gut, FieldsMut<T> gu, int order);
+template <class T, class S>
+void launch_rhs(const Launch &L, const GridDev &g, const SceneDev &s,
+                Fields<T> alpha, Fields<T> uh, S *b, const RedScratch &rs,
+                double *bnorm2);
+template <class T, class S>
+void launch_update(const Launch &L, const GridDev &g, const SceneDev &s,
+                   Fields<T> alpha, Fields<T> uh, const S *P, FieldsMut<T> u);
+template <class T>
+void launch_loss(const Launch &L, const GridDev &g, int kind, Fields<T> u,
+                 FieldsMut<T> gu, bool want_grad, const RedScratch &rs,
+                 double *J);
+template <class T, class S>
+void launch_adj_gp(const Launch &L, const GridDev &g, Fields<T> alpha,
+                   Fields<T> gu, S *gp, const RedScratch &rs, double *norm2);
+template <class T, class S>
+void launch_adj_face(const Launch &L, const GridDev &g, const SceneDev &s,
+                     Fields<T> alpha, Fields<T> uh, const S *P, const S *y,
+                     Fields<T> gu, FieldsMut<T> guh, const RedScratch &rs,
+                     double *gtheta);
+// Gauge of a closed box: subtract the mean over active cells (sum of face
+// fractions > 0) from the cell field v; optionally return ||v||^2 after.
+// scratch holds 3 doubles.
+template <class T, class S>
+void launch_remove_mean(const Launch &L, const GridDev &g, Fields<T> alpha,
+                        S *v, const RedScratch &rs, double *scratch);
+
+// ----------------------------------------------------------- solver ops ---
+// r = b - A x in precision S (fine operator with fractions of type T);
+// also writes r converted to V into rin (may be null) and ||r||^2.
+template <class S, class T, class V>
+void launch_residual_outer(const Launch &L, const LevelView<T> &lv,
+                           const S *b, const S *x, S *r, V *rin,
+                           const RedScratch &rs, double *norm2);
+// x += e (V -> S)
+template <class S, class V>
+void launch_axpy_outer(const Launch &L, int64_t n, S *x, const V *e);
+
+template <class V>
+void launch_cg_init(const Launch &L, int64_t n, const V *r, const V *z, V *d,
+                    CGState *st, const RedScratch &rs, double rel_tol);
+template <class V, class TA>
+void launch_apply_dot(const Launch &L, const LevelView<TA> &lv, const V *d,
+                      V *q, CGState *st, const RedScratch &rs);
+template <class V>
+void launch_cg_xr(const Launch &L, int64_t n, V *x, V *r, const V *d,
+                  const V *q, CGState *st, const RedScratch &rs,
+                  bool preconditioned);
+template <class V>
+void launch_cg_rz(const Launch &L, int64_t n, const V *r, const V *z,
+                  CGState *st, const RedScratch &rs);
+template <class V>
+void launch_cg_d(const Launch &L, int64_t n, const V *z, V *d,
+                 const CGState *st);
+
+// Multigrid pieces.
+template <class TI, class TO>
+void launch_mg_coarsen(const Launch &L, const LevelView<TI> &fine,
+                       int cnx, int cny, int cnz, TO *ax, TO *ay, TO *az);
+template <class V, class TA>
+void launch_mg_smooth(const Launch &L, const LevelView<TA> &lv, V *x,
+                      const V *b, int color, const CGState *st, int kclass);
+template <class V, class TA>
+void launch_mg_residual(const Launch &L, const LevelView<TA> &lv, const V *x,
+                        const V *b, V *r, const CGState *st);
+template <class V, class TA>
+void launch_mg_restrict(const Launch &L, const LevelView<TA> &fine,
+                        const LevelView<TA> &coarse, const V *rf, V *bc,
+                        const CGState *st);
+template <class V, class TF, class TC>
+void launch_mg_prolong(const Launch &L, const LevelView<TF> &fine,
+                       const LevelView<TC> &coarse, const V *xc, V *xf,
+                       const CGState *st);
+
+// The levels at and below `first` handled by one thread block: a whole
+// V-cycle on the small grids (levels first .. nlev-1), x zeroed inside.
+template <class V, class TA>
+struct CoarseChain {
+  int first, nlev;
+  LevelView<TA> lv[kMaxLevels];
+  V *x[kMaxLevels];
+  V *b[kMaxLevels];
+  V *r[kMaxLevels];
+  int smooth;         // sweeps per level
+  int coarsest_sweeps;
+};
+template <class V, class TA>
+void launch_mg_coarse_chain(const Launch &L, const CoarseChain<V, TA> &ch,
+                            const CGState *st);
+
+}  // namespace nf

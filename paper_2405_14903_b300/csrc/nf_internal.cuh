@@ -1,0 +1,204 @@
+// Internal definitions shared by the libnf translation units.
+//
+// Layout (device): face component d of a grid with nx*ny*nz cells is a dense
+// array with x fastest; the own axis of component d has one extra sample.
+// Cell (i, j, k) has linear index (k*ny + j)*nx + i.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+
+#include "../../include/nf.h"
+
+namespace nf {
+
+constexpr int kMaxLevels = 12;
+constexpr int kBlock = 256;          // threads per block of the stencil kernels
+constexpr int kRedBlocks = 148 * 4;  // blocks of grid-stride reduction kernels
+
+struct GridDev {
+  int nx, ny, nz;
+  double dx, dt, rho, c;  // c = dt / (rho dx)
+  int outlet, oj0, ok0, ow, oh;
+
+  __host__ __device__ int64_t ncell() const { return (int64_t)nx * ny * nz; }
+  __host__ __device__ int fnx(int d) const { return nx + (d == 0); }
+  __host__ __device__ int fny(int d) const { return ny + (d == 1); }
+  __host__ __device__ int fnz(int d) const { return nz + (d == 2); }
+  __host__ __device__ int64_t nface(int d) const {
+    return (int64_t)fnx(d) * fny(d) * fnz(d);
+  }
+  __host__ __device__ int64_t cell(int i, int j, int k) const {
+    return ((int64_t)k * ny + j) * nx + i;
+  }
+  __host__ __device__ int64_t face(int d, int i, int j, int k) const {
+    return ((int64_t)k * fny(d) + j) * fnx(d) + i;
+  }
+  // Linear face index -> (i, j, k) of component d.
+  __host__ __device__ void face_ijk(int d, int64_t f, int &i, int &j,
+                                    int &k) const {
+    int fx = fnx(d), fy = fny(d);
+    i = (int)(f % fx);
+    int64_t r = f / fx;
+    j = (int)(r % fy);
+    k = (int)(r / fy);
+  }
+  __host__ __device__ void cell_ijk(int64_t c, int &i, int &j, int &k) const {
+    i = (int)(c % nx);
+    int64_t r = c / nx;
+    j = (int)(r % ny);
+    k = (int)(r / ny);
+  }
+  // Is face (d; i, j, k) on the box boundary?
+  __host__ __device__ bool boundary(int d, int i, int j, int k) const {
+    int o = d == 0 ? i : (d == 1 ? j : k);
+    int n = d == 0 ? nx : (d == 1 ? ny : nz);
+    return o == 0 || o == n;
+  }
+  __host__ __device__ bool outlet_face(int d, int i, int j, int k) const {
+    return outlet && d == 0 && i == nx && j >= oj0 && j < oj0 + ow &&
+           k >= ok0 && k < ok0 + oh;
+  }
+};
+
+// Scene state at one time t (built on the host in double precision).
+struct SceneDev {
+  int kind;
+  int K;
+  double t;
+  // sphere: centre c(t) = c0 + v t, radius, velocity v = theta
+  double sc[3], sr, sv[3];
+  // chamber: centre, axes, min axis, radius s(t), rate sdot(t) and their
+  // theta derivatives; duct box centre and half extents (fluid inside)
+  double cc[3], ca[3], camin, cs, csdot, cds[8], cdsdot[8];
+  double dc[3], dh[3];
+  // plate: centre, half extents, angle, cos/sin, rate, theta derivatives
+  double pc[3], ph[3], pang, pcos, psin, pomega, pdang[4], pdomega[4];
+  // static spheres (device array of nspheres x 4 doubles)
+  const double *spheres;
+  int nspheres;
+};
+
+// ------------------------------------------------------------ launches ----
+struct Prof;  // CUDA-event timing of one kernel class (util.h)
+void prof_begin(Prof *p, int kclass, cudaStream_t s, int *slot);
+void prof_end(Prof *p, int slot, cudaStream_t s);
+
+struct Launch {
+  cudaStream_t s;
+  int64_t *counter;  // host-side count of kernels issued
+  Prof *prof;        // null unless nf_profile is active
+};
+
+// Brackets one launch with CUDA events when its class is being profiled.
+struct ProfScope {
+  Prof *p;
+  cudaStream_t s;
+  int slot = -1;
+  ProfScope(const Launch &L, int kclass) : p(L.prof), s(L.s) {
+    if (p) prof_begin(p, kclass, s, &slot);
+  }
+  ~ProfScope() {
+    if (p && slot >= 0) prof_end(p, slot, s);
+  }
+};
+
+inline unsigned nblocks(int64_t n, int b = kBlock) {
+  return (unsigned)((n + b - 1) / b);
+}
+
+// ----------------------------------------------------------- reductions ----
+// Deterministic grid reduction: every block writes its partial sums, the
+// last block to finish adds them in fixed block order. Results do not depend
+// on scheduling, so a recomputed forward reproduces the same bits.
+struct RedScratch {
+  double *partials;      // kRedBlocks * kMaxWidth
+  unsigned int *ticket;  // one counter, reset by the last block
+};
+constexpr int kMaxWidth = 16;
+
+template <int W>
+__device__ inline void block_sum(double (&v)[W], double *smem /*W*32*/) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    double x = v[w];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) smem[w * 32 + warp] = x;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      double x = lane < nw ? smem[w * 32 + lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      v[w] = x;  // valid in thread 0
+    }
+  }
+  __syncthreads();
+}
+
+// Write this block's partials; returns true in every thread of the block that
+// finishes last, after which `tot` holds the fixed-order grand totals.
+template <int W>
+__device__ inline bool grid_sum(double (&v)[W], const RedScratch &rs,
+                                double (&tot)[W]) {
+  __shared__ double smem[W * 32];
+  __shared__ bool last;
+  block_sum<W>(v, smem);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) rs.partials[blockIdx.x * W + w] = v[w];
+    __threadfence();
+    unsigned t = atomicAdd(rs.ticket, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double acc[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) acc[w] = 0.0;
+  // fixed order: thread t sums blocks t, t + blockDim, ...
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+      acc[w] += *((volatile double *)&rs.partials[b * W + w]);
+  }
+  block_sum<W>(acc, smem);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) smem[w] = acc[w];
+    *rs.ticket = 0u;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int w = 0; w < W; ++w) tot[w] = smem[w];
+  __syncthreads();
+  return true;
+}
+
+// ---------------------------------------------------------- conversions ----
+__device__ __forceinline__ float ld(const float *p) { return *p; }
+__device__ __forceinline__ double ld(const double *p) { return *p; }
+__device__ __forceinline__ float ld(const __nv_bfloat16 *p) {
+  return __bfloat162float(*p);
+}
+template <class T>
+__device__ __forceinline__ T cvt(double x);
+template <>
+__device__ __forceinline__ float cvt<float>(double x) { return (float)x; }
+template <>
+__device__ __forceinline__ double cvt<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16>(double x) {
+  return __float2bfloat16((float)x);
+}
+
+}  // namespace nf

@@ -1,0 +1,306 @@
+// Host orchestration of the pressure solve A P = b (Eq. projection_matrix).
+//
+// Outer loop: iterative refinement in precision S, r = b - A P computed with
+// FP64 arithmetic (k_residual_outer); inner loop: CG (plain or V-cycle
+// preconditioned) in precision V on A e = r, then P += e. With S = V the
+// inner solve targets the final tolerance and the outer loop only confirms
+// it; with S = double, V = float (MIXED) each inner solve reduces the
+// residual by `inner_tol`.
+//
+// Iteration kernels stop themselves once the device-side CGState says the
+// solve is done, so iterations are enqueued in batches and the host polls
+// the state once per batch.
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "util.h"
+
+namespace nf {
+
+struct SolveStats {
+  int iters = 0;
+  int outer = 0;
+  double rel = 0.0;
+  int status = NF_OK;
+};
+
+template <class T, class S, class V, class TA>
+class Solver {
+ public:
+  Solver(Ctx *ctx, const GridDev &g, const nf_config &cfg)
+      : ctx_(ctx), g_(g), cfg_(cfg) {}
+
+  // Allocates the hierarchy. Returns NF_OK or an error status.
+  int init(Alloc &A) {
+    n_ = g_.ncell();
+    CKS(A.get(&r_, n_ * sizeof(S)));
+    CKS(A.get(&rin_, n_ * sizeof(V)));
+    CKS(A.get(&e_, n_ * sizeof(V)));
+    CKS(A.get(&z_, n_ * sizeof(V)));
+    CKS(A.get(&d_, n_ * sizeof(V)));
+    CKS(A.get(&q_, n_ * sizeof(V)));
+    CKS(A.get(&st_, sizeof(CGState)));
+    CKS(A.get(&norm2_, 2 * sizeof(double)));
+    mg_ = cfg_.solver == NF_SOLVER_MGPCG;
+    // level 0 uses the episode's fractions (type T); levels >= 1 own TA arrays
+    int nx = g_.nx, ny = g_.ny, nz = g_.nz;
+    double c = g_.c;
+    levels_.clear();
+    levels_.push_back(Level{nx, ny, nz, c});
+    if (mg_) {
+      const int mn = std::max(2, cfg_.mg_coarsest);
+      while (nx % 2 == 0 && ny % 2 == 0 && nz % 2 == 0 && nx / 2 >= mn &&
+             ny / 2 >= mn && nz / 2 >= mn && (int)levels_.size() < kMaxLevels) {
+        nx /= 2;
+        ny /= 2;
+        nz /= 2;
+        c *= 0.5;  // c_l = dt / (rho dx_l), dx_l = 2 dx_{l-1}
+        levels_.push_back(Level{nx, ny, nz, c});
+      }
+      for (size_t l = 0; l < levels_.size(); ++l) {
+        Level &L = levels_[l];
+        const int64_t nc = (int64_t)L.nx * L.ny * L.nz;
+        if (l > 0) {
+          CKS(A.get(&L.ax, (int64_t)(L.nx + 1) * L.ny * L.nz * sizeof(TA)));
+          CKS(A.get(&L.ay, (int64_t)L.nx * (L.ny + 1) * L.nz * sizeof(TA)));
+          CKS(A.get(&L.az, (int64_t)L.nx * L.ny * (L.nz + 1) * sizeof(TA)));
+          CKS(A.get(&L.x, nc * sizeof(V)));
+          CKS(A.get(&L.b, nc * sizeof(V)));
+        }
+        CKS(A.get(&L.r, nc * sizeof(V)));
+      }
+      // first level handled inside the one-block chain kernel
+      first_chain_ = (int)levels_.size() - 1;
+      while (first_chain_ > 0) {
+        const Level &L = levels_[first_chain_ - 1];
+        if ((int64_t)L.nx * L.ny * L.nz > kChainCells) break;
+        --first_chain_;
+      }
+    }
+    return NF_OK;
+  }
+
+  // New fractions for level 0 (device arrays of type T): rebuild coarse
+  // fractions (mean of the four fine sub-faces).
+  void set_fractions(const T *ax, const T *ay, const T *az) {
+    ax0_ = ax;
+    ay0_ = ay;
+    az0_ = az;
+    if (!mg_) return;
+    Launch L = ctx_->launch();
+    for (size_t l = 1; l < levels_.size(); ++l) {
+      Level &C = levels_[l];
+      if (l == 1)
+        launch_mg_coarsen<T, TA>(L, view0(), C.nx, C.ny, C.nz, (TA *)C.ax,
+                                 (TA *)C.ay, (TA *)C.az);
+      else
+        launch_mg_coarsen<TA, TA>(L, viewc(l - 1), C.nx, C.ny, C.nz,
+                                  (TA *)C.ax, (TA *)C.ay, (TA *)C.az);
+    }
+  }
+
+  // Solve A x = b (x overwritten). bnorm2 is ||b||^2 already on the host.
+  SolveStats solve(const S *b, S *x, double bnorm2) {
+    SolveStats out;
+    Launch L = ctx_->launch();
+    cudaMemsetAsync(x, 0, n_ * sizeof(S), L.s);
+    if (!(bnorm2 > 0.0)) {
+      out.rel = 0.0;
+      if (!std::isfinite(bnorm2)) out.status = NF_E_DIVERGED;
+      return out;
+    }
+    const double tol = cfg_.tol;
+    const bool mixed = sizeof(S) != sizeof(V);
+    double rn2 = residual(b, x);  // r = b - A 0
+    out.rel = std::sqrt(rn2 / bnorm2);
+    int total = 0;
+    for (int pass = 0; pass < kMaxOuter && out.rel > tol; ++pass) {
+      if (!std::isfinite(rn2)) {
+        out.status = NF_E_DIVERGED;
+        break;
+      }
+      double inner = mixed ? std::max(cfg_.inner_tol, 0.5 * tol / out.rel)
+                           : 0.5 * tol / out.rel;
+      inner = std::min(inner, 0.5);
+      int it = 0, done = 0;
+      inner_solve(inner, cfg_.max_iters - total, &it, &done);
+      total += it;
+      out.outer += 1;
+      launch_axpy_outer<S, V>(L, n_, x, (const V *)e_);
+      rn2 = residual(b, x);
+      out.rel = std::sqrt(rn2 / bnorm2);
+      if (done == 3 || !std::isfinite(rn2)) {
+        out.status = NF_E_DIVERGED;
+        break;
+      }
+      if (total >= cfg_.max_iters) break;
+      if (done == 2 && it == 0) break;  // no progress possible
+    }
+    out.iters = total;
+    if (out.status == NF_OK && out.rel > tol) out.status = NF_E_NOT_CONVERGED;
+    return out;
+  }
+
+  int levels() const { return (int)levels_.size(); }
+
+ private:
+  struct Level {
+    int nx, ny, nz;
+    double c;
+    void *ax = nullptr, *ay = nullptr, *az = nullptr;
+    void *x = nullptr, *b = nullptr, *r = nullptr;
+  };
+  static constexpr int kMaxOuter = 12;
+  static constexpr int kChainCells = 16 * 16 * 16;
+  static constexpr int kBatch = 4;
+  static constexpr int kCoarsestSweeps = 24;
+
+  LevelView<T> view0() const {
+    return LevelView<T>{g_.nx, g_.ny, g_.nz, g_.c, ax0_, ay0_, az0_};
+  }
+  LevelView<TA> viewc(size_t l) const {
+    const Level &L = levels_[l];
+    return LevelView<TA>{L.nx, L.ny, L.nz, L.c, (const TA *)L.ax,
+                         (const TA *)L.ay, (const TA *)L.az};
+  }
+
+  double residual(const S *b, const S *x) {
+    Launch L = ctx_->launch();
+    launch_residual_outer<S, T, V>(L, view0(), b, x, (S *)r_, (V *)rin_,
+                                   ctx_->rs, (double *)norm2_);
+    return ctx_->read_double((double *)norm2_);
+  }
+
+  void smooth(int l, V *x, const V *b, int color, const CGState *st) {
+    Launch L = ctx_->launch();
+    if (l == 0)
+      launch_mg_smooth<V, T>(L, view0(), x, b, color, st, NF_K_MG_SMOOTH0);
+    else
+      launch_mg_smooth<V, TA>(L, viewc(l), x, b, color, st, NF_K_MG_SMOOTH);
+  }
+
+  CoarseChain<V, TA> chain(int first) const {
+    CoarseChain<V, TA> ch;
+    ch.first = first;
+    ch.nlev = (int)levels_.size();
+    for (int l = first; l < ch.nlev; ++l) {
+      ch.lv[l] = viewc(l);
+      ch.x[l] = (V *)levels_[l].x;
+      ch.b[l] = (V *)levels_[l].b;
+      ch.r[l] = (V *)levels_[l].r;
+    }
+    ch.smooth = std::max(1, cfg_.mg_smooth);
+    ch.coarsest_sweeps = kCoarsestSweeps;
+    return ch;
+  }
+
+  // z = M r: one symmetric V-cycle (red-black pre-smoothing, black-red
+  // post-smoothing) from z = 0. Levels above kChainCells cells run as grid
+  // kernels, the small ones inside one thread block.
+  void precondition(const V *r, V *z, const CGState *st) {
+    Launch L = ctx_->launch();
+    const int nl = (int)levels_.size();
+    const int F = std::max(1, first_chain_);  // level 0 always on grid kernels
+    const int nu = std::max(1, cfg_.mg_smooth);
+    const int down = std::min(F, nl - 1);     // levels with a coarser level
+    for (int l = 0; l < down; ++l) {
+      V *x = l == 0 ? z : (V *)levels_[l].x;
+      const V *b = l == 0 ? r : (const V *)levels_[l].b;
+      const int64_t nc = (int64_t)levels_[l].nx * levels_[l].ny * levels_[l].nz;
+      cudaMemsetAsync(x, 0, nc * sizeof(V), L.s);
+      for (int s = 0; s < nu; ++s) {
+        smooth(l, x, b, 0, st);
+        smooth(l, x, b, 1, st);
+      }
+      if (l == 0)
+        launch_mg_residual<V, T>(L, view0(), x, b, (V *)levels_[0].r, st);
+      else
+        launch_mg_residual<V, TA>(L, viewc(l), x, b, (V *)levels_[l].r, st);
+      const LevelView<TA> f{levels_[l].nx, levels_[l].ny, levels_[l].nz, 0.0,
+                            nullptr, nullptr, nullptr};
+      launch_mg_restrict<V, TA>(L, f, viewc(l + 1), (const V *)levels_[l].r,
+                                (V *)levels_[l + 1].b, st);
+    }
+    if (nl == 1) {
+      // no coarser grid: symmetric Gauss-Seidel sweeps only
+      cudaMemsetAsync(z, 0, n_ * sizeof(V), L.s);
+      for (int s = 0; s < kCoarsestSweeps; ++s) {
+        smooth(0, z, r, 0, st);
+        smooth(0, z, r, 1, st);
+      }
+      for (int s = 0; s < kCoarsestSweeps; ++s) {
+        smooth(0, z, r, 1, st);
+        smooth(0, z, r, 0, st);
+      }
+      return;
+    }
+    launch_mg_coarse_chain<V, TA>(L, chain(down), st);
+    for (int l = down - 1; l >= 0; --l) {
+      V *x = l == 0 ? z : (V *)levels_[l].x;
+      const V *b = l == 0 ? r : (const V *)levels_[l].b;
+      if (l == 0)
+        launch_mg_prolong<V, T, TA>(L, view0(), viewc(l + 1),
+                                    (const V *)levels_[l + 1].x, x, st);
+      else
+        launch_mg_prolong<V, TA, TA>(L, viewc(l), viewc(l + 1),
+                                     (const V *)levels_[l + 1].x, x, st);
+      for (int s = 0; s < nu; ++s) {
+        smooth(l, x, b, 1, st);
+        smooth(l, x, b, 0, st);
+      }
+    }
+  }
+
+  void inner_solve(double rel_tol, int max_it, int *iters, int *done) {
+    Launch L = ctx_->launch();
+    CGState *st = (CGState *)st_;
+    V *r = (V *)rin_, *z = (V *)z_, *d = (V *)d_, *q = (V *)q_, *e = (V *)e_;
+    cudaMemsetAsync(e, 0, n_ * sizeof(V), L.s);
+    if (mg_) {
+      precondition(r, z, nullptr);
+      launch_cg_init<V>(L, n_, r, z, d, st, ctx_->rs, rel_tol);
+    } else {
+      launch_cg_init<V>(L, n_, r, r, d, st, ctx_->rs, rel_tol);
+    }
+    const LevelView<T> lv = view0();
+    int issued = 0;
+    CGState hs{};
+    while (issued < max_it) {
+      const int batch = std::min(kBatch, max_it - issued);
+      for (int b = 0; b < batch; ++b) {
+        launch_apply_dot<V, T>(L, lv, d, q, st, ctx_->rs);
+        launch_cg_xr<V>(L, n_, e, r, d, q, st, ctx_->rs, mg_);
+        if (mg_) {
+          precondition(r, z, st);
+          launch_cg_rz<V>(L, n_, r, z, st, ctx_->rs);
+          launch_cg_d<V>(L, n_, z, d, st);
+        } else {
+          launch_cg_d<V>(L, n_, r, d, st);
+        }
+      }
+      issued += batch;
+      ctx_->read_bytes(&hs, st, sizeof(CGState));
+      if (hs.done) break;
+    }
+    *iters = hs.iters;
+    *done = hs.done;
+  }
+
+  Ctx *ctx_;
+  GridDev g_;
+  nf_config cfg_;
+  int64_t n_ = 0;
+  bool mg_ = false;
+  int first_chain_ = 0;
+  std::vector<Level> levels_;
+  const T *ax0_ = nullptr, *ay0_ = nullptr, *az0_ = nullptr;
+  void *r_ = nullptr, *rin_ = nullptr, *e_ = nullptr, *z_ = nullptr,
+       *d_ = nullptr, *q_ = nullptr, *st_ = nullptr, *norm2_ = nullptr;
+};
+
+}  // namespace nf

@@ -1,0 +1,96 @@
+"""The C ABI library loads and exports every declared entry point (no GPU).
+
+No compute call is made here: only symbol lookup, struct layouts and
+argument checks that fail before any device is touched.
+"""
+
+import ctypes
+import os
+import re
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "nf.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(nf_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2405_14903_b300 import _lib
+    return _lib.lib
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("nf_create", "nf_destroy", "nf_episode_create", "nf_set_params",
+                     "nf_set_velocity", "nf_step", "nf_backward_step", "nf_backward",
+                     "nf_get_velocity", "nf_get_pressure", "nf_get_fractions", "nf_loss",
+                     "nf_status_string"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_python_signatures_cover_the_header():
+    from paper_2405_14903_b300 import _lib
+    bound = {n for n, _, _ in _lib.SIGNATURES}
+    assert set(declared_functions()) <= bound
+
+
+def test_kernel_class_names_match_the_header():
+    from paper_2405_14903_b300 import _lib
+    src = open(HEADER).read()
+    codes = dict(re.findall(r"#define NF_K_([A-Z0-9_]+) (\d+)", src))
+    assert int(codes.pop("COUNT")) == len(_lib.KCLASS)
+    for name, code in codes.items():
+        assert _lib.KCLASS[int(code)] == name.lower()
+
+
+def test_status_strings_and_defaults(lib):
+    from paper_2405_14903_b300 import _lib
+    for s in range(0, 8):
+        assert lib.nf_status_string(s)
+    cfg = _lib.Config()
+    assert lib.nf_config_default(ctypes.byref(cfg)) == 0
+    assert cfg.precision == _lib.PREC["mixed"] and cfg.solver == _lib.SOLVER["mgpcg"]
+    assert cfg.checkpoint_every == 10 and abs(cfg.tol - 1e-6) < 1e-18
+
+
+def test_invalid_arguments_are_rejected_without_a_device(lib):
+    from paper_2405_14903_b300 import _lib
+    assert lib.nf_config_default(None) == _lib.NF_E_INVALID
+    assert lib.nf_create(None, None) == _lib.NF_E_INVALID
+    assert lib.nf_destroy(None) == _lib.NF_E_INVALID
+    cfg = _lib.Config()
+    lib.nf_config_default(ctypes.byref(cfg))
+    cfg.tol = -1.0
+    h = ctypes.c_void_p()
+    assert lib.nf_create(ctypes.byref(h), ctypes.byref(cfg)) == _lib.NF_E_INVALID
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    # the ctypes mirrors must have the sizes the C compiler gives the header's
+    # structs (compiled here with the host compiler)
+    from paper_2405_14903_b300 import _lib
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no host C compiler")
+    src = tmp_path / "sz.c"
+    src.write_text('#include <stdio.h>\n#include "nf.h"\nint main(void){printf("%zu %zu %zu %zu", '
+                   'sizeof(nf_config), sizeof(nf_grid), sizeof(nf_scene), sizeof(nf_step_stats));return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.check_call([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    sizes = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    assert sizes == [ctypes.sizeof(_lib.Config), ctypes.sizeof(_lib.Grid),
+                     ctypes.sizeof(_lib.Scene), ctypes.sizeof(_lib.StepStats)]
