@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Throughput of the differentiable rollout: cell-steps/s of forward + adjoint.
+
+Workload (one bench step): the pulsing chamber of 128^3 cells with a 16 x 16
+outlet patch, 100 time steps of dt = 0.005 (RK2 advection, rasterisation,
+MIXED MGPCG projection to relative residual 1e-6), the outflow loss, and the
+full adjoint with checkpoints every 10 steps (segments recomputed). value =
+128^3 * 100 / seconds per bench step.
+
+Also reported: the end-to-end figure through the public API with host
+buffers (``e2e``), the same GPU's plain FP64 CG and FP64 MGPCG paths on a
+shorter rollout of the same scene, the roofline of the dominant kernel, the
+FP64 CPU oracle on a bounded sample (``cpu_baseline``), and the SM clocks
+sampled during the timed region.
+
+``--impl reference`` times the FP64 CPU oracle itself on bounded samples of
+the same workload (there is no other reference implementation).
+
+Launch: ``python bench.py [--gpus N] [--steps K] [--warmup W]``; for N > 1
+under torchrun every rank runs an independent replica (weak scaling).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import nf_inputs as I  # noqa: E402
+
+METRIC = "cell-steps/s fwd+adjoint at 128^3 (rel res <= 1e-6)"
+UNIT = "cell-steps/s"
+HBM_FALLBACK = 6400.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--rollout", type=int, default=100)
+    ap.add_argument("--plain-rollout", type=int, default=10)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip FP64 comparison paths, e2e and the CPU baseline")
+    ap.add_argument("--cpu-n", type=int, default=64,
+                    help="grid of the bounded CPU oracle sample")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK, "fallback"
+
+
+# ---------------------------------------------------------------- clocks ----
+
+class Clocks:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------- workloads ----
+
+def chamber(n, steps, seed):
+    return I.config_chamber(n, steps=steps, seed=seed, duct_half_cells=max(2, 8 * n // 128))
+
+
+# Algorithmic bytes per cell of the kernels the roofline may name (FP32
+# fields, FP32 fractions on the finest level): what the operation must move.
+ALG_BYTES_PER_CELL = {
+    # red-black half sweep: x of the other colour (n/2), b (n/2), the six
+    # fractions of the updated cells = every face once (3n), x written (n/2)
+    "mg_smooth0": 4 * 0.5 + 4 * 0.5 + 3 * 4 + 4 * 0.5,
+    "apply_dot": 4 + 3 * 4 + 4,            # d, three fraction arrays, q
+    "cg_xr": 4 * 4 + 2 * 4,                # x, r, d, q read; x, r written
+    "residual64": 8 + 8 + 3 * 4 + 8 + 4,   # b, x (FP64), fractions, r64, r32
+}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    import paper_2405_14903_b300 as P
+    dev = f"cuda:{local_rank}"
+    n, T = args.n, args.rollout
+    cfg = chamber(n, T, seed=rank)
+    ncell = n ** 3
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    ctx = P.Context("mixed", "mgpcg", tol=1e-6, max_iters=1000, checkpoint_every=10,
+                    cfl_max=cfg["cfl_max"], device=local_rank)
+    ep = ctx.episode(cfg["grid"], cfg["scene"])
+    u0 = [torch.zeros(s, dtype=torch.float32, device=dev) for s in ep.face_shapes]
+    stats = {}
+
+    def one_step():
+        ep.set_velocity(u0, project=False)
+        fs = ep.step(T)
+        J, gU = ep.loss("outflow", want_grad=True)
+        gth, _, bs = ep.backward(gU, want_gU0=False)
+        stats["fwd"], stats["bwd"] = fs, bs
+        return J, gth
+
+    # warm-up; the first one also times every kernel class to find the
+    # dominant kernel of the step
+    ctx.profile("all")
+    one_step()
+    torch.cuda.synchronize(dev)
+    shares = {k: ctx.profile_read(k) for k in P._lib.KCLASS}
+    ctx.profile(None)
+    dominant = max(shares, key=lambda k: shares[k][1])
+    for _ in range(max(0, args.warmup - 1)):
+        one_step()
+    torch.cuda.synchronize(dev)
+
+    # timed region; launches of the roofline kernel are bracketed by CUDA
+    # events on the library's stream (torch's current stream)
+    roof_class = dominant if dominant in ALG_BYTES_PER_CELL else "mg_smooth0"
+    ctx.profile(roof_class)
+    clocks = Clocks(local_rank) if rank == 0 else None
+    launches0 = ctx.launches()
+    barrier()
+    torch.cuda.synchronize(dev)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        J, gth = one_step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    launches = ctx.launches() - launches0
+    clk = clocks.stop() if clocks else None
+    nl, kms = ctx.profile_read(roof_class)
+    ctx.profile(None)
+
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_per_step = float(t.item()) / args.steps
+    value = world * ncell * T / (ms_per_step / 1e3)
+
+    out = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
+               warmup=args.warmup, ms_per_step=ms_per_step, higher_is_better=True,
+               scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+               config=dict(workload=f"pulsing chamber {n}^3, {T} steps dt=0.005, 16x16 outlet, "
+                                    "outflow loss; forward rollout + full adjoint",
+                           grid=n, rollout_steps=T, checkpoint_every=10,
+                           cfl_max=cfg["cfl_max"], substeps_executed=int(stats["fwd"]["steps"]),
+                           precision="FP32 MGPCG, BF16 coarse-level fractions, FP64 dots and "
+                                     "FP64 iterative refinement to rel res 1e-6",
+                           l2="inputs larger than L2 (episode state and tape > 1 GB)",
+                           parallelism=f"replicas x{world}"),
+               gpu_launches=int(launches), iterations=dict(fwd=stats["fwd"], bwd=stats["bwd"]),
+               loss=J, dJ_dtheta=[float(x) for x in gth], clocks=clk)
+    if rank != 0:
+        return None
+
+    peak, src = peaks()
+    per_launch = ALG_BYTES_PER_CELL[roof_class] * ncell
+    avg_ms = kms / max(nl, 1)
+    achieved = per_launch / (avg_ms / 1e3) / 1e9 if nl else None
+    out["roofline"] = dict(bound="hbm", kernel=roof_class, achieved=achieved, peak=peak,
+                           peak_source=src, unit="GB/s",
+                           frac=(achieved / peak) if achieved else None, traffic=None,
+                           launches=nl, avg_us=1e3 * avg_ms, alg_bytes_per_launch=per_launch)
+    tot = sum(v[1] for v in shares.values()) or 1.0
+    out["kernel_shares"] = {k: round(v[1] / tot, 4) for k, v in
+                            sorted(shares.items(), key=lambda kv: -kv[1][1]) if v[1] > 0}
+    if not args.no_extras:
+        out["e2e"] = run_e2e(args, torch, cfg, dev, ep)
+        out["fp64_plain"] = run_plain(args, P, torch, dev)
+        out["cpu_baseline"] = cpu_baseline(args)
+    ep.close()
+    ctx.close()
+    return out
+
+
+def run_e2e(args, torch, cfg, dev, ep):
+    """The same metric through the public API with pinned host buffers."""
+    T = args.rollout
+    u_host = [torch.zeros(s, dtype=torch.float32).pin_memory() for s in ep.face_shapes]
+    theta = np.asarray(cfg["scene"]["theta"], dtype=np.float64)
+    h2d = sum(u.numel() * 4 for u in u_host) + theta.nbytes
+
+    def one():
+        ep.set_params(theta)
+        ep.set_velocity(u_host, project=False)
+        ep.step(T)
+        J, gU = ep.loss("outflow", want_grad=True)
+        gth, _, _ = ep.backward(gU, want_gU0=False)      # lands in host memory
+        return J, gth
+
+    one()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        J, gth = one()
+    torch.cuda.synchronize(dev)
+    dt = (time.perf_counter() - t0) / args.steps
+    return dict(value=args.n ** 3 * T / dt, unit=UNIT, h2d_bytes_per_step=int(h2d),
+                d2h_bytes_per_step=int(8 + gth.nbytes), ms_per_step=1e3 * dt)
+
+
+def run_plain(args, P, torch, dev):
+    """The same GPU's FP64 CG and FP64 MGPCG on a shorter rollout."""
+    res = {}
+    T = args.plain_rollout
+    for solver in ("cg", "mgpcg"):
+        cfg = chamber(args.n, T, seed=0)
+        ctx = P.Context("fp64", solver, tol=1e-6, max_iters=20000, checkpoint_every=10,
+                        cfl_max=cfg["cfl_max"])
+        ep = ctx.episode(cfg["grid"], cfg["scene"])
+        u0 = [torch.zeros(s, dtype=torch.float64, device=dev) for s in ep.face_shapes]
+
+        def one():
+            ep.set_velocity(u0, project=False)
+            fs = ep.step(T)
+            J, gU = ep.loss("outflow", want_grad=True)
+            gth, _, bs = ep.backward(gU, want_gU0=False)
+            return fs, bs
+
+        one()
+        torch.cuda.synchronize(dev)
+        s = torch.cuda.current_stream(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        fs, bs = one()
+        e1.record(s)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        res[solver] = dict(value=args.n ** 3 * T / (ms / 1e3), unit=UNIT, rollout_steps=T,
+                           substeps=int(fs["steps"]), ms_per_rollout=ms,
+                           fwd_iters=fs["iters"], bwd_iters=bs["iters"])
+        ep.close()
+        ctx.close()
+    return res
+
+
+def cpu_baseline(args):
+    """The FP64 oracle on a bounded sample: one forward + adjoint step of the
+    same chamber scene on a coarser grid, scaled to cell-steps/s."""
+    from oracle import Grid
+    from oracle import step as S
+    n = args.cpu_n
+    cfg = chamber(n, 1, seed=0)
+    g = Grid(cfg["grid"])
+    t0 = time.perf_counter()
+    U, tape = S.step(g, cfg["scene"], cfg["u0"], 0, 1e-6)
+    J, gU = S.outflow(g, U)
+    S.rollout_backward(g, cfg["scene"], [tape], gU, 1e-6)
+    dt = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", "0")) or os.cpu_count()
+    return dict(value=n ** 3 / dt, unit=UNIT, cores=threads, kind="oracle",
+                sample=f"1 step (forward + adjoint) of the same chamber scene on {n}^3 "
+                       f"(FP64 NumPy, unpreconditioned CG to 1e-6), scaled per cell-step; "
+                       f"a coarser grid needs fewer CG iterations, so this flatters the oracle",
+                seconds=dt)
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return None
+    K, W = args.steps, args.warmup
+    for _ in range(W):
+        cpu_baseline(args)
+    vals = [cpu_baseline(args) for _ in range(K)]
+    v = float(np.mean([x["value"] for x in vals]))
+    secs = float(np.mean([x["seconds"] for x in vals]))
+    base = vals[-1]
+    return dict(metric=METRIC, value=v, unit=UNIT, n_gpus=1, steps=K, warmup=W,
+                ms_per_step=1e3 * secs, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
+                config=dict(workload=f"pulsing chamber, bounded sample: {base['sample']}",
+                            grid=args.cpu_n),
+                cpu_baseline=dict(value=v, unit=UNIT, cores=base["cores"], kind="oracle",
+                                  sample=base["sample"]),
+                e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank)
+    else:
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl")
+        out = run_ours(args, rank, world, local_rank)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

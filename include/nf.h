@@ -93,6 +93,10 @@ typedef struct nf_config {
   int advect_order;       /* 2 = RK2 midpoint backtrace, 1 = forward Euler    */
   int checkpoint_every;   /* rollout checkpoint interval C (steps)            */
   size_t hbm_budget;      /* admission budget for episode state; 0 = none     */
+  double cfl_max;         /* 0: nf_step advances steps of dt. > 0: nf_step
+                             advances frames of dt, each split into
+                             m = ceil(max|U| dt / (dx cfl_max)) equal substeps
+                             (velocity at the frame start)                   */
 } nf_config;
 
 typedef struct nf_grid {
@@ -129,7 +133,7 @@ typedef struct nf_step_stats {
 
 /* Fill *cfg with defaults: device 0, own stream, MIXED, MGPCG, tol 1e-6,
    max_iters 500, inner_tol 1e-3, mg_smooth 2, mg_coarsest 4, RK2,
-   checkpoint_every 10, no budget. */
+   checkpoint_every 10, no budget, cfl_max 0 (no sub-stepping). */
 int nf_config_default(nf_config *cfg);
 
 /* Create a context on cfg->device. *out receives the handle. */
@@ -169,13 +173,16 @@ int nf_set_params(nf_ctx *ctx, int64_t id, const double *theta, int K);
 int nf_set_velocity(nf_ctx *ctx, int64_t id, const void *const u[3],
                     int dtype, int mem, int project, nf_step_stats *st);
 
-/* Advance nsteps time steps: rasterise alpha and u_s at t_{n+1}, advect
-   (Eq. advection_matrix), solve Eq. projection_matrix, apply the blended
-   update U = S (U^ - c G P) + (I - S) U_s (c = dt / (rho dx)). In a closed
-   box (no outlet) the right-hand side is projected to zero mean over the
-   active cells and the pressure is returned with zero mean there. Records
-   checkpoints every checkpoint_every steps for nf_backward. Returns
-   NF_E_NOT_CONVERGED if a solve hit max_iters (the step is still applied). */
+/* Advance nsteps time steps (or frames, when cfl_max > 0: each frame of dt
+   is split into substeps by the CFL rule; the rule of Table 1's caption).
+   One step of length h from t to t + h: rasterise alpha and u_s at t + h,
+   advect (Eq. advection_matrix), solve Eq. projection_matrix, apply the
+   blended update U = S (U^ - c G P) + (I - S) U_s with c = h / (rho dx).
+   On fluid components that touch no open face the right-hand side is
+   projected to zero mean and the pressure is returned with zero mean.
+   Records checkpoints every checkpoint_every steps for nf_backward; st->steps
+   counts the steps taken. Returns NF_E_NOT_CONVERGED if a solve hit
+   max_iters (the step is still applied). */
 int nf_step(nf_ctx *ctx, int64_t id, int nsteps, nf_step_stats *st);
 
 /* Loss of the current velocity: J (host double) and optionally dJ/dU into

@@ -142,14 +142,19 @@ def config_sphere(n=32, *, seed=0, steps=20, dt=0.01, sigma=0.1, tol=1e-10):
 
 
 def config_chamber(n=128, *, seed=0, steps=100, dt=0.005, tol=1e-6,
-                   duct_half_cells=8):
-    """Pulsing chamber with one outlet patch (128^3, 100 steps)."""
+                   duct_half_cells=8, cfl_max=8.0):
+    """Pulsing chamber with one outlet patch (128^3, 100 frames of dt).
+
+    Each frame is split into steps under the CFL rule with ``cfl_max``
+    (0 disables sub-stepping: one step per frame).
+    """
     g = make_grid(n, dt, outlet=centred_outlet(n, 2 * duct_half_cells))
     rng = np.random.Generator(np.random.PCG64(seed))
     theta = rng.uniform(-0.05, 0.05, size=8)
     sc = chamber_scene(theta, g["dx"], duct_half_cells=duct_half_cells)
     return dict(name=f"chamber{n}", grid=g, scene=sc, u0=zero_faces(g),
-                project_initial=False, steps=steps, tol=tol, loss="outflow")
+                project_initial=False, steps=steps, tol=tol, loss="outflow",
+                cfl_max=float(cfl_max))
 
 
 def config_plate(n=64, *, seed=0, steps=16, dt=0.01, sigma=0.1, tol=1e-10):

@@ -15,6 +15,8 @@ lattice ``X - shift_e`` with ``shift_e = 1/2`` on every axis but ``e``.
 
 from __future__ import annotations
 
+import copy
+
 import numpy as np
 
 
@@ -45,6 +47,13 @@ class Grid:
 
     def zeros_faces(self):
         return [np.zeros(self.face_shape(d)) for d in range(3)]
+
+    def with_dt(self, h):
+        """The same grid for a step of length h (advection and c = h / (rho dx))."""
+        g = copy.copy(self)
+        g.dt = float(h)
+        g.c = g.dt / (g.rho * g.dx)
+        return g
 
 
 def axis_of(d):

@@ -10,6 +10,13 @@ solid-velocity gradients into the shape and control parameters:
 An optional initial projection (the seeded noise made divergence free with
 the t = 0 cut-cell system) is part of the rollout and of its adjoint.
 Every forward quantity the adjoint needs is kept (no checkpointing here).
+
+Sub-stepping (Sec. 3, Table 1 caption: steps are taken under the CFL
+condition, so more steps are simulated than frames): with ``cfl_max > 0`` a
+rollout advances frames of length dt, each split into
+``m = ceil(max|U| dt / (dx cfl_max))`` equal steps, max|U| taken over all
+faces at the start of the frame; step k of frame f ends at
+``t = (f m + k + 1) dt / m``.
 """
 
 from __future__ import annotations
@@ -30,16 +37,18 @@ def geometry_at(g: Grid, scene, t, with_grad=False):
     return ras.fractions(g, scene, t), ras.face_solid_velocity(g, scene, t)
 
 
-def step(g: Grid, scene, U, n, tol, order=2, velocity_rule="blend"):
-    """Advance ``U^n`` to ``U^{n+1}``; returns the new field and a tape."""
-    t1 = (n + 1) * g.dt
+def step(g: Grid, scene, U, n, tol, order=2, velocity_rule="blend", t1=None):
+    """Advance ``U^n`` by one step of length ``g.dt`` ending at ``t1``
+    (default ``(n + 1) dt``); returns the new field and a tape."""
+    if t1 is None:
+        t1 = (n + 1) * g.dt
     alpha, us = geometry_at(g, scene, t1)
     Ut = adv.advect(g, U, order)
     Uh = adv.viscosity(g, Ut)
     Unew, P, info = prj.project(g, alpha, us, Uh, tol, velocity_rule)
     tape = dict(kind="step", t=t1, U=U, Uh=Uh, P=P, alpha=alpha, us=us,
                 system=info["system"], iters=info["iters"],
-                rel_residual=info["rel_residual"], order=order)
+                rel_residual=info["rel_residual"], order=order, grid=g)
     return Unew, tape
 
 
@@ -48,24 +57,38 @@ def initial_projection(g: Grid, scene, U0, tol):
     U, P, info = prj.project(g, alpha, us, U0, tol)
     tape = dict(kind="project", t=0.0, U=U0, Uh=U0, P=P, alpha=alpha, us=us,
                 system=info["system"], iters=info["iters"],
-                rel_residual=info["rel_residual"])
+                rel_residual=info["rel_residual"], grid=g)
     return U, tape
 
 
-def rollout(g: Grid, scene, U0, nsteps, tol, project_initial=True, order=2):
+def substeps(g: Grid, U, cfl_max):
+    """Number of equal steps of a frame under the CFL rule."""
+    if not cfl_max:
+        return 1
+    umax = max(float(np.max(np.abs(u))) for u in U)
+    return max(1, int(np.ceil(umax * g.dt / (g.dx * cfl_max))))
+
+
+def rollout(g: Grid, scene, U0, nsteps, tol, project_initial=True, order=2,
+            cfl_max=0.0):
+    """``nsteps`` steps (or frames, with ``cfl_max > 0``) from ``U0``."""
     tapes = []
     U = [u.copy() for u in U0]
     if project_initial:
         U, tape = initial_projection(g, scene, U, tol)
         tapes.append(tape)
-    for n in range(nsteps):
-        U, tape = step(g, scene, U, n, tol, order)
-        tapes.append(tape)
+    for f in range(nsteps):
+        m = substeps(g, U, cfl_max)
+        gs = g.with_dt(g.dt / m)
+        for k in range(m):
+            t1 = (f * m + k + 1) * gs.dt
+            U, tape = step(gs, scene, U, None, tol, order, t1=t1)
+            tapes.append(tape)
     return U, tapes
 
 
 def _theta_terms(g: Grid, scene, tape, gS, gUs):
-    _, _, dalpha, dus = geometry_at(g, scene, tape["t"], with_grad=True)
+    _, _, dalpha, dus = geometry_at(tape["grid"], scene, tape["t"], with_grad=True)
     K = len(scene.get("theta", []))
     gth = np.zeros(K)
     for d in range(3):
@@ -76,14 +99,15 @@ def _theta_terms(g: Grid, scene, tape, gS, gUs):
 
 def step_adjoint(g: Grid, scene, tape, gU, tol):
     """Map ``dJ/dU^{n+1}`` to ``dJ/dU^n`` and this step's ``dJ/dtheta``."""
+    gs = tape["grid"]
     gUh, gS, gUs, y, info = prj.project_adjoint(
-        g, tape["alpha"], tape["us"], tape["Uh"], tape["P"], gU, tol,
+        gs, tape["alpha"], tape["us"], tape["Uh"], tape["P"], gU, tol,
         system=tape["system"])
-    gth = _theta_terms(g, scene, tape, gS, gUs)
+    gth = _theta_terms(gs, scene, tape, gS, gUs)
     if tape["kind"] == "project":
         return gUh, gth
-    gUt = adv.viscosity_adjoint(g, gUh)
-    gUn = adv.advect_adjoint(g, tape["U"], gUt, tape["order"])
+    gUt = adv.viscosity_adjoint(gs, gUh)
+    gUn = adv.advect_adjoint(gs, tape["U"], gUt, tape["order"])
     return gUn, gth
 
 
@@ -127,7 +151,8 @@ def loss_and_grad(cfg, theta=None, tol=None):
     if theta is not None:
         scene["theta"] = list(theta)
     tol = cfg["tol"] if tol is None else tol
-    U, tapes = rollout(g, scene, cfg["u0"], cfg["steps"], tol, cfg["project_initial"])
+    U, tapes = rollout(g, scene, cfg["u0"], cfg["steps"], tol, cfg["project_initial"],
+                       cfl_max=cfg.get("cfl_max", 0.0))
     J, gU = LOSSES[cfg["loss"]](g, U)
     gU0, gth = rollout_backward(g, scene, tapes, gU, tol)
     return J, gth, dict(U=U, tapes=tapes, gU0=gU0)
@@ -138,7 +163,8 @@ def loss_only(cfg, theta, tol=None):
     scene = dict(cfg["scene"])
     scene["theta"] = list(theta)
     tol = cfg["tol"] if tol is None else tol
-    U, _ = rollout(g, scene, cfg["u0"], cfg["steps"], tol, cfg["project_initial"])
+    U, _ = rollout(g, scene, cfg["u0"], cfg["steps"], tol, cfg["project_initial"],
+                   cfl_max=cfg.get("cfl_max", 0.0))
     return LOSSES[cfg["loss"]](g, U)[0]
 
 

@@ -36,7 +36,8 @@ class Config(C.Structure):
                 ("tol", C.c_double), ("max_iters", C.c_int),
                 ("inner_tol", C.c_double), ("mg_smooth", C.c_int),
                 ("mg_coarsest", C.c_int), ("advect_order", C.c_int),
-                ("checkpoint_every", C.c_int), ("hbm_budget", C.c_size_t)]
+                ("checkpoint_every", C.c_int), ("hbm_budget", C.c_size_t),
+                ("cfl_max", C.c_double)]
 
 
 class Grid(C.Structure):

@@ -115,7 +115,7 @@ class Context:
 
     def __init__(self, precision="mixed", solver="mgpcg", tol=1e-6, max_iters=500,
                  inner_tol=1e-3, mg_smooth=2, mg_coarsest=4, advect_order=2,
-                 checkpoint_every=10, hbm_budget=0, device=0, stream=None):
+                 checkpoint_every=10, hbm_budget=0, cfl_max=0.0, device=0, stream=None):
         cfg = L.Config()
         _check(lib.nf_config_default(C.byref(cfg)))
         cfg.device = device
@@ -134,6 +134,7 @@ class Context:
         cfg.advect_order = advect_order
         cfg.checkpoint_every = checkpoint_every
         cfg.hbm_budget = int(hbm_budget)
+        cfg.cfl_max = float(cfl_max)
         self.precision = precision
         self.device = device
         self._h = C.c_void_p()

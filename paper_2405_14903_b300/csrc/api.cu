@@ -46,9 +46,31 @@ void Alloc::free_all() {
 // ------------------------------------------------------------ profiling ---
 static constexpr size_t kProfSlots = 4096;
 
+static constexpr int kGraphSlot = 1 << 30;
+
+void GraphEvents::clear() {
+  for (auto &e : ev) cudaEventDestroy(e);
+  ev.clear();
+  cls.clear();
+  iter.clear();
+}
+
 void prof_begin(Prof *p, int kclass, cudaStream_t s, int *slot) {
   *slot = -1;
   if (p->kclass != -1 && p->kclass != kclass) return;
+  if (p->capture_ev) {
+    GraphEvents &ge = *p->capture_ev;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    ge.ev.push_back(a);
+    ge.ev.push_back(b);
+    ge.cls.push_back(kclass);
+    ge.iter.push_back(p->capture_iter);
+    cudaEventRecordWithFlags(a, s, cudaEventRecordExternal);
+    *slot = kGraphSlot | (int)(ge.cls.size() - 1);
+    return;
+  }
   if (p->ev.empty()) {
     p->ev.resize(2 * kProfSlots);
     p->cls.resize(kProfSlots);
@@ -61,7 +83,25 @@ void prof_begin(Prof *p, int kclass, cudaStream_t s, int *slot) {
 }
 
 void prof_end(Prof *p, int slot, cudaStream_t s) {
+  if (slot & kGraphSlot) {
+    cudaEventRecordWithFlags(p->capture_ev->ev[2 * (slot & ~kGraphSlot) + 1], s,
+                             cudaEventRecordExternal);
+    return;
+  }
   cudaEventRecord(p->ev[2 * slot + 1], s);
+}
+
+void Prof::collect(const GraphEvents &ge, int iters) {
+  for (size_t i = 0; i < ge.cls.size(); ++i) {
+    if (ge.iter[i] >= iters) continue;
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, ge.ev[2 * i], ge.ev[2 * i + 1]) == cudaSuccess) {
+      launches[ge.cls[i]] += 1;
+      ms[ge.cls[i]] += t;
+    } else {
+      cudaGetLastError();
+    }
+  }
 }
 
 void Prof::drain(cudaStream_t s) {
@@ -156,6 +196,7 @@ int nf_config_default(nf_config *cfg) {
   cfg->advect_order = 2;
   cfg->checkpoint_every = 10;
   cfg->hbm_budget = 0;
+  cfg->cfl_max = 0.0;
   return NF_OK;
 }
 
@@ -185,7 +226,7 @@ int nf_create(nf_ctx **out, const nf_config *cfg) {
       (cfg->solver != NF_SOLVER_CG && cfg->solver != NF_SOLVER_MGPCG) ||
       !(cfg->tol > 0) || cfg->max_iters <= 0 ||
       (cfg->advect_order != 1 && cfg->advect_order != 2) ||
-      cfg->checkpoint_every <= 0 || cfg->mg_smooth < 0) {
+      cfg->checkpoint_every <= 0 || cfg->mg_smooth < 0 || !(cfg->cfl_max >= 0.0)) {
     set_error("nf_create: invalid configuration");
     return NF_E_INVALID;
   }
@@ -392,6 +433,7 @@ int nf_profile(nf_ctx *ctx, int kclass) {
   if (ctx->c.prof.used) ctx->c.prof.drain(ctx->c.stream);
   ctx->c.prof.reset();
   ctx->c.prof.kclass = kclass;
+  ctx->c.prof.gen += 1;  // graphs are re-captured with (or without) events
   return NF_OK;
 }
 

@@ -8,18 +8,26 @@
 // deterministic (no float atomics, fixed-order reductions), so the recomputed
 // segment reproduces the recorded rollout bit for bit.
 //
-// Gauge: in a closed box (no outlet) A is singular with the constants on the
-// active cells as null space. The right-hand side is projected to zero mean
-// there (a no-op for consistent data, the least-squares reading otherwise)
-// and the pressure is returned with zero mean; the adjoint does the same for
-// dJ/dP and the adjoint variable y, so the parameter gradient matches the
-// derivative of that reading.
+// Sub-stepping: with cfl_max > 0 every frame of length dt is split into m
+// equal steps, m = ceil(max|U| dt / (dx cfl_max)) from the velocity at the
+// frame start (the CFL rule the paper applies between frames, Table 1). The
+// time t_{k+1} and length h_k of every step are kept in the tape, so the
+// recomputation and the adjoint replay the same schedule.
+//
+// Gauge: on a fluid component that touches no open face A is singular with
+// the constants on the component as null space. There the right-hand side is
+// projected to zero mean (a no-op for consistent data, the least-squares
+// reading otherwise) and the pressure is returned with zero mean; the
+// adjoint does the same for dJ/dP and the adjoint variable y, so the
+// parameter gradient is the derivative of that reading. Components are
+// labelled on the device after every rasterisation that precedes a solve.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <memory>
 #include <vector>
 
+#include "components.h"
 #include "episode.h"
 #include "kernels.h"
 #include "solver.cuh"
@@ -79,6 +87,8 @@ static SceneDev scene_at(const nf_scene &sc, double t, const double *d_spheres) 
       }
       s.cs = r;
       s.csdot = rd;
+      s.crate = rd / r;
+      for (int k = 0; k < 8; ++k) s.cdus[k] = (s.cdsdot[k] * r - rd * s.cds[k]) / (r * r);
       const double x0 = c[7], hw = c[8];
       s.dc[0] = 0.5 * (x0 + 2.0);
       s.dc[1] = c[1];
@@ -186,6 +196,7 @@ class EpisodeImpl : public EpisodeBase {
                      cudaMemcpyHostToDevice));
     }
     CKS(solver_.init(A_));
+    CKS(cc_.init(A_, ncell_));
     Launch L = ctx_->launch();
     CKC(cudaMemsetAsync(U_, 0, nfaces_ * sizeof(T), L.s));
     CKC(cudaMemsetAsync(P_, 0, ncell_ * sizeof(S), L.s));
@@ -222,7 +233,7 @@ class EpisodeImpl : public EpisodeBase {
       const SceneDev sd = scene_at(sc_, 0.0, dsph_);
       launch_rasterize<T>(L, g_, sd, mut(alpha_));
       SolveStats ss;
-      CKS(project_faces(sd, Uinit_, Pinit_, U_, &ss));
+      CKS(project_faces(g_, sd, Uinit_, Pinit_, U_, &ss));
       CKC(cudaMemcpyAsync(Uh_, Uinit_, nfaces_ * sizeof(T), cudaMemcpyDeviceToDevice, L.s));
       CKC(cudaMemcpyAsync(P_, Pinit_, ncell_ * sizeof(S), cudaMemcpyDeviceToDevice, L.s));
       acc_stats(&s, ss);
@@ -238,27 +249,48 @@ class EpisodeImpl : public EpisodeBase {
     if (nsteps < 0) return invalid("step: nsteps < 0%s", "");
     nf_step_stats s{};
     int worst = NF_OK;
-    for (int i = 0; i < nsteps; ++i) {
-      const int C = std::max(1, ctx_->cfg.checkpoint_every);
-      if (n_ % C == 0) {
-        const int idx = n_ / C;
-        while ((int)ckpt_.size() <= idx) {
-          T *p = nullptr;
-          CKS(faces(&p));
-          ckpt_.push_back(p);
-        }
-        CKC(cudaMemcpyAsync(ckpt_[idx], U_, nfaces_ * sizeof(T),
-                            cudaMemcpyDeviceToDevice, ctx_->stream));
+    const double cfl = ctx_->cfg.cfl_max;
+    for (int i = 0; i < nsteps && worst != NF_E_DIVERGED; ++i) {
+      int m = 1;
+      if (cfl > 0.0) {
+        const double umax = max_speed();
+        if (!std::isfinite(umax)) return diverged("step: non-finite velocity");
+        m = std::max(1, (int)std::ceil(umax * g_.dt / (g_.dx * cfl)));
       }
-      SolveStats ss;
-      CKS(forward_step(n_, U_, U_, Uh_, P_, &ss));
-      acc_stats(&s, ss);
-      s.steps += 1;
-      if (ss.status != NF_OK && worst == NF_OK) worst = ss.status;
-      if (ss.status == NF_E_DIVERGED) break;
-      ++n_;
-      n_rev_ = n_;
-      seg_start_ = -1;  // a new step invalidates the cached segment
+      const int f = frames_;
+      for (int sub = 0; sub < m; ++sub) {
+        // t = (f + (sub + 1) / m) dt, exact for m = 1
+        const double h = g_.dt / m;
+        const double t1 = (double)(f * (int64_t)m + sub + 1) * h;
+        const int C = std::max(1, ctx_->cfg.checkpoint_every);
+        if (n_ % C == 0) {
+          const int idx = n_ / C;
+          while ((int)ckpt_.size() <= idx) {
+            T *p = nullptr;
+            CKS(faces(&p));
+            ckpt_.push_back(p);
+          }
+          CKC(cudaMemcpyAsync(ckpt_[idx], U_, nfaces_ * sizeof(T),
+                              cudaMemcpyDeviceToDevice, ctx_->stream));
+        }
+        ts_.resize(n_ + 1);
+        hs_.resize(n_ + 1);
+        ts_[n_] = t1;
+        hs_[n_] = h;
+        SolveStats ss;
+        CKS(forward_step(n_, U_, U_, Uh_, P_, &ss));
+        acc_stats(&s, ss);
+        s.steps += 1;
+        if (ss.status != NF_OK && worst == NF_OK) worst = ss.status;
+        if (ss.status == NF_E_DIVERGED) {
+          worst = NF_E_DIVERGED;
+          break;
+        }
+        ++n_;
+        n_rev_ = n_;
+        seg_start_ = -1;  // a new step invalidates the cached segment
+      }
+      ++frames_;
     }
     if (st) *st = s;
     CKS(check_launch());
@@ -367,6 +399,28 @@ class EpisodeImpl : public EpisodeBase {
     set_error(msg);
     return NF_E_STATE;
   }
+  int diverged(const char *msg) {
+    set_error(msg);
+    return NF_E_DIVERGED;
+  }
+  // max |U| over all faces (synchronises the stream)
+  double max_speed() {
+    Launch L = ctx_->launch();
+    unsigned long long *mx = (unsigned long long *)(dscal_ + 2);
+    launch_absmax_faces<T>(L, g_, cview(U_), mx);
+    unsigned long long bits = 0;
+    ctx_->read_bytes(&bits, mx, sizeof(bits));
+    double v;
+    std::memcpy(&v, &bits, sizeof(v));
+    return v;
+  }
+  // Grid description of a step of length h (advection and operator scale).
+  GridDev grid_h(double h) const {
+    GridDev g = g_;
+    g.dt = h;
+    g.c = h / (g_.rho * g_.dx);
+    return g;
+  }
   int check_launch() {
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
@@ -436,43 +490,43 @@ class EpisodeImpl : public EpisodeBase {
 
   void clear_tape() {
     n_ = 0;
+    frames_ = 0;
+    ts_.clear();
+    hs_.clear();
     n_rev_ = 0;
     init_proj_ = false;
     init_reverted_ = false;
     seg_start_ = -1;
   }
 
-  // Zero mean over the active cells (closed boxes only); returns ||v||^2
-  // after the projection, or `n2` unchanged when the box has an outlet.
-  double gauge(S *v, double n2) {
-    if (g_.outlet) return n2;
-    Launch L = ctx_->launch();
-    launch_remove_mean<T, S>(L, g_, cview(alpha_), v, ctx_->rs, dscal_ + 4);
-    return ctx_->read_double(dscal_ + 6);
-  }
+  // Zero mean on every floating component; returns ||v||^2 afterwards.
+  double gauge(S *v, double n2) { return cc_.gauge<S>(ctx_, ncell_, v, n2); }
 
   // ----------------------------------------------------------- forward ----
   // Right-hand side, solve and blended update for fractions alpha_ (already
   // rasterised for scene state sd): uh -> P, u_out.
-  int project_faces(const SceneDev &sd, const T *uh, S *P, T *u_out,
-                    SolveStats *ss) {
+  int project_faces(const GridDev &g, const SceneDev &sd, const T *uh, S *P,
+                    T *u_out, SolveStats *ss) {
     Launch L = ctx_->launch();
-    launch_rhs<T, S>(L, g_, sd, cview(alpha_), cview(uh), b_, ctx_->rs, dscal_);
+    CKS(cc_.label<T>(ctx_, g, cview(alpha_)));
+    launch_rhs<T, S>(L, g, sd, cview(alpha_), cview(uh), b_, ctx_->rs, dscal_);
     solver_.set_fractions(comp(alpha_, 0), comp(alpha_, 1), comp(alpha_, 2));
     const double bn2 = gauge(b_, ctx_->read_double(dscal_));
     *ss = solver_.solve(b_, P, bn2);
     gauge(P, 0.0);
-    launch_update<T, S>(L, g_, sd, cview(alpha_), cview(uh), P, mut(u_out));
+    launch_update<T, S>(L, g, sd, cview(alpha_), cview(uh), P, mut(u_out));
     return NF_OK;
   }
 
-  // Step m (t_{m+1} = (m + 1) dt): u_in -> uh, P, u_out (u_out may alias u_in).
+  // Step m (from ts_[m] - hs_[m] to ts_[m]): u_in -> uh, P, u_out (u_out
+  // may alias u_in).
   int forward_step(int m, const T *u_in, T *u_out, T *uh, S *P, SolveStats *ss) {
     Launch L = ctx_->launch();
-    const SceneDev sd = scene_at(sc_, (m + 1) * g_.dt, dsph_);
-    launch_rasterize<T>(L, g_, sd, mut(alpha_));
-    launch_advect<T>(L, g_, cview(u_in), mut(uh), ctx_->cfg.advect_order);
-    return project_faces(sd, uh, P, u_out, ss);
+    const GridDev g = grid_h(hs_[m]);
+    const SceneDev sd = scene_at(sc_, ts_[m], dsph_);
+    launch_rasterize<T>(L, g, sd, mut(alpha_));
+    launch_advect<T>(L, g, cview(u_in), mut(uh), ctx_->cfg.advect_order);
+    return project_faces(g, sd, uh, P, u_out, ss);
   }
 
   // ---------------------------------------------------------- backward ----
@@ -511,16 +565,17 @@ class EpisodeImpl : public EpisodeBase {
 
   // Adjoint of one projection (fractions alpha_ for scene state sd) with
   // the forward's U^ = uh and pressure P: gU_ -> gUh_, theta gradient.
-  int adjoint_projection(const SceneDev &sd, const T *uh, const S *P,
-                         double *gth, nf_step_stats *st) {
+  int adjoint_projection(const GridDev &g, const SceneDev &sd, const T *uh,
+                         const S *P, double *gth, nf_step_stats *st) {
     Launch L = ctx_->launch();
+    CKS(cc_.label<T>(ctx_, g, cview(alpha_)));
     solver_.set_fractions(comp(alpha_, 0), comp(alpha_, 1), comp(alpha_, 2));
-    launch_adj_gp<T, S>(L, g_, cview(alpha_), cview(gU_), gP_, ctx_->rs, dscal_);
+    launch_adj_gp<T, S>(L, g, cview(alpha_), cview(gU_), gP_, ctx_->rs, dscal_);
     const double n2 = gauge(gP_, ctx_->read_double(dscal_));
     const SolveStats ss = solver_.solve(gP_, y_, n2);
     gauge(y_, 0.0);
     acc_stats(st, ss);
-    launch_adj_face<T, S>(L, g_, sd, cview(alpha_), cview(uh), P, y_, cview(gU_),
+    launch_adj_face<T, S>(L, g, sd, cview(alpha_), cview(uh), P, y_, cview(gU_),
                           mut(gUh_), ctx_->rs, dscal_ + 8);
     if (sd.K > 0) {
       double h[kMaxParams];
@@ -538,7 +593,7 @@ class EpisodeImpl : public EpisodeBase {
         return state_err("backward_step: nothing left to revert");
       const SceneDev sd = scene_at(sc_, 0.0, dsph_);
       launch_rasterize<T>(L, g_, sd, mut(alpha_));
-      const int rc = adjoint_projection(sd, Uinit_, Pinit_, gth, st);
+      const int rc = adjoint_projection(g_, sd, Uinit_, Pinit_, gth, st);
       CKC(cudaMemcpyAsync(gU_, gUh_, nfaces_ * sizeof(T), cudaMemcpyDeviceToDevice, L.s));
       init_reverted_ = true;
       return rc;
@@ -548,10 +603,11 @@ class EpisodeImpl : public EpisodeBase {
     const int s = m / C;
     if (seg_start_ != s * C) CKS(recompute_segment(s, st));
     const int k = m - seg_start_;
-    const SceneDev sd = scene_at(sc_, (m + 1) * g_.dt, dsph_);
-    launch_rasterize<T>(L, g_, sd, mut(alpha_));
-    const int rc = adjoint_projection(sd, segUh_[k], segP_[k], gth, st);
-    launch_advect_adjoint<T>(L, g_, cview(segU_[k]), cview(gUh_), mut(gUb_),
+    const GridDev g = grid_h(hs_[m]);
+    const SceneDev sd = scene_at(sc_, ts_[m], dsph_);
+    launch_rasterize<T>(L, g, sd, mut(alpha_));
+    const int rc = adjoint_projection(g, sd, segUh_[k], segP_[k], gth, st);
+    launch_advect_adjoint<T>(L, g, cview(segU_[k]), cview(gUh_), mut(gUb_),
                              ctx_->cfg.advect_order);
     std::swap(gU_, gUb_);
     n_rev_ = m;
@@ -563,16 +619,18 @@ class EpisodeImpl : public EpisodeBase {
   GridDev g_;
   nf_scene sc_;
   Solver<T, S, V, TA> solver_;
+  Components cc_;
   Alloc A_;
   int64_t nfaces_ = 0, ncell_ = 0;
   T *U_ = nullptr, *Uh_ = nullptr, *alpha_ = nullptr;
   T *gU_ = nullptr, *gUb_ = nullptr, *gUh_ = nullptr, *tmpU_ = nullptr;
   S *P_ = nullptr, *b_ = nullptr, *gP_ = nullptr, *y_ = nullptr;
   void *stage_ = nullptr;
-  double *dscal_ = nullptr;  // [0] norms, [1] loss, [4..7) gauge, [8..16) dJ/dtheta
+  double *dscal_ = nullptr;  // [0] norms, [1] loss, [8..16) dJ/dtheta
   double *dsph_ = nullptr;
   // tape
-  int n_ = 0, n_rev_ = 0;
+  int n_ = 0, n_rev_ = 0, frames_ = 0;
+  std::vector<double> ts_, hs_;  // end time and length of every step
   bool init_proj_ = false, init_reverted_ = false;
   T *Uinit_ = nullptr;
   S *Pinit_ = nullptr;
@@ -590,6 +648,7 @@ size_t episode_base_bytes(const nf_config &cfg, const nf_grid &g) {
   const size_t s = cfg.precision == NF_PREC_FP32 ? 4 : 8;
   const size_t v = cfg.precision == NF_PREC_FP64 ? 8 : 4;
   size_t b = 6 * nf * t + 4 * nc * s + nc * 8;  // fields, scalars, staging
+  b += nc * 20;                                  // component labels, gauge
   b += nc * s + 5 * nc * v;                      // solver vectors
   b += (nc * (2 * v + 3 * t)) * 2 / 7 + nc * v;  // hierarchy (approx.)
   return b;

@@ -1,0 +1,241 @@
+// Connected fluid components of the active cells and the gauge of the
+// components that touch no open face (Sec. 2.3.1, Projection: the cut-cell
+// system is singular on such a component, with the constants as null space).
+//
+// Labelling: union-find by hooking roots to the smaller index, repeated until
+// a round finds every face with alpha > 0 joining cells of equal root; the
+// final label of a cell is the smallest cell index of its component, so the
+// result does not depend on scheduling.
+//
+// Gauge: on every floating component the field is shifted to zero mean. The
+// per-component sums are accumulated as 64-bit fixed-point integers (scale
+// 2^(62 - bits) / max|v| with 2^bits >= the cell count, so no sum overflows),
+// whose atomic additions are exact and order independent, so a recomputed
+// forward reproduces the same bits.
+#include "components.h"
+
+namespace nf {
+
+template <class T>
+__device__ __forceinline__ bool active_cell(const GridDev &g, const Fields<T> &a,
+                                            int i, int j, int k) {
+  return (a.x[g.face(0, i, j, k)] + a.x[g.face(0, i + 1, j, k)] +
+          a.y[g.face(1, i, j, k)] + a.y[g.face(1, i, j + 1, k)] +
+          a.z[g.face(2, i, j, k)] + a.z[g.face(2, i, j, k + 1)]) > T(0);
+}
+
+__device__ __forceinline__ int cc_find(const int *lab, int x) {
+  const volatile int *l = lab;
+  for (;;) {
+    const int p = l[x];
+    if (p == x) return x;
+    x = p;
+  }
+}
+
+template <class T>
+__global__ void k_cc_init(GridDev g, Fields<T> a, int *lab) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.ncell();
+       c += (int64_t)gridDim.x * blockDim.x) {
+    int i, j, k;
+    g.cell_ijk(c, i, j, k);
+    lab[c] = active_cell(g, a, i, j, k) ? (int)c : -1;
+  }
+}
+
+template <class T>
+__global__ void k_cc_hook(GridDev g, Fields<T> a, int *lab, int *changed) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.ncell();
+       c += (int64_t)gridDim.x * blockDim.x) {
+    if (((const volatile int *)lab)[c] < 0) continue;
+    int i, j, k;
+    g.cell_ijk(c, i, j, k);
+    // faces towards +x, +y, +z neighbours
+    for (int d = 0; d < 3; ++d) {
+      const int ni = i + (d == 0), nj = j + (d == 1), nk = k + (d == 2);
+      if (ni >= g.nx || nj >= g.ny || nk >= g.nz) continue;
+      const T af = d == 0 ? a.x[g.face(0, ni, j, k)]
+                          : (d == 1 ? a.y[g.face(1, i, nj, k)] : a.z[g.face(2, i, j, nk)]);
+      if (!(af > T(0))) continue;
+      const int64_t nb = g.cell(ni, nj, nk);
+      const int ra = cc_find(lab, (int)c), rb = cc_find(lab, (int)nb);
+      if (ra != rb) {
+        atomicMin(lab + (ra > rb ? ra : rb), ra < rb ? ra : rb);
+        *changed = 1;
+      }
+    }
+  }
+}
+
+__global__ void k_cc_compress(int64_t n, int *lab) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    if (lab[c] >= 0) lab[c] = cc_find(lab, (int)c);
+  }
+}
+
+// ground[root] = 1 for components with an open (outlet) face; counts the
+// floating roots into *nfloat.
+__global__ void k_cc_ground(GridDev g, const int *lab, int *ground) {
+  if (!g.outlet) return;
+  const int64_t n = (int64_t)g.ow * g.oh;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int j = g.oj0 + (int)(t % g.ow), k = g.ok0 + (int)(t / g.ow);
+    const int r = lab[g.cell(g.nx - 1, j, k)];
+    if (r >= 0) ground[r] = 1;
+  }
+}
+
+__global__ void k_cc_count(int64_t n, const int *lab, const int *ground,
+                           int *nfloat) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x)
+    if (lab[c] == (int)c && !ground[c]) atomicAdd(nfloat, 1);
+}
+
+__device__ __forceinline__ bool floating(const int *lab, const int *ground,
+                                         int64_t c, int &r) {
+  r = lab[c];
+  return r >= 0 && !ground[r];
+}
+
+template <class S>
+__global__ void k_gauge_max(int64_t n, const int *lab, const int *ground,
+                            const S *v, unsigned long long *mx) {
+  double m = 0.0;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    int r;
+    if (floating(lab, ground, c, r)) m = fmax(m, fabs((double)v[c]));
+  }
+  // bit patterns of non-negative doubles order like their values
+  if (m > 0.0) atomicMax(mx, (unsigned long long)__double_as_longlong(m));
+}
+
+__device__ __forceinline__ double fixed_scale(unsigned long long mxbits,
+                                              int bits) {
+  const double mx = __longlong_as_double((long long)mxbits);
+  int e = 0;
+  frexp(mx > 0.0 ? mx : 1.0, &e);  // mx < 2^e
+  return ldexp(1.0, 62 - bits - e);
+}
+
+template <class S>
+__global__ void k_gauge_sum(int64_t n, const int *lab, const int *ground,
+                            const S *v, const unsigned long long *mx, int bits,
+                            unsigned long long *csum, int *ccnt) {
+  const double sc = fixed_scale(*mx, bits);
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    int r;
+    if (!floating(lab, ground, c, r)) continue;
+    const long long q = llrint((double)v[c] * sc);
+    atomicAdd(csum + r, (unsigned long long)q);
+    atomicAdd(ccnt + r, 1);
+  }
+}
+
+template <class S>
+__global__ void k_gauge_sub(int64_t n, const int *lab, const int *ground, S *v,
+                            const unsigned long long *mx, int bits,
+                            const unsigned long long *csum, const int *ccnt,
+                            RedScratch rs, double *norm2) {
+  const double sc = fixed_scale(*mx, bits);
+  double acc[1] = {0.0};
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    int r;
+    double x = (double)v[c];
+    if (floating(lab, ground, c, r)) {
+      const double mean = (double)(long long)csum[r] / sc / (double)ccnt[r];
+      x -= mean;
+      v[c] = (S)x;
+    }
+    acc[0] += x * x;
+  }
+  double tot[1];
+  if (grid_sum<1>(acc, rs, tot) && threadIdx.x == 0) *norm2 = tot[0];
+}
+
+// ------------------------------------------------------------ launchers ---
+static inline unsigned cc_blocks(int64_t n) {
+  const unsigned b = nblocks(n);
+  return b < 148u * 16u ? b : 148u * 16u;
+}
+
+template <class T>
+int Components::label(Ctx *ctx, const GridDev &g, Fields<T> alpha) {
+  Launch L = ctx->launch();
+  const int64_t n = g.ncell();
+  {
+    ProfScope _ps(L, NF_K_GAUGE);
+    k_cc_init<T><<<cc_blocks(n), kBlock, 0, L.s>>>(g, alpha, lab);
+    ++*L.counter;
+  }
+  int h[2] = {0, 0};
+  for (int round = 0; round < kMaxRounds; ++round) {
+    cudaMemsetAsync(scal, 0, sizeof(int), L.s);
+    {
+      ProfScope _ps(L, NF_K_GAUGE);
+      k_cc_hook<T><<<cc_blocks(n), kBlock, 0, L.s>>>(g, alpha, lab, (int *)scal);
+      k_cc_compress<<<cc_blocks(n), kBlock, 0, L.s>>>(n, lab);
+      *L.counter += 2;
+    }
+    ctx->read_bytes(h, scal, sizeof(int));
+    if (h[0] == 0) break;
+    if (round == kMaxRounds - 1) {
+      set_error("component labelling did not converge");
+      return NF_E_NOT_CONVERGED;
+    }
+  }
+  cudaMemsetAsync(ground, 0, n * sizeof(int), L.s);
+  cudaMemsetAsync((int *)scal + 1, 0, sizeof(int), L.s);
+  {
+    ProfScope _ps(L, NF_K_GAUGE);
+    k_cc_ground<<<cc_blocks((int64_t)g.ow * g.oh + 1), kBlock, 0, L.s>>>(g, lab, ground);
+    k_cc_count<<<cc_blocks(n), kBlock, 0, L.s>>>(n, lab, ground, (int *)scal + 1);
+    *L.counter += 2;
+  }
+  ctx->read_bytes(h, scal, 2 * sizeof(int));
+  nfloat = h[1];
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? NF_OK : cuda_fail(e, "component labelling");
+}
+
+template <class S>
+double Components::gauge(Ctx *ctx, int64_t n, S *v, double norm2) {
+  if (nfloat == 0) return norm2;
+  Launch L = ctx->launch();
+  unsigned long long *mx = (unsigned long long *)((char *)scal + 16);
+  double *nrm = (double *)((char *)scal + 24);
+  cudaMemsetAsync(mx, 0, sizeof(unsigned long long), L.s);
+  cudaMemsetAsync(csum, 0, n * sizeof(unsigned long long), L.s);
+  cudaMemsetAsync(ccnt, 0, n * sizeof(int), L.s);
+  int bits = 1;
+  while (bits < 40 && ((int64_t)1 << bits) < n) ++bits;
+  ProfScope _ps(L, NF_K_GAUGE);
+  k_gauge_max<S><<<cc_blocks(n), kBlock, 0, L.s>>>(n, lab, ground, v, mx);
+  k_gauge_sum<S><<<cc_blocks(n), kBlock, 0, L.s>>>(n, lab, ground, v, mx, bits, csum,
+                                                   ccnt);
+  k_gauge_sub<S><<<kRedBlocks, kBlock, 0, L.s>>>(n, lab, ground, v, mx, bits, csum, ccnt,
+                                                 ctx->rs, nrm);
+  *L.counter += 3;
+  return ctx->read_double(nrm);
+}
+
+int Components::init(Alloc &A, int64_t n) {
+  CKS(A.get(&lab, n * sizeof(int)));
+  CKS(A.get(&ground, n * sizeof(int)));
+  CKS(A.get(&ccnt, n * sizeof(int)));
+  CKS(A.get(&csum, n * sizeof(unsigned long long)));
+  CKS(A.get(&scal, 64));
+  return NF_OK;
+}
+
+template int Components::label<float>(Ctx *, const GridDev &, Fields<float>);
+template int Components::label<double>(Ctx *, const GridDev &, Fields<double>);
+template double Components::gauge<float>(Ctx *, int64_t, float *, double);
+template double Components::gauge<double>(Ctx *, int64_t, double *, double);
+
+}  // namespace nf

@@ -71,6 +71,20 @@ __device__ __forceinline__ V apply_cell(const LevelView<TA> &lv, const V *x,
   return V(lv.c) * (dg * x[c] - nb);
 }
 
+// Multigrid residual b - A x, zero on inactive cells: the restriction is
+// R = P^T / 4 with the prolongation P masked to active fine cells, so the
+// residual it restricts must vanish where P is masked (keeps M symmetric).
+template <class V, class TA>
+__device__ __forceinline__ V residual_cell(const LevelView<TA> &lv, const V *x,
+                                           const V *b, int i, int j, int k,
+                                           int64_t c) {
+  const Six<V> s = six<V>(lv, i, j, k);
+  const V dg = s.diag();
+  if (!(dg > V(0))) return V(0);
+  const V nb = nbsum<V>(s, x, lv.nx, lv.ny, lv.nz, i, j, k, c);
+  return b[c] - V(lv.c) * (dg * x[c] - nb);
+}
+
 // Gauss-Seidel update of one cell: x = (b + c nb) / (c diag); 0 if inactive.
 template <class V, class TA>
 __device__ __forceinline__ V gs_cell(const LevelView<TA> &lv, const V *x,
@@ -168,9 +182,8 @@ __global__ void k_residual_outer(LevelView<T> lv, const S *b, const S *x, S *r,
   const int64_t n = lv.ncell();
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
        c += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(c % lv.nx);
-    const int64_t q = c / lv.nx;
-    const int j = (int)(q % lv.ny), k = (int)(q / lv.ny);
+    int i, j, k;
+    GridDev::decomp(c, lv.nx, lv.ny, i, j, k);
     const Six<double> s = six<double>(lv, i, j, k);
     const double dg = s.diag();
     double rv = 0.0;
@@ -194,22 +207,28 @@ __global__ void k_axpy_outer(int64_t n, S *x, const V *e) {
 }
 
 // ------------------------------------------------------------------ CG -----
+// Dots: each thread accumulates its few grid-stride terms (2M cells over
+// 151k threads: ~14) in the vector type, the block and grid sums are FP64 in
+// fixed order. FP64 arithmetic per element would cost more than the memory
+// traffic on this part, whose FP64 rate is 1/64 of FP32.
 template <class V>
 __global__ void k_cg_init(int64_t n, const V *r, const V *z, V *d, CGState *st,
-                          RedScratch rs, double rel_tol) {
-  double v[2] = {0.0, 0.0};
+                          RedScratch rs) {
+  // per-thread partials in V (a few terms each), block and grid sums in FP64
+  V p0 = V(0), p1 = V(0);
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
        c += (int64_t)gridDim.x * blockDim.x) {
     const V rc = r[c], zc = z[c];
     d[c] = zc;
-    v[0] += (double)rc * (double)zc;
-    v[1] += (double)rc * (double)rc;
+    p0 += rc * zc;
+    p1 += rc * rc;
   }
+  double v[2] = {(double)p0, (double)p1};
   double tot[2];
   if (grid_sum<2>(v, rs, tot) && threadIdx.x == 0) {
     st->rz = tot[0];
     st->rr = tot[1];
-    st->stop2 = rel_tol * rel_tol * tot[1];
+    st->stop2 = st->tol * st->tol * tot[1];
     st->iters = 0;
     st->alpha = st->beta = st->dq = 0.0;
     st->done = (tot[1] == 0.0) ? 1 : (isfinite(tot[0]) && isfinite(tot[1]) ? 0 : 3);
@@ -221,17 +240,17 @@ template <class V, class TA>
 __global__ void k_apply_dot(LevelView<TA> lv, const V *d, V *q, CGState *st,
                             RedScratch rs) {
   if (stopped(st)) return;
-  double v[1] = {0.0};
+  V p = V(0);
   const int64_t n = lv.ncell();
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
        c += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(c % lv.nx);
-    const int64_t t = c / lv.nx;
-    const int j = (int)(t % lv.ny), k = (int)(t / lv.ny);
+    int i, j, k;
+    GridDev::decomp(c, lv.nx, lv.ny, i, j, k);
     const V qc = apply_cell<V, TA>(lv, d, i, j, k, c);
     q[c] = qc;
-    v[0] += (double)d[c] * (double)qc;
+    p += d[c] * qc;
   }
+  double v[1] = {(double)p};
   double tot[1];
   if (grid_sum<1>(v, rs, tot) && threadIdx.x == 0) {
     st->dq = tot[0];
@@ -247,14 +266,15 @@ __global__ void k_cg_xr(int64_t n, V *x, V *r, const V *d, const V *q,
                         CGState *st, RedScratch rs, bool preconditioned) {
   if (stopped(st)) return;
   const V a = (V)st->alpha;
-  double v[1] = {0.0};
+  V p = V(0);
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
        c += (int64_t)gridDim.x * blockDim.x) {
     x[c] += a * d[c];
     const V rc = r[c] - a * q[c];
     r[c] = rc;
-    v[0] += (double)rc * (double)rc;
+    p += rc * rc;
   }
+  double v[1] = {(double)p};
   double tot[1];
   if (grid_sum<1>(v, rs, tot) && threadIdx.x == 0) {
     st->rr = tot[0];
@@ -274,10 +294,11 @@ template <class V>
 __global__ void k_cg_rz(int64_t n, const V *r, const V *z, CGState *st,
                         RedScratch rs) {
   if (stopped(st)) return;
-  double v[1] = {0.0};
+  V p = V(0);
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
        c += (int64_t)gridDim.x * blockDim.x)
-    v[0] += (double)r[c] * (double)z[c];
+    p += r[c] * z[c];
+  double v[1] = {(double)p};
   double tot[1];
   if (grid_sum<1>(v, rs, tot) && threadIdx.x == 0) {
     if (!(tot[0] > 0.0) || !isfinite(tot[0])) {
@@ -308,9 +329,8 @@ __global__ void k_mg_coarsen(LevelView<TI> f, int cnx, int cny, int cnz, TO *ax,
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   Lv F{f.nx, f.ny, f.nz};
   if (t < n0) {
-    const int I = (int)(t % (cnx + 1));
-    const int64_t q = t / (cnx + 1);
-    const int J = (int)(q % cny), K = (int)(q / cny);
+    int I, J, K;
+    GridDev::decomp(t, cnx + 1, cny, I, J, K);
     float s = 0.f;
     for (int b = 0; b < 2; ++b)
       for (int a = 0; a < 2; ++a) s += (float)ld(f.ax + F.fx(2 * I, 2 * J + a, 2 * K + b));
@@ -319,9 +339,8 @@ __global__ void k_mg_coarsen(LevelView<TI> f, int cnx, int cny, int cnz, TO *ax,
   }
   t -= n0;
   if (t < n1) {
-    const int I = (int)(t % cnx);
-    const int64_t q = t / cnx;
-    const int J = (int)(q % (cny + 1)), K = (int)(q / (cny + 1));
+    int I, J, K;
+    GridDev::decomp(t, cnx, cny + 1, I, J, K);
     float s = 0.f;
     for (int b = 0; b < 2; ++b)
       for (int a = 0; a < 2; ++a) s += (float)ld(f.ay + F.fy(2 * I + a, 2 * J, 2 * K + b));
@@ -330,9 +349,8 @@ __global__ void k_mg_coarsen(LevelView<TI> f, int cnx, int cny, int cnz, TO *ax,
   }
   t -= n1;
   if (t < n2) {
-    const int I = (int)(t % cnx);
-    const int64_t q = t / cnx;
-    const int J = (int)(q % cny), K = (int)(q / cny);
+    int I, J, K;
+    GridDev::decomp(t, cnx, cny, I, J, K);
     float s = 0.f;
     for (int b = 0; b < 2; ++b)
       for (int a = 0; a < 2; ++a) s += (float)ld(f.az + F.fz(2 * I + a, 2 * J + b, 2 * K));
@@ -349,9 +367,8 @@ __global__ void k_mg_smooth(LevelView<TA> lv, V *x, const V *b, int color,
   const int64_t n = (int64_t)hx * lv.ny * lv.nz;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const int ii = (int)(t % hx);
-    const int64_t q = t / hx;
-    const int j = (int)(q % lv.ny), k = (int)(q / lv.ny);
+    int ii, j, k;
+    GridDev::decomp(t, hx, lv.ny, ii, j, k);
     const int i = 2 * ii + ((j + k + color) & 1);
     if (i >= lv.nx) continue;
     const int64_t c = ((int64_t)k * lv.ny + j) * lv.nx + i;
@@ -366,10 +383,9 @@ __global__ void k_mg_residual(LevelView<TA> lv, const V *x, const V *b, V *r,
   const int64_t n = lv.ncell();
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
        c += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(c % lv.nx);
-    const int64_t q = c / lv.nx;
-    const int j = (int)(q % lv.ny), k = (int)(q / lv.ny);
-    r[c] = b[c] - apply_cell<V, TA>(lv, x, i, j, k, c);
+    int i, j, k;
+    GridDev::decomp(c, lv.nx, lv.ny, i, j, k);
+    r[c] = residual_cell<V, TA>(lv, x, b, i, j, k, c);
   }
 }
 
@@ -380,9 +396,8 @@ __global__ void k_mg_restrict(int fnx, int fny, int fnz, int cnx, int cny,
   const int64_t n = (int64_t)cnx * cny * cnz;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
        c += (int64_t)gridDim.x * blockDim.x) {
-    const int I = (int)(c % cnx);
-    const int64_t q = c / cnx;
-    const int J = (int)(q % cny), K = (int)(q / cny);
+    int I, J, K;
+    GridDev::decomp(c, cnx, cny, I, J, K);
     bc[c] = restrict_cell<V>(fnx, fny, fnz, cnx, cny, cnz, rf, I, J, K);
   }
 }
@@ -395,9 +410,8 @@ __global__ void k_mg_prolong(LevelView<TF> f, int cnx, int cny, int cnz,
   const int64_t n = f.ncell();
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
        c += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(c % f.nx);
-    const int64_t q = c / f.nx;
-    const int j = (int)(q % f.ny), k = (int)(q / f.ny);
+    int i, j, k;
+    GridDev::decomp(c, f.nx, f.ny, i, j, k);
     if (!(six<float>(f, i, j, k).diag() > 0.f)) continue;
     xf[c] += prolong_cell<V>(cnx, cny, cnz, xc, i, j, k);
   }
@@ -439,7 +453,7 @@ k_mg_coarse_chain(CoarseChain<V, TA> ch, const CGState *st) {
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
       const int i = t % lv.nx, q = t / lv.nx;
       const int j = q % lv.ny, k = q / lv.ny;
-      ch.r[l][t] = ch.b[l][t] - apply_cell<V, TA>(lv, ch.x[l], i, j, k, t);
+      ch.r[l][t] = residual_cell<V, TA>(lv, ch.x[l], ch.b[l], i, j, k, t);
     }
     __syncthreads();
     const LevelView<TA> &cv = ch.lv[l + 1];
@@ -503,9 +517,9 @@ void launch_axpy_outer(const Launch &L, int64_t n, S *x, const V *e) {
 }
 template <class V>
 void launch_cg_init(const Launch &L, int64_t n, const V *r, const V *z, V *d,
-                    CGState *st, const RedScratch &rs, double rel_tol) {
+                    CGState *st, const RedScratch &rs) {
   ProfScope _ps(L, NF_K_CG_INIT);
-  k_cg_init<V><<<kRedBlocks, kBlock, 0, L.s>>>(n, r, z, d, st, rs, rel_tol);
+  k_cg_init<V><<<kRedBlocks, kBlock, 0, L.s>>>(n, r, z, d, st, rs);
   ++*L.counter;
 }
 template <class V, class TA>
@@ -590,7 +604,7 @@ void launch_mg_coarse_chain(const Launch &L, const CoarseChain<V, TA> &ch,
 #define NF_INST_V(V)                                                           \
   template void launch_cg_init<V>(const Launch &, int64_t, const V *,        \
                                   const V *, V *, CGState *,                  \
-                                  const RedScratch &, double);                \
+                                  const RedScratch &);                        \
   template void launch_cg_xr<V>(const Launch &, int64_t, V *, V *, const V *,\
                                 const V *, CGState *, const RedScratch &,     \
                                 bool);                                        \

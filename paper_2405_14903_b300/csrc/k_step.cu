@@ -138,11 +138,17 @@ __device__ __forceinline__ T *comp(FieldsMut<T> &u, int e) {
 }
 
 // ---------------------------------------------------------- rasterise -----
+template <class T>
+__device__ __forceinline__ double band_fraction(const GridDev &g,
+                                                const SceneDev &s, double x,
+                                                double y, double z);
+
 // alpha_f = (1/64) sum over 4x4x4 cell-centred subsamples of the face's
 // dx^3 control volume of H(phi), H = clamp(1/2 + phi / (dx/4), 0, 1).
 // Faces whose centre is farther than 0.8 dx from the interface are saturated
 // (subsamples lie within 0.65 dx of the centre and phi is 1-Lipschitz), so
-// only the narrow band evaluates the 64 samples, in FP64.
+// only the narrow band evaluates the 64 samples (directly in FP64 for FP64
+// fields, with the narrow-band evaluator of scene.cuh for FP32 fields).
 template <class T>
 __global__ void k_rasterize(GridDev g, SceneDev s, FieldsMut<T> alpha) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -156,11 +162,11 @@ __global__ void k_rasterize(GridDev g, SceneDev s, FieldsMut<T> alpha) {
     a[f] = g.outlet_face(d, i, j, k) ? T(1) : T(0);
     return;
   }
-  double X, Y, Z;
-  face_pos(d, i, j, k, X, Y, Z);
-  const float pc = scene_phi<float>(s, (float)(X * g.dx), (float)(Y * g.dx),
-                                    (float)(Z * g.dx));
-  const float margin = 0.8f * (float)g.dx;
+  const float hf = (float)g.dx;
+  const float pc = scene_phi<float>(s, (i + (d == 0 ? 0.f : 0.5f)) * hf,
+                                    (j + (d == 1 ? 0.f : 0.5f)) * hf,
+                                    (k + (d == 2 ? 0.f : 0.5f)) * hf);
+  const float margin = 0.8f * hf;
   if (pc > margin) {
     a[f] = T(1);
     return;
@@ -169,21 +175,59 @@ __global__ void k_rasterize(GridDev g, SceneDev s, FieldsMut<T> alpha) {
     a[f] = T(0);
     return;
   }
+  double X, Y, Z;
+  face_pos(d, i, j, k, X, Y, Z);
+  a[f] = T(band_fraction<T>(g, s, X * g.dx, Y * g.dx, Z * g.dx));
+}
+
+// alpha of a band face: the 64-sample ramp average. FP64 fields evaluate
+// phi directly in FP64; FP32 fields use the narrow-band evaluator.
+template <class T>
+__device__ __forceinline__ double band_fraction(const GridDev &g,
+                                                const SceneDev &s, double x,
+                                                double y, double z) {
+  if (sizeof(T) == 4) {
+    LocalSdf L;
+    L.init(s, x, y, z, g.dx);
+    if (!L.overflow) {
+      // saturated samples are counted exactly; only the few samples inside
+      // the ramp are summed in FP32
+      const float inv_w = (float)(4.0 / g.dx), h = (float)g.dx;
+      int full = 0;
+      float part = 0.f;
+      for (int c = 0; c < 4; ++c) {
+        const float oz = ((c + 0.5f) * 0.25f - 0.5f) * h;
+        for (int b = 0; b < 4; ++b) {
+          const float oy = ((b + 0.5f) * 0.25f - 0.5f) * h;
+          for (int q = 0; q < 4; ++q) {
+            const float ox = ((q + 0.5f) * 0.25f - 0.5f) * h;
+            const float hv = 0.5f + L.phi(ox, oy, oz) * inv_w;
+            if (hv >= 1.f)
+              ++full;
+            else if (hv > 0.f)
+              part += hv;
+          }
+        }
+      }
+      return ((double)full + (double)part) * (1.0 / 64.0);
+    }
+  }
   const double inv_w = 4.0 / g.dx;
   double acc = 0.0;
   for (int c = 0; c < 4; ++c) {
-    const double z = (Z + (c + 0.5) * 0.25 - 0.5) * g.dx;
+    const double zz = z + ((c + 0.5) * 0.25 - 0.5) * g.dx;
     for (int b = 0; b < 4; ++b) {
-      const double y = (Y + (b + 0.5) * 0.25 - 0.5) * g.dx;
+      const double yy = y + ((b + 0.5) * 0.25 - 0.5) * g.dx;
       for (int q = 0; q < 4; ++q) {
-        const double x = (X + (q + 0.5) * 0.25 - 0.5) * g.dx;
-        const double h = 0.5 + scene_phi<double>(s, x, y, z) * inv_w;
-        acc += fmin(fmax(h, 0.0), 1.0);
+        const double xx = x + ((q + 0.5) * 0.25 - 0.5) * g.dx;
+        const double hv = 0.5 + scene_phi<double>(s, xx, yy, zz) * inv_w;
+        acc += fmin(fmax(hv, 0.0), 1.0);
       }
     }
   }
-  a[f] = T(acc * (1.0 / 64.0));
+  return acc * (1.0 / 64.0);
 }
+
 
 // ------------------------------------------------------------- advect -----
 // Positions are carried as (integer lattice base, small fractional offset)
@@ -311,15 +355,17 @@ __global__ void k_advect_adjoint(GridDev g, Fields<T> u, Fields<T> gut,
 
 // ----------------------------------------------------- face helpers -------
 // Solid velocity of a component-d face (0 on the box boundary), evaluated in
-// the field precision T.
+// the field precision T (positions formed in T: no FP64 for FP32 fields).
 template <class T>
 __device__ __forceinline__ T face_us(const GridDev &g, const SceneDev &s,
                                      int d, int i, int j, int k) {
   if (s.kind == NF_SCENE_NONE || s.kind == NF_SCENE_SPHERES) return T(0);
   if (g.boundary(d, i, j, k)) return T(0);
-  double X, Y, Z;
-  face_pos(d, i, j, k, X, Y, Z);
-  return scene_us<T>(s, d, T(X * g.dx), T(Y * g.dx), T(Z * g.dx));
+  const T h = T(g.dx);
+  const T X = (T(i) + (d == 0 ? T(0) : T(0.5))) * h;
+  const T Y = (T(j) + (d == 1 ? T(0) : T(0.5))) * h;
+  const T Z = (T(k) + (d == 2 ? T(0) : T(0.5))) * h;
+  return scene_us<T>(s, d, X, Y, Z);
 }
 
 // Sum of the six face fractions of cell (i, j, k).
@@ -342,11 +388,14 @@ __device__ __forceinline__ void face_cells(const GridDev &g, int d, int i,
 }
 
 // --------------------------------------------------------------- rhs ------
-// b = G^T (S U^ + (I - S) U_s) on active cells (sum alpha > 0), else 0.
-// G^T v at a cell is v(low face) - v(high face), summed over the axes.
+// b = G^T (S U^ + (I - S) U_s) / c on active cells (sum alpha > 0), else 0.
+// G^T v at a cell is v(low face) - v(high face), summed over the axes. The
+// division by c = dt / (rho dx) lets the solver use the unit-scale operator
+// G^T S G, whose coefficients do not depend on the step length.
 template <class T, class S>
 __global__ void k_rhs(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
                       S *b, RedScratch rs, double *bnorm2) {
+  const double inv_c = 1.0 / g.c;
   double v[1] = {0.0};
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
        c < g.ncell(); c += (int64_t)gridDim.x * blockDim.x) {
@@ -369,54 +418,13 @@ __global__ void k_rhs(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
         acc += sg * (double)(az * uh.z[fz] +
                              (T(1) - az) * face_us<T>(g, s, 2, i, j, K[side]));
       }
+      acc *= inv_c;
     }
     b[c] = (S)acc;
     v[0] += acc * acc;
   }
   double tot[1];
   if (grid_sum<1>(v, rs, tot) && threadIdx.x == 0) *bnorm2 = tot[0];
-}
-
-// ------------------------------------------------------------- gauge ------
-// Sum and count of v over active cells.
-template <class T, class S>
-__global__ void k_active_sum(GridDev g, Fields<T> alpha, const S *v,
-                             RedScratch rs, double *out) {
-  double acc[2] = {0.0, 0.0};
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-       c < g.ncell(); c += (int64_t)gridDim.x * blockDim.x) {
-    int i, j, k;
-    g.cell_ijk(c, i, j, k);
-    if (cell_diag(g, alpha, i, j, k) > T(0)) {
-      acc[0] += (double)v[c];
-      acc[1] += 1.0;
-    }
-  }
-  double tot[2];
-  if (grid_sum<2>(acc, rs, tot) && threadIdx.x == 0) {
-    out[0] = tot[0];
-    out[1] = tot[1];
-  }
-}
-
-// v -= mean on active cells; ||v||^2 of the result into out[2].
-template <class T, class S>
-__global__ void k_sub_mean(GridDev g, Fields<T> alpha, S *v, RedScratch rs,
-                           double *out) {
-  const double mean = out[1] > 0.0 ? out[0] / out[1] : 0.0;
-  double acc[1] = {0.0};
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-       c < g.ncell(); c += (int64_t)gridDim.x * blockDim.x) {
-    int i, j, k;
-    g.cell_ijk(c, i, j, k);
-    if (cell_diag(g, alpha, i, j, k) > T(0)) {
-      const double x = (double)v[c] - mean;
-      v[c] = (S)x;
-      acc[0] += x * x;
-    }
-  }
-  double tot[1];
-  if (grid_sum<1>(acc, rs, tot) && threadIdx.x == 0) out[2] = tot[0];
 }
 
 // ------------------------------------------------------------- update -----
@@ -432,9 +440,9 @@ __global__ void k_update(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
   g.face_ijk(d, f, i, j, k);
   int64_t cL, cR;
   face_cells(g, d, i, j, k, cL, cR);
-  const double pR = cR >= 0 ? (double)P[cR] : 0.0;
-  const double pL = cL >= 0 ? (double)P[cL] : 0.0;
-  const T gp = (T)(g.c * (pR - pL));
+  const S pR = cR >= 0 ? P[cR] : S(0);
+  const S pL = cL >= 0 ? P[cL] : S(0);
+  const T gp = T(g.c) * (T)(pR - pL);
   const T a = comp(alpha, d)[f];
   comp(u, d)[f] = a * (comp(uh, d)[f] - gp) + (T(1) - a) * face_us<T>(g, s, d, i, j, k);
 }
@@ -481,7 +489,59 @@ __global__ void k_loss_outflow(GridDev g, Fields<T> u, FieldsMut<T> gu,
 }
 
 // ------------------------------------------------------------ adjoint -----
-// gP = -c G^T (S gU) on active cells.
+// d alpha / d theta of a band face: (1/64) sum over the subsamples inside
+// the ramp of (4 / dx) d phi / d theta; the same evaluator (and precision)
+// as band_fraction.
+template <class T>
+__device__ __forceinline__ void band_dalpha(const GridDev &g, const SceneDev &s,
+                                            double x, double y, double z, T *da) {
+  for (int q = 0; q < kMaxParams; ++q) da[q] = T(0);
+  if (sizeof(T) == 4) {
+    LocalSdf L;
+    L.init(s, x, y, z, g.dx);
+    if (!L.overflow) {
+      const float inv_w = (float)(4.0 / g.dx), h = (float)g.dx;
+      float tmp[kMaxParams];
+      for (int c = 0; c < 4; ++c) {
+        const float oz = ((c + 0.5f) * 0.25f - 0.5f) * h;
+        for (int b = 0; b < 4; ++b) {
+          const float oy = ((b + 0.5f) * 0.25f - 0.5f) * h;
+          for (int q = 0; q < 4; ++q) {
+            const float ox = ((q + 0.5f) * 0.25f - 0.5f) * h;
+            const float hv = 0.5f + L.phi(ox, oy, oz) * inv_w;
+            if (hv > 0.f && hv < 1.f) {
+              L.dphi(s, ox, oy, oz, tmp);
+              for (int p = 0; p < s.K; ++p) da[p] += (T)(inv_w * tmp[p]);
+            }
+          }
+        }
+      }
+      for (int p = 0; p < s.K; ++p) da[p] *= T(1.0 / 64.0);
+      return;
+    }
+  }
+  const double inv_w = 4.0 / g.dx;
+  double tmp[kMaxParams], acc[kMaxParams];
+  for (int p = 0; p < kMaxParams; ++p) acc[p] = 0.0;
+  for (int cz = 0; cz < 4; ++cz) {
+    const double zz = z + ((cz + 0.5) * 0.25 - 0.5) * g.dx;
+    for (int cy = 0; cy < 4; ++cy) {
+      const double yy = y + ((cy + 0.5) * 0.25 - 0.5) * g.dx;
+      for (int cx = 0; cx < 4; ++cx) {
+        const double xx = x + ((cx + 0.5) * 0.25 - 0.5) * g.dx;
+        const double hv = 0.5 + scene_phi<double>(s, xx, yy, zz) * inv_w;
+        if (hv > 0.0 && hv < 1.0) {
+          scene_dphi(s, xx, yy, zz, tmp);
+          for (int p = 0; p < s.K; ++p) acc[p] += inv_w * tmp[p];
+        }
+      }
+    }
+  }
+  for (int p = 0; p < s.K; ++p) da[p] = (T)(acc[p] * (1.0 / 64.0));
+}
+
+// gP / c = -G^T (S gU) on active cells (dJ/dP of the update, divided by c
+// for the unit-scale solver operator, like the forward right-hand side).
 template <class T, class S>
 __global__ void k_adj_gp(GridDev g, Fields<T> alpha, Fields<T> gu, S *gp,
                          RedScratch rs, double *norm2) {
@@ -499,7 +559,7 @@ __global__ void k_adj_gp(GridDev g, Fields<T> alpha, Fields<T> gu, S *gp,
       acc = (double)(alpha.x[f0] * gu.x[f0]) - (double)(alpha.x[f0p] * gu.x[f0p]) +
             (double)(alpha.y[f1] * gu.y[f1]) - (double)(alpha.y[f1p] * gu.y[f1p]) +
             (double)(alpha.z[f2] * gu.z[f2]) - (double)(alpha.z[f2p] * gu.z[f2p]);
-      acc *= -g.c;
+      acc = -acc;
     }
     gp[c] = (S)acc;
     v[0] += acc * acc;
@@ -517,9 +577,11 @@ template <class T, class S>
 __global__ void k_adj_face(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
                            const S *P, const S *y, Fields<T> gu,
                            FieldsMut<T> guh, RedScratch rs, double *gtheta) {
-  double acc[kMaxParams];
+  // per-thread partial sums in the field precision (each thread adds a few
+  // dozen faces), block and grid sums in FP64
+  T acc[kMaxParams];
 #pragma unroll
-  for (int q = 0; q < kMaxParams; ++q) acc[q] = 0.0;
+  for (int q = 0; q < kMaxParams; ++q) acc[q] = T(0);
   const int64_t n = g.nface(0) + g.nface(1) + g.nface(2);
   const double c = g.c;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
@@ -539,45 +601,66 @@ __global__ void k_adj_face(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
     if (s.K == 0 || g.boundary(d, i, j, k)) continue;
     const double Uh = (double)comp(uh, d)[f];
     const double us = (double)face_us<T>(g, s, d, i, j, k);
-    const double gUs = (1.0 - a) * (gU + Gy);
-    const double gS = gU * (Uh - c * GP - us) + Gy * (Uh - us) - c * Gy * GP;
+    const T gUs = (T)((1.0 - a) * (gU + Gy));
+    const T gS = (T)(gU * (Uh - c * GP - us) + Gy * (Uh - us) - c * Gy * GP);
     double X, Y, Z;
     face_pos(d, i, j, k, X, Y, Z);
-    double tmp[kMaxParams];
-    if (gUs != 0.0 && s.kind != NF_SCENE_SPHERES) {
-      scene_dus(s, d, X * g.dx, Y * g.dx, Z * g.dx, tmp);
-      for (int q = 0; q < s.K; ++q) acc[q] += gUs * tmp[q];
+    if (gUs != T(0) && s.kind != NF_SCENE_SPHERES) {
+      if (sizeof(T) == 4) {
+        float tmp[kMaxParams];
+        scene_dus_f(s, d, (float)(X * g.dx), (float)(Y * g.dx), (float)(Z * g.dx), tmp);
+        for (int q = 0; q < s.K; ++q) acc[q] += gUs * (T)tmp[q];
+      } else {
+        double tmp[kMaxParams];
+        scene_dus(s, d, X * g.dx, Y * g.dx, Z * g.dx, tmp);
+        for (int q = 0; q < s.K; ++q) acc[q] += gUs * (T)tmp[q];
+      }
     }
-    if (gS == 0.0) continue;
+    if (gS == T(0)) continue;
     const float pc = scene_phi<float>(s, (float)(X * g.dx), (float)(Y * g.dx),
                                       (float)(Z * g.dx));
     const float margin = 0.8f * (float)g.dx;
     if (pc > margin || pc < -margin) continue;
-    const double inv_w = 4.0 / g.dx;
-    double da[kMaxParams];
-    for (int q = 0; q < s.K; ++q) da[q] = 0.0;
-    for (int cz = 0; cz < 4; ++cz) {
-      const double z = (Z + (cz + 0.5) * 0.25 - 0.5) * g.dx;
-      for (int cy = 0; cy < 4; ++cy) {
-        const double yy = (Y + (cy + 0.5) * 0.25 - 0.5) * g.dx;
-        for (int cx = 0; cx < 4; ++cx) {
-          const double x = (X + (cx + 0.5) * 0.25 - 0.5) * g.dx;
-          const double h = 0.5 + scene_phi<double>(s, x, yy, z) * inv_w;
-          if (h > 0.0 && h < 1.0) {
-            scene_dphi(s, x, yy, z, tmp);
-            for (int q = 0; q < s.K; ++q) da[q] += inv_w * tmp[q];
-          }
-        }
-      }
-    }
-    for (int q = 0; q < s.K; ++q) acc[q] += gS * da[q] * (1.0 / 64.0);
+    T da[kMaxParams];
+    band_dalpha<T>(g, s, X * g.dx, Y * g.dx, Z * g.dx, da);
+    for (int q = 0; q < s.K; ++q) acc[q] += gS * da[q];
   }
+  double dacc[kMaxParams];
+#pragma unroll
+  for (int q = 0; q < kMaxParams; ++q) dacc[q] = (double)acc[q];
   double tot[kMaxParams];
-  if (grid_sum<kMaxParams>(acc, rs, tot) && threadIdx.x == 0)
+  if (grid_sum<kMaxParams>(dacc, rs, tot) && threadIdx.x == 0)
     for (int q = 0; q < kMaxParams; ++q) gtheta[q] = tot[q];
 }
 
+// max |u| over every face (CFL rule), as the bits of a non-negative double
+// (their integer order is the numeric order, so atomicMax is exact).
+template <class T>
+__global__ void k_absmax_faces(GridDev g, Fields<T> u, unsigned long long *out) {
+  double m = 0.0;
+  const int64_t n = g.nface(0) + g.nface(1) + g.nface(2);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int d;
+    int64_t f;
+    split_face(g, t, d, f);
+    m = fmax(m, fabs((double)comp(u, d)[f]));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0)
+    atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
 // ------------------------------------------------------------ launchers ---
+template <class T>
+void launch_absmax_faces(const Launch &L, const GridDev &g, Fields<T> u,
+                         unsigned long long *out) {
+  cudaMemsetAsync(out, 0, sizeof(unsigned long long), L.s);
+  ProfScope _ps(L, NF_K_LOSS);
+  k_absmax_faces<T><<<kRedBlocks, kBlock, 0, L.s>>>(g, u, out);
+  ++*L.counter;
+}
+
 template <class T>
 void launch_rasterize(const Launch &L, const GridDev &g, const SceneDev &s,
                       FieldsMut<T> alpha) {
@@ -615,15 +698,6 @@ void launch_rhs(const Launch &L, const GridDev &g, const SceneDev &s,
   ProfScope _ps(L, NF_K_RHS);
   k_rhs<T, S><<<kRedBlocks, kBlock, 0, L.s>>>(g, s, alpha, uh, b, rs, bnorm2);
   ++*L.counter;
-}
-
-template <class T, class S>
-void launch_remove_mean(const Launch &L, const GridDev &g, Fields<T> alpha,
-                        S *v, const RedScratch &rs, double *scratch) {
-  ProfScope _ps(L, NF_K_GAUGE);
-  k_active_sum<T, S><<<kRedBlocks, kBlock, 0, L.s>>>(g, alpha, v, rs, scratch);
-  k_sub_mean<T, S><<<kRedBlocks, kBlock, 0, L.s>>>(g, alpha, v, rs, scratch);
-  *L.counter += 2;
 }
 
 template <class T, class S>
@@ -676,7 +750,9 @@ void launch_adj_face(const Launch &L, const GridDev &g, const SceneDev &s,
                                          int);                               \
   template void launch_loss<T>(const Launch &, const GridDev &, int,        \
                                Fields<T>, FieldsMut<T>, bool,                \
-                               const RedScratch &, double *);
+                               const RedScratch &, double *);                \
+  template void launch_absmax_faces<T>(const Launch &, const GridDev &,     \
+                                       Fields<T>, unsigned long long *);
 #define NF_INST_TS(T, S)                                                      \
   template void launch_rhs<T, S>(const Launch &, const GridDev &,           \
                                  const SceneDev &, Fields<T>, Fields<T>, S *,\
@@ -691,10 +767,7 @@ void launch_adj_face(const Launch &L, const GridDev &g, const SceneDev &s,
                                       const SceneDev &, Fields<T>, Fields<T>,\
                                       const S *, const S *, Fields<T>,       \
                                       FieldsMut<T>, const RedScratch &,      \
-                                      double *);                             \
-  template void launch_remove_mean<T, S>(const Launch &, const GridDev &,   \
-                                         Fields<T>, S *, const RedScratch &, \
-                                         double *);
+                                      double *);
 NF_INST_T(float)
 NF_INST_T(double)
 NF_INST_TS(float, float)

@@ -22,6 +22,7 @@ struct FieldsMut {
 // kernel returns immediately once `done` is set, so the host may enqueue
 // iterations in batches and poll rarely without changing the result.
 struct CGState {
+  double tol;    // relative tolerance of the inner solve (set by the host)
   double rz;     // <r, z>
   double dq;     // <d, A d>
   double rr;     // <r, r>
@@ -62,6 +63,10 @@ template <class T>
 void launch_loss(const Launch &L, const GridDev &g, int kind, Fields<T> u,
                  FieldsMut<T> gu, bool want_grad, const RedScratch &rs,
                  double *J);
+// max |u| over all faces into *out (the bits of a double).
+template <class T>
+void launch_absmax_faces(const Launch &L, const GridDev &g, Fields<T> u,
+                         unsigned long long *out);
 template <class T, class S>
 void launch_adj_gp(const Launch &L, const GridDev &g, Fields<T> alpha,
                    Fields<T> gu, S *gp, const RedScratch &rs, double *norm2);
@@ -70,12 +75,6 @@ void launch_adj_face(const Launch &L, const GridDev &g, const SceneDev &s,
                      Fields<T> alpha, Fields<T> uh, const S *P, const S *y,
                      Fields<T> gu, FieldsMut<T> guh, const RedScratch &rs,
                      double *gtheta);
-// Gauge of a closed box: subtract the mean over active cells (sum of face
-// fractions > 0) from the cell field v; optionally return ||v||^2 after.
-// scratch holds 3 doubles.
-template <class T, class S>
-void launch_remove_mean(const Launch &L, const GridDev &g, Fields<T> alpha,
-                        S *v, const RedScratch &rs, double *scratch);
 
 // ----------------------------------------------------------- solver ops ---
 // r = b - A x in precision S (fine operator with fractions of type T);
@@ -88,9 +87,10 @@ void launch_residual_outer(const Launch &L, const LevelView<T> &lv,
 template <class S, class V>
 void launch_axpy_outer(const Launch &L, int64_t n, S *x, const V *e);
 
+// d = z, <r, z>, <r, r>; stop when <r, r> <= st->tol^2 <r0, r0>.
 template <class V>
 void launch_cg_init(const Launch &L, int64_t n, const V *r, const V *z, V *d,
-                    CGState *st, const RedScratch &rs, double rel_tol);
+                    CGState *st, const RedScratch &rs);
 template <class V, class TA>
 void launch_apply_dot(const Launch &L, const LevelView<TA> &lv, const V *d,
                       V *q, CGState *st, const RedScratch &rs);

@@ -37,20 +37,23 @@ struct GridDev {
   __host__ __device__ int64_t face(int d, int i, int j, int k) const {
     return ((int64_t)k * fny(d) + j) * fnx(d) + i;
   }
-  // Linear face index -> (i, j, k) of component d.
+  // Linear face index -> (i, j, k) of component d. Arrays hold fewer than
+  // 2^32 entries, so the decode uses 32-bit unsigned division (64-bit
+  // integer division is a long instruction sequence on the GPU).
   __host__ __device__ void face_ijk(int d, int64_t f, int &i, int &j,
                                     int &k) const {
-    int fx = fnx(d), fy = fny(d);
-    i = (int)(f % fx);
-    int64_t r = f / fx;
-    j = (int)(r % fy);
-    k = (int)(r / fy);
+    decomp(f, fnx(d), fny(d), i, j, k);
   }
   __host__ __device__ void cell_ijk(int64_t c, int &i, int &j, int &k) const {
-    i = (int)(c % nx);
-    int64_t r = c / nx;
-    j = (int)(r % ny);
-    k = (int)(r / ny);
+    decomp(c, nx, ny, i, j, k);
+  }
+  __host__ __device__ static void decomp(int64_t c, int nx, int ny, int &i,
+                                         int &j, int &k) {
+    const uint32_t u = (uint32_t)c, q = u / (uint32_t)nx;
+    i = (int)(u - q * (uint32_t)nx);
+    const uint32_t kk = q / (uint32_t)ny;
+    j = (int)(q - kk * (uint32_t)ny);
+    k = (int)kk;
   }
   // Is face (d; i, j, k) on the box boundary?
   __host__ __device__ bool boundary(int d, int i, int j, int k) const {
@@ -73,7 +76,8 @@ struct SceneDev {
   double sc[3], sr, sv[3];
   // chamber: centre, axes, min axis, radius s(t), rate sdot(t) and their
   // theta derivatives; duct box centre and half extents (fluid inside)
-  double cc[3], ca[3], camin, cs, csdot, cds[8], cdsdot[8];
+  double cc[3], ca[3], camin, cs, csdot, crate, cds[8], cdsdot[8];  // crate = sdot / s
+  double cdus[8];  // d(sdot / s) / d theta
   double dc[3], dh[3];
   // plate: centre, half extents, angle, cos/sin, rate, theta derivatives
   double pc[3], ph[3], pang, pcos, psin, pomega, pdang[4], pdomega[4];

@@ -99,7 +99,7 @@ __device__ __forceinline__ R scene_us(const SceneDev &s, int d, R x, R y,
     case NF_SCENE_CHAMBER: {
       if (!chamber_ell_active<R>(s, x, y, z)) return R(0);
       R r = d == 0 ? x - R(s.cc[0]) : (d == 1 ? y - R(s.cc[1]) : z - R(s.cc[2]));
-      return R(s.csdot / s.cs) * r;
+      return R(s.crate) * r;
     }
     case NF_SCENE_PLATE: {
       if (d == 0) return -R(s.pomega) * (y - R(s.pc[1]));
@@ -143,6 +143,29 @@ __device__ __forceinline__ void scene_dphi(const SceneDev &s, double x,
   }
 }
 
+// d u_s,d / d theta at x (K values), FP32 (selector and factors only).
+__device__ __forceinline__ void scene_dus_f(const SceneDev &s, int d, float x,
+                                            float y, float z, float *out) {
+  switch (s.kind) {
+    case NF_SCENE_SPHERE:
+      for (int k = 0; k < 3; ++k) out[k] = (k == d) ? 1.f : 0.f;
+      return;
+    case NF_SCENE_CHAMBER: {
+      const bool e = chamber_ell_active<float>(s, x, y, z);
+      const float r = d == 0 ? x - (float)s.cc[0] : (d == 1 ? y - (float)s.cc[1] : z - (float)s.cc[2]);
+      for (int k = 0; k < 8; ++k) out[k] = e ? (float)s.cdus[k] * r : 0.f;
+      return;
+    }
+    case NF_SCENE_PLATE: {
+      const float f = d == 0 ? -(y - (float)s.pc[1]) : (d == 1 ? (x - (float)s.pc[0]) : 0.f);
+      for (int k = 0; k < 4; ++k) out[k] = f * (float)s.pdomega[k];
+      return;
+    }
+    default:
+      for (int k = 0; k < s.K; ++k) out[k] = 0.f;
+  }
+}
+
 // d u_s,d / d theta at x (K values).
 __device__ __forceinline__ void scene_dus(const SceneDev &s, int d, double x,
                                           double y, double z, double *out) {
@@ -153,9 +176,7 @@ __device__ __forceinline__ void scene_dus(const SceneDev &s, int d, double x,
     case NF_SCENE_CHAMBER: {
       bool e = chamber_ell_active<double>(s, x, y, z);
       double r = d == 0 ? x - s.cc[0] : (d == 1 ? y - s.cc[1] : z - s.cc[2]);
-      double inv = 1.0 / (s.cs * s.cs);
-      for (int k = 0; k < 8; ++k)
-        out[k] = e ? (s.cdsdot[k] * s.cs - s.csdot * s.cds[k]) * inv * r : 0.0;
+      for (int k = 0; k < 8; ++k) out[k] = e ? s.cdus[k] * r : 0.0;
       return;
     }
     case NF_SCENE_PLATE: {
@@ -167,5 +188,189 @@ __device__ __forceinline__ void scene_dus(const SceneDev &s, int d, double x,
       for (int k = 0; k < s.K; ++k) out[k] = 0.0;
   }
 }
+
+}  // namespace nf
+
+namespace nf {
+
+// --------------------------------------------------- narrow-band phi -----
+// phi at points x_f + delta near a face centre x_f, with |delta| <= dx:
+// the centre quantities are formed in FP64 once, the increments in FP32
+// without cancellation, e.g. |d + delta| - |d| = (2 d.delta + |delta|^2) /
+// (|d + delta| + |d|) and, per box axis, |p + delta| - |p| = sign(p) delta
+// when |p| > |delta|. Near the interface every retained quantity is O(dx),
+// so the FP32 result carries an absolute error of ~1e-7 dx while the bulk
+// of the arithmetic (64 samples per face) is FP32.
+struct LocalSdf {
+  int kind;
+  // sphere(s): offset of the face centre from the centre, its norm, radius
+  float d[4][3], dn[4], r[4];
+  int nsph;
+  // chamber ellipsoid: e = (x_f - c0) / a, rho_c = |e|, 1 / a, amin, s
+  float e[3], rho, inva[3], amin;
+  double phic_ell;
+  // boxes (duct of the chamber, plate): per-axis p and q = |p| - h at the
+  // centre, and the rotation (plate) taking offsets into the box frame
+  float bp[3], bq[3], rc, rs;
+  bool has_box;
+  bool overflow;  // more candidate spheres than kept: evaluate in FP64
+
+  __device__ void init(const SceneDev &s, double x, double y, double z,
+                       double dx) {
+    kind = s.kind;
+    has_box = false;
+    overflow = false;
+    nsph = 0;
+    rc = 1.f;
+    rs = 0.f;
+    if (kind == NF_SCENE_SPHERE) {
+      const double a = x - s.sc[0], b = y - s.sc[1], c = z - s.sc[2];
+      nsph = 1;
+      d[0][0] = (float)a;
+      d[0][1] = (float)b;
+      d[0][2] = (float)c;
+      dn[0] = (float)sqrt(a * a + b * b + c * c);
+      r[0] = (float)(sqrt(a * a + b * b + c * c) - s.sr);  // phi at the centre
+    } else if (kind == NF_SCENE_SPHERES) {
+      // candidate spheres: within 1.6 dx (twice the control-volume radius)
+      // of the best centre value can be the minimum somewhere in the volume
+      double best = 1.0e3;
+      for (int i = 0; i < s.nspheres; ++i) {
+        const double *p = s.spheres + 4 * i;
+        const double a = x - p[0], b = y - p[1], c = z - p[2];
+        best = fmin(best, sqrt(a * a + b * b + c * c) - p[3]);
+      }
+      for (int i = 0; i < s.nspheres; ++i) {
+        const double *p = s.spheres + 4 * i;
+        const double a = x - p[0], b = y - p[1], c = z - p[2];
+        const double n = sqrt(a * a + b * b + c * c);
+        if (n - p[3] > best + 1.6 * dx) continue;
+        if (nsph == 4) {  // too many candidates: caller evaluates in FP64
+          overflow = true;
+          break;
+        }
+        d[nsph][0] = (float)a;
+        d[nsph][1] = (float)b;
+        d[nsph][2] = (float)c;
+        dn[nsph] = (float)n;
+        r[nsph] = (float)(n - p[3]);
+        ++nsph;
+      }
+    } else if (kind == NF_SCENE_CHAMBER) {
+      const double ex = (x - s.cc[0]) / s.ca[0], ey = (y - s.cc[1]) / s.ca[1],
+                   ez = (z - s.cc[2]) / s.ca[2];
+      const double rr = sqrt(ex * ex + ey * ey + ez * ez);
+      e[0] = (float)ex;
+      e[1] = (float)ey;
+      e[2] = (float)ez;
+      rho = (float)rr;
+      inva[0] = (float)(1.0 / s.ca[0]);
+      inva[1] = (float)(1.0 / s.ca[1]);
+      inva[2] = (float)(1.0 / s.ca[2]);
+      amin = (float)s.camin;
+      phic_ell = s.camin * (s.cs - rr);
+      box_init(x - s.dc[0], y - s.dc[1], z - s.dc[2], s.dh);
+    } else if (kind == NF_SCENE_PLATE) {
+      const double rx = x - s.pc[0], ry = y - s.pc[1], rz = z - s.pc[2];
+      rc = (float)s.pcos;
+      rs = (float)s.psin;
+      box_init(s.pcos * rx + s.psin * ry, -s.psin * rx + s.pcos * ry, rz, s.ph);
+    }
+  }
+
+  __device__ void box_init(double px, double py, double pz, const double *h) {
+    has_box = true;
+    const double p[3] = {px, py, pz};
+    for (int a = 0; a < 3; ++a) {
+      bp[a] = (float)p[a];
+      bq[a] = (float)(fabs(p[a]) - h[a]);
+    }
+  }
+
+  // |p + o| - |p| without cancellation.
+  __device__ static float absdiff(float p, float o) {
+    if (fabsf(p) >= fabsf(o)) return p >= 0.f ? o : -o;
+    return fabsf(p + o) - fabsf(p);
+  }
+
+  // box SDF (positive outside) at the centre offset by o (box frame)
+  __device__ float box(float ox, float oy, float oz) const {
+    const float qx = bq[0] + absdiff(bp[0], ox);
+    const float qy = bq[1] + absdiff(bp[1], oy);
+    const float qz = bq[2] + absdiff(bp[2], oz);
+    const float mx = fmaxf(qx, 0.f), my = fmaxf(qy, 0.f), mz = fmaxf(qz, 0.f);
+    return sqrtf(mx * mx + my * my + mz * mz) + fminf(fmaxf(qx, fmaxf(qy, qz)), 0.f);
+  }
+
+  // phi at x_f + (ox, oy, oz) (world offsets, |o| <= dx)
+  __device__ float phi(float ox, float oy, float oz) const {
+    switch (kind) {
+      case NF_SCENE_SPHERE:
+      case NF_SCENE_SPHERES: {
+        float best = 1.0e3f;
+        for (int i = 0; i < nsph; ++i) {
+          const float a = d[i][0] + ox, b = d[i][1] + oy, c = d[i][2] + oz;
+          const float num = 2.f * (d[i][0] * ox + d[i][1] * oy + d[i][2] * oz) +
+                            (ox * ox + oy * oy + oz * oz);
+          const float den = sqrtf(a * a + b * b + c * c) + dn[i];
+          best = fminf(best, r[i] + (den > 0.f ? num / den : 0.f));
+        }
+        return best;
+      }
+      case NF_SCENE_CHAMBER: {
+        const float ex = ox * inva[0], ey = oy * inva[1], ez = oz * inva[2];
+        const float a = e[0] + ex, b = e[1] + ey, c = e[2] + ez;
+        const float num = 2.f * (e[0] * ex + e[1] * ey + e[2] * ez) +
+                          (ex * ex + ey * ey + ez * ez);
+        const float den = sqrtf(a * a + b * b + c * c) + rho;
+        const float pe = (float)phic_ell - amin * (den > 0.f ? num / den : 0.f);
+        return fmaxf(pe, -box(ox, oy, oz));
+      }
+      case NF_SCENE_PLATE:
+        return box(rc * ox + rs * oy, -rs * ox + rc * oy, oz);
+      default:
+        return 1.0e3f;
+    }
+  }
+
+  // d phi / d theta at x_f + o (K values, FP32); xs are world coordinates
+  __device__ void dphi(const SceneDev &s, float ox, float oy, float oz,
+                       float *out) const {
+    switch (kind) {
+      case NF_SCENE_SPHERE: {
+        const float a = d[0][0] + ox, b = d[0][1] + oy, c = d[0][2] + oz;
+        const float n = sqrtf(a * a + b * b + c * c);
+        const float inv = n > 0.f ? (float)(-s.t) / n : 0.f;
+        out[0] = a * inv;
+        out[1] = b * inv;
+        out[2] = c * inv;
+        return;
+      }
+      case NF_SCENE_CHAMBER: {
+        const float ex = ox * inva[0], ey = oy * inva[1], ez = oz * inva[2];
+        const float a = e[0] + ex, b = e[1] + ey, c = e[2] + ez;
+        const float num = 2.f * (e[0] * ex + e[1] * ey + e[2] * ez) +
+                          (ex * ex + ey * ey + ez * ez);
+        const float den = sqrtf(a * a + b * b + c * c) + rho;
+        const float pe = (float)phic_ell - amin * (den > 0.f ? num / den : 0.f);
+        const bool ell = pe >= -box(ox, oy, oz);
+        for (int k = 0; k < 8; ++k) out[k] = ell ? (float)(s.camin * s.cds[k]) : 0.f;
+        return;
+      }
+      case NF_SCENE_PLATE: {
+        const float px = bp[0] + (rc * ox + rs * oy), py = bp[1] + (-rs * ox + rc * oy),
+                    pz = bp[2] + oz;
+        double gx, gy, gz;
+        box_sdf_grad((double)px, (double)py, (double)pz, s.ph[0], s.ph[1], s.ph[2],
+                     gx, gy, gz);
+        const float dang = (float)gx * py - (float)gy * px;
+        for (int k = 0; k < 4; ++k) out[k] = dang * (float)s.pdang[k];
+        return;
+      }
+      default:
+        for (int k = 0; k < s.K; ++k) out[k] = 0.f;
+    }
+  }
+};
 
 }  // namespace nf

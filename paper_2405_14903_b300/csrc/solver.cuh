@@ -32,8 +32,12 @@ struct SolveStats {
 template <class T, class S, class V, class TA>
 class Solver {
  public:
+  // The operator is the unit-scale G^T S G (c = 1 on the finest level,
+  // c_l = 2^-l below); callers pass b / c for A = c G^T S G.
   Solver(Ctx *ctx, const GridDev &g, const nf_config &cfg)
-      : ctx_(ctx), g_(g), cfg_(cfg) {}
+      : ctx_(ctx), g_(g), cfg_(cfg) {
+    g_.c = 1.0;
+  }
 
   // Allocates the hierarchy. Returns NF_OK or an error status.
   int init(Alloc &A) {
@@ -158,7 +162,7 @@ class Solver {
   static constexpr int kMaxOuter = 12;
   static constexpr int kChainCells = 16 * 16 * 16;
   static constexpr int kBatch = 4;
-  static constexpr int kCoarsestSweeps = 24;
+  static constexpr int kCoarsestSweeps = 8;
 
   LevelView<T> view0() const {
     return LevelView<T>{g_.nx, g_.ny, g_.nz, g_.c, ax0_, ay0_, az0_};
@@ -256,35 +260,130 @@ class Solver {
     }
   }
 
-  void inner_solve(double rel_tol, int max_it, int *iters, int *done) {
+  // ------------------------------------------------------------ graphs --
+  // The per-solve setup (e = 0, z = M r, d = z, dots) and a batch of kBatch
+  // CG iterations are captured once per solver and replayed: every kernel
+  // argument is fixed (pointers, level sizes, unit-scale coefficients; the
+  // inner tolerance lives in CGState), so one capture serves every solve.
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    int kernels = 0;  // kernel launches per replay
+    int gen = -1;     // profiling generation the capture was made under
+    GraphEvents ev;   // event pairs of profiled kernels (when profiling)
+  };
+
+  void init_body() {
     Launch L = ctx_->launch();
     CGState *st = (CGState *)st_;
-    V *r = (V *)rin_, *z = (V *)z_, *d = (V *)d_, *q = (V *)q_, *e = (V *)e_;
+    V *r = (V *)rin_, *z = (V *)z_, *d = (V *)d_, *e = (V *)e_;
+    ctx_->prof.capture_iter = 0;
     cudaMemsetAsync(e, 0, n_ * sizeof(V), L.s);
     if (mg_) {
       precondition(r, z, nullptr);
-      launch_cg_init<V>(L, n_, r, z, d, st, ctx_->rs, rel_tol);
+      launch_cg_init<V>(L, n_, r, z, d, st, ctx_->rs);
     } else {
-      launch_cg_init<V>(L, n_, r, r, d, st, ctx_->rs, rel_tol);
+      launch_cg_init<V>(L, n_, r, r, d, st, ctx_->rs);
     }
+  }
+
+  void iterations(int count) {
+    Launch L = ctx_->launch();
+    CGState *st = (CGState *)st_;
+    V *r = (V *)rin_, *z = (V *)z_, *d = (V *)d_, *q = (V *)q_, *e = (V *)e_;
     const LevelView<T> lv = view0();
-    int issued = 0;
-    CGState hs{};
-    while (issued < max_it) {
-      const int batch = std::min(kBatch, max_it - issued);
-      for (int b = 0; b < batch; ++b) {
-        launch_apply_dot<V, T>(L, lv, d, q, st, ctx_->rs);
-        launch_cg_xr<V>(L, n_, e, r, d, q, st, ctx_->rs, mg_);
-        if (mg_) {
-          precondition(r, z, st);
-          launch_cg_rz<V>(L, n_, r, z, st, ctx_->rs);
-          launch_cg_d<V>(L, n_, z, d, st);
-        } else {
-          launch_cg_d<V>(L, n_, r, d, st);
-        }
+    for (int b = 0; b < count; ++b) {
+      ctx_->prof.capture_iter = b;
+      launch_apply_dot<V, T>(L, lv, d, q, st, ctx_->rs);
+      launch_cg_xr<V>(L, n_, e, r, d, q, st, ctx_->rs, mg_);
+      if (mg_) {
+        precondition(r, z, st);
+        launch_cg_rz<V>(L, n_, r, z, st, ctx_->rs);
+        launch_cg_d<V>(L, n_, z, d, st);
+      } else {
+        launch_cg_d<V>(L, n_, r, d, st);
       }
-      issued += batch;
+    }
+  }
+
+  template <class F>
+  bool ensure_graph(Graph &G, F body) {
+    if (!graphs_ok_) return false;
+    if (G.exec && G.gen == ctx_->prof.gen) return true;
+    if (G.exec) {
+      cudaGraphExecDestroy(G.exec);
+      G.exec = nullptr;
+    }
+    G.ev.clear();
+    if (!cap_ && cudaStreamCreateWithFlags(&cap_, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      graphs_ok_ = false;
+      return false;
+    }
+    const int64_t before = ctx_->launches;
+    ctx_->capture = cap_;
+    if (ctx_->prof.kclass != -2) ctx_->prof.capture_ev = &G.ev;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap_, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      body();
+      e = cudaStreamEndCapture(cap_, &graph);
+    }
+    ctx_->capture = nullptr;
+    ctx_->prof.capture_ev = nullptr;
+    G.kernels = (int)(ctx_->launches - before);
+    ctx_->launches = before;  // counted at every replay instead
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&G.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      G.exec = nullptr;
+      graphs_ok_ = false;
+      return false;
+    }
+    G.gen = ctx_->prof.gen;
+    return true;
+  }
+
+  void replay(Graph &G) {
+    cudaGraphLaunch(G.exec, ctx_->stream);
+    ctx_->launches += G.kernels;
+  }
+
+  void inner_solve(double rel_tol, int max_it, int *iters, int *done) {
+    CGState *st = (CGState *)st_;
+    // the tolerance goes to device memory through a pinned slot that no
+    // earlier copy still reads (every solve synchronised the stream since)
+    double *slot = (double *)((char *)ctx_->pinned + 2048);
+    *slot = rel_tol;
+    cudaMemcpyAsync(&st->tol, slot, sizeof(double), cudaMemcpyHostToDevice, ctx_->stream);
+    const bool g_init = ensure_graph(init_g_, [&] { init_body(); });
+    if (g_init)
+      replay(init_g_);
+    else
+      init_body();
+    int issued = 0, seen = 0;
+    CGState hs{};
+    bool init_collected = !g_init;
+    while (issued < max_it) {
+      const bool full = max_it - issued >= kBatch;
+      const bool g_batch = full && ensure_graph(batch_g_, [&] { iterations(kBatch); });
+      if (g_batch)
+        replay(batch_g_);
+      else
+        iterations(full ? kBatch : max_it - issued);
+      issued += full ? kBatch : max_it - issued;
       ctx_->read_bytes(&hs, st, sizeof(CGState));
+      if (!init_collected) {
+        ctx_->prof.collect(init_g_.ev, 1);
+        init_collected = true;
+      }
+      if (g_batch) {
+        // iterations of this replay that ran to the end (the one that met
+        // the tolerance skipped its preconditioner)
+        const int ran = hs.iters - seen - (hs.done ? 1 : 0);
+        ctx_->prof.collect(batch_g_.ev, ran > 0 ? ran : 0);
+      }
+      seen = hs.iters;
       if (hs.done) break;
     }
     *iters = hs.iters;
@@ -301,6 +400,16 @@ class Solver {
   const T *ax0_ = nullptr, *ay0_ = nullptr, *az0_ = nullptr;
   void *r_ = nullptr, *rin_ = nullptr, *e_ = nullptr, *z_ = nullptr,
        *d_ = nullptr, *q_ = nullptr, *st_ = nullptr, *norm2_ = nullptr;
+  cudaStream_t cap_ = nullptr;
+  bool graphs_ok_ = true;
+  Graph init_g_, batch_g_;
+
+ public:
+  ~Solver() {
+    if (init_g_.exec) cudaGraphExecDestroy(init_g_.exec);
+    if (batch_g_.exec) cudaGraphExecDestroy(batch_g_.exec);
+    if (cap_) cudaStreamDestroy(cap_);
+  }
 };
 
 }  // namespace nf

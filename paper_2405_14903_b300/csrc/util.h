@@ -24,9 +24,20 @@ int cuda_fail(cudaError_t e, const char *what);
     if (_e != cudaSuccess) return ::nf::cuda_fail(_e, #x); \
   } while (0)
 
+// Event pairs recorded inside a captured graph (external event-record
+// nodes around the profiled kernels), tagged with the iteration of the
+// captured batch they belong to.
+struct GraphEvents {
+  std::vector<cudaEvent_t> ev;  // 2 per pair
+  std::vector<int> cls, iter;
+  void clear();
+  ~GraphEvents() { clear(); }
+};
+
 // CUDA-event timing of the launches of one kernel class (or all classes).
-// Event pairs come from a fixed pool; a full pool is drained (stream
-// synchronised, elapsed times accumulated) and reused.
+// Direct launches use event pairs from a fixed pool; a full pool is drained
+// (stream synchronised, elapsed times accumulated) and reused. Launches
+// inside graphs use the graph's own pairs, read after each replay.
 struct Prof {
   int kclass = -2;              // -2 off, -1 every class, else one NF_K_*
   std::vector<cudaEvent_t> ev;  // 2 per slot
@@ -34,8 +45,13 @@ struct Prof {
   size_t used = 0;
   int64_t launches[NF_K_COUNT] = {};
   double ms[NF_K_COUNT] = {};
+  GraphEvents *capture_ev = nullptr;  // set while a graph is being captured
+  int capture_iter = 0;               // iteration tag of captured launches
+  int gen = 0;                        // bumped by nf_profile
   void drain(cudaStream_t s);
   void reset();
+  // Add the pairs of a completed replay whose iteration tag is < iters.
+  void collect(const GraphEvents &ge, int iters);
   ~Prof();
 };
 
@@ -49,9 +65,11 @@ struct Ctx {
   void *pinned = nullptr;  // small pinned host buffer for status readback
   size_t bytes_in_use = 0;
   Prof prof;
+  cudaStream_t capture = nullptr;  // set while a graph is being captured
 
   Launch launch() {
-    return Launch{stream, &launches, prof.kclass == -2 ? nullptr : &prof};
+    return Launch{capture ? capture : stream, &launches,
+                  prof.kclass == -2 ? nullptr : &prof};
   }
   // Synchronous readback of a small device value (synchronises the stream).
   double read_double(const double *dptr);
