@@ -177,7 +177,8 @@ __device__ __forceinline__ bool stopped(const CGState *st) {
 // ------------------------------------------------------ outer residual -----
 template <class S, class T, class V>
 __global__ void k_residual_outer(LevelView<T> lv, const S *b, const S *x, S *r,
-                                 V *rin, RedScratch rs, double *norm2) {
+                                 V *rin, double scale, RedScratch rs,
+                                 double *norm2) {
   double v[1] = {0.0};
   const int64_t n = lv.ncell();
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
@@ -192,7 +193,7 @@ __global__ void k_residual_outer(LevelView<T> lv, const S *b, const S *x, S *r,
       rv = (double)b[c] - lv.c * (dg * (double)x[c] - nb);
     }
     r[c] = (S)rv;
-    if (rin) rin[c] = (V)rv;
+    if (rin) rin[c] = (V)(rv * scale);
     v[0] += rv * rv;
   }
   double tot[1];
@@ -200,10 +201,10 @@ __global__ void k_residual_outer(LevelView<T> lv, const S *b, const S *x, S *r,
 }
 
 template <class S, class V>
-__global__ void k_axpy_outer(int64_t n, S *x, const V *e) {
+__global__ void k_axpy_outer(int64_t n, S *x, const V *e, double inv) {
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
        c += (int64_t)gridDim.x * blockDim.x)
-    x[c] = (S)((double)x[c] + (double)e[c]);
+    x[c] = (S)((double)x[c] + inv * (double)e[c]);
 }
 
 // ------------------------------------------------------------------ CG -----
@@ -503,16 +504,16 @@ static inline unsigned gs_blocks(int64_t n) {
 
 template <class S, class T, class V>
 void launch_residual_outer(const Launch &L, const LevelView<T> &lv, const S *b,
-                           const S *x, S *r, V *rin, const RedScratch &rs,
-                           double *norm2) {
+                           const S *x, S *r, V *rin, double scale,
+                           const RedScratch &rs, double *norm2) {
   ProfScope _ps(L, NF_K_RESIDUAL64);
-  k_residual_outer<S, T, V><<<kRedBlocks, kBlock, 0, L.s>>>(lv, b, x, r, rin, rs, norm2);
+  k_residual_outer<S, T, V><<<kRedBlocks, kBlock, 0, L.s>>>(lv, b, x, r, rin, scale, rs, norm2);
   ++*L.counter;
 }
 template <class S, class V>
-void launch_axpy_outer(const Launch &L, int64_t n, S *x, const V *e) {
+void launch_axpy_outer(const Launch &L, int64_t n, S *x, const V *e, double inv) {
   ProfScope _ps(L, NF_K_AXPY64);
-  k_axpy_outer<S, V><<<gs_blocks(n), kBlock, 0, L.s>>>(n, x, e);
+  k_axpy_outer<S, V><<<gs_blocks(n), kBlock, 0, L.s>>>(n, x, e, inv);
   ++*L.counter;
 }
 template <class V>
@@ -645,11 +646,11 @@ template void launch_mg_coarsen<float, __nv_bfloat16>(const Launch &, const Leve
 template void launch_mg_coarsen<__nv_bfloat16, __nv_bfloat16>(const Launch &, const LevelView<__nv_bfloat16> &, int, int, int, __nv_bfloat16 *, __nv_bfloat16 *, __nv_bfloat16 *);
 template void launch_mg_coarsen<double, double>(const Launch &, const LevelView<double> &, int, int, int, double *, double *, double *);
 
-template void launch_residual_outer<double, float, float>(const Launch &, const LevelView<float> &, const double *, const double *, double *, float *, const RedScratch &, double *);
-template void launch_residual_outer<float, float, float>(const Launch &, const LevelView<float> &, const float *, const float *, float *, float *, const RedScratch &, double *);
-template void launch_residual_outer<double, double, double>(const Launch &, const LevelView<double> &, const double *, const double *, double *, double *, const RedScratch &, double *);
-template void launch_axpy_outer<double, float>(const Launch &, int64_t, double *, const float *);
-template void launch_axpy_outer<float, float>(const Launch &, int64_t, float *, const float *);
-template void launch_axpy_outer<double, double>(const Launch &, int64_t, double *, const double *);
+template void launch_residual_outer<double, float, float>(const Launch &, const LevelView<float> &, const double *, const double *, double *, float *, double, const RedScratch &, double *);
+template void launch_residual_outer<float, float, float>(const Launch &, const LevelView<float> &, const float *, const float *, float *, float *, double, const RedScratch &, double *);
+template void launch_residual_outer<double, double, double>(const Launch &, const LevelView<double> &, const double *, const double *, double *, double *, double, const RedScratch &, double *);
+template void launch_axpy_outer<double, float>(const Launch &, int64_t, double *, const float *, double);
+template void launch_axpy_outer<float, float>(const Launch &, int64_t, float *, const float *, double);
+template void launch_axpy_outer<double, double>(const Launch &, int64_t, double *, const double *, double);
 
 }  // namespace nf

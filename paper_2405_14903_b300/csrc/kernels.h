@@ -78,14 +78,16 @@ void launch_adj_face(const Launch &L, const GridDev &g, const SceneDev &s,
 
 // ----------------------------------------------------------- solver ops ---
 // r = b - A x in precision S (fine operator with fractions of type T);
-// also writes r converted to V into rin (may be null) and ||r||^2.
+// also writes scale * r converted to V into rin (may be null) and ||r||^2
+// (unscaled). scale is a power of two that brings rin to unit size, so that
+// the V-typed inner solve neither underflows nor overflows.
 template <class S, class T, class V>
 void launch_residual_outer(const Launch &L, const LevelView<T> &lv,
-                           const S *b, const S *x, S *r, V *rin,
+                           const S *b, const S *x, S *r, V *rin, double scale,
                            const RedScratch &rs, double *norm2);
-// x += e (V -> S)
+// x += inv * e (V -> S); inv undoes the scale of the inner system.
 template <class S, class V>
-void launch_axpy_outer(const Launch &L, int64_t n, S *x, const V *e);
+void launch_axpy_outer(const Launch &L, int64_t n, S *x, const V *e, double inv);
 
 // d = z, <r, z>, <r, r>; stop when <r, r> <= st->tol^2 <r0, r0>.
 template <class V>

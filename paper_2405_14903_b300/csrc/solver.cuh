@@ -120,7 +120,11 @@ class Solver {
     }
     const double tol = cfg_.tol;
     const bool mixed = sizeof(S) != sizeof(V);
-    double rn2 = residual(b, x);  // r = b - A 0
+    // the inner system is solved for scale * r, scale a power of two close
+    // to 1 / ||r||: tiny right-hand sides (an adjoint far from its loss)
+    // would otherwise underflow in the V-typed dots
+    double scale = unit_scale(std::sqrt(bnorm2));
+    double rn2 = residual(b, x, scale);  // r = b - A 0
     out.rel = std::sqrt(rn2 / bnorm2);
     int total = 0;
     for (int pass = 0; pass < kMaxOuter && out.rel > tol; ++pass) {
@@ -132,11 +136,17 @@ class Solver {
                            : 0.5 * tol / out.rel;
       inner = std::min(inner, 0.5);
       int it = 0, done = 0;
-      inner_solve(inner, cfg_.max_iters - total, &it, &done);
+      double rr_in = 0.0;
+      inner_solve(inner, cfg_.max_iters - total, &it, &done, &rr_in);
       total += it;
       out.outer += 1;
-      launch_axpy_outer<S, V>(L, n_, x, (const V *)e_);
-      rn2 = residual(b, x);
+      launch_axpy_outer<S, V>(L, n_, x, (const V *)e_, 1.0 / scale);
+      // next scale from the inner recurrence's final residual (unscaled),
+      // floored at the V rounding level of the current residual
+      const double rn = std::sqrt(rn2);
+      const double pred = std::max(std::sqrt(rr_in) / scale, 1e-7 * rn);
+      scale = unit_scale(pred);
+      rn2 = residual(b, x, scale);
       out.rel = std::sqrt(rn2 / bnorm2);
       if (done == 3 || !std::isfinite(rn2)) {
         out.status = NF_E_DIVERGED;
@@ -173,9 +183,15 @@ class Solver {
                          (const TA *)L.ay, (const TA *)L.az};
   }
 
-  double residual(const S *b, const S *x) {
+  // 2^-e with 2^e within a factor 2 of v (1 when v is 0 or not finite)
+  static double unit_scale(double v) {
+    if (!(v > 0.0) || !std::isfinite(v)) return 1.0;
+    return std::ldexp(1.0, -std::ilogb(v));
+  }
+
+  double residual(const S *b, const S *x, double scale) {
     Launch L = ctx_->launch();
-    launch_residual_outer<S, T, V>(L, view0(), b, x, (S *)r_, (V *)rin_,
+    launch_residual_outer<S, T, V>(L, view0(), b, x, (S *)r_, (V *)rin_, scale,
                                    ctx_->rs, (double *)norm2_);
     return ctx_->read_double((double *)norm2_);
   }
@@ -349,7 +365,8 @@ class Solver {
     ctx_->launches += G.kernels;
   }
 
-  void inner_solve(double rel_tol, int max_it, int *iters, int *done) {
+  void inner_solve(double rel_tol, int max_it, int *iters, int *done,
+                   double *rr) {
     CGState *st = (CGState *)st_;
     // the tolerance goes to device memory through a pinned slot that no
     // earlier copy still reads (every solve synchronised the stream since)
@@ -388,6 +405,7 @@ class Solver {
     }
     *iters = hs.iters;
     *done = hs.done;
+    *rr = hs.rr;
   }
 
   Ctx *ctx_;
