@@ -134,6 +134,15 @@ ALG_BYTES_PER_CELL = {
 }
 
 
+# DRAM bytes per cell of one launch (dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture, divided by the level's cells).
+# The smoother was captured at 256^3, where its working set exceeds L2; the
+# figure scales linearly with cells. None once the kernel has changed since.
+DRAM_BYTES_PER_CELL = {
+    "mg_smooth0": (265.0e6 + 55.6e6) / 256 ** 3,
+}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     torch.cuda.set_device(local_rank)
@@ -225,7 +234,9 @@ def run_ours(args, rank, world, local_rank):
     achieved = per_launch / (avg_ms / 1e3) / 1e9 if nl else None
     out["roofline"] = dict(bound="hbm", kernel=roof_class, achieved=achieved, peak=peak,
                            peak_source=src, unit="GB/s",
-                           frac=(achieved / peak) if achieved else None, traffic=None,
+                           frac=(achieved / peak) if achieved else None,
+                           traffic=(DRAM_BYTES_PER_CELL[roof_class] * ncell
+                                    if DRAM_BYTES_PER_CELL.get(roof_class) else None),
                            launches=nl, avg_us=1e3 * avg_ms, alg_bytes_per_launch=per_launch)
     tot = sum(v[1] for v in shares.values()) or 1.0
     out["kernel_shares"] = {k: round(v[1] / tot, 4) for k, v in
@@ -303,22 +314,27 @@ def run_plain(args, P, torch, dev):
 
 def cpu_baseline(args):
     """The FP64 oracle on a bounded sample: one forward + adjoint step of the
-    same chamber scene on a coarser grid, scaled to cell-steps/s."""
+    same chamber scene on a coarser grid, scaled to cell-steps/s. The oracle
+    is plain NumPy; BLAS is held to one thread so that `cores` is what ran."""
+    from threadpoolctl import threadpool_limits
+
     from oracle import Grid
     from oracle import step as S
     n = args.cpu_n
     cfg = chamber(n, 1, seed=0)
     g = Grid(cfg["grid"])
-    t0 = time.perf_counter()
-    U, tape = S.step(g, cfg["scene"], cfg["u0"], 0, 1e-6)
-    J, gU = S.outflow(g, U)
-    S.rollout_backward(g, cfg["scene"], [tape], gU, 1e-6)
-    dt = time.perf_counter() - t0
-    threads = int(os.environ.get("OMP_NUM_THREADS", "0")) or os.cpu_count()
-    return dict(value=n ** 3 / dt, unit=UNIT, cores=threads, kind="oracle",
+    with threadpool_limits(limits=1):
+        t0 = time.perf_counter()
+        U, tape = S.step(g, cfg["scene"], cfg["u0"], 0, 1e-6)
+        J, gU = S.outflow(g, U)
+        S.rollout_backward(g, cfg["scene"], [tape], gU, 1e-6)
+        dt = time.perf_counter() - t0
+    return dict(value=n ** 3 / dt, unit=UNIT, cores=1, host_cpus=os.cpu_count(),
+                kind="oracle",
                 sample=f"1 step (forward + adjoint) of the same chamber scene on {n}^3 "
-                       f"(FP64 NumPy, unpreconditioned CG to 1e-6), scaled per cell-step; "
-                       f"a coarser grid needs fewer CG iterations, so this flatters the oracle",
+                       f"(FP64 NumPy, unpreconditioned CG to 1e-6, one thread), scaled per "
+                       f"cell-step; a coarser grid needs fewer CG iterations, so this "
+                       f"flatters the oracle",
                 seconds=dt)
 
 

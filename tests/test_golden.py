@@ -1,0 +1,55 @@
+"""Stored oracle values (tests/golden/oracle_small.json).
+
+CPU: the oracle still produces them (guards its arithmetic against
+unintended change). GPU: the CUDA path matches them in every precision mode
+(FP64 to 1e-8, FP32 and MIXED to the 1e-4 gradient bar).
+"""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+from tests.golden.make_golden import CASES, compute
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+with open(os.path.join(HERE, "golden", "oracle_small.json")) as f:
+    GOLDEN = json.load(f)["cases"]
+
+
+def _rel(a, b):
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_oracle_reproduces_stored_values(name):
+    got = compute(name)
+    ref = GOLDEN[name]
+    assert got["steps"] == ref["steps"]
+    assert abs(got["loss"] - ref["loss"]) <= 1e-9 * abs(ref["loss"])
+    assert _rel(got["dJ_dtheta"], ref["dJ_dtheta"]) <= 1e-8
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,jtol,gtol", [("fp64", 1e-9, 1e-8), ("mixed", 1e-5, 1e-4),
+                                            ("fp32", 1e-5, 1e-4)])
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_cuda_path_matches_stored_values(nf, name, prec, jtol, gtol):
+    import torch
+    cfg = CASES[name]()
+    ref = GOLDEN[name]
+    ctx = nf.Context(prec, "mgpcg", tol={"fp64": 1e-12, "mixed": 1e-10, "fp32": 1e-6}[prec],
+                     max_iters=3000, checkpoint_every=2, cfl_max=cfg.get("cfl_max", 0.0))
+    ep = ctx.episode(cfg["grid"], cfg["scene"])
+    ep.set_velocity([torch.tensor(x, device="cuda", dtype=torch.float64) for x in cfg["u0"]],
+                    project=cfg["project_initial"])
+    st = ep.step(cfg["steps"])
+    J, gU = ep.loss(cfg["loss"], want_grad=True)
+    gth, _, _ = ep.backward(gU)
+    ep.close()
+    ctx.close()
+    assert st["steps"] + int(cfg["project_initial"]) == ref["steps"]
+    assert abs(J - ref["loss"]) <= jtol * abs(ref["loss"])
+    assert _rel(gth, ref["dJ_dtheta"]) <= gtol

@@ -150,3 +150,23 @@ def test_chamber_outflow_equals_geometric_volume_rate_and_its_gradient():
     g_geo = np.array([g.dx ** 2 * _active_boundary_flux(g, alpha, [dus[d][..., k] for d in range(3)])
                       for k in range(K)])
     np.testing.assert_allclose(g_adj, g_geo, rtol=1e-7, atol=1e-9 * np.abs(g_geo).max())
+
+
+def test_substepped_chamber_keeps_the_outflow_identity():
+    # CFL sub-stepping (Table 1: more steps than frames): the frame ends at
+    # t = frames * dt whatever the split, so the final outflow still equals
+    # the geometric volume rate at that time, and so does its gradient
+    cfg = I.config_chamber(16, steps=3, duct_half_cells=2, cfl_max=1.0)
+    J, g_adj, info = S.loss_and_grad(cfg, tol=1e-13)
+    assert len(info["tapes"]) > cfg["steps"], "no frame was split"
+    g = Grid(cfg["grid"])
+    t = cfg["steps"] * g.dt
+    assert abs(info["tapes"][-1]["t"] - t) <= 1e-15
+    alpha = rasterize.fractions(g, cfg["scene"], t)
+    us, dus = rasterize.face_solid_velocity(g, cfg["scene"], t, with_grad=True)
+    geo = g.dx ** 2 * _active_boundary_flux(g, alpha, us)
+    assert abs(J - geo) <= 1e-9 * abs(J)
+    K = len(cfg["scene"]["theta"])
+    g_geo = np.array([g.dx ** 2 * _active_boundary_flux(g, alpha, [dus[d][..., k] for d in range(3)])
+                      for k in range(K)])
+    np.testing.assert_allclose(g_adj, g_geo, rtol=1e-7, atol=1e-9 * np.abs(g_geo).max())
