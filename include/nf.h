@@ -262,6 +262,47 @@ int nf_profile(nf_ctx *ctx, int kclass);
    nf_profile (synchronises the stream). */
 int nf_profile_read(nf_ctx *ctx, int kclass, int64_t *launches, double *ms);
 
+/* ---------------------------------------------------------- no-alloc ---
+   nf_loss_noalloc: the loss of nf_loss (kinetic energy 1/2 sum u^2 dx^3, or
+   the net flux sum u_x dx^2 through the outlet patch) and optionally dJ/dU,
+   for a caller's face-velocity triple, with no context, no episode and no
+   allocation of any kind. The paper has no counterpart: this is a service
+   entry point of this library, not a step of the method.
+
+   Who needs it: callers that must not allocate device memory at this point,
+   e.g. a reward or loss evaluation inside an environment loop whose device
+   memory is held by another allocator (a framework's caching pool, or a
+   serving process admitted under a fixed HBM budget), or any loop where the
+   device-wide synchronisation of cudaMalloc/cudaFree would stall other work.
+
+   g       grid (nx, ny, nz >= 1, dx > 0; the outlet fields for the outflow
+           loss; dt and rho are ignored).
+   u       three DEVICE arrays of the current device, component d of shape
+           [nz + (d==2)][ny + (d==1)][nx + (d==0)], x fastest, dtype NF_F32
+           or NF_F64. Host pointers are rejected with NF_E_INVALID.
+   gU      NULL, or three device arrays of the same shapes and dtype that
+           receive dJ/dU.
+   J       host double that receives the loss.
+   stream  cudaStream_t to run on (NULL: the legacy default stream). The call
+           returns after synchronising this stream.
+
+   Scratch: a file-scope device array of NF_NOALLOC_SCRATCH_BYTES (8 KiB:
+   block partials, a ticket counter and the result of the deterministic
+   fixed-order reduction) used by every call on a device. Maximum size: each
+   face component may hold at most NF_NOALLOC_MAX_FACES entries (32-bit index
+   decode); larger grids are rejected with NF_E_INVALID before any device
+   work. The ticket is cleared (cudaMemsetAsync on `stream`) at every call.
+   The first call on each device looks up the array's device address
+   (cudaGetSymbolAddress with that device current, checked: NF_E_CUDA on
+   failure) and caches it; make that first call before any stream capture.
+   Calls that overlap in time on one device (other streams, other threads)
+   share the scratch and race: serialise them. Results equal nf_loss's for
+   the same velocity (same kernel, same summation order). */
+#define NF_NOALLOC_SCRATCH_BYTES 8192
+#define NF_NOALLOC_MAX_FACES 2147483647LL
+int nf_loss_noalloc(const nf_grid *g, int loss_kind, const void *const u[3],
+                    void *const gU[3], int dtype, double *J, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

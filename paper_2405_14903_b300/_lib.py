@@ -85,6 +85,8 @@ SIGNATURES = [
     ("nf_set_velocity", C.c_int, [_vp, _i64, PP, C.c_int, C.c_int, C.c_int, C.POINTER(StepStats)]),
     ("nf_step", C.c_int, [_vp, _i64, C.c_int, C.POINTER(StepStats)]),
     ("nf_loss", C.c_int, [_vp, _i64, C.c_int, C.POINTER(C.c_double), PP, C.c_int, C.c_int]),
+    ("nf_loss_noalloc", C.c_int, [C.POINTER(Grid), C.c_int, PP, PP, C.c_int,
+                                  C.POINTER(C.c_double), _vp]),
     ("nf_backward_step", C.c_int, [_vp, _i64, PP, PP, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(StepStats)]),
     ("nf_backward", C.c_int, [_vp, _i64, PP, PP, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(StepStats)]),
     ("nf_get_velocity", C.c_int, [_vp, _i64, PP, C.c_int, C.c_int]),

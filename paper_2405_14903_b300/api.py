@@ -110,6 +110,27 @@ def _ptrs(arrs):
     return L.P3(*[a.ctypes.data for a in nps]), code, L.NF_MEM_HOST, nps
 
 
+def loss_noalloc(kind, grid, u, gU=None, stream=None):
+    """``nf_loss_noalloc``: the loss of ``Episode.loss`` for the device face
+    triple ``u`` (CUDA tensors of one dtype) on ``grid`` (a grid
+    description), with no context or episode and nothing allocated, here or
+    in the library. ``gU``, if given, is the caller's triple (same shapes and
+    dtype) that receives dJ/dU. Runs on torch's current stream (or
+    ``stream``) and returns ``J``."""
+    arrs = list(u) + (list(gU) if gU is not None else [])
+    if not all(isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous() for t in arrs):
+        raise TypeError("u and gU must be contiguous CUDA tensors")
+    p, code, _, keep = _ptrs(u)
+    pg = _ptrs(gU)[0] if gU is not None else None
+    if stream is None:
+        stream = torch.cuda.current_stream(keep[0].device).cuda_stream or L.CUDA_STREAM_LEGACY
+    g = grid_struct(grid)
+    J = C.c_double()
+    _check(lib.nf_loss_noalloc(C.byref(g), L.LOSS[kind], p, pg, code, C.byref(J), stream),
+           C.c_void_p())
+    return J.value
+
+
 class Context:
     """An ``nf_ctx``: one device, one stream, one precision/solver setting."""
 
