@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--plain-rollout", type=int, default=10)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip FP64 comparison paths, e2e and the CPU baseline")
+    ap.add_argument("--inner-tol", type=float, default=1e-3,
+                    help="relative tolerance of each FP32 inner solve (MIXED refinement)")
+    ap.add_argument("--mg-smooth", type=int, default=2,
+                    help="red-black Gauss-Seidel sweeps before and after each coarse correction")
     ap.add_argument("--cpu-n", type=int, default=64,
                     help="grid of the bounded CPU oracle sample")
     return ap.parse_args()
@@ -124,23 +128,22 @@ def chamber(n, steps, seed):
 
 # Algorithmic bytes per cell of the kernels the roofline may name (FP32
 # fields, FP32 fractions on the finest level): what the operation must move.
-ALG_BYTES_PER_CELL = {
-    # red-black half sweep: x of the other colour (n/2), b (n/2), the six
-    # fractions of the updated cells = every face once (3n), x written (n/2)
-    "mg_smooth0": 4 * 0.5 + 4 * 0.5 + 3 * 4 + 4 * 0.5,
-    "apply_dot": 4 + 3 * 4 + 4,            # d, three fraction arrays, q
-    "cg_xr": 4 * 4 + 2 * 4,                # x, r, d, q read; x, r written
-    "residual64": 8 + 8 + 3 * 4 + 8 + 4,   # b, x (FP64), fractions, r64, r32
-}
+def alg_bytes_per_cell(kclass, nu):
+    if kclass == "mg_smooth0":
+        # red-black half sweep: x of the other colour (n/2), b (n/2), the six
+        # fractions of the updated cells = every face once (3n), x written (n/2)
+        return 4 * 0.5 + 4 * 0.5 + 3 * 4 + 4 * 0.5
+    return {
+        "apply_dot": 4 + 3 * 4 + 4,            # d, three fraction arrays, q
+        "cg_xr": 4 * 4 + 2 * 4,                # x, r, d, q read; x, r written
+        "residual64": 8 + 8 + 3 * 4 + 8 + 4,   # b, x (FP64), fractions, r64, r32
+    }.get(kclass)
 
 
 # DRAM bytes per cell of one launch (dram__bytes_read.sum +
-# dram__bytes_write.sum from one ncu capture, divided by the level's cells).
-# The smoother was captured at 256^3, where its working set exceeds L2; the
-# figure scales linearly with cells. None once the kernel has changed since.
-DRAM_BYTES_PER_CELL = {
-    "mg_smooth0": (265.0e6 + 55.6e6) / 256 ** 3,
-}
+# dram__bytes_write.sum from one ncu capture, divided by the level's cells),
+# for kernels unchanged since their capture; None otherwise.
+DRAM_BYTES_PER_CELL = {}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -158,7 +161,8 @@ def run_ours(args, rank, world, local_rank):
             dist.barrier()
 
     ctx = P.Context("mixed", "mgpcg", tol=1e-6, max_iters=1000, checkpoint_every=10,
-                    cfl_max=cfg["cfl_max"], device=local_rank)
+                    cfl_max=cfg["cfl_max"], inner_tol=args.inner_tol,
+                    mg_smooth=args.mg_smooth, device=local_rank)
     ep = ctx.episode(cfg["grid"], cfg["scene"])
     u0 = [torch.zeros(s, dtype=torch.float32, device=dev) for s in ep.face_shapes]
     stats = {}
@@ -185,7 +189,7 @@ def run_ours(args, rank, world, local_rank):
 
     # timed region; launches of the roofline kernel are bracketed by CUDA
     # events on the library's stream (torch's current stream)
-    roof_class = dominant if dominant in ALG_BYTES_PER_CELL else "mg_smooth0"
+    roof_class = dominant if alg_bytes_per_cell(dominant, args.mg_smooth) else "mg_smooth0"
     ctx.profile(roof_class)
     clocks = Clocks(local_rank) if rank == 0 else None
     launches0 = ctx.launches()
@@ -221,6 +225,7 @@ def run_ours(args, rank, world, local_rank):
                            cfl_max=cfg["cfl_max"], substeps_executed=int(stats["fwd"]["steps"]),
                            precision="FP32 MGPCG, BF16 coarse-level fractions, FP64 dots and "
                                      "FP64 iterative refinement to rel res 1e-6",
+                           inner_tol=args.inner_tol, mg_smooth=args.mg_smooth,
                            l2="inputs larger than L2 (episode state and tape > 1 GB)",
                            parallelism=f"replicas x{world}"),
                gpu_launches=int(launches), iterations=dict(fwd=stats["fwd"], bwd=stats["bwd"]),
@@ -229,7 +234,7 @@ def run_ours(args, rank, world, local_rank):
         return None
 
     peak, src = peaks()
-    per_launch = ALG_BYTES_PER_CELL[roof_class] * ncell
+    per_launch = alg_bytes_per_cell(roof_class, args.mg_smooth) * ncell
     avg_ms = kms / max(nl, 1)
     achieved = per_launch / (avg_ms / 1e3) / 1e9 if nl else None
     out["roofline"] = dict(bound="hbm", kernel=roof_class, achieved=achieved, peak=peak,

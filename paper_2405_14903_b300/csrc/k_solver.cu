@@ -6,6 +6,7 @@
 // fractions = mean of the four fine sub-faces, operator rediscretised with
 // c_l = dt / (rho dx_l)).
 #include "kernels.h"
+#include "util.h"
 
 namespace nf {
 
@@ -234,6 +235,32 @@ __global__ void k_cg_init(int64_t n, const V *r, const V *z, V *d, CGState *st,
     st->alpha = st->beta = st->dq = 0.0;
     st->done = (tot[1] == 0.0) ? 1 : (isfinite(tot[0]) && isfinite(tot[1]) ? 0 : 3);
     if (st->done == 0 && !(tot[0] > 0.0)) st->done = 2;
+  }
+}
+
+template <class V>
+__global__ void k_cg_continue(int64_t n, const V *r, const V *z, CGState *st,
+                              RedScratch rs) {
+  V p0 = V(0), p1 = V(0);
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const V rc = r[c];
+    p0 += rc * z[c];
+    p1 += rc * rc;
+  }
+  double v[2] = {(double)p0, (double)p1};
+  double tot[2];
+  if (grid_sum<2>(v, rs, tot) && threadIdx.x == 0) {
+    const double s = st->ratio, rz_old = st->rz * s * s;
+    st->rr = tot[1];
+    st->stop2 = st->tol * st->tol * tot[1];
+    st->iters = 0;
+    st->alpha = st->dq = 0.0;
+    st->done = (tot[1] == 0.0) ? 1 : (isfinite(tot[0]) && isfinite(tot[1]) ? 0 : 3);
+    if (st->done == 0 && !(tot[0] > 0.0 && rz_old > 0.0)) st->done = 2;
+    // d = z + (s beta) d brings the old direction to the new scale
+    st->beta = st->done == 0 ? tot[0] / rz_old * s : 0.0;
+    st->rz = tot[0];
   }
 }
 
@@ -496,6 +523,142 @@ k_mg_coarse_chain(CoarseChain<V, TA> ch, const CGState *st) {
   }
 }
 
+// Shared-memory version of the chain: every array of the chain levels (x, b,
+// r and the fractions, the latter converted to FA) lives in shared memory for
+// the whole sub-V-cycle; global memory is read once (fractions, b of the
+// first chain level) and written once (x of the first chain level).
+template <class TA>
+struct ChainFA {
+  using type = float;
+};
+template <>
+struct ChainFA<double> {
+  using type = double;
+};
+
+// Byte offsets of x, b, r, ax, ay, az of every chain level; returns the total.
+template <class V, class TA>
+__host__ __device__ inline size_t chain_layout(const CoarseChain<V, TA> &ch,
+                                               size_t off[kMaxLevels][6]) {
+  using FA = typename ChainFA<TA>::type;
+  size_t o = 0;
+  auto take = [&o](size_t bytes) {
+    const size_t at = o;
+    o += (bytes + 15) & ~(size_t)15;
+    return at;
+  };
+  for (int l = ch.first; l < ch.nlev; ++l) {
+    const LevelView<TA> &v = ch.lv[l];
+    const size_t nc = (size_t)v.nx * v.ny * v.nz;
+    off[l][0] = take(nc * sizeof(V));
+    off[l][1] = take(nc * sizeof(V));
+    off[l][2] = take(l + 1 < ch.nlev ? nc * sizeof(V) : 0);
+    off[l][3] = take((size_t)(v.nx + 1) * v.ny * v.nz * sizeof(FA));
+    off[l][4] = take((size_t)v.nx * (v.ny + 1) * v.nz * sizeof(FA));
+    off[l][5] = take((size_t)v.nx * v.ny * (v.nz + 1) * sizeof(FA));
+  }
+  return o;
+}
+
+template <class FA, class TA>
+__device__ void blk_load(FA *dst, const TA *src, int n) {
+  for (int t = threadIdx.x; t < n; t += blockDim.x) dst[t] = (FA)ld(src + t);
+}
+
+template <class V, class TA>
+__global__ void __launch_bounds__(1024, 1)
+k_mg_chain_smem(CoarseChain<V, TA> ch, const CGState *st) {
+  if (stopped(st)) return;
+  using FA = typename ChainFA<TA>::type;
+  extern __shared__ __align__(16) unsigned char smem[];
+  size_t off[kMaxLevels][6];
+  chain_layout(ch, off);
+  const int first = ch.first, last = ch.nlev - 1;
+  auto view = [&](int l) {
+    const LevelView<TA> &g = ch.lv[l];
+    return LevelView<FA>{g.nx, g.ny, g.nz, g.c, (const FA *)(smem + off[l][3]),
+                         (const FA *)(smem + off[l][4]),
+                         (const FA *)(smem + off[l][5])};
+  };
+  auto X = [&](int l) { return (V *)(smem + off[l][0]); };
+  auto B = [&](int l) { return (V *)(smem + off[l][1]); };
+  auto R = [&](int l) { return (V *)(smem + off[l][2]); };
+  for (int l = first; l <= last; ++l) {
+    const LevelView<TA> &g = ch.lv[l];
+    blk_load((FA *)(smem + off[l][3]), g.ax, (g.nx + 1) * g.ny * g.nz);
+    blk_load((FA *)(smem + off[l][4]), g.ay, g.nx * (g.ny + 1) * g.nz);
+    blk_load((FA *)(smem + off[l][5]), g.az, g.nx * g.ny * (g.nz + 1));
+  }
+  {
+    const int n = (int)ch.lv[first].ncell();
+    for (int t = threadIdx.x; t < n; t += blockDim.x) B(first)[t] = ch.b[first][t];
+  }
+  __syncthreads();
+  for (int l = first; l <= last; ++l) {
+    const LevelView<FA> lv = view(l);
+    const int n = (int)lv.ncell();
+    V *x = X(l);
+    const V *b = B(l);
+    for (int t = threadIdx.x; t < n; t += blockDim.x) x[t] = V(0);
+    __syncthreads();
+    if (l == last) break;
+    for (int s = 0; s < ch.smooth; ++s) {
+      blk_smooth(lv, x, b, 0);
+      blk_smooth(lv, x, b, 1);
+    }
+    V *r = R(l);
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      const int i = t % lv.nx, q = t / lv.nx;
+      const int j = q % lv.ny, k = q / lv.ny;
+      r[t] = residual_cell<V, FA>(lv, x, b, i, j, k, t);
+    }
+    __syncthreads();
+    const LevelView<TA> &cv = ch.lv[l + 1];
+    const int nc = (int)cv.ncell();
+    V *bc = B(l + 1);
+    for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+      const int I = t % cv.nx, q = t / cv.nx;
+      const int J = q % cv.ny, K = q / cv.ny;
+      bc[t] = restrict_cell<V>(lv.nx, lv.ny, lv.nz, cv.nx, cv.ny, cv.nz, r, I, J, K);
+    }
+    __syncthreads();
+  }
+  {
+    const LevelView<FA> lv = view(last);
+    for (int s = 0; s < ch.coarsest_sweeps; ++s) {
+      blk_smooth(lv, X(last), B(last), 0);
+      blk_smooth(lv, X(last), B(last), 1);
+    }
+    for (int s = 0; s < ch.coarsest_sweeps; ++s) {
+      blk_smooth(lv, X(last), B(last), 1);
+      blk_smooth(lv, X(last), B(last), 0);
+    }
+  }
+  for (int l = last - 1; l >= first; --l) {
+    const LevelView<FA> lv = view(l);
+    const LevelView<TA> &cv = ch.lv[l + 1];
+    const int n = (int)lv.ncell();
+    V *x = X(l);
+    const V *xc = X(l + 1);
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      const int i = t % lv.nx, q = t / lv.nx;
+      const int j = q % lv.ny, k = q / lv.ny;
+      if (six<float>(lv, i, j, k).diag() > 0.f)
+        x[t] += prolong_cell<V>(cv.nx, cv.ny, cv.nz, xc, i, j, k);
+    }
+    __syncthreads();
+    for (int s = 0; s < ch.smooth; ++s) {
+      blk_smooth(lv, x, B(l), 1);
+      blk_smooth(lv, x, B(l), 0);
+    }
+  }
+  {
+    const int n = (int)ch.lv[first].ncell();
+    const V *x = X(first);
+    for (int t = threadIdx.x; t < n; t += blockDim.x) ch.x[first][t] = x[t];
+  }
+}
+
 // ------------------------------------------------------------ launchers ---
 static inline unsigned gs_blocks(int64_t n) {
   const unsigned b = nblocks(n);
@@ -521,6 +684,13 @@ void launch_cg_init(const Launch &L, int64_t n, const V *r, const V *z, V *d,
                     CGState *st, const RedScratch &rs) {
   ProfScope _ps(L, NF_K_CG_INIT);
   k_cg_init<V><<<kRedBlocks, kBlock, 0, L.s>>>(n, r, z, d, st, rs);
+  ++*L.counter;
+}
+template <class V>
+void launch_cg_continue(const Launch &L, int64_t n, const V *r, const V *z,
+                        CGState *st, const RedScratch &rs) {
+  ProfScope _ps(L, NF_K_CG_INIT);
+  k_cg_continue<V><<<kRedBlocks, kBlock, 0, L.s>>>(n, r, z, st, rs);
   ++*L.counter;
 }
 template <class V, class TA>
@@ -595,10 +765,24 @@ void launch_mg_prolong(const Launch &L, const LevelView<TF> &fine,
   ++*L.counter;
 }
 template <class V, class TA>
+size_t mg_chain_smem_bytes(const CoarseChain<V, TA> &ch) {
+  size_t off[kMaxLevels][6];
+  return chain_layout(ch, off);
+}
+template <class V, class TA>
+int prepare_mg_chain(int smem_limit) {
+  const cudaError_t e = cudaFuncSetAttribute(
+      k_mg_chain_smem<V, TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit);
+  return e == cudaSuccess ? NF_OK : cuda_fail(e, "cudaFuncSetAttribute(chain)");
+}
+template <class V, class TA>
 void launch_mg_coarse_chain(const Launch &L, const CoarseChain<V, TA> &ch,
                             const CGState *st) {
   ProfScope _ps(L, NF_K_MG_CHAIN);
-  k_mg_coarse_chain<V, TA><<<1, 1024, 0, L.s>>>(ch, st);
+  if (ch.smem_bytes > 0)
+    k_mg_chain_smem<V, TA><<<1, 1024, ch.smem_bytes, L.s>>>(ch, st);
+  else
+    k_mg_coarse_chain<V, TA><<<1, 1024, 0, L.s>>>(ch, st);
   ++*L.counter;
 }
 
@@ -606,6 +790,9 @@ void launch_mg_coarse_chain(const Launch &L, const CoarseChain<V, TA> &ch,
   template void launch_cg_init<V>(const Launch &, int64_t, const V *,        \
                                   const V *, V *, CGState *,                  \
                                   const RedScratch &);                        \
+  template void launch_cg_continue<V>(const Launch &, int64_t, const V *,    \
+                                      const V *, CGState *,                   \
+                                      const RedScratch &);                    \
   template void launch_cg_xr<V>(const Launch &, int64_t, V *, V *, const V *,\
                                 const V *, CGState *, const RedScratch &,     \
                                 bool);                                        \
@@ -629,7 +816,9 @@ void launch_mg_coarse_chain(const Launch &L, const CoarseChain<V, TA> &ch,
                                           V *, const CGState *);              \
   template void launch_mg_coarse_chain<V, TA>(const Launch &,                \
                                               const CoarseChain<V, TA> &,     \
-                                              const CGState *);
+                                              const CGState *);               \
+  template size_t mg_chain_smem_bytes<V, TA>(const CoarseChain<V, TA> &);    \
+  template int prepare_mg_chain<V, TA>(int);
 NF_INST_V(float)
 NF_INST_V(double)
 NF_INST_VA(float, float)

@@ -23,6 +23,7 @@ struct FieldsMut {
 // iterations in batches and poll rarely without changing the result.
 struct CGState {
   double tol;    // relative tolerance of the inner solve (set by the host)
+  double ratio;  // scale of this pass's r over the previous pass's (host)
   double rz;     // <r, z>
   double dq;     // <d, A d>
   double rr;     // <r, r>
@@ -93,6 +94,12 @@ void launch_axpy_outer(const Launch &L, int64_t n, S *x, const V *e, double inv)
 template <class V>
 void launch_cg_init(const Launch &L, int64_t n, const V *r, const V *z, V *d,
                     CGState *st, const RedScratch &rs);
+// Continue the previous pass's search direction after its residual was
+// replaced by the true one (reliable update): with s = st->ratio,
+// beta = <r, z> / (s^2 <r, z>_old) and, through launch_cg_d, d = z + s beta d.
+template <class V>
+void launch_cg_continue(const Launch &L, int64_t n, const V *r, const V *z,
+                        CGState *st, const RedScratch &rs);
 template <class V, class TA>
 void launch_apply_dot(const Launch &L, const LevelView<TA> &lv, const V *d,
                       V *q, CGState *st, const RedScratch &rs);
@@ -137,9 +144,17 @@ struct CoarseChain {
   V *r[kMaxLevels];
   int smooth;         // sweeps per level
   int coarsest_sweeps;
+  int smem_bytes;     // > 0: run the chain in that much dynamic shared memory
 };
 template <class V, class TA>
 void launch_mg_coarse_chain(const Launch &L, const CoarseChain<V, TA> &ch,
                             const CGState *st);
+// Shared memory the chain needs with every level resident (bytes).
+template <class V, class TA>
+size_t mg_chain_smem_bytes(const CoarseChain<V, TA> &ch);
+// Allow the shared-memory chain kernel up to smem_limit bytes (call once per
+// device, outside stream capture).
+template <class V, class TA>
+int prepare_mg_chain(int smem_limit);
 
 }  // namespace nf

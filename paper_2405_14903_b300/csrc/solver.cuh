@@ -5,7 +5,10 @@
 // preconditioned) in precision V on A e = r, then P += e. With S = V the
 // inner solve targets the final tolerance and the outer loop only confirms
 // it; with S = double, V = float (MIXED) each inner solve reduces the
-// residual by `inner_tol`.
+// residual by `inner_tol`. A pass that follows a converged pass keeps its
+// search direction (reliable update: the recurrence residual is replaced by
+// the true FP64 one and CG continues) while the two residuals agree, so the
+// Krylov space is not lost at every refinement.
 //
 // Iteration kernels stop themselves once the device-side CGState says the
 // solve is done, so iterations are enqueued in batches and the host polls
@@ -13,6 +16,7 @@
 #pragma once
 
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -85,6 +89,19 @@ class Solver {
         if ((int64_t)L.nx * L.ny * L.nz > kChainCells) break;
         --first_chain_;
       }
+      // run the chain from shared memory when all of its levels fit
+      const int nl = (int)levels_.size();
+      if (nl > 1) {
+        int dev = 0, limit = 0;
+        CKC(cudaGetDevice(&dev));
+        CKC(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        const size_t need = mg_chain_smem_bytes(chain(std::min(std::max(1, first_chain_), nl - 1)));
+        if (need <= (size_t)limit) {
+          const int rc = prepare_mg_chain<V, TA>(limit);
+          if (rc != NF_OK) return rc;
+          chain_smem_ = (int)need;
+        }
+      }
     }
     return NF_OK;
   }
@@ -127,6 +144,8 @@ class Solver {
     double rn2 = residual(b, x, scale);  // r = b - A 0
     out.rel = std::sqrt(rn2 / bnorm2);
     int total = 0;
+    double prev_scale = scale;
+    bool can_cont = false;
     for (int pass = 0; pass < kMaxOuter && out.rel > tol; ++pass) {
       if (!std::isfinite(rn2)) {
         out.status = NF_E_DIVERGED;
@@ -137,7 +156,12 @@ class Solver {
       inner = std::min(inner, 0.5);
       int it = 0, done = 0;
       double rr_in = 0.0;
-      inner_solve(inner, cfg_.max_iters - total, &it, &done, &rr_in);
+      const bool cont = pass > 0 && can_cont;
+      inner_solve(inner, cfg_.max_iters - total, &it, &done, &rr_in, cont,
+                  scale / prev_scale);
+      if (cont && done == 2 && it == 0)  // no usable direction: start afresh
+        inner_solve(inner, cfg_.max_iters - total, &it, &done, &rr_in, false, 1.0);
+      prev_scale = scale;
       total += it;
       out.outer += 1;
       launch_axpy_outer<S, V>(L, n_, x, (const V *)e_, 1.0 / scale);
@@ -148,6 +172,10 @@ class Solver {
       scale = unit_scale(pred);
       rn2 = residual(b, x, scale);
       out.rel = std::sqrt(rn2 / bnorm2);
+      // the next pass may keep the search direction only while the
+      // recurrence residual still tracks the true one (it drifts below it
+      // once V rounding stalls the true residual)
+      can_cont = done == 1 && std::sqrt(rn2) <= 2.0 * std::sqrt(rr_in) / prev_scale;
       if (done == 3 || !std::isfinite(rn2)) {
         out.status = NF_E_DIVERGED;
         break;
@@ -216,6 +244,7 @@ class Solver {
     }
     ch.smooth = std::max(1, cfg_.mg_smooth);
     ch.coarsest_sweeps = kCoarsestSweeps;
+    ch.smem_bytes = chain_smem_;
     return ch;
   }
 
@@ -302,6 +331,25 @@ class Solver {
     }
   }
 
+  // Continuation of a converged pass after the true residual replaced the
+  // recurrence one: e = 0, z = M r, beta from the rescaled old <r, z>,
+  // d = z + beta d.
+  void cont_body() {
+    Launch L = ctx_->launch();
+    CGState *st = (CGState *)st_;
+    V *r = (V *)rin_, *z = (V *)z_, *d = (V *)d_, *e = (V *)e_;
+    ctx_->prof.capture_iter = 0;
+    cudaMemsetAsync(e, 0, n_ * sizeof(V), L.s);
+    if (mg_) {
+      precondition(r, z, nullptr);
+      launch_cg_continue<V>(L, n_, r, z, st, ctx_->rs);
+      launch_cg_d<V>(L, n_, z, d, st);
+    } else {
+      launch_cg_continue<V>(L, n_, r, r, st, ctx_->rs);
+      launch_cg_d<V>(L, n_, r, d, st);
+    }
+  }
+
   void iterations(int count) {
     Launch L = ctx_->launch();
     CGState *st = (CGState *)st_;
@@ -366,16 +414,23 @@ class Solver {
   }
 
   void inner_solve(double rel_tol, int max_it, int *iters, int *done,
-                   double *rr) {
+                   double *rr, bool cont, double ratio) {
     CGState *st = (CGState *)st_;
-    // the tolerance goes to device memory through a pinned slot that no
-    // earlier copy still reads (every solve synchronised the stream since)
+    // tolerance and scale ratio go to device memory through a pinned slot
+    // that no earlier copy still reads (every pass synchronised the stream)
     double *slot = (double *)((char *)ctx_->pinned + 2048);
-    *slot = rel_tol;
-    cudaMemcpyAsync(&st->tol, slot, sizeof(double), cudaMemcpyHostToDevice, ctx_->stream);
-    const bool g_init = ensure_graph(init_g_, [&] { init_body(); });
+    slot[0] = rel_tol;
+    slot[1] = ratio;
+    static_assert(offsetof(CGState, ratio) == offsetof(CGState, tol) + sizeof(double),
+                  "tol and ratio are copied together");
+    cudaMemcpyAsync(&st->tol, slot, 2 * sizeof(double), cudaMemcpyHostToDevice, ctx_->stream);
+    Graph &G0 = cont ? cont_g_ : init_g_;
+    const bool g_init = cont ? ensure_graph(cont_g_, [&] { cont_body(); })
+                             : ensure_graph(init_g_, [&] { init_body(); });
     if (g_init)
-      replay(init_g_);
+      replay(G0);
+    else if (cont)
+      cont_body();
     else
       init_body();
     int issued = 0, seen = 0;
@@ -391,7 +446,7 @@ class Solver {
       issued += full ? kBatch : max_it - issued;
       ctx_->read_bytes(&hs, st, sizeof(CGState));
       if (!init_collected) {
-        ctx_->prof.collect(init_g_.ev, 1);
+        ctx_->prof.collect(G0.ev, 1);
         init_collected = true;
       }
       if (g_batch) {
@@ -414,17 +469,19 @@ class Solver {
   int64_t n_ = 0;
   bool mg_ = false;
   int first_chain_ = 0;
+  int chain_smem_ = 0;  // dynamic shared memory of the chain kernel (0: global)
   std::vector<Level> levels_;
   const T *ax0_ = nullptr, *ay0_ = nullptr, *az0_ = nullptr;
   void *r_ = nullptr, *rin_ = nullptr, *e_ = nullptr, *z_ = nullptr,
        *d_ = nullptr, *q_ = nullptr, *st_ = nullptr, *norm2_ = nullptr;
   cudaStream_t cap_ = nullptr;
   bool graphs_ok_ = true;
-  Graph init_g_, batch_g_;
+  Graph init_g_, cont_g_, batch_g_;
 
  public:
   ~Solver() {
     if (init_g_.exec) cudaGraphExecDestroy(init_g_.exec);
+    if (cont_g_.exec) cudaGraphExecDestroy(cont_g_.exec);
     if (batch_g_.exec) cudaGraphExecDestroy(batch_g_.exec);
     if (cap_) cudaStreamDestroy(cap_);
   }
