@@ -58,6 +58,17 @@ def parse():
                     help="relative tolerance of each FP32 inner solve (MIXED refinement)")
     ap.add_argument("--mg-smooth", type=int, default=2,
                     help="red-black Gauss-Seidel sweeps before and after each coarse correction")
+    ap.add_argument("--coarsest-sweeps", type=int, default=8,
+                    help="symmetric sweep pairs on the coarsest multigrid level")
+    ap.add_argument("--band-sweeps", type=int, default=0,
+                    help="extra sweeps on the finest level's boundary band")
+    ap.add_argument("--mg-transfer", default="constant", choices=["trilinear", "constant"],
+                    help="multigrid prolongation and restriction")
+    ap.add_argument("--coarse-weight", type=float, default=1.8,
+                    help="scale of the coarse-grid correction")
+    ap.add_argument("--mg-coarsest", type=int, default=4,
+                    help="stop coarsening at this many cells per edge")
+    ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-n", type=int, default=64,
                     help="grid of the bounded CPU oracle sample")
     return ap.parse_args()
@@ -162,7 +173,10 @@ def run_ours(args, rank, world, local_rank):
 
     ctx = P.Context("mixed", "mgpcg", tol=1e-6, max_iters=1000, checkpoint_every=10,
                     cfl_max=cfg["cfl_max"], inner_tol=args.inner_tol,
-                    mg_smooth=args.mg_smooth, device=local_rank)
+                    mg_smooth=args.mg_smooth, mg_coarsest_sweeps=args.coarsest_sweeps,
+                    mg_coarsest=args.mg_coarsest, mg_band_sweeps=args.band_sweeps,
+                    mg_transfer=args.mg_transfer, mg_coarse_weight=args.coarse_weight,
+                    device=local_rank)
     ep = ctx.episode(cfg["grid"], cfg["scene"])
     u0 = [torch.zeros(s, dtype=torch.float32, device=dev) for s in ep.face_shapes]
     stats = {}
@@ -226,6 +240,9 @@ def run_ours(args, rank, world, local_rank):
                            precision="FP32 MGPCG, BF16 coarse-level fractions, FP64 dots and "
                                      "FP64 iterative refinement to rel res 1e-6",
                            inner_tol=args.inner_tol, mg_smooth=args.mg_smooth,
+                           mg_coarsest=args.mg_coarsest, coarsest_sweeps=args.coarsest_sweeps,
+                           band_sweeps=args.band_sweeps, mg_transfer=args.mg_transfer,
+                           coarse_weight=args.coarse_weight,
                            l2="inputs larger than L2 (episode state and tape > 1 GB)",
                            parallelism=f"replicas x{world}"),
                gpu_launches=int(launches), iterations=dict(fwd=stats["fwd"], bwd=stats["bwd"]),
@@ -317,23 +334,33 @@ def run_plain(args, P, torch, dev):
     return res
 
 
-def cpu_baseline(args):
-    """The FP64 oracle on a bounded sample: one forward + adjoint step of the
-    same chamber scene on a coarser grid, scaled to cell-steps/s. The oracle
-    is plain NumPy; BLAS is held to one thread so that `cores` is what ran."""
-    from threadpoolctl import threadpool_limits
-
+def _cpu_sample(n):
+    """One forward + adjoint step of the chamber scene on n^3 by the oracle."""
     from oracle import Grid
     from oracle import step as S
-    n = args.cpu_n
     cfg = chamber(n, 1, seed=0)
     g = Grid(cfg["grid"])
-    with threadpool_limits(limits=1):
-        t0 = time.perf_counter()
-        U, tape = S.step(g, cfg["scene"], cfg["u0"], 0, 1e-6)
-        J, gU = S.outflow(g, U)
-        S.rollout_backward(g, cfg["scene"], [tape], gU, 1e-6)
-        dt = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    U, tape = S.step(g, cfg["scene"], cfg["u0"], 0, 1e-6)
+    J, gU = S.outflow(g, U)
+    S.rollout_backward(g, cfg["scene"], [tape], gU, 1e-6)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(args):
+    """The FP64 oracle on a bounded sample: one forward + adjoint step of the
+    same chamber scene on a coarser grid, scaled to cell-steps/s. It runs in
+    a child interpreter with BLAS and OpenMP held to one thread, so `cores`
+    is what ran."""
+    n = args.cpu_n
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
+               MKL_NUM_THREADS="1", NUMEXPR_NUM_THREADS="1")
+    res = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample",
+                          "--cpu-n", str(n)], env=env, capture_output=True, text=True,
+                         timeout=1800)
+    if res.returncode != 0:
+        raise RuntimeError(f"CPU oracle sample failed: {res.stderr[-2000:]}")
+    dt = float(res.stdout.strip().splitlines()[-1])
     return dict(value=n ** 3 / dt, unit=UNIT, cores=1, host_cpus=os.cpu_count(),
                 kind="oracle",
                 sample=f"1 step (forward + adjoint) of the same chamber scene on {n}^3 "
@@ -365,6 +392,9 @@ def run_reference(args, rank):
 
 def main():
     args = parse()
+    if args.cpu_sample:
+        print(_cpu_sample(args.cpu_n))
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

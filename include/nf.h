@@ -97,6 +97,20 @@ typedef struct nf_config {
                              advances frames of dt, each split into
                              m = ceil(max|U| dt / (dx cfl_max)) equal substeps
                              (velocity at the frame start)                   */
+  int mg_coarsest_sweeps; /* symmetric red-black sweep pairs on the coarsest
+                             multigrid level (0: the default, 8)             */
+  int mg_band_sweeps;     /* extra red-black sweeps on the finest level's
+                             boundary band (cells with a cut face and their
+                             neighbours) before pre- and after post-smoothing */
+  int mg_transfer;        /* 0: trilinear prolongation, restriction P^T / 4;
+                             1: piecewise-constant prolongation, restriction
+                             by the mean of the eight children (the coarse
+                             operators are then Galerkin)                    */
+  double mg_coarse_weight; /* scale w of every coarse-grid correction, in
+                             (0, 2) (0: 1); applied as sqrt(w) on restriction
+                             and prolongation so the V-cycle stays symmetric.
+                             w near 2 offsets the weak piecewise-constant
+                             coarse space (over-correction)                 */
 } nf_config;
 
 typedef struct nf_grid {
@@ -133,7 +147,9 @@ typedef struct nf_step_stats {
 
 /* Fill *cfg with defaults: device 0, own stream, MIXED, MGPCG, tol 1e-6,
    max_iters 500, inner_tol 1e-3, mg_smooth 2, mg_coarsest 4, RK2,
-   checkpoint_every 10, no budget, cfl_max 0 (no sub-stepping). */
+   checkpoint_every 10, no budget, cfl_max 0 (no sub-stepping),
+   mg_coarsest_sweeps 8, mg_band_sweeps 0, mg_transfer 1 (constant),
+   mg_coarse_weight 1.8. */
 int nf_config_default(nf_config *cfg);
 
 /* Create a context on cfg->device. *out receives the handle. */

@@ -37,7 +37,9 @@ class Config(C.Structure):
                 ("inner_tol", C.c_double), ("mg_smooth", C.c_int),
                 ("mg_coarsest", C.c_int), ("advect_order", C.c_int),
                 ("checkpoint_every", C.c_int), ("hbm_budget", C.c_size_t),
-                ("cfl_max", C.c_double)]
+                ("cfl_max", C.c_double), ("mg_coarsest_sweeps", C.c_int),
+                ("mg_band_sweeps", C.c_int), ("mg_transfer", C.c_int),
+                ("mg_coarse_weight", C.c_double)]
 
 
 class Grid(C.Structure):

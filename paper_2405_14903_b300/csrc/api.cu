@@ -197,6 +197,10 @@ int nf_config_default(nf_config *cfg) {
   cfg->checkpoint_every = 10;
   cfg->hbm_budget = 0;
   cfg->cfl_max = 0.0;
+  cfg->mg_coarsest_sweeps = 8;
+  cfg->mg_band_sweeps = 0;
+  cfg->mg_transfer = 1;
+  cfg->mg_coarse_weight = 1.8;
   return NF_OK;
 }
 
@@ -226,7 +230,10 @@ int nf_create(nf_ctx **out, const nf_config *cfg) {
       (cfg->solver != NF_SOLVER_CG && cfg->solver != NF_SOLVER_MGPCG) ||
       !(cfg->tol > 0) || cfg->max_iters <= 0 ||
       (cfg->advect_order != 1 && cfg->advect_order != 2) ||
-      cfg->checkpoint_every <= 0 || cfg->mg_smooth < 0 || !(cfg->cfl_max >= 0.0)) {
+      cfg->checkpoint_every <= 0 || cfg->mg_smooth < 0 || !(cfg->cfl_max >= 0.0) ||
+      cfg->mg_coarsest_sweeps < 0 || cfg->mg_band_sweeps < 0 ||
+      (cfg->mg_transfer != 0 && cfg->mg_transfer != 1) ||
+      !(cfg->mg_coarse_weight >= 0.0 && cfg->mg_coarse_weight < 2.0)) {
     set_error("nf_create: invalid configuration");
     return NF_E_INVALID;
   }

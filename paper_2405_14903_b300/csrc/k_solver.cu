@@ -116,28 +116,56 @@ __device__ __forceinline__ void rweights(int I, int n, float w[4]) {
   }
 }
 
+// Transfer modes between levels: kTransferTrilinear (P trilinear, clamped
+// at the box; R = P^T / 4) or kTransferConstant (P copies the parent, R is
+// the mean of the eight children: with that pair the coarse operator built
+// from the mean sub-face fractions and c / 2 is exactly the Galerkin
+// operator R A P, so the coarse correction is an A-orthogonal projection).
+constexpr int kTransferTrilinear = 0, kTransferConstant = 1;
+
 template <class V>
 __device__ __forceinline__ V restrict_cell(int fnx, int fny, int fnz, int cnx,
                                            int cny, int cnz, const V *rf, int I,
-                                           int J, int K) {
+                                           int J, int K, int mode) {
+  if (mode == kTransferConstant) {
+    V acc = V(0);
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const V *row = rf + ((int64_t)(2 * K + c) * fny + (2 * J + b)) * fnx + 2 * I;
+        acc += row[0];
+        acc += row[1];
+      }
+    return V(0.125) * acc;
+  }
+  // fine offsets 2I-1 .. 2I+2 per axis; an offset outside the fine grid has
+  // weight 0 and reads a clamped (valid) index, so all 64 loads are
+  // unconditional and can be issued together
   float wx[4], wy[4], wz[4];
   rweights(I, cnx, wx);
   rweights(J, cny, wy);
   rweights(K, cnz, wz);
+  int ix[4], iy[4], iz[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = 2 * I - 1 + a, j = 2 * J - 1 + a, k = 2 * K - 1 + a;
+    if (i < 0 || i >= fnx) wx[a] = 0.f;
+    if (j < 0 || j >= fny) wy[a] = 0.f;
+    if (k < 0 || k >= fnz) wz[a] = 0.f;
+    ix[a] = min(max(i, 0), fnx - 1);
+    iy[a] = min(max(j, 0), fny - 1);
+    iz[a] = min(max(k, 0), fnz - 1);
+  }
   V acc = V(0);
+#pragma unroll
   for (int c = 0; c < 4; ++c) {
-    const int k = 2 * K - 1 + c;
-    if (k < 0 || k >= fnz || wz[c] == 0.f) continue;
+#pragma unroll
     for (int b = 0; b < 4; ++b) {
-      const int j = 2 * J - 1 + b;
-      if (j < 0 || j >= fny || wy[b] == 0.f) continue;
       const V wzy = V(wz[c] * wy[b]);
-      const V *row = rf + ((int64_t)k * fny + j) * fnx;
-      for (int a = 0; a < 4; ++a) {
-        const int i = 2 * I - 1 + a;
-        if (i < 0 || i >= fnx || wx[a] == 0.f) continue;
-        acc += wzy * V(wx[a]) * row[i];
-      }
+      const V *row = rf + ((int64_t)iz[c] * fny + iy[b]) * fnx;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) acc += wzy * V(wx[a]) * row[ix[a]];
     }
   }
   return V(0.25) * acc;
@@ -147,7 +175,10 @@ __device__ __forceinline__ V restrict_cell(int fnx, int fny, int fnz, int cnx,
 // (i, j, k).
 template <class V>
 __device__ __forceinline__ V prolong_cell(int cnx, int cny, int cnz,
-                                          const V *xc, int i, int j, int k) {
+                                          const V *xc, int i, int j, int k,
+                                          int mode) {
+  if (mode == kTransferConstant)
+    return xc[((int64_t)(k >> 1) * cny + (j >> 1)) * cnx + (i >> 1)];
   int I[2], J[2], K[2];
   auto ax = [](int f, int n, int *C) {
     const int c0 = f >> 1;
@@ -175,6 +206,56 @@ __device__ __forceinline__ bool stopped(const CGState *st) {
   return st != nullptr && *(volatile const int *)&st->done != 0;
 }
 
+// ------------------------------------------------------------- ILP ------
+// Grid-stride kernels walk cells in batches of ILP cells per thread (cells
+// c0, c0 + stride, ...): every load of a batch is issued before its results
+// are used or stored, so a thread keeps several cells' loads in flight
+// instead of one (the compiler may not move a load above a store through a
+// possibly aliasing pointer). Per-thread accumulation still runs over cells
+// in increasing order, so reductions are unchanged.
+constexpr int kIlpStream = 4;   // streaming vector kernels
+constexpr int kIlpStencil = 1;  // 7-point stencil kernels (one cell: registers)
+
+// The 13 operands of one cell's 7-point operator: the six face fractions,
+// the six neighbour values (0 outside the grid) and the centre value.
+template <class R>
+struct Nb7 {
+  R xm, xp, ym, yp, zm, zp;
+  R vxm, vxp, vym, vyp, vzm, vzp, vc;
+  __device__ __forceinline__ R diag() const { return xm + xp + ym + yp + zm + zp; }
+  // sum_f alpha_f x_nb(f) in the order x-, x+, y-, y+, z-, z+
+  __device__ __forceinline__ R nb() const {
+    R acc = R(0);
+    acc += xm * vxm;
+    acc += xp * vxp;
+    acc += ym * vym;
+    acc += yp * vyp;
+    acc += zm * vzm;
+    acc += zp * vzp;
+    return acc;
+  }
+};
+template <class R, class TA, class X>
+__device__ __forceinline__ void gather7(Nb7<R> &g, const LevelView<TA> &lv,
+                                        const X *x, int i, int j, int k,
+                                        int64_t c) {
+  const Six<R> s = six<R>(lv, i, j, k);
+  g.xm = s.xm;
+  g.xp = s.xp;
+  g.ym = s.ym;
+  g.yp = s.yp;
+  g.zm = s.zm;
+  g.zp = s.zp;
+  const int64_t sy = lv.nx, sz = (int64_t)lv.nx * lv.ny;
+  g.vxm = i > 0 ? (R)x[c - 1] : R(0);
+  g.vxp = i < lv.nx - 1 ? (R)x[c + 1] : R(0);
+  g.vym = j > 0 ? (R)x[c - sy] : R(0);
+  g.vyp = j < lv.ny - 1 ? (R)x[c + sy] : R(0);
+  g.vzm = k > 0 ? (R)x[c - sz] : R(0);
+  g.vzp = k < lv.nz - 1 ? (R)x[c + sz] : R(0);
+  g.vc = (R)x[c];
+}
+
 // ------------------------------------------------------ outer residual -----
 template <class S, class T, class V>
 __global__ void k_residual_outer(LevelView<T> lv, const S *b, const S *x, S *r,
@@ -182,20 +263,32 @@ __global__ void k_residual_outer(LevelView<T> lv, const S *b, const S *x, S *r,
                                  double *norm2) {
   double v[1] = {0.0};
   const int64_t n = lv.ncell();
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
-       c += (int64_t)gridDim.x * blockDim.x) {
-    int i, j, k;
-    GridDev::decomp(c, lv.nx, lv.ny, i, j, k);
-    const Six<double> s = six<double>(lv, i, j, k);
-    const double dg = s.diag();
-    double rv = 0.0;
-    if (dg > 0.0) {
-      const double nb = nbsum<double>(s, x, lv.nx, lv.ny, lv.nz, i, j, k, c);
-      rv = (double)b[c] - lv.c * (dg * (double)x[c] - nb);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  constexpr int U = kIlpStencil;
+  for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c0 < n;
+       c0 += U * stride) {
+    Nb7<double> g[U];
+    double bv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t c = c0 + u * stride;
+      if (c >= n) break;
+      int i, j, k;
+      GridDev::decomp(c, lv.nx, lv.ny, i, j, k);
+      gather7(g[u], lv, x, i, j, k, c);
+      bv[u] = (double)b[c];
     }
-    r[c] = (S)rv;
-    if (rin) rin[c] = (V)(rv * scale);
-    v[0] += rv * rv;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t c = c0 + u * stride;
+      if (c >= n) break;
+      const double dg = g[u].diag();
+      double rv = 0.0;
+      if (dg > 0.0) rv = bv[u] - lv.c * (dg * g[u].vc - g[u].nb());
+      r[c] = (S)rv;
+      if (rin) rin[c] = (V)(rv * scale);
+      v[0] += rv * rv;
+    }
   }
   double tot[1];
   if (grid_sum<1>(v, rs, tot) && threadIdx.x == 0) *norm2 = tot[0];
@@ -203,9 +296,26 @@ __global__ void k_residual_outer(LevelView<T> lv, const S *b, const S *x, S *r,
 
 template <class S, class V>
 __global__ void k_axpy_outer(int64_t n, S *x, const V *e, double inv) {
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
-       c += (int64_t)gridDim.x * blockDim.x)
-    x[c] = (S)((double)x[c] + inv * (double)e[c]);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  constexpr int U = kIlpStream;
+  for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c0 < n;
+       c0 += U * stride) {
+    S xv[U];
+    V ev[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t c = c0 + u * stride;
+      if (c < n) {
+        xv[u] = x[c];
+        ev[u] = e[c];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t c = c0 + u * stride;
+      if (c < n) x[c] = (S)((double)xv[u] + inv * (double)ev[u]);
+    }
+  }
 }
 
 // ------------------------------------------------------------------ CG -----
@@ -218,12 +328,28 @@ __global__ void k_cg_init(int64_t n, const V *r, const V *z, V *d, CGState *st,
                           RedScratch rs) {
   // per-thread partials in V (a few terms each), block and grid sums in FP64
   V p0 = V(0), p1 = V(0);
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
-       c += (int64_t)gridDim.x * blockDim.x) {
-    const V rc = r[c], zc = z[c];
-    d[c] = zc;
-    p0 += rc * zc;
-    p1 += rc * rc;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  constexpr int U = kIlpStream;
+  for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c0 < n;
+       c0 += U * stride) {
+    V rv[U], zv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t c = c0 + u * stride;
+      if (c < n) {
+        rv[u] = r[c];
+        zv[u] = z[c];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t c = c0 + u * stride;
+      if (c < n) {
+        d[c] = zv[u];
+        p0 += rv[u] * zv[u];
+        p1 += rv[u] * rv[u];
+      }
+    }
   }
   double v[2] = {(double)p0, (double)p1};
   double tot[2];
@@ -242,11 +368,27 @@ template <class V>
 __global__ void k_cg_continue(int64_t n, const V *r, const V *z, CGState *st,
                               RedScratch rs) {
   V p0 = V(0), p1 = V(0);
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
-       c += (int64_t)gridDim.x * blockDim.x) {
-    const V rc = r[c];
-    p0 += rc * z[c];
-    p1 += rc * rc;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  constexpr int U = kIlpStream;
+  for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c0 < n;
+       c0 += U * stride) {
+    V rv[U], zv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t c = c0 + u * stride;
+      if (c < n) {
+        rv[u] = r[c];
+        zv[u] = z[c];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t c = c0 + u * stride;
+      if (c < n) {
+        p0 += rv[u] * zv[u];
+        p1 += rv[u] * rv[u];
+      }
+    }
   }
   double v[2] = {(double)p0, (double)p1};
   double tot[2];
@@ -270,13 +412,28 @@ __global__ void k_apply_dot(LevelView<TA> lv, const V *d, V *q, CGState *st,
   if (stopped(st)) return;
   V p = V(0);
   const int64_t n = lv.ncell();
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
-       c += (int64_t)gridDim.x * blockDim.x) {
-    int i, j, k;
-    GridDev::decomp(c, lv.nx, lv.ny, i, j, k);
-    const V qc = apply_cell<V, TA>(lv, d, i, j, k, c);
-    q[c] = qc;
-    p += d[c] * qc;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  constexpr int U = kIlpStencil;
+  for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c0 < n;
+       c0 += U * stride) {
+    Nb7<V> g[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t c = c0 + u * stride;
+      if (c >= n) break;
+      int i, j, k;
+      GridDev::decomp(c, lv.nx, lv.ny, i, j, k);
+      gather7(g[u], lv, d, i, j, k, c);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t c = c0 + u * stride;
+      if (c >= n) break;
+      const V dg = g[u].diag();
+      const V qc = dg > V(0) ? V(lv.c) * (dg * g[u].vc - g[u].nb()) : V(0);
+      q[c] = qc;
+      p += g[u].vc * qc;
+    }
   }
   double v[1] = {(double)p};
   double tot[1];
@@ -295,12 +452,31 @@ __global__ void k_cg_xr(int64_t n, V *x, V *r, const V *d, const V *q,
   if (stopped(st)) return;
   const V a = (V)st->alpha;
   V p = V(0);
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
-       c += (int64_t)gridDim.x * blockDim.x) {
-    x[c] += a * d[c];
-    const V rc = r[c] - a * q[c];
-    r[c] = rc;
-    p += rc * rc;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  constexpr int U = kIlpStream;
+  for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c0 < n;
+       c0 += U * stride) {
+    V xv[U], rv[U], dv[U], qv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t c = c0 + u * stride;
+      if (c < n) {
+        xv[u] = x[c];
+        rv[u] = r[c];
+        dv[u] = d[c];
+        qv[u] = q[c];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t c = c0 + u * stride;
+      if (c < n) {
+        x[c] = xv[u] + a * dv[u];
+        const V rc = rv[u] - a * qv[u];
+        r[c] = rc;
+        p += rc * rc;
+      }
+    }
   }
   double v[1] = {(double)p};
   double tot[1];
@@ -323,9 +499,23 @@ __global__ void k_cg_rz(int64_t n, const V *r, const V *z, CGState *st,
                         RedScratch rs) {
   if (stopped(st)) return;
   V p = V(0);
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
-       c += (int64_t)gridDim.x * blockDim.x)
-    p += r[c] * z[c];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  constexpr int U = kIlpStream;
+  for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c0 < n;
+       c0 += U * stride) {
+    V rv[U], zv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t c = c0 + u * stride;
+      if (c < n) {
+        rv[u] = r[c];
+        zv[u] = z[c];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (c0 + u * stride < n) p += rv[u] * zv[u];
+  }
   double v[1] = {(double)p};
   double tot[1];
   if (grid_sum<1>(v, rs, tot) && threadIdx.x == 0) {
@@ -342,9 +532,25 @@ template <class V>
 __global__ void k_cg_d(int64_t n, const V *z, V *d, const CGState *st) {
   if (stopped(st)) return;
   const V b = (V)st->beta;
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
-       c += (int64_t)gridDim.x * blockDim.x)
-    d[c] = z[c] + b * d[c];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  constexpr int U = kIlpStream;
+  for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c0 < n;
+       c0 += U * stride) {
+    V zv[U], dv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t c = c0 + u * stride;
+      if (c < n) {
+        zv[u] = z[c];
+        dv[u] = d[c];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t c = c0 + u * stride;
+      if (c < n) d[c] = zv[u] + b * dv[u];
+    }
+  }
 }
 
 // ----------------------------------------------------------- multigrid -----
@@ -386,6 +592,67 @@ __global__ void k_mg_coarsen(LevelView<TI> f, int cnx, int cny, int cnz, TO *ax,
   }
 }
 
+// ------------------------------------------------------ boundary band -----
+// Cells next to the solid (an own face with alpha < 1) and their active
+// neighbours get extra Gauss-Seidel sweeps: the coarse-grid correction is
+// weakest there (cut cells, small fractions), so smoothing them alone buys
+// most of what more full sweeps would.
+template <class TA>
+__global__ void k_band_mark(LevelView<TA> lv, unsigned char *m) {
+  const int64_t n = lv.ncell();
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    int i, j, k;
+    GridDev::decomp(c, lv.nx, lv.ny, i, j, k);
+    const Six<float> s = six<float>(lv, i, j, k);
+    const bool cut = s.xm < 1.f || s.xp < 1.f || s.ym < 1.f || s.yp < 1.f ||
+                     s.zm < 1.f || s.zp < 1.f;
+    m[c] = (s.diag() > 0.f && cut) ? 1 : 0;
+  }
+}
+
+// Active cells marked or next to a marked cell, appended to the list of
+// their colour (order does not matter: cells of one colour update
+// independently).
+template <class TA>
+__global__ void k_band_collect(LevelView<TA> lv, const unsigned char *m,
+                               int *list0, int *list1, int *count) {
+  const int64_t n = lv.ncell();
+  const int64_t sy = lv.nx, sz = (int64_t)lv.nx * lv.ny;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    int i, j, k;
+    GridDev::decomp(c, lv.nx, lv.ny, i, j, k);
+    bool in = m[c] != 0;
+    if (!in) {
+      if (!(six<float>(lv, i, j, k).diag() > 0.f)) continue;
+      in = (i > 0 && m[c - 1]) || (i < lv.nx - 1 && m[c + 1]) ||
+           (j > 0 && m[c - sy]) || (j < lv.ny - 1 && m[c + sy]) ||
+           (k > 0 && m[c - sz]) || (k < lv.nz - 1 && m[c + sz]);
+    }
+    if (!in) continue;
+    const int col = (i + j + k) & 1;
+    const int at = atomicAdd(count + col, 1);
+    (col ? list1 : list0)[at] = (int)c;
+  }
+}
+
+// Gauss-Seidel update of the band cells of one colour.
+template <class V, class TA>
+__global__ void k_band_smooth(LevelView<TA> lv, V *x, const V *b,
+                              const int *list, const int *count,
+                              const CGState *st) {
+  if (stopped(st)) return;
+  const int n = *count;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += gridDim.x * blockDim.x) {
+    const int64_t c = list[t];
+    int i, j, k;
+    GridDev::decomp(c, lv.nx, lv.ny, i, j, k);
+    x[c] = gs_cell<V, TA>(lv, x, b, i, j, k, c);
+  }
+}
+
 // Red-black Gauss-Seidel half sweep over cells with (i + j + k) % 2 == color.
 template <class V, class TA>
 __global__ void k_mg_smooth(LevelView<TA> lv, V *x, const V *b, int color,
@@ -393,55 +660,153 @@ __global__ void k_mg_smooth(LevelView<TA> lv, V *x, const V *b, int color,
   if (stopped(st)) return;
   const int hx = (lv.nx + 1) >> 1;
   const int64_t n = (int64_t)hx * lv.ny * lv.nz;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    int ii, j, k;
-    GridDev::decomp(t, hx, lv.ny, ii, j, k);
-    const int i = 2 * ii + ((j + k + color) & 1);
-    if (i >= lv.nx) continue;
-    const int64_t c = ((int64_t)k * lv.ny + j) * lv.nx + i;
-    x[c] = gs_cell<V, TA>(lv, x, b, i, j, k, c);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  constexpr int U = kIlpStencil;
+  const V cc = V(lv.c);
+  for (int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t0 < n;
+       t0 += U * stride) {
+    Nb7<V> g[U];
+    V bv[U];
+    int64_t cell[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      cell[u] = -1;
+      const int64_t t = t0 + u * stride;
+      if (t >= n) break;
+      int ii, j, k;
+      GridDev::decomp(t, hx, lv.ny, ii, j, k);
+      const int i = 2 * ii + ((j + k + color) & 1);
+      if (i >= lv.nx) continue;
+      const int64_t c = ((int64_t)k * lv.ny + j) * lv.nx + i;
+      cell[u] = c;
+      gather7(g[u], lv, x, i, j, k, c);
+      bv[u] = b[c];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (cell[u] < 0) continue;
+      const V dg = g[u].diag();
+      x[cell[u]] = dg > V(0) ? (bv[u] + cc * g[u].nb()) / (cc * dg) : V(0);
+    }
+  }
+}
+
+// Prolongation normaliser of fine cell (i, j, k): 1 / (sum of the trilinear
+// weights of its active coarse cells), 0 if none is active. The V-cycle uses
+// P' = N P and R' = P'^T / 4 = P^T N / 4: near a Neumann (solid) boundary the
+// plain trilinear P would mix in inactive coarse cells, whose value is 0, and
+// damp the correction as if the wall were a zero-pressure boundary.
+template <class TC>
+__device__ __forceinline__ float pnorm_cell(const LevelView<TC> &cv, int i,
+                                            int j, int k) {
+  int I[2], J[2], K[2];
+  auto ax = [](int f, int n, int *C) {
+    const int c0 = f >> 1;
+    int c1 = (f & 1) ? c0 + 1 : c0 - 1;
+    if (c1 < 0 || c1 >= n) c1 = c0;
+    C[0] = c0;
+    C[1] = c1;
+  };
+  ax(i, cv.nx, I);
+  ax(j, cv.ny, J);
+  ax(k, cv.nz, K);
+  const float w[2] = {0.75f, 0.25f};
+  float s = 0.f;
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+        if (six<float>(cv, I[a], J[b], K[c]).diag() > 0.f) s += w[c] * w[b] * w[a];
+  return s > 0.f ? 1.f / s : 0.f;
+}
+
+template <class TC>
+__global__ void k_mg_pnorm(int fnx, int fny, int fnz, LevelView<TC> cv, float *pn,
+                           float scale) {
+  const int64_t n = (int64_t)fnx * fny * fnz;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    int i, j, k;
+    GridDev::decomp(c, fnx, fny, i, j, k);
+    pn[c] = scale * pnorm_cell(cv, i, j, k);
   }
 }
 
 template <class V, class TA>
 __global__ void k_mg_residual(LevelView<TA> lv, const V *x, const V *b, V *r,
-                              const CGState *st) {
+                              const float *pn, const CGState *st) {
   if (stopped(st)) return;
   const int64_t n = lv.ncell();
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
-       c += (int64_t)gridDim.x * blockDim.x) {
-    int i, j, k;
-    GridDev::decomp(c, lv.nx, lv.ny, i, j, k);
-    r[c] = residual_cell<V, TA>(lv, x, b, i, j, k, c);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  constexpr int U = kIlpStencil;
+  for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c0 < n;
+       c0 += U * stride) {
+    Nb7<V> g[U];
+    V bv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t c = c0 + u * stride;
+      if (c >= n) break;
+      int i, j, k;
+      GridDev::decomp(c, lv.nx, lv.ny, i, j, k);
+      gather7(g[u], lv, x, i, j, k, c);
+      bv[u] = b[c];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t c = c0 + u * stride;
+      if (c >= n) break;
+      const V dg = g[u].diag();
+      const V rv = dg > V(0) ? bv[u] - V(lv.c) * (dg * g[u].vc - g[u].nb()) : V(0);
+      r[c] = pn ? rv * V(pn[c]) : rv;
+    }
   }
 }
 
 template <class V>
 __global__ void k_mg_restrict(int fnx, int fny, int fnz, int cnx, int cny,
-                              int cnz, const V *rf, V *bc, const CGState *st) {
+                              int cnz, const V *rf, V *bc, int mode,
+                              const CGState *st) {
   if (stopped(st)) return;
   const int64_t n = (int64_t)cnx * cny * cnz;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
        c += (int64_t)gridDim.x * blockDim.x) {
     int I, J, K;
     GridDev::decomp(c, cnx, cny, I, J, K);
-    bc[c] = restrict_cell<V>(fnx, fny, fnz, cnx, cny, cnz, rf, I, J, K);
+    bc[c] = restrict_cell<V>(fnx, fny, fnz, cnx, cny, cnz, rf, I, J, K, mode);
   }
 }
 
 // x_f += P x_c on active fine cells.
 template <class V, class TF>
 __global__ void k_mg_prolong(LevelView<TF> f, int cnx, int cny, int cnz,
-                             const V *xc, V *xf, const CGState *st) {
+                             const V *xc, V *xf, const float *pn, int mode,
+                             const CGState *st) {
   if (stopped(st)) return;
   const int64_t n = f.ncell();
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
-       c += (int64_t)gridDim.x * blockDim.x) {
-    int i, j, k;
-    GridDev::decomp(c, f.nx, f.ny, i, j, k);
-    if (!(six<float>(f, i, j, k).diag() > 0.f)) continue;
-    xf[c] += prolong_cell<V>(cnx, cny, cnz, xc, i, j, k);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  constexpr int U = kIlpStencil;
+  for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c0 < n;
+       c0 += U * stride) {
+    bool act[U];
+    V add[U], xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t c = c0 + u * stride;
+      act[u] = false;
+      if (c >= n) break;
+      int i, j, k;
+      GridDev::decomp(c, f.nx, f.ny, i, j, k);
+      act[u] = six<float>(f, i, j, k).diag() > 0.f;
+      add[u] = prolong_cell<V>(cnx, cny, cnz, xc, i, j, k, mode);
+      if (pn) add[u] *= V(pn[c]);
+      xv[u] = xf[c];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (act[u]) xf[c0 + u * stride] = xv[u] + add[u];
   }
 }
 
@@ -481,7 +846,7 @@ k_mg_coarse_chain(CoarseChain<V, TA> ch, const CGState *st) {
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
       const int i = t % lv.nx, q = t / lv.nx;
       const int j = q % lv.ny, k = q / lv.ny;
-      ch.r[l][t] = residual_cell<V, TA>(lv, ch.x[l], ch.b[l], i, j, k, t);
+      ch.r[l][t] = residual_cell<V, TA>(lv, ch.x[l], ch.b[l], i, j, k, t) * V(ch.pn[l][t]);
     }
     __syncthreads();
     const LevelView<TA> &cv = ch.lv[l + 1];
@@ -490,7 +855,7 @@ k_mg_coarse_chain(CoarseChain<V, TA> ch, const CGState *st) {
       const int I = t % cv.nx, q = t / cv.nx;
       const int J = q % cv.ny, K = q / cv.ny;
       ch.b[l + 1][t] = restrict_cell<V>(lv.nx, lv.ny, lv.nz, cv.nx, cv.ny,
-                                        cv.nz, ch.r[l], I, J, K);
+                                        cv.nz, ch.r[l], I, J, K, ch.transfer);
     }
     __syncthreads();
   }
@@ -513,7 +878,9 @@ k_mg_coarse_chain(CoarseChain<V, TA> ch, const CGState *st) {
       const int i = t % lv.nx, q = t / lv.nx;
       const int j = q % lv.ny, k = q / lv.ny;
       if (six<float>(lv, i, j, k).diag() > 0.f)
-        ch.x[l][t] += prolong_cell<V>(cv.nx, cv.ny, cv.nz, ch.x[l + 1], i, j, k);
+        ch.x[l][t] += prolong_cell<V>(cv.nx, cv.ny, cv.nz, ch.x[l + 1], i, j, k,
+                                      ch.transfer) *
+                      V(ch.pn[l][t]);
     }
     __syncthreads();
     for (int s = 0; s < ch.smooth; ++s) {
@@ -610,7 +977,7 @@ k_mg_chain_smem(CoarseChain<V, TA> ch, const CGState *st) {
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
       const int i = t % lv.nx, q = t / lv.nx;
       const int j = q % lv.ny, k = q / lv.ny;
-      r[t] = residual_cell<V, FA>(lv, x, b, i, j, k, t);
+      r[t] = residual_cell<V, FA>(lv, x, b, i, j, k, t) * V(ch.pn[l][t]);
     }
     __syncthreads();
     const LevelView<TA> &cv = ch.lv[l + 1];
@@ -619,7 +986,8 @@ k_mg_chain_smem(CoarseChain<V, TA> ch, const CGState *st) {
     for (int t = threadIdx.x; t < nc; t += blockDim.x) {
       const int I = t % cv.nx, q = t / cv.nx;
       const int J = q % cv.ny, K = q / cv.ny;
-      bc[t] = restrict_cell<V>(lv.nx, lv.ny, lv.nz, cv.nx, cv.ny, cv.nz, r, I, J, K);
+      bc[t] = restrict_cell<V>(lv.nx, lv.ny, lv.nz, cv.nx, cv.ny, cv.nz, r, I, J, K,
+                               ch.transfer);
     }
     __syncthreads();
   }
@@ -644,7 +1012,8 @@ k_mg_chain_smem(CoarseChain<V, TA> ch, const CGState *st) {
       const int i = t % lv.nx, q = t / lv.nx;
       const int j = q % lv.ny, k = q / lv.ny;
       if (six<float>(lv, i, j, k).diag() > 0.f)
-        x[t] += prolong_cell<V>(cv.nx, cv.ny, cv.nz, xc, i, j, k);
+        x[t] += prolong_cell<V>(cv.nx, cv.ny, cv.nz, xc, i, j, k, ch.transfer) *
+                V(ch.pn[l][t]);
     }
     __syncthreads();
     for (int s = 0; s < ch.smooth; ++s) {
@@ -739,29 +1108,64 @@ void launch_mg_smooth(const Launch &L, const LevelView<TA> &lv, V *x,
   k_mg_smooth<V, TA><<<gs_blocks(n), kBlock, 0, L.s>>>(lv, x, b, color, st);
   ++*L.counter;
 }
+template <class TA>
+void launch_band_build(const Launch &L, const LevelView<TA> &lv,
+                       unsigned char *mark, int *list0, int *list1, int *count) {
+  ProfScope _ps(L, NF_K_MG_COARSEN);
+  cudaMemsetAsync(count, 0, 2 * sizeof(int), L.s);
+  k_band_mark<TA><<<gs_blocks(lv.ncell()), kBlock, 0, L.s>>>(lv, mark);
+  k_band_collect<TA><<<gs_blocks(lv.ncell()), kBlock, 0, L.s>>>(lv, mark, list0,
+                                                                list1, count);
+  *L.counter += 2;
+}
+template <class V, class TA>
+void launch_band_smooth(const Launch &L, const LevelView<TA> &lv, V *x,
+                        const V *b, const int *list, const int *count,
+                        const CGState *st) {
+  ProfScope _ps(L, NF_K_MG_SMOOTH0);
+  k_band_smooth<V, TA><<<kRedBlocks, kBlock, 0, L.s>>>(lv, x, b, list, count, st);
+  ++*L.counter;
+}
 template <class V, class TA>
 void launch_mg_residual(const Launch &L, const LevelView<TA> &lv, const V *x,
-                        const V *b, V *r, const CGState *st) {
+                        const V *b, V *r, const float *pn, const CGState *st) {
   ProfScope _ps(L, NF_K_MG_RESIDUAL);
-  k_mg_residual<V, TA><<<gs_blocks(lv.ncell()), kBlock, 0, L.s>>>(lv, x, b, r, st);
+  k_mg_residual<V, TA><<<gs_blocks(lv.ncell()), kBlock, 0, L.s>>>(lv, x, b, r, pn, st);
   ++*L.counter;
 }
 template <class V, class TA>
 void launch_mg_restrict(const Launch &L, const LevelView<TA> &fine,
                         const LevelView<TA> &coarse, const V *rf, V *bc,
-                        const CGState *st) {
+                        int mode, const CGState *st) {
   ProfScope _ps(L, NF_K_MG_RESTRICT);
   k_mg_restrict<V><<<gs_blocks(coarse.ncell()), kBlock, 0, L.s>>>(
-      fine.nx, fine.ny, fine.nz, coarse.nx, coarse.ny, coarse.nz, rf, bc, st);
+      fine.nx, fine.ny, fine.nz, coarse.nx, coarse.ny, coarse.nz, rf, bc, mode, st);
   ++*L.counter;
 }
 template <class V, class TF, class TC>
 void launch_mg_prolong(const Launch &L, const LevelView<TF> &fine,
                        const LevelView<TC> &coarse, const V *xc, V *xf,
-                       const CGState *st) {
+                       const float *pn, int mode, const CGState *st) {
   ProfScope _ps(L, NF_K_MG_PROLONG);
   k_mg_prolong<V, TF><<<gs_blocks(fine.ncell()), kBlock, 0, L.s>>>(
-      fine, coarse.nx, coarse.ny, coarse.nz, xc, xf, st);
+      fine, coarse.nx, coarse.ny, coarse.nz, xc, xf, pn, mode, st);
+  ++*L.counter;
+}
+__global__ void k_fill(int64_t n, float *p, float v) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x)
+    p[c] = v;
+}
+void launch_mg_fill(const Launch &L, int64_t n, float *p, float v) {
+  k_fill<<<gs_blocks(n), kBlock, 0, L.s>>>(n, p, v);
+  ++*L.counter;
+}
+template <class TC>
+void launch_mg_pnorm(const Launch &L, int fnx, int fny, int fnz,
+                     const LevelView<TC> &coarse, float *pn, float scale) {
+  ProfScope _ps(L, NF_K_MG_COARSEN);
+  const int64_t n = (int64_t)fnx * fny * fnz;
+  k_mg_pnorm<TC><<<gs_blocks(n), kBlock, 0, L.s>>>(fnx, fny, fnz, coarse, pn, scale);
   ++*L.counter;
 }
 template <class V, class TA>
@@ -807,13 +1211,18 @@ void launch_mg_coarse_chain(const Launch &L, const CoarseChain<V, TA> &ch,
   template void launch_mg_smooth<V, TA>(const Launch &, const LevelView<TA> &,\
                                         V *, const V *, int, const CGState *, \
                                         int);                                 \
+  template void launch_band_smooth<V, TA>(const Launch &,                    \
+                                          const LevelView<TA> &, V *,         \
+                                          const V *, const int *,             \
+                                          const int *, const CGState *);      \
   template void launch_mg_residual<V, TA>(const Launch &,                    \
                                           const LevelView<TA> &, const V *,   \
-                                          const V *, V *, const CGState *);   \
+                                          const V *, V *, const float *,      \
+                                          const CGState *);                   \
   template void launch_mg_restrict<V, TA>(const Launch &,                    \
                                           const LevelView<TA> &,              \
                                           const LevelView<TA> &, const V *,   \
-                                          V *, const CGState *);              \
+                                          V *, int, const CGState *);              \
   template void launch_mg_coarse_chain<V, TA>(const Launch &,                \
                                               const CoarseChain<V, TA> &,     \
                                               const CGState *);               \
@@ -821,14 +1230,21 @@ void launch_mg_coarse_chain(const Launch &L, const CoarseChain<V, TA> &ch,
   template int prepare_mg_chain<V, TA>(int);
 NF_INST_V(float)
 NF_INST_V(double)
+template void launch_band_build<float>(const Launch &, const LevelView<float> &,
+                                       unsigned char *, int *, int *, int *);
+template void launch_band_build<double>(const Launch &, const LevelView<double> &,
+                                        unsigned char *, int *, int *, int *);
 NF_INST_VA(float, float)
 NF_INST_VA(float, __nv_bfloat16)
 NF_INST_VA(double, double)
 
-template void launch_mg_prolong<float, float, float>(const Launch &, const LevelView<float> &, const LevelView<float> &, const float *, float *, const CGState *);
-template void launch_mg_prolong<float, float, __nv_bfloat16>(const Launch &, const LevelView<float> &, const LevelView<__nv_bfloat16> &, const float *, float *, const CGState *);
-template void launch_mg_prolong<float, __nv_bfloat16, __nv_bfloat16>(const Launch &, const LevelView<__nv_bfloat16> &, const LevelView<__nv_bfloat16> &, const float *, float *, const CGState *);
-template void launch_mg_prolong<double, double, double>(const Launch &, const LevelView<double> &, const LevelView<double> &, const double *, double *, const CGState *);
+template void launch_mg_prolong<float, float, float>(const Launch &, const LevelView<float> &, const LevelView<float> &, const float *, float *, const float *, int, const CGState *);
+template void launch_mg_prolong<float, float, __nv_bfloat16>(const Launch &, const LevelView<float> &, const LevelView<__nv_bfloat16> &, const float *, float *, const float *, int, const CGState *);
+template void launch_mg_prolong<float, __nv_bfloat16, __nv_bfloat16>(const Launch &, const LevelView<__nv_bfloat16> &, const LevelView<__nv_bfloat16> &, const float *, float *, const float *, int, const CGState *);
+template void launch_mg_prolong<double, double, double>(const Launch &, const LevelView<double> &, const LevelView<double> &, const double *, double *, const float *, int, const CGState *);
+template void launch_mg_pnorm<float>(const Launch &, int, int, int, const LevelView<float> &, float *, float);
+template void launch_mg_pnorm<__nv_bfloat16>(const Launch &, int, int, int, const LevelView<__nv_bfloat16> &, float *, float);
+template void launch_mg_pnorm<double>(const Launch &, int, int, int, const LevelView<double> &, float *, float);
 
 template void launch_mg_coarsen<float, float>(const Launch &, const LevelView<float> &, int, int, int, float *, float *, float *);
 template void launch_mg_coarsen<float, __nv_bfloat16>(const Launch &, const LevelView<float> &, int, int, int, __nv_bfloat16 *, __nv_bfloat16 *, __nv_bfloat16 *);

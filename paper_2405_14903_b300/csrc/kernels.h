@@ -122,16 +122,26 @@ template <class V, class TA>
 void launch_mg_smooth(const Launch &L, const LevelView<TA> &lv, V *x,
                       const V *b, int color, const CGState *st, int kclass);
 template <class V, class TA>
+// r = N (b - A x) with N the prolongation normaliser pn (null: N = I).
 void launch_mg_residual(const Launch &L, const LevelView<TA> &lv, const V *x,
-                        const V *b, V *r, const CGState *st);
+                        const V *b, V *r, const float *pn, const CGState *st);
 template <class V, class TA>
+// b_c = R r_f; mode 0: R = P^T / 4 with trilinear P, 1: mean of the eight
+// children (P copies the parent).
 void launch_mg_restrict(const Launch &L, const LevelView<TA> &fine,
                         const LevelView<TA> &coarse, const V *rf, V *bc,
-                        const CGState *st);
+                        int mode, const CGState *st);
 template <class V, class TF, class TC>
+// x_f += N P x_c on active fine cells (pn null: N = I).
 void launch_mg_prolong(const Launch &L, const LevelView<TF> &fine,
                        const LevelView<TC> &coarse, const V *xc, V *xf,
-                       const CGState *st);
+                       const float *pn, int mode, const CGState *st);
+// pn = N: 1 / (sum of the trilinear prolongation weights of the active
+// coarse cells) per fine cell, 0 where none is active.
+void launch_mg_fill(const Launch &L, int64_t n, float *p, float v);
+template <class TC>
+void launch_mg_pnorm(const Launch &L, int fnx, int fny, int fnz,
+                     const LevelView<TC> &coarse, float *pn, float scale);
 
 // The levels at and below `first` handled by one thread block: a whole
 // V-cycle on the small grids (levels first .. nlev-1), x zeroed inside.
@@ -142,6 +152,8 @@ struct CoarseChain {
   V *x[kMaxLevels];
   V *b[kMaxLevels];
   V *r[kMaxLevels];
+  const float *pn[kMaxLevels];  // prolongation normaliser of each level
+  int transfer;                 // 0 trilinear, 1 constant (see restrict)
   int smooth;         // sweeps per level
   int coarsest_sweeps;
   int smem_bytes;     // > 0: run the chain in that much dynamic shared memory
@@ -149,6 +161,16 @@ struct CoarseChain {
 template <class V, class TA>
 void launch_mg_coarse_chain(const Launch &L, const CoarseChain<V, TA> &ch,
                             const CGState *st);
+// Boundary band of the finest level: active cells with a face alpha < 1 and
+// their active neighbours, listed per colour (count[0], count[1]).
+template <class TA>
+void launch_band_build(const Launch &L, const LevelView<TA> &lv,
+                       unsigned char *mark, int *list0, int *list1, int *count);
+// Gauss-Seidel update of the listed cells of one colour.
+template <class V, class TA>
+void launch_band_smooth(const Launch &L, const LevelView<TA> &lv, V *x,
+                        const V *b, const int *list, const int *count,
+                        const CGState *st);
 // Shared memory the chain needs with every level resident (bytes).
 template <class V, class TA>
 size_t mg_chain_smem_bytes(const CoarseChain<V, TA> &ch);

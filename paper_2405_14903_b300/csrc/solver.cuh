@@ -81,6 +81,13 @@ class Solver {
           CKS(A.get(&L.b, nc * sizeof(V)));
         }
         CKS(A.get(&L.r, nc * sizeof(V)));
+        CKS(A.get(&L.pn, nc * sizeof(float)));
+      }
+      if (cfg_.mg_band_sweeps > 0 && levels_.size() > 1) {
+        CKS(A.get(&band_mark_, n_));
+        CKS(A.get(&band_list_[0], (n_ / 2 + 1) * sizeof(int)));
+        CKS(A.get(&band_list_[1], (n_ / 2 + 1) * sizeof(int)));
+        CKS(A.get(&band_count_, 2 * sizeof(int)));
       }
       // first level handled inside the one-block chain kernel
       first_chain_ = (int)levels_.size() - 1;
@@ -114,6 +121,9 @@ class Solver {
     az0_ = az;
     if (!mg_) return;
     Launch L = ctx_->launch();
+    if (band_count_)
+      launch_band_build<T>(L, view0(), (unsigned char *)band_mark_, (int *)band_list_[0],
+                           (int *)band_list_[1], (int *)band_count_);
     for (size_t l = 1; l < levels_.size(); ++l) {
       Level &C = levels_[l];
       if (l == 1)
@@ -122,6 +132,15 @@ class Solver {
       else
         launch_mg_coarsen<TA, TA>(L, viewc(l - 1), C.nx, C.ny, C.nz,
                                   (TA *)C.ax, (TA *)C.ay, (TA *)C.az);
+    }
+    for (size_t l = 0; l + 1 < levels_.size(); ++l) {
+      const Level &F = levels_[l];
+      // sqrt of the coarse-correction weight on each side keeps R' = P'^T / 4
+      const float w = (float)std::sqrt(cfg_.mg_coarse_weight > 0 ? cfg_.mg_coarse_weight : 1.0);
+      if (cfg_.mg_transfer == 0)
+        launch_mg_pnorm<TA>(L, F.nx, F.ny, F.nz, viewc(l + 1), (float *)F.pn, w);
+      else  // a constant P needs no normaliser
+        launch_mg_fill(L, (int64_t)F.nx * F.ny * F.nz, (float *)F.pn, w);
     }
   }
 
@@ -196,11 +215,14 @@ class Solver {
     double c;
     void *ax = nullptr, *ay = nullptr, *az = nullptr;
     void *x = nullptr, *b = nullptr, *r = nullptr;
+    void *pn = nullptr;  // prolongation normaliser (levels with a coarser one)
   };
   static constexpr int kMaxOuter = 12;
   static constexpr int kChainCells = 16 * 16 * 16;
   static constexpr int kBatch = 4;
-  static constexpr int kCoarsestSweeps = 8;
+  int coarsest_sweeps() const {
+    return cfg_.mg_coarsest_sweeps > 0 ? cfg_.mg_coarsest_sweeps : 8;
+  }
 
   LevelView<T> view0() const {
     return LevelView<T>{g_.nx, g_.ny, g_.nz, g_.c, ax0_, ay0_, az0_};
@@ -232,6 +254,27 @@ class Solver {
       launch_mg_smooth<V, TA>(L, viewc(l), x, b, color, st, NF_K_MG_SMOOTH);
   }
 
+  // Extra sweeps on the finest level's boundary band: red-black before the
+  // pre-smoothing (first = 0), black-red after the post-smoothing (first =
+  // 1), so the V-cycle stays symmetric.
+  void band(V *x, const V *b, int first, const CGState *st) {
+    if (!band_count_) return;
+    Launch L = ctx_->launch();
+    const int *cnt = (const int *)band_count_;
+    for (int s = 0; s < cfg_.mg_band_sweeps; ++s) {
+      launch_band_smooth<V, T>(L, view0(), x, b, (const int *)band_list_[first], cnt + first, st);
+      launch_band_smooth<V, T>(L, view0(), x, b, (const int *)band_list_[first ^ 1],
+                               cnt + (first ^ 1), st);
+    }
+  }
+
+  // Prolongation normaliser of level l for the grid kernels (null: none).
+  const float *pnorm(int l) const {
+    const bool unit = cfg_.mg_transfer != 0 &&
+                      (cfg_.mg_coarse_weight == 1.0 || cfg_.mg_coarse_weight == 0.0);
+    return unit ? nullptr : (const float *)levels_[l].pn;
+  }
+
   CoarseChain<V, TA> chain(int first) const {
     CoarseChain<V, TA> ch;
     ch.first = first;
@@ -241,9 +284,11 @@ class Solver {
       ch.x[l] = (V *)levels_[l].x;
       ch.b[l] = (V *)levels_[l].b;
       ch.r[l] = (V *)levels_[l].r;
+      ch.pn[l] = (const float *)levels_[l].pn;
     }
+    ch.transfer = cfg_.mg_transfer;
     ch.smooth = std::max(1, cfg_.mg_smooth);
-    ch.coarsest_sweeps = kCoarsestSweeps;
+    ch.coarsest_sweeps = coarsest_sweeps();
     ch.smem_bytes = chain_smem_;
     return ch;
   }
@@ -262,27 +307,28 @@ class Solver {
       const V *b = l == 0 ? r : (const V *)levels_[l].b;
       const int64_t nc = (int64_t)levels_[l].nx * levels_[l].ny * levels_[l].nz;
       cudaMemsetAsync(x, 0, nc * sizeof(V), L.s);
+      if (l == 0) band(x, b, 0, st);
       for (int s = 0; s < nu; ++s) {
         smooth(l, x, b, 0, st);
         smooth(l, x, b, 1, st);
       }
       if (l == 0)
-        launch_mg_residual<V, T>(L, view0(), x, b, (V *)levels_[0].r, st);
+        launch_mg_residual<V, T>(L, view0(), x, b, (V *)levels_[0].r, pnorm(0), st);
       else
-        launch_mg_residual<V, TA>(L, viewc(l), x, b, (V *)levels_[l].r, st);
+        launch_mg_residual<V, TA>(L, viewc(l), x, b, (V *)levels_[l].r, pnorm(l), st);
       const LevelView<TA> f{levels_[l].nx, levels_[l].ny, levels_[l].nz, 0.0,
                             nullptr, nullptr, nullptr};
       launch_mg_restrict<V, TA>(L, f, viewc(l + 1), (const V *)levels_[l].r,
-                                (V *)levels_[l + 1].b, st);
+                                (V *)levels_[l + 1].b, cfg_.mg_transfer, st);
     }
     if (nl == 1) {
       // no coarser grid: symmetric Gauss-Seidel sweeps only
       cudaMemsetAsync(z, 0, n_ * sizeof(V), L.s);
-      for (int s = 0; s < kCoarsestSweeps; ++s) {
+      for (int s = 0; s < coarsest_sweeps(); ++s) {
         smooth(0, z, r, 0, st);
         smooth(0, z, r, 1, st);
       }
-      for (int s = 0; s < kCoarsestSweeps; ++s) {
+      for (int s = 0; s < coarsest_sweeps(); ++s) {
         smooth(0, z, r, 1, st);
         smooth(0, z, r, 0, st);
       }
@@ -294,14 +340,17 @@ class Solver {
       const V *b = l == 0 ? r : (const V *)levels_[l].b;
       if (l == 0)
         launch_mg_prolong<V, T, TA>(L, view0(), viewc(l + 1),
-                                    (const V *)levels_[l + 1].x, x, st);
+                                    (const V *)levels_[l + 1].x, x, pnorm(0),
+                                    cfg_.mg_transfer, st);
       else
         launch_mg_prolong<V, TA, TA>(L, viewc(l), viewc(l + 1),
-                                     (const V *)levels_[l + 1].x, x, st);
+                                     (const V *)levels_[l + 1].x, x, pnorm(l),
+                                     cfg_.mg_transfer, st);
       for (int s = 0; s < nu; ++s) {
         smooth(l, x, b, 1, st);
         smooth(l, x, b, 0, st);
       }
+      if (l == 0) band(x, b, 1, st);
     }
   }
 
@@ -470,6 +519,7 @@ class Solver {
   bool mg_ = false;
   int first_chain_ = 0;
   int chain_smem_ = 0;  // dynamic shared memory of the chain kernel (0: global)
+  void *band_mark_ = nullptr, *band_list_[2] = {nullptr, nullptr}, *band_count_ = nullptr;
   std::vector<Level> levels_;
   const T *ax0_ = nullptr, *ay0_ = nullptr, *az0_ = nullptr;
   void *r_ = nullptr, *rin_ = nullptr, *e_ = nullptr, *z_ = nullptr,

@@ -283,3 +283,25 @@ def test_hbm_budget_refuses_admission(nf):
     with pytest.raises(nf.NFError) as e:
         ctx.episode(cfg["grid"], cfg["scene"])
     assert e.value.status == 2
+
+
+# ------------------------------------------------------ solver variants ----
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("variant", [
+    dict(mg_transfer="trilinear", mg_coarse_weight=1.0),
+    dict(mg_transfer="trilinear", mg_coarse_weight=1.0, mg_band_sweeps=1),
+    dict(mg_transfer="constant", mg_coarse_weight=1.0, mg_smooth=1),
+    dict(mg_transfer="constant", mg_coarse_weight=1.9, mg_coarsest_sweeps=2),
+], ids=["trilinear", "trilinear_band", "constant_unweighted", "constant_1.9"])
+def test_multigrid_variants_match_oracle(nf, prec, variant):
+    # the preconditioner changes the iterations, never the solution
+    cfg, Jo, gtho, info = oracle_rollout("chamber_sub")
+    ctx = make_ctx(nf, prec, cfg=cfg, checkpoint_every=2, **variant)
+    ep = ctx.episode(cfg["grid"], cfg["scene"])
+    ep.set_velocity(device_u(cfg), project=cfg["project_initial"])
+    ep.step(cfg["steps"])
+    J, gU = ep.loss(cfg["loss"], want_grad=True)
+    gth, _, st = ep.backward(gU)
+    assert abs(J - Jo) <= VEL_TOL[prec] * abs(Jo)
+    assert np.linalg.norm(gth - gtho) <= GRAD_TOL[prec] * np.linalg.norm(gtho)
