@@ -8,17 +8,16 @@
 namespace nf {
 
 struct Components {
-  static constexpr int kMaxRounds = 256;
   int *lab = nullptr;      // root cell of each active cell, -1 if inactive
   int *ground = nullptr;   // per root: 1 if the component has an open face
   int *ccnt = nullptr;     // per root: cell count (gauge scratch)
   unsigned long long *csum = nullptr;  // per root: fixed-point sum
-  void *scal = nullptr;    // [0] changed, [1] floating count, +16 max, +24 norm
+  void *scal = nullptr;    // [1] floating count, +16 max, +24 norm
   int nfloat = 0;          // floating components found by the last label()
 
   int init(Alloc &A, int64_t ncell);
   // Label the components of the cells with sum alpha > 0 and find those
-  // with an open face. Synchronises the stream (a few small readbacks).
+  // with an open face. Synchronises the stream once (the floating count).
   template <class T>
   int label(Ctx *ctx, const GridDev &g, Fields<T> alpha);
   // Shift v to zero mean on every floating component; returns ||v||^2

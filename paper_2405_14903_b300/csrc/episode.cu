@@ -3,7 +3,7 @@
 //
 // Rollout tape: the velocity U^{mC} is saved before every C-th step. To
 // revert step m the library restores U^{sC} (s = m / C), recomputes the
-// segment's steps storing (U^k, U^k hat, P^k) for each, then runs the
+// segment's steps storing (U^k, U^k hat, P^k, alpha^k) for each, then runs the
 // adjoint of the segment's steps in reverse. The forward kernels are
 // deterministic (no float atomics, fixed-order reductions), so the recomputed
 // segment reproduces the recorded rollout bit for bit.
@@ -532,14 +532,17 @@ class EpisodeImpl : public EpisodeBase {
   // ---------------------------------------------------------- backward ----
   int ensure_segment_buffers(int C) {
     while ((int)segU_.size() < C) {
-      T *a = nullptr, *b = nullptr;
+      T *a = nullptr, *b = nullptr, *f = nullptr;
       S *p = nullptr;
       CKS(faces(&a));
       CKS(faces(&b));
+      CKS(faces(&f));
       CKS(A_.get(&p, ncell_ * sizeof(S)));
       segU_.push_back(a);
       segUh_.push_back(b);
+      segA_.push_back(f);
       segP_.push_back(p);
+      segFloat_.push_back(-1);
     }
     if (!tmpU_) CKS(faces(&tmpU_));
     return NF_OK;
@@ -557,6 +560,12 @@ class EpisodeImpl : public EpisodeBase {
       T *out = (k + 1 < end - start) ? segU_[k + 1] : tmpU_;
       SolveStats ss;
       CKS(forward_step(m, segU_[k], out, segUh_[k], segP_[k], &ss));
+      // keep the step's fractions for its adjoint (saves a rasterisation)
+      // and whether any component floats (if none, the adjoint needs no
+      // labels: its gauge is the identity)
+      CKC(cudaMemcpyAsync(segA_[k], alpha_, nfaces_ * sizeof(T),
+                          cudaMemcpyDeviceToDevice, ctx_->stream));
+      segFloat_[k] = cc_.nfloat;
       acc_stats(st, ss);
     }
     seg_start_ = start;
@@ -566,9 +575,13 @@ class EpisodeImpl : public EpisodeBase {
   // Adjoint of one projection (fractions alpha_ for scene state sd) with
   // the forward's U^ = uh and pressure P: gU_ -> gUh_, theta gradient.
   int adjoint_projection(const GridDev &g, const SceneDev &sd, const T *uh,
-                         const S *P, double *gth, nf_step_stats *st) {
+                         const S *P, double *gth, nf_step_stats *st,
+                         bool relabel = true) {
     Launch L = ctx_->launch();
-    CKS(cc_.label<T>(ctx_, g, cview(alpha_)));
+    if (relabel)
+      CKS(cc_.label<T>(ctx_, g, cview(alpha_)));
+    else
+      cc_.nfloat = 0;
     solver_.set_fractions(comp(alpha_, 0), comp(alpha_, 1), comp(alpha_, 2));
     launch_adj_gp<T, S>(L, g, cview(alpha_), cview(gU_), gP_, ctx_->rs, dscal_);
     const double n2 = gauge(gP_, ctx_->read_double(dscal_));
@@ -605,8 +618,10 @@ class EpisodeImpl : public EpisodeBase {
     const int k = m - seg_start_;
     const GridDev g = grid_h(hs_[m]);
     const SceneDev sd = scene_at(sc_, ts_[m], dsph_);
-    launch_rasterize<T>(L, g, sd, mut(alpha_));
-    const int rc = adjoint_projection(g, sd, segUh_[k], segP_[k], gth, st);
+    // the step's fractions, kept by the recompute (the solver's captured
+    // graphs read alpha_, so they are copied back rather than pointed to)
+    CKC(cudaMemcpyAsync(alpha_, segA_[k], nfaces_ * sizeof(T), cudaMemcpyDeviceToDevice, L.s));
+    const int rc = adjoint_projection(g, sd, segUh_[k], segP_[k], gth, st, segFloat_[k] != 0);
     launch_advect_adjoint<T>(L, g, cview(segU_[k]), cview(gUh_), mut(gUb_),
                              ctx_->cfg.advect_order);
     std::swap(gU_, gUb_);
@@ -636,8 +651,9 @@ class EpisodeImpl : public EpisodeBase {
   S *Pinit_ = nullptr;
   std::vector<T *> ckpt_;
   int seg_start_ = -1;
-  std::vector<T *> segU_, segUh_;
+  std::vector<T *> segU_, segUh_, segA_;
   std::vector<S *> segP_;
+  std::vector<int> segFloat_;  // floating components of each segment step
 };
 
 size_t episode_base_bytes(const nf_config &cfg, const nf_grid &g) {

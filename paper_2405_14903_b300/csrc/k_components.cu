@@ -2,10 +2,16 @@
 // components that touch no open face (Sec. 2.3.1, Projection: the cut-cell
 // system is singular on such a component, with the constants as null space).
 //
-// Labelling: union-find by hooking roots to the smaller index, repeated until
-// a round finds every face with alpha > 0 joining cells of equal root; the
-// final label of a cell is the smallest cell index of its component, so the
-// result does not depend on scheduling.
+// Labelling: lock-free union-find. A union hooks the larger root under the
+// smaller one with compare-and-swap, retrying if another thread moved the
+// root first, so roots only ever decrease and no cycle can form. Two levels:
+// every 8x8x8 tile first unions the faces inside it in shared memory (its
+// local root, the smallest local index, is also the smallest global index of
+// the tile component: both orders are lexicographic in (k, j, i)); then the
+// faces on tile borders are unioned in global memory over that much smaller
+// forest, and a last pass points every cell at its root. The root of a
+// component is its smallest cell index, so the labels do not depend on
+// scheduling.
 //
 // Gauge: on every floating component the field is shifted to zero mean. The
 // per-component sums are accumulated as 64-bit fixed-point integers (scale
@@ -33,39 +39,100 @@ __device__ __forceinline__ int cc_find(const int *lab, int x) {
   }
 }
 
-template <class T>
-__global__ void k_cc_init(GridDev g, Fields<T> a, int *lab) {
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.ncell();
-       c += (int64_t)gridDim.x * blockDim.x) {
-    int i, j, k;
-    g.cell_ijk(c, i, j, k);
-    lab[c] = active_cell(g, a, i, j, k) ? (int)c : -1;
+// Root of x, halving the path on the way (every cell visited is pointed at
+// its grandparent, still an ancestor: benign under concurrent updates).
+__device__ __forceinline__ int cc_find_halve(int *lab, int x) {
+  volatile int *l = lab;
+  int p = l[x];
+  while (p != x) {
+    const int g = l[p];
+    if (g != p) l[x] = g;
+    x = p;
+    p = g;
   }
+  return x;
 }
 
+__device__ __forceinline__ void cc_union(int *lab, int a, int b);
+
+constexpr int kCcTile = 8;
+
 template <class T>
-__global__ void k_cc_hook(GridDev g, Fields<T> a, int *lab, int *changed) {
+__global__ void __launch_bounds__(kCcTile * kCcTile * kCcTile)
+k_cc_tile(GridDev g, Fields<T> a, int *lab) {
+  __shared__ int par[kCcTile * kCcTile * kCcTile];
+  const int li = threadIdx.x, lj = threadIdx.y, lk = threadIdx.z;
+  const int i0 = blockIdx.x * kCcTile, j0 = blockIdx.y * kCcTile, k0 = blockIdx.z * kCcTile;
+  const int i = i0 + li, j = j0 + lj, k = k0 + lk;
+  const int t = (lk * kCcTile + lj) * kCcTile + li;
+  const bool in = i < g.nx && j < g.ny && k < g.nz;
+  const bool act = in && active_cell(g, a, i, j, k);
+  par[t] = act ? t : -1;
+  __syncthreads();
+  if (act) {
+    for (int d = 0; d < 3; ++d) {
+      const int ni = i + (d == 0), nj = j + (d == 1), nk = k + (d == 2);
+      const int mi = li + (d == 0), mj = lj + (d == 1), mk = lk + (d == 2);
+      if (mi >= kCcTile || mj >= kCcTile || mk >= kCcTile) continue;
+      if (ni >= g.nx || nj >= g.ny || nk >= g.nz) continue;
+      const T af = d == 0 ? a.x[g.face(0, ni, j, k)]
+                          : (d == 1 ? a.y[g.face(1, i, nj, k)] : a.z[g.face(2, i, j, nk)]);
+      if (!(af > T(0))) continue;
+      cc_union(par, t, (mk * kCcTile + mj) * kCcTile + mi);
+    }
+  }
+  __syncthreads();
+  if (!in) return;
+  int root = -1;
+  if (act) {
+    const int r = cc_find(par, t);
+    root = (int)g.cell(i0 + r % kCcTile, j0 + (r / kCcTile) % kCcTile,
+                       k0 + r / (kCcTile * kCcTile));
+  }
+  lab[g.cell(i, j, k)] = root;
+}
+
+// Union across tile borders: the faces from a tile's last layer to the next
+// tile, in the forest of tile roots.
+template <class T>
+__global__ void k_cc_merge(GridDev g, Fields<T> a, int *lab) {
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.ncell();
        c += (int64_t)gridDim.x * blockDim.x) {
-    if (((const volatile int *)lab)[c] < 0) continue;
     int i, j, k;
     g.cell_ijk(c, i, j, k);
-    // faces towards +x, +y, +z neighbours
+    const bool bx = (i % kCcTile) == kCcTile - 1, by = (j % kCcTile) == kCcTile - 1,
+               bz = (k % kCcTile) == kCcTile - 1;
+    if (!(bx || by || bz)) continue;
+    if (((const volatile int *)lab)[c] < 0) continue;
     for (int d = 0; d < 3; ++d) {
+      if (!(d == 0 ? bx : (d == 1 ? by : bz))) continue;
       const int ni = i + (d == 0), nj = j + (d == 1), nk = k + (d == 2);
       if (ni >= g.nx || nj >= g.ny || nk >= g.nz) continue;
       const T af = d == 0 ? a.x[g.face(0, ni, j, k)]
                           : (d == 1 ? a.y[g.face(1, i, nj, k)] : a.z[g.face(2, i, j, nk)]);
       if (!(af > T(0))) continue;
-      const int64_t nb = g.cell(ni, nj, nk);
-      const int ra = cc_find(lab, (int)c), rb = cc_find(lab, (int)nb);
-      if (ra != rb) {
-        atomicMin(lab + (ra > rb ? ra : rb), ra < rb ? ra : rb);
-        *changed = 1;
-      }
+      cc_union(lab, (int)c, (int)g.cell(ni, nj, nk));
     }
   }
 }
+
+__device__ __forceinline__ void cc_union(int *lab, int a, int b) {
+  int ra = cc_find_halve(lab, a), rb = cc_find_halve(lab, b);
+  while (ra != rb) {
+    if (ra > rb) {
+      const int t = ra;
+      ra = rb;
+      rb = t;
+    }
+    // hook the larger root rb under ra if rb is still a root
+    const int old = atomicCAS(lab + rb, rb, ra);
+    if (old == rb) return;
+    rb = cc_find_halve(lab, old);
+    ra = cc_find_halve(lab, ra);
+  }
+}
+
+
 
 __global__ void k_cc_compress(int64_t n, int *lab) {
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
@@ -168,26 +235,15 @@ template <class T>
 int Components::label(Ctx *ctx, const GridDev &g, Fields<T> alpha) {
   Launch L = ctx->launch();
   const int64_t n = g.ncell();
+  int h[2] = {0, 0};
   {
     ProfScope _ps(L, NF_K_GAUGE);
-    k_cc_init<T><<<cc_blocks(n), kBlock, 0, L.s>>>(g, alpha, lab);
-    ++*L.counter;
-  }
-  int h[2] = {0, 0};
-  for (int round = 0; round < kMaxRounds; ++round) {
-    cudaMemsetAsync(scal, 0, sizeof(int), L.s);
-    {
-      ProfScope _ps(L, NF_K_GAUGE);
-      k_cc_hook<T><<<cc_blocks(n), kBlock, 0, L.s>>>(g, alpha, lab, (int *)scal);
-      k_cc_compress<<<cc_blocks(n), kBlock, 0, L.s>>>(n, lab);
-      *L.counter += 2;
-    }
-    ctx->read_bytes(h, scal, sizeof(int));
-    if (h[0] == 0) break;
-    if (round == kMaxRounds - 1) {
-      set_error("component labelling did not converge");
-      return NF_E_NOT_CONVERGED;
-    }
+    const dim3 tiles((g.nx + kCcTile - 1) / kCcTile, (g.ny + kCcTile - 1) / kCcTile,
+                     (g.nz + kCcTile - 1) / kCcTile);
+    k_cc_tile<T><<<tiles, dim3(kCcTile, kCcTile, kCcTile), 0, L.s>>>(g, alpha, lab);
+    k_cc_merge<T><<<cc_blocks(n), kBlock, 0, L.s>>>(g, alpha, lab);
+    k_cc_compress<<<cc_blocks(n), kBlock, 0, L.s>>>(n, lab);
+    *L.counter += 3;
   }
   cudaMemsetAsync(ground, 0, n * sizeof(int), L.s);
   cudaMemsetAsync((int *)scal + 1, 0, sizeof(int), L.s);
