@@ -111,6 +111,8 @@ typedef struct nf_config {
                              and prolongation so the V-cycle stays symmetric.
                              w near 2 offsets the weak piecewise-constant
                              coarse space (over-correction)                 */
+  int mg_smooth_coarse;   /* sweeps on the levels below the finest (0: as
+                             mg_smooth)                                      */
 } nf_config;
 
 typedef struct nf_grid {
@@ -149,7 +151,7 @@ typedef struct nf_step_stats {
    max_iters 500, inner_tol 1e-3, mg_smooth 2, mg_coarsest 4, RK2,
    checkpoint_every 10, no budget, cfl_max 0 (no sub-stepping),
    mg_coarsest_sweeps 8, mg_band_sweeps 0, mg_transfer 1 (constant),
-   mg_coarse_weight 1.8. */
+   mg_coarse_weight 1.9, mg_smooth_coarse 0. */
 int nf_config_default(nf_config *cfg);
 
 /* Create a context on cfg->device. *out receives the handle. */

@@ -137,8 +137,8 @@ class Context:
     def __init__(self, precision="mixed", solver="mgpcg", tol=1e-6, max_iters=500,
                  inner_tol=1e-3, mg_smooth=2, mg_coarsest=4, advect_order=2,
                  checkpoint_every=10, hbm_budget=0, cfl_max=0.0, mg_coarsest_sweeps=8,
-                 mg_band_sweeps=0, mg_transfer="constant", mg_coarse_weight=1.8,
-                 device=0, stream=None):
+                 mg_band_sweeps=0, mg_transfer="constant", mg_coarse_weight=1.9,
+                 mg_smooth_coarse=0, device=0, stream=None):
         cfg = L.Config()
         _check(lib.nf_config_default(C.byref(cfg)))
         cfg.device = device
@@ -162,6 +162,7 @@ class Context:
         cfg.mg_band_sweeps = int(mg_band_sweeps)
         cfg.mg_transfer = {"trilinear": 0, "constant": 1}[mg_transfer]
         cfg.mg_coarse_weight = float(mg_coarse_weight)
+        cfg.mg_smooth_coarse = int(mg_smooth_coarse)
         self.precision = precision
         self.device = device
         self._h = C.c_void_p()

@@ -200,7 +200,8 @@ int nf_config_default(nf_config *cfg) {
   cfg->mg_coarsest_sweeps = 8;
   cfg->mg_band_sweeps = 0;
   cfg->mg_transfer = 1;
-  cfg->mg_coarse_weight = 1.8;
+  cfg->mg_coarse_weight = 1.9;
+  cfg->mg_smooth_coarse = 0;
   return NF_OK;
 }
 
@@ -233,7 +234,8 @@ int nf_create(nf_ctx **out, const nf_config *cfg) {
       cfg->checkpoint_every <= 0 || cfg->mg_smooth < 0 || !(cfg->cfl_max >= 0.0) ||
       cfg->mg_coarsest_sweeps < 0 || cfg->mg_band_sweeps < 0 ||
       (cfg->mg_transfer != 0 && cfg->mg_transfer != 1) ||
-      !(cfg->mg_coarse_weight >= 0.0 && cfg->mg_coarse_weight < 2.0)) {
+      !(cfg->mg_coarse_weight >= 0.0 && cfg->mg_coarse_weight < 2.0) ||
+      cfg->mg_smooth_coarse < 0) {
     set_error("nf_create: invalid configuration");
     return NF_E_INVALID;
   }
@@ -297,9 +299,14 @@ int nf_episode_create(nf_ctx *ctx, const nf_grid *g, const nf_scene *s,
     set_error("nf_episode_create: null argument");
     return NF_E_INVALID;
   }
+  // the kernels index face arrays with 32-bit integers
+  const int64_t max_faces = std::max({(int64_t)(g->nx + 1) * g->ny * g->nz,
+                                      (int64_t)g->nx * (g->ny + 1) * g->nz,
+                                      (int64_t)g->nx * g->ny * (g->nz + 1)});
   if (g->nx < 4 || g->ny < 4 || g->nz < 4 || !(g->dx > 0) || !(g->dt > 0) ||
-      (int64_t)g->nx * g->ny * g->nz > ((int64_t)1 << 31)) {
-    set_error("nf_episode_create: grid must have >= 4 cells per axis, dx > 0, dt > 0");
+      max_faces > (int64_t)INT32_MAX) {
+    set_error("nf_episode_create: grid must have >= 4 cells per axis, dx > 0, dt > 0 "
+              "and fewer than 2^31 faces per component");
     return NF_E_INVALID;
   }
   if (g->outlet && (g->outlet_j0 < 0 || g->outlet_k0 < 0 || g->outlet_w <= 0 ||

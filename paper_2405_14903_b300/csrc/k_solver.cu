@@ -256,35 +256,67 @@ __device__ __forceinline__ void gather7(Nb7<R> &g, const LevelView<TA> &lv,
   g.vc = (R)x[c];
 }
 
+// ------------------------------------------------------------ rows ------
+// Stencil kernels walk the grid by rows (j, k): one warp per row in a
+// grid-stride loop over rows, lanes along x. A row costs one integer
+// division; every face index follows from the cell index c with adds
+// (ax: c + row, ay: c + k nx, az: c) in 32-bit arithmetic (episodes are
+// limited to fewer than 2^31 faces per component).
+struct RowWalk {
+  int lane, warp, nwarps;
+  __device__ __forceinline__ RowWalk() {
+    lane = threadIdx.x & 31;
+    warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+  }
+};
+
+template <class R, class TA, class X>
+__device__ __forceinline__ void gather7r(Nb7<R> &g, const LevelView<TA> &lv,
+                                         const X *x, int i, int j, int k, int c,
+                                         int row) {
+  const int nx = lv.nx, nxy = lv.nx * lv.ny;
+  const int fy = c + k * nx;
+  g.xm = (R)ld(lv.ax + c + row);
+  g.xp = (R)ld(lv.ax + c + row + 1);
+  g.ym = (R)ld(lv.ay + fy);
+  g.yp = (R)ld(lv.ay + fy + nx);
+  g.zm = (R)ld(lv.az + c);
+  g.zp = (R)ld(lv.az + c + nxy);
+  g.vxm = i > 0 ? (R)x[c - 1] : R(0);
+  g.vxp = i < nx - 1 ? (R)x[c + 1] : R(0);
+  g.vym = j > 0 ? (R)x[c - nx] : R(0);
+  g.vyp = j < lv.ny - 1 ? (R)x[c + nx] : R(0);
+  g.vzm = k > 0 ? (R)x[c - nxy] : R(0);
+  g.vzp = k < lv.nz - 1 ? (R)x[c + nxy] : R(0);
+  g.vc = (R)x[c];
+}
+
+// Blocks of kBlock threads giving one warp per row (at most kRedBlocks * 8).
+inline unsigned row_blocks(int nrows) {
+  const unsigned w = kBlock / 32;
+  const unsigned b = (unsigned)((nrows + w - 1) / w);
+  return b < (unsigned)kRedBlocks * 8 ? b : (unsigned)kRedBlocks * 8;
+}
+
 // ------------------------------------------------------ outer residual -----
 template <class S, class T, class V>
 __global__ void k_residual_outer(LevelView<T> lv, const S *b, const S *x, S *r,
                                  V *rin, double scale, RedScratch rs,
                                  double *norm2) {
   double v[1] = {0.0};
-  const int64_t n = lv.ncell();
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  constexpr int U = kIlpStencil;
-  for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c0 < n;
-       c0 += U * stride) {
-    Nb7<double> g[U];
-    double bv[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t c = c0 + u * stride;
-      if (c >= n) break;
-      int i, j, k;
-      GridDev::decomp(c, lv.nx, lv.ny, i, j, k);
-      gather7(g[u], lv, x, i, j, k, c);
-      bv[u] = (double)b[c];
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t c = c0 + u * stride;
-      if (c >= n) break;
-      const double dg = g[u].diag();
+  const RowWalk w;
+  const int nrows = lv.ny * lv.nz;
+  for (int row = w.warp; row < nrows; row += w.nwarps) {
+    const int k = row / lv.ny, j = row - k * lv.ny;
+    const int base = row * lv.nx;
+    for (int i = w.lane; i < lv.nx; i += 32) {
+      const int c = base + i;
+      Nb7<double> g;
+      gather7r(g, lv, x, i, j, k, c, row);
+      const double dg = g.diag();
       double rv = 0.0;
-      if (dg > 0.0) rv = bv[u] - lv.c * (dg * g[u].vc - g[u].nb());
+      if (dg > 0.0) rv = (double)b[c] - lv.c * (dg * g.vc - g.nb());
       r[c] = (S)rv;
       if (rin) rin[c] = (V)(rv * scale);
       v[0] += rv * rv;
@@ -411,28 +443,20 @@ __global__ void k_apply_dot(LevelView<TA> lv, const V *d, V *q, CGState *st,
                             RedScratch rs) {
   if (stopped(st)) return;
   V p = V(0);
-  const int64_t n = lv.ncell();
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  constexpr int U = kIlpStencil;
-  for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c0 < n;
-       c0 += U * stride) {
-    Nb7<V> g[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t c = c0 + u * stride;
-      if (c >= n) break;
-      int i, j, k;
-      GridDev::decomp(c, lv.nx, lv.ny, i, j, k);
-      gather7(g[u], lv, d, i, j, k, c);
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t c = c0 + u * stride;
-      if (c >= n) break;
-      const V dg = g[u].diag();
-      const V qc = dg > V(0) ? V(lv.c) * (dg * g[u].vc - g[u].nb()) : V(0);
+  const RowWalk w;
+  const int nrows = lv.ny * lv.nz;
+  const V cc = V(lv.c);
+  for (int row = w.warp; row < nrows; row += w.nwarps) {
+    const int k = row / lv.ny, j = row - k * lv.ny;
+    const int base = row * lv.nx;
+    for (int i = w.lane; i < lv.nx; i += 32) {
+      const int c = base + i;
+      Nb7<V> g;
+      gather7r(g, lv, d, i, j, k, c, row);
+      const V dg = g.diag();
+      const V qc = dg > V(0) ? cc * (dg * g.vc - g.nb()) : V(0);
       q[c] = qc;
-      p += g[u].vc * qc;
+      p += g.vc * qc;
     }
   }
   double v[1] = {(double)p};
@@ -658,35 +682,22 @@ template <class V, class TA>
 __global__ void k_mg_smooth(LevelView<TA> lv, V *x, const V *b, int color,
                             const CGState *st) {
   if (stopped(st)) return;
+  const RowWalk w;
+  const int nrows = lv.ny * lv.nz;
   const int hx = (lv.nx + 1) >> 1;
-  const int64_t n = (int64_t)hx * lv.ny * lv.nz;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  constexpr int U = kIlpStencil;
   const V cc = V(lv.c);
-  for (int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t0 < n;
-       t0 += U * stride) {
-    Nb7<V> g[U];
-    V bv[U];
-    int64_t cell[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      cell[u] = -1;
-      const int64_t t = t0 + u * stride;
-      if (t >= n) break;
-      int ii, j, k;
-      GridDev::decomp(t, hx, lv.ny, ii, j, k);
-      const int i = 2 * ii + ((j + k + color) & 1);
+  for (int row = w.warp; row < nrows; row += w.nwarps) {
+    const int k = row / lv.ny, j = row - k * lv.ny;
+    const int base = row * lv.nx;
+    const int p = (j + k + color) & 1;
+    for (int m = w.lane; m < hx; m += 32) {
+      const int i = 2 * m + p;
       if (i >= lv.nx) continue;
-      const int64_t c = ((int64_t)k * lv.ny + j) * lv.nx + i;
-      cell[u] = c;
-      gather7(g[u], lv, x, i, j, k, c);
-      bv[u] = b[c];
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      if (cell[u] < 0) continue;
-      const V dg = g[u].diag();
-      x[cell[u]] = dg > V(0) ? (bv[u] + cc * g[u].nb()) / (cc * dg) : V(0);
+      const int c = base + i;
+      Nb7<V> g;
+      gather7r(g, lv, x, i, j, k, c, row);
+      const V dg = g.diag();
+      x[c] = dg > V(0) ? (b[c] + cc * g.nb()) / (cc * dg) : V(0);
     }
   }
 }
@@ -738,28 +749,18 @@ template <class V, class TA>
 __global__ void k_mg_residual(LevelView<TA> lv, const V *x, const V *b, V *r,
                               const float *pn, const CGState *st) {
   if (stopped(st)) return;
-  const int64_t n = lv.ncell();
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  constexpr int U = kIlpStencil;
-  for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c0 < n;
-       c0 += U * stride) {
-    Nb7<V> g[U];
-    V bv[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t c = c0 + u * stride;
-      if (c >= n) break;
-      int i, j, k;
-      GridDev::decomp(c, lv.nx, lv.ny, i, j, k);
-      gather7(g[u], lv, x, i, j, k, c);
-      bv[u] = b[c];
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t c = c0 + u * stride;
-      if (c >= n) break;
-      const V dg = g[u].diag();
-      const V rv = dg > V(0) ? bv[u] - V(lv.c) * (dg * g[u].vc - g[u].nb()) : V(0);
+  const RowWalk w;
+  const int nrows = lv.ny * lv.nz;
+  const V cc = V(lv.c);
+  for (int row = w.warp; row < nrows; row += w.nwarps) {
+    const int k = row / lv.ny, j = row - k * lv.ny;
+    const int base = row * lv.nx;
+    for (int i = w.lane; i < lv.nx; i += 32) {
+      const int c = base + i;
+      Nb7<V> g;
+      gather7r(g, lv, x, i, j, k, c, row);
+      const V dg = g.diag();
+      const V rv = dg > V(0) ? b[c] - cc * (dg * g.vc - g.nb()) : V(0);
       r[c] = pn ? rv * V(pn[c]) : rv;
     }
   }
@@ -770,12 +771,23 @@ __global__ void k_mg_restrict(int fnx, int fny, int fnz, int cnx, int cny,
                               int cnz, const V *rf, V *bc, int mode,
                               const CGState *st) {
   if (stopped(st)) return;
-  const int64_t n = (int64_t)cnx * cny * cnz;
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
-       c += (int64_t)gridDim.x * blockDim.x) {
-    int I, J, K;
-    GridDev::decomp(c, cnx, cny, I, J, K);
-    bc[c] = restrict_cell<V>(fnx, fny, fnz, cnx, cny, cnz, rf, I, J, K, mode);
+  const RowWalk w;
+  const int nrows = cny * cnz;
+  for (int row = w.warp; row < nrows; row += w.nwarps) {
+    const int K = row / cny, J = row - K * cny;
+    const int base = row * cnx;
+    for (int I = w.lane; I < cnx; I += 32) {
+      if (mode == kTransferConstant) {
+        // mean of the eight children (fine dims are twice the coarse ones)
+        const int f0 = ((2 * K) * fny + 2 * J) * fnx + 2 * I;
+        const int sy = fnx, sz = fnx * fny;
+        const V s = rf[f0] + rf[f0 + 1] + rf[f0 + sy] + rf[f0 + sy + 1] + rf[f0 + sz] +
+                    rf[f0 + sz + 1] + rf[f0 + sz + sy] + rf[f0 + sz + sy + 1];
+        bc[base + I] = V(0.125) * s;
+      } else {
+        bc[base + I] = restrict_cell<V>(fnx, fny, fnz, cnx, cny, cnz, rf, I, J, K, mode);
+      }
+    }
   }
 }
 
@@ -785,28 +797,23 @@ __global__ void k_mg_prolong(LevelView<TF> f, int cnx, int cny, int cnz,
                              const V *xc, V *xf, const float *pn, int mode,
                              const CGState *st) {
   if (stopped(st)) return;
-  const int64_t n = f.ncell();
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  constexpr int U = kIlpStencil;
-  for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c0 < n;
-       c0 += U * stride) {
-    bool act[U];
-    V add[U], xv[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t c = c0 + u * stride;
-      act[u] = false;
-      if (c >= n) break;
-      int i, j, k;
-      GridDev::decomp(c, f.nx, f.ny, i, j, k);
-      act[u] = six<float>(f, i, j, k).diag() > 0.f;
-      add[u] = prolong_cell<V>(cnx, cny, cnz, xc, i, j, k, mode);
-      if (pn) add[u] *= V(pn[c]);
-      xv[u] = xf[c];
+  const RowWalk w;
+  const int nrows = f.ny * f.nz;
+  const int nx = f.nx, nxy = f.nx * f.ny;
+  for (int row = w.warp; row < nrows; row += w.nwarps) {
+    const int k = row / f.ny, j = row - k * f.ny;
+    const int base = row * nx;
+    for (int i = w.lane; i < nx; i += 32) {
+      const int c = base + i;
+      const int fy = c + k * nx;
+      const float dg = (float)ld(f.ax + c + row) + (float)ld(f.ax + c + row + 1) +
+                       (float)ld(f.ay + fy) + (float)ld(f.ay + fy + nx) +
+                       (float)ld(f.az + c) + (float)ld(f.az + c + nxy);
+      if (!(dg > 0.f)) continue;
+      V add = prolong_cell<V>(cnx, cny, cnz, xc, i, j, k, mode);
+      if (pn) add *= V(pn[c]);
+      xf[c] += add;
     }
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (act[u]) xf[c0 + u * stride] = xv[u] + add[u];
   }
 }
 
@@ -1103,9 +1110,8 @@ void launch_mg_coarsen(const Launch &L, const LevelView<TI> &fine, int cnx,
 template <class V, class TA>
 void launch_mg_smooth(const Launch &L, const LevelView<TA> &lv, V *x,
                       const V *b, int color, const CGState *st, int kclass) {
-  const int64_t n = (int64_t)((lv.nx + 1) / 2) * lv.ny * lv.nz;
   ProfScope _ps(L, kclass);
-  k_mg_smooth<V, TA><<<gs_blocks(n), kBlock, 0, L.s>>>(lv, x, b, color, st);
+  k_mg_smooth<V, TA><<<row_blocks(lv.ny * lv.nz), kBlock, 0, L.s>>>(lv, x, b, color, st);
   ++*L.counter;
 }
 template <class TA>
@@ -1130,7 +1136,7 @@ template <class V, class TA>
 void launch_mg_residual(const Launch &L, const LevelView<TA> &lv, const V *x,
                         const V *b, V *r, const float *pn, const CGState *st) {
   ProfScope _ps(L, NF_K_MG_RESIDUAL);
-  k_mg_residual<V, TA><<<gs_blocks(lv.ncell()), kBlock, 0, L.s>>>(lv, x, b, r, pn, st);
+  k_mg_residual<V, TA><<<row_blocks(lv.ny * lv.nz), kBlock, 0, L.s>>>(lv, x, b, r, pn, st);
   ++*L.counter;
 }
 template <class V, class TA>
@@ -1138,7 +1144,7 @@ void launch_mg_restrict(const Launch &L, const LevelView<TA> &fine,
                         const LevelView<TA> &coarse, const V *rf, V *bc,
                         int mode, const CGState *st) {
   ProfScope _ps(L, NF_K_MG_RESTRICT);
-  k_mg_restrict<V><<<gs_blocks(coarse.ncell()), kBlock, 0, L.s>>>(
+  k_mg_restrict<V><<<row_blocks(coarse.ny * coarse.nz), kBlock, 0, L.s>>>(
       fine.nx, fine.ny, fine.nz, coarse.nx, coarse.ny, coarse.nz, rf, bc, mode, st);
   ++*L.counter;
 }
@@ -1147,7 +1153,7 @@ void launch_mg_prolong(const Launch &L, const LevelView<TF> &fine,
                        const LevelView<TC> &coarse, const V *xc, V *xf,
                        const float *pn, int mode, const CGState *st) {
   ProfScope _ps(L, NF_K_MG_PROLONG);
-  k_mg_prolong<V, TF><<<gs_blocks(fine.ncell()), kBlock, 0, L.s>>>(
+  k_mg_prolong<V, TF><<<row_blocks(fine.ny * fine.nz), kBlock, 0, L.s>>>(
       fine, coarse.nx, coarse.ny, coarse.nz, xc, xf, pn, mode, st);
   ++*L.counter;
 }

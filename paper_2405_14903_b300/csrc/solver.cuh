@@ -287,7 +287,7 @@ class Solver {
       ch.pn[l] = (const float *)levels_[l].pn;
     }
     ch.transfer = cfg_.mg_transfer;
-    ch.smooth = std::max(1, cfg_.mg_smooth);
+    ch.smooth = cfg_.mg_smooth_coarse > 0 ? cfg_.mg_smooth_coarse : std::max(1, cfg_.mg_smooth);
     ch.coarsest_sweeps = coarsest_sweeps();
     ch.smem_bytes = chain_smem_;
     return ch;
@@ -300,7 +300,8 @@ class Solver {
     Launch L = ctx_->launch();
     const int nl = (int)levels_.size();
     const int F = std::max(1, first_chain_);  // level 0 always on grid kernels
-    const int nu = std::max(1, cfg_.mg_smooth);
+    const int nu0 = std::max(1, cfg_.mg_smooth);
+    const int nuc = cfg_.mg_smooth_coarse > 0 ? cfg_.mg_smooth_coarse : nu0;
     const int down = std::min(F, nl - 1);     // levels with a coarser level
     for (int l = 0; l < down; ++l) {
       V *x = l == 0 ? z : (V *)levels_[l].x;
@@ -308,6 +309,7 @@ class Solver {
       const int64_t nc = (int64_t)levels_[l].nx * levels_[l].ny * levels_[l].nz;
       cudaMemsetAsync(x, 0, nc * sizeof(V), L.s);
       if (l == 0) band(x, b, 0, st);
+      const int nu = l == 0 ? nu0 : nuc;
       for (int s = 0; s < nu; ++s) {
         smooth(l, x, b, 0, st);
         smooth(l, x, b, 1, st);
@@ -346,6 +348,7 @@ class Solver {
         launch_mg_prolong<V, TA, TA>(L, viewc(l), viewc(l + 1),
                                      (const V *)levels_[l + 1].x, x, pnorm(l),
                                      cfg_.mg_transfer, st);
+      const int nu = l == 0 ? nu0 : nuc;
       for (int s = 0; s < nu; ++s) {
         smooth(l, x, b, 1, st);
         smooth(l, x, b, 0, st);
