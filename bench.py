@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--plain-rollout", type=int, default=10)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip FP64 comparison paths, e2e and the CPU baseline")
+    ap.add_argument("--tol", type=float, default=1e-6,
+                    help="relative residual of every projection (the metric's 1e-6)")
     ap.add_argument("--inner-tol", type=float, default=1e-3,
                     help="relative tolerance of each FP32 inner solve (MIXED refinement)")
     ap.add_argument("--mg-smooth", type=int, default=2,
@@ -173,7 +175,7 @@ def run_ours(args, rank, world, local_rank):
             import torch.distributed as dist
             dist.barrier()
 
-    ctx = P.Context("mixed", "mgpcg", tol=1e-6, max_iters=1000, checkpoint_every=10,
+    ctx = P.Context("mixed", "mgpcg", tol=args.tol, max_iters=1000, checkpoint_every=10,
                     cfl_max=cfg["cfl_max"], inner_tol=args.inner_tol,
                     mg_smooth=args.mg_smooth, mg_coarsest_sweeps=args.coarsest_sweeps,
                     mg_coarsest=args.mg_coarsest, mg_band_sweeps=args.band_sweeps,
@@ -240,8 +242,9 @@ def run_ours(args, rank, world, local_rank):
                                     "outflow loss; forward rollout + full adjoint",
                            grid=n, rollout_steps=T, checkpoint_every=10,
                            cfl_max=cfg["cfl_max"], substeps_executed=int(stats["fwd"]["steps"]),
-                           precision="FP32 MGPCG, BF16 coarse-level fractions, FP64 dots and "
-                                     "FP64 iterative refinement to rel res 1e-6",
+                           precision="FP32 MGPCG (V-cycle, CG vectors; BF16 coarse-level "
+                                     "fractions), FP32 per-thread dot partials summed in FP64, "
+                                     f"FP64 residual refinement to rel res {args.tol:g}",
                            inner_tol=args.inner_tol, mg_smooth=args.mg_smooth,
                            mg_coarsest=args.mg_coarsest, coarsest_sweeps=args.coarsest_sweeps,
                            band_sweeps=args.band_sweeps, mg_transfer=args.mg_transfer,

@@ -280,6 +280,82 @@ int nf_profile(nf_ctx *ctx, int kclass);
    nf_profile (synchronises the stream). */
 int nf_profile_read(nf_ctx *ctx, int kclass, int64_t *launches, double *ms);
 
+/* ----------------------------------------------------------- serving ---
+   A request loop over many concurrent gym-style episodes (one simulated
+   environment each, Sec. 3's environments behind a reset / step protocol),
+   for the pattern of serving many environments from one GPU: episodes stay
+   resident on the device, are admitted under an HBM budget, and their
+   requests run on `slots` worker streams at once, so a request that arrives
+   while others are on the GPU starts as soon as a slot and memory allow and
+   its kernels overlap theirs (continuous batching). Requests of one episode
+   run in submission order on the slot that opened it; results do not depend
+   on what else is in flight (the kernels are deterministic per episode).
+
+   Kinds:
+     NF_REQ_OPEN          create episode `episode` (a client-chosen key) from
+                          `grid` and `scene`, velocity at rest. Waits, queued,
+                          while the budget cannot hold it.
+     NF_REQ_STEP          advance `frames` frames (nf_step).
+     NF_REQ_STEP_ADJOINT  advance `frames` frames, then the loss `loss_kind`
+                          of the final velocity and dJ/dtheta by BPTT over
+                          the episode's whole rollout (nf_backward).
+     NF_REQ_CLOSE         destroy the episode; its memory returns to the
+                          budget and admits waiting OPENs (FIFO).
+   Budget: an OPEN reserves episode_estimate = the episode's base state plus
+   its rollout tape for checkpoint_every steps; after every request the
+   reservation follows the episode's actual bytes where they are larger.
+   Errors are per request (nf_result.status); a request for an unknown or
+   failed episode completes with NF_E_INVALID / NF_E_STATE. */
+typedef struct nf_server nf_server;
+
+#define NF_REQ_OPEN 0
+#define NF_REQ_STEP 1
+#define NF_REQ_STEP_ADJOINT 2
+#define NF_REQ_CLOSE 3
+
+typedef struct nf_request {
+  int kind;               /* NF_REQ_*                                         */
+  int64_t episode;        /* client key of the episode                        */
+  nf_grid grid;           /* OPEN                                             */
+  nf_scene scene;         /* OPEN (spheres: host array, copied at submit)     */
+  int frames;             /* STEP, STEP_ADJOINT                               */
+  int loss_kind;          /* STEP_ADJOINT: NF_LOSS_*                          */
+} nf_request;
+
+typedef struct nf_result {
+  int status;             /* NF_OK or the request's error                     */
+  int kind;
+  int64_t episode;
+  double loss;            /* STEP_ADJOINT                                     */
+  double g_theta[NF_MAX_PARAMS]; /* STEP_ADJOINT: dJ/dtheta                   */
+  nf_step_stats fwd, bwd; /* solver statistics of the step and the adjoint    */
+  double submit_ms, start_ms, end_ms; /* server clock, ms since creation     */
+  size_t episode_bytes;   /* device bytes of the episode after the request    */
+} nf_result;
+
+typedef struct nf_server_stats {
+  int64_t submitted, completed, open_waiting, episodes;
+  size_t bytes_reserved, bytes_peak, budget;
+  int slots;
+} nf_server_stats;
+
+/* cfg: precision, solver and tolerances of every episode (its device and
+   stream fields are ignored: each slot creates its own stream on
+   cfg->device). slots >= 1. hbm_budget: bytes of episode state (0: no
+   limit). */
+int nf_server_create(const nf_config *cfg, int slots, size_t hbm_budget,
+                     nf_server **out);
+/* Queue a request; *ticket identifies its result. Never blocks on the GPU. */
+int nf_server_submit(nf_server *srv, const nf_request *req, int64_t *ticket);
+/* Wait up to wait_ms (0: do not wait, < 0: forever) for a ticket's result;
+   NF_OK and the result (then forgotten by the server), or NF_E_TIMEOUT. */
+int nf_server_poll(nf_server *srv, int64_t ticket, int wait_ms, nf_result *out);
+/* Wait until every submitted request has completed (wait_ms as in poll). */
+int nf_server_drain(nf_server *srv, int wait_ms);
+int nf_server_stats_get(nf_server *srv, nf_server_stats *out);
+/* Stops the workers after their current request, destroys all episodes. */
+int nf_server_destroy(nf_server *srv);
+
 /* ---------------------------------------------------------- no-alloc ---
    nf_loss_noalloc: the loss of nf_loss (kinetic energy 1/2 sum u^2 dx^3, or
    the net flux sum u_x dx^2 through the outlet patch) and optionally dJ/dU,

@@ -7,8 +7,9 @@ paper_2405_14903_b300/build.py``): there is no CPU fallback.
 """
 
 from ._lib import LIB_PATH  # noqa: F401  (loads libnf.so or raises)
-from .api import Context, Episode, NFError, NotConvergedWarning, loss_noalloc  # noqa: F401
+from .api import Context, Episode, NFError, NotConvergedWarning, Server, loss_noalloc  # noqa: F401
 from .autograd import rollout_loss  # noqa: F401
 
-__all__ = ["Context", "Episode", "NFError", "NotConvergedWarning", "rollout_loss", "loss_noalloc",
+__all__ = ["Context", "Episode", "NFError", "NotConvergedWarning", "Server", "rollout_loss",
+           "loss_noalloc",
            "LIB_PATH"]

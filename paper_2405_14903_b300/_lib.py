@@ -66,6 +66,28 @@ class StepStats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Request(C.Structure):
+    _fields_ = [("kind", C.c_int), ("episode", C.c_int64), ("grid", Grid),
+                ("scene", Scene), ("frames", C.c_int), ("loss_kind", C.c_int)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int), ("kind", C.c_int), ("episode", C.c_int64),
+                ("loss", C.c_double), ("g_theta", C.c_double * MAX_PARAMS),
+                ("fwd", StepStats), ("bwd", StepStats),
+                ("submit_ms", C.c_double), ("start_ms", C.c_double),
+                ("end_ms", C.c_double), ("episode_bytes", C.c_size_t)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64),
+                ("open_waiting", C.c_int64), ("episodes", C.c_int64),
+                ("bytes_reserved", C.c_size_t), ("bytes_peak", C.c_size_t),
+                ("budget", C.c_size_t), ("slots", C.c_int)]
+
+
+REQ = {"open": 0, "step": 1, "step_adjoint": 2, "close": 3}
+
 P3 = C.c_void_p * 3          # a (x, y, z) triple of array pointers
 PP = C.POINTER(C.c_void_p)   # how a triple (or NULL) is passed
 _vp = C.c_void_p
@@ -99,6 +121,12 @@ SIGNATURES = [
     ("nf_launch_count", C.c_int, [_vp, C.POINTER(_i64)]),
     ("nf_profile", C.c_int, [_vp, C.c_int]),
     ("nf_profile_read", C.c_int, [_vp, C.c_int, C.POINTER(_i64), C.POINTER(C.c_double)]),
+    ("nf_server_create", C.c_int, [C.POINTER(Config), C.c_int, C.c_size_t, C.POINTER(_vp)]),
+    ("nf_server_submit", C.c_int, [_vp, C.POINTER(Request), C.POINTER(_i64)]),
+    ("nf_server_poll", C.c_int, [_vp, _i64, C.c_int, C.POINTER(Result)]),
+    ("nf_server_drain", C.c_int, [_vp, C.c_int]),
+    ("nf_server_stats_get", C.c_int, [_vp, C.POINTER(ServerStats)]),
+    ("nf_server_destroy", C.c_int, [_vp]),
 ]
 
 

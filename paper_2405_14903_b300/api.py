@@ -131,38 +131,44 @@ def loss_noalloc(kind, grid, u, gU=None, stream=None):
     return J.value
 
 
+def _config(precision="mixed", solver="mgpcg", tol=1e-6, max_iters=500,
+            inner_tol=1e-3, mg_smooth=2, mg_coarsest=4, advect_order=2,
+            checkpoint_every=10, hbm_budget=0, cfl_max=0.0, mg_coarsest_sweeps=8,
+            mg_band_sweeps=0, mg_transfer="constant", mg_coarse_weight=1.9,
+            mg_smooth_coarse=0, device=0, stream=0):
+    """An ``nf_config`` from keyword arguments (defaults of nf_config_default)."""
+    cfg = L.Config()
+    _check(lib.nf_config_default(C.byref(cfg)))
+    cfg.device = device
+    cfg.stream = stream
+    cfg.precision = L.PREC[precision]
+    cfg.solver = L.SOLVER[solver]
+    cfg.tol = tol
+    cfg.max_iters = max_iters
+    cfg.inner_tol = inner_tol
+    cfg.mg_smooth = mg_smooth
+    cfg.mg_coarsest = mg_coarsest
+    cfg.advect_order = advect_order
+    cfg.checkpoint_every = checkpoint_every
+    cfg.hbm_budget = int(hbm_budget)
+    cfg.cfl_max = float(cfl_max)
+    cfg.mg_coarsest_sweeps = int(mg_coarsest_sweeps)
+    cfg.mg_band_sweeps = int(mg_band_sweeps)
+    cfg.mg_transfer = {"trilinear": 0, "constant": 1}[mg_transfer]
+    cfg.mg_coarse_weight = float(mg_coarse_weight)
+    cfg.mg_smooth_coarse = int(mg_smooth_coarse)
+    return cfg
+
+
 class Context:
     """An ``nf_ctx``: one device, one stream, one precision/solver setting."""
 
-    def __init__(self, precision="mixed", solver="mgpcg", tol=1e-6, max_iters=500,
-                 inner_tol=1e-3, mg_smooth=2, mg_coarsest=4, advect_order=2,
-                 checkpoint_every=10, hbm_budget=0, cfl_max=0.0, mg_coarsest_sweeps=8,
-                 mg_band_sweeps=0, mg_transfer="constant", mg_coarse_weight=1.9,
-                 mg_smooth_coarse=0, device=0, stream=None):
-        cfg = L.Config()
-        _check(lib.nf_config_default(C.byref(cfg)))
-        cfg.device = device
+    def __init__(self, precision="mixed", solver="mgpcg", device=0, stream=None, **kw):
         if stream is None:
             stream = torch.cuda.current_stream(device).cuda_stream
             if not stream:
                 stream = L.CUDA_STREAM_LEGACY
-        cfg.stream = stream
-        cfg.precision = L.PREC[precision]
-        cfg.solver = L.SOLVER[solver]
-        cfg.tol = tol
-        cfg.max_iters = max_iters
-        cfg.inner_tol = inner_tol
-        cfg.mg_smooth = mg_smooth
-        cfg.mg_coarsest = mg_coarsest
-        cfg.advect_order = advect_order
-        cfg.checkpoint_every = checkpoint_every
-        cfg.hbm_budget = int(hbm_budget)
-        cfg.cfl_max = float(cfl_max)
-        cfg.mg_coarsest_sweeps = int(mg_coarsest_sweeps)
-        cfg.mg_band_sweeps = int(mg_band_sweeps)
-        cfg.mg_transfer = {"trilinear": 0, "constant": 1}[mg_transfer]
-        cfg.mg_coarse_weight = float(mg_coarse_weight)
-        cfg.mg_smooth_coarse = int(mg_smooth_coarse)
+        cfg = _config(precision=precision, solver=solver, device=device, stream=stream, **kw)
         self.precision = precision
         self.device = device
         self._h = C.c_void_p()
@@ -334,3 +340,82 @@ class Episode:
         n = C.c_int()
         _check(lib.nf_get_step(self._c, self.id, C.byref(n)), self._c)
         return n.value
+
+
+class Server:
+    """``nf_server``: continuous batching of many episodes over ``slots``
+    concurrent worker streams, admitted under ``hbm_budget`` bytes.
+
+    Episodes are named by client keys. ``open`` / ``step`` / ``close`` queue
+    requests and return tickets; ``poll`` returns a result dict (or None on
+    timeout). Keyword arguments configure every episode like ``Context``.
+    """
+
+    def __init__(self, slots=4, hbm_budget=0, device=0, **cfg_kw):
+        cfg = _config(device=device, stream=0, **cfg_kw)
+        h = C.c_void_p()
+        _check(lib.nf_server_create(C.byref(cfg), int(slots), int(hbm_budget), C.byref(h)),
+               C.c_void_p())
+        self._h = h
+        self._keep = {}
+
+    def _submit(self, req):
+        t = C.c_int64()
+        _check(lib.nf_server_submit(self._h, C.byref(req), C.byref(t)), C.c_void_p())
+        return t.value
+
+    def open(self, key, grid_desc, scene):
+        req = L.Request()
+        req.kind = L.REQ["open"]
+        req.episode = int(key)
+        req.grid = grid_struct(grid_desc)
+        sc, keep = scene_struct(scene)
+        req.scene = sc
+        t = self._submit(req)       # the server copies the sphere list
+        del keep
+        return t
+
+    def step(self, key, frames=1, adjoint=False, loss="outflow"):
+        req = L.Request()
+        req.kind = L.REQ["step_adjoint" if adjoint else "step"]
+        req.episode = int(key)
+        req.frames = int(frames)
+        req.loss_kind = L.LOSS[loss]
+        return self._submit(req)
+
+    def close(self, key):
+        req = L.Request()
+        req.kind = L.REQ["close"]
+        req.episode = int(key)
+        return self._submit(req)
+
+    def poll(self, ticket, wait_ms=-1):
+        r = L.Result()
+        st = lib.nf_server_poll(self._h, int(ticket), int(wait_ms), C.byref(r))
+        if st == L.NF_E_TIMEOUT:
+            return None
+        _check(st, C.c_void_p())
+        return dict(status=r.status, kind=r.kind, episode=r.episode, loss=r.loss,
+                    g_theta=np.array(r.g_theta[:]), fwd=r.fwd.as_dict(), bwd=r.bwd.as_dict(),
+                    submit_ms=r.submit_ms, start_ms=r.start_ms, end_ms=r.end_ms,
+                    episode_bytes=r.episode_bytes)
+
+    def drain(self, wait_ms=-1):
+        st = lib.nf_server_drain(self._h, int(wait_ms))
+        return st == L.NF_OK
+
+    def stats(self):
+        s = L.ServerStats()
+        _check(lib.nf_server_stats_get(self._h, C.byref(s)), C.c_void_p())
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def close_server(self):
+        if self._h:
+            lib.nf_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close_server()
+        except Exception:
+            pass

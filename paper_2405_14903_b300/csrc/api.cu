@@ -9,6 +9,7 @@
 #include <new>
 #include <string>
 
+#include "ctx.h"
 #include "episode.h"
 #include "util.h"
 
@@ -145,11 +146,6 @@ void Ctx::read_bytes(void *host, const void *dev, size_t n) {
 
 }  // namespace nf
 
-struct nf_ctx {
-  nf::Ctx c;
-  std::map<int64_t, std::unique_ptr<nf::EpisodeBase>> eps;
-  int64_t next_id = 1;
-};
 
 using nf::set_error;
 

@@ -288,6 +288,7 @@ class EpisodeImpl : public EpisodeBase {
         }
         ++n_;
         n_rev_ = n_;
+        init_reverted_ = false;  // a later backward covers the whole history
         seg_start_ = -1;  // a new step invalidates the cached segment
       }
       ++frames_;
@@ -339,6 +340,25 @@ class EpisodeImpl : public EpisodeBase {
       return state_err("backward: no recorded step to revert");
     for (int d = 0; d < 3; ++d)
       CKS(copy_in(comp(gU_, d), gU_final[d], g_.nface(d), dtype, mem));
+    return backward_from_gU(gU0, dtype, mem, g_theta, st);
+  }
+
+  int loss_backward(int kind, double *J, double *g_theta, nf_step_stats *st) override {
+    if (kind != NF_LOSS_KINETIC && kind != NF_LOSS_OUTFLOW)
+      return invalid("loss_backward: unknown kind %d", kind);
+    if (kind == NF_LOSS_OUTFLOW && !g_.outlet)
+      return invalid("loss_backward: outflow needs an outlet%s", "");
+    if (n_rev_ == 0 && !(init_proj_ && !init_reverted_))
+      return state_err("loss_backward: no recorded step to revert");
+    Launch L = ctx_->launch();
+    launch_loss<T>(L, g_, kind, cview(U_), mut(gU_), true, ctx_->rs, dscal_ + 1);
+    if (J) *J = ctx_->read_double(dscal_ + 1);
+    return backward_from_gU(nullptr, NF_F32, NF_MEM_DEVICE, g_theta, st);
+  }
+
+  // BPTT from dJ/dU^final already in gU_.
+  int backward_from_gU(void *const gU0[3], int dtype, int mem, double *g_theta,
+                       nf_step_stats *st) {
     nf_step_stats s{};
     double gth[kMaxParams] = {0};
     int worst = NF_OK;

@@ -21,6 +21,10 @@ class EpisodeBase {
   virtual int backward(const void *const gU_final[3], void *const gU0[3],
                        int dtype, int mem, double *g_theta,
                        nf_step_stats *st) = 0;
+  // The loss of the current velocity and dJ/dtheta by BPTT over the whole
+  // recorded rollout, with dJ/dU kept on the device.
+  virtual int loss_backward(int kind, double *J, double *g_theta,
+                            nf_step_stats *st) = 0;
   // which: 0 velocity, 1 advected velocity, 2 fractions
   virtual int get_faces(int which, void *const dst[3], int dtype, int mem) = 0;
   virtual int get_pressure(void *dst, int dtype, int mem) = 0;

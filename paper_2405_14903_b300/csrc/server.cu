@@ -1,0 +1,379 @@
+// Serving loop of many concurrent episodes (include/nf.h, "serving").
+//
+// Design: `slots` worker threads, each owning an nf_ctx (its own CUDA stream,
+// reduction scratch and captured solver graphs). An episode is bound to the
+// slot that admits it; its requests run there in submission order, while the
+// other slots run other episodes' requests at the same time on their own
+// streams, so the device overlaps their kernels. Admission: an OPEN reserves
+// an estimate of the episode's device bytes against the budget; OPENs that
+// do not fit wait in FIFO order (and so do the requests queued behind them)
+// until a CLOSE returns memory.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <functional>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <set>
+#include <thread>
+#include <vector>
+
+#include "ctx.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Job {
+  int64_t ticket = 0;
+  nf_request req{};
+  std::vector<double> spheres;  // owned copy of an OPEN's sphere list
+  double submit_ms = 0.0;
+};
+
+struct EpisodeRec {
+  int slot = -1;           // -1 until admitted
+  int64_t id = 0;          // episode id inside the slot's nf_ctx
+  bool created = false;
+  bool failed = false;
+  size_t estimate = 0;     // reservation made at admission
+  size_t reserved = 0;     // bytes currently held against the budget
+  std::deque<Job> waiting; // the OPEN and later requests, until admitted
+};
+
+struct Slot {
+  nf_ctx *ctx = nullptr;
+  std::deque<Job> queue;
+  std::condition_variable cv;
+  std::thread worker;
+  int pending = 0;         // queued + running requests
+};
+
+}  // namespace
+
+struct nf_server {
+  nf_config cfg{};
+  int device = 0;
+  size_t budget = 0, reserved = 0, peak = 0;
+  std::vector<std::unique_ptr<Slot>> slots;
+  std::map<int64_t, EpisodeRec> eps;
+  std::deque<int64_t> open_wait;
+  std::map<int64_t, nf_result> done;
+  std::set<int64_t> in_flight;
+  std::mutex mu;
+  std::condition_variable done_cv;
+  int64_t next_ticket = 1, submitted = 0, completed = 0;
+  bool stop = false;
+  Clock::time_point t0 = Clock::now();
+
+  double now_ms() const {
+    return std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+  }
+
+  size_t estimate(const nf_grid &g) const {
+    const size_t nf = (size_t)(g.nx + 1) * g.ny * g.nz + (size_t)g.nx * (g.ny + 1) * g.nz +
+                      (size_t)g.nx * g.ny * (g.nz + 1);
+    const size_t nc = (size_t)g.nx * g.ny * g.nz;
+    const size_t t = cfg.precision == NF_PREC_FP64 ? 8 : 4;
+    const size_t s = cfg.precision == NF_PREC_FP32 ? 4 : 8;
+    const size_t C = (size_t)std::max(1, cfg.checkpoint_every);
+    // base state + a segment's tape (U, U^, alpha, P per step) + checkpoints
+    return nf::episode_base_bytes(cfg, g) + (C + 2) * (3 * nf * t + nc * s);
+  }
+
+  // The slot with the fewest queued or running requests.
+  int pick_slot() const {
+    int best = 0;
+    for (int s = 1; s < (int)slots.size(); ++s)
+      if (slots[s]->pending < slots[best]->pending) best = s;
+    return best;
+  }
+
+  void enqueue(int s, Job &&job) {
+    slots[s]->queue.push_back(std::move(job));
+    slots[s]->pending += 1;
+    slots[s]->cv.notify_one();
+  }
+
+  bool fits(size_t bytes) const { return budget == 0 || reserved + bytes <= budget; }
+
+  void admit(int64_t key, EpisodeRec &rec) {
+    rec.slot = pick_slot();
+    rec.reserved = rec.estimate;
+    reserved += rec.reserved;
+    peak = std::max(peak, reserved);
+    while (!rec.waiting.empty()) {
+      enqueue(rec.slot, std::move(rec.waiting.front()));
+      rec.waiting.pop_front();
+    }
+    (void)key;
+  }
+
+  // Admit waiting OPENs in arrival order while the budget allows.
+  void admit_waiting() {
+    while (!open_wait.empty()) {
+      auto it = eps.find(open_wait.front());
+      if (it == eps.end()) {
+        open_wait.pop_front();
+        continue;
+      }
+      if (!fits(it->second.estimate)) break;
+      admit(it->first, it->second);
+      open_wait.pop_front();
+    }
+  }
+
+  void finish(int64_t ticket, const nf_result &res) {
+    done[ticket] = res;
+    in_flight.erase(ticket);
+    completed += 1;
+    done_cv.notify_all();
+  }
+
+  nf_result immediate(const Job &job, int status) const {
+    nf_result r{};
+    r.status = status;
+    r.kind = job.req.kind;
+    r.episode = job.req.episode;
+    r.submit_ms = r.start_ms = r.end_ms = job.submit_ms;
+    return r;
+  }
+
+  void work(int s);
+};
+
+void nf_server::work(int s) {
+  cudaSetDevice(device);
+  Slot &slot = *slots[s];
+  for (;;) {
+    Job job;
+    int64_t id = 0;
+    bool created = false, failed = false;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      slot.cv.wait(lk, [&] { return stop || !slot.queue.empty(); });
+      if (slot.queue.empty()) return;  // stop requested and nothing left
+      job = std::move(slot.queue.front());
+      slot.queue.pop_front();
+      auto it = eps.find(job.req.episode);
+      if (it != eps.end()) {
+        id = it->second.id;
+        created = it->second.created;
+        failed = it->second.failed;
+      }
+    }
+    nf_result res{};
+    res.kind = job.req.kind;
+    res.episode = job.req.episode;
+    res.submit_ms = job.submit_ms;
+    res.start_ms = now_ms();
+    size_t bytes = 0;
+    if (job.req.kind == NF_REQ_OPEN) {
+      nf_scene sc = job.req.scene;
+      sc.spheres = job.spheres.empty() ? nullptr : job.spheres.data();
+      res.status = nf_episode_create(slot.ctx, &job.req.grid, &sc, &id);
+      created = res.status == NF_OK;
+    } else if (failed || !created) {
+      res.status = NF_E_STATE;
+    } else if (job.req.kind == NF_REQ_STEP || job.req.kind == NF_REQ_STEP_ADJOINT) {
+      res.status = nf_step(slot.ctx, id, job.req.frames, &res.fwd);
+      if (job.req.kind == NF_REQ_STEP_ADJOINT &&
+          (res.status == NF_OK || res.status == NF_E_NOT_CONVERGED)) {
+        auto e = slot.ctx->eps.find(id);
+        const int rc = e == slot.ctx->eps.end()
+                           ? NF_E_STATE
+                           : e->second->loss_backward(job.req.loss_kind, &res.loss,
+                                                      res.g_theta, &res.bwd);
+        if (rc != NF_OK && res.status == NF_OK) res.status = rc;
+      }
+    } else if (job.req.kind == NF_REQ_CLOSE) {
+      res.status = nf_episode_destroy(slot.ctx, id);
+    } else {
+      res.status = NF_E_INVALID;
+    }
+    if (job.req.kind != NF_REQ_CLOSE && created) nf_episode_bytes(slot.ctx, id, &bytes);
+    nf_synchronize(slot.ctx);
+    res.end_ms = now_ms();
+    res.episode_bytes = bytes;
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      slot.pending -= 1;
+      auto it = eps.find(job.req.episode);
+      if (it != eps.end()) {
+        EpisodeRec &rec = it->second;
+        if (job.req.kind == NF_REQ_OPEN) {
+          rec.id = id;
+          rec.created = created;
+          rec.failed = !created;
+          if (rec.failed) {  // nothing stays resident: release the reservation
+            reserved -= std::min(reserved, rec.reserved);
+            rec.reserved = 0;
+          }
+        }
+        if (job.req.kind == NF_REQ_CLOSE) {
+          // memory returns to the budget
+          reserved -= std::min(reserved, rec.reserved);
+          eps.erase(it);
+        } else if (bytes > rec.reserved) {
+          reserved += bytes - rec.reserved;
+          rec.reserved = bytes;
+          peak = std::max(peak, reserved);
+        }
+        admit_waiting();
+      }
+      finish(job.ticket, res);
+    }
+  }
+}
+
+extern "C" int nf_server_create(const nf_config *cfg, int slots, size_t hbm_budget,
+                                nf_server **out) {
+  if (!cfg || !out || slots < 1 || slots > 64) {
+    nf::set_error("nf_server_create: need a config, an output and 1..64 slots");
+    return NF_E_INVALID;
+  }
+  *out = nullptr;
+  auto srv = std::make_unique<nf_server>();
+  srv->cfg = *cfg;
+  srv->device = cfg->device;
+  srv->budget = hbm_budget;
+  for (int s = 0; s < slots; ++s) {
+    nf_config c = *cfg;
+    c.stream = nullptr;  // every slot runs on a stream of its own
+    auto slot = std::make_unique<Slot>();
+    const int rc = nf_create(&slot->ctx, &c);
+    if (rc != NF_OK) {
+      for (auto &p : srv->slots) nf_destroy(p->ctx);
+      return rc;
+    }
+    srv->slots.push_back(std::move(slot));
+  }
+  for (int s = 0; s < slots; ++s)
+    srv->slots[s]->worker = std::thread(&nf_server::work, srv.get(), s);
+  *out = srv.release();
+  return NF_OK;
+}
+
+extern "C" int nf_server_submit(nf_server *srv, const nf_request *req, int64_t *ticket) {
+  if (!srv || !req || !ticket) {
+    nf::set_error("nf_server_submit: null argument");
+    return NF_E_INVALID;
+  }
+  Job job;
+  job.req = *req;
+  if (req->kind == NF_REQ_OPEN && req->scene.kind == NF_SCENE_SPHERES &&
+      req->scene.nspheres > 0) {
+    if (!req->scene.spheres) {
+      nf::set_error("nf_server_submit: spheres scene without a sphere list");
+      return NF_E_INVALID;
+    }
+    job.spheres.assign(req->scene.spheres, req->scene.spheres + 4 * req->scene.nspheres);
+  }
+  job.req.scene.spheres = nullptr;
+  std::lock_guard<std::mutex> lk(srv->mu);
+  if (srv->stop) return NF_E_STATE;
+  job.ticket = srv->next_ticket++;
+  job.submit_ms = srv->now_ms();
+  *ticket = job.ticket;
+  srv->submitted += 1;
+  srv->in_flight.insert(job.ticket);
+  const int64_t key = req->episode;
+  auto it = srv->eps.find(key);
+  if (req->kind == NF_REQ_OPEN) {
+    if (it != srv->eps.end()) {
+      srv->finish(job.ticket, srv->immediate(job, NF_E_INVALID));
+      return NF_OK;
+    }
+    EpisodeRec rec;
+    rec.estimate = srv->estimate(req->grid);
+    if (srv->budget && rec.estimate > srv->budget) {
+      srv->finish(job.ticket, srv->immediate(job, NF_E_OOM));
+      return NF_OK;
+    }
+    EpisodeRec &r = srv->eps.emplace(key, std::move(rec)).first->second;
+    r.waiting.push_back(std::move(job));
+    if (srv->open_wait.empty() && srv->fits(r.estimate))
+      srv->admit(key, r);
+    else
+      srv->open_wait.push_back(key);
+    return NF_OK;
+  }
+  if (req->kind != NF_REQ_STEP && req->kind != NF_REQ_STEP_ADJOINT &&
+      req->kind != NF_REQ_CLOSE) {
+    srv->finish(job.ticket, srv->immediate(job, NF_E_INVALID));
+    return NF_OK;
+  }
+  if (it == srv->eps.end()) {
+    srv->finish(job.ticket, srv->immediate(job, NF_E_INVALID));
+    return NF_OK;
+  }
+  if (it->second.slot < 0)
+    it->second.waiting.push_back(std::move(job));
+  else
+    srv->enqueue(it->second.slot, std::move(job));
+  return NF_OK;
+}
+
+static bool wait_for(nf_server *srv, std::unique_lock<std::mutex> &lk, int wait_ms,
+                     const std::function<bool()> &ready) {
+  if (wait_ms < 0) {
+    srv->done_cv.wait(lk, ready);
+    return true;
+  }
+  return srv->done_cv.wait_for(lk, std::chrono::milliseconds(wait_ms), ready);
+}
+
+extern "C" int nf_server_poll(nf_server *srv, int64_t ticket, int wait_ms, nf_result *out) {
+  if (!srv || !out) {
+    nf::set_error("nf_server_poll: null argument");
+    return NF_E_INVALID;
+  }
+  std::unique_lock<std::mutex> lk(srv->mu);
+  if (!srv->done.count(ticket) && !srv->in_flight.count(ticket)) {
+    nf::set_error("nf_server_poll: unknown or already collected ticket");
+    return NF_E_INVALID;
+  }
+  if (!wait_for(srv, lk, wait_ms, [&] { return srv->done.count(ticket) > 0; }))
+    return NF_E_TIMEOUT;
+  *out = srv->done[ticket];
+  srv->done.erase(ticket);
+  return NF_OK;
+}
+
+extern "C" int nf_server_drain(nf_server *srv, int wait_ms) {
+  if (!srv) return NF_E_INVALID;
+  std::unique_lock<std::mutex> lk(srv->mu);
+  return wait_for(srv, lk, wait_ms, [&] { return srv->completed == srv->submitted; })
+             ? NF_OK
+             : NF_E_TIMEOUT;
+}
+
+extern "C" int nf_server_stats_get(nf_server *srv, nf_server_stats *out) {
+  if (!srv || !out) return NF_E_INVALID;
+  std::lock_guard<std::mutex> lk(srv->mu);
+  out->submitted = srv->submitted;
+  out->completed = srv->completed;
+  out->open_waiting = (int64_t)srv->open_wait.size();
+  out->episodes = (int64_t)srv->eps.size();
+  out->bytes_reserved = srv->reserved;
+  out->bytes_peak = srv->peak;
+  out->budget = srv->budget;
+  out->slots = (int)srv->slots.size();
+  return NF_OK;
+}
+
+extern "C" int nf_server_destroy(nf_server *srv) {
+  if (!srv) return NF_E_INVALID;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->stop = true;
+    for (auto &s : srv->slots) s->cv.notify_all();
+  }
+  for (auto &s : srv->slots)
+    if (s->worker.joinable()) s->worker.join();
+  for (auto &s : srv->slots) nf_destroy(s->ctx);
+  delete srv;
+  return NF_OK;
+}

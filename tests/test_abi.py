@@ -87,10 +87,28 @@ def test_struct_layouts_match_the_header(tmp_path):
     if gcc is None:
         pytest.skip("no host C compiler")
     src = tmp_path / "sz.c"
-    src.write_text('#include <stdio.h>\n#include "nf.h"\nint main(void){printf("%zu %zu %zu %zu", '
-                   'sizeof(nf_config), sizeof(nf_grid), sizeof(nf_scene), sizeof(nf_step_stats));return 0;}\n')
+    src.write_text('#include <stdio.h>\n#include "nf.h"\nint main(void){printf("%zu %zu %zu %zu %zu %zu %zu", '
+                   'sizeof(nf_config), sizeof(nf_grid), sizeof(nf_scene), sizeof(nf_step_stats), '
+                   'sizeof(nf_request), sizeof(nf_result), sizeof(nf_server_stats));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.check_call([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     sizes = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     assert sizes == [ctypes.sizeof(_lib.Config), ctypes.sizeof(_lib.Grid),
-                     ctypes.sizeof(_lib.Scene), ctypes.sizeof(_lib.StepStats)]
+                     ctypes.sizeof(_lib.Scene), ctypes.sizeof(_lib.StepStats),
+                     ctypes.sizeof(_lib.Request), ctypes.sizeof(_lib.Result),
+                     ctypes.sizeof(_lib.ServerStats)]
+
+
+def test_server_rejects_bad_arguments_without_a_device(lib):
+    from paper_2405_14903_b300 import _lib
+    cfg = _lib.Config()
+    lib.nf_config_default(ctypes.byref(cfg))
+    h = ctypes.c_void_p()
+    assert lib.nf_server_create(None, 2, 0, ctypes.byref(h)) == _lib.NF_E_INVALID
+    assert lib.nf_server_create(ctypes.byref(cfg), 0, 0, ctypes.byref(h)) == _lib.NF_E_INVALID
+    assert lib.nf_server_create(ctypes.byref(cfg), 65, 0, ctypes.byref(h)) == _lib.NF_E_INVALID
+    assert lib.nf_server_submit(None, None, None) == _lib.NF_E_INVALID
+    r = _lib.Result()
+    assert lib.nf_server_poll(None, 1, 0, ctypes.byref(r)) == _lib.NF_E_INVALID
+    assert lib.nf_server_drain(None, 0) == _lib.NF_E_INVALID
+    assert lib.nf_server_destroy(None) == _lib.NF_E_INVALID
