@@ -288,8 +288,10 @@ int nf_profile_read(nf_ctx *ctx, int kclass, int64_t *launches, double *ms);
    requests run on `slots` worker streams at once, so a request that arrives
    while others are on the GPU starts as soon as a slot and memory allow and
    its kernels overlap theirs (continuous batching). Requests of one episode
-   run in submission order on the slot that opened it; results do not depend
-   on what else is in flight (the kernels are deterministic per episode).
+   run in submission order on the slot that opened it; its forward results
+   do not depend on what else is in flight (bitwise: the forward kernels are
+   deterministic), its gradients only to rounding (the advection adjoint
+   scatters with float atomics).
 
    Kinds:
      NF_REQ_OPEN          create episode `episode` (a client-chosen key) from

@@ -1,9 +1,11 @@
 """The serving loop (nf_server): continuous batching over concurrent slots.
 
-Each episode's result must be the same alone and in the mix (bitwise: the
-kernels of one episode are deterministic whatever else runs on the device)
-and the same as through the direct episode API; admission must respect the
-HBM budget; bad requests fail alone.
+Each episode's result must be the same alone and in the mix: the forward
+(loss, solver iterations) bitwise, since its kernels are deterministic
+whatever else runs on the device; the gradient to rounding (the advection
+adjoint scatters with float atomics, whose order varies from run to run even
+alone). Results must also match the direct episode API; admission must
+respect the HBM budget; bad requests fail alone.
 """
 
 import numpy as np
@@ -22,14 +24,14 @@ def _episodes():
     for key, (kind, n) in enumerate([("sphere", 16), ("chamber", 16), ("plate", 16),
                                      ("sphere", 24), ("chamber", 24), ("plate", 20)]):
         if kind == "sphere":
-            cfg = I.config_sphere(n, steps=0)
+            cfg = I.config_sphere(n)
             cfg["scene"] = dict(cfg["scene"], theta=[0.1 + 0.01 * key, 0.02, -0.01])
             loss = "kinetic_energy"
         elif kind == "chamber":
-            cfg = I.config_chamber(n, steps=0, seed=key, duct_half_cells=2)
+            cfg = I.config_chamber(n, seed=key, duct_half_cells=2)
             loss = "outflow"
         else:
-            cfg = I.config_plate(n, steps=0, seed=key)
+            cfg = I.config_plate(n, seed=key)
             loss = "kinetic_energy"
         out.append(dict(key=100 + key, grid=cfg["grid"], scene=cfg["scene"], loss=loss))
     return out
@@ -79,8 +81,9 @@ def test_each_result_is_the_same_alone_and_in_the_mix(nf):
         assert all(r["status"] == 0 for r in res), res
         a, m = alone[ep["key"]], res[2]
         assert m["loss"] == a["loss"]
-        assert np.array_equal(m["g_theta"], a["g_theta"])
         assert m["fwd"]["iters"] == a["fwd"]["iters"]
+        g_a = np.asarray(a["g_theta"])
+        assert np.linalg.norm(m["g_theta"] - g_a) <= 1e-6 * np.linalg.norm(g_a)
     # requests of different episodes were on the device at the same time
     spans = sorted((r["start_ms"], r["end_ms"]) for res in mixed.values() for r in res)
     for (s0, e0), (s1, e1) in zip(spans, spans[1:]):
@@ -102,7 +105,7 @@ def test_served_result_matches_the_direct_api(nf):
     ctx.close()
     K = len(ep["scene"]["theta"])
     assert res[2]["loss"] == J
-    np.testing.assert_allclose(res[2]["g_theta"][:K], gth, rtol=1e-12, atol=0)
+    assert np.linalg.norm(res[2]["g_theta"][:K] - gth) <= 1e-6 * np.linalg.norm(gth)
 
 
 def test_admission_waits_for_memory_and_respects_the_budget(nf):
