@@ -72,6 +72,15 @@ def parse():
                     help="scale of the coarse-grid correction")
     ap.add_argument("--mg-coarsest", type=int, default=4,
                     help="stop coarsening at this many cells per edge")
+    ap.add_argument("--workload", default="rollout", choices=["rollout", "serving"],
+                    help="rollout: the chamber fwd+adjoint metric; serving: the episode mix")
+    ap.add_argument("--serve-count", type=int, default=512, help="episodes in the serving mix")
+    ap.add_argument("--serve-rate", type=float, default=0.03,
+                    help="Poisson arrival rate of episodes (per ms)")
+    ap.add_argument("--serve-requests", type=int, default=2,
+                    help="step requests per episode (one frame each)")
+    ap.add_argument("--serve-slots", type=int, default=8, help="concurrent worker slots")
+    ap.add_argument("--serve-budget-gb", type=float, default=150.0, help="admission budget")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-n", type=int, default=64,
                     help="grid of the bounded CPU oracle sample")
@@ -377,6 +386,91 @@ def cpu_baseline(args):
                 seconds=dt)
 
 
+# -------------------------------------------------------------- serving ----
+
+def _serve_episode(kind, n, seed):
+    """Grid, scene and loss of one episode of the mix (configs 1-3 scenes)."""
+    rng = np.random.default_rng(seed)
+    if kind == "sphere":
+        cfg = I.config_sphere(n)
+        v = (0.1 + 0.05 * rng.uniform(-1, 1), 0.05 * rng.uniform(-1, 1), 0.05 * rng.uniform(-1, 1))
+        cfg["scene"] = I.sphere_scene(v=v)
+        return cfg["grid"], cfg["scene"], "kinetic_energy"
+    if kind == "chamber":
+        cfg = chamber(n, 100, seed % (1 << 16))
+        return cfg["grid"], cfg["scene"], "outflow"
+    cfg = I.config_plate(n, seed=seed % (1 << 16))
+    return cfg["grid"], cfg["scene"], "kinetic_energy"
+
+
+def _serve_run(P, plan, slots, budget):
+    srv = P.Server(slots=slots, hbm_budget=budget, precision="mixed", tol=1e-6,
+                   max_iters=1000, cfl_max=8.0, checkpoint_every=10)
+    tickets = []
+    t0 = time.perf_counter()
+    for ep in plan:
+        wait = ep["arrival_ms"] / 1e3 - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        ts = [srv.open(ep["key"], ep["grid"], ep["scene"])]
+        ts += [srv.step(ep["key"], frames=1, adjoint=a, loss=ep["loss"]) for a in ep["adjoint"]]
+        ts.append(srv.close(ep["key"]))
+        tickets.append((ep, ts))
+    srv.drain()
+    wall = time.perf_counter() - t0
+    stats = srv.stats()
+    lat = {"step": [], "step_adjoint": []}
+    cell_frames, failed = 0, 0
+    for ep, ts in tickets:
+        res = [srv.poll(t) for t in ts]
+        failed += sum(1 for r in res if r["status"] not in (0, 3))
+        for r, a in zip(res[1:-1], ep["adjoint"]):
+            lat["step_adjoint" if a else "step"].append(r["end_ms"] - r["submit_ms"])
+            cell_frames += ep["cells"]
+    srv.close_server()
+    every = lat["step"] + lat["step_adjoint"]
+    pct = lambda v, q: float(np.percentile(v, q)) if v else None  # noqa: E731
+    return dict(value=cell_frames / wall, unit="cell-frames/s", wall_s=wall,
+                requests=len(every), failed=failed,
+                p50_ms=pct(every, 50), p99_ms=pct(every, 99),
+                step_p50_ms=pct(lat["step"], 50), step_p99_ms=pct(lat["step"], 99),
+                adjoint_p50_ms=pct(lat["step_adjoint"], 50),
+                adjoint_p99_ms=pct(lat["step_adjoint"], 99),
+                slots=slots, bytes_peak=int(stats["bytes_peak"]))
+
+
+def run_serving(args):
+    """Config 5: Poisson arrivals of episodes (grid sizes 32..192, scenes of
+    configs 1-3), each issuing one-frame step requests of which a seeded 30 %
+    carry the adjoint, then closing; the same schedule served with `slots`
+    concurrent slots and one episode at a time."""
+    import torch
+    import paper_2405_14903_b300 as P
+    torch.cuda.set_device(0)
+    mix = I.serving_mix(seed=0, count=args.serve_count, rate_per_ms=args.serve_rate)
+    rng = np.random.default_rng(12345)
+    plan = []
+    for key, m in enumerate(mix):
+        grid, scene, loss = _serve_episode(m["scene_kind"], m["n"], m["seed"])
+        plan.append(dict(key=key, arrival_ms=m["arrival_ms"], grid=grid, scene=scene, loss=loss,
+                         cells=m["n"] ** 3,
+                         adjoint=[bool(x) for x in rng.uniform(size=args.serve_requests) < 0.3]))
+    budget = int(args.serve_budget_gb * 1e9)
+    ours = _serve_run(P, plan, args.serve_slots, budget)
+    one = _serve_run(P, plan, 1, budget)
+    return dict(metric="served cell-frames/s, serving mix (p50/p99 request latency)",
+                value=ours["value"], unit="cell-frames/s", n_gpus=1, steps=1, warmup=0,
+                ms_per_step=1e3 * ours["wall_s"], higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f32", data="synthetic",
+                config=dict(workload=f"{args.serve_count} episodes, Poisson arrivals at "
+                                     f"{args.serve_rate}/ms, grids 32-192^3, sphere/chamber/"
+                                     f"plate scenes, {args.serve_requests} one-frame requests "
+                                     "per episode, 30 % with adjoint, MIXED MGPCG 1e-6",
+                            slots=args.serve_slots, budget_gb=args.serve_budget_gb),
+                p50_ms=ours["p50_ms"], p99_ms=ours["p99_ms"], served=ours,
+                one_episode_at_a_time=one)
+
+
 def run_reference(args, rank):
     if rank != 0:
         return None
@@ -407,6 +501,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         out = run_reference(args, rank)
+    elif args.workload == "serving":
+        out = run_serving(args) if rank == 0 else None
     else:
         if world > 1:
             import torch

@@ -27,11 +27,14 @@ int cuda_fail(cudaError_t e, const char *what) {
 int Alloc::get(void **p, size_t n) {
   *p = nullptr;
   if (n == 0) n = 16;
-  const cudaError_t e = cudaMalloc(p, n);
+  // stream-ordered: unlike cudaMalloc / cudaFree this never synchronises
+  // the device, so episodes created or destroyed while others run (the
+  // serving slots) do not stall the other streams
+  const cudaError_t e = cudaMallocAsync(p, n, stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
-    return cuda_fail(e, "cudaMalloc");
+    return cuda_fail(e, "cudaMallocAsync");
   }
   ptrs.push_back(*p);
   bytes += n;
@@ -39,7 +42,7 @@ int Alloc::get(void **p, size_t n) {
 }
 
 void Alloc::free_all() {
-  for (void *p : ptrs) cudaFree(p);
+  for (void *p : ptrs) cudaFreeAsync(p, stream);
   ptrs.clear();
   bytes = 0;
 }
@@ -244,6 +247,16 @@ int nf_create(nf_ctx **out, const nf_config *cfg) {
   if (e != cudaSuccess) {
     delete ctx;
     return nf::cuda_fail(e, "cudaSetDevice");
+  }
+  {
+    // episode memory comes from this process's default pool of the device
+    // (stream-ordered); keep freed blocks for reuse instead of returning
+    // them at every synchronisation
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, cfg->device) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
   }
   if (cfg->stream) {
     ctx->c.stream = (cudaStream_t)cfg->stream;

@@ -153,6 +153,7 @@ class EpisodeImpl : public EpisodeBase {
  public:
   EpisodeImpl(Ctx *ctx, const nf_grid &gr, const nf_scene &sc)
       : ctx_(ctx), g_(make_grid(gr)), sc_(sc), solver_(ctx, make_grid(gr), ctx->cfg) {
+    A_.stream = ctx->stream;
     sc_.K = scene_K(sc.kind);
     sc_.spheres = nullptr;
   }
@@ -192,8 +193,9 @@ class EpisodeImpl : public EpisodeBase {
     CKS(A_.get(&dscal_, 64 * sizeof(double)));
     if (sc.kind == NF_SCENE_SPHERES && sc.nspheres > 0) {
       CKS(A_.get(&dsph_, (size_t)sc.nspheres * 4 * sizeof(double)));
-      CKC(cudaMemcpy(dsph_, sc.spheres, (size_t)sc.nspheres * 4 * sizeof(double),
-                     cudaMemcpyHostToDevice));
+      CKC(cudaMemcpyAsync(dsph_, sc.spheres, (size_t)sc.nspheres * 4 * sizeof(double),
+                          cudaMemcpyHostToDevice, ctx_->stream));
+      CKC(cudaStreamSynchronize(ctx_->stream));  // the host list is the caller's
     }
     CKS(solver_.init(A_));
     CKS(cc_.init(A_, ncell_));

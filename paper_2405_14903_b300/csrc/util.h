@@ -76,10 +76,13 @@ struct Ctx {
   void read_bytes(void *host, const void *dev, size_t n);
 };
 
-// Device allocations of one owner (an episode); freed together.
+// Device allocations of one owner (an episode), stream-ordered on `stream`
+// (the owner's stream: memory is used in that stream's order); freed
+// together.
 struct Alloc {
   std::vector<void *> ptrs;
   size_t bytes = 0;
+  cudaStream_t stream = nullptr;
   int get(void **p, size_t n);
   template <class P>
   int get(P **p, size_t n) {
