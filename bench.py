@@ -72,7 +72,7 @@ def parse():
                     help="scale of the coarse-grid correction")
     ap.add_argument("--mg-coarsest", type=int, default=4,
                     help="stop coarsening at this many cells per edge")
-    ap.add_argument("--workload", default="rollout", choices=["rollout", "serving"],
+    ap.add_argument("--workload", default="rollout", choices=["rollout", "serving", "precision"],
                     help="rollout: the chamber fwd+adjoint metric; serving: the episode mix")
     ap.add_argument("--serve-count", type=int, default=512, help="episodes in the serving mix")
     ap.add_argument("--serve-rate", type=float, default=0.03,
@@ -471,6 +471,78 @@ def run_serving(args):
                 one_episode_at_a_time=one)
 
 
+# ------------------------------------------------------------ precision ----
+
+# kernel classes of the pressure solve (everything but geometry, advection,
+# right-hand side, update, labelling and gauge)
+SOLVER_CLASSES = ("residual64", "axpy64", "cg_init", "apply_dot", "cg_xr", "cg_rz", "cg_d",
+                  "mg_coarsen", "mg_smooth", "mg_residual", "mg_restrict", "mg_prolong",
+                  "mg_chain", "mg_smooth0")
+
+
+def run_precision(args):
+    """Config 4: one projection of a divergent N(0, 1) velocity around 64 static
+    spheres at 256^3, to relative residual 1e-8, by FP64 MGPCG, FP32 MGPCG and
+    MIXED (FP32 CG, BF16-coarse V-cycle, FP64 refinement). The velocity error
+    is measured against FP64 MGPCG to 1e-12 (the oracle's unpreconditioned CG
+    does not finish at this size; FP64 MGPCG is pinned to it at small sizes)."""
+    import torch
+    import paper_2405_14903_b300 as P
+    torch.cuda.set_device(0)
+    n = args.n if args.n != 128 else 256
+    cfg = I.config_spheres(n, tol=1e-8)
+    u0 = [torch.tensor(x, device="cuda", dtype=torch.float64) for x in cfg["u0"]]
+
+    def project(precision, tol):
+        ctx = P.Context(precision, "mgpcg", tol=tol, max_iters=5000)
+        ep = ctx.episode(cfg["grid"], cfg["scene"])
+        ep.set_velocity(u0, project=False)         # warm the solver (graphs, pools)
+        ep.set_velocity(u0, project=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s = torch.cuda.current_stream()
+        ctx.profile("all")
+        e0.record(s)
+        st = ep.set_velocity(u0, project=True)
+        e1.record(s)
+        torch.cuda.synchronize()
+        solve_ms = sum(ctx.profile_read(k)[1] for k in SOLVER_CLASSES)
+        ctx.profile(None)
+        u = [x.double() for x in ep.velocity(dtype=torch.float64)]
+        ep.close()
+        ctx.close()
+        return dict(st, solve_ms=solve_ms), e0.elapsed_time(e1), u
+
+    st_ref, _, u_ref = project("fp64", 1e-12)
+    ref_norm = float(torch.sqrt(sum((x * x).sum() for x in u_ref)))
+    ncell = n ** 3
+    variants = {}
+    for name, prec in (("fp64_mgpcg", "fp64"), ("fp32_mgpcg", "fp32"), ("mixed", "mixed")):
+        st, ms, u = project(prec, 1e-8)
+        err = float(torch.sqrt(sum(((a - b) ** 2).sum() for a, b in zip(u, u_ref)))) / ref_norm
+        vb = 8 if prec == "fp64" else 4
+        # algorithmic bytes of one PCG iteration: apply (d, 3 fractions, q),
+        # CG updates (x, r, d, q, z) and one V-cycle (4 fine sweeps of 18,
+        # residual 20, restrict 4.5, prolong 8, coarse levels x 8/7)
+        it_bytes = ncell * (vb * 5 + vb * 2 * 5 + (4 * 18 + 20 + 4.5 + 8) * vb / 4 * 8 / 7)
+        variants[name] = dict(iterations=st["iters"], outer=st["outer"],
+                              velocity_norm=float(torch.sqrt(sum((x * x).sum() for x in u))),
+                              rel_residual=st["rel_residual"], projection_ms=ms,
+                              solve_kernel_ms=st["solve_ms"],
+                              achieved_gbs=it_bytes * st["iters"] / (st["solve_ms"] / 1e3) / 1e9,
+                              velocity_rel_err=err,
+                              converged=st["rel_residual"] <= 1e-8)
+    return dict(metric="single projection at 256^3 to rel res 1e-8 (config 4)",
+                value=variants["mixed"]["solve_kernel_ms"], unit="ms", n_gpus=1, steps=1,
+                warmup=1, ms_per_step=variants["mixed"]["projection_ms"], higher_is_better=False,
+                scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+                config=dict(workload=f"{n}^3, 64 static spheres r in [0.02, 0.08], "
+                                     "N(0,1) divergent face velocity, one cut-cell projection",
+                            reference="FP64 MGPCG to 1e-12",
+                            reference_norm=ref_norm, reference_stats=st_ref),
+                variants=variants)
+
+
 def run_reference(args, rank):
     if rank != 0:
         return None
@@ -503,6 +575,8 @@ def main():
         out = run_reference(args, rank)
     elif args.workload == "serving":
         out = run_serving(args) if rank == 0 else None
+    elif args.workload == "precision":
+        out = run_precision(args) if rank == 0 else None
     else:
         if world > 1:
             import torch

@@ -199,6 +199,7 @@ class EpisodeImpl : public EpisodeBase {
     }
     CKS(solver_.init(A_));
     CKS(cc_.init(A_, ncell_));
+    solver_.set_projector(&cc_);
     Launch L = ctx_->launch();
     CKC(cudaMemsetAsync(U_, 0, nfaces_ * sizeof(T), L.s));
     CKC(cudaMemsetAsync(P_, 0, ncell_ * sizeof(S), L.s));

@@ -154,11 +154,30 @@ __global__ void k_cc_ground(GridDev g, const int *lab, int *ground) {
   }
 }
 
+// Counts the floating roots into *nfloat and gives each a slot.
 __global__ void k_cc_count(int64_t n, const int *lab, const int *ground,
-                           int *nfloat) {
+                           int *nfloat, int *fslot) {
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
        c += (int64_t)gridDim.x * blockDim.x)
-    if (lab[c] == (int)c && !ground[c]) atomicAdd(nfloat, 1);
+    if (lab[c] == (int)c && !ground[c]) fslot[c] = atomicAdd(nfloat, 1);
+}
+
+// Cells per floating slot (warp-aggregated: the lanes of a warp usually
+// share one component).
+__global__ void k_cc_fcount(int64_t n, const int *lab, const int *ground,
+                            const int *fslot, int *fcnt) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x; c0 < n;
+       c0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = c0 + threadIdx.x;
+    int slot = -1;
+    if (c < n) {
+      const int r = lab[c];
+      if (r >= 0 && !ground[r]) slot = fslot[r];
+    }
+    const unsigned same = __match_any_sync(0xffffffffu, slot);
+    if (slot >= 0 && lane == __ffs(same) - 1) atomicAdd(fcnt + slot, __popc(same));
+  }
 }
 
 __device__ __forceinline__ bool floating(const int *lab, const int *ground,
@@ -225,6 +244,78 @@ __global__ void k_gauge_sub(int64_t n, const int *lab, const int *ground, S *v,
   if (grid_sum<1>(acc, rs, tot) && threadIdx.x == 0) *norm2 = tot[0];
 }
 
+// ------------------------------------------- projection inside the solve ---
+// v -= mean per floating component, with the component sums accumulated in
+// 64-bit fixed point (exact, order independent) and combined per warp before
+// the atomics: on a domain that floats as a whole every cell has one slot.
+template <class V>
+__global__ void k_proj_max(int64_t n, const int *lab, const int *ground,
+                           const int *nfloat, const V *v, unsigned long long *mx) {
+  if (*(volatile const int *)nfloat == 0) return;
+  double m = 0.0;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int r = lab[c];
+    if (r >= 0 && !ground[r]) m = fmax(m, fabs((double)v[c]));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0)
+    atomicMax(mx, (unsigned long long)__double_as_longlong(m));
+}
+
+__global__ void k_proj_zero(const int *nfloat, unsigned long long *fsum) {
+  const int nf = *(volatile const int *)nfloat;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nf; s += gridDim.x * blockDim.x)
+    fsum[s] = 0ull;
+}
+
+template <class V>
+__global__ void k_proj_sum(int64_t n, const int *lab, const int *ground,
+                           const int *nfloat, const int *fslot, const V *v,
+                           const unsigned long long *mx, int bits,
+                           unsigned long long *fsum) {
+  if (*(volatile const int *)nfloat == 0) return;
+  const double sc = fixed_scale(*mx, bits);
+  const int lane = threadIdx.x & 31;
+  for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x; c0 < n;
+       c0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = c0 + threadIdx.x;
+    int slot = -1;
+    long long q = 0;
+    if (c < n) {
+      const int r = lab[c];
+      if (r >= 0 && !ground[r]) {
+        slot = fslot[r];
+        q = llrint((double)v[c] * sc);
+      }
+    }
+    const unsigned same = __match_any_sync(0xffffffffu, slot);
+    if (same == 0xffffffffu) {
+      // one slot for the whole warp: add the 64-bit values in registers
+      for (int o = 16; o > 0; o >>= 1) q += __shfl_down_sync(0xffffffffu, q, o);
+      if (lane == 0 && slot >= 0) atomicAdd(fsum + slot, (unsigned long long)q);
+    } else if (slot >= 0) {
+      atomicAdd(fsum + slot, (unsigned long long)q);
+    }
+  }
+}
+
+template <class V>
+__global__ void k_proj_sub(int64_t n, const int *lab, const int *ground,
+                           const int *nfloat, const int *fslot, V *v,
+                           const unsigned long long *mx, int bits,
+                           const unsigned long long *fsum, const int *fcnt) {
+  if (*(volatile const int *)nfloat == 0) return;
+  const double sc = fixed_scale(*mx, bits);
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int r = lab[c];
+    if (r < 0 || ground[r]) continue;
+    const int s = fslot[r];
+    v[c] = (V)((double)v[c] - (double)(long long)fsum[s] / sc / (double)fcnt[s]);
+  }
+}
+
 // ------------------------------------------------------------ launchers ---
 static inline unsigned cc_blocks(int64_t n) {
   const unsigned b = nblocks(n);
@@ -250,11 +341,17 @@ int Components::label(Ctx *ctx, const GridDev &g, Fields<T> alpha) {
   {
     ProfScope _ps(L, NF_K_GAUGE);
     k_cc_ground<<<cc_blocks((int64_t)g.ow * g.oh + 1), kBlock, 0, L.s>>>(g, lab, ground);
-    k_cc_count<<<cc_blocks(n), kBlock, 0, L.s>>>(n, lab, ground, (int *)scal + 1);
+    k_cc_count<<<cc_blocks(n), kBlock, 0, L.s>>>(n, lab, ground, (int *)scal + 1, fslot);
     *L.counter += 2;
   }
   ctx->read_bytes(h, scal, 2 * sizeof(int));
   nfloat = h[1];
+  if (nfloat > 0) {
+    cudaMemsetAsync(fcnt, 0, (size_t)nfloat * sizeof(int), L.s);
+    ProfScope _ps(L, NF_K_GAUGE);
+    k_cc_fcount<<<cc_blocks(n), kBlock, 0, L.s>>>(n, lab, ground, fslot, fcnt);
+    ++*L.counter;
+  }
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? NF_OK : cuda_fail(e, "component labelling");
 }
@@ -280,14 +377,37 @@ double Components::gauge(Ctx *ctx, int64_t n, S *v, double norm2) {
   return ctx->read_double(nrm);
 }
 
+template <class V>
+void Components::project(const Launch &L, int64_t n, V *v) {
+  const int *nf = (const int *)scal + 1;
+  unsigned long long *mx = (unsigned long long *)((char *)scal + 32);
+  int bits = 1;
+  while (bits < 40 && ((int64_t)1 << bits) < n) ++bits;
+  cudaMemsetAsync(mx, 0, sizeof(unsigned long long), L.s);
+  ProfScope _ps(L, NF_K_GAUGE);
+  k_proj_max<V><<<cc_blocks(n), kBlock, 0, L.s>>>(n, lab, ground, nf, v, mx);
+  k_proj_zero<<<64, kBlock, 0, L.s>>>(nf, fsum);
+  k_proj_sum<V><<<cc_blocks(n), kBlock, 0, L.s>>>(n, lab, ground, nf, fslot, v, mx, bits,
+                                                  fsum);
+  k_proj_sub<V><<<cc_blocks(n), kBlock, 0, L.s>>>(n, lab, ground, nf, fslot, v, mx, bits,
+                                                  fsum, fcnt);
+  *L.counter += 4;
+}
+
 int Components::init(Alloc &A, int64_t n) {
   CKS(A.get(&lab, n * sizeof(int)));
   CKS(A.get(&ground, n * sizeof(int)));
   CKS(A.get(&ccnt, n * sizeof(int)));
   CKS(A.get(&csum, n * sizeof(unsigned long long)));
+  CKS(A.get(&fslot, n * sizeof(int)));
+  CKS(A.get(&fcnt, n * sizeof(int)));
+  CKS(A.get(&fsum, n * sizeof(unsigned long long)));
   CKS(A.get(&scal, 64));
   return NF_OK;
 }
+
+template void Components::project<float>(const Launch &, int64_t, float *);
+template void Components::project<double>(const Launch &, int64_t, double *);
 
 template int Components::label<float>(Ctx *, const GridDev &, Fields<float>);
 template int Components::label<double>(Ctx *, const GridDev &, Fields<double>);

@@ -21,6 +21,7 @@
 #include <string>
 #include <vector>
 
+#include "components.h"
 #include "kernels.h"
 #include "util.h"
 
@@ -156,6 +157,7 @@ class Solver {
     }
     const double tol = cfg_.tol;
     const bool mixed = sizeof(S) != sizeof(V);
+    proj_now_ = mg_ && proj_ != nullptr && proj_->nfloat > 0;
     // the inner system is solved for scale * r, scale a power of two close
     // to 1 / ||r||: tiny right-hand sides (an adjoint far from its loss)
     // would otherwise underflow in the V-typed dots
@@ -208,6 +210,10 @@ class Solver {
   }
 
   int levels() const { return (int)levels_.size(); }
+
+  // Components of the episode, whose floating part the preconditioner
+  // projects out (labels must be current when solve() is called).
+  void set_projector(Components *c) { proj_ = c; }
 
  private:
   struct Level {
@@ -296,7 +302,16 @@ class Solver {
   // z = M r: one symmetric V-cycle (red-black pre-smoothing, black-red
   // post-smoothing) from z = 0. Levels above kChainCells cells run as grid
   // kernels, the small ones inside one thread block.
+  // z = P M r with P the zero-mean projection of every floating component
+  // (when the system has one): on a singular system the V-cycle's coarse
+  // sweeps add a null-space constant that grows once rounding makes r
+  // slightly inconsistent, and P keeps the preconditioner on the range.
   void precondition(const V *r, V *z, const CGState *st) {
+    vcycle(r, z, st);
+    if (proj_now_) proj_->project<V>(ctx_->launch(), n_, z);
+  }
+
+  void vcycle(const V *r, V *z, const CGState *st) {
     Launch L = ctx_->launch();
     const int nl = (int)levels_.size();
     const int F = std::max(1, first_chain_);  // level 0 always on grid kernels
@@ -476,9 +491,10 @@ class Solver {
     static_assert(offsetof(CGState, ratio) == offsetof(CGState, tol) + sizeof(double),
                   "tol and ratio are copied together");
     cudaMemcpyAsync(&st->tol, slot, 2 * sizeof(double), cudaMemcpyHostToDevice, ctx_->stream);
-    Graph &G0 = cont ? cont_g_ : init_g_;
-    const bool g_init = cont ? ensure_graph(cont_g_, [&] { cont_body(); })
-                             : ensure_graph(init_g_, [&] { init_body(); });
+    const int pv = proj_now_ ? 1 : 0;
+    Graph &G0 = cont ? cont_g_[pv] : init_g_[pv];
+    const bool g_init = cont ? ensure_graph(cont_g_[pv], [&] { cont_body(); })
+                             : ensure_graph(init_g_[pv], [&] { init_body(); });
     if (g_init)
       replay(G0);
     else if (cont)
@@ -490,9 +506,9 @@ class Solver {
     bool init_collected = !g_init;
     while (issued < max_it) {
       const bool full = max_it - issued >= kBatch;
-      const bool g_batch = full && ensure_graph(batch_g_, [&] { iterations(kBatch); });
+      const bool g_batch = full && ensure_graph(batch_g_[pv], [&] { iterations(kBatch); });
       if (g_batch)
-        replay(batch_g_);
+        replay(batch_g_[pv]);
       else
         iterations(full ? kBatch : max_it - issued);
       issued += full ? kBatch : max_it - issued;
@@ -505,7 +521,7 @@ class Solver {
         // iterations of this replay that ran to the end (the one that met
         // the tolerance skipped its preconditioner)
         const int ran = hs.iters - seen - (hs.done ? 1 : 0);
-        ctx_->prof.collect(batch_g_.ev, ran > 0 ? ran : 0);
+        ctx_->prof.collect(batch_g_[pv].ev, ran > 0 ? ran : 0);
       }
       seen = hs.iters;
       if (hs.done) break;
@@ -529,13 +545,17 @@ class Solver {
        *d_ = nullptr, *q_ = nullptr, *st_ = nullptr, *norm2_ = nullptr;
   cudaStream_t cap_ = nullptr;
   bool graphs_ok_ = true;
-  Graph init_g_, cont_g_, batch_g_;
+  Graph init_g_[2], cont_g_[2], batch_g_[2];  // [1]: with the projection
+  Components *proj_ = nullptr;  // the episode's components (null: none)
+  bool proj_now_ = false;       // this solve's system has a floating part
 
  public:
   ~Solver() {
-    if (init_g_.exec) cudaGraphExecDestroy(init_g_.exec);
-    if (cont_g_.exec) cudaGraphExecDestroy(cont_g_.exec);
-    if (batch_g_.exec) cudaGraphExecDestroy(batch_g_.exec);
+    for (int p = 0; p < 2; ++p) {
+      if (init_g_[p].exec) cudaGraphExecDestroy(init_g_[p].exec);
+      if (cont_g_[p].exec) cudaGraphExecDestroy(cont_g_[p].exec);
+      if (batch_g_[p].exec) cudaGraphExecDestroy(batch_g_[p].exec);
+    }
     if (cap_) cudaStreamDestroy(cap_);
   }
 };
