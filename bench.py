@@ -68,6 +68,8 @@ def parse():
                     help="multigrid prolongation and restriction")
     ap.add_argument("--mg-smooth-coarse", type=int, default=0,
                     help="sweeps on the coarse levels (0: as --mg-smooth)")
+    ap.add_argument("--tape-fractions", type=int, default=1,
+                    help="1: the tape keeps each step's fractions (no re-rasterising)")
     ap.add_argument("--coarse-weight", type=float, default=1.9,
                     help="scale of the coarse-grid correction")
     ap.add_argument("--mg-coarsest", type=int, default=4,
@@ -189,7 +191,7 @@ def run_ours(args, rank, world, local_rank):
                     mg_smooth=args.mg_smooth, mg_coarsest_sweeps=args.coarsest_sweeps,
                     mg_coarsest=args.mg_coarsest, mg_band_sweeps=args.band_sweeps,
                     mg_transfer=args.mg_transfer, mg_coarse_weight=args.coarse_weight,
-                    mg_smooth_coarse=args.mg_smooth_coarse,
+                    mg_smooth_coarse=args.mg_smooth_coarse, tape_fractions=bool(args.tape_fractions),
                     device=local_rank)
     ep = ctx.episode(cfg["grid"], cfg["scene"])
     u0 = [torch.zeros(s, dtype=torch.float32, device=dev) for s in ep.face_shapes]
@@ -259,6 +261,7 @@ def run_ours(args, rank, world, local_rank):
                            band_sweeps=args.band_sweeps, mg_transfer=args.mg_transfer,
                            coarse_weight=args.coarse_weight,
                            mg_smooth_coarse=args.mg_smooth_coarse,
+                           tape_fractions=bool(args.tape_fractions),
                            l2="inputs larger than L2 (episode state and tape > 1 GB)",
                            parallelism=f"replicas x{world}"),
                gpu_launches=int(launches), iterations=dict(fwd=stats["fwd"], bwd=stats["bwd"]),

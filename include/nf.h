@@ -113,6 +113,10 @@ typedef struct nf_config {
                              coarse space (over-correction)                 */
   int mg_smooth_coarse;   /* sweeps on the levels below the finest (0: as
                              mg_smooth)                                      */
+  int tape_fractions;     /* 1: the rollout tape keeps every step's face
+                             fractions (one face triple per step), so the
+                             backward pass copies them instead of
+                             rasterising again; 0: recompute them           */
 } nf_config;
 
 typedef struct nf_grid {
@@ -151,7 +155,7 @@ typedef struct nf_step_stats {
    max_iters 500, inner_tol 1e-3, mg_smooth 2, mg_coarsest 4, RK2,
    checkpoint_every 10, no budget, cfl_max 0 (no sub-stepping),
    mg_coarsest_sweeps 8, mg_band_sweeps 0, mg_transfer 1 (constant),
-   mg_coarse_weight 1.9, mg_smooth_coarse 0. */
+   mg_coarse_weight 1.9, mg_smooth_coarse 0, tape_fractions 0. */
 int nf_config_default(nf_config *cfg);
 
 /* Create a context on cfg->device. *out receives the handle. */

@@ -39,7 +39,8 @@ class Config(C.Structure):
                 ("checkpoint_every", C.c_int), ("hbm_budget", C.c_size_t),
                 ("cfl_max", C.c_double), ("mg_coarsest_sweeps", C.c_int),
                 ("mg_band_sweeps", C.c_int), ("mg_transfer", C.c_int),
-                ("mg_coarse_weight", C.c_double), ("mg_smooth_coarse", C.c_int)]
+                ("mg_coarse_weight", C.c_double), ("mg_smooth_coarse", C.c_int),
+                ("tape_fractions", C.c_int)]
 
 
 class Grid(C.Structure):

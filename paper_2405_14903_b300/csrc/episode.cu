@@ -512,6 +512,7 @@ class EpisodeImpl : public EpisodeBase {
   }
 
   void clear_tape() {
+    std::fill(tapeA_ok_.begin(), tapeA_ok_.end(), 0);
     n_ = 0;
     frames_ = 0;
     ts_.clear();
@@ -547,7 +548,22 @@ class EpisodeImpl : public EpisodeBase {
     Launch L = ctx_->launch();
     const GridDev g = grid_h(hs_[m]);
     const SceneDev sd = scene_at(sc_, ts_[m], dsph_);
-    launch_rasterize<T>(L, g, sd, mut(alpha_));
+    if (m < (int)tapeA_.size() && tapeA_[m] && tapeA_ok_[m]) {
+      // recomputed step: the fractions kept by the first pass (bit-identical
+      // to rasterising them again)
+      CKC(cudaMemcpyAsync(alpha_, tapeA_[m], nfaces_ * sizeof(T), cudaMemcpyDeviceToDevice, L.s));
+    } else {
+      launch_rasterize<T>(L, g, sd, mut(alpha_));
+      if (ctx_->cfg.tape_fractions) {
+        if ((int)tapeA_.size() <= m) {
+          tapeA_.resize(m + 1, nullptr);
+          tapeA_ok_.resize(m + 1, 0);
+        }
+        if (!tapeA_[m]) CKS(faces(&tapeA_[m]));
+        CKC(cudaMemcpyAsync(tapeA_[m], alpha_, nfaces_ * sizeof(T), cudaMemcpyDeviceToDevice, L.s));
+        tapeA_ok_[m] = 1;
+      }
+    }
     launch_advect<T>(L, g, cview(u_in), mut(uh), ctx_->cfg.advect_order);
     return project_faces(g, sd, uh, P, u_out, ss);
   }
@@ -677,6 +693,8 @@ class EpisodeImpl : public EpisodeBase {
   std::vector<T *> segU_, segUh_, segA_;
   std::vector<S *> segP_;
   std::vector<int> segFloat_;  // floating components of each segment step
+  std::vector<T *> tapeA_;     // fractions of every step (tape_fractions)
+  std::vector<char> tapeA_ok_; // tapeA_[m] holds step m of the current tape
 };
 
 size_t episode_base_bytes(const nf_config &cfg, const nf_grid &g) {

@@ -791,6 +791,37 @@ __global__ void k_mg_restrict(int fnx, int fny, int fnz, int cnx, int cny,
   }
 }
 
+// Fused residual and restriction for the constant transfer: every coarse
+// cell adds the residuals of its eight children (times the normaliser pn,
+// here the uniform sqrt of the coarse weight) without storing the fine
+// residual: b_c = pn / 8 sum_children (b - A x).
+template <class V, class TA>
+__global__ void k_mg_resrestrict(LevelView<TA> lv, const V *x, const V *b,
+                                 int cnx, int cny, int cnz, V *bc, float pn,
+                                 const CGState *st) {
+  if (stopped(st)) return;
+  const RowWalk w;
+  const int nrows = cny * cnz;
+  const V cc = V(lv.c);
+  for (int row = w.warp; row < nrows; row += w.nwarps) {
+    const int K = row / cny, J = row - K * cny;
+    for (int I = w.lane; I < cnx; I += 32) {
+      V acc = V(0);
+#pragma unroll 2
+      for (int ch = 0; ch < 8; ++ch) {
+        const int i = 2 * I + (ch & 1), j = 2 * J + ((ch >> 1) & 1), k = 2 * K + (ch >> 2);
+        const int frow = k * lv.ny + j;
+        const int c = frow * lv.nx + i;
+        Nb7<V> g;
+        gather7r(g, lv, x, i, j, k, c, frow);
+        const V dg = g.diag();
+        if (dg > V(0)) acc += b[c] - cc * (dg * g.vc - g.nb());
+      }
+      bc[row * cnx + I] = V(0.125) * V(pn) * acc;
+    }
+  }
+}
+
 // x_f += P x_c on active fine cells.
 template <class V, class TF>
 __global__ void k_mg_prolong(LevelView<TF> f, int cnx, int cny, int cnz,
@@ -1140,6 +1171,15 @@ void launch_mg_residual(const Launch &L, const LevelView<TA> &lv, const V *x,
   ++*L.counter;
 }
 template <class V, class TA>
+void launch_mg_resrestrict(const Launch &L, const LevelView<TA> &fine, const V *x,
+                           const V *b, int cnx, int cny, int cnz, V *bc, float pn,
+                           const CGState *st) {
+  ProfScope _ps(L, NF_K_MG_RESTRICT);
+  k_mg_resrestrict<V, TA><<<row_blocks(cny * cnz), kBlock, 0, L.s>>>(fine, x, b, cnx, cny,
+                                                                     cnz, bc, pn, st);
+  ++*L.counter;
+}
+template <class V, class TA>
 void launch_mg_restrict(const Launch &L, const LevelView<TA> &fine,
                         const LevelView<TA> &coarse, const V *rf, V *bc,
                         int mode, const CGState *st) {
@@ -1225,6 +1265,10 @@ void launch_mg_coarse_chain(const Launch &L, const CoarseChain<V, TA> &ch,
                                           const LevelView<TA> &, const V *,   \
                                           const V *, V *, const float *,      \
                                           const CGState *);                   \
+  template void launch_mg_resrestrict<V, TA>(const Launch &,                 \
+                                             const LevelView<TA> &, const V *,\
+                                             const V *, int, int, int, V *,   \
+                                             float, const CGState *);         \
   template void launch_mg_restrict<V, TA>(const Launch &,                    \
                                           const LevelView<TA> &,              \
                                           const LevelView<TA> &, const V *,   \

@@ -121,18 +121,24 @@ void launch_mg_coarsen(const Launch &L, const LevelView<TI> &fine,
 template <class V, class TA>
 void launch_mg_smooth(const Launch &L, const LevelView<TA> &lv, V *x,
                       const V *b, int color, const CGState *st, int kclass);
-template <class V, class TA>
 // r = N (b - A x) with N the prolongation normaliser pn (null: N = I).
+template <class V, class TA>
 void launch_mg_residual(const Launch &L, const LevelView<TA> &lv, const V *x,
                         const V *b, V *r, const float *pn, const CGState *st);
+// Constant transfer, fused: b_c = pn / 8 * sum over the eight children of
+// (b - A x), without storing the fine residual.
 template <class V, class TA>
+void launch_mg_resrestrict(const Launch &L, const LevelView<TA> &fine, const V *x,
+                           const V *b, int cnx, int cny, int cnz, V *bc, float pn,
+                           const CGState *st);
 // b_c = R r_f; mode 0: R = P^T / 4 with trilinear P, 1: mean of the eight
 // children (P copies the parent).
+template <class V, class TA>
 void launch_mg_restrict(const Launch &L, const LevelView<TA> &fine,
                         const LevelView<TA> &coarse, const V *rf, V *bc,
                         int mode, const CGState *st);
-template <class V, class TF, class TC>
 // x_f += N P x_c on active fine cells (pn null: N = I).
+template <class V, class TF, class TC>
 void launch_mg_prolong(const Launch &L, const LevelView<TF> &fine,
                        const LevelView<TC> &coarse, const V *xc, V *xf,
                        const float *pn, int mode, const CGState *st);

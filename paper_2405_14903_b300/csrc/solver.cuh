@@ -329,14 +329,24 @@ class Solver {
         smooth(l, x, b, 0, st);
         smooth(l, x, b, 1, st);
       }
-      if (l == 0)
-        launch_mg_residual<V, T>(L, view0(), x, b, (V *)levels_[0].r, pnorm(0), st);
-      else
-        launch_mg_residual<V, TA>(L, viewc(l), x, b, (V *)levels_[l].r, pnorm(l), st);
-      const LevelView<TA> f{levels_[l].nx, levels_[l].ny, levels_[l].nz, 0.0,
-                            nullptr, nullptr, nullptr};
-      launch_mg_restrict<V, TA>(L, f, viewc(l + 1), (const V *)levels_[l].r,
-                                (V *)levels_[l + 1].b, cfg_.mg_transfer, st);
+      const Level &C = levels_[l + 1];
+      if (cfg_.mg_transfer == 1) {
+        // constant transfer: residual and restriction in one pass
+        const float w = (float)std::sqrt(cfg_.mg_coarse_weight > 0 ? cfg_.mg_coarse_weight : 1.0);
+        if (l == 0)
+          launch_mg_resrestrict<V, T>(L, view0(), x, b, C.nx, C.ny, C.nz, (V *)C.b, w, st);
+        else
+          launch_mg_resrestrict<V, TA>(L, viewc(l), x, b, C.nx, C.ny, C.nz, (V *)C.b, w, st);
+      } else {
+        if (l == 0)
+          launch_mg_residual<V, T>(L, view0(), x, b, (V *)levels_[0].r, pnorm(0), st);
+        else
+          launch_mg_residual<V, TA>(L, viewc(l), x, b, (V *)levels_[l].r, pnorm(l), st);
+        const LevelView<TA> f{levels_[l].nx, levels_[l].ny, levels_[l].nz, 0.0,
+                              nullptr, nullptr, nullptr};
+        launch_mg_restrict<V, TA>(L, f, viewc(l + 1), (const V *)levels_[l].r, (V *)C.b,
+                                  cfg_.mg_transfer, st);
+      }
     }
     if (nl == 1) {
       // no coarser grid: symmetric Gauss-Seidel sweeps only
