@@ -65,6 +65,7 @@ static SceneDev scene_at(const nf_scene &sc, double t, const double *d_spheres) 
         s.sc[a] = c[a] + th[a] * t;
       }
       s.sr = c[3];
+      s.fdscale[0] = (float)(-t);
       break;
     case NF_SCENE_CHAMBER: {
       for (int a = 0; a < 3; ++a) {
@@ -72,6 +73,7 @@ static SceneDev scene_at(const nf_scene &sc, double t, const double *d_spheres) 
         s.ca[a] = c[3 + a];
       }
       s.camin = std::min(s.ca[0], std::min(s.ca[1], s.ca[2]));
+      for (int a = 0; a < 3; ++a) s.cinva[a] = 1.0 / s.ca[a];
       const double T = c[6];
       double r = 1.0, rd = 0.0;
       for (int k = 1; k <= 4; ++k) {
@@ -89,6 +91,8 @@ static SceneDev scene_at(const nf_scene &sc, double t, const double *d_spheres) 
       s.csdot = rd;
       s.crate = rd / r;
       for (int k = 0; k < 8; ++k) s.cdus[k] = (s.cdsdot[k] * r - rd * s.cds[k]) / (r * r);
+      for (int k = 0; k < 8; ++k) s.fdscale[k] = (float)(s.camin * s.cds[k]);
+      for (int a = 0; a < 3; ++a) s.finva[a] = (float)s.cinva[a];
       const double x0 = c[7], hw = c[8];
       s.dc[0] = 0.5 * (x0 + 2.0);
       s.dc[1] = c[1];
@@ -114,6 +118,7 @@ static SceneDev scene_at(const nf_scene &sc, double t, const double *d_spheres) 
       for (int k = 0; k < 4; ++k) s.pdang[k] = s.pdomega[k] = 0.0;
       s.pdang[seg] = 1.0 - tau;
       s.pdang[seg + 1] = tau;
+      for (int k = 0; k < 4; ++k) s.fdscale[k] = (float)s.pdang[k];
       s.pdomega[seg] = -1.0 / L;
       s.pdomega[seg + 1] = 1.0 / L;
       break;
@@ -125,6 +130,25 @@ static SceneDev scene_at(const nf_scene &sc, double t, const double *d_spheres) 
     default:
       break;
   }
+  for (int a = 0; a < 3; ++a) {
+    s.f_sc[a] = (float)s.sc[a];
+    s.f_sv[a] = (float)s.sv[a];
+    s.f_cc[a] = (float)s.cc[a];
+    s.f_dc[a] = (float)s.dc[a];
+    s.f_dh[a] = (float)s.dh[a];
+    s.f_pc[a] = (float)s.pc[a];
+    s.f_ph[a] = (float)s.ph[a];
+    s.finva[a] = (float)s.cinva[a];
+  }
+  s.f_sr = (float)s.sr;
+  s.f_camin = (float)s.camin;
+  s.f_cs = (float)s.cs;
+  s.f_crate = (float)s.crate;
+  s.f_pcos = (float)s.pcos;
+  s.f_psin = (float)s.psin;
+  s.f_pomega = (float)s.pomega;
+  for (int k = 0; k < 8; ++k) s.f_cdus[k] = (float)s.cdus[k];
+  for (int k = 0; k < 4; ++k) s.f_pdomega[k] = (float)s.pdomega[k];
   return s;
 }
 

@@ -150,7 +150,8 @@ __device__ __forceinline__ double band_fraction(const GridDev &g,
 // only the narrow band evaluates the 64 samples (directly in FP64 for FP64
 // fields, with the narrow-band evaluator of scene.cuh for FP32 fields).
 template <class T>
-__global__ void k_rasterize(GridDev g, SceneDev s, FieldsMut<T> alpha) {
+__global__ void __launch_bounds__(kBlock, 4)
+k_rasterize(GridDev g, SceneDev s, FieldsMut<T> alpha) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int d;
   int64_t f;
@@ -489,55 +490,52 @@ __global__ void k_loss_outflow(GridDev g, Fields<T> u, FieldsMut<T> gu,
 }
 
 // ------------------------------------------------------------ adjoint -----
-// d alpha / d theta of a band face: (1/64) sum over the subsamples inside
-// the ramp of (4 / dx) d phi / d theta; the same evaluator (and precision)
-// as band_fraction.
+// The 64-sample ramp derivative of one band face shared by a warp: lane l
+// evaluates samples l and l + 32 with the narrow-band evaluator L (FP32
+// fields; initialised once per face by one lane) or directly in FP64; out
+// receives this lane's part of sum_samples (4 / dx) d phi / d theta, to be
+// summed over the warp.
 template <class T>
-__device__ __forceinline__ void band_dalpha(const GridDev &g, const SceneDev &s,
-                                            double x, double y, double z, T *da) {
-  for (int q = 0; q < kMaxParams; ++q) da[q] = T(0);
-  if (sizeof(T) == 4) {
-    LocalSdf L;
-    L.init(s, x, y, z, g.dx);
-    if (!L.overflow) {
-      const float inv_w = (float)(4.0 / g.dx), h = (float)g.dx;
-      float tmp[kMaxParams];
-      for (int c = 0; c < 4; ++c) {
-        const float oz = ((c + 0.5f) * 0.25f - 0.5f) * h;
-        for (int b = 0; b < 4; ++b) {
-          const float oy = ((b + 0.5f) * 0.25f - 0.5f) * h;
-          for (int q = 0; q < 4; ++q) {
-            const float ox = ((q + 0.5f) * 0.25f - 0.5f) * h;
-            const float hv = 0.5f + L.phi(ox, oy, oz) * inv_w;
-            if (hv > 0.f && hv < 1.f) {
-              L.dphi(s, ox, oy, oz, tmp);
-              for (int p = 0; p < s.K; ++p) da[p] += (T)(inv_w * tmp[p]);
-            }
-          }
-        }
+__device__ __forceinline__ void band_dalpha_lanes(const GridDev &g, const SceneDev &s,
+                                                  const LocalSdf *L, double x, double y,
+                                                  double z, int lane, T *out) {
+#pragma unroll
+  for (int q = 0; q < kMaxParams; ++q) out[q] = T(0);
+  if (sizeof(T) == 4 && !L->overflow) {
+    const float inv_w = (float)(4.0 / g.dx), h = (float)g.dx;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int sm = lane + 32 * half;
+      const float ox = (((sm & 3) + 0.5f) * 0.25f - 0.5f) * h;
+      const float oy = ((((sm >> 2) & 3) + 0.5f) * 0.25f - 0.5f) * h;
+      const float oz = (((sm >> 4) + 0.5f) * 0.25f - 0.5f) * h;
+      const float hv = 0.5f + L->phi(ox, oy, oz) * inv_w;
+      if (hv > 0.f && hv < 1.f) {
+        float tmp[kMaxParams];
+        L->dphi(s, ox, oy, oz, tmp);
+#pragma unroll
+        for (int p = 0; p < kMaxParams; ++p)
+          if (p < s.K) out[p] += (T)(inv_w * tmp[p]);
       }
-      for (int p = 0; p < s.K; ++p) da[p] *= T(1.0 / 64.0);
-      return;
     }
+    return;
   }
   const double inv_w = 4.0 / g.dx;
-  double tmp[kMaxParams], acc[kMaxParams];
-  for (int p = 0; p < kMaxParams; ++p) acc[p] = 0.0;
-  for (int cz = 0; cz < 4; ++cz) {
-    const double zz = z + ((cz + 0.5) * 0.25 - 0.5) * g.dx;
-    for (int cy = 0; cy < 4; ++cy) {
-      const double yy = y + ((cy + 0.5) * 0.25 - 0.5) * g.dx;
-      for (int cx = 0; cx < 4; ++cx) {
-        const double xx = x + ((cx + 0.5) * 0.25 - 0.5) * g.dx;
-        const double hv = 0.5 + scene_phi<double>(s, xx, yy, zz) * inv_w;
-        if (hv > 0.0 && hv < 1.0) {
-          scene_dphi(s, xx, yy, zz, tmp);
-          for (int p = 0; p < s.K; ++p) acc[p] += inv_w * tmp[p];
-        }
-      }
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    const int sm = lane + 32 * half;
+    const double xx = x + (((sm & 3) + 0.5) * 0.25 - 0.5) * g.dx;
+    const double yy = y + ((((sm >> 2) & 3) + 0.5) * 0.25 - 0.5) * g.dx;
+    const double zz = z + (((sm >> 4) + 0.5) * 0.25 - 0.5) * g.dx;
+    const double hv = 0.5 + scene_phi<double>(s, xx, yy, zz) * inv_w;
+    if (hv > 0.0 && hv < 1.0) {
+      double tmp[kMaxParams];
+      scene_dphi(s, xx, yy, zz, tmp);
+#pragma unroll
+      for (int p = 0; p < kMaxParams; ++p)
+        if (p < s.K) out[p] += (T)(inv_w * tmp[p]);
     }
   }
-  for (int p = 0; p < s.K; ++p) da[p] = (T)(acc[p] * (1.0 / 64.0));
 }
 
 // gP / c = -G^T (S gU) on active cells (dJ/dP of the update, divided by c
@@ -583,47 +581,92 @@ __global__ void k_adj_face(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
 #pragma unroll
   for (int q = 0; q < kMaxParams; ++q) acc[q] = T(0);
   const int64_t n = g.nface(0) + g.nface(1) + g.nface(2);
-  const double c = g.c;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    int d;
-    int64_t f;
-    split_face(g, t, d, f);
-    int i, j, k;
-    g.face_ijk(d, f, i, j, k);
-    int64_t cL, cR;
-    face_cells(g, d, i, j, k, cL, cR);
-    const double GP = (cR >= 0 ? (double)P[cR] : 0.0) - (cL >= 0 ? (double)P[cL] : 0.0);
-    const double Gy = (cR >= 0 ? (double)y[cR] : 0.0) - (cL >= 0 ? (double)y[cL] : 0.0);
-    const double a = (double)comp(alpha, d)[f];
-    const double gU = (double)comp(gu, d)[f];
-    comp(guh, d)[f] = (T)(a * (gU + Gy));
-    if (s.K == 0 || g.boundary(d, i, j, k)) continue;
-    const double Uh = (double)comp(uh, d)[f];
-    const double us = (double)face_us<T>(g, s, d, i, j, k);
-    const T gUs = (T)((1.0 - a) * (gU + Gy));
-    const T gS = (T)(gU * (Uh - c * GP - us) + Gy * (Uh - us) - c * Gy * GP);
-    double X, Y, Z;
-    face_pos(d, i, j, k, X, Y, Z);
-    if (gUs != T(0) && s.kind != NF_SCENE_SPHERES) {
-      if (sizeof(T) == 4) {
-        float tmp[kMaxParams];
-        scene_dus_f(s, d, (float)(X * g.dx), (float)(Y * g.dx), (float)(Z * g.dx), tmp);
-        for (int q = 0; q < s.K; ++q) acc[q] += gUs * (T)tmp[q];
-      } else {
-        double tmp[kMaxParams];
-        scene_dus(s, d, X * g.dx, Y * g.dx, Z * g.dx, tmp);
-        for (int q = 0; q < s.K; ++q) acc[q] += gUs * (T)tmp[q];
+  const T cT = T(g.c), h = T(g.dx);
+  const float margin = 0.8f * (float)g.dx;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  __shared__ LocalSdf sdf[kBlock / 32];
+  // Each warp takes 32 consecutive faces at a time: every lane does its own
+  // face's per-face work; then the whole warp evaluates the 64-sample
+  // derivative of each band face of the chunk in turn (band faces are
+  // sparse, so one lane per band face would leave the others idle).
+  for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
+    const int64_t t = base + lane;
+    bool band = false;
+    T gS = T(0);
+    double Xd = 0.0, Yd = 0.0, Zd = 0.0;
+    do {
+      if (t >= n) break;
+      int d;
+      int64_t f;
+      split_face(g, t, d, f);
+      int i, j, k;
+      g.face_ijk(d, f, i, j, k);
+      int64_t cL, cR;
+      face_cells(g, d, i, j, k, cL, cR);
+      // differences of the pressure-precision fields, the rest in T
+      const T Gy = (T)((cR >= 0 ? y[cR] : S(0)) - (cL >= 0 ? y[cL] : S(0)));
+      const T a = comp(alpha, d)[f];
+      const T gU = comp(gu, d)[f];
+      comp(guh, d)[f] = a * (gU + Gy);
+      if (s.K == 0 || g.boundary(d, i, j, k)) break;
+      const T X = (T(i) + (d == 0 ? T(0) : T(0.5))) * h;
+      const T Y = (T(j) + (d == 1 ? T(0) : T(0.5))) * h;
+      const T Z = (T(k) + (d == 2 ? T(0) : T(0.5))) * h;
+      // solid-velocity term: its weight (1 - alpha) is exactly 0 where a = 1
+      const T gUs = (T(1) - a) * (gU + Gy);
+      if (gUs != T(0) && s.kind != NF_SCENE_SPHERES) {
+        if (sizeof(T) == 4) {
+          float tmp[kMaxParams];
+          scene_dus_f(s, d, (float)X, (float)Y, (float)Z, tmp);
+#pragma unroll
+          for (int q = 0; q < kMaxParams; ++q)
+            if (q < s.K) acc[q] += gUs * (T)tmp[q];
+        } else {
+          double tmp[kMaxParams];
+          scene_dus(s, d, (double)X, (double)Y, (double)Z, tmp);
+#pragma unroll
+          for (int q = 0; q < kMaxParams; ++q)
+            if (q < s.K) acc[q] += gUs * (T)tmp[q];
+        }
       }
+      // fraction term: d alpha / d theta vanishes off the narrow band (the
+      // rasteriser's own test)
+      const float pc = scene_phi<float>(s, (float)X, (float)Y, (float)Z);
+      if (pc > margin || pc < -margin) break;
+      const T GP = (T)((cR >= 0 ? P[cR] : S(0)) - (cL >= 0 ? P[cL] : S(0)));
+      const T Uh = comp(uh, d)[f];
+      const T us = face_us<T>(g, s, d, i, j, k);
+      gS = gU * (Uh - cT * GP - us) + Gy * (Uh - us) - cT * Gy * GP;
+      if (gS == T(0)) break;
+      face_pos(d, i, j, k, Xd, Yd, Zd);
+      band = true;
+    } while (false);
+    unsigned todo = __ballot_sync(0xffffffffu, band);
+    while (todo) {
+      const int src = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const double bx = __shfl_sync(0xffffffffu, Xd, src) * g.dx;
+      const double by = __shfl_sync(0xffffffffu, Yd, src) * g.dx;
+      const double bz = __shfl_sync(0xffffffffu, Zd, src) * g.dx;
+      const T gSb = __shfl_sync(0xffffffffu, gS, src);
+      // the face's FP64 centre evaluation, once, shared through the warp's
+      // slot (FP64 work scales with the lanes that run it)
+      LocalSdf *L = &sdf[threadIdx.x >> 5];
+      if (sizeof(T) == 4 && lane == 0) L->init(s, bx, by, bz, g.dx);
+      __syncwarp();
+      T part[kMaxParams];
+      band_dalpha_lanes<T>(g, s, L, bx, by, bz, lane, part);
+#pragma unroll
+      for (int q = 0; q < kMaxParams; ++q) {
+        T v = part[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0 && q < s.K) acc[q] += gSb * (v * T(1.0 / 64.0));
+      }
+      __syncwarp();  // the slot is rewritten for the next band face
     }
-    if (gS == T(0)) continue;
-    const float pc = scene_phi<float>(s, (float)(X * g.dx), (float)(Y * g.dx),
-                                      (float)(Z * g.dx));
-    const float margin = 0.8f * (float)g.dx;
-    if (pc > margin || pc < -margin) continue;
-    T da[kMaxParams];
-    band_dalpha<T>(g, s, X * g.dx, Y * g.dx, Z * g.dx, da);
-    for (int q = 0; q < s.K; ++q) acc[q] += gS * da[q];
   }
   double dacc[kMaxParams];
 #pragma unroll

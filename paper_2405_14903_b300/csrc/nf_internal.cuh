@@ -78,6 +78,16 @@ struct SceneDev {
   // theta derivatives; duct box centre and half extents (fluid inside)
   double cc[3], ca[3], camin, cs, csdot, crate, cds[8], cdsdot[8];  // crate = sdot / s
   double cdus[8];  // d(sdot / s) / d theta
+  double cinva[3]; // 1 / ca (no divisions on the device)
+  // FP32 copies for the narrow-band evaluator: the derivative scales of
+  // d phi / d theta (chamber amin ds/dtheta_k, plate dangle/dtheta_k, sphere
+  // -t) and the chamber's 1 / ca
+  float fdscale[8], finva[3];
+  // FP32 mirrors of the fields the FP32 evaluators read (rounded once per
+  // scene state on the host: a double-to-float conversion per evaluation
+  // runs on the FP64 pipe)
+  float f_sc[3], f_sr, f_sv[3], f_cc[3], f_camin, f_cs, f_crate, f_dc[3], f_dh[3], f_cdus[8];
+  float f_pc[3], f_ph[3], f_pcos, f_psin, f_pomega, f_pdomega[4];
   double dc[3], dh[3];
   // plate: centre, half extents, angle, cos/sin, rate, theta derivatives
   double pc[3], ph[3], pang, pcos, psin, pomega, pdang[4], pdomega[4];

@@ -41,13 +41,57 @@ __device__ __forceinline__ void box_sdf_grad(double px, double py, double pz,
     gz = sz;
 }
 
+// sqrt(v) to near FP64 accuracy from the FP32 root and one Newton step in
+// FP64 (a few FP64 multiply-adds instead of the FP64 square root, which is
+// slow on a part whose FP64 rate is 1/64 of FP32). v >= 0.
+__device__ __forceinline__ double fsqrt_refined(double v) {
+  const float r0 = sqrtf((float)v);
+  if (!(r0 > 0.f)) return 0.0;
+  const double r = (double)r0;
+  return r + (v - r * r) * (double)(0.5f / r0);
+}
+
+// The same gradient in FP32 (the narrow-band sub-samples of the FP32 path).
+__device__ __forceinline__ void box_sdf_grad_f(float px, float py, float pz, float hx,
+                                               float hy, float hz, float &gx, float &gy,
+                                               float &gz) {
+  const float qx = fabsf(px) - hx, qy = fabsf(py) - hy, qz = fabsf(pz) - hz;
+  const float sx = px >= 0.f ? 1.f : -1.f, sy = py >= 0.f ? 1.f : -1.f,
+              sz = pz >= 0.f ? 1.f : -1.f;
+  const float mx = fmaxf(qx, 0.f), my = fmaxf(qy, 0.f), mz = fmaxf(qz, 0.f);
+  const float n = sqrtf(mx * mx + my * my + mz * mz);
+  if (n > 0.f) {
+    gx = sx * mx / n;
+    gy = sy * my / n;
+    gz = sz * mz / n;
+    return;
+  }
+  gx = gy = gz = 0.f;
+  if (qx >= qy && qx >= qz)
+    gx = sx;
+  else if (qy >= qz)
+    gy = sy;
+  else
+    gz = sz;
+}
+
+// A scene parameter in the evaluator's precision R: the FP32 mirror for
+// float, the double itself otherwise.
+template <class R>
+__device__ __forceinline__ R P(double d, float f) {
+  if constexpr (sizeof(R) == 4)
+    return f;
+  else
+    return d;
+}
+
 // Fluid-positive level set phi(x) of the scene at its time.
 template <class R>
 __device__ __forceinline__ R scene_phi(const SceneDev &s, R x, R y, R z) {
   switch (s.kind) {
     case NF_SCENE_SPHERE: {
-      R dx = x - R(s.sc[0]), dy = y - R(s.sc[1]), dz = z - R(s.sc[2]);
-      return sqrt(dx * dx + dy * dy + dz * dz) - R(s.sr);
+      R dx = x - P<R>(s.sc[0], s.f_sc[0]), dy = y - P<R>(s.sc[1], s.f_sc[1]), dz = z - P<R>(s.sc[2], s.f_sc[2]);
+      return sqrt(dx * dx + dy * dy + dz * dz) - P<R>(s.sr, s.f_sr);
     }
     case NF_SCENE_SPHERES: {
       R best = R(1.0e3);
@@ -59,18 +103,18 @@ __device__ __forceinline__ R scene_phi(const SceneDev &s, R x, R y, R z) {
       return best;
     }
     case NF_SCENE_CHAMBER: {
-      R ex = (x - R(s.cc[0])) / R(s.ca[0]), ey = (y - R(s.cc[1])) / R(s.ca[1]),
-        ez = (z - R(s.cc[2])) / R(s.ca[2]);
-      R pe = R(s.camin) * (R(s.cs) - sqrt(ex * ex + ey * ey + ez * ez));
-      R pd = -box_sdf<R>(x - R(s.dc[0]), y - R(s.dc[1]), z - R(s.dc[2]),
-                         R(s.dh[0]), R(s.dh[1]), R(s.dh[2]));
+      R ex = (x - P<R>(s.cc[0], s.f_cc[0])) * P<R>(s.cinva[0], s.finva[0]), ey = (y - P<R>(s.cc[1], s.f_cc[1])) * P<R>(s.cinva[1], s.finva[1]),
+        ez = (z - P<R>(s.cc[2], s.f_cc[2])) * P<R>(s.cinva[2], s.finva[2]);
+      R pe = P<R>(s.camin, s.f_camin) * (P<R>(s.cs, s.f_cs) - sqrt(ex * ex + ey * ey + ez * ez));
+      R pd = -box_sdf<R>(x - P<R>(s.dc[0], s.f_dc[0]), y - P<R>(s.dc[1], s.f_dc[1]), z - P<R>(s.dc[2], s.f_dc[2]),
+                         P<R>(s.dh[0], s.f_dh[0]), P<R>(s.dh[1], s.f_dh[1]), P<R>(s.dh[2], s.f_dh[2]));
       return fmax(pe, pd);
     }
     case NF_SCENE_PLATE: {
-      R rx = x - R(s.pc[0]), ry = y - R(s.pc[1]), rz = z - R(s.pc[2]);
-      R c = R(s.pcos), sn = R(s.psin);
-      return box_sdf<R>(c * rx + sn * ry, -sn * rx + c * ry, rz, R(s.ph[0]),
-                        R(s.ph[1]), R(s.ph[2]));
+      R rx = x - P<R>(s.pc[0], s.f_pc[0]), ry = y - P<R>(s.pc[1], s.f_pc[1]), rz = z - P<R>(s.pc[2], s.f_pc[2]);
+      R c = P<R>(s.pcos, s.f_pcos), sn = P<R>(s.psin, s.f_psin);
+      return box_sdf<R>(c * rx + sn * ry, -sn * rx + c * ry, rz, P<R>(s.ph[0], s.f_ph[0]),
+                        P<R>(s.ph[1], s.f_ph[1]), P<R>(s.ph[2], s.f_ph[2]));
     }
     default:
       return R(1.0e3);
@@ -81,11 +125,11 @@ __device__ __forceinline__ R scene_phi(const SceneDev &s, R x, R y, R z) {
 template <class R>
 __device__ __forceinline__ bool chamber_ell_active(const SceneDev &s, R x, R y,
                                                    R z) {
-  R ex = (x - R(s.cc[0])) / R(s.ca[0]), ey = (y - R(s.cc[1])) / R(s.ca[1]),
-    ez = (z - R(s.cc[2])) / R(s.ca[2]);
-  R pe = R(s.camin) * (R(s.cs) - sqrt(ex * ex + ey * ey + ez * ez));
-  R pd = -box_sdf<R>(x - R(s.dc[0]), y - R(s.dc[1]), z - R(s.dc[2]),
-                     R(s.dh[0]), R(s.dh[1]), R(s.dh[2]));
+  R ex = (x - P<R>(s.cc[0], s.f_cc[0])) * P<R>(s.cinva[0], s.finva[0]), ey = (y - P<R>(s.cc[1], s.f_cc[1])) * P<R>(s.cinva[1], s.finva[1]),
+    ez = (z - P<R>(s.cc[2], s.f_cc[2])) * P<R>(s.cinva[2], s.finva[2]);
+  R pe = P<R>(s.camin, s.f_camin) * (P<R>(s.cs, s.f_cs) - sqrt(ex * ex + ey * ey + ez * ez));
+  R pd = -box_sdf<R>(x - P<R>(s.dc[0], s.f_dc[0]), y - P<R>(s.dc[1], s.f_dc[1]), z - P<R>(s.dc[2], s.f_dc[2]),
+                     P<R>(s.dh[0], s.f_dh[0]), P<R>(s.dh[1], s.f_dh[1]), P<R>(s.dh[2], s.f_dh[2]));
   return pe >= pd;
 }
 
@@ -95,15 +139,15 @@ __device__ __forceinline__ R scene_us(const SceneDev &s, int d, R x, R y,
                                       R z) {
   switch (s.kind) {
     case NF_SCENE_SPHERE:
-      return R(s.sv[d]);
+      return P<R>(s.sv[d], s.f_sv[d]);
     case NF_SCENE_CHAMBER: {
       if (!chamber_ell_active<R>(s, x, y, z)) return R(0);
-      R r = d == 0 ? x - R(s.cc[0]) : (d == 1 ? y - R(s.cc[1]) : z - R(s.cc[2]));
-      return R(s.crate) * r;
+      R r = d == 0 ? x - P<R>(s.cc[0], s.f_cc[0]) : (d == 1 ? y - P<R>(s.cc[1], s.f_cc[1]) : z - P<R>(s.cc[2], s.f_cc[2]));
+      return P<R>(s.crate, s.f_crate) * r;
     }
     case NF_SCENE_PLATE: {
-      if (d == 0) return -R(s.pomega) * (y - R(s.pc[1]));
-      if (d == 1) return R(s.pomega) * (x - R(s.pc[0]));
+      if (d == 0) return -P<R>(s.pomega, s.f_pomega) * (y - P<R>(s.pc[1], s.f_pc[1]));
+      if (d == 1) return P<R>(s.pomega, s.f_pomega) * (x - P<R>(s.pc[0], s.f_pc[0]));
       return R(0);
     }
     default:
@@ -139,7 +183,8 @@ __device__ __forceinline__ void scene_dphi(const SceneDev &s, double x,
       return;
     }
     default:
-      for (int k = 0; k < s.K; ++k) out[k] = 0.0;
+#pragma unroll
+      for (int k = 0; k < kMaxParams; ++k) out[k] = 0.0;
   }
 }
 
@@ -152,17 +197,18 @@ __device__ __forceinline__ void scene_dus_f(const SceneDev &s, int d, float x,
       return;
     case NF_SCENE_CHAMBER: {
       const bool e = chamber_ell_active<float>(s, x, y, z);
-      const float r = d == 0 ? x - (float)s.cc[0] : (d == 1 ? y - (float)s.cc[1] : z - (float)s.cc[2]);
-      for (int k = 0; k < 8; ++k) out[k] = e ? (float)s.cdus[k] * r : 0.f;
+      const float r = d == 0 ? x - s.f_cc[0] : (d == 1 ? y - s.f_cc[1] : z - s.f_cc[2]);
+      for (int k = 0; k < 8; ++k) out[k] = e ? s.f_cdus[k] * r : 0.f;
       return;
     }
     case NF_SCENE_PLATE: {
-      const float f = d == 0 ? -(y - (float)s.pc[1]) : (d == 1 ? (x - (float)s.pc[0]) : 0.f);
-      for (int k = 0; k < 4; ++k) out[k] = f * (float)s.pdomega[k];
+      const float f = d == 0 ? -(y - s.f_pc[1]) : (d == 1 ? (x - s.f_pc[0]) : 0.f);
+      for (int k = 0; k < 4; ++k) out[k] = f * s.f_pdomega[k];
       return;
     }
     default:
-      for (int k = 0; k < s.K; ++k) out[k] = 0.f;
+#pragma unroll
+      for (int k = 0; k < kMaxParams; ++k) out[k] = 0.f;
   }
 }
 
@@ -185,7 +231,8 @@ __device__ __forceinline__ void scene_dus(const SceneDev &s, int d, double x,
       return;
     }
     default:
-      for (int k = 0; k < s.K; ++k) out[k] = 0.0;
+#pragma unroll
+      for (int k = 0; k < kMaxParams; ++k) out[k] = 0.0;
   }
 }
 
@@ -209,6 +256,11 @@ struct LocalSdf {
   // chamber ellipsoid: e = (x_f - c0) / a, rho_c = |e|, 1 / a, amin, s
   float e[3], rho, inva[3], amin;
   double phic_ell;
+  float phic_f;         // phic_ell rounded once
+  // per-face constants of d phi / d theta, rounded to FP32 once: chamber
+  // amin * ds/dtheta_k, plate dangle/dtheta_k, sphere -t
+  float dscale[8];
+  float bh[3];          // box half extents (plate gradient)
   // boxes (duct of the chamber, plate): per-axis p and q = |p| - h at the
   // centre, and the rotation (plate) taking offsets into the box frame
   float bp[3], bq[3], rc, rs;
@@ -229,8 +281,10 @@ struct LocalSdf {
       d[0][0] = (float)a;
       d[0][1] = (float)b;
       d[0][2] = (float)c;
-      dn[0] = (float)sqrt(a * a + b * b + c * c);
-      r[0] = (float)(sqrt(a * a + b * b + c * c) - s.sr);  // phi at the centre
+      const double n = fsqrt_refined(a * a + b * b + c * c);
+      dn[0] = (float)n;
+      r[0] = (float)(n - s.sr);  // phi at the centre
+      dscale[0] = s.fdscale[0];
     } else if (kind == NF_SCENE_SPHERES) {
       // candidate spheres: within 1.6 dx (twice the control-volume radius)
       // of the best centre value can be the minimum somewhere in the volume
@@ -257,24 +311,30 @@ struct LocalSdf {
         ++nsph;
       }
     } else if (kind == NF_SCENE_CHAMBER) {
-      const double ex = (x - s.cc[0]) / s.ca[0], ey = (y - s.cc[1]) / s.ca[1],
-                   ez = (z - s.cc[2]) / s.ca[2];
-      const double rr = sqrt(ex * ex + ey * ey + ez * ez);
+      const double ex = (x - s.cc[0]) * s.cinva[0], ey = (y - s.cc[1]) * s.cinva[1],
+                   ez = (z - s.cc[2]) * s.cinva[2];
+      const double rr = fsqrt_refined(ex * ex + ey * ey + ez * ez);
       e[0] = (float)ex;
       e[1] = (float)ey;
       e[2] = (float)ez;
       rho = (float)rr;
-      inva[0] = (float)(1.0 / s.ca[0]);
-      inva[1] = (float)(1.0 / s.ca[1]);
-      inva[2] = (float)(1.0 / s.ca[2]);
-      amin = (float)s.camin;
+      inva[0] = s.finva[0];
+      inva[1] = s.finva[1];
+      inva[2] = s.finva[2];
+      amin = s.f_camin;
       phic_ell = s.camin * (s.cs - rr);
+      phic_f = (float)phic_ell;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) dscale[k] = s.fdscale[k];
       box_init(x - s.dc[0], y - s.dc[1], z - s.dc[2], s.dh);
     } else if (kind == NF_SCENE_PLATE) {
       const double rx = x - s.pc[0], ry = y - s.pc[1], rz = z - s.pc[2];
-      rc = (float)s.pcos;
-      rs = (float)s.psin;
+      rc = s.f_pcos;
+      rs = s.f_psin;
       box_init(s.pcos * rx + s.psin * ry, -s.psin * rx + s.pcos * ry, rz, s.ph);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) dscale[k] = s.fdscale[k];
+      for (int a = 0; a < 3; ++a) bh[a] = s.f_ph[a];
     }
   }
 
@@ -323,7 +383,7 @@ struct LocalSdf {
         const float num = 2.f * (e[0] * ex + e[1] * ey + e[2] * ez) +
                           (ex * ex + ey * ey + ez * ez);
         const float den = sqrtf(a * a + b * b + c * c) + rho;
-        const float pe = (float)phic_ell - amin * (den > 0.f ? num / den : 0.f);
+        const float pe = phic_f - amin * (den > 0.f ? num / den : 0.f);
         return fmaxf(pe, -box(ox, oy, oz));
       }
       case NF_SCENE_PLATE:
@@ -340,7 +400,7 @@ struct LocalSdf {
       case NF_SCENE_SPHERE: {
         const float a = d[0][0] + ox, b = d[0][1] + oy, c = d[0][2] + oz;
         const float n = sqrtf(a * a + b * b + c * c);
-        const float inv = n > 0.f ? (float)(-s.t) / n : 0.f;
+        const float inv = n > 0.f ? dscale[0] / n : 0.f;
         out[0] = a * inv;
         out[1] = b * inv;
         out[2] = c * inv;
@@ -352,23 +412,23 @@ struct LocalSdf {
         const float num = 2.f * (e[0] * ex + e[1] * ey + e[2] * ez) +
                           (ex * ex + ey * ey + ez * ez);
         const float den = sqrtf(a * a + b * b + c * c) + rho;
-        const float pe = (float)phic_ell - amin * (den > 0.f ? num / den : 0.f);
+        const float pe = phic_f - amin * (den > 0.f ? num / den : 0.f);
         const bool ell = pe >= -box(ox, oy, oz);
-        for (int k = 0; k < 8; ++k) out[k] = ell ? (float)(s.camin * s.cds[k]) : 0.f;
+        for (int k = 0; k < 8; ++k) out[k] = ell ? dscale[k] : 0.f;
         return;
       }
       case NF_SCENE_PLATE: {
         const float px = bp[0] + (rc * ox + rs * oy), py = bp[1] + (-rs * ox + rc * oy),
                     pz = bp[2] + oz;
-        double gx, gy, gz;
-        box_sdf_grad((double)px, (double)py, (double)pz, s.ph[0], s.ph[1], s.ph[2],
-                     gx, gy, gz);
-        const float dang = (float)gx * py - (float)gy * px;
-        for (int k = 0; k < 4; ++k) out[k] = dang * (float)s.pdang[k];
+        float gx, gy, gz;
+        box_sdf_grad_f(px, py, pz, bh[0], bh[1], bh[2], gx, gy, gz);
+        const float dang = gx * py - gy * px;
+        for (int k = 0; k < 4; ++k) out[k] = dang * dscale[k];
         return;
       }
       default:
-        for (int k = 0; k < s.K; ++k) out[k] = 0.f;
+  #pragma unroll
+      for (int k = 0; k < kMaxParams; ++k) out[k] = 0.f;
     }
   }
 };
