@@ -117,6 +117,11 @@ typedef struct nf_config {
                              fractions (one face triple per step), so the
                              backward pass copies them instead of
                              rasterising again; 0: recompute them           */
+  int mg_persistent;      /* 1: the coarse levels of at most 64^3 cells above
+                             the one-block chain run, with the chain, as the
+                             phases of one cooperative kernel (constant
+                             transfer only); 0: one launch per phase.
+                             Same arithmetic either way                      */
 } nf_config;
 
 typedef struct nf_grid {
@@ -155,7 +160,8 @@ typedef struct nf_step_stats {
    max_iters 500, inner_tol 1e-3, mg_smooth 2, mg_coarsest 4, RK2,
    checkpoint_every 10, no budget, cfl_max 0 (no sub-stepping),
    mg_coarsest_sweeps 8, mg_band_sweeps 0, mg_transfer 1 (constant),
-   mg_coarse_weight 1.9, mg_smooth_coarse 0, tape_fractions 0. */
+   mg_coarse_weight 1.9, mg_smooth_coarse 0, tape_fractions 0,
+   mg_persistent 1. */
 int nf_config_default(nf_config *cfg);
 
 /* Create a context on cfg->device. *out receives the handle. */
@@ -275,7 +281,8 @@ int nf_launch_count(nf_ctx *ctx, int64_t *count);
 #define NF_K_CAST 21
 #define NF_K_MG_SMOOTH0 22    /* finest level  */
 #define NF_K_GAUGE 23
-#define NF_K_COUNT 24
+#define NF_K_MG_MID 24        /* coarse levels + chain, one cooperative kernel */
+#define NF_K_COUNT 25
 
 /* Start timing launches of kernel class `kclass` (NF_K_*), or of every class
    with kclass = -1; kclass = -2 stops. Resets the accumulated totals. */

@@ -27,7 +27,7 @@ CUDA_STREAM_LEGACY = 1   # cudaStreamLegacy: the legacy default stream
 KCLASS = ["rasterize", "advect", "rhs", "update", "loss", "adj_gp", "adj_face",
           "adj_advect", "residual64", "axpy64", "cg_init", "apply_dot", "cg_xr",
           "cg_rz", "cg_d", "mg_coarsen", "mg_smooth", "mg_residual", "mg_restrict",
-          "mg_prolong", "mg_chain", "cast", "mg_smooth0", "gauge"]
+          "mg_prolong", "mg_chain", "cast", "mg_smooth0", "gauge", "mg_mid"]
 
 
 class Config(C.Structure):
@@ -40,7 +40,7 @@ class Config(C.Structure):
                 ("cfl_max", C.c_double), ("mg_coarsest_sweeps", C.c_int),
                 ("mg_band_sweeps", C.c_int), ("mg_transfer", C.c_int),
                 ("mg_coarse_weight", C.c_double), ("mg_smooth_coarse", C.c_int),
-                ("tape_fractions", C.c_int)]
+                ("tape_fractions", C.c_int), ("mg_persistent", C.c_int)]
 
 
 class Grid(C.Structure):

@@ -677,29 +677,99 @@ __global__ void k_band_smooth(LevelView<TA> lv, V *x, const V *b,
   }
 }
 
-// Red-black Gauss-Seidel half sweep over cells with (i + j + k) % 2 == color.
-template <class V, class TA>
-__global__ void k_mg_smooth(LevelView<TA> lv, V *x, const V *b, int color,
-                            const CGState *st) {
-  if (stopped(st)) return;
-  const RowWalk w;
+// New value of cell c = (i, j, k) (row = k ny + j) under a half sweep.
+template <class V, class TA, int MODE>
+__device__ __forceinline__ V sweep_cell(const LevelView<TA> &lv, const V *x,
+                                        const V *b, int i, int j, int k, int c,
+                                        int row, V cc, const Fold<V> &f) {
+  if (MODE == kSweepZero) {
+    const int nx = lv.nx, nxy = lv.nx * lv.ny, fy = c + k * nx;
+    const V dg = (V)ld(lv.ax + c + row) + (V)ld(lv.ax + c + row + 1) + (V)ld(lv.ay + fy) +
+                 (V)ld(lv.ay + fy + nx) + (V)ld(lv.az + c) + (V)ld(lv.az + c + nxy);
+    return dg > V(0) ? b[c] / (cc * dg) : V(0);
+  }
+  Nb7<V> g;
+  gather7r(g, lv, x, i, j, k, c, row);
+  if (MODE == kSweepProlong) {
+    const int cxy = f.cnx * f.cny;
+    const int pc = ((k >> 1) * f.cny + (j >> 1)) * f.cnx + (i >> 1);
+    if (i > 0) g.vxm += f.xc[(i & 1) ? pc : pc - 1] * f.w;
+    if (i < lv.nx - 1) g.vxp += f.xc[(i & 1) ? pc + 1 : pc] * f.w;
+    if (j > 0) g.vym += f.xc[(j & 1) ? pc : pc - f.cnx] * f.w;
+    if (j < lv.ny - 1) g.vyp += f.xc[(j & 1) ? pc + f.cnx : pc] * f.w;
+    if (k > 0) g.vzm += f.xc[(k & 1) ? pc : pc - cxy] * f.w;
+    if (k < lv.nz - 1) g.vzp += f.xc[(k & 1) ? pc + cxy : pc] * f.w;
+  }
+  const V dg = g.diag();
+  return dg > V(0) ? (b[c] + cc * g.nb()) / (cc * dg) : V(0);
+}
+
+// Half sweep over the rows of a level, one warp per row (warps warp,
+// warp + nwarps, ...; lanes along x).
+template <class V, class TA, int MODE>
+__device__ __forceinline__ void sweep_rows(const LevelView<TA> &lv, V *x,
+                                           const V *b, int color,
+                                           const Fold<V> &f, int warp,
+                                           int nwarps, int lane) {
   const int nrows = lv.ny * lv.nz;
   const int hx = (lv.nx + 1) >> 1;
   const V cc = V(lv.c);
-  for (int row = w.warp; row < nrows; row += w.nwarps) {
+  for (int row = warp; row < nrows; row += nwarps) {
     const int k = row / lv.ny, j = row - k * lv.ny;
     const int base = row * lv.nx;
     const int p = (j + k + color) & 1;
-    for (int m = w.lane; m < hx; m += 32) {
+    for (int m = lane; m < hx; m += 32) {
       const int i = 2 * m + p;
       if (i >= lv.nx) continue;
       const int c = base + i;
-      Nb7<V> g;
-      gather7r(g, lv, x, i, j, k, c, row);
-      const V dg = g.diag();
-      x[c] = dg > V(0) ? (b[c] + cc * g.nb()) / (cc * dg) : V(0);
+      x[c] = sweep_cell<V, TA, MODE>(lv, x, b, i, j, k, c, row, cc, f);
     }
   }
+}
+
+// Constant-transfer restriction of the residual of coarse cell (I, J, K):
+// the sum over its eight children of (b - A x) (inactive children add 0).
+template <class V, class TA>
+__device__ __forceinline__ V resrestrict_cell(const LevelView<TA> &lv,
+                                              const V *x, const V *b, int I,
+                                              int J, int K, V cc) {
+  V acc = V(0);
+#pragma unroll 2
+  for (int ch = 0; ch < 8; ++ch) {
+    const int i = 2 * I + (ch & 1), j = 2 * J + ((ch >> 1) & 1), k = 2 * K + (ch >> 2);
+    const int frow = k * lv.ny + j;
+    const int c = frow * lv.nx + i;
+    Nb7<V> g;
+    gather7r(g, lv, x, i, j, k, c, frow);
+    const V dg = g.diag();
+    if (dg > V(0)) acc += b[c] - cc * (dg * g.vc - g.nb());
+  }
+  return acc;
+}
+
+// b_c = pn / 8 sum_children (b - A x) over the coarse rows of a level.
+template <class V, class TA>
+__device__ __forceinline__ void resrestrict_rows(const LevelView<TA> &lv,
+                                                 const V *x, const V *b,
+                                                 int cnx, int cny, int cnz,
+                                                 V *bc, float pn, int warp,
+                                                 int nwarps, int lane) {
+  const int nrows = cny * cnz;
+  const V cc = V(lv.c);
+  for (int row = warp; row < nrows; row += nwarps) {
+    const int K = row / cny, J = row - K * cny;
+    for (int I = lane; I < cnx; I += 32)
+      bc[row * cnx + I] = V(0.125) * V(pn) * resrestrict_cell<V, TA>(lv, x, b, I, J, K, cc);
+  }
+}
+
+// Red-black Gauss-Seidel half sweep over cells with (i + j + k) % 2 == color.
+template <class V, class TA, int MODE>
+__global__ void k_mg_smooth(LevelView<TA> lv, V *x, const V *b, int color,
+                            Fold<V> f, const CGState *st) {
+  if (stopped(st)) return;
+  const RowWalk w;
+  sweep_rows<V, TA, MODE>(lv, x, b, color, f, w.warp, w.nwarps, w.lane);
 }
 
 // Prolongation normaliser of fine cell (i, j, k): 1 / (sum of the trilinear
@@ -801,25 +871,7 @@ __global__ void k_mg_resrestrict(LevelView<TA> lv, const V *x, const V *b,
                                  const CGState *st) {
   if (stopped(st)) return;
   const RowWalk w;
-  const int nrows = cny * cnz;
-  const V cc = V(lv.c);
-  for (int row = w.warp; row < nrows; row += w.nwarps) {
-    const int K = row / cny, J = row - K * cny;
-    for (int I = w.lane; I < cnx; I += 32) {
-      V acc = V(0);
-#pragma unroll 2
-      for (int ch = 0; ch < 8; ++ch) {
-        const int i = 2 * I + (ch & 1), j = 2 * J + ((ch >> 1) & 1), k = 2 * K + (ch >> 2);
-        const int frow = k * lv.ny + j;
-        const int c = frow * lv.nx + i;
-        Nb7<V> g;
-        gather7r(g, lv, x, i, j, k, c, frow);
-        const V dg = g.diag();
-        if (dg > V(0)) acc += b[c] - cc * (dg * g.vc - g.nb());
-      }
-      bc[row * cnx + I] = V(0.125) * V(pn) * acc;
-    }
-  }
+  resrestrict_rows<V, TA>(lv, x, b, cnx, cny, cnz, bc, pn, w.warp, w.nwarps, w.lane);
 }
 
 // x_f += P x_c on active fine cells.
@@ -929,9 +981,10 @@ k_mg_coarse_chain(CoarseChain<V, TA> ch, const CGState *st) {
 }
 
 // Shared-memory version of the chain: every array of the chain levels (x, b,
-// r and the fractions, the latter converted to FA) lives in shared memory for
-// the whole sub-V-cycle; global memory is read once (fractions, b of the
-// first chain level) and written once (x of the first chain level).
+// the fractions converted to FA, and r for the trilinear transfer) lives in
+// shared memory for the whole sub-V-cycle; global memory is read once
+// (fractions, b of the first chain level) and written once (x of the first
+// chain level).
 template <class TA>
 struct ChainFA {
   using type = float;
@@ -952,12 +1005,13 @@ __host__ __device__ inline size_t chain_layout(const CoarseChain<V, TA> &ch,
     o += (bytes + 15) & ~(size_t)15;
     return at;
   };
+  const bool need_r = ch.transfer != kTransferConstant;  // the fused restriction needs none
   for (int l = ch.first; l < ch.nlev; ++l) {
     const LevelView<TA> &v = ch.lv[l];
     const size_t nc = (size_t)v.nx * v.ny * v.nz;
     off[l][0] = take(nc * sizeof(V));
     off[l][1] = take(nc * sizeof(V));
-    off[l][2] = take(l + 1 < ch.nlev ? nc * sizeof(V) : 0);
+    off[l][2] = take(need_r && l + 1 < ch.nlev ? nc * sizeof(V) : 0);
     off[l][3] = take((size_t)(v.nx + 1) * v.ny * v.nz * sizeof(FA));
     off[l][4] = take((size_t)v.nx * (v.ny + 1) * v.nz * sizeof(FA));
     off[l][5] = take((size_t)v.nx * v.ny * (v.nz + 1) * sizeof(FA));
@@ -965,52 +1019,112 @@ __host__ __device__ inline size_t chain_layout(const CoarseChain<V, TA> &ch,
   return o;
 }
 
-template <class FA, class TA>
-__device__ void blk_load(FA *dst, const TA *src, int n) {
-  for (int t = threadIdx.x; t < n; t += blockDim.x) dst[t] = (FA)ld(src + t);
-}
-
-template <class V, class TA>
-__global__ void __launch_bounds__(1024, 1)
-k_mg_chain_smem(CoarseChain<V, TA> ch, const CGState *st) {
-  if (stopped(st)) return;
-  using FA = typename ChainFA<TA>::type;
-  extern __shared__ __align__(16) unsigned char smem[];
-  size_t off[kMaxLevels][6];
-  chain_layout(ch, off);
-  const int first = ch.first, last = ch.nlev - 1;
-  auto view = [&](int l) {
-    const LevelView<TA> &g = ch.lv[l];
-    return LevelView<FA>{g.nx, g.ny, g.nz, g.c, (const FA *)(smem + off[l][3]),
-                         (const FA *)(smem + off[l][4]),
-                         (const FA *)(smem + off[l][5])};
-  };
-  auto X = [&](int l) { return (V *)(smem + off[l][0]); };
-  auto B = [&](int l) { return (V *)(smem + off[l][1]); };
-  auto R = [&](int l) { return (V *)(smem + off[l][2]); };
-  for (int l = first; l <= last; ++l) {
-    const LevelView<TA> &g = ch.lv[l];
-    blk_load((FA *)(smem + off[l][3]), g.ax, (g.nx + 1) * g.ny * g.nz);
-    blk_load((FA *)(smem + off[l][4]), g.ay, g.nx * (g.ny + 1) * g.nz);
-    blk_load((FA *)(smem + off[l][5]), g.az, g.nx * g.ny * (g.nz + 1));
-  }
-  {
-    const int n = (int)ch.lv[first].ncell();
-    for (int t = threadIdx.x; t < n; t += blockDim.x) B(first)[t] = ch.b[first][t];
+// Half sweep of a block-resident level by the whole block (cells of one
+// colour in order, 32-bit unsigned index arithmetic).
+template <class V, class FA, int MODE>
+__device__ void blk_sweep(const LevelView<FA> &lv, V *x, const V *b, int color,
+                          const Fold<V> &f) {
+  const unsigned hx = (unsigned)(lv.nx + 1) >> 1, ny = (unsigned)lv.ny;
+  const unsigned n = hx * ny * (unsigned)lv.nz;
+  const V cc = V(lv.c);
+  for (unsigned t = threadIdx.x; t < n; t += blockDim.x) {
+    const unsigned row = t / hx, m = t - row * hx;
+    const unsigned k = row / ny, j = row - k * ny;
+    const int i = (int)(2 * m + ((j + k + color) & 1));
+    if (i >= lv.nx) continue;
+    const int c = (int)row * lv.nx + i;
+    x[c] = sweep_cell<V, FA, MODE>(lv, x, b, i, (int)j, (int)k, c, (int)row, cc, f);
   }
   __syncthreads();
+}
+
+// b_c = pn / 8 sum_children (b - A x) for every cell of a block-resident
+// coarse level.
+template <class V, class FA>
+__device__ void blk_resrestrict(const LevelView<FA> &lv, const V *x, const V *b,
+                                int cnx, int cny, int cnz, V *bc, float pn) {
+  const unsigned n = (unsigned)cnx * cny * cnz;
+  const V cc = V(lv.c);
+  for (unsigned t = threadIdx.x; t < n; t += blockDim.x) {
+    const unsigned q = t / (unsigned)cnx, I = t - q * cnx;
+    const unsigned K = q / (unsigned)cny, J = q - K * cny;
+    bc[t] = V(0.125) * V(pn) * resrestrict_cell<V, FA>(lv, x, b, (int)I, (int)J, (int)K, cc);
+  }
+  __syncthreads();
+}
+
+// Copy of n values into shared memory, eight loads in flight per thread.
+template <class D, class S>
+__device__ __forceinline__ void blk_load(D *dst, const S *src, int n) {
+  constexpr int U = 8;
+  for (int t0 = threadIdx.x; t0 < n; t0 += U * blockDim.x) {
+    D v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int t = t0 + u * blockDim.x;
+      v[u] = t < n ? (D)ld(src + t) : D(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int t = t0 + u * blockDim.x;
+      if (t < n) dst[t] = v[u];
+    }
+  }
+}
+
+// The chain's whole sub-V-cycle by one thread block in `smem` (at least
+// mg_chain_smem_bytes). Reads b of the first chain level and writes its x
+// (global memory); every other array stays in shared memory. With the
+// constant transfer the residual is restricted in one pass and the
+// prolongation is folded into the first post-smoothing half sweep.
+template <class V, class TA>
+__device__ void chain_body(const CoarseChain<V, TA> &ch, unsigned char *smem) {
+  using FA = typename ChainFA<TA>::type;
+  __shared__ unsigned soff[kMaxLevels][6];
+  if (threadIdx.x == 0) {
+    size_t off[kMaxLevels][6];
+    chain_layout(ch, off);
+    for (int l = ch.first; l < ch.nlev; ++l)
+      for (int q = 0; q < 6; ++q) soff[l][q] = (unsigned)off[l][q];
+  }
+  __syncthreads();
+  const int first = ch.first, last = ch.nlev - 1;
+  const bool fused = ch.transfer == kTransferConstant;
+  auto view = [&](int l) {
+    const LevelView<TA> &g = ch.lv[l];
+    return LevelView<FA>{g.nx, g.ny, g.nz, g.c, (const FA *)(smem + soff[l][3]),
+                         (const FA *)(smem + soff[l][4]),
+                         (const FA *)(smem + soff[l][5])};
+  };
+  auto X = [&](int l) { return (V *)(smem + soff[l][0]); };
+  auto B = [&](int l) { return (V *)(smem + soff[l][1]); };
+  auto R = [&](int l) { return (V *)(smem + soff[l][2]); };
+  const Fold<V> none{nullptr, 0, 0, V(0)};
+  blk_load(B(first), ch.b[first], (int)ch.lv[first].ncell());
   for (int l = first; l <= last; ++l) {
+    const LevelView<TA> &g = ch.lv[l];
+    blk_load((FA *)(smem + soff[l][3]), g.ax, (g.nx + 1) * g.ny * g.nz);
+    blk_load((FA *)(smem + soff[l][4]), g.ay, g.nx * (g.ny + 1) * g.nz);
+    blk_load((FA *)(smem + soff[l][5]), g.az, g.nx * g.ny * (g.nz + 1));
+  }
+  __syncthreads();
+  for (int l = first; l < last; ++l) {
     const LevelView<FA> lv = view(l);
-    const int n = (int)lv.ncell();
     V *x = X(l);
     const V *b = B(l);
-    for (int t = threadIdx.x; t < n; t += blockDim.x) x[t] = V(0);
-    __syncthreads();
-    if (l == last) break;
     for (int s = 0; s < ch.smooth; ++s) {
-      blk_smooth(lv, x, b, 0);
-      blk_smooth(lv, x, b, 1);
+      if (s == 0)
+        blk_sweep<V, FA, kSweepZero>(lv, x, b, 0, none);
+      else
+        blk_sweep<V, FA, kSweepPlain>(lv, x, b, 0, none);
+      blk_sweep<V, FA, kSweepPlain>(lv, x, b, 1, none);
     }
+    const LevelView<TA> &cv = ch.lv[l + 1];
+    if (fused) {
+      blk_resrestrict<V, FA>(lv, x, b, cv.nx, cv.ny, cv.nz, B(l + 1), ch.pnu);
+      continue;
+    }
+    const int n = (int)lv.ncell();
     V *r = R(l);
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
       const int i = t % lv.nx, q = t / lv.nx;
@@ -1018,7 +1132,6 @@ k_mg_chain_smem(CoarseChain<V, TA> ch, const CGState *st) {
       r[t] = residual_cell<V, FA>(lv, x, b, i, j, k, t) * V(ch.pn[l][t]);
     }
     __syncthreads();
-    const LevelView<TA> &cv = ch.lv[l + 1];
     const int nc = (int)cv.ncell();
     V *bc = B(l + 1);
     for (int t = threadIdx.x; t < nc; t += blockDim.x) {
@@ -1032,19 +1145,34 @@ k_mg_chain_smem(CoarseChain<V, TA> ch, const CGState *st) {
   {
     const LevelView<FA> lv = view(last);
     for (int s = 0; s < ch.coarsest_sweeps; ++s) {
-      blk_smooth(lv, X(last), B(last), 0);
-      blk_smooth(lv, X(last), B(last), 1);
+      if (s == 0)
+        blk_sweep<V, FA, kSweepZero>(lv, X(last), B(last), 0, none);
+      else
+        blk_sweep<V, FA, kSweepPlain>(lv, X(last), B(last), 0, none);
+      blk_sweep<V, FA, kSweepPlain>(lv, X(last), B(last), 1, none);
     }
     for (int s = 0; s < ch.coarsest_sweeps; ++s) {
-      blk_smooth(lv, X(last), B(last), 1);
-      blk_smooth(lv, X(last), B(last), 0);
+      blk_sweep<V, FA, kSweepPlain>(lv, X(last), B(last), 1, none);
+      blk_sweep<V, FA, kSweepPlain>(lv, X(last), B(last), 0, none);
     }
   }
   for (int l = last - 1; l >= first; --l) {
     const LevelView<FA> lv = view(l);
     const LevelView<TA> &cv = ch.lv[l + 1];
-    const int n = (int)lv.ncell();
     V *x = X(l);
+    const V *b = B(l);
+    if (fused) {
+      const Fold<V> f{X(l + 1), cv.nx, cv.ny, V(ch.pnu)};
+      for (int s = 0; s < ch.smooth; ++s) {
+        if (s == 0)
+          blk_sweep<V, FA, kSweepProlong>(lv, x, b, 1, f);
+        else
+          blk_sweep<V, FA, kSweepPlain>(lv, x, b, 1, none);
+        blk_sweep<V, FA, kSweepPlain>(lv, x, b, 0, none);
+      }
+      continue;
+    }
+    const int n = (int)lv.ncell();
     const V *xc = X(l + 1);
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
       const int i = t % lv.nx, q = t / lv.nx;
@@ -1055,14 +1183,115 @@ k_mg_chain_smem(CoarseChain<V, TA> ch, const CGState *st) {
     }
     __syncthreads();
     for (int s = 0; s < ch.smooth; ++s) {
-      blk_smooth(lv, x, B(l), 1);
-      blk_smooth(lv, x, B(l), 0);
+      blk_sweep<V, FA, kSweepPlain>(lv, x, b, 1, none);
+      blk_sweep<V, FA, kSweepPlain>(lv, x, b, 0, none);
     }
   }
   {
     const int n = (int)ch.lv[first].ncell();
     const V *x = X(first);
     for (int t = threadIdx.x; t < n; t += blockDim.x) ch.x[first][t] = x[t];
+  }
+}
+
+template <class V, class TA>
+__global__ void __launch_bounds__(1024, 1)
+k_mg_chain_smem(CoarseChain<V, TA> ch, const CGState *st) {
+  if (stopped(st)) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  chain_body<V, TA>(ch, smem);
+}
+
+// ------------------------------------------------ persistent mid levels ---
+// Levels too small to fill the GPU with one launch per half sweep (each
+// launch costs a few microseconds of issue and tail) and too large for one
+// thread block run inside one cooperative kernel: every phase (half sweep,
+// fused residual-restriction, the first post-smoothing half sweep with the
+// prolongation folded in) is a grid-stride loop over rows, consecutive
+// phases are separated by a grid-wide barrier, and between the down and the
+// up sweep block 0 runs the shared-memory chain while the others wait.
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier of a cooperative launch: every block adds one to *bar
+// and waits until it reaches target (phases so far x blocks). Each wait is
+// bounded: after kBarrierNs the waiting block sets *err, and every block
+// leaves at its next barrier. Returns false (the same in all threads of the
+// block) when the kernel must stop.
+constexpr unsigned long long kBarrierNs = 1000000000ull;
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target,
+                                             int *err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    const unsigned long long t0 = globaltimer_ns();
+    int e = 0;
+    while (*(volatile unsigned *)bar < target) {
+      if ((e = *(volatile int *)err) != 0) break;
+      if (globaltimer_ns() - t0 > kBarrierNs) {
+        atomicExch(err, 1);
+        e = 1;
+        break;
+      }
+      __nanosleep(20);
+    }
+    __threadfence();
+    ok = e == 0;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <class V, class TA>
+__global__ void __launch_bounds__(1024, 1)
+k_mg_mid(MidSpan<V, TA> m, CoarseChain<V, TA> ch, const CGState *st) {
+  if (stopped(st) || *(volatile int *)m.err != 0) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const RowWalk rw;
+  const Fold<V> none{nullptr, 0, 0, V(0)};
+  unsigned phase = 0;
+  auto sync = [&]() { return grid_barrier(m.bar, ++phase * gridDim.x, m.err); };
+  for (int l = m.lo; l < m.hi; ++l) {
+    const LevelView<TA> lv = m.lv[l];
+    V *x = m.x[l];
+    const V *b = m.b[l];
+    for (int s = 0; s < m.smooth; ++s) {
+      if (s == 0)
+        sweep_rows<V, TA, kSweepZero>(lv, x, b, 0, none, rw.warp, rw.nwarps, rw.lane);
+      else
+        sweep_rows<V, TA, kSweepPlain>(lv, x, b, 0, none, rw.warp, rw.nwarps, rw.lane);
+      if (!sync()) return;
+      sweep_rows<V, TA, kSweepPlain>(lv, x, b, 1, none, rw.warp, rw.nwarps, rw.lane);
+      if (!sync()) return;
+    }
+    const LevelView<TA> cv = m.lv[l + 1];
+    resrestrict_rows<V, TA>(lv, x, b, cv.nx, cv.ny, cv.nz, m.b[l + 1], m.w, rw.warp,
+                            rw.nwarps, rw.lane);
+    if (!sync()) return;
+  }
+  if (blockIdx.x == 0) chain_body<V, TA>(ch, smem);
+  if (!sync()) return;
+  for (int l = m.hi - 1; l >= m.lo; --l) {
+    const LevelView<TA> lv = m.lv[l];
+    V *x = m.x[l];
+    const V *b = m.b[l];
+    const Fold<V> f{m.x[l + 1], m.lv[l + 1].nx, m.lv[l + 1].ny, V(m.w)};
+    for (int s = 0; s < m.smooth; ++s) {
+      if (s == 0)
+        sweep_rows<V, TA, kSweepProlong>(lv, x, b, 1, f, rw.warp, rw.nwarps, rw.lane);
+      else
+        sweep_rows<V, TA, kSweepPlain>(lv, x, b, 1, none, rw.warp, rw.nwarps, rw.lane);
+      if (!sync()) return;
+      sweep_rows<V, TA, kSweepPlain>(lv, x, b, 0, none, rw.warp, rw.nwarps, rw.lane);
+      // the end of the kernel orders the last phase before the next launch
+      if (l > m.lo || s + 1 < m.smooth)
+        if (!sync()) return;
+    }
   }
 }
 
@@ -1140,9 +1369,16 @@ void launch_mg_coarsen(const Launch &L, const LevelView<TI> &fine, int cnx,
 }
 template <class V, class TA>
 void launch_mg_smooth(const Launch &L, const LevelView<TA> &lv, V *x,
-                      const V *b, int color, const CGState *st, int kclass) {
+                      const V *b, int color, int mode, const Fold<V> &f,
+                      const CGState *st, int kclass) {
   ProfScope _ps(L, kclass);
-  k_mg_smooth<V, TA><<<row_blocks(lv.ny * lv.nz), kBlock, 0, L.s>>>(lv, x, b, color, st);
+  const unsigned nb = row_blocks(lv.ny * lv.nz);
+  if (mode == kSweepZero)
+    k_mg_smooth<V, TA, kSweepZero><<<nb, kBlock, 0, L.s>>>(lv, x, b, color, f, st);
+  else if (mode == kSweepProlong)
+    k_mg_smooth<V, TA, kSweepProlong><<<nb, kBlock, 0, L.s>>>(lv, x, b, color, f, st);
+  else
+    k_mg_smooth<V, TA, kSweepPlain><<<nb, kBlock, 0, L.s>>>(lv, x, b, color, f, st);
   ++*L.counter;
 }
 template <class TA>
@@ -1219,11 +1455,48 @@ size_t mg_chain_smem_bytes(const CoarseChain<V, TA> &ch) {
   size_t off[kMaxLevels][6];
   return chain_layout(ch, off);
 }
+// Allow a kernel the opt-in shared memory left beside its static shared
+// variables as dynamic shared memory.
+template <class K>
+static cudaError_t allow_dynamic_smem(K kernel, int smem_limit) {
+  cudaFuncAttributes a{};
+  cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              smem_limit - (int)a.sharedSizeBytes);
+}
 template <class V, class TA>
 int prepare_mg_chain(int smem_limit) {
-  const cudaError_t e = cudaFuncSetAttribute(
-      k_mg_chain_smem<V, TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_limit);
+  const cudaError_t e = allow_dynamic_smem(k_mg_chain_smem<V, TA>, smem_limit);
   return e == cudaSuccess ? NF_OK : cuda_fail(e, "cudaFuncSetAttribute(chain)");
+}
+template <class V, class TA>
+int prepare_mg_mid(int smem_limit, int smem) {
+  int dev = 0, coop = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      allow_dynamic_smem(k_mg_mid<V, TA>, smem_limit) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mg_mid<V, TA>, 1024, smem) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return coop ? per_sm * sms : 0;
+}
+template <class V, class TA>
+int launch_mg_mid(const Launch &L, const MidSpan<V, TA> &m,
+                  const CoarseChain<V, TA> &ch, const CGState *st, int blocks) {
+  ProfScope _ps(L, NF_K_MG_MID);
+  cudaMemsetAsync(m.bar, 0, sizeof(unsigned), L.s);
+  MidSpan<V, TA> a0 = m;
+  CoarseChain<V, TA> a1 = ch;
+  const CGState *a2 = st;
+  void *args[] = {(void *)&a0, (void *)&a1, (void *)&a2};
+  const cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_mg_mid<V, TA>, dim3(blocks),
+                                                    dim3(1024), args, (size_t)ch.smem_bytes, L.s);
+  ++*L.counter;
+  return e == cudaSuccess ? NF_OK : cuda_fail(e, "cooperative launch (k_mg_mid)");
 }
 template <class V, class TA>
 void launch_mg_coarse_chain(const Launch &L, const CoarseChain<V, TA> &ch,
@@ -1255,8 +1528,8 @@ void launch_mg_coarse_chain(const Launch &L, const CoarseChain<V, TA> &ch,
                                         const V *, V *, CGState *,            \
                                         const RedScratch &);                  \
   template void launch_mg_smooth<V, TA>(const Launch &, const LevelView<TA> &,\
-                                        V *, const V *, int, const CGState *, \
-                                        int);                                 \
+                                        V *, const V *, int, int,             \
+                                        const Fold<V> &, const CGState *, int);\
   template void launch_band_smooth<V, TA>(const Launch &,                    \
                                           const LevelView<TA> &, V *,         \
                                           const V *, const int *,             \
@@ -1277,7 +1550,11 @@ void launch_mg_coarse_chain(const Launch &L, const CoarseChain<V, TA> &ch,
                                               const CoarseChain<V, TA> &,     \
                                               const CGState *);               \
   template size_t mg_chain_smem_bytes<V, TA>(const CoarseChain<V, TA> &);    \
-  template int prepare_mg_chain<V, TA>(int);
+  template int prepare_mg_chain<V, TA>(int);                                 \
+  template int prepare_mg_mid<V, TA>(int, int);                              \
+  template int launch_mg_mid<V, TA>(const Launch &, const MidSpan<V, TA> &,  \
+                                    const CoarseChain<V, TA> &,               \
+                                    const CGState *, int);
 NF_INST_V(float)
 NF_INST_V(double)
 template void launch_band_build<float>(const Launch &, const LevelView<float> &,

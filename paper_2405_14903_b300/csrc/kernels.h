@@ -31,6 +31,7 @@ struct CGState {
   double stop2;  // stop when <r, r> <= stop2
   int iters;
   int done;      // 0 running, 1 converged, 2 breakdown, 3 non-finite
+  int err;       // set by the device when a bounded wait expired (host resets)
 };
 
 // One multigrid level: dimensions, operator scale c = dt / (rho dx_l) and
@@ -115,12 +116,36 @@ void launch_cg_d(const Launch &L, int64_t n, const V *z, V *d,
                  const CGState *st);
 
 // Multigrid pieces.
+// What a red-black half sweep folds into the x it reads (all three give
+// the same cell values as the separate passes they replace):
+//  kSweepPlain   x as stored;
+//  kSweepZero    x = 0 before the sweep: the first half sweep of a level
+//                from a zero guess reads no x and needs no zeroing pass (the
+//                cells of the other colour are written by the next half
+//                sweep, which does not read them);
+//  kSweepProlong x += w P x_c before the sweep, P the constant transfer on
+//                active cells: only the other colour's prolonged values are
+//                read (the swept colour is overwritten without being read,
+//                and the next half sweep overwrites the other colour), so
+//                the correction is added on the fly and never stored. An
+//                inactive neighbour has a zero fraction towards the cell, so
+//                adding its correction changes nothing.
+constexpr int kSweepPlain = 0, kSweepZero = 1, kSweepProlong = 2;
+template <class V>
+struct Fold {
+  const V *xc;  // coarse correction (kSweepProlong)
+  int cnx, cny;
+  V w;          // uniform normaliser (sqrt of the coarse-correction weight)
+};
+
 template <class TI, class TO>
 void launch_mg_coarsen(const Launch &L, const LevelView<TI> &fine,
                        int cnx, int cny, int cnz, TO *ax, TO *ay, TO *az);
+// Red-black half sweep of colour `color`; mode kSweep* with its fold f.
 template <class V, class TA>
 void launch_mg_smooth(const Launch &L, const LevelView<TA> &lv, V *x,
-                      const V *b, int color, const CGState *st, int kclass);
+                      const V *b, int color, int mode, const Fold<V> &f,
+                      const CGState *st, int kclass);
 // r = N (b - A x) with N the prolongation normaliser pn (null: N = I).
 template <class V, class TA>
 void launch_mg_residual(const Launch &L, const LevelView<TA> &lv, const V *x,
@@ -163,10 +188,36 @@ struct CoarseChain {
   int smooth;         // sweeps per level
   int coarsest_sweeps;
   int smem_bytes;     // > 0: run the chain in that much dynamic shared memory
+  float pnu;          // constant transfer: the uniform normaliser (pn's value)
 };
 template <class V, class TA>
 void launch_mg_coarse_chain(const Launch &L, const CoarseChain<V, TA> &ch,
                             const CGState *st);
+// Levels lo .. hi-1 of a V-cycle run as phases of one cooperative kernel
+// (k_mg_mid), level hi and below by its block 0 as the shared-memory chain.
+// Constant transfer only. x of level lo is not read (the first half sweep
+// starts from zero); x of level lo holds the post-smoothed correction after.
+template <class V, class TA>
+struct MidSpan {
+  int lo, hi;
+  int smooth;         // sweeps per level
+  float w;            // uniform normaliser of the constant transfer
+  LevelView<TA> lv[kMaxLevels];
+  V *x[kMaxLevels];
+  V *b[kMaxLevels];
+  unsigned *bar;      // barrier counter (zeroed by the launcher)
+  int *err;           // set to 1 when a barrier wait expired
+};
+// Launches k_mg_mid cooperatively on `blocks` blocks of 1024 threads with
+// the chain's shared memory; returns NF_OK or NF_E_CUDA.
+template <class V, class TA>
+int launch_mg_mid(const Launch &L, const MidSpan<V, TA> &m,
+                  const CoarseChain<V, TA> &ch, const CGState *st, int blocks);
+// Co-resident blocks of k_mg_mid with `smem` bytes of dynamic shared memory
+// on the current device (0: the cooperative path is unavailable).
+template <class V, class TA>
+int prepare_mg_mid(int smem_limit, int smem);
+
 // Boundary band of the finest level: active cells with a face alpha < 1 and
 // their active neighbours, listed per colour (count[0], count[1]).
 template <class TA>

@@ -99,15 +99,36 @@ class Solver {
       }
       // run the chain from shared memory when all of its levels fit
       const int nl = (int)levels_.size();
+      const int down = std::min(std::max(1, first_chain_), nl - 1);
+      int limit = 0;
       if (nl > 1) {
-        int dev = 0, limit = 0;
+        int dev = 0;
         CKC(cudaGetDevice(&dev));
         CKC(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        const size_t need = mg_chain_smem_bytes(chain(std::min(std::max(1, first_chain_), nl - 1)));
-        if (need <= (size_t)limit) {
+        // (headroom for the kernels' few static shared variables)
+        const size_t need = mg_chain_smem_bytes(chain(down));
+        if (need + 1024 <= (size_t)limit) {
           const int rc = prepare_mg_chain<V, TA>(limit);
           if (rc != NF_OK) return rc;
           chain_smem_ = (int)need;
+        }
+      }
+      // the small grid levels above the chain (at most kMidCells cells)
+      // run, with the chain, inside one cooperative kernel: one warp per row
+      // of the largest of them, capped at the co-resident blocks
+      if (cfg_.mg_persistent && cfg_.mg_transfer == 1 && chain_smem_ > 0 && nl > 2) {
+        int lo = down;
+        while (lo > 1 && (int64_t)levels_[lo - 1].nx * levels_[lo - 1].ny * levels_[lo - 1].nz <=
+                             kMidCells)
+          --lo;
+        if (lo < down) {
+          const int cap = prepare_mg_mid<V, TA>(limit, chain_smem_);
+          const int want = (levels_[lo].ny * levels_[lo].nz + 31) / 32;
+          if (cap > 0) {
+            CKS(A.get(&bar_, sizeof(unsigned)));
+            mid_lo_ = lo;
+            mid_blocks_ = std::min(cap, std::max(1, want));
+          }
         }
       }
     }
@@ -136,8 +157,7 @@ class Solver {
     }
     for (size_t l = 0; l + 1 < levels_.size(); ++l) {
       const Level &F = levels_[l];
-      // sqrt of the coarse-correction weight on each side keeps R' = P'^T / 4
-      const float w = (float)std::sqrt(cfg_.mg_coarse_weight > 0 ? cfg_.mg_coarse_weight : 1.0);
+      const float w = coarse_w();
       if (cfg_.mg_transfer == 0)
         launch_mg_pnorm<TA>(L, F.nx, F.ny, F.nz, viewc(l + 1), (float *)F.pn, w);
       else  // a constant P needs no normaliser
@@ -150,6 +170,7 @@ class Solver {
     SolveStats out;
     Launch L = ctx_->launch();
     cudaMemsetAsync(x, 0, n_ * sizeof(S), L.s);
+    cudaMemsetAsync(&((CGState *)st_)->err, 0, sizeof(int), L.s);
     if (!(bnorm2 > 0.0)) {
       out.rel = 0.0;
       if (!std::isfinite(bnorm2)) out.status = NF_E_DIVERGED;
@@ -185,6 +206,10 @@ class Solver {
       prev_scale = scale;
       total += it;
       out.outer += 1;
+      if (done == 5) {  // a bounded device wait expired
+        out.status = NF_E_TIMEOUT;
+        break;
+      }
       launch_axpy_outer<S, V>(L, n_, x, (const V *)e_, 1.0 / scale);
       // next scale from the inner recurrence's final residual (unscaled),
       // floored at the V rounding level of the current residual
@@ -225,9 +250,18 @@ class Solver {
   };
   static constexpr int kMaxOuter = 12;
   static constexpr int kChainCells = 16 * 16 * 16;
+  static constexpr int64_t kMidCells = 64 * 64 * 64;
   static constexpr int kBatch = 4;
   int coarsest_sweeps() const {
     return cfg_.mg_coarsest_sweeps > 0 ? cfg_.mg_coarsest_sweeps : 8;
+  }
+  // sqrt of the coarse-correction weight, applied on each side (P' = w P,
+  // R' = w R) so that R' = P'^T / 8 stays the transpose pair
+  float coarse_w() const {
+    return (float)std::sqrt(cfg_.mg_coarse_weight > 0 ? cfg_.mg_coarse_weight : 1.0);
+  }
+  int nu_coarse() const {
+    return cfg_.mg_smooth_coarse > 0 ? cfg_.mg_smooth_coarse : std::max(1, cfg_.mg_smooth);
   }
 
   LevelView<T> view0() const {
@@ -252,12 +286,13 @@ class Solver {
     return ctx_->read_double((double *)norm2_);
   }
 
-  void smooth(int l, V *x, const V *b, int color, const CGState *st) {
+  void smooth(int l, V *x, const V *b, int color, const CGState *st,
+              int mode = kSweepPlain, const Fold<V> &f = Fold<V>{nullptr, 0, 0, V(0)}) {
     Launch L = ctx_->launch();
     if (l == 0)
-      launch_mg_smooth<V, T>(L, view0(), x, b, color, st, NF_K_MG_SMOOTH0);
+      launch_mg_smooth<V, T>(L, view0(), x, b, color, mode, f, st, NF_K_MG_SMOOTH0);
     else
-      launch_mg_smooth<V, TA>(L, viewc(l), x, b, color, st, NF_K_MG_SMOOTH);
+      launch_mg_smooth<V, TA>(L, viewc(l), x, b, color, mode, f, st, NF_K_MG_SMOOTH);
   }
 
   // Extra sweeps on the finest level's boundary band: red-black before the
@@ -293,10 +328,27 @@ class Solver {
       ch.pn[l] = (const float *)levels_[l].pn;
     }
     ch.transfer = cfg_.mg_transfer;
-    ch.smooth = cfg_.mg_smooth_coarse > 0 ? cfg_.mg_smooth_coarse : std::max(1, cfg_.mg_smooth);
+    ch.smooth = nu_coarse();
     ch.coarsest_sweeps = coarsest_sweeps();
     ch.smem_bytes = chain_smem_;
+    ch.pnu = coarse_w();
     return ch;
+  }
+
+  MidSpan<V, TA> mid(int lo, int hi) const {
+    MidSpan<V, TA> m{};
+    m.lo = lo;
+    m.hi = hi;
+    m.smooth = nu_coarse();
+    m.w = coarse_w();
+    for (int l = lo; l <= hi; ++l) {
+      m.lv[l] = viewc(l);
+      m.x[l] = (V *)levels_[l].x;
+      m.b[l] = (V *)levels_[l].b;
+    }
+    m.bar = (unsigned *)bar_;
+    m.err = &((CGState *)st_)->err;
+    return m;
   }
 
   // z = M r: one symmetric V-cycle (red-black pre-smoothing, black-red
@@ -314,25 +366,65 @@ class Solver {
   void vcycle(const V *r, V *z, const CGState *st) {
     Launch L = ctx_->launch();
     const int nl = (int)levels_.size();
+    if (nl == 1) {
+      // no coarser grid: symmetric Gauss-Seidel sweeps only
+      cudaMemsetAsync(z, 0, n_ * sizeof(V), L.s);
+      for (int s = 0; s < coarsest_sweeps(); ++s) {
+        smooth(0, z, r, 0, st);
+        smooth(0, z, r, 1, st);
+      }
+      for (int s = 0; s < coarsest_sweeps(); ++s) {
+        smooth(0, z, r, 1, st);
+        smooth(0, z, r, 0, st);
+      }
+      return;
+    }
     const int F = std::max(1, first_chain_);  // level 0 always on grid kernels
-    const int nu0 = std::max(1, cfg_.mg_smooth);
-    const int nuc = cfg_.mg_smooth_coarse > 0 ? cfg_.mg_smooth_coarse : nu0;
     const int down = std::min(F, nl - 1);     // levels with a coarser level
-    for (int l = 0; l < down; ++l) {
+    // levels [0, gl) as one launch per phase; [gl, down) and the chain in
+    // one cooperative kernel when that is set up, else per phase too
+    const int gl = mid_lo_ > 0 ? mid_lo_ : down;
+    down_levels(0, gl, r, z, st);
+    bool done = false;
+    if (mid_lo_ > 0) {
+      if (launch_mg_mid<V, TA>(L, mid(gl, down), chain(down), st, mid_blocks_) == NF_OK) {
+        done = true;
+      } else {  // no cooperative launch here: per-phase launches from now on
+        cudaGetLastError();
+        mid_lo_ = 0;
+      }
+    }
+    if (!done) {
+      down_levels(gl, down, r, z, st);
+      launch_mg_coarse_chain<V, TA>(L, chain(down), st);
+      up_levels(gl, down, r, z, st);
+    }
+    up_levels(0, gl, r, z, st);
+  }
+
+  // Pre-smoothing and restriction of levels lo .. hi-1 (level 0: x = z,
+  // b = r), one launch per phase. x starts from zero: the first half sweep
+  // reads no x, unless the boundary band sweeps first.
+  void down_levels(int lo, int hi, const V *r, V *z, const CGState *st) {
+    Launch L = ctx_->launch();
+    for (int l = lo; l < hi; ++l) {
       V *x = l == 0 ? z : (V *)levels_[l].x;
       const V *b = l == 0 ? r : (const V *)levels_[l].b;
-      const int64_t nc = (int64_t)levels_[l].nx * levels_[l].ny * levels_[l].nz;
-      cudaMemsetAsync(x, 0, nc * sizeof(V), L.s);
-      if (l == 0) band(x, b, 0, st);
-      const int nu = l == 0 ? nu0 : nuc;
+      const bool banded = l == 0 && band_count_;
+      if (banded) {
+        const int64_t nc = (int64_t)levels_[l].nx * levels_[l].ny * levels_[l].nz;
+        cudaMemsetAsync(x, 0, nc * sizeof(V), L.s);
+        band(x, b, 0, st);
+      }
+      const int nu = l == 0 ? std::max(1, cfg_.mg_smooth) : nu_coarse();
       for (int s = 0; s < nu; ++s) {
-        smooth(l, x, b, 0, st);
+        smooth(l, x, b, 0, st, s == 0 && !banded ? kSweepZero : kSweepPlain);
         smooth(l, x, b, 1, st);
       }
       const Level &C = levels_[l + 1];
       if (cfg_.mg_transfer == 1) {
         // constant transfer: residual and restriction in one pass
-        const float w = (float)std::sqrt(cfg_.mg_coarse_weight > 0 ? cfg_.mg_coarse_weight : 1.0);
+        const float w = coarse_w();
         if (l == 0)
           launch_mg_resrestrict<V, T>(L, view0(), x, b, C.nx, C.ny, C.nz, (V *)C.b, w, st);
         else
@@ -348,33 +440,31 @@ class Solver {
                                   cfg_.mg_transfer, st);
       }
     }
-    if (nl == 1) {
-      // no coarser grid: symmetric Gauss-Seidel sweeps only
-      cudaMemsetAsync(z, 0, n_ * sizeof(V), L.s);
-      for (int s = 0; s < coarsest_sweeps(); ++s) {
-        smooth(0, z, r, 0, st);
-        smooth(0, z, r, 1, st);
-      }
-      for (int s = 0; s < coarsest_sweeps(); ++s) {
-        smooth(0, z, r, 1, st);
-        smooth(0, z, r, 0, st);
-      }
-      return;
-    }
-    launch_mg_coarse_chain<V, TA>(L, chain(down), st);
-    for (int l = down - 1; l >= 0; --l) {
+  }
+
+  // Prolongation and post-smoothing of levels hi-1 .. lo. With the constant
+  // transfer the prolongation is folded into the first half sweep.
+  void up_levels(int lo, int hi, const V *r, V *z, const CGState *st) {
+    Launch L = ctx_->launch();
+    for (int l = hi - 1; l >= lo; --l) {
       V *x = l == 0 ? z : (V *)levels_[l].x;
       const V *b = l == 0 ? r : (const V *)levels_[l].b;
-      if (l == 0)
-        launch_mg_prolong<V, T, TA>(L, view0(), viewc(l + 1),
-                                    (const V *)levels_[l + 1].x, x, pnorm(0),
+      const Level &C = levels_[l + 1];
+      const int nu = l == 0 ? std::max(1, cfg_.mg_smooth) : nu_coarse();
+      int s = 0;
+      if (cfg_.mg_transfer == 1) {
+        const Fold<V> f{(const V *)C.x, C.nx, C.ny, V(coarse_w())};
+        smooth(l, x, b, 1, st, kSweepProlong, f);
+        smooth(l, x, b, 0, st);
+        s = 1;
+      } else if (l == 0) {
+        launch_mg_prolong<V, T, TA>(L, view0(), viewc(l + 1), (const V *)C.x, x, pnorm(0),
                                     cfg_.mg_transfer, st);
-      else
-        launch_mg_prolong<V, TA, TA>(L, viewc(l), viewc(l + 1),
-                                     (const V *)levels_[l + 1].x, x, pnorm(l),
+      } else {
+        launch_mg_prolong<V, TA, TA>(L, viewc(l), viewc(l + 1), (const V *)C.x, x, pnorm(l),
                                      cfg_.mg_transfer, st);
-      const int nu = l == 0 ? nu0 : nuc;
-      for (int s = 0; s < nu; ++s) {
+      }
+      for (; s < nu; ++s) {
         smooth(l, x, b, 1, st);
         smooth(l, x, b, 0, st);
       }
@@ -534,10 +624,10 @@ class Solver {
         ctx_->prof.collect(batch_g_[pv].ev, ran > 0 ? ran : 0);
       }
       seen = hs.iters;
-      if (hs.done) break;
+      if (hs.done || hs.err) break;
     }
     *iters = hs.iters;
-    *done = hs.done;
+    *done = hs.err ? 5 : hs.done;
     *rr = hs.rr;
   }
 
@@ -548,6 +638,9 @@ class Solver {
   bool mg_ = false;
   int first_chain_ = 0;
   int chain_smem_ = 0;  // dynamic shared memory of the chain kernel (0: global)
+  int mid_lo_ = 0;      // first level inside the cooperative kernel (0: none)
+  int mid_blocks_ = 0;  // its grid
+  void *bar_ = nullptr; // its barrier counter
   void *band_mark_ = nullptr, *band_list_[2] = {nullptr, nullptr}, *band_count_ = nullptr;
   std::vector<Level> levels_;
   const T *ax0_ = nullptr, *ay0_ = nullptr, *az0_ = nullptr;

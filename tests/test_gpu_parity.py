@@ -306,3 +306,34 @@ def test_multigrid_variants_match_oracle(nf, prec, variant):
     gth, _, st = ep.backward(gU)
     assert abs(J - Jo) <= VEL_TOL[prec] * abs(Jo)
     assert np.linalg.norm(gth - gtho) <= GRAD_TOL[prec] * np.linalg.norm(gtho)
+
+
+# ------------------------------------------- persistent coarse levels ----
+# From 48^3 up, coarse levels of at most 64^3 cells lie between the finest
+# levels (one launch per phase) and the one-block chain; they run as the
+# phases of one cooperative kernel unless mg_persistent is off. Both paths
+# do the same per-cell arithmetic, so they take the same iterations.
+
+@functools.lru_cache(maxsize=None)
+def oracle_projection(n, kind):
+    cfg = I.config_sphere(n, steps=0) if kind == "sphere" else I.config_spheres(n, count=8)
+    U, _ = S.initial_projection(Grid(cfg["grid"]), cfg["scene"], cfg["u0"], 1e-12)
+    return cfg, U
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
+@pytest.mark.parametrize("case", [(64, "sphere"), (48, "spheres")], ids=["sphere64", "spheres48"])
+def test_persistent_coarse_levels_match_per_phase_launches_and_oracle(nf, prec, case):
+    cfg, U_ref = oracle_projection(*case)
+    out = {}
+    for persistent in (True, False):
+        ctx = make_ctx(nf, prec, mg_persistent=persistent)
+        ep = ctx.episode(cfg["grid"], cfg["scene"])
+        st = ep.set_velocity(device_u(cfg), project=True)
+        out[persistent] = (st, host(ep.velocity()))
+        ep.close()
+        ctx.close()
+    (sp, up), (sn, un) = out[True], out[False]
+    assert sp["iters"] == sn["iters"] and sp["outer"] == sn["outer"]
+    assert rel(up, un) <= (1e-12 if prec == "fp64" else 1e-6)
+    assert rel(up, U_ref) <= VEL_TOL[prec]
