@@ -176,8 +176,11 @@ def alg_bytes_per_cell(kclass, nu):
 
 # DRAM bytes per cell of one launch (dram__bytes_read.sum +
 # dram__bytes_write.sum from one ncu capture, divided by the level's cells),
-# for kernels unchanged since their capture; None otherwise.
-DRAM_BYTES_PER_CELL = {}
+# for kernels unchanged since their capture; None otherwise. mg_smooth0: the
+# V-cycle's mix of the three half-sweep modes (zero start 26.39 MB, six plain
+# 34.78 MB, prolongation folded 35.83 MB; writes stay in L2) at 128^3,
+# profiles/k_mg_smooth_chamber128.md.
+DRAM_BYTES_PER_CELL = {"mg_smooth0": (26.39 + 6 * 34.78 + 35.83) * 1e6 / 8 / 128 ** 3}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -291,8 +294,10 @@ def run_ours(args, rank, world, local_rank):
     out["roofline"] = dict(bound="hbm", kernel=roof_class, achieved=achieved, peak=peak,
                            peak_source=src, unit="GB/s",
                            frac=(achieved / peak) if achieved else None,
+                           # the capture was taken at 128^3 (cold cache under ncu)
                            traffic=(DRAM_BYTES_PER_CELL[roof_class] * ncell
-                                    if DRAM_BYTES_PER_CELL.get(roof_class) else None),
+                                    if DRAM_BYTES_PER_CELL.get(roof_class) and n == 128
+                                    and args.mg_smooth == 2 else None),
                            launches=nl, avg_us=1e3 * avg_ms, alg_bytes_per_launch=per_launch,
                            timing="CUDA events around every launch of the kernel, over one "
                                   "step of the same workload run right after the timed region")

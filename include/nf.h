@@ -255,6 +255,9 @@ int nf_get_step(nf_ctx *ctx, int64_t id, int *n);
 int nf_launch_count(nf_ctx *ctx, int64_t *count);
 
 /* ------------------------------------------------------------- profiling */
+/* Environment: NF_GRAPHS=0 makes the solver launch every kernel directly
+   instead of replaying CUDA graphs of its iteration batches (for profilers
+   that cannot follow stream capture). Kernels and results are unchanged. */
 /* Kernel classes that nf_profile can time (CUDA events on the context's
    stream bracketing every launch of the class). */
 #define NF_K_RASTERIZE 0

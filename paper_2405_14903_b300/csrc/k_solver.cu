@@ -5,6 +5,8 @@
 // smoothing, trilinear prolongation, restriction R = P^T / 4, coarse
 // fractions = mean of the four fine sub-faces, operator rediscretised with
 // c_l = dt / (rho dx_l)).
+#include <cmath>
+
 #include "kernels.h"
 #include "util.h"
 
@@ -300,8 +302,10 @@ inline unsigned row_blocks(int nrows) {
 }
 
 // ------------------------------------------------------ outer residual -----
+// r = b - A x in FP64 arithmetic, scaled into rin (V), and ||r||^2 (FP64
+// per-thread partials, block and grid sums).
 template <class S, class T, class V>
-__global__ void k_residual_outer(LevelView<T> lv, const S *b, const S *x, S *r,
+__global__ void k_residual_outer(LevelView<T> lv, const S *b, const S *x,
                                  V *rin, double scale, RedScratch rs,
                                  double *norm2) {
   double v[1] = {0.0};
@@ -317,13 +321,111 @@ __global__ void k_residual_outer(LevelView<T> lv, const S *b, const S *x, S *r,
       const double dg = g.diag();
       double rv = 0.0;
       if (dg > 0.0) rv = (double)b[c] - lv.c * (dg * g.vc - g.nb());
-      r[c] = (S)rv;
-      if (rin) rin[c] = (V)(rv * scale);
+      rin[c] = (V)(rv * scale);
       v[0] += rv * rv;
     }
   }
   double tot[1];
   if (grid_sum<1>(v, rs, tot) && threadIdx.x == 0) *norm2 = tot[0];
+}
+
+// The same residual for S = double, T = V = float without FP64 arithmetic
+// (FP64 runs at 1/64 of the FP32 rate on this part, and every float-double
+// conversion is an FP64 instruction): each FP64 value of x and b is split
+// by integer operations on its bits into a float pair h + l (48 bits),
+// scaled by 2^es so that the values are of unit size, and
+// r = b - sum_f alpha_f (x_c - x_nb) is formed with error-free float
+// transformations (two-sum, FMA two-product). The absolute error is about
+// 2^-44 max|x|, far below the refinement tolerance. c must be 1 (the solver's
+// finest level is unit scale).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// d 2^es = h + l; values below 2^-74 after scaling become 0, values at or
+// above 2^128 infinity (the solve then reports divergence), NaN stays NaN.
+__device__ __forceinline__ void split_f64(double d, int es, float &h, float &l) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  const unsigned sign = hi & 0x80000000u;
+  const int ef = e - (1023 - 127) + es;  // float biased exponent of h
+  if (e == 0x7ff) {
+    h = __int_as_float((int)(sign | 0x7fc00000u));
+    l = 0.f;
+    return;
+  }
+  if (e == 0 || ef <= 0) {
+    h = 0.f;
+    l = 0.f;
+    return;
+  }
+  if (ef >= 255) {
+    h = __int_as_float((int)(sign | 0x7f800000u));
+    l = 0.f;
+    return;
+  }
+  // h: the leading 24 significant bits (truncated); l: the other 29, whose
+  // unit is 2^(ef - 127 - 52)
+  h = __int_as_float((int)(sign | ((unsigned)ef << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29)));
+  const int pe = ef - 52;
+  const float m = pe > 0 ? __uint2float_rn(lo & 0x1fffffffu) * __int_as_float(pe << 23) : 0.f;
+  l = sign ? -m : m;
+}
+
+__global__ void k_residual_outer_df(LevelView<float> lv, const double *b,
+                                    const double *x, float *rin, int es,
+                                    float rscale, double scale, RedScratch rs,
+                                    double *norm2) {
+  float acc = 0.f;
+  const RowWalk w;
+  const int nrows = lv.ny * lv.nz;
+  const int nx = lv.nx, nxy = lv.nx * lv.ny;
+  for (int row = w.warp; row < nrows; row += w.nwarps) {
+    const int k = row / lv.ny, j = row - k * lv.ny;
+    const int base = row * nx;
+    for (int i = w.lane; i < nx; i += 32) {
+      const int c = base + i;
+      const int fy = c + k * nx;
+      const float a[6] = {ld(lv.ax + c + row), ld(lv.ax + c + row + 1), ld(lv.ay + fy),
+                          ld(lv.ay + fy + nx), ld(lv.az + c), ld(lv.az + c + nxy)};
+      const bool has[6] = {i > 0, i < nx - 1, j > 0, j < lv.ny - 1, k > 0, k < lv.nz - 1};
+      const int nb[6] = {c - 1, c + 1, c - nx, c + nx, c - nxy, c + nxy};
+      float rv = 0.f;
+      if (a[0] + a[1] + a[2] + a[3] + a[4] + a[5] > 0.f) {
+        float ch, cl;
+        split_f64(x[c], es, ch, cl);
+        float S = 0.f, E = 0.f;  // sum_f alpha_f (x_c - x_nb) = S + E
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+          if (a[f] == 0.f) continue;
+          float nh = 0.f, nl = 0.f;
+          if (has[f]) split_f64(x[nb[f]], es, nh, nl);
+          float d, t;  // x_c - x_nb = d + t
+          two_sum(ch, -nh, d, t);
+          t = __fadd_rn(t, __fsub_rn(cl, nl));
+          const float p = __fmul_rn(a[f], d);
+          const float q = __fmaf_rn(a[f], t, __fmaf_rn(a[f], d, -p));
+          float s2, e2;
+          two_sum(S, p, s2, e2);
+          S = s2;
+          E = __fadd_rn(E, __fadd_rn(e2, q));
+        }
+        float bh, bl;
+        split_f64(b[c], es, bh, bl);
+        float rh, re;
+        two_sum(bh, -S, rh, re);
+        rv = __fadd_rn(rh, __fadd_rn(re, __fsub_rn(bl, E)));
+      }
+      const float ri = __fmul_rn(rv, rscale);
+      rin[c] = ri;
+      acc = __fmaf_rn(ri, ri, acc);
+    }
+  }
+  double v[1] = {(double)acc}, tot[1];
+  if (grid_sum<1>(v, rs, tot) && threadIdx.x == 0) *norm2 = tot[0] / (scale * scale);
 }
 
 template <class S, class V>
@@ -1019,15 +1121,16 @@ __host__ __device__ inline size_t chain_layout(const CoarseChain<V, TA> &ch,
   return o;
 }
 
-// Half sweep of a block-resident level by the whole block (cells of one
-// colour in order, 32-bit unsigned index arithmetic).
+// Half sweep of a block-resident level: cells of one colour in order, cell
+// t0, t0 + stride, ... per thread (32-bit unsigned index arithmetic).
 template <class V, class FA, int MODE>
-__device__ void blk_sweep(const LevelView<FA> &lv, V *x, const V *b, int color,
-                          const Fold<V> &f) {
+__device__ __forceinline__ void sweep_cells(const LevelView<FA> &lv, V *x, const V *b,
+                                            int color, const Fold<V> &f, unsigned t0,
+                                            unsigned stride) {
   const unsigned hx = (unsigned)(lv.nx + 1) >> 1, ny = (unsigned)lv.ny;
   const unsigned n = hx * ny * (unsigned)lv.nz;
   const V cc = V(lv.c);
-  for (unsigned t = threadIdx.x; t < n; t += blockDim.x) {
+  for (unsigned t = t0; t < n; t += stride) {
     const unsigned row = t / hx, m = t - row * hx;
     const unsigned k = row / ny, j = row - k * ny;
     const int i = (int)(2 * m + ((j + k + color) & 1));
@@ -1035,7 +1138,21 @@ __device__ void blk_sweep(const LevelView<FA> &lv, V *x, const V *b, int color,
     const int c = (int)row * lv.nx + i;
     x[c] = sweep_cell<V, FA, MODE>(lv, x, b, i, (int)j, (int)k, c, (int)row, cc, f);
   }
+}
+// ... by the whole block
+template <class V, class FA, int MODE>
+__device__ void blk_sweep(const LevelView<FA> &lv, V *x, const V *b, int color,
+                          const Fold<V> &f) {
+  sweep_cells<V, FA, MODE>(lv, x, b, color, f, threadIdx.x, blockDim.x);
   __syncthreads();
+}
+// ... by the calling warp alone (a level of at most 64 cells: one cell of
+// each colour per lane, no block-wide barrier between half sweeps)
+template <class V, class FA, int MODE>
+__device__ void warp_sweep(const LevelView<FA> &lv, V *x, const V *b, int color,
+                           const Fold<V> &f) {
+  sweep_cells<V, FA, MODE>(lv, x, b, color, f, threadIdx.x & 31u, 32u);
+  __syncwarp();
 }
 
 // b_c = pn / 8 sum_children (b - A x) for every cell of a block-resident
@@ -1144,16 +1261,35 @@ __device__ void chain_body(const CoarseChain<V, TA> &ch, unsigned char *smem) {
   }
   {
     const LevelView<FA> lv = view(last);
-    for (int s = 0; s < ch.coarsest_sweeps; ++s) {
-      if (s == 0)
-        blk_sweep<V, FA, kSweepZero>(lv, X(last), B(last), 0, none);
-      else
-        blk_sweep<V, FA, kSweepPlain>(lv, X(last), B(last), 0, none);
-      blk_sweep<V, FA, kSweepPlain>(lv, X(last), B(last), 1, none);
-    }
-    for (int s = 0; s < ch.coarsest_sweeps; ++s) {
-      blk_sweep<V, FA, kSweepPlain>(lv, X(last), B(last), 1, none);
-      blk_sweep<V, FA, kSweepPlain>(lv, X(last), B(last), 0, none);
+    V *x = X(last);
+    const V *b = B(last);
+    if (lv.ncell() <= 64) {
+      if (threadIdx.x < 32) {
+        for (int s = 0; s < ch.coarsest_sweeps; ++s) {
+          if (s == 0)
+            warp_sweep<V, FA, kSweepZero>(lv, x, b, 0, none);
+          else
+            warp_sweep<V, FA, kSweepPlain>(lv, x, b, 0, none);
+          warp_sweep<V, FA, kSweepPlain>(lv, x, b, 1, none);
+        }
+        for (int s = 0; s < ch.coarsest_sweeps; ++s) {
+          warp_sweep<V, FA, kSweepPlain>(lv, x, b, 1, none);
+          warp_sweep<V, FA, kSweepPlain>(lv, x, b, 0, none);
+        }
+      }
+      __syncthreads();
+    } else {
+      for (int s = 0; s < ch.coarsest_sweeps; ++s) {
+        if (s == 0)
+          blk_sweep<V, FA, kSweepZero>(lv, x, b, 0, none);
+        else
+          blk_sweep<V, FA, kSweepPlain>(lv, x, b, 0, none);
+        blk_sweep<V, FA, kSweepPlain>(lv, x, b, 1, none);
+      }
+      for (int s = 0; s < ch.coarsest_sweeps; ++s) {
+        blk_sweep<V, FA, kSweepPlain>(lv, x, b, 1, none);
+        blk_sweep<V, FA, kSweepPlain>(lv, x, b, 0, none);
+      }
     }
   }
   for (int l = last - 1; l >= first; --l) {
@@ -1216,31 +1352,43 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
   return t;
 }
 
-// Grid-wide barrier of a cooperative launch: every block adds one to *bar
-// and waits until it reaches target (phases so far x blocks). Each wait is
-// bounded: after kBarrierNs the waiting block sets *err, and every block
-// leaves at its next barrier. Returns false (the same in all threads of the
-// block) when the kernel must stop.
+// Grid-wide barrier of a cooperative launch: after the block's threads meet,
+// thread 0 adds one to *bar with release semantics (the block's writes,
+// ordered before it by the CTA barrier, become visible with the arrival)
+// and spins with acquire loads until *bar reaches target (phases so far x
+// blocks). Each wait is bounded: every 256 polls it checks *err and the
+// clock, and after kBarrierNs it sets *err; every block then leaves at its
+// next barrier. Returns false (the same in all threads of the block) when
+// the kernel must stop.
 constexpr unsigned long long kBarrierNs = 1000000000ull;
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target,
                                              int *err) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(bar, 1u);
-    const unsigned long long t0 = globaltimer_ns();
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+    unsigned long long t0 = 0;
+    unsigned spins = 0;
     int e = 0;
-    while (*(volatile unsigned *)bar < target) {
-      if ((e = *(volatile int *)err) != 0) break;
-      if (globaltimer_ns() - t0 > kBarrierNs) {
-        atomicExch(err, 1);
-        e = 1;
-        break;
+    for (;;) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+      if (v >= target) break;
+      if ((++spins & 255u) == 0) {
+        if (*(volatile int *)err != 0) {
+          e = 1;
+          break;
+        }
+        const unsigned long long t = globaltimer_ns();
+        if (t0 == 0) {
+          t0 = t;
+        } else if (t - t0 > kBarrierNs) {
+          atomicExch(err, 1);
+          e = 1;
+          break;
+        }
       }
-      __nanosleep(20);
     }
-    __threadfence();
     ok = e == 0;
   }
   __syncthreads();
@@ -1303,10 +1451,20 @@ static inline unsigned gs_blocks(int64_t n) {
 
 template <class S, class T, class V>
 void launch_residual_outer(const Launch &L, const LevelView<T> &lv, const S *b,
-                           const S *x, S *r, V *rin, double scale,
+                           const S *x, V *rin, double scale, int es,
                            const RedScratch &rs, double *norm2) {
   ProfScope _ps(L, NF_K_RESIDUAL64);
-  k_residual_outer<S, T, V><<<kRedBlocks, kBlock, 0, L.s>>>(lv, b, x, r, rin, scale, rs, norm2);
+  if constexpr (sizeof(S) == 8 && sizeof(T) == 4 && sizeof(V) == 4) {
+    // split arithmetic needs c = 1 and the scale of rin in float range
+    const double rscale = std::ldexp(scale, -es);
+    if (lv.c == 1.0 && rscale >= 0x1p-120 && rscale <= 0x1p120) {
+      k_residual_outer_df<<<kRedBlocks, kBlock, 0, L.s>>>(lv, b, x, rin, es, (float)rscale,
+                                                         scale, rs, norm2);
+      ++*L.counter;
+      return;
+    }
+  }
+  k_residual_outer<S, T, V><<<kRedBlocks, kBlock, 0, L.s>>>(lv, b, x, rin, scale, rs, norm2);
   ++*L.counter;
 }
 template <class S, class V>
@@ -1578,9 +1736,9 @@ template void launch_mg_coarsen<float, __nv_bfloat16>(const Launch &, const Leve
 template void launch_mg_coarsen<__nv_bfloat16, __nv_bfloat16>(const Launch &, const LevelView<__nv_bfloat16> &, int, int, int, __nv_bfloat16 *, __nv_bfloat16 *, __nv_bfloat16 *);
 template void launch_mg_coarsen<double, double>(const Launch &, const LevelView<double> &, int, int, int, double *, double *, double *);
 
-template void launch_residual_outer<double, float, float>(const Launch &, const LevelView<float> &, const double *, const double *, double *, float *, double, const RedScratch &, double *);
-template void launch_residual_outer<float, float, float>(const Launch &, const LevelView<float> &, const float *, const float *, float *, float *, double, const RedScratch &, double *);
-template void launch_residual_outer<double, double, double>(const Launch &, const LevelView<double> &, const double *, const double *, double *, double *, double, const RedScratch &, double *);
+template void launch_residual_outer<double, float, float>(const Launch &, const LevelView<float> &, const double *, const double *, float *, double, int, const RedScratch &, double *);
+template void launch_residual_outer<float, float, float>(const Launch &, const LevelView<float> &, const float *, const float *, float *, double, int, const RedScratch &, double *);
+template void launch_residual_outer<double, double, double>(const Launch &, const LevelView<double> &, const double *, const double *, double *, double, int, const RedScratch &, double *);
 template void launch_axpy_outer<double, float>(const Launch &, int64_t, double *, const float *, double);
 template void launch_axpy_outer<float, float>(const Launch &, int64_t, float *, const float *, double);
 template void launch_axpy_outer<double, double>(const Launch &, int64_t, double *, const double *, double);

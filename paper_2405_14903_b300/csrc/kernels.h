@@ -79,13 +79,14 @@ void launch_adj_face(const Launch &L, const GridDev &g, const SceneDev &s,
                      double *gtheta);
 
 // ----------------------------------------------------------- solver ops ---
-// r = b - A x in precision S (fine operator with fractions of type T);
-// also writes scale * r converted to V into rin (may be null) and ||r||^2
-// (unscaled). scale is a power of two that brings rin to unit size, so that
-// the V-typed inner solve neither underflows nor overflows.
+// r = b - A x (fine operator with fractions of type T, x and b of type S),
+// written as scale * r converted to V into rin, and ||r||^2 (unscaled).
+// scale is a power of two that brings rin to unit size, so that the V-typed
+// inner solve neither underflows nor overflows; 2^es is a power of two that
+// brings b to unit size (used by the FP64-free MIXED variant).
 template <class S, class T, class V>
 void launch_residual_outer(const Launch &L, const LevelView<T> &lv,
-                           const S *b, const S *x, S *r, V *rin, double scale,
+                           const S *b, const S *x, V *rin, double scale, int es,
                            const RedScratch &rs, double *norm2);
 // x += inv * e (V -> S); inv undoes the scale of the inner system.
 template <class S, class V>

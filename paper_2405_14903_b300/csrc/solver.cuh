@@ -18,6 +18,8 @@
 #include <algorithm>
 #include <cstddef>
 #include <cmath>
+#include <cstdlib>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -42,12 +44,15 @@ class Solver {
   Solver(Ctx *ctx, const GridDev &g, const nf_config &cfg)
       : ctx_(ctx), g_(g), cfg_(cfg) {
     g_.c = 1.0;
+    // NF_GRAPHS=0: launch every kernel directly (for profilers that cannot
+    // follow stream capture); the kernels and results are the same
+    const char *env = std::getenv("NF_GRAPHS");
+    if (env && std::strcmp(env, "0") == 0) graphs_ok_ = false;
   }
 
   // Allocates the hierarchy. Returns NF_OK or an error status.
   int init(Alloc &A) {
     n_ = g_.ncell();
-    CKS(A.get(&r_, n_ * sizeof(S)));
     CKS(A.get(&rin_, n_ * sizeof(V)));
     CKS(A.get(&e_, n_ * sizeof(V)));
     CKS(A.get(&z_, n_ * sizeof(V)));
@@ -183,6 +188,7 @@ class Solver {
     // to 1 / ||r||: tiny right-hand sides (an adjoint far from its loss)
     // would otherwise underflow in the V-typed dots
     double scale = unit_scale(std::sqrt(bnorm2));
+    es_ = std::max(-900, std::min(900, -std::ilogb(std::sqrt(bnorm2))));
     double rn2 = residual(b, x, scale);  // r = b - A 0
     out.rel = std::sqrt(rn2 / bnorm2);
     int total = 0;
@@ -281,8 +287,8 @@ class Solver {
 
   double residual(const S *b, const S *x, double scale) {
     Launch L = ctx_->launch();
-    launch_residual_outer<S, T, V>(L, view0(), b, x, (S *)r_, (V *)rin_, scale,
-                                   ctx_->rs, (double *)norm2_);
+    launch_residual_outer<S, T, V>(L, view0(), b, x, (V *)rin_, scale, es_, ctx_->rs,
+                                   (double *)norm2_);
     return ctx_->read_double((double *)norm2_);
   }
 
@@ -644,7 +650,8 @@ class Solver {
   void *band_mark_ = nullptr, *band_list_[2] = {nullptr, nullptr}, *band_count_ = nullptr;
   std::vector<Level> levels_;
   const T *ax0_ = nullptr, *ay0_ = nullptr, *az0_ = nullptr;
-  void *r_ = nullptr, *rin_ = nullptr, *e_ = nullptr, *z_ = nullptr,
+  int es_ = 0;  // 2^es_ brings the current right-hand side to unit size
+  void *rin_ = nullptr, *e_ = nullptr, *z_ = nullptr,
        *d_ = nullptr, *q_ = nullptr, *st_ = nullptr, *norm2_ = nullptr;
   cudaStream_t cap_ = nullptr;
   bool graphs_ok_ = true;
