@@ -207,6 +207,14 @@ __device__ __forceinline__ V prolong_cell(int cnx, int cny, int cnz,
 __device__ __forceinline__ bool stopped(const CGState *st) {
   return st != nullptr && *(volatile const int *)&st->done != 0;
 }
+// The same flag for kernels that check it late: the load is issued first,
+// the kernel issues its first data loads, and only its first store waits
+// for the flag (one L2 round trip less per block). Blocks of one launch all
+// read the same value: the flag changes only at the end of a grid reduction,
+// after every block of that launch has read it.
+__device__ __forceinline__ int stop_flag(const CGState *st) {
+  return st != nullptr ? *(volatile const int *)&st->done : 0;
+}
 
 // ------------------------------------------------------------- ILP ------
 // Grid-stride kernels walk cells in batches of ILP cells per thread (cells
@@ -543,7 +551,7 @@ __global__ void k_cg_continue(int64_t n, const V *r, const V *z, CGState *st,
 template <class V, class TA>
 __global__ void k_apply_dot(LevelView<TA> lv, const V *d, V *q, CGState *st,
                             RedScratch rs) {
-  if (stopped(st)) return;
+  const int stop = stop_flag(st);
   V p = V(0);
   const RowWalk w;
   const int nrows = lv.ny * lv.nz;
@@ -557,10 +565,12 @@ __global__ void k_apply_dot(LevelView<TA> lv, const V *d, V *q, CGState *st,
       gather7r(g, lv, d, i, j, k, c, row);
       const V dg = g.diag();
       const V qc = dg > V(0) ? cc * (dg * g.vc - g.nb()) : V(0);
+      if (stop) return;
       q[c] = qc;
       p += g.vc * qc;
     }
   }
+  if (stop) return;  // every thread of every block (none reaches the grid sum)
   double v[1] = {(double)p};
   double tot[1];
   if (grid_sum<1>(v, rs, tot) && threadIdx.x == 0) {
@@ -575,7 +585,7 @@ __global__ void k_apply_dot(LevelView<TA> lv, const V *d, V *q, CGState *st,
 template <class V>
 __global__ void k_cg_xr(int64_t n, V *x, V *r, const V *d, const V *q,
                         CGState *st, RedScratch rs, bool preconditioned) {
-  if (stopped(st)) return;
+  const int stop = stop_flag(st);
   const V a = (V)st->alpha;
   V p = V(0);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -593,6 +603,7 @@ __global__ void k_cg_xr(int64_t n, V *x, V *r, const V *d, const V *q,
         qv[u] = q[c];
       }
     }
+    if (stop) return;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int64_t c = c0 + u * stride;
@@ -604,6 +615,7 @@ __global__ void k_cg_xr(int64_t n, V *x, V *r, const V *d, const V *q,
       }
     }
   }
+  if (stop) return;  // every thread of every block (none reaches the grid sum)
   double v[1] = {(double)p};
   double tot[1];
   if (grid_sum<1>(v, rs, tot) && threadIdx.x == 0) {
@@ -623,7 +635,7 @@ __global__ void k_cg_xr(int64_t n, V *x, V *r, const V *d, const V *q,
 template <class V>
 __global__ void k_cg_rz(int64_t n, const V *r, const V *z, CGState *st,
                         RedScratch rs) {
-  if (stopped(st)) return;
+  const int stop = stop_flag(st);
   V p = V(0);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   constexpr int U = kIlpStream;
@@ -638,10 +650,12 @@ __global__ void k_cg_rz(int64_t n, const V *r, const V *z, CGState *st,
         zv[u] = z[c];
       }
     }
+    if (stop) return;
 #pragma unroll
     for (int u = 0; u < U; ++u)
       if (c0 + u * stride < n) p += rv[u] * zv[u];
   }
+  if (stop) return;  // every thread of every block (none reaches the grid sum)
   double v[1] = {(double)p};
   double tot[1];
   if (grid_sum<1>(v, rs, tot) && threadIdx.x == 0) {
@@ -656,7 +670,7 @@ __global__ void k_cg_rz(int64_t n, const V *r, const V *z, CGState *st,
 
 template <class V>
 __global__ void k_cg_d(int64_t n, const V *z, V *d, const CGState *st) {
-  if (stopped(st)) return;
+  const int stop = stop_flag(st);
   const V b = (V)st->beta;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   constexpr int U = kIlpStream;
@@ -671,6 +685,7 @@ __global__ void k_cg_d(int64_t n, const V *z, V *d, const CGState *st) {
         dv[u] = d[c];
       }
     }
+    if (stop) return;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int64_t c = c0 + u * stride;
@@ -779,6 +794,21 @@ __global__ void k_band_smooth(LevelView<TA> lv, V *x, const V *b,
   }
 }
 
+// Neighbour values plus the prolonged coarse correction w x_c of their
+// parents (constant transfer; the neighbours that exist).
+template <class V>
+__device__ __forceinline__ void add_fold(Nb7<V> &g, const Fold<V> &f, int nx, int ny,
+                                         int nz, int i, int j, int k) {
+  const int cxy = f.cnx * f.cny;
+  const int pc = ((k >> 1) * f.cny + (j >> 1)) * f.cnx + (i >> 1);
+  if (i > 0) g.vxm += f.xc[(i & 1) ? pc : pc - 1] * f.w;
+  if (i < nx - 1) g.vxp += f.xc[(i & 1) ? pc + 1 : pc] * f.w;
+  if (j > 0) g.vym += f.xc[(j & 1) ? pc : pc - f.cnx] * f.w;
+  if (j < ny - 1) g.vyp += f.xc[(j & 1) ? pc + f.cnx : pc] * f.w;
+  if (k > 0) g.vzm += f.xc[(k & 1) ? pc : pc - cxy] * f.w;
+  if (k < nz - 1) g.vzp += f.xc[(k & 1) ? pc + cxy : pc] * f.w;
+}
+
 // New value of cell c = (i, j, k) (row = k ny + j) under a half sweep.
 template <class V, class TA, int MODE>
 __device__ __forceinline__ V sweep_cell(const LevelView<TA> &lv, const V *x,
@@ -792,16 +822,7 @@ __device__ __forceinline__ V sweep_cell(const LevelView<TA> &lv, const V *x,
   }
   Nb7<V> g;
   gather7r(g, lv, x, i, j, k, c, row);
-  if (MODE == kSweepProlong) {
-    const int cxy = f.cnx * f.cny;
-    const int pc = ((k >> 1) * f.cny + (j >> 1)) * f.cnx + (i >> 1);
-    if (i > 0) g.vxm += f.xc[(i & 1) ? pc : pc - 1] * f.w;
-    if (i < lv.nx - 1) g.vxp += f.xc[(i & 1) ? pc + 1 : pc] * f.w;
-    if (j > 0) g.vym += f.xc[(j & 1) ? pc : pc - f.cnx] * f.w;
-    if (j < lv.ny - 1) g.vyp += f.xc[(j & 1) ? pc + f.cnx : pc] * f.w;
-    if (k > 0) g.vzm += f.xc[(k & 1) ? pc : pc - cxy] * f.w;
-    if (k < lv.nz - 1) g.vzp += f.xc[(k & 1) ? pc + cxy : pc] * f.w;
-  }
+  if (MODE == kSweepProlong) add_fold(g, f, lv.nx, lv.ny, lv.nz, i, j, k);
   const V dg = g.diag();
   return dg > V(0) ? (b[c] + cc * g.nb()) / (cc * dg) : V(0);
 }
@@ -812,7 +833,7 @@ template <class V, class TA, int MODE>
 __device__ __forceinline__ void sweep_rows(const LevelView<TA> &lv, V *x,
                                            const V *b, int color,
                                            const Fold<V> &f, int warp,
-                                           int nwarps, int lane) {
+                                           int nwarps, int lane, int stop = 0) {
   const int nrows = lv.ny * lv.nz;
   const int hx = (lv.nx + 1) >> 1;
   const V cc = V(lv.c);
@@ -824,21 +845,29 @@ __device__ __forceinline__ void sweep_rows(const LevelView<TA> &lv, V *x,
       const int i = 2 * m + p;
       if (i >= lv.nx) continue;
       const int c = base + i;
-      x[c] = sweep_cell<V, TA, MODE>(lv, x, b, i, j, k, c, row, cc, f);
+      const V v = sweep_cell<V, TA, MODE>(lv, x, b, i, j, k, c, row, cc, f);
+      if (stop) return;
+      x[c] = v;
     }
   }
 }
 
-// Constant-transfer restriction of the residual of coarse cell (I, J, K):
-// the sum over its eight children of (b - A x) (inactive children add 0).
+// Constant-transfer restriction of the residual of coarse cell (I, J, K)
+// after pre-smoothing: the sum over its eight children of (b - A x). The
+// last pre-smoothing half sweep updated the odd cells ((i + j + k) odd) from
+// their even neighbours, which it did not change, so the residual of every
+// odd cell is zero (up to the rounding of that update) and only the four
+// even children are summed (inactive children add 0).
 template <class V, class TA>
 __device__ __forceinline__ V resrestrict_cell(const LevelView<TA> &lv,
                                               const V *x, const V *b, int I,
                                               int J, int K, V cc) {
   V acc = V(0);
-#pragma unroll 2
-  for (int ch = 0; ch < 8; ++ch) {
-    const int i = 2 * I + (ch & 1), j = 2 * J + ((ch >> 1) & 1), k = 2 * K + (ch >> 2);
+#pragma unroll
+  for (int ch = 0; ch < 4; ++ch) {
+    // even children (a, b, c) = (0,0,0), (1,1,0), (1,0,1), (0,1,1)
+    const int a = (ch == 1 || ch == 2), bb = (ch == 1 || ch == 3), cz = (ch >= 2);
+    const int i = 2 * I + a, j = 2 * J + bb, k = 2 * K + cz;
     const int frow = k * lv.ny + j;
     const int c = frow * lv.nx + i;
     Nb7<V> g;
@@ -855,13 +884,16 @@ __device__ __forceinline__ void resrestrict_rows(const LevelView<TA> &lv,
                                                  const V *x, const V *b,
                                                  int cnx, int cny, int cnz,
                                                  V *bc, float pn, int warp,
-                                                 int nwarps, int lane) {
+                                                 int nwarps, int lane, int stop = 0) {
   const int nrows = cny * cnz;
   const V cc = V(lv.c);
   for (int row = warp; row < nrows; row += nwarps) {
     const int K = row / cny, J = row - K * cny;
-    for (int I = lane; I < cnx; I += 32)
-      bc[row * cnx + I] = V(0.125) * V(pn) * resrestrict_cell<V, TA>(lv, x, b, I, J, K, cc);
+    for (int I = lane; I < cnx; I += 32) {
+      const V v = V(0.125) * V(pn) * resrestrict_cell<V, TA>(lv, x, b, I, J, K, cc);
+      if (stop) return;
+      bc[row * cnx + I] = v;
+    }
   }
 }
 
@@ -869,9 +901,9 @@ __device__ __forceinline__ void resrestrict_rows(const LevelView<TA> &lv,
 template <class V, class TA, int MODE>
 __global__ void k_mg_smooth(LevelView<TA> lv, V *x, const V *b, int color,
                             Fold<V> f, const CGState *st) {
-  if (stopped(st)) return;
+  const int stop = stop_flag(st);
   const RowWalk w;
-  sweep_rows<V, TA, MODE>(lv, x, b, color, f, w.warp, w.nwarps, w.lane);
+  sweep_rows<V, TA, MODE>(lv, x, b, color, f, w.warp, w.nwarps, w.lane, stop);
 }
 
 // Prolongation normaliser of fine cell (i, j, k): 1 / (sum of the trilinear
@@ -971,9 +1003,9 @@ template <class V, class TA>
 __global__ void k_mg_resrestrict(LevelView<TA> lv, const V *x, const V *b,
                                  int cnx, int cny, int cnz, V *bc, float pn,
                                  const CGState *st) {
-  if (stopped(st)) return;
+  const int stop = stop_flag(st);
   const RowWalk w;
-  resrestrict_rows<V, TA>(lv, x, b, cnx, cny, cnz, bc, pn, w.warp, w.nwarps, w.lane);
+  resrestrict_rows<V, TA>(lv, x, b, cnx, cny, cnz, bc, pn, w.warp, w.nwarps, w.lane, stop);
 }
 
 // x_f += P x_c on active fine cells.
@@ -1083,23 +1115,22 @@ k_mg_coarse_chain(CoarseChain<V, TA> ch, const CGState *st) {
 }
 
 // Shared-memory version of the chain: every array of the chain levels (x, b,
-// the fractions converted to FA, and r for the trilinear transfer) lives in
-// shared memory for the whole sub-V-cycle; global memory is read once
-// (fractions, b of the first chain level) and written once (x of the first
-// chain level).
+// the fractions, the inverse diagonal, and r for the trilinear transfer)
+// lives in shared memory for the whole sub-V-cycle; global memory is read
+// once (fractions, b of the first chain level) and written once (x of the
+// first chain level).
+// Fractions keep their storage type in shared memory, so that they arrive
+// by bulk copies (converted at every read, one instruction for BF16).
 template <class TA>
 struct ChainFA {
-  using type = float;
-};
-template <>
-struct ChainFA<double> {
-  using type = double;
+  using type = TA;
 };
 
-// Byte offsets of x, b, r, ax, ay, az of every chain level; returns the total.
+// Byte offsets of x, b, r, ax, ay, az and the inverse diagonal of every
+// chain level; returns the total.
 template <class V, class TA>
 __host__ __device__ inline size_t chain_layout(const CoarseChain<V, TA> &ch,
-                                               size_t off[kMaxLevels][6]) {
+                                               size_t off[kMaxLevels][7]) {
   using FA = typename ChainFA<TA>::type;
   size_t o = 0;
   auto take = [&o](size_t bytes) {
@@ -1117,74 +1148,172 @@ __host__ __device__ inline size_t chain_layout(const CoarseChain<V, TA> &ch,
     off[l][3] = take((size_t)(v.nx + 1) * v.ny * v.nz * sizeof(FA));
     off[l][4] = take((size_t)v.nx * (v.ny + 1) * v.nz * sizeof(FA));
     off[l][5] = take((size_t)v.nx * v.ny * (v.nz + 1) * sizeof(FA));
+    off[l][6] = take(nc * sizeof(V));
   }
   return o;
 }
 
-// Half sweep of a block-resident level: cells of one colour in order, cell
-// t0, t0 + stride, ... per thread (32-bit unsigned index arithmetic).
+// t / d for t < 2^17 and d < 2^15 as a multiply-high: with m = ceil(2^32 / d)
+// the error term t (m d - 2^32) / 2^32 stays below 1 / d.
+struct UDiv {
+  unsigned d, m;
+  __device__ __forceinline__ unsigned q(unsigned t) const {
+    return d == 1u ? t : __umulhi(t, m);
+  }
+};
+__device__ __forceinline__ UDiv make_udiv(unsigned d) {
+  return UDiv{d, d == 1u ? 0u : 0xFFFFFFFFu / d + 1u};
+}
+
+// One block-resident chain level: arrays in shared memory (the fractions
+// as FA), the inverse diagonal 1 / (c dg) (0 on inactive cells) and the
+// divisions of its index arithmetic.
+template <class V, class FA>
+struct CLev {
+  LevelView<FA> lv;
+  V *x, *b, *dinv;
+  UDiv hx, ny;  // half row (cells of one colour per row), rows per plane
+};
+
+// Half sweep of a chain level over the cells t0, t0 + stride, ... of one
+// colour: x = (b + c nb) / (c dg) with the division replaced by dinv.
 template <class V, class FA, int MODE>
-__device__ __forceinline__ void sweep_cells(const LevelView<FA> &lv, V *x, const V *b,
-                                            int color, const Fold<V> &f, unsigned t0,
-                                            unsigned stride) {
-  const unsigned hx = (unsigned)(lv.nx + 1) >> 1, ny = (unsigned)lv.ny;
-  const unsigned n = hx * ny * (unsigned)lv.nz;
-  const V cc = V(lv.c);
+__device__ __forceinline__ void csweep_cells(const CLev<V, FA> &L, int color,
+                                             const Fold<V> &f, unsigned t0,
+                                             unsigned stride) {
+  const unsigned n = L.hx.d * L.ny.d * (unsigned)L.lv.nz;
+  const V cc = V(L.lv.c);
   for (unsigned t = t0; t < n; t += stride) {
-    const unsigned row = t / hx, m = t - row * hx;
-    const unsigned k = row / ny, j = row - k * ny;
+    const unsigned row = L.hx.q(t), m = t - row * L.hx.d;
+    const unsigned k = L.ny.q(row), j = row - k * L.ny.d;
     const int i = (int)(2 * m + ((j + k + color) & 1));
-    if (i >= lv.nx) continue;
-    const int c = (int)row * lv.nx + i;
-    x[c] = sweep_cell<V, FA, MODE>(lv, x, b, i, (int)j, (int)k, c, (int)row, cc, f);
+    if (i >= L.lv.nx) continue;
+    const int c = (int)row * L.lv.nx + i;
+    if (MODE == kSweepZero) {
+      L.x[c] = L.b[c] * L.dinv[c];
+      continue;
+    }
+    Nb7<V> g;
+    gather7r(g, L.lv, L.x, i, (int)j, (int)k, c, (int)row);
+    if (MODE == kSweepProlong) add_fold(g, f, L.lv.nx, L.lv.ny, L.lv.nz, i, (int)j, (int)k);
+    L.x[c] = (L.b[c] + cc * g.nb()) * L.dinv[c];
   }
 }
-// ... by the whole block
 template <class V, class FA, int MODE>
-__device__ void blk_sweep(const LevelView<FA> &lv, V *x, const V *b, int color,
-                          const Fold<V> &f) {
-  sweep_cells<V, FA, MODE>(lv, x, b, color, f, threadIdx.x, blockDim.x);
+__device__ __forceinline__ void blk_sweep(const CLev<V, FA> &L, int color,
+                                          const Fold<V> &f) {
+  csweep_cells<V, FA, MODE>(L, color, f, threadIdx.x, blockDim.x);
   __syncthreads();
-}
-// ... by the calling warp alone (a level of at most 64 cells: one cell of
-// each colour per lane, no block-wide barrier between half sweeps)
-template <class V, class FA, int MODE>
-__device__ void warp_sweep(const LevelView<FA> &lv, V *x, const V *b, int color,
-                           const Fold<V> &f) {
-  sweep_cells<V, FA, MODE>(lv, x, b, color, f, threadIdx.x & 31u, 32u);
-  __syncwarp();
 }
 
 // b_c = pn / 8 sum_children (b - A x) for every cell of a block-resident
-// coarse level.
+// coarse level (even children only: see resrestrict_cell).
 template <class V, class FA>
-__device__ void blk_resrestrict(const LevelView<FA> &lv, const V *x, const V *b,
-                                int cnx, int cny, int cnz, V *bc, float pn) {
+__device__ void blk_resrestrict(const CLev<V, FA> &L, int cnx, int cny, int cnz, V *bc,
+                                float pn) {
+  const UDiv ux = make_udiv((unsigned)cnx), uy = make_udiv((unsigned)cny);
   const unsigned n = (unsigned)cnx * cny * cnz;
-  const V cc = V(lv.c);
+  const V cc = V(L.lv.c);
   for (unsigned t = threadIdx.x; t < n; t += blockDim.x) {
-    const unsigned q = t / (unsigned)cnx, I = t - q * cnx;
-    const unsigned K = q / (unsigned)cny, J = q - K * cny;
-    bc[t] = V(0.125) * V(pn) * resrestrict_cell<V, FA>(lv, x, b, (int)I, (int)J, (int)K, cc);
+    const unsigned q = ux.q(t), I = t - q * cnx;
+    const unsigned K = uy.q(q), J = q - K * cny;
+    bc[t] = V(0.125) * V(pn) * resrestrict_cell<V, FA>(L.lv, L.x, L.b, (int)I, (int)J, (int)K, cc);
   }
   __syncthreads();
 }
 
-// Copy of n values into shared memory, eight loads in flight per thread.
-template <class D, class S>
-__device__ __forceinline__ void blk_load(D *dst, const S *src, int n) {
-  constexpr int U = 8;
-  for (int t0 = threadIdx.x; t0 < n; t0 += U * blockDim.x) {
-    D v[U];
+// The coarsest level's symmetric sweeps when each colour has at most 32
+// cells: one warp, each lane keeps its cell of each colour (fractions,
+// neighbour indices, dinv, b) in registers; only x lives in shared memory.
+template <class V, class FA>
+__device__ void warp_coarsest(const CLev<V, FA> &L, int sweeps) {
+  const unsigned lane = threadIdx.x & 31u;
+  const int nx = L.lv.nx, ny = L.lv.ny, nz = L.lv.nz, nxy = nx * ny;
+  const unsigned n = L.hx.d * L.ny.d * (unsigned)nz;
+  const V cc = V(L.lv.c);
+  int cell[2], nb[2][6];
+  V a[2][6], di[2], bv[2];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int t = t0 + u * blockDim.x;
-      v[u] = t < n ? (D)ld(src + t) : D(0);
+  for (int col = 0; col < 2; ++col) {
+    cell[col] = -1;
+    const unsigned t = lane;
+    const unsigned row = L.hx.q(t), m = t - row * L.hx.d;
+    const unsigned k = L.ny.q(row), j = row - k * L.ny.d;
+    const int i = (int)(2 * m + ((j + k + col) & 1));
+    if (t < n && i < nx) {
+      const int c = (int)row * nx + i, fy = c + (int)k * nx;
+      cell[col] = c;
+      a[col][0] = (V)ld(L.lv.ax + c + row);
+      a[col][1] = (V)ld(L.lv.ax + c + row + 1);
+      a[col][2] = (V)ld(L.lv.ay + fy);
+      a[col][3] = (V)ld(L.lv.ay + fy + nx);
+      a[col][4] = (V)ld(L.lv.az + c);
+      a[col][5] = (V)ld(L.lv.az + c + nxy);
+      nb[col][0] = i > 0 ? c - 1 : -1;
+      nb[col][1] = i < nx - 1 ? c + 1 : -1;
+      nb[col][2] = (int)j > 0 ? c - nx : -1;
+      nb[col][3] = (int)j < ny - 1 ? c + nx : -1;
+      nb[col][4] = (int)k > 0 ? c - nxy : -1;
+      nb[col][5] = (int)k < nz - 1 ? c + nxy : -1;
+      di[col] = L.dinv[c];
+      bv[col] = L.b[c];
     }
+  }
+  auto update = [&](int col, bool zero) {
+    if (cell[col] < 0) return;
+    V acc = V(0);
+    if (!zero) {
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int t = t0 + u * blockDim.x;
-      if (t < n) dst[t] = v[u];
+      for (int q = 0; q < 6; ++q) acc += a[col][q] * (nb[col][q] >= 0 ? L.x[nb[col][q]] : V(0));
+    }
+    L.x[cell[col]] = (bv[col] + cc * acc) * di[col];
+  };
+  for (int s = 0; s < sweeps; ++s) {
+    update(0, s == 0);
+    __syncwarp();
+    update(1, false);
+    __syncwarp();
+  }
+  for (int s = 0; s < sweeps; ++s) {
+    update(1, false);
+    __syncwarp();
+    update(0, false);
+    __syncwarp();
+  }
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Every bounded wait on the device (grid barriers, mbarriers) gives up
+// after this long.
+constexpr unsigned long long kBarrierNs = 1000000000ull;
+
+// Bounded wait for phase `parity` of an mbarrier: true once it completed;
+// after kBarrierNs sets *err (when given) and returns false.
+__device__ __forceinline__ bool mbar_wait(unsigned mb, unsigned parity, int *err) {
+  unsigned long long t0 = 0;
+  unsigned spins = 0;
+  for (;;) {
+    unsigned ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; "
+        "selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(mb), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((++spins & 255u) == 0) {
+      const unsigned long long t = globaltimer_ns();
+      if (t0 == 0) {
+        t0 = t;
+      } else if (t - t0 > kBarrierNs) {
+        if (err) atomicExch(err, 1);
+        return false;
+      }
     }
   }
 }
@@ -1197,135 +1326,208 @@ __device__ __forceinline__ void blk_load(D *dst, const S *src, int n) {
 template <class V, class TA>
 __device__ void chain_body(const CoarseChain<V, TA> &ch, unsigned char *smem) {
   using FA = typename ChainFA<TA>::type;
-  __shared__ unsigned soff[kMaxLevels][6];
+  __shared__ unsigned soff[kMaxLevels][7];
+  __shared__ UDiv sdiv[kMaxLevels][2];
+  __shared__ const TA *seg_src[3 * kMaxLevels];
+  __shared__ unsigned seg_dst[3 * kMaxLevels], seg_end[3 * kMaxLevels];
+  const int first = ch.first, last = ch.nlev - 1;
+  const int nseg = 3 * (last - first + 1);
   if (threadIdx.x == 0) {
-    size_t off[kMaxLevels][6];
+    size_t off[kMaxLevels][7];
     chain_layout(ch, off);
-    for (int l = ch.first; l < ch.nlev; ++l)
-      for (int q = 0; q < 6; ++q) soff[l][q] = (unsigned)off[l][q];
+    unsigned e = 0;
+    for (int l = first; l <= last; ++l) {
+      const LevelView<TA> &g = ch.lv[l];
+      for (int q = 0; q < 7; ++q) soff[l][q] = (unsigned)off[l][q];
+      sdiv[l][0] = make_udiv((unsigned)(g.nx + 1) >> 1);
+      sdiv[l][1] = make_udiv((unsigned)g.ny);
+      const int s0 = 3 * (l - first);
+      const TA *src[3] = {g.ax, g.ay, g.az};
+      const unsigned cnt[3] = {(unsigned)((g.nx + 1) * g.ny * g.nz),
+                               (unsigned)(g.nx * (g.ny + 1) * g.nz),
+                               (unsigned)(g.nx * g.ny * (g.nz + 1))};
+      for (int q = 0; q < 3; ++q) {
+        seg_src[s0 + q] = src[q];
+        seg_dst[s0 + q] = soff[l][3 + q];
+        e += cnt[q];
+        seg_end[s0 + q] = e;
+      }
+    }
   }
   __syncthreads();
-  const int first = ch.first, last = ch.nlev - 1;
   const bool fused = ch.transfer == kTransferConstant;
-  auto view = [&](int l) {
+  auto lev = [&](int l) {
     const LevelView<TA> &g = ch.lv[l];
-    return LevelView<FA>{g.nx, g.ny, g.nz, g.c, (const FA *)(smem + soff[l][3]),
-                         (const FA *)(smem + soff[l][4]),
-                         (const FA *)(smem + soff[l][5])};
+    CLev<V, FA> L;
+    L.lv = LevelView<FA>{g.nx, g.ny, g.nz, g.c, (const FA *)(smem + soff[l][3]),
+                         (const FA *)(smem + soff[l][4]), (const FA *)(smem + soff[l][5])};
+    L.x = (V *)(smem + soff[l][0]);
+    L.b = (V *)(smem + soff[l][1]);
+    L.dinv = (V *)(smem + soff[l][6]);
+    L.hx = sdiv[l][0];
+    L.ny = sdiv[l][1];
+    return L;
   };
-  auto X = [&](int l) { return (V *)(smem + soff[l][0]); };
-  auto B = [&](int l) { return (V *)(smem + soff[l][1]); };
   auto R = [&](int l) { return (V *)(smem + soff[l][2]); };
   const Fold<V> none{nullptr, 0, 0, V(0)};
-  blk_load(B(first), ch.b[first], (int)ch.lv[first].ncell());
+  // global -> shared: thread 0 issues a bulk copy of every 16-byte-aligned
+  // array (b of the first level, the fractions of every level), tracked by
+  // one mbarrier; ragged tails and unaligned arrays are copied by plain
+  // loads meanwhile
+  {
+    __shared__ __align__(8) unsigned long long mbar;
+    const unsigned mb = (unsigned)__cvta_generic_to_shared(&mbar);
+    const int nb0 = (int)ch.lv[first].ncell();
+    V *bs = (V *)(smem + soff[first][1]);
+    if (threadIdx.x == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // bytes a bulk copy takes: both addresses 16-byte aligned, a multiple of 16
+    auto bulk_bytes = [](const void *dst, const void *src, unsigned bytes) {
+      return (((uintptr_t)src | (uintptr_t)__cvta_generic_to_shared(dst)) & 15u) ? 0u
+                                                                               : (bytes & ~15u);
+    };
+    if (threadIdx.x == 0) {
+      unsigned tx = bulk_bytes(bs, ch.b[first], (unsigned)(nb0 * sizeof(V)));
+      for (int sg = 0; sg < nseg; ++sg) {
+        const unsigned cnt = seg_end[sg] - (sg ? seg_end[sg - 1] : 0u);
+        tx += bulk_bytes(smem + seg_dst[sg], seg_src[sg], cnt * (unsigned)sizeof(TA));
+      }
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(tx)
+                   : "memory");
+      auto issue = [&](void *dst, const void *src, unsigned bytes) {
+        const unsigned nbulk = bulk_bytes(dst, src, bytes);
+        if (nbulk == 0) return;
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+            "[%3];" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+            "l"(src), "r"(nbulk), "r"(mb)
+            : "memory");
+      };
+      issue(bs, ch.b[first], (unsigned)(nb0 * sizeof(V)));
+      for (int sg = 0; sg < nseg; ++sg) {
+        const unsigned cnt = seg_end[sg] - (sg ? seg_end[sg - 1] : 0u);
+        issue(smem + seg_dst[sg], seg_src[sg], cnt * (unsigned)sizeof(TA));
+      }
+    }
+    {
+      const unsigned done0 = bulk_bytes(bs, ch.b[first], (unsigned)(nb0 * sizeof(V))) / sizeof(V);
+      for (int t = (int)done0 + threadIdx.x; t < nb0; t += blockDim.x) bs[t] = ch.b[first][t];
+      for (int sg = 0; sg < nseg; ++sg) {
+        const unsigned cnt = seg_end[sg] - (sg ? seg_end[sg - 1] : 0u);
+        TA *dst = (TA *)(smem + seg_dst[sg]);
+        const unsigned done = bulk_bytes(dst, seg_src[sg], cnt * (unsigned)sizeof(TA)) / sizeof(TA);
+        for (unsigned t = done + threadIdx.x; t < cnt; t += blockDim.x) dst[t] = seg_src[sg][t];
+      }
+    }
+    // the block decides together (a wait that expired in one thread ends the
+    // chain in all of them); copies still in flight land (bounded) first
+    const bool landed = mbar_wait(mb, 0, ch.err);
+    if (!__syncthreads_and(landed)) {
+      mbar_wait(mb, 0, nullptr);
+      return;
+    }
+  }
+  // inverse diagonals of every chain level
   for (int l = first; l <= last; ++l) {
-    const LevelView<TA> &g = ch.lv[l];
-    blk_load((FA *)(smem + soff[l][3]), g.ax, (g.nx + 1) * g.ny * g.nz);
-    blk_load((FA *)(smem + soff[l][4]), g.ay, g.nx * (g.ny + 1) * g.nz);
-    blk_load((FA *)(smem + soff[l][5]), g.az, g.nx * g.ny * (g.nz + 1));
+    const CLev<V, FA> L = lev(l);
+    const UDiv ux = make_udiv((unsigned)L.lv.nx);
+    const unsigned n = (unsigned)L.lv.ncell();
+    const V cc = V(L.lv.c);
+    for (unsigned t = threadIdx.x; t < n; t += blockDim.x) {
+      const unsigned row = ux.q(t), i = t - row * L.lv.nx;
+      const unsigned k = L.ny.q(row), j = row - k * L.ny.d;
+      const Six<V> sx = six<V>(L.lv, (int)i, (int)j, (int)k);
+      const V dg = sx.diag();
+      L.dinv[t] = dg > V(0) ? V(1) / (cc * dg) : V(0);
+    }
   }
   __syncthreads();
   for (int l = first; l < last; ++l) {
-    const LevelView<FA> lv = view(l);
-    V *x = X(l);
-    const V *b = B(l);
+    const CLev<V, FA> L = lev(l);
     for (int s = 0; s < ch.smooth; ++s) {
       if (s == 0)
-        blk_sweep<V, FA, kSweepZero>(lv, x, b, 0, none);
+        blk_sweep<V, FA, kSweepZero>(L, 0, none);
       else
-        blk_sweep<V, FA, kSweepPlain>(lv, x, b, 0, none);
-      blk_sweep<V, FA, kSweepPlain>(lv, x, b, 1, none);
+        blk_sweep<V, FA, kSweepPlain>(L, 0, none);
+      blk_sweep<V, FA, kSweepPlain>(L, 1, none);
     }
     const LevelView<TA> &cv = ch.lv[l + 1];
+    V *bc = (V *)(smem + soff[l + 1][1]);
     if (fused) {
-      blk_resrestrict<V, FA>(lv, x, b, cv.nx, cv.ny, cv.nz, B(l + 1), ch.pnu);
+      blk_resrestrict<V, FA>(L, cv.nx, cv.ny, cv.nz, bc, ch.pnu);
       continue;
     }
-    const int n = (int)lv.ncell();
+    const int n = (int)L.lv.ncell();
     V *r = R(l);
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
-      const int i = t % lv.nx, q = t / lv.nx;
-      const int j = q % lv.ny, k = q / lv.ny;
-      r[t] = residual_cell<V, FA>(lv, x, b, i, j, k, t) * V(ch.pn[l][t]);
+      const int i = t % L.lv.nx, q = t / L.lv.nx;
+      const int j = q % L.lv.ny, k = q / L.lv.ny;
+      r[t] = residual_cell<V, FA>(L.lv, L.x, L.b, i, j, k, t) * V(ch.pn[l][t]);
     }
     __syncthreads();
     const int nc = (int)cv.ncell();
-    V *bc = B(l + 1);
     for (int t = threadIdx.x; t < nc; t += blockDim.x) {
       const int I = t % cv.nx, q = t / cv.nx;
       const int J = q % cv.ny, K = q / cv.ny;
-      bc[t] = restrict_cell<V>(lv.nx, lv.ny, lv.nz, cv.nx, cv.ny, cv.nz, r, I, J, K,
+      bc[t] = restrict_cell<V>(L.lv.nx, L.lv.ny, L.lv.nz, cv.nx, cv.ny, cv.nz, r, I, J, K,
                                ch.transfer);
     }
     __syncthreads();
   }
   {
-    const LevelView<FA> lv = view(last);
-    V *x = X(last);
-    const V *b = B(last);
-    if (lv.ncell() <= 64) {
-      if (threadIdx.x < 32) {
-        for (int s = 0; s < ch.coarsest_sweeps; ++s) {
-          if (s == 0)
-            warp_sweep<V, FA, kSweepZero>(lv, x, b, 0, none);
-          else
-            warp_sweep<V, FA, kSweepPlain>(lv, x, b, 0, none);
-          warp_sweep<V, FA, kSweepPlain>(lv, x, b, 1, none);
-        }
-        for (int s = 0; s < ch.coarsest_sweeps; ++s) {
-          warp_sweep<V, FA, kSweepPlain>(lv, x, b, 1, none);
-          warp_sweep<V, FA, kSweepPlain>(lv, x, b, 0, none);
-        }
-      }
+    const CLev<V, FA> L = lev(last);
+    if (L.hx.d * L.ny.d * (unsigned)L.lv.nz <= 32u) {
+      if (threadIdx.x < 32) warp_coarsest<V, FA>(L, ch.coarsest_sweeps);
       __syncthreads();
     } else {
       for (int s = 0; s < ch.coarsest_sweeps; ++s) {
         if (s == 0)
-          blk_sweep<V, FA, kSweepZero>(lv, x, b, 0, none);
+          blk_sweep<V, FA, kSweepZero>(L, 0, none);
         else
-          blk_sweep<V, FA, kSweepPlain>(lv, x, b, 0, none);
-        blk_sweep<V, FA, kSweepPlain>(lv, x, b, 1, none);
+          blk_sweep<V, FA, kSweepPlain>(L, 0, none);
+        blk_sweep<V, FA, kSweepPlain>(L, 1, none);
       }
       for (int s = 0; s < ch.coarsest_sweeps; ++s) {
-        blk_sweep<V, FA, kSweepPlain>(lv, x, b, 1, none);
-        blk_sweep<V, FA, kSweepPlain>(lv, x, b, 0, none);
+        blk_sweep<V, FA, kSweepPlain>(L, 1, none);
+        blk_sweep<V, FA, kSweepPlain>(L, 0, none);
       }
     }
   }
   for (int l = last - 1; l >= first; --l) {
-    const LevelView<FA> lv = view(l);
+    const CLev<V, FA> L = lev(l);
     const LevelView<TA> &cv = ch.lv[l + 1];
-    V *x = X(l);
-    const V *b = B(l);
+    const V *xc = (const V *)(smem + soff[l + 1][0]);
     if (fused) {
-      const Fold<V> f{X(l + 1), cv.nx, cv.ny, V(ch.pnu)};
+      const Fold<V> f{xc, cv.nx, cv.ny, V(ch.pnu)};
       for (int s = 0; s < ch.smooth; ++s) {
         if (s == 0)
-          blk_sweep<V, FA, kSweepProlong>(lv, x, b, 1, f);
+          blk_sweep<V, FA, kSweepProlong>(L, 1, f);
         else
-          blk_sweep<V, FA, kSweepPlain>(lv, x, b, 1, none);
-        blk_sweep<V, FA, kSweepPlain>(lv, x, b, 0, none);
+          blk_sweep<V, FA, kSweepPlain>(L, 1, none);
+        blk_sweep<V, FA, kSweepPlain>(L, 0, none);
       }
       continue;
     }
-    const int n = (int)lv.ncell();
-    const V *xc = X(l + 1);
+    const int n = (int)L.lv.ncell();
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
-      const int i = t % lv.nx, q = t / lv.nx;
-      const int j = q % lv.ny, k = q / lv.ny;
-      if (six<float>(lv, i, j, k).diag() > 0.f)
-        x[t] += prolong_cell<V>(cv.nx, cv.ny, cv.nz, xc, i, j, k, ch.transfer) *
-                V(ch.pn[l][t]);
+      const int i = t % L.lv.nx, q = t / L.lv.nx;
+      const int j = q % L.lv.ny, k = q / L.lv.ny;
+      if (six<float>(L.lv, i, j, k).diag() > 0.f)
+        L.x[t] += prolong_cell<V>(cv.nx, cv.ny, cv.nz, xc, i, j, k, ch.transfer) *
+                  V(ch.pn[l][t]);
     }
     __syncthreads();
     for (int s = 0; s < ch.smooth; ++s) {
-      blk_sweep<V, FA, kSweepPlain>(lv, x, b, 1, none);
-      blk_sweep<V, FA, kSweepPlain>(lv, x, b, 0, none);
+      blk_sweep<V, FA, kSweepPlain>(L, 1, none);
+      blk_sweep<V, FA, kSweepPlain>(L, 0, none);
     }
   }
   {
     const int n = (int)ch.lv[first].ncell();
-    const V *x = X(first);
+    const V *x = (const V *)(smem + soff[first][0]);
     for (int t = threadIdx.x; t < n; t += blockDim.x) ch.x[first][t] = x[t];
   }
 }
@@ -1346,11 +1548,6 @@ k_mg_chain_smem(CoarseChain<V, TA> ch, const CGState *st) {
 // prolongation folded in) is a grid-stride loop over rows, consecutive
 // phases are separated by a grid-wide barrier, and between the down and the
 // up sweep block 0 runs the shared-memory chain while the others wait.
-__device__ __forceinline__ unsigned long long globaltimer_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
 
 // Grid-wide barrier of a cooperative launch: after the block's threads meet,
 // thread 0 adds one to *bar with release semantics (the block's writes,
@@ -1360,7 +1557,6 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 // clock, and after kBarrierNs it sets *err; every block then leaves at its
 // next barrier. Returns false (the same in all threads of the block) when
 // the kernel must stop.
-constexpr unsigned long long kBarrierNs = 1000000000ull;
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target,
                                              int *err) {
   __shared__ int ok;
@@ -1398,7 +1594,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target,
 template <class V, class TA>
 __global__ void __launch_bounds__(1024, 1)
 k_mg_mid(MidSpan<V, TA> m, CoarseChain<V, TA> ch, const CGState *st) {
-  if (stopped(st) || *(volatile int *)m.err != 0) return;
+  const int stop = stop_flag(st) | *(volatile int *)m.err;
   extern __shared__ __align__(16) unsigned char smem[];
   const RowWalk rw;
   const Fold<V> none{nullptr, 0, 0, V(0)};
@@ -1410,9 +1606,11 @@ k_mg_mid(MidSpan<V, TA> m, CoarseChain<V, TA> ch, const CGState *st) {
     const V *b = m.b[l];
     for (int s = 0; s < m.smooth; ++s) {
       if (s == 0)
-        sweep_rows<V, TA, kSweepZero>(lv, x, b, 0, none, rw.warp, rw.nwarps, rw.lane);
+        sweep_rows<V, TA, kSweepZero>(lv, x, b, 0, none, rw.warp, rw.nwarps, rw.lane,
+                                      l == m.lo ? stop : 0);
       else
         sweep_rows<V, TA, kSweepPlain>(lv, x, b, 0, none, rw.warp, rw.nwarps, rw.lane);
+      if (stop) return;  // (the same in every block: no barrier is left waiting)
       if (!sync()) return;
       sweep_rows<V, TA, kSweepPlain>(lv, x, b, 1, none, rw.warp, rw.nwarps, rw.lane);
       if (!sync()) return;
@@ -1444,9 +1642,11 @@ k_mg_mid(MidSpan<V, TA> m, CoarseChain<V, TA> ch, const CGState *st) {
 }
 
 // ------------------------------------------------------------ launchers ---
+// Grid-stride streaming kernels: at most one wave (148 SMs x 8 blocks of
+// kBlock threads), so every block pays its start-up latency once.
 static inline unsigned gs_blocks(int64_t n) {
-  const unsigned b = nblocks(n);
-  return b < (unsigned)kRedBlocks * 8 ? b : (unsigned)kRedBlocks * 8;
+  const unsigned b = nblocks(n), wave = 148u * 8u;
+  return b < wave ? b : wave;
 }
 
 template <class S, class T, class V>
@@ -1610,7 +1810,7 @@ void launch_mg_pnorm(const Launch &L, int fnx, int fny, int fnz,
 }
 template <class V, class TA>
 size_t mg_chain_smem_bytes(const CoarseChain<V, TA> &ch) {
-  size_t off[kMaxLevels][6];
+  size_t off[kMaxLevels][7];
   return chain_layout(ch, off);
 }
 // Allow a kernel the opt-in shared memory left beside its static shared

@@ -190,6 +190,7 @@ struct CoarseChain {
   int coarsest_sweeps;
   int smem_bytes;     // > 0: run the chain in that much dynamic shared memory
   float pnu;          // constant transfer: the uniform normaliser (pn's value)
+  int *err;           // set to 1 when a bounded wait of the chain expired
 };
 template <class V, class TA>
 void launch_mg_coarse_chain(const Launch &L, const CoarseChain<V, TA> &ch,

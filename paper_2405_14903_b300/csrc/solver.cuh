@@ -338,6 +338,7 @@ class Solver {
     ch.coarsest_sweeps = coarsest_sweeps();
     ch.smem_bytes = chain_smem_;
     ch.pnu = coarse_w();
+    ch.err = &((CGState *)st_)->err;
     return ch;
   }
 
