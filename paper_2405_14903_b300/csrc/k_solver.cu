@@ -437,7 +437,8 @@ __global__ void k_residual_outer_df(LevelView<float> lv, const double *b,
 }
 
 template <class S, class V>
-__global__ void k_axpy_outer(int64_t n, S *x, const V *e, double inv) {
+__global__ void __launch_bounds__(kBlock, sizeof(S) + sizeof(V) <= 12 ? 8 : 6)
+k_axpy_outer(int64_t n, S *x, const V *e, double inv) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   constexpr int U = kIlpStream;
   for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c0 < n;
@@ -466,7 +467,7 @@ __global__ void k_axpy_outer(int64_t n, S *x, const V *e, double inv) {
 // fixed order. FP64 arithmetic per element would cost more than the memory
 // traffic on this part, whose FP64 rate is 1/64 of FP32.
 template <class V>
-__global__ void k_cg_init(int64_t n, const V *r, const V *z, V *d, CGState *st,
+__global__ void __launch_bounds__(kBlock, 4) k_cg_init(int64_t n, const V *r, const V *z, V *d, CGState *st,
                           RedScratch rs) {
   // per-thread partials in V (a few terms each), block and grid sums in FP64
   V p0 = V(0), p1 = V(0);
@@ -507,7 +508,7 @@ __global__ void k_cg_init(int64_t n, const V *r, const V *z, V *d, CGState *st,
 }
 
 template <class V>
-__global__ void k_cg_continue(int64_t n, const V *r, const V *z, CGState *st,
+__global__ void __launch_bounds__(kBlock, 4) k_cg_continue(int64_t n, const V *r, const V *z, CGState *st,
                               RedScratch rs) {
   V p0 = V(0), p1 = V(0);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -583,7 +584,7 @@ __global__ void k_apply_dot(LevelView<TA> lv, const V *d, V *q, CGState *st,
 }
 
 template <class V>
-__global__ void k_cg_xr(int64_t n, V *x, V *r, const V *d, const V *q,
+__global__ void __launch_bounds__(kBlock, 4) k_cg_xr(int64_t n, V *x, V *r, const V *d, const V *q,
                         CGState *st, RedScratch rs, bool preconditioned) {
   const int stop = stop_flag(st);
   const V a = (V)st->alpha;
@@ -633,7 +634,7 @@ __global__ void k_cg_xr(int64_t n, V *x, V *r, const V *d, const V *q,
 }
 
 template <class V>
-__global__ void k_cg_rz(int64_t n, const V *r, const V *z, CGState *st,
+__global__ void __launch_bounds__(kBlock, 4) k_cg_rz(int64_t n, const V *r, const V *z, CGState *st,
                         RedScratch rs) {
   const int stop = stop_flag(st);
   V p = V(0);
@@ -669,9 +670,18 @@ __global__ void k_cg_rz(int64_t n, const V *r, const V *z, CGState *st,
 }
 
 template <class V>
-__global__ void k_cg_d(int64_t n, const V *z, V *d, const CGState *st) {
+__global__ void __launch_bounds__(kBlock, sizeof(V) == 4 ? 8 : 6) k_cg_d(int64_t n, const V *z, V *d, CGState *st, int loop,
+                       cudaGraphConditionalHandle handle) {
   const int stop = stop_flag(st);
   const V b = (V)st->beta;
+  if (loop && blockIdx.x == 0 && threadIdx.x == 0) {
+    // end of a body of the device-side loop: continue while the solve runs,
+    // under its iteration budget, and the bodies stay below max_it + 4 (so
+    // the loop ends even if no iteration is counted)
+    const int loops = ++st->loops;
+    const bool more = st->done == 0 && st->iters < st->max_it && loops < st->max_it + 4;
+    cudaGraphSetConditional(handle, more ? 1u : 0u);
+  }
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   constexpr int U = kIlpStream;
   for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c0 < n;
@@ -1643,7 +1653,8 @@ k_mg_mid(MidSpan<V, TA> m, CoarseChain<V, TA> ch, const CGState *st) {
 
 // ------------------------------------------------------------ launchers ---
 // Grid-stride streaming kernels: at most one wave (148 SMs x 8 blocks of
-// kBlock threads), so every block pays its start-up latency once.
+// kBlock threads; their launch bounds keep 8 blocks resident), so every
+// block pays its start-up latency once.
 static inline unsigned gs_blocks(int64_t n) {
   const unsigned b = nblocks(n), wave = 148u * 8u;
   return b < wave ? b : wave;
@@ -1710,10 +1721,11 @@ void launch_cg_rz(const Launch &L, int64_t n, const V *r, const V *z,
   ++*L.counter;
 }
 template <class V>
-void launch_cg_d(const Launch &L, int64_t n, const V *z, V *d,
-                 const CGState *st) {
+void launch_cg_d(const Launch &L, int64_t n, const V *z, V *d, CGState *st,
+                 const cudaGraphConditionalHandle *loop) {
   ProfScope _ps(L, NF_K_CG_D);
-  k_cg_d<V><<<gs_blocks(n), kBlock, 0, L.s>>>(n, z, d, st);
+  k_cg_d<V><<<gs_blocks(n), kBlock, 0, L.s>>>(n, z, d, st, loop != nullptr,
+                                                loop ? *loop : cudaGraphConditionalHandle{});
   ++*L.counter;
 }
 template <class TI, class TO>
@@ -1880,7 +1892,7 @@ void launch_mg_coarse_chain(const Launch &L, const CoarseChain<V, TA> &ch,
   template void launch_cg_rz<V>(const Launch &, int64_t, const V *,          \
                                 const V *, CGState *, const RedScratch &);    \
   template void launch_cg_d<V>(const Launch &, int64_t, const V *, V *,      \
-                               const CGState *);
+                               CGState *, const cudaGraphConditionalHandle *);
 #define NF_INST_VA(V, TA)                                                      \
   template void launch_apply_dot<V, TA>(const Launch &, const LevelView<TA> &,\
                                         const V *, V *, CGState *,            \

@@ -24,6 +24,8 @@ struct FieldsMut {
 struct CGState {
   double tol;    // relative tolerance of the inner solve (set by the host)
   double ratio;  // scale of this pass's r over the previous pass's (host)
+  int max_it;    // iterations this pass may take (host)
+  int loops;     // iteration bodies the device loop ran this pass (host zeroes)
   double rz;     // <r, z>
   double dq;     // <d, A d>
   double rr;     // <r, r>
@@ -112,9 +114,12 @@ void launch_cg_xr(const Launch &L, int64_t n, V *x, V *r, const V *d,
 template <class V>
 void launch_cg_rz(const Launch &L, int64_t n, const V *r, const V *z,
                   CGState *st, const RedScratch &rs);
+// d = z + beta d. With `loop` (the WHILE handle of the device-side CG loop,
+// whose body this launch ends) block 0 also decides whether the loop runs
+// another iteration.
 template <class V>
-void launch_cg_d(const Launch &L, int64_t n, const V *z, V *d,
-                 const CGState *st);
+void launch_cg_d(const Launch &L, int64_t n, const V *z, V *d, CGState *st,
+                 const cudaGraphConditionalHandle *loop = nullptr);
 
 // Multigrid pieces.
 // What a red-black half sweep folds into the x it reads (all three give

@@ -524,23 +524,78 @@ class Solver {
     }
   }
 
-  void iterations(int count) {
+  // `count` CG iterations; with `loop` the last launch also decides
+  // whether the device-side loop runs another body.
+  void iterations(int count, const cudaGraphConditionalHandle *loop = nullptr) {
     Launch L = ctx_->launch();
     CGState *st = (CGState *)st_;
     V *r = (V *)rin_, *z = (V *)z_, *d = (V *)d_, *q = (V *)q_, *e = (V *)e_;
     const LevelView<T> lv = view0();
     for (int b = 0; b < count; ++b) {
       ctx_->prof.capture_iter = b;
+      const cudaGraphConditionalHandle *last = b + 1 == count ? loop : nullptr;
       launch_apply_dot<V, T>(L, lv, d, q, st, ctx_->rs);
       launch_cg_xr<V>(L, n_, e, r, d, q, st, ctx_->rs, mg_);
       if (mg_) {
         precondition(r, z, st);
         launch_cg_rz<V>(L, n_, r, z, st, ctx_->rs);
-        launch_cg_d<V>(L, n_, z, d, st);
+        launch_cg_d<V>(L, n_, z, d, st, last);
       } else {
-        launch_cg_d<V>(L, n_, r, d, st);
+        launch_cg_d<V>(L, n_, r, d, st, last);
       }
     }
+  }
+
+  // The device-side iteration loop: a graph whose WHILE node runs one CG
+  // iteration per body, continued by its last kernel until the solve is done or
+  // its budget is spent, so a pass needs one launch and one read-back and
+  // no iteration runs after convergence. Not used while profiling (event
+  // nodes may not live in a conditional body) or if the capture fails.
+  struct Loop {
+    cudaGraphExec_t exec = nullptr;
+    int kernels = 0;  // kernel launches per body
+  };
+  bool ensure_loop(Loop &G) {
+    if (!graphs_ok_ || !loops_ok_ || ctx_->prof.kclass != -2) return false;
+    if (G.exec) return true;
+    if (!cap_ && cudaStreamCreateWithFlags(&cap_, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      loops_ok_ = false;
+      return false;
+    }
+    cudaGraph_t g = nullptr;
+    cudaGraphConditionalHandle h = 0;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p);
+    const int64_t before = ctx_->launches;
+    if (e == cudaSuccess)
+      e = cudaStreamBeginCaptureToGraph(cap_, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      ctx_->capture = cap_;
+      iterations(1, &h);
+      ctx_->capture = nullptr;
+      cudaGraph_t body = nullptr;
+      e = cudaStreamEndCapture(cap_, &body);
+    }
+    G.kernels = (int)(ctx_->launches - before);
+    ctx_->launches = before;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&G.exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      G.exec = nullptr;
+      loops_ok_ = false;
+      return false;
+    }
+    return true;
   }
 
   template <class F>
@@ -595,9 +650,15 @@ class Solver {
     double *slot = (double *)((char *)ctx_->pinned + 2048);
     slot[0] = rel_tol;
     slot[1] = ratio;
-    static_assert(offsetof(CGState, ratio) == offsetof(CGState, tol) + sizeof(double),
-                  "tol and ratio are copied together");
-    cudaMemcpyAsync(&st->tol, slot, 2 * sizeof(double), cudaMemcpyHostToDevice, ctx_->stream);
+    int *islot = (int *)(slot + 2);
+    islot[0] = max_it;
+    islot[1] = 0;
+    static_assert(offsetof(CGState, ratio) == offsetof(CGState, tol) + sizeof(double) &&
+                      offsetof(CGState, max_it) == offsetof(CGState, tol) + 2 * sizeof(double) &&
+                      offsetof(CGState, loops) == offsetof(CGState, max_it) + sizeof(int),
+                  "tol, ratio, max_it and loops are copied together");
+    cudaMemcpyAsync(&st->tol, slot, 2 * sizeof(double) + 2 * sizeof(int), cudaMemcpyHostToDevice,
+                    ctx_->stream);
     const int pv = proj_now_ ? 1 : 0;
     Graph &G0 = cont ? cont_g_[pv] : init_g_[pv];
     const bool g_init = cont ? ensure_graph(cont_g_[pv], [&] { cont_body(); })
@@ -608,8 +669,24 @@ class Solver {
       cont_body();
     else
       init_body();
-    int issued = 0, seen = 0;
     CGState hs{};
+    bool looped = false;
+    if (g_init && ensure_loop(loop_g_[pv])) {
+      looped = cudaGraphLaunch(loop_g_[pv].exec, ctx_->stream) == cudaSuccess;
+      if (!looped) {  // not launchable here: the batches below continue the pass
+        cudaGetLastError();
+        loops_ok_ = false;
+      }
+    }
+    if (looped) {
+      ctx_->read_bytes(&hs, st, sizeof(CGState));
+      ctx_->launches += (int64_t)hs.loops * loop_g_[pv].kernels;
+      *iters = hs.iters;
+      *done = hs.err ? 5 : hs.done;
+      *rr = hs.rr;
+      return;
+    }
+    int issued = 0, seen = 0;
     bool init_collected = !g_init;
     while (issued < max_it) {
       const bool full = max_it - issued >= kBatch;
@@ -656,13 +733,16 @@ class Solver {
        *d_ = nullptr, *q_ = nullptr, *st_ = nullptr, *norm2_ = nullptr;
   cudaStream_t cap_ = nullptr;
   bool graphs_ok_ = true;
+  bool loops_ok_ = true;
   Graph init_g_[2], cont_g_[2], batch_g_[2];  // [1]: with the projection
+  Loop loop_g_[2];
   Components *proj_ = nullptr;  // the episode's components (null: none)
   bool proj_now_ = false;       // this solve's system has a floating part
 
  public:
   ~Solver() {
     for (int p = 0; p < 2; ++p) {
+      if (loop_g_[p].exec) cudaGraphExecDestroy(loop_g_[p].exec);
       if (init_g_[p].exec) cudaGraphExecDestroy(init_g_[p].exec);
       if (cont_g_[p].exec) cudaGraphExecDestroy(cont_g_[p].exec);
       if (batch_g_[p].exec) cudaGraphExecDestroy(batch_g_[p].exec);
