@@ -72,7 +72,7 @@ def parse():
                     help="1: the tape keeps each step's fractions (no re-rasterising)")
     ap.add_argument("--coarse-weight", type=float, default=1.9,
                     help="scale of the coarse-grid correction")
-    ap.add_argument("--mg-persistent", type=int, default=1,
+    ap.add_argument("--mg-persistent", type=int, default=0,
                     help="1: coarse levels <= 64^3 and the chain in one cooperative kernel")
     ap.add_argument("--mg-coarsest", type=int, default=4,
                     help="stop coarsening at this many cells per edge")

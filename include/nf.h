@@ -120,8 +120,10 @@ typedef struct nf_config {
   int mg_persistent;      /* 1: the coarse levels of at most 64^3 cells above
                              the one-block chain run, with the chain, as the
                              phases of one cooperative kernel (constant
-                             transfer only); 0: one launch per phase.
-                             Same arithmetic either way                      */
+                             transfer only); 0: one launch per phase (inside
+                             the solver's device-side CG loop these launches
+                             cost no more than the cooperative kernel's grid
+                             barriers). Same arithmetic either way           */
 } nf_config;
 
 typedef struct nf_grid {
@@ -161,7 +163,7 @@ typedef struct nf_step_stats {
    checkpoint_every 10, no budget, cfl_max 0 (no sub-stepping),
    mg_coarsest_sweeps 8, mg_band_sweeps 0, mg_transfer 1 (constant),
    mg_coarse_weight 1.9, mg_smooth_coarse 0, tape_fractions 0,
-   mg_persistent 1. */
+   mg_persistent 0. */
 int nf_config_default(nf_config *cfg);
 
 /* Create a context on cfg->device. *out receives the handle. */

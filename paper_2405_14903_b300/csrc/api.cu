@@ -202,7 +202,7 @@ int nf_config_default(nf_config *cfg) {
   cfg->mg_coarse_weight = 1.9;
   cfg->mg_smooth_coarse = 0;
   cfg->tape_fractions = 0;
-  cfg->mg_persistent = 1;
+  cfg->mg_persistent = 0;
   return NF_OK;
 }
 

@@ -585,7 +585,8 @@ __global__ void k_apply_dot(LevelView<TA> lv, const V *d, V *q, CGState *st,
 
 template <class V>
 __global__ void __launch_bounds__(kBlock, 4) k_cg_xr(int64_t n, V *x, V *r, const V *d, const V *q,
-                        CGState *st, RedScratch rs, bool preconditioned) {
+                        CGState *st, RedScratch rs, bool preconditioned, int loop,
+                        LoopHandles h) {
   const int stop = stop_flag(st);
   const V a = (V)st->alpha;
   V p = V(0);
@@ -629,6 +630,16 @@ __global__ void __launch_bounds__(kBlock, 4) k_cg_xr(int64_t n, V *x, V *r, cons
     } else if (!preconditioned) {
       st->beta = tot[0] / st->rz;
       st->rz = tot[0];
+    }
+    if (loop) {
+      // in the device-side loop: the rest of the body runs only while the
+      // solve runs; a finished solve also ends the loop
+      if (st->done) {
+        cudaGraphSetConditional(h.body, 0u);
+        cudaGraphSetConditional(h.tail, 0u);
+      } else {
+        cudaGraphSetConditional(h.tail, 1u);
+      }
     }
   }
 }
@@ -1708,9 +1719,10 @@ void launch_apply_dot(const Launch &L, const LevelView<TA> &lv, const V *d,
 template <class V>
 void launch_cg_xr(const Launch &L, int64_t n, V *x, V *r, const V *d,
                   const V *q, CGState *st, const RedScratch &rs,
-                  bool preconditioned) {
+                  bool preconditioned, const LoopHandles *loop) {
   ProfScope _ps(L, NF_K_CG_XR);
-  k_cg_xr<V><<<kRedBlocks, kBlock, 0, L.s>>>(n, x, r, d, q, st, rs, preconditioned);
+  k_cg_xr<V><<<kRedBlocks, kBlock, 0, L.s>>>(n, x, r, d, q, st, rs, preconditioned,
+                                             loop != nullptr, loop ? *loop : LoopHandles{});
   ++*L.counter;
 }
 template <class V>
@@ -1888,7 +1900,7 @@ void launch_mg_coarse_chain(const Launch &L, const CoarseChain<V, TA> &ch,
                                       const RedScratch &);                    \
   template void launch_cg_xr<V>(const Launch &, int64_t, V *, V *, const V *,\
                                 const V *, CGState *, const RedScratch &,     \
-                                bool);                                        \
+                                bool, const LoopHandles *);                   \
   template void launch_cg_rz<V>(const Launch &, int64_t, const V *,          \
                                 const V *, CGState *, const RedScratch &);    \
   template void launch_cg_d<V>(const Launch &, int64_t, const V *, V *,      \

@@ -107,10 +107,19 @@ void launch_cg_continue(const Launch &L, int64_t n, const V *r, const V *z,
 template <class V, class TA>
 void launch_apply_dot(const Launch &L, const LevelView<TA> &lv, const V *d,
                       V *q, CGState *st, const RedScratch &rs);
+// The conditional handles of the device-side CG loop: `body` (WHILE: run
+// another iteration) and `tail` (IF: run the rest of this iteration after
+// the x, r update).
+struct LoopHandles {
+  cudaGraphConditionalHandle body, tail;
+};
+// x += alpha d, r -= alpha q, <r, r>, done when <r, r> <= stop2. With `loop`
+// it also sets the loop's conditions: a finished solve skips the rest of the
+// iteration and ends the loop.
 template <class V>
 void launch_cg_xr(const Launch &L, int64_t n, V *x, V *r, const V *d,
                   const V *q, CGState *st, const RedScratch &rs,
-                  bool preconditioned);
+                  bool preconditioned, const LoopHandles *loop = nullptr);
 template <class V>
 void launch_cg_rz(const Launch &L, int64_t n, const V *r, const V *z,
                   CGState *st, const RedScratch &rs);

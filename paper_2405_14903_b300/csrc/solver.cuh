@@ -524,36 +524,48 @@ class Solver {
     }
   }
 
-  // `count` CG iterations; with `loop` the last launch also decides
-  // whether the device-side loop runs another body.
-  void iterations(int count, const cudaGraphConditionalHandle *loop = nullptr) {
-    Launch L = ctx_->launch();
-    CGState *st = (CGState *)st_;
-    V *r = (V *)rin_, *z = (V *)z_, *d = (V *)d_, *q = (V *)q_, *e = (V *)e_;
-    const LevelView<T> lv = view0();
+  void iterations(int count) {
     for (int b = 0; b < count; ++b) {
       ctx_->prof.capture_iter = b;
-      const cudaGraphConditionalHandle *last = b + 1 == count ? loop : nullptr;
-      launch_apply_dot<V, T>(L, lv, d, q, st, ctx_->rs);
-      launch_cg_xr<V>(L, n_, e, r, d, q, st, ctx_->rs, mg_);
-      if (mg_) {
-        precondition(r, z, st);
-        launch_cg_rz<V>(L, n_, r, z, st, ctx_->rs);
-        launch_cg_d<V>(L, n_, z, d, st, last);
-      } else {
-        launch_cg_d<V>(L, n_, r, d, st, last);
-      }
+      iteration_head(nullptr);
+      iteration_tail(nullptr);
+    }
+  }
+  // One CG iteration in two parts: q = A d, alpha, x and r updates (with
+  // `loop`: setting the device loop's conditions) ...
+  void iteration_head(const LoopHandles *loop) {
+    Launch L = ctx_->launch();
+    CGState *st = (CGState *)st_;
+    V *r = (V *)rin_, *d = (V *)d_, *q = (V *)q_, *e = (V *)e_;
+    launch_apply_dot<V, T>(L, view0(), d, q, st, ctx_->rs);
+    launch_cg_xr<V>(L, n_, e, r, d, q, st, ctx_->rs, mg_, loop);
+  }
+  // ... and z = M r, beta, d = z + beta d (with `loop`: deciding whether the
+  // device loop runs another iteration).
+  void iteration_tail(const LoopHandles *loop) {
+    Launch L = ctx_->launch();
+    CGState *st = (CGState *)st_;
+    V *r = (V *)rin_, *z = (V *)z_, *d = (V *)d_;
+    const cudaGraphConditionalHandle *body = loop ? &loop->body : nullptr;
+    if (mg_) {
+      precondition(r, z, st);
+      launch_cg_rz<V>(L, n_, r, z, st, ctx_->rs);
+      launch_cg_d<V>(L, n_, z, d, st, body);
+    } else {
+      launch_cg_d<V>(L, n_, r, d, st, body);
     }
   }
 
   // The device-side iteration loop: a graph whose WHILE node runs one CG
-  // iteration per body, continued by its last kernel until the solve is done or
-  // its budget is spent, so a pass needs one launch and one read-back and
-  // no iteration runs after convergence. Not used while profiling (event
+  // iteration per body, continued by its last kernel until the solve is
+  // done or its budget is spent, so a pass needs one launch and one
+  // read-back. Inside the body an IF node holds everything after the x, r
+  // update: the iteration that meets the tolerance skips its V-cycle (the
+  // update kernel clears both conditions). Not used while profiling (event
   // nodes may not live in a conditional body) or if the capture fails.
   struct Loop {
     cudaGraphExec_t exec = nullptr;
-    int kernels = 0;  // kernel launches per body
+    int head = 0, tail = 0;  // kernel launches of the two parts of a body
   };
   bool ensure_loop(Loop &G) {
     if (!graphs_ok_ || !loops_ok_ || ctx_->prof.kclass != -2) return false;
@@ -563,29 +575,69 @@ class Solver {
       loops_ok_ = false;
       return false;
     }
+    // graph: WHILE { head; IF { tail } }
     cudaGraph_t g = nullptr;
-    cudaGraphConditionalHandle h = 0;
+    LoopHandles h{};
     cudaError_t e = cudaGraphCreate(&g, 0);
-    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
-    cudaGraphNodeParams p{};
-    p.type = cudaGraphNodeTypeConditional;
-    p.conditional.handle = h;
-    p.conditional.type = cudaGraphCondTypeWhile;
-    p.conditional.size = 1;
-    cudaGraphNode_t node = nullptr;
-    if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h.body, g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams wp{};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = h.body;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t wnode = nullptr;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &wp);
+    cudaGraph_t body = e == cudaSuccess ? wp.conditional.phGraph_out[0] : nullptr;
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h.tail, body, 1, cudaGraphCondAssignDefault);
     const int64_t before = ctx_->launches;
+    int64_t mid = before;
     if (e == cudaSuccess)
-      e = cudaStreamBeginCaptureToGraph(cap_, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+      e = cudaStreamBeginCaptureToGraph(cap_, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      ctx_->capture = cap_;
+      iteration_head(&h);
+      mid = ctx_->launches;
+      ctx_->capture = nullptr;
+      cudaGraph_t out = nullptr;
+      e = cudaStreamEndCapture(cap_, &out);
+    }
+    // the head is a chain: its one node without dependents precedes the IF
+    cudaGraphNode_t leaf = nullptr;
+    if (e == cudaSuccess) {
+      size_t n = 0;
+      e = cudaGraphGetNodes(body, nullptr, &n);
+      std::vector<cudaGraphNode_t> nodes(n);
+      if (e == cudaSuccess && n > 0) e = cudaGraphGetNodes(body, nodes.data(), &n);
+      int leaves = 0;
+      for (size_t i = 0; e == cudaSuccess && i < n; ++i) {
+        size_t nd = 0;
+        e = cudaGraphNodeGetDependentNodes(nodes[i], nullptr, nullptr, &nd);
+        if (e == cudaSuccess && nd == 0) {
+          leaf = nodes[i];
+          ++leaves;
+        }
+      }
+      if (e == cudaSuccess && leaves != 1) e = cudaErrorInvalidValue;
+    }
+    cudaGraphNodeParams ip{};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = h.tail;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    cudaGraphNode_t inode = nullptr;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&inode, body, &leaf, nullptr, 1, &ip);
+    if (e == cudaSuccess)
+      e = cudaStreamBeginCaptureToGraph(cap_, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                         cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
       ctx_->capture = cap_;
-      iterations(1, &h);
+      iteration_tail(&h);
       ctx_->capture = nullptr;
-      cudaGraph_t body = nullptr;
-      e = cudaStreamEndCapture(cap_, &body);
+      cudaGraph_t out = nullptr;
+      e = cudaStreamEndCapture(cap_, &out);
     }
-    G.kernels = (int)(ctx_->launches - before);
+    G.head = (int)(mid - before);
+    G.tail = (int)(ctx_->launches - mid);
     ctx_->launches = before;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&G.exec, g, 0);
     if (g) cudaGraphDestroy(g);
@@ -680,7 +732,10 @@ class Solver {
     }
     if (looped) {
       ctx_->read_bytes(&hs, st, sizeof(CGState));
-      ctx_->launches += (int64_t)hs.loops * loop_g_[pv].kernels;
+      // bodies that ran the tail are counted on the device; a converged
+      // solve ran one more body without it
+      const int64_t bodies = hs.loops + (hs.done == 1 ? 1 : 0);
+      ctx_->launches += bodies * loop_g_[pv].head + (int64_t)hs.loops * loop_g_[pv].tail;
       *iters = hs.iters;
       *done = hs.err ? 5 : hs.done;
       *rr = hs.rr;
