@@ -216,6 +216,16 @@ __device__ __forceinline__ int stop_flag(const CGState *st) {
   return st != nullptr ? *(volatile const int *)&st->done : 0;
 }
 
+// Programmatic dependent launch: kernels launched by launch_pdl may start
+// while their predecessor in the stream finishes. Each such kernel first
+// waits until the predecessor has completed and its writes are visible,
+// then lets its own successor's blocks be scheduled (they wait the same
+// way). Without the launch attribute both instructions are no-ops.
+__device__ __forceinline__ void pdl_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ------------------------------------------------------------- ILP ------
 // Grid-stride kernels walk cells in batches of ILP cells per thread (cells
 // c0, c0 + stride, ...): every load of a batch is issued before its results
@@ -387,6 +397,7 @@ __global__ void k_residual_outer_df(LevelView<float> lv, const double *b,
                                     const double *x, float *rin, int es,
                                     float rscale, double scale, RedScratch rs,
                                     double *norm2) {
+  pdl_wait();
   float acc = 0.f;
   const RowWalk w;
   const int nrows = lv.ny * lv.nz;
@@ -439,6 +450,7 @@ __global__ void k_residual_outer_df(LevelView<float> lv, const double *b,
 template <class S, class V>
 __global__ void __launch_bounds__(kBlock, sizeof(S) + sizeof(V) <= 12 ? 8 : 6)
 k_axpy_outer(int64_t n, S *x, const V *e, double inv) {
+  pdl_wait();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   constexpr int U = kIlpStream;
   for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c0 < n;
@@ -469,6 +481,7 @@ k_axpy_outer(int64_t n, S *x, const V *e, double inv) {
 template <class V>
 __global__ void __launch_bounds__(kBlock, 4) k_cg_init(int64_t n, const V *r, const V *z, V *d, CGState *st,
                           RedScratch rs) {
+  pdl_wait();
   // per-thread partials in V (a few terms each), block and grid sums in FP64
   V p0 = V(0), p1 = V(0);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -510,6 +523,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_cg_init(int64_t n, const V *r, co
 template <class V>
 __global__ void __launch_bounds__(kBlock, 4) k_cg_continue(int64_t n, const V *r, const V *z, CGState *st,
                               RedScratch rs) {
+  pdl_wait();
   V p0 = V(0), p1 = V(0);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   constexpr int U = kIlpStream;
@@ -552,6 +566,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_cg_continue(int64_t n, const V *r
 template <class V, class TA>
 __global__ void k_apply_dot(LevelView<TA> lv, const V *d, V *q, CGState *st,
                             RedScratch rs) {
+  pdl_wait();
   const int stop = stop_flag(st);
   V p = V(0);
   const RowWalk w;
@@ -587,6 +602,7 @@ template <class V>
 __global__ void __launch_bounds__(kBlock, 4) k_cg_xr(int64_t n, V *x, V *r, const V *d, const V *q,
                         CGState *st, RedScratch rs, bool preconditioned, int loop,
                         LoopHandles h) {
+  pdl_wait();
   const int stop = stop_flag(st);
   const V a = (V)st->alpha;
   V p = V(0);
@@ -647,6 +663,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_cg_xr(int64_t n, V *x, V *r, cons
 template <class V>
 __global__ void __launch_bounds__(kBlock, 4) k_cg_rz(int64_t n, const V *r, const V *z, CGState *st,
                         RedScratch rs) {
+  pdl_wait();
   const int stop = stop_flag(st);
   V p = V(0);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -683,6 +700,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_cg_rz(int64_t n, const V *r, cons
 template <class V>
 __global__ void __launch_bounds__(kBlock, sizeof(V) == 4 ? 8 : 6) k_cg_d(int64_t n, const V *z, V *d, CGState *st, int loop,
                        cudaGraphConditionalHandle handle) {
+  pdl_wait();
   const int stop = stop_flag(st);
   const V b = (V)st->beta;
   if (loop && blockIdx.x == 0 && threadIdx.x == 0) {
@@ -922,6 +940,7 @@ __device__ __forceinline__ void resrestrict_rows(const LevelView<TA> &lv,
 template <class V, class TA, int MODE>
 __global__ void k_mg_smooth(LevelView<TA> lv, V *x, const V *b, int color,
                             Fold<V> f, const CGState *st) {
+  pdl_wait();
   const int stop = stop_flag(st);
   const RowWalk w;
   sweep_rows<V, TA, MODE>(lv, x, b, color, f, w.warp, w.nwarps, w.lane, stop);
@@ -1024,6 +1043,7 @@ template <class V, class TA>
 __global__ void k_mg_resrestrict(LevelView<TA> lv, const V *x, const V *b,
                                  int cnx, int cny, int cnz, V *bc, float pn,
                                  const CGState *st) {
+  pdl_wait();
   const int stop = stop_flag(st);
   const RowWalk w;
   resrestrict_rows<V, TA>(lv, x, b, cnx, cny, cnz, bc, pn, w.warp, w.nwarps, w.lane, stop);
@@ -1556,6 +1576,7 @@ __device__ void chain_body(const CoarseChain<V, TA> &ch, unsigned char *smem) {
 template <class V, class TA>
 __global__ void __launch_bounds__(1024, 1)
 k_mg_chain_smem(CoarseChain<V, TA> ch, const CGState *st) {
+  pdl_wait();
   if (stopped(st)) return;
   extern __shared__ __align__(16) unsigned char smem[];
   chain_body<V, TA>(ch, smem);
@@ -1663,6 +1684,23 @@ k_mg_mid(MidSpan<V, TA> m, CoarseChain<V, TA> ch, const CGState *st) {
 }
 
 // ------------------------------------------------------------ launchers ---
+// Launch with programmatic dependent launch allowed (the kernel calls
+// pdl_wait() before reading anything its predecessor wrote).
+template <class... P, class... A>
+static void launch_pdl(void (*kernel)(P...), unsigned grid, unsigned block, size_t smem,
+                       cudaStream_t s, A... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, (P)args...);
+}
 // Grid-stride streaming kernels: at most one wave (148 SMs x 8 blocks of
 // kBlock threads; their launch bounds keep 8 blocks resident), so every
 // block pays its start-up latency once.
@@ -1680,8 +1718,8 @@ void launch_residual_outer(const Launch &L, const LevelView<T> &lv, const S *b,
     // split arithmetic needs c = 1 and the scale of rin in float range
     const double rscale = std::ldexp(scale, -es);
     if (lv.c == 1.0 && rscale >= 0x1p-120 && rscale <= 0x1p120) {
-      k_residual_outer_df<<<kRedBlocks, kBlock, 0, L.s>>>(lv, b, x, rin, es, (float)rscale,
-                                                         scale, rs, norm2);
+      launch_pdl(k_residual_outer_df, kRedBlocks, kBlock, 0, L.s, lv, b, x, rin, es,
+                 (float)rscale, scale, rs, norm2);
       ++*L.counter;
       return;
     }
@@ -1692,28 +1730,28 @@ void launch_residual_outer(const Launch &L, const LevelView<T> &lv, const S *b,
 template <class S, class V>
 void launch_axpy_outer(const Launch &L, int64_t n, S *x, const V *e, double inv) {
   ProfScope _ps(L, NF_K_AXPY64);
-  k_axpy_outer<S, V><<<gs_blocks(n), kBlock, 0, L.s>>>(n, x, e, inv);
+  launch_pdl(k_axpy_outer<S, V>, gs_blocks(n), kBlock, 0, L.s, n, x, e, inv);
   ++*L.counter;
 }
 template <class V>
 void launch_cg_init(const Launch &L, int64_t n, const V *r, const V *z, V *d,
                     CGState *st, const RedScratch &rs) {
   ProfScope _ps(L, NF_K_CG_INIT);
-  k_cg_init<V><<<kRedBlocks, kBlock, 0, L.s>>>(n, r, z, d, st, rs);
+  launch_pdl(k_cg_init<V>, kRedBlocks, kBlock, 0, L.s, n, r, z, d, st, rs);
   ++*L.counter;
 }
 template <class V>
 void launch_cg_continue(const Launch &L, int64_t n, const V *r, const V *z,
                         CGState *st, const RedScratch &rs) {
   ProfScope _ps(L, NF_K_CG_INIT);
-  k_cg_continue<V><<<kRedBlocks, kBlock, 0, L.s>>>(n, r, z, st, rs);
+  launch_pdl(k_cg_continue<V>, kRedBlocks, kBlock, 0, L.s, n, r, z, st, rs);
   ++*L.counter;
 }
 template <class V, class TA>
 void launch_apply_dot(const Launch &L, const LevelView<TA> &lv, const V *d,
                       V *q, CGState *st, const RedScratch &rs) {
   ProfScope _ps(L, NF_K_APPLY_DOT);
-  k_apply_dot<V, TA><<<kRedBlocks, kBlock, 0, L.s>>>(lv, d, q, st, rs);
+  launch_pdl(k_apply_dot<V, TA>, kRedBlocks, kBlock, 0, L.s, lv, d, q, st, rs);
   ++*L.counter;
 }
 template <class V>
@@ -1721,23 +1759,23 @@ void launch_cg_xr(const Launch &L, int64_t n, V *x, V *r, const V *d,
                   const V *q, CGState *st, const RedScratch &rs,
                   bool preconditioned, const LoopHandles *loop) {
   ProfScope _ps(L, NF_K_CG_XR);
-  k_cg_xr<V><<<kRedBlocks, kBlock, 0, L.s>>>(n, x, r, d, q, st, rs, preconditioned,
-                                             loop != nullptr, loop ? *loop : LoopHandles{});
+  launch_pdl(k_cg_xr<V>, kRedBlocks, kBlock, 0, L.s, n, x, r, d, q, st, rs, preconditioned,
+             (int)(loop != nullptr), loop ? *loop : LoopHandles{});
   ++*L.counter;
 }
 template <class V>
 void launch_cg_rz(const Launch &L, int64_t n, const V *r, const V *z,
                   CGState *st, const RedScratch &rs) {
   ProfScope _ps(L, NF_K_CG_RZ);
-  k_cg_rz<V><<<kRedBlocks, kBlock, 0, L.s>>>(n, r, z, st, rs);
+  launch_pdl(k_cg_rz<V>, kRedBlocks, kBlock, 0, L.s, n, r, z, st, rs);
   ++*L.counter;
 }
 template <class V>
 void launch_cg_d(const Launch &L, int64_t n, const V *z, V *d, CGState *st,
                  const cudaGraphConditionalHandle *loop) {
   ProfScope _ps(L, NF_K_CG_D);
-  k_cg_d<V><<<gs_blocks(n), kBlock, 0, L.s>>>(n, z, d, st, loop != nullptr,
-                                                loop ? *loop : cudaGraphConditionalHandle{});
+  launch_pdl(k_cg_d<V>, gs_blocks(n), kBlock, 0, L.s, n, z, d, st, (int)(loop != nullptr),
+             loop ? *loop : cudaGraphConditionalHandle{});
   ++*L.counter;
 }
 template <class TI, class TO>
@@ -1756,11 +1794,11 @@ void launch_mg_smooth(const Launch &L, const LevelView<TA> &lv, V *x,
   ProfScope _ps(L, kclass);
   const unsigned nb = row_blocks(lv.ny * lv.nz);
   if (mode == kSweepZero)
-    k_mg_smooth<V, TA, kSweepZero><<<nb, kBlock, 0, L.s>>>(lv, x, b, color, f, st);
+    launch_pdl(k_mg_smooth<V, TA, kSweepZero>, nb, kBlock, 0, L.s, lv, x, b, color, f, st);
   else if (mode == kSweepProlong)
-    k_mg_smooth<V, TA, kSweepProlong><<<nb, kBlock, 0, L.s>>>(lv, x, b, color, f, st);
+    launch_pdl(k_mg_smooth<V, TA, kSweepProlong>, nb, kBlock, 0, L.s, lv, x, b, color, f, st);
   else
-    k_mg_smooth<V, TA, kSweepPlain><<<nb, kBlock, 0, L.s>>>(lv, x, b, color, f, st);
+    launch_pdl(k_mg_smooth<V, TA, kSweepPlain>, nb, kBlock, 0, L.s, lv, x, b, color, f, st);
   ++*L.counter;
 }
 template <class TA>
@@ -1793,8 +1831,8 @@ void launch_mg_resrestrict(const Launch &L, const LevelView<TA> &fine, const V *
                            const V *b, int cnx, int cny, int cnz, V *bc, float pn,
                            const CGState *st) {
   ProfScope _ps(L, NF_K_MG_RESTRICT);
-  k_mg_resrestrict<V, TA><<<row_blocks(cny * cnz), kBlock, 0, L.s>>>(fine, x, b, cnx, cny,
-                                                                     cnz, bc, pn, st);
+  launch_pdl(k_mg_resrestrict<V, TA>, row_blocks(cny * cnz), kBlock, 0, L.s, fine, x, b, cnx, cny,
+             cnz, bc, pn, st);
   ++*L.counter;
 }
 template <class V, class TA>
@@ -1885,7 +1923,7 @@ void launch_mg_coarse_chain(const Launch &L, const CoarseChain<V, TA> &ch,
                             const CGState *st) {
   ProfScope _ps(L, NF_K_MG_CHAIN);
   if (ch.smem_bytes > 0)
-    k_mg_chain_smem<V, TA><<<1, 1024, ch.smem_bytes, L.s>>>(ch, st);
+    launch_pdl(k_mg_chain_smem<V, TA>, 1u, 1024u, (size_t)ch.smem_bytes, L.s, ch, st);
   else
     k_mg_coarse_chain<V, TA><<<1, 1024, 0, L.s>>>(ch, st);
   ++*L.counter;

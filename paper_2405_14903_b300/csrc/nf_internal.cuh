@@ -179,11 +179,13 @@ __device__ inline bool grid_sum(double (&v)[W], const RedScratch &rs,
   double acc[W];
 #pragma unroll
   for (int w = 0; w < W; ++w) acc[w] = 0.0;
-  // fixed order: thread t sums blocks t, t + blockDim, ...
+  // fixed order: thread t sums blocks t, t + blockDim, ... The partials are
+  // read past L1 (the scratch is reused by every reduction, so this SM's L1
+  // may hold an older kernel's values) and without volatile, so a thread's
+  // loads are all in flight before its sums.
   for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
 #pragma unroll
-    for (int w = 0; w < W; ++w)
-      acc[w] += *((volatile double *)&rs.partials[b * W + w]);
+    for (int w = 0; w < W; ++w) acc[w] += __ldcg(&rs.partials[b * W + w]);
   }
   block_sum<W>(acc, smem);
   if (threadIdx.x == 0) {
