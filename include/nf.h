@@ -259,7 +259,11 @@ int nf_launch_count(nf_ctx *ctx, int64_t *count);
 /* ------------------------------------------------------------- profiling */
 /* Environment: NF_GRAPHS=0 makes the solver launch every kernel directly
    instead of replaying CUDA graphs of its iteration batches (for profilers
-   that cannot follow stream capture). Kernels and results are unchanged. */
+   that cannot follow stream capture). Kernels and results are unchanged.
+   NF_TEST_STALL_WAITS=1 (test hook, read when an episode is created) makes
+   the solver's bounded device waits wait for something that never comes,
+   so that they expire (after about a second) and the solve returns
+   NF_E_TIMEOUT; the context stays usable. */
 /* Kernel classes that nf_profile can time (CUDA events on the context's
    stream bracketing every launch of the class). */
 #define NF_K_RASTERIZE 0

@@ -649,8 +649,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_cg_xr(int64_t n, V *x, V *r, cons
     }
     if (loop) {
       // in the device-side loop: the rest of the body runs only while the
-      // solve runs; a finished solve also ends the loop
-      if (st->done) {
+      // solve runs; a finished (or abandoned) solve also ends the loop
+      if (st->done || st->err) {
         cudaGraphSetConditional(h.body, 0u);
         cudaGraphSetConditional(h.tail, 0u);
       } else {
@@ -708,7 +708,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(V) == 4 ? 8 : 6) k_cg_d(int64_t
     // under its iteration budget, and the bodies stay below max_it + 4 (so
     // the loop ends even if no iteration is counted)
     const int loops = ++st->loops;
-    const bool more = st->done == 0 && st->iters < st->max_it && loops < st->max_it + 4;
+    const bool more = st->done == 0 && st->err == 0 && st->iters < st->max_it &&
+                      loops < st->max_it + 4;
     cudaGraphSetConditional(handle, more ? 1u : 0u);
   }
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -1367,6 +1368,9 @@ __device__ __forceinline__ bool mbar_wait(unsigned mb, unsigned parity, int *err
 template <class V, class TA>
 __device__ void chain_body(const CoarseChain<V, TA> &ch, unsigned char *smem) {
   using FA = typename ChainFA<TA>::type;
+  // a bounded wait expired: the solve is being abandoned (decided by the
+  // whole block, since another block may set the word meanwhile)
+  if (__syncthreads_or(ch.err != nullptr && *(volatile int *)ch.err != 0)) return;
   __shared__ unsigned soff[kMaxLevels][7];
   __shared__ UDiv sdiv[kMaxLevels][2];
   __shared__ const TA *seg_src[3 * kMaxLevels];
@@ -1431,7 +1435,7 @@ __device__ void chain_body(const CoarseChain<V, TA> &ch, unsigned char *smem) {
                                                                                : (bytes & ~15u);
     };
     if (threadIdx.x == 0) {
-      unsigned tx = bulk_bytes(bs, ch.b[first], (unsigned)(nb0 * sizeof(V)));
+      unsigned tx = bulk_bytes(bs, ch.b[first], (unsigned)(nb0 * sizeof(V))) + 16u * ch.stall;
       for (int sg = 0; sg < nseg; ++sg) {
         const unsigned cnt = seg_end[sg] - (sg ? seg_end[sg - 1] : 0u);
         tx += bulk_bytes(smem + seg_dst[sg], seg_src[sg], cnt * (unsigned)sizeof(TA));
@@ -1641,7 +1645,7 @@ k_mg_mid(MidSpan<V, TA> m, CoarseChain<V, TA> ch, const CGState *st) {
   const RowWalk rw;
   const Fold<V> none{nullptr, 0, 0, V(0)};
   unsigned phase = 0;
-  auto sync = [&]() { return grid_barrier(m.bar, ++phase * gridDim.x, m.err); };
+  auto sync = [&]() { return grid_barrier(m.bar, ++phase * gridDim.x + m.stall, m.err); };
   for (int l = m.lo; l < m.hi; ++l) {
     const LevelView<TA> lv = m.lv[l];
     V *x = m.x[l];

@@ -205,6 +205,7 @@ struct CoarseChain {
   int smem_bytes;     // > 0: run the chain in that much dynamic shared memory
   float pnu;          // constant transfer: the uniform normaliser (pn's value)
   int *err;           // set to 1 when a bounded wait of the chain expired
+  int stall;          // test hook: expect 16 bytes more than the copies bring
 };
 template <class V, class TA>
 void launch_mg_coarse_chain(const Launch &L, const CoarseChain<V, TA> &ch,
@@ -223,6 +224,7 @@ struct MidSpan {
   V *b[kMaxLevels];
   unsigned *bar;      // barrier counter (zeroed by the launcher)
   int *err;           // set to 1 when a barrier wait expired
+  int stall;          // test hook: every barrier waits for one block more
 };
 // Launches k_mg_mid cooperatively on `blocks` blocks of 1024 threads with
 // the chain's shared memory; returns NF_OK or NF_E_CUDA.

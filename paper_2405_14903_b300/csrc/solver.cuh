@@ -48,6 +48,11 @@ class Solver {
     // follow stream capture); the kernels and results are the same
     const char *env = std::getenv("NF_GRAPHS");
     if (env && std::strcmp(env, "0") == 0) graphs_ok_ = false;
+    // NF_TEST_STALL_WAITS=1: the device's bounded waits (grid barriers,
+    // the chain's mbarrier) wait for something that never comes, so that
+    // a test sees them expire into NF_E_TIMEOUT
+    const char *stall = std::getenv("NF_TEST_STALL_WAITS");
+    stall_ = stall && std::strcmp(stall, "1") == 0 ? 1 : 0;
   }
 
   // Allocates the hierarchy. Returns NF_OK or an error status.
@@ -339,6 +344,7 @@ class Solver {
     ch.smem_bytes = chain_smem_;
     ch.pnu = coarse_w();
     ch.err = &((CGState *)st_)->err;
+    ch.stall = stall_;
     return ch;
   }
 
@@ -355,6 +361,7 @@ class Solver {
     }
     m.bar = (unsigned *)bar_;
     m.err = &((CGState *)st_)->err;
+    m.stall = stall_;
     return m;
   }
 
@@ -789,6 +796,7 @@ class Solver {
   cudaStream_t cap_ = nullptr;
   bool graphs_ok_ = true;
   bool loops_ok_ = true;
+  int stall_ = 0;  // test hook (NF_TEST_STALL_WAITS)
   Graph init_g_[2], cont_g_[2], batch_g_[2];  // [1]: with the projection
   Loop loop_g_[2];
   Components *proj_ = nullptr;  // the episode's components (null: none)

@@ -337,3 +337,63 @@ def test_persistent_coarse_levels_match_per_phase_launches_and_oracle(nf, prec, 
     assert sp["iters"] == sn["iters"] and sp["outer"] == sn["outer"]
     assert rel(up, un) <= (1e-12 if prec == "fp64" else 1e-6)
     assert rel(up, U_ref) <= VEL_TOL[prec]
+
+
+# ------------------------------------------------------- bounded waits ----
+# Every device wait (the cooperative kernel's grid barriers, the chain's
+# mbarrier) gives up after about a second. The test hook makes them wait for
+# something that never comes: the solve must end with NF_E_TIMEOUT (status 5)
+# within seconds and the context must stay usable.
+
+@pytest.mark.parametrize("persistent", [False, True], ids=["chain_mbarrier", "grid_barrier"])
+def test_expired_device_waits_report_timeout_and_the_context_recovers(nf, monkeypatch, persistent):
+    import time
+    cfg = I.config_sphere(64, steps=0)
+    monkeypatch.setenv("NF_TEST_STALL_WAITS", "1")
+    ctx = make_ctx(nf, "mixed", mg_persistent=persistent, max_iters=50)
+    ep = ctx.episode(cfg["grid"], cfg["scene"])
+    monkeypatch.delenv("NF_TEST_STALL_WAITS")
+    t0 = time.time()
+    with pytest.raises(nf.NFError) as e:
+        ep.set_velocity(device_u(cfg), project=True)
+    assert e.value.status == 5
+    assert time.time() - t0 < 60
+    ep.close()
+    ctx.close()
+    ctx = make_ctx(nf, "mixed", mg_persistent=persistent)   # without the hook
+    ep = ctx.episode(cfg["grid"], cfg["scene"])
+    st = ep.set_velocity(device_u(cfg), project=True)
+    assert st["rel_residual"] <= SOLVE_TOL["mixed"]
+    ep.close()
+    ctx.close()
+
+
+# -------------------------------------------------------- launch paths ----
+# The solver runs its iterations in a device-side conditional-graph loop by
+# default, in replayed batches of graphs while profiling, and as direct
+# launches with NF_GRAPHS=0. The kernels and their order are the same (the
+# other paths only add launches that return at once), so a forward rollout
+# gives the same bits and iteration counts on all three.
+
+def test_launch_paths_give_the_same_bits(nf, monkeypatch):
+    cfg = CONFIGS["chamber_sub"]()
+
+    def run(profile=False, graphs=True):
+        if not graphs:
+            monkeypatch.setenv("NF_GRAPHS", "0")
+        ctx = make_ctx(nf, "mixed", cfg=cfg)
+        if profile:
+            ctx.profile("all")
+        ep = ctx.episode(cfg["grid"], cfg["scene"])
+        monkeypatch.delenv("NF_GRAPHS", raising=False)
+        ep.set_velocity(device_u(cfg), project=cfg["project_initial"])
+        st = ep.step(cfg["steps"])
+        U = host(ep.velocity())
+        ep.close()
+        ctx.close()
+        return st, U
+
+    (sa, ua), (sb, ub), (sc, uc) = run(), run(profile=True), run(graphs=False)
+    assert sa["iters"] == sb["iters"] == sc["iters"] and sa["outer"] == sb["outer"] == sc["outer"]
+    for x, y, z in zip(ua, ub, uc):
+        assert np.array_equal(x, y) and np.array_equal(x, z)
