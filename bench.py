@@ -72,6 +72,8 @@ def parse():
                     help="1: the tape keeps each step's fractions (no re-rasterising)")
     ap.add_argument("--coarse-weight", type=float, default=1.9,
                     help="scale of the coarse-grid correction")
+    ap.add_argument("--residual-fp64", type=int, default=0,
+                    help="1: MIXED refinement residual in FP64 arithmetic (0: split-float)")
     ap.add_argument("--mg-persistent", type=int, default=0,
                     help="1: coarse levels <= 64^3 and the chain in one cooperative kernel")
     ap.add_argument("--mg-coarsest", type=int, default=4,
@@ -204,7 +206,7 @@ def run_ours(args, rank, world, local_rank):
                     mg_transfer=args.mg_transfer, mg_coarse_weight=args.coarse_weight,
                     mg_smooth_coarse=args.mg_smooth_coarse, tape_fractions=bool(args.tape_fractions),
                     mg_persistent=bool(args.mg_persistent),
-                    device=local_rank)
+                    residual_fp64=bool(args.residual_fp64), device=local_rank)
     ep = ctx.episode(cfg["grid"], cfg["scene"])
     u0 = [torch.zeros(s, dtype=torch.float32, device=dev) for s in ep.face_shapes]
     stats = {}
@@ -272,7 +274,10 @@ def run_ours(args, rank, world, local_rank):
                            cfl_max=cfg["cfl_max"], substeps_executed=int(stats["fwd"]["steps"]),
                            precision="FP32 MGPCG (V-cycle, CG vectors; BF16 coarse-level "
                                      "fractions), FP32 per-thread dot partials summed in FP64, "
-                                     f"FP64 residual refinement to rel res {args.tol:g}",
+                                     f"FP64 refinement (x, b FP64) to rel res {args.tol:g}, its "
+                                     "residual in "
+                                     + ("FP64 arithmetic" if args.residual_fp64 else
+                                        "split-float arithmetic (48-bit, no FP64 instructions)"),
                            inner_tol=args.inner_tol, mg_smooth=args.mg_smooth,
                            mg_coarsest=args.mg_coarsest, coarsest_sweeps=args.coarsest_sweeps,
                            band_sweeps=args.band_sweeps, mg_transfer=args.mg_transfer,
@@ -280,6 +285,7 @@ def run_ours(args, rank, world, local_rank):
                            mg_smooth_coarse=args.mg_smooth_coarse,
                            tape_fractions=bool(args.tape_fractions),
                            mg_persistent=bool(args.mg_persistent),
+                           residual_fp64=bool(args.residual_fp64),
                            l2="inputs larger than L2 (episode state and tape > 1 GB)",
                            parallelism=f"replicas x{world}"),
                gpu_launches=int(launches), iterations=dict(fwd=stats["fwd"], bwd=stats["bwd"]),

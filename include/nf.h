@@ -124,6 +124,12 @@ typedef struct nf_config {
                              the solver's device-side CG loop these launches
                              cost no more than the cooperative kernel's grid
                              barriers). Same arithmetic either way           */
+  int residual_fp64;      /* MIXED refinement residual r = b - A x (x, b FP64):
+                             1: FP64 arithmetic; 0: split-float arithmetic
+                             (each FP64 value as a float pair, error-free
+                             float transforms: ~48 significant bits, error
+                             about 2^-44 max|x|), free of FP64 instructions,
+                             which run at 1/64 of the FP32 rate here         */
 } nf_config;
 
 typedef struct nf_grid {
@@ -163,7 +169,7 @@ typedef struct nf_step_stats {
    checkpoint_every 10, no budget, cfl_max 0 (no sub-stepping),
    mg_coarsest_sweeps 8, mg_band_sweeps 0, mg_transfer 1 (constant),
    mg_coarse_weight 1.9, mg_smooth_coarse 0, tape_fractions 0,
-   mg_persistent 0. */
+   mg_persistent 0, residual_fp64 0. */
 int nf_config_default(nf_config *cfg);
 
 /* Create a context on cfg->device. *out receives the handle. */

@@ -1715,13 +1715,13 @@ static inline unsigned gs_blocks(int64_t n) {
 
 template <class S, class T, class V>
 void launch_residual_outer(const Launch &L, const LevelView<T> &lv, const S *b,
-                           const S *x, V *rin, double scale, int es,
+                           const S *x, V *rin, double scale, int es, bool split,
                            const RedScratch &rs, double *norm2) {
   ProfScope _ps(L, NF_K_RESIDUAL64);
   if constexpr (sizeof(S) == 8 && sizeof(T) == 4 && sizeof(V) == 4) {
     // split arithmetic needs c = 1 and the scale of rin in float range
     const double rscale = std::ldexp(scale, -es);
-    if (lv.c == 1.0 && rscale >= 0x1p-120 && rscale <= 0x1p120) {
+    if (split && lv.c == 1.0 && rscale >= 0x1p-120 && rscale <= 0x1p120) {
       launch_pdl(k_residual_outer_df, kRedBlocks, kBlock, 0, L.s, lv, b, x, rin, es,
                  (float)rscale, scale, rs, norm2);
       ++*L.counter;
@@ -2002,9 +2002,9 @@ template void launch_mg_coarsen<float, __nv_bfloat16>(const Launch &, const Leve
 template void launch_mg_coarsen<__nv_bfloat16, __nv_bfloat16>(const Launch &, const LevelView<__nv_bfloat16> &, int, int, int, __nv_bfloat16 *, __nv_bfloat16 *, __nv_bfloat16 *);
 template void launch_mg_coarsen<double, double>(const Launch &, const LevelView<double> &, int, int, int, double *, double *, double *);
 
-template void launch_residual_outer<double, float, float>(const Launch &, const LevelView<float> &, const double *, const double *, float *, double, int, const RedScratch &, double *);
-template void launch_residual_outer<float, float, float>(const Launch &, const LevelView<float> &, const float *, const float *, float *, double, int, const RedScratch &, double *);
-template void launch_residual_outer<double, double, double>(const Launch &, const LevelView<double> &, const double *, const double *, double *, double, int, const RedScratch &, double *);
+template void launch_residual_outer<double, float, float>(const Launch &, const LevelView<float> &, const double *, const double *, float *, double, int, bool, const RedScratch &, double *);
+template void launch_residual_outer<float, float, float>(const Launch &, const LevelView<float> &, const float *, const float *, float *, double, int, bool, const RedScratch &, double *);
+template void launch_residual_outer<double, double, double>(const Launch &, const LevelView<double> &, const double *, const double *, double *, double, int, bool, const RedScratch &, double *);
 template void launch_axpy_outer<double, float>(const Launch &, int64_t, double *, const float *, double);
 template void launch_axpy_outer<float, float>(const Launch &, int64_t, float *, const float *, double);
 template void launch_axpy_outer<double, double>(const Launch &, int64_t, double *, const double *, double);

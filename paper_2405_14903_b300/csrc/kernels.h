@@ -85,11 +85,12 @@ void launch_adj_face(const Launch &L, const GridDev &g, const SceneDev &s,
 // written as scale * r converted to V into rin, and ||r||^2 (unscaled).
 // scale is a power of two that brings rin to unit size, so that the V-typed
 // inner solve neither underflows nor overflows; 2^es is a power of two that
-// brings b to unit size (used by the FP64-free MIXED variant).
+// brings b to unit size (used by the split-float MIXED variant, taken when
+// `split` and S = double, T = V = float).
 template <class S, class T, class V>
 void launch_residual_outer(const Launch &L, const LevelView<T> &lv,
                            const S *b, const S *x, V *rin, double scale, int es,
-                           const RedScratch &rs, double *norm2);
+                           bool split, const RedScratch &rs, double *norm2);
 // x += inv * e (V -> S); inv undoes the scale of the inner system.
 template <class S, class V>
 void launch_axpy_outer(const Launch &L, int64_t n, S *x, const V *e, double inv);

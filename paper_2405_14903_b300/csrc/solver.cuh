@@ -292,8 +292,8 @@ class Solver {
 
   double residual(const S *b, const S *x, double scale) {
     Launch L = ctx_->launch();
-    launch_residual_outer<S, T, V>(L, view0(), b, x, (V *)rin_, scale, es_, ctx_->rs,
-                                   (double *)norm2_);
+    launch_residual_outer<S, T, V>(L, view0(), b, x, (V *)rin_, scale, es_,
+                                   cfg_.residual_fp64 == 0, ctx_->rs, (double *)norm2_);
     return ctx_->read_double((double *)norm2_);
   }
 

@@ -294,7 +294,9 @@ def test_hbm_budget_refuses_admission(nf):
     dict(mg_transfer="constant", mg_coarse_weight=1.0, mg_smooth=1),
     dict(mg_transfer="constant", mg_coarse_weight=1.8, mg_coarsest_sweeps=2),
     dict(mg_smooth=2, mg_smooth_coarse=1),
-], ids=["trilinear", "trilinear_band", "constant_unweighted", "constant_1.8", "coarse_nu1"])
+    dict(residual_fp64=True),
+], ids=["trilinear", "trilinear_band", "constant_unweighted", "constant_1.8", "coarse_nu1",
+        "residual_fp64"])
 def test_multigrid_variants_match_oracle(nf, prec, variant):
     # the preconditioner changes the iterations, never the solution
     cfg, Jo, gtho, info = oracle_rollout("chamber_sub")
