@@ -123,7 +123,8 @@ __device__ __forceinline__ void rweights(int I, int n, float w[4]) {
 // the mean of the eight children: with that pair the coarse operator built
 // from the mean sub-face fractions and c / 2 is exactly the Galerkin
 // operator R A P, so the coarse correction is an A-orthogonal projection).
-constexpr int kTransferTrilinear = 0, kTransferConstant = 1;
+[[maybe_unused]] constexpr int kTransferTrilinear = 0;
+constexpr int kTransferConstant = 1;
 
 template <class V>
 __device__ __forceinline__ V restrict_cell(int fnx, int fny, int fnz, int cnx,
@@ -233,8 +234,7 @@ __device__ __forceinline__ void pdl_wait() {
 // instead of one (the compiler may not move a load above a store through a
 // possibly aliasing pointer). Per-thread accumulation still runs over cells
 // in increasing order, so reductions are unchanged.
-constexpr int kIlpStream = 4;   // streaming vector kernels
-constexpr int kIlpStencil = 1;  // 7-point stencil kernels (one cell: registers)
+constexpr int kIlpStream = 4;   // streaming vector kernels (stencils: one cell per step)
 
 // The 13 operands of one cell's 7-point operator: the six face fractions,
 // the six neighbour values (0 outside the grid) and the centre value.
