@@ -72,6 +72,8 @@ def parse():
                     help="1: the tape keeps each step's fractions (no re-rasterising)")
     ap.add_argument("--coarse-weight", type=float, default=1.9,
                     help="scale of the coarse-grid correction")
+    ap.add_argument("--mg-cluster", type=int, default=0,
+                    help="1: coarse levels above an 8^3 local chain on one thread-block cluster")
     ap.add_argument("--residual-fp64", type=int, default=0,
                     help="1: MIXED refinement residual in FP64 arithmetic (0: split-float)")
     ap.add_argument("--mg-persistent", type=int, default=0,
@@ -206,6 +208,7 @@ def run_ours(args, rank, world, local_rank):
                     mg_transfer=args.mg_transfer, mg_coarse_weight=args.coarse_weight,
                     mg_smooth_coarse=args.mg_smooth_coarse, tape_fractions=bool(args.tape_fractions),
                     mg_persistent=bool(args.mg_persistent),
+                    mg_cluster=bool(args.mg_cluster),
                     residual_fp64=bool(args.residual_fp64), device=local_rank)
     ep = ctx.episode(cfg["grid"], cfg["scene"])
     u0 = [torch.zeros(s, dtype=torch.float32, device=dev) for s in ep.face_shapes]
@@ -285,6 +288,7 @@ def run_ours(args, rank, world, local_rank):
                            mg_smooth_coarse=args.mg_smooth_coarse,
                            tape_fractions=bool(args.tape_fractions),
                            mg_persistent=bool(args.mg_persistent),
+                           mg_cluster=bool(args.mg_cluster),
                            residual_fp64=bool(args.residual_fp64),
                            l2="inputs larger than L2 (episode state and tape > 1 GB)",
                            parallelism=f"replicas x{world}"),

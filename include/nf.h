@@ -124,6 +124,16 @@ typedef struct nf_config {
                              the solver's device-side CG loop these launches
                              cost no more than the cooperative kernel's grid
                              barriers). Same arithmetic either way           */
+  int mg_cluster;         /* 1: the coarse levels just above an 8^3-or-smaller
+                             local chain (planes splitting evenly over 8
+                             CTAs, FP32 data, constant transfer; 32^3 and
+                             16^3 at 128^3) run as z-slabs on one 8-CTA
+                             thread-block cluster with the chain on its CTA
+                             0 (distributed shared memory, cluster barriers);
+                             0: one launch per phase (inside the device-side
+                             CG loop these cost about as much, and the local
+                             chain's serial part dominates either way).
+                             Same arithmetic                                  */
   int residual_fp64;      /* MIXED refinement residual r = b - A x (x, b FP64):
                              1: FP64 arithmetic; 0: split-float arithmetic
                              (each FP64 value as a float pair, error-free
@@ -169,7 +179,7 @@ typedef struct nf_step_stats {
    checkpoint_every 10, no budget, cfl_max 0 (no sub-stepping),
    mg_coarsest_sweeps 8, mg_band_sweeps 0, mg_transfer 1 (constant),
    mg_coarse_weight 1.9, mg_smooth_coarse 0, tape_fractions 0,
-   mg_persistent 0, residual_fp64 0. */
+   mg_persistent 0, mg_cluster 0, residual_fp64 0. */
 int nf_config_default(nf_config *cfg);
 
 /* Create a context on cfg->device. *out receives the handle. */

@@ -41,7 +41,7 @@ class Config(C.Structure):
                 ("mg_band_sweeps", C.c_int), ("mg_transfer", C.c_int),
                 ("mg_coarse_weight", C.c_double), ("mg_smooth_coarse", C.c_int),
                 ("tape_fractions", C.c_int), ("mg_persistent", C.c_int),
-                ("residual_fp64", C.c_int)]
+                ("mg_cluster", C.c_int), ("residual_fp64", C.c_int)]
 
 
 class Grid(C.Structure):

@@ -136,7 +136,7 @@ def _config(precision="mixed", solver="mgpcg", tol=1e-6, max_iters=500,
             checkpoint_every=10, hbm_budget=0, cfl_max=0.0, mg_coarsest_sweeps=8,
             mg_band_sweeps=0, mg_transfer="constant", mg_coarse_weight=1.9,
             mg_smooth_coarse=0, tape_fractions=False, mg_persistent=False,
-            residual_fp64=False, device=0, stream=0):
+            mg_cluster=False, residual_fp64=False, device=0, stream=0):
     """An ``nf_config`` from keyword arguments (defaults of nf_config_default)."""
     cfg = L.Config()
     _check(lib.nf_config_default(C.byref(cfg)))
@@ -160,6 +160,7 @@ def _config(precision="mixed", solver="mgpcg", tol=1e-6, max_iters=500,
     cfg.mg_smooth_coarse = int(mg_smooth_coarse)
     cfg.tape_fractions = int(bool(tape_fractions))
     cfg.mg_persistent = int(bool(mg_persistent))
+    cfg.mg_cluster = int(bool(mg_cluster))
     cfg.residual_fp64 = int(bool(residual_fp64))
     return cfg
 

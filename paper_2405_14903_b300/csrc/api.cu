@@ -203,6 +203,7 @@ int nf_config_default(nf_config *cfg) {
   cfg->mg_smooth_coarse = 0;
   cfg->tape_fractions = 0;
   cfg->mg_persistent = 0;
+  cfg->mg_cluster = 0;
   cfg->residual_fp64 = 0;
   return NF_OK;
 }
@@ -239,7 +240,8 @@ int nf_create(nf_ctx **out, const nf_config *cfg) {
       !(cfg->mg_coarse_weight >= 0.0 && cfg->mg_coarse_weight < 2.0) ||
       cfg->mg_smooth_coarse < 0 || (cfg->tape_fractions != 0 && cfg->tape_fractions != 1) ||
       (cfg->mg_persistent != 0 && cfg->mg_persistent != 1) ||
-      (cfg->residual_fp64 != 0 && cfg->residual_fp64 != 1)) {
+      (cfg->residual_fp64 != 0 && cfg->residual_fp64 != 1) ||
+      (cfg->mg_cluster != 0 && cfg->mg_cluster != 1)) {
     set_error("nf_create: invalid configuration");
     return NF_E_INVALID;
   }

@@ -7,6 +7,8 @@
 // c_l = dt / (rho dx_l)).
 #include <cmath>
 
+#include <cooperative_groups.h>
+
 #include "kernels.h"
 #include "util.h"
 
@@ -1440,6 +1442,9 @@ __device__ void chain_body(const CoarseChain<V, TA> &ch, unsigned char *smem) {
         const unsigned cnt = seg_end[sg] - (sg ? seg_end[sg - 1] : 0u);
         tx += bulk_bytes(smem + seg_dst[sg], seg_src[sg], cnt * (unsigned)sizeof(TA));
       }
+      // b may have been written by other CTAs of a cluster (generic stores
+      // made visible by a cluster barrier): order them before the copies
+      asm volatile("fence.proxy.async.global;" ::: "memory");
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(tx)
                    : "memory");
       auto issue = [&](void *dst, const void *src, unsigned bytes) {
@@ -1584,6 +1589,284 @@ k_mg_chain_smem(CoarseChain<V, TA> ch, const CGState *st) {
   if (stopped(st)) return;
   extern __shared__ __align__(16) unsigned char smem[];
   chain_body<V, TA>(ch, smem);
+}
+
+
+// --------------------------------------------- coarse levels on a cluster ---
+// The levels just above the local chain (at 128^3: 32^3 and 16^3) split into
+// z-slabs over the kClusterCtas CTAs of one thread-block cluster: each CTA
+// keeps its slab's x, b and fractions (and, for levels that the per-launch
+// path sweeps inside the chain, the inverse diagonal) in shared memory,
+// reads the x planes just across its slab boundaries from its neighbours'
+// shared memory, and the phases are separated by the cluster's hardware
+// barrier instead of kernel launches. Slabs of consecutive levels line up
+// (an even number of planes per CTA), so restriction outputs and
+// prolongation parents stay in the CTA. CTA 0 runs the local chain between
+// the down and the up sweeps. Every CTA passes the same barriers in the same
+// order (the only early exit, the stop flag, is read before the first one
+// and is the same for all), so no CTA can be left waiting. Per cell the
+// arithmetic is the per-launch path's: division for the levels it sweeps as
+// grid kernels, the inverse diagonal for those it sweeps in the chain, and
+// the prolongation as an explicit pass that stores the values the folded
+// sweep forms on the fly.
+namespace cgr = cooperative_groups;
+
+template <class V, class TA>
+struct Slab {
+  int nx, ny, nz, P, z0;
+  double c;
+  V *x, *b, *dinv;           // dinv null: sweep by division
+  const TA *ax, *ay, *az;    // faces of the slab's cells (az: P + 1 planes)
+  const V *xdn, *xup;        // x of the CTAs below and above (null at the ends)
+};
+
+template <class V, class TA>
+__device__ __forceinline__ void slab_gather(Nb7<V> &g, const Slab<V, TA> &S, int i, int j,
+                                            int kk, int c) {
+  const int row = kk * S.ny + j, nx = S.nx, nxy = S.nx * S.ny, k = S.z0 + kk;
+  g.xm = (V)ld(S.ax + c + row);
+  g.xp = (V)ld(S.ax + c + row + 1);
+  g.ym = (V)ld(S.ay + c + kk * nx);
+  g.yp = (V)ld(S.ay + c + kk * nx + nx);
+  g.zm = (V)ld(S.az + c);
+  g.zp = (V)ld(S.az + c + nxy);
+  g.vxm = i > 0 ? S.x[c - 1] : V(0);
+  g.vxp = i < nx - 1 ? S.x[c + 1] : V(0);
+  g.vym = j > 0 ? S.x[c - nx] : V(0);
+  g.vyp = j < S.ny - 1 ? S.x[c + nx] : V(0);
+  g.vzm = k > 0 ? (kk > 0 ? S.x[c - nxy] : S.xdn[c + (S.P - 1) * nxy]) : V(0);
+  g.vzp = k < S.nz - 1 ? (kk < S.P - 1 ? S.x[c + nxy] : S.xup[c - (S.P - 1) * nxy]) : V(0);
+  g.vc = S.x[c];
+}
+
+// Half sweep of colour `color` over the slab (zero: x = 0 before it).
+template <class V, class TA, bool ZERO>
+__device__ void slab_sweep(const Slab<V, TA> &S, int color) {
+  const int hx = S.nx >> 1;
+  const int n = S.P * S.ny * hx;
+  const V cc = V(S.c);
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const int row = t / hx, m = t - row * hx;
+    const int kk = row / S.ny, j = row - kk * S.ny;
+    const int i = 2 * m + ((j + S.z0 + kk + color) & 1);
+    const int c = row * S.nx + i;
+    V v;
+    if (S.dinv) {
+      if (ZERO) {
+        v = S.b[c] * S.dinv[c];
+      } else {
+        Nb7<V> g;
+        slab_gather(g, S, i, j, kk, c);
+        v = (S.b[c] + cc * g.nb()) * S.dinv[c];
+      }
+    } else if (ZERO) {
+      const int nx = S.nx, nxy = S.nx * S.ny;
+      const V dg = (V)ld(S.ax + c + row) + (V)ld(S.ax + c + row + 1) +
+                   (V)ld(S.ay + c + kk * nx) + (V)ld(S.ay + c + kk * nx + nx) +
+                   (V)ld(S.az + c) + (V)ld(S.az + c + nxy);
+      v = dg > V(0) ? S.b[c] / (cc * dg) : V(0);
+    } else {
+      Nb7<V> g;
+      slab_gather(g, S, i, j, kk, c);
+      const V dg = g.diag();
+      v = dg > V(0) ? (S.b[c] + cc * g.nb()) / (cc * dg) : V(0);
+    }
+    S.x[c] = v;
+  }
+}
+
+// Restriction of the slab's residual (four even children, as
+// resrestrict_cell) into the coarse slab: bc indexed locally, or globally
+// (the level below is the local chain's) when `global`.
+template <class V, class TA>
+__device__ void slab_resrestrict(const Slab<V, TA> &F, V *bc, bool global, float pn) {
+  const int cnx = F.nx >> 1, cny = F.ny >> 1, cP = F.P >> 1, cz0 = F.z0 >> 1;
+  const int n = cP * cny * cnx;
+  const V cc = V(F.c);
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const int q = t / cnx, I = t - q * cnx;
+    const int KK = q / cny, J = q - KK * cny;
+    V acc = V(0);
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch) {
+      const int a = (ch == 1 || ch == 2), bb = (ch == 1 || ch == 3), cz = (ch >= 2);
+      const int i = 2 * I + a, j = 2 * J + bb, kk = 2 * KK + cz;
+      const int c = (kk * F.ny + j) * F.nx + i;
+      Nb7<V> g;
+      slab_gather(g, F, i, j, kk, c);
+      const V dg = g.diag();
+      if (dg > V(0)) acc += F.b[c] - cc * (dg * g.vc - g.nb());
+    }
+    const int out = global ? ((cz0 + KK) * cny + J) * cnx + I : t;
+    bc[out] = V(0.125) * V(pn) * acc;
+  }
+}
+
+// x += w x_c(parent) on the slab's active cells; the parents are the coarse
+// slab (local indices) or the local chain's first level (global indices).
+template <class V, class TA>
+__device__ void slab_prolong(const Slab<V, TA> &S, const V *xc, bool global, V w) {
+  const int cnx = S.nx >> 1, cny = S.ny >> 1;
+  const int n = S.P * S.ny * S.nx;
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    const int row = c / S.nx, i = c - row * S.nx;
+    const int kk = row / S.ny, j = row - kk * S.ny;
+    const int nx = S.nx, nxy = S.nx * S.ny;
+    const float dg = (float)ld(S.ax + c + row) + (float)ld(S.ax + c + row + 1) +
+                     (float)ld(S.ay + c + kk * nx) + (float)ld(S.ay + c + kk * nx + nx) +
+                     (float)ld(S.az + c) + (float)ld(S.az + c + nxy);
+    if (!(dg > 0.f)) continue;
+    const int K = global ? (S.z0 + kk) >> 1 : kk >> 1;
+    S.x[c] += xc[(K * cny + (j >> 1)) * cnx + (i >> 1)] * w;
+  }
+}
+
+template <class V, class TA>
+__global__ void __launch_bounds__(1024, 1)
+k_mg_cluster(ClusterSpan<V, TA> m, CoarseChain<V, TA> ch, const CGState *st) {
+  if (stopped(st)) return;  // the same value in every CTA: no barrier is passed
+  cgr::cluster_group cl = cgr::this_cluster();
+  const int r = (int)cl.block_rank();
+  extern __shared__ __align__(16) unsigned char smem[];
+  auto slab = [&](int l) {
+    const LevelView<TA> &g = m.lv[l];
+    Slab<V, TA> S;
+    S.nx = g.nx;
+    S.ny = g.ny;
+    S.nz = g.nz;
+    S.P = g.nz / kClusterCtas;
+    S.z0 = r * S.P;
+    S.c = g.c;
+    S.x = (V *)(smem + m.off[l][0]);
+    S.b = (V *)(smem + m.off[l][1]);
+    S.dinv = m.use_dinv[l] ? (V *)(smem + m.off[l][5]) : nullptr;
+    S.ax = (const TA *)(smem + m.off[l][2]);
+    S.ay = (const TA *)(smem + m.off[l][3]);
+    S.az = (const TA *)(smem + m.off[l][4]);
+    S.xdn = r > 0 ? cl.map_shared_rank(S.x, r - 1) : nullptr;
+    S.xup = r < kClusterCtas - 1 ? cl.map_shared_rank(S.x, r + 1) : nullptr;
+    return S;
+  };
+  // the slabs' fractions (and b of the first level) from global memory:
+  // thread 0 issues bulk copies of the contiguous slab arrays on one
+  // mbarrier, the other threads copy any part a bulk copy cannot take
+  {
+    __shared__ __align__(8) unsigned long long mbar;
+    const unsigned mb = (unsigned)__cvta_generic_to_shared(&mbar);
+    struct Seg {
+      void *dst;
+      const void *src;
+      unsigned bytes;
+    };
+    Seg seg[3 * kMaxLevels + 1];
+    int ns = 0;
+    for (int l = m.lo; l < m.hi; ++l) {
+      const LevelView<TA> &g = m.lv[l];
+      const int P = g.nz / kClusterCtas, z0 = r * P;
+      const size_t nxy = (size_t)g.nx * g.ny;
+      seg[ns++] = {smem + m.off[l][2], g.ax + (size_t)z0 * g.ny * (g.nx + 1),
+                   (unsigned)(P * g.ny * (g.nx + 1) * sizeof(TA))};
+      seg[ns++] = {smem + m.off[l][3], g.ay + (size_t)z0 * (g.ny + 1) * g.nx,
+                   (unsigned)(P * (g.ny + 1) * g.nx * sizeof(TA))};
+      seg[ns++] = {smem + m.off[l][4], g.az + (size_t)z0 * nxy,
+                   (unsigned)((P + 1) * nxy * sizeof(TA))};
+    }
+    {
+      const LevelView<TA> &g = m.lv[m.lo];
+      const size_t n = (size_t)(g.nz / kClusterCtas) * g.nx * g.ny;
+      seg[ns++] = {smem + m.off[m.lo][1], m.b_lo + (size_t)r * n, (unsigned)(n * sizeof(V))};
+    }
+    // bytes a bulk copy takes: both addresses 16-byte aligned, a multiple of 16
+    auto bulk = [](const Seg &q) {
+      return (((uintptr_t)q.src | (uintptr_t)__cvta_generic_to_shared(q.dst)) & 15u)
+                 ? 0u
+                 : (q.bytes & ~15u);
+    };
+    if (threadIdx.x == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned tx = 0;
+      for (int q = 0; q < ns; ++q) tx += bulk(seg[q]);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(tx)
+                   : "memory");
+      for (int q = 0; q < ns; ++q) {
+        const unsigned nb = bulk(seg[q]);
+        if (nb == 0) continue;
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+            "[%3];" ::"r"((unsigned)__cvta_generic_to_shared(seg[q].dst)),
+            "l"(seg[q].src), "r"(nb), "r"(mb)
+            : "memory");
+      }
+    }
+    for (int q = 0; q < ns; ++q) {
+      const unsigned done = bulk(seg[q]);
+      for (unsigned t = done + threadIdx.x; t < seg[q].bytes; t += blockDim.x)
+        ((unsigned char *)seg[q].dst)[t] = ((const unsigned char *)seg[q].src)[t];
+    }
+    // an expired wait (error word set, the solve reports NF_E_TIMEOUT) still
+    // passes every barrier below, after the copies had a second bound to land
+    if (!mbar_wait(mb, 0, ch.err)) mbar_wait(mb, 0, nullptr);
+  }
+  __syncthreads();
+  // inverse diagonals (the chain's formula) where the per-launch path uses them
+  for (int l = m.lo; l < m.hi; ++l) {
+    if (!m.use_dinv[l]) continue;
+    const Slab<V, TA> S = slab(l);
+    const LevelView<TA> lvs{S.nx, S.ny, S.P, S.c, S.ax, S.ay, S.az};
+    const V cc = V(S.c);
+    const int n = S.P * S.ny * S.nx;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+      const int row = c / S.nx, i = c - row * S.nx;
+      const int kk = row / S.ny, j = row - kk * S.ny;
+      const V dg = six<V>(lvs, i, j, kk).diag();
+      S.dinv[c] = dg > V(0) ? V(1) / (cc * dg) : V(0);
+    }
+  }
+  __syncthreads();
+  for (int l = m.lo; l < m.hi; ++l) {
+    const Slab<V, TA> S = slab(l);
+    for (int s = 0; s < m.smooth; ++s) {
+      if (s == 0)
+        slab_sweep<V, TA, true>(S, 0);
+      else
+        slab_sweep<V, TA, false>(S, 0);
+      cl.sync();
+      slab_sweep<V, TA, false>(S, 1);
+      cl.sync();
+    }
+    if (l + 1 < m.hi)
+      slab_resrestrict<V, TA>(S, (V *)(smem + m.off[l + 1][1]), false, m.w);
+    else
+      slab_resrestrict<V, TA>(S, m.b_hi, true, m.w);
+    cl.sync();
+  }
+  if (r == 0) chain_body<V, TA>(ch, smem + m.chain_off);
+  cl.sync();
+  for (int l = m.hi - 1; l >= m.lo; --l) {
+    const Slab<V, TA> S = slab(l);
+    if (l + 1 < m.hi)
+      slab_prolong<V, TA>(S, (const V *)(smem + m.off[l + 1][0]), false, V(m.w));
+    else
+      slab_prolong<V, TA>(S, m.x_hi, true, V(m.w));
+    cl.sync();
+    for (int s = 0; s < m.smooth; ++s) {
+      slab_sweep<V, TA, false>(S, 1);
+      cl.sync();
+      slab_sweep<V, TA, false>(S, 0);
+      cl.sync();
+    }
+  }
+  {
+    const LevelView<TA> &g = m.lv[m.lo];
+    const int n = (g.nz / kClusterCtas) * g.nx * g.ny;
+    const V *src = (const V *)(smem + m.off[m.lo][0]);
+    V *dst = m.x_lo + (size_t)r * n;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) dst[t] = src[t];
+  }
 }
 
 // ------------------------------------------------ persistent mid levels ---
@@ -1909,6 +2192,50 @@ int prepare_mg_mid(int smem_limit, int smem) {
   return coop ? per_sm * sms : 0;
 }
 template <class V, class TA>
+bool prepare_mg_cluster(int smem_limit, int smem) {
+  if (allow_dynamic_smem(k_mg_cluster<V, TA>, smem_limit) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(kClusterCtas);
+  cfg.blockDim = dim3(1024);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = kClusterCtas;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, (void *)k_mg_cluster<V, TA>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return clusters >= 1;
+}
+template <class V, class TA>
+int launch_mg_cluster(const Launch &L, const ClusterSpan<V, TA> &m,
+                      const CoarseChain<V, TA> &ch, const CGState *st, int smem) {
+  ProfScope _ps(L, NF_K_MG_CHAIN);
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(kClusterCtas);
+  cfg.blockDim = dim3(1024);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = L.s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = kClusterCtas;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_mg_cluster<V, TA>, m, ch, st);
+  ++*L.counter;
+  return e == cudaSuccess ? NF_OK : cuda_fail(e, "cluster launch (k_mg_cluster)");
+}
+template <class V, class TA>
 int launch_mg_mid(const Launch &L, const MidSpan<V, TA> &m,
                   const CoarseChain<V, TA> &ch, const CGState *st, int blocks) {
   ProfScope _ps(L, NF_K_MG_MID);
@@ -1976,6 +2303,11 @@ void launch_mg_coarse_chain(const Launch &L, const CoarseChain<V, TA> &ch,
   template size_t mg_chain_smem_bytes<V, TA>(const CoarseChain<V, TA> &);    \
   template int prepare_mg_chain<V, TA>(int);                                 \
   template int prepare_mg_mid<V, TA>(int, int);                              \
+  template bool prepare_mg_cluster<V, TA>(int, int);                         \
+  template int launch_mg_cluster<V, TA>(const Launch &,                      \
+                                        const ClusterSpan<V, TA> &,           \
+                                        const CoarseChain<V, TA> &,           \
+                                        const CGState *, int);                \
   template int launch_mg_mid<V, TA>(const Launch &, const MidSpan<V, TA> &,  \
                                     const CoarseChain<V, TA> &,               \
                                     const CGState *, int);

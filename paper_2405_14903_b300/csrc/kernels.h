@@ -227,6 +227,35 @@ struct MidSpan {
   int *err;           // set to 1 when a barrier wait expired
   int stall;          // test hook: every barrier waits for one block more
 };
+// Levels lo .. hi-1 of a V-cycle split into z-slabs over the CTAs of one
+// thread-block cluster (k_mg_cluster; each level's nz a multiple of
+// 2 kClusterCtas, FP32 data, constant transfer), level hi and below (the
+// local chain) on CTA 0. x of level lo is written to x_lo at the end; b of
+// level lo is read from b_lo.
+constexpr int kClusterCtas = 8;
+template <class V, class TA>
+struct ClusterSpan {
+  int lo, hi;
+  int smooth;         // sweeps per level
+  float w;            // uniform normaliser of the constant transfer
+  LevelView<TA> lv[kMaxLevels];
+  int use_dinv[kMaxLevels];  // 1: sweep with the inverse diagonal (as in the chain)
+  unsigned off[kMaxLevels][6];  // per-CTA shared memory: x, b, ax, ay, az, dinv
+  unsigned chain_off;           // CTA 0's chain region
+  V *x_lo;
+  const V *b_lo;
+  V *b_hi;            // the local chain's b (global), written by the restriction
+  const V *x_hi;      // the local chain's x (global), read by the prolongation
+};
+// Launches k_mg_cluster (one cluster of kClusterCtas CTAs of 1024 threads,
+// `smem` bytes of dynamic shared memory each); NF_OK or NF_E_CUDA.
+template <class V, class TA>
+int launch_mg_cluster(const Launch &L, const ClusterSpan<V, TA> &m,
+                      const CoarseChain<V, TA> &ch, const CGState *st, int smem);
+// Allows k_mg_cluster `smem` bytes and returns whether one cluster fits.
+template <class V, class TA>
+bool prepare_mg_cluster(int smem_limit, int smem);
+
 // Launches k_mg_mid cooperatively on `blocks` blocks of 1024 threads with
 // the chain's shared memory; returns NF_OK or NF_E_CUDA.
 template <class V, class TA>

@@ -141,6 +141,48 @@ class Solver {
           }
         }
       }
+      // otherwise the levels just above an 8^3-or-smaller local chain whose
+      // planes split evenly (an even number per CTA) run on one thread-block
+      // cluster, the local chain on its CTA 0
+      if (cfg_.mg_cluster && !mid_lo_ && sizeof(V) == 4 && cfg_.mg_transfer == 1 && nl > 2 &&
+          chain_smem_ > 0) {
+        int lo = -1, hi = -1;
+        for (int l = 1; l < nl - 1; ++l) {
+          const Level &L = levels_[l];
+          const int64_t nc = (int64_t)L.nx * L.ny * L.nz;
+          const bool ok = nc > 512 && nc <= kClusterCells && L.nz % (2 * kClusterCtas) == 0;
+          if (ok && lo < 0) lo = l;
+          if (lo >= 0) {
+            if (!ok) break;
+            hi = l + 1;
+          }
+        }
+        if (lo >= 1 && hi > lo && hi < nl) {
+          size_t o = 0;
+          auto take = [&o](size_t bytes) {
+            const size_t at = o;
+            o += (bytes + 15) & ~(size_t)15;
+            return (unsigned)at;
+          };
+          for (int l = lo; l < hi; ++l) {
+            const Level &L = levels_[l];
+            const size_t P = (size_t)L.nz / kClusterCtas, nxy = (size_t)L.nx * L.ny;
+            cl_off_[l][0] = take(P * nxy * sizeof(V));
+            cl_off_[l][1] = take(P * nxy * sizeof(V));
+            cl_off_[l][2] = take(P * L.ny * (L.nx + 1) * sizeof(TA));
+            cl_off_[l][3] = take(P * (L.ny + 1) * L.nx * sizeof(TA));
+            cl_off_[l][4] = take((P + 1) * nxy * sizeof(TA));
+            cl_off_[l][5] = l >= down ? take(P * nxy * sizeof(V)) : 0u;
+          }
+          cl_chain_off_ = (unsigned)o;
+          const size_t total = o + mg_chain_smem_bytes(chain(hi));
+          if (total + 1024 <= (size_t)limit && prepare_mg_cluster<V, TA>(limit, (int)total)) {
+            cl_lo_ = lo;
+            cl_hi_ = hi;
+            cl_smem_ = (int)total;
+          }
+        }
+      }
     }
     return NF_OK;
   }
@@ -262,6 +304,7 @@ class Solver {
   static constexpr int kMaxOuter = 12;
   static constexpr int kChainCells = 16 * 16 * 16;
   static constexpr int64_t kMidCells = 64 * 64 * 64;
+  static constexpr int64_t kClusterCells = 32 * 32 * 32;
   static constexpr int kBatch = 4;
   int coarsest_sweeps() const {
     return cfg_.mg_coarsest_sweeps > 0 ? cfg_.mg_coarsest_sweeps : 8;
@@ -348,6 +391,26 @@ class Solver {
     return ch;
   }
 
+  ClusterSpan<V, TA> cluster() const {
+    ClusterSpan<V, TA> m{};
+    m.lo = cl_lo_;
+    m.hi = cl_hi_;
+    m.smooth = nu_coarse();
+    m.w = coarse_w();
+    const int down = std::min(std::max(1, first_chain_), (int)levels_.size() - 1);
+    for (int l = cl_lo_; l <= cl_hi_; ++l) m.lv[l] = viewc(l);
+    for (int l = cl_lo_; l < cl_hi_; ++l) {
+      m.use_dinv[l] = l >= down ? 1 : 0;
+      for (int q = 0; q < 6; ++q) m.off[l][q] = cl_off_[l][q];
+    }
+    m.chain_off = cl_chain_off_;
+    m.x_lo = (V *)levels_[cl_lo_].x;
+    m.b_lo = (const V *)levels_[cl_lo_].b;
+    m.b_hi = (V *)levels_[cl_hi_].b;
+    m.x_hi = (const V *)levels_[cl_hi_].x;
+    return m;
+  }
+
   MidSpan<V, TA> mid(int lo, int hi) const {
     MidSpan<V, TA> m{};
     m.lo = lo;
@@ -397,7 +460,7 @@ class Solver {
     const int down = std::min(F, nl - 1);     // levels with a coarser level
     // levels [0, gl) as one launch per phase; [gl, down) and the chain in
     // one cooperative kernel when that is set up, else per phase too
-    const int gl = mid_lo_ > 0 ? mid_lo_ : down;
+    const int gl = mid_lo_ > 0 ? mid_lo_ : (cl_lo_ > 0 ? cl_lo_ : down);
     down_levels(0, gl, r, z, st);
     bool done = false;
     if (mid_lo_ > 0) {
@@ -406,6 +469,13 @@ class Solver {
       } else {  // no cooperative launch here: per-phase launches from now on
         cudaGetLastError();
         mid_lo_ = 0;
+      }
+    } else if (cl_lo_ > 0) {
+      if (launch_mg_cluster<V, TA>(L, cluster(), chain(cl_hi_), st, cl_smem_) == NF_OK) {
+        done = true;
+      } else {  // no cluster launch here: per-phase launches from now on
+        cudaGetLastError();
+        cl_lo_ = 0;
       }
     }
     if (!done) {
@@ -784,6 +854,10 @@ class Solver {
   bool mg_ = false;
   int first_chain_ = 0;
   int chain_smem_ = 0;  // dynamic shared memory of the chain kernel (0: global)
+  int cl_lo_ = 0, cl_hi_ = 0;  // levels on the thread-block cluster (0: none)
+  int cl_smem_ = 0;
+  unsigned cl_off_[kMaxLevels][6] = {};
+  unsigned cl_chain_off_ = 0;
   int mid_lo_ = 0;      // first level inside the cooperative kernel (0: none)
   int mid_blocks_ = 0;  // its grid
   void *bar_ = nullptr; // its barrier counter

@@ -399,3 +399,27 @@ def test_launch_paths_give_the_same_bits(nf, monkeypatch):
     assert sa["iters"] == sb["iters"] == sc["iters"] and sa["outer"] == sb["outer"] == sc["outer"]
     for x, y, z in zip(ua, ub, uc):
         assert np.array_equal(x, y) and np.array_equal(x, z)
+
+
+# ------------------------------------------------ cluster coarse levels ----
+# With mg_cluster, from 64^3 up the levels just above an 8^3 chain (32^3
+# and 16^3) run as z-slabs on one 8-CTA thread-block cluster. Per cell the
+# arithmetic is the per-launch path's, so a projection gives the same bits
+# and iterations either way.
+
+@pytest.mark.parametrize("n", [64, 128])
+def test_cluster_coarse_levels_give_the_per_launch_bits(nf, n):
+    cfg = I.config_chamber(n, steps=1, seed=0, duct_half_cells=max(2, n // 16))
+    out = {}
+    for cluster in (True, False):
+        ctx = make_ctx(nf, "mixed", cfg=cfg, mg_cluster=cluster, tol=1e-8)
+        ep = ctx.episode(cfg["grid"], cfg["scene"])
+        st = ep.set_velocity(device_u(cfg, torch.float32), project=True)
+        fst = ep.step(1)
+        out[cluster] = (st, fst, host(ep.velocity()))
+        ep.close()
+        ctx.close()
+    (s1, f1, u1), (s0, f0, u0) = out[True], out[False]
+    assert s1["iters"] == s0["iters"] and f1["iters"] == f0["iters"]
+    for a, b in zip(u1, u0):
+        assert np.array_equal(a, b)
