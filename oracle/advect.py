@@ -9,8 +9,12 @@ where ``u(x)`` interpolates each component on its own staggered lattice.
 Sample points are clamped to each lattice's box (periodic grids wrap).
 
 Viscosity (Sec. 2.3.1, Eq. viscosity_matrix; Appendix B, Eq. apply_force):
-explicit Euler with the 7-point Laplacian of each component on its own
-lattice. Only periodic grids are supported here (the Taylor-Green check).
+explicit Euler ``U^ = (I - nu dt / dx^2 G^T G) U~`` applied to each component
+on its own face lattice, where ``G`` takes the difference across every edge
+joining two neighbouring lattice points. On a periodic grid the edges wrap
+around; in a closed box the lattice ends at the walls and has no edge
+beyond them, so ``-G^T G`` is the lattice's graph Laplacian (no flux through
+its ends). ``G^T G`` is symmetric, so the adjoint is the same map.
 
 Adjoint (Sec. 2.3.2, Viscosity and Advection): the transpose of the
 linearisation, including the dependence of the interpolation weights on the
@@ -67,23 +71,32 @@ def advect_adjoint(g: Grid, U, gUt, order=2):
     return gU
 
 
-def _laplacian_periodic(u):
-    out = -6.0 * u
+def _gtg(u, periodic):
+    """``G^T G u`` on one component's lattice (array axes = lattice axes)."""
+    out = np.zeros_like(u)
     for ax in range(3):
-        out += np.roll(u, 1, axis=ax) + np.roll(u, -1, axis=ax)
+        if periodic:
+            e = np.roll(u, -1, axis=ax) - u          # edge (i, i+1), wrapping
+            out += np.roll(e, 1, axis=ax) - e        # G^T: +e at i+1, -e at i
+        else:
+            e = np.diff(u, axis=ax)                  # the n - 1 interior edges
+            lo = [slice(None)] * 3
+            hi = [slice(None)] * 3
+            lo[ax] = slice(0, -1)
+            hi[ax] = slice(1, None)
+            out[tuple(lo)] -= e
+            out[tuple(hi)] += e
     return out
 
 
 def viscosity(g: Grid, Ut):
-    """``U^ = U~ + nu dt / dx^2 L U~`` (component-wise, periodic grids)."""
+    """``U^ = (I - nu dt / dx^2 G^T G) U~``, component by component."""
     if g.nu == 0.0:
         return [u.copy() for u in Ut]
-    if not g.periodic:
-        raise NotImplementedError("explicit viscosity is implemented for periodic grids")
     k = g.nu * g.dt / (g.dx * g.dx)
-    return [u + k * _laplacian_periodic(u) for u in Ut]
+    return [u - k * _gtg(u, g.periodic) for u in Ut]
 
 
 def viscosity_adjoint(g: Grid, gUh):
-    """The periodic Laplacian is symmetric, so the adjoint is the same map."""
+    """``G^T G`` is symmetric, so the adjoint is the same map."""
     return viscosity(g, gUh)
