@@ -80,6 +80,9 @@ def parse():
                     help="1: coarse levels <= 64^3 and the chain in one cooperative kernel")
     ap.add_argument("--mg-coarsest", type=int, default=4,
                     help="stop coarsening at this many cells per edge")
+    ap.add_argument("--nu", type=float, default=0.0,
+                    help="kinematic viscosity of the chamber (0: the inviscid metric); "
+                         "nu > 0 adds explicit viscosity to every step and its adjoint")
     ap.add_argument("--workload", default="rollout", choices=["rollout", "serving", "precision"],
                     help="rollout: the chamber fwd+adjoint metric; serving: the episode mix")
     ap.add_argument("--serve-count", type=int, default=512, help="episodes in the serving mix")
@@ -175,6 +178,8 @@ def alg_bytes_per_cell(kclass, nu):
         "apply_dot": 4 + 3 * 4 + 4,            # d, three fraction arrays, q
         "cg_xr": 4 * 4 + 2 * 4,                # x, r, d, q read; x, r written
         "residual64": 8 + 8 + 3 * 4 + 8 + 4,   # b, x (FP64), fractions, r64, r32
+        # three face values per cell read once and written once (FP32)
+        "viscosity": 3 * (4 + 4),
     }.get(kclass)
 
 
@@ -194,6 +199,7 @@ def run_ours(args, rank, world, local_rank):
     dev = f"cuda:{local_rank}"
     n, T = args.n, args.rollout
     cfg = chamber(n, T, seed=rank)
+    cfg["grid"]["nu"] = float(args.nu)
     ncell = n ** 3
 
     def barrier():
@@ -260,6 +266,14 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize(dev)
     nl, kms = ctx.profile_read(roof_class)
     ctx.profile(None)
+    visc = None
+    if args.nu > 0:
+        # the viscosity kernel (forward and adjoint launches) over one more step
+        ctx.profile("viscosity")
+        one_step()
+        torch.cuda.synchronize(dev)
+        visc = ctx.profile_read("viscosity")
+        ctx.profile(None)
 
     t = torch.tensor([ms], dtype=torch.float64, device=dev)
     if world > 1:
@@ -273,7 +287,7 @@ def run_ours(args, rank, world, local_rank):
                scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
                config=dict(workload=f"pulsing chamber {n}^3, {T} steps dt=0.005, 16x16 outlet, "
                                     "outflow loss; forward rollout + full adjoint",
-                           grid=n, rollout_steps=T, checkpoint_every=10,
+                           grid=n, rollout_steps=T, checkpoint_every=10, nu=float(args.nu),
                            cfl_max=cfg["cfl_max"], substeps_executed=int(stats["fwd"]["steps"]),
                            precision="FP32 MGPCG (V-cycle, CG vectors; BF16 coarse-level "
                                      "fractions), FP32 per-thread dot partials summed in FP64, "
@@ -311,6 +325,17 @@ def run_ours(args, rank, world, local_rank):
                            launches=nl, avg_us=1e3 * avg_ms, alg_bytes_per_launch=per_launch,
                            timing="CUDA events around every launch of the kernel, over one "
                                   "step of the same workload run right after the timed region")
+    if visc is not None and visc[0]:
+        # faces of the three components: one read and one write of each
+        nfaces = 3 * (n + 1) * n * n
+        vb = 2 * 4 * nfaces
+        vms = visc[1] / visc[0]
+        va = vb / (vms / 1e3) / 1e9
+        out["viscosity_roofline"] = dict(
+            bound="hbm", kernel="viscosity", achieved=va, peak=peak, peak_source=src,
+            unit="GB/s", frac=va / peak, traffic=None, launches=visc[0], avg_us=1e3 * vms,
+            alg_bytes_per_launch=vb,
+            timing="CUDA events around every launch, over one step after the timed region")
     tot = sum(v[1] for v in shares.values()) or 1.0
     out["kernel_shares"] = {k: round(v[1] / tot, 4) for k, v in
                             sorted(shares.items(), key=lambda kv: -kv[1][1]) if v[1] > 0}

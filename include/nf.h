@@ -149,6 +149,15 @@ typedef struct nf_grid {
   double rho;             /* density (1 in every shipped scene)               */
   int outlet;             /* 0: closed box; 1: open patch on the high-x wall  */
   int outlet_j0, outlet_k0, outlet_w, outlet_h; /* patch cells in y and z   */
+  /* kinematic viscosity (>= 0; 0 = inviscid). With nu > 0 every step applies
+     explicit viscosity (Sec. 2.3.1, Eq. viscosity_matrix) between advection
+     and projection: U^ = (I - nu h / dx^2 G^T G) U~ for each component on
+     its own face lattice, G the difference across each edge between two
+     neighbouring lattice points inside the box (none past the walls), h the
+     step length. Explicit Euler is stable for nu h / dx^2 <= 1/6; larger
+     values are accepted and computed as written. Costs one extra face
+     field per episode and one stencil pass each way per step.            */
+  double nu;
 } nf_grid;
 
 typedef struct nf_scene {
@@ -198,7 +207,9 @@ int nf_synchronize(nf_ctx *ctx);
 /* ---------------------------------------------------------------- episode */
 
 /* Create an episode: a grid, a scene with parameters theta, zero velocity,
-   step counter 0. Admission: NF_E_OOM when its device state would exceed the
+   step counter 0. NF_E_INVALID for a grid with fewer than 4 cells on an
+   axis, dx, dt <= 0, nu < 0 or not finite, or an outlet patch off the
+   high-x wall. Admission: NF_E_OOM when its device state would exceed the
    context's HBM budget. Geometry is evaluated analytically at
    t_{n+1} = (n + 1) dt in every step (Sec. 2.3.1, Projection). */
 int nf_episode_create(nf_ctx *ctx, const nf_grid *g, const nf_scene *s,
@@ -222,7 +233,8 @@ int nf_set_velocity(nf_ctx *ctx, int64_t id, const void *const u[3],
 /* Advance nsteps time steps (or frames, when cfl_max > 0: each frame of dt
    is split into substeps by the CFL rule; the rule of Table 1's caption).
    One step of length h from t to t + h: rasterise alpha and u_s at t + h,
-   advect (Eq. advection_matrix), solve Eq. projection_matrix, apply the
+   advect (Eq. advection_matrix), apply viscosity when nu > 0 (Eq.
+   viscosity_matrix), solve Eq. projection_matrix, apply the
    blended update U = S (U^ - c G P) + (I - S) U_s with c = h / (rho dx).
    On fluid components that touch no open face the right-hand side is
    projected to zero mean and the pressure is returned with zero mean.
@@ -262,7 +274,8 @@ int nf_get_pressure(nf_ctx *ctx, int64_t id, void *p, int dtype, int mem);
 /* Face fractions alpha of the last step (3 face arrays). */
 int nf_get_fractions(nf_ctx *ctx, int64_t id, void *const a[3], int dtype,
                      int mem);
-/* Advected velocity U^ of the last step (3 face arrays). */
+/* Velocity U^ of the last step before projection: advected, then viscous
+   when nu > 0 (3 face arrays). */
 int nf_get_advected(nf_ctx *ctx, int64_t id, void *const u[3], int dtype,
                     int mem);
 /* Step counter n (the velocity is U^n). */
@@ -307,7 +320,8 @@ int nf_launch_count(nf_ctx *ctx, int64_t *count);
 #define NF_K_MG_SMOOTH0 22    /* finest level  */
 #define NF_K_GAUGE 23
 #define NF_K_MG_MID 24        /* coarse levels + chain, one cooperative kernel */
-#define NF_K_COUNT 25
+#define NF_K_VISCOSITY 25     /* explicit viscosity, forward and adjoint */
+#define NF_K_COUNT 26
 
 /* Start timing launches of kernel class `kclass` (NF_K_*), or of every class
    with kclass = -1; kclass = -2 stops. Resets the accumulated totals. */

@@ -27,7 +27,8 @@ CUDA_STREAM_LEGACY = 1   # cudaStreamLegacy: the legacy default stream
 KCLASS = ["rasterize", "advect", "rhs", "update", "loss", "adj_gp", "adj_face",
           "adj_advect", "residual64", "axpy64", "cg_init", "apply_dot", "cg_xr",
           "cg_rz", "cg_d", "mg_coarsen", "mg_smooth", "mg_residual", "mg_restrict",
-          "mg_prolong", "mg_chain", "cast", "mg_smooth0", "gauge", "mg_mid"]
+          "mg_prolong", "mg_chain", "cast", "mg_smooth0", "gauge", "mg_mid",
+          "viscosity"]
 
 
 class Config(C.Structure):
@@ -49,7 +50,7 @@ class Grid(C.Structure):
                 ("dx", C.c_double), ("dt", C.c_double), ("rho", C.c_double),
                 ("outlet", C.c_int), ("outlet_j0", C.c_int),
                 ("outlet_k0", C.c_int), ("outlet_w", C.c_int),
-                ("outlet_h", C.c_int)]
+                ("outlet_h", C.c_int), ("nu", C.c_double)]
 
 
 class Scene(C.Structure):

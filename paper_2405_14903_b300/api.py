@@ -52,8 +52,7 @@ def grid_struct(desc):
     g.dx, g.dt, g.rho = desc["dx"], desc["dt"], desc.get("rho", 1.0)
     if desc.get("periodic", False):
         raise ValueError("the CUDA path implements closed boxes (walls and an outlet patch)")
-    if desc.get("nu", 0.0):
-        raise ValueError("the CUDA path implements the inviscid step (nu = 0)")
+    g.nu = float(desc.get("nu", 0.0))
     o = desc.get("outlet")
     if o:
         if o["axis"] != 0 or o["side"] != 1:

@@ -2,6 +2,7 @@
 // and episode bookkeeping, HBM admission, kernel-class profiling and error
 // plumbing. No exception crosses the ABI; every entry point returns a status.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -323,6 +324,10 @@ int nf_episode_create(nf_ctx *ctx, const nf_grid *g, const nf_scene *s,
       max_faces > (int64_t)INT32_MAX) {
     set_error("nf_episode_create: grid must have >= 4 cells per axis, dx > 0, dt > 0 "
               "and fewer than 2^31 faces per component");
+    return NF_E_INVALID;
+  }
+  if (!(g->nu >= 0.0) || !std::isfinite(g->nu)) {
+    set_error("nf_episode_create: viscosity nu must be finite and >= 0");
     return NF_E_INVALID;
   }
   if (g->outlet && (g->outlet_j0 < 0 || g->outlet_k0 < 0 || g->outlet_w <= 0 ||

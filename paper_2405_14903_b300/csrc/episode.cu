@@ -191,6 +191,7 @@ class EpisodeImpl : public EpisodeBase {
     g.dt = gr.dt;
     g.rho = gr.rho > 0 ? gr.rho : 1.0;
     g.c = g.dt / (g.rho * g.dx);
+    g.nu = gr.nu;
     g.outlet = gr.outlet;
     g.oj0 = gr.outlet_j0;
     g.ok0 = gr.outlet_k0;
@@ -208,6 +209,7 @@ class EpisodeImpl : public EpisodeBase {
     CKS(faces(&gU_));
     CKS(faces(&gUb_));
     CKS(faces(&gUh_));
+    if (g_.nu > 0.0) CKS(faces(&Ut_));  // U~ before viscosity, dJ/dU~ after
     CKS(A_.get(&P_, ncell_ * sizeof(S)));
     CKS(A_.get(&b_, ncell_ * sizeof(S)));
     CKS(A_.get(&gP_, ncell_ * sizeof(S)));
@@ -588,7 +590,13 @@ class EpisodeImpl : public EpisodeBase {
         tapeA_ok_[m] = 1;
       }
     }
-    launch_advect<T>(L, g, cview(u_in), mut(uh), ctx_->cfg.advect_order);
+    if (Ut_) {
+      // U~ = B(U) U, then U^ = (I - nu h / dx^2 G^T G) U~ (Sec. 2.3.1)
+      launch_advect<T>(L, g, cview(u_in), mut(Ut_), ctx_->cfg.advect_order);
+      launch_viscosity<T>(L, g, cview(Ut_), mut(uh));
+    } else {
+      launch_advect<T>(L, g, cview(u_in), mut(uh), ctx_->cfg.advect_order);
+    }
     return project_faces(g, sd, uh, P, u_out, ss);
   }
 
@@ -685,7 +693,14 @@ class EpisodeImpl : public EpisodeBase {
     // graphs read alpha_, so they are copied back rather than pointed to)
     CKC(cudaMemcpyAsync(alpha_, segA_[k], nfaces_ * sizeof(T), cudaMemcpyDeviceToDevice, L.s));
     const int rc = adjoint_projection(g, sd, segUh_[k], segP_[k], gth, st, segFloat_[k] != 0);
-    launch_advect_adjoint<T>(L, g, cview(segU_[k]), cview(gUh_), mut(gUb_),
+    const T *gUt = gUh_;
+    if (Ut_) {
+      // dJ/dU~ = (I - nu h / dx^2 G^T G) dJ/dU^ (Sec. 2.3.2; the map is
+      // symmetric). Ut_ is free here: the recompute above is done with it.
+      launch_viscosity<T>(L, g, cview(gUh_), mut(Ut_));
+      gUt = Ut_;
+    }
+    launch_advect_adjoint<T>(L, g, cview(segU_[k]), cview(gUt), mut(gUb_),
                              ctx_->cfg.advect_order);
     std::swap(gU_, gUb_);
     n_rev_ = m;
@@ -702,6 +717,7 @@ class EpisodeImpl : public EpisodeBase {
   int64_t nfaces_ = 0, ncell_ = 0;
   T *U_ = nullptr, *Uh_ = nullptr, *alpha_ = nullptr;
   T *gU_ = nullptr, *gUb_ = nullptr, *gUh_ = nullptr, *tmpU_ = nullptr;
+  T *Ut_ = nullptr;  // viscous grids only: U~ (forward), dJ/dU~ (adjoint)
   S *P_ = nullptr, *b_ = nullptr, *gP_ = nullptr, *y_ = nullptr;
   void *stage_ = nullptr;
   double *dscal_ = nullptr;  // [0] norms, [1] loss, [8..16) dJ/dtheta
@@ -728,7 +744,7 @@ size_t episode_base_bytes(const nf_config &cfg, const nf_grid &g) {
   const size_t t = cfg.precision == NF_PREC_FP64 ? 8 : 4;
   const size_t s = cfg.precision == NF_PREC_FP32 ? 4 : 8;
   const size_t v = cfg.precision == NF_PREC_FP64 ? 8 : 4;
-  size_t b = 6 * nf * t + 4 * nc * s + nc * 8;  // fields, scalars, staging
+  size_t b = (g.nu > 0.0 ? 7 : 6) * nf * t + 4 * nc * s + nc * 8;  // fields, scalars, staging
   b += nc * 20;                                  // component labels, gauge
   b += nc * s + 5 * nc * v;                      // solver vectors
   b += (nc * (2 * v + 3 * t)) * 2 / 7 + nc * v;  // hierarchy (approx.)

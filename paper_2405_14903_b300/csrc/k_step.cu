@@ -388,6 +388,36 @@ __device__ __forceinline__ void face_cells(const GridDev &g, int d, int i,
   cL = o > 0 ? g.cell(i - (d == 0), j - (d == 1), k - (d == 2)) : -1;
 }
 
+// ---------------------------------------------------------- viscosity -----
+// Explicit viscosity (Eq. viscosity_matrix): out = in - kv G^T G in on each
+// component's own face lattice, kv = nu h / dx^2. G differences the values
+// across every edge between two neighbouring lattice points inside the box,
+// so a face at the end of a lattice row has no neighbour past it (-G^T G is
+// the lattice's graph Laplacian). G^T G is symmetric, so the same kernel maps
+// dJ/dU^ to dJ/dU~ in the adjoint (Sec. 2.3.2, Viscosity and Advection).
+// in and out must not overlap.
+template <class T>
+__global__ void k_viscosity(GridDev g, Fields<T> in, FieldsMut<T> out, T kv) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int d;
+  int64_t f;
+  if (!split_face(g, t, d, f)) return;
+  int i, j, k;
+  g.face_ijk(d, f, i, j, k);
+  const int nx = g.fnx(d), ny = g.fny(d), nz = g.fnz(d);
+  const int64_t sy = nx, sz = (int64_t)nx * ny;
+  const T *u = comp(in, d);
+  const T c = u[f];
+  T acc = T(0);
+  if (i > 0) acc += u[f - 1] - c;
+  if (i + 1 < nx) acc += u[f + 1] - c;
+  if (j > 0) acc += u[f - sy] - c;
+  if (j + 1 < ny) acc += u[f + sy] - c;
+  if (k > 0) acc += u[f - sz] - c;
+  if (k + 1 < nz) acc += u[f + sz] - c;
+  comp(out, d)[f] = c + kv * acc;
+}
+
 // --------------------------------------------------------------- rhs ------
 // b = G^T (S U^ + (I - S) U_s) / c on active cells (sum alpha > 0), else 0.
 // G^T v at a cell is v(low face) - v(high face), summed over the axes. The
@@ -734,6 +764,16 @@ void launch_advect_adjoint(const Launch &L, const GridDev &g, Fields<T> u,
   ++*L.counter;
 }
 
+template <class T>
+void launch_viscosity(const Launch &L, const GridDev &g, Fields<T> in,
+                      FieldsMut<T> out) {
+  const int64_t n = g.nface(0) + g.nface(1) + g.nface(2);
+  const double kv = g.nu * g.dt / (g.dx * g.dx);
+  ProfScope _ps(L, NF_K_VISCOSITY);
+  k_viscosity<T><<<nblocks(n), kBlock, 0, L.s>>>(g, in, out, T(kv));
+  ++*L.counter;
+}
+
 template <class T, class S>
 void launch_rhs(const Launch &L, const GridDev &g, const SceneDev &s,
                 Fields<T> alpha, Fields<T> uh, S *b, const RedScratch &rs,
@@ -791,6 +831,8 @@ void launch_adj_face(const Launch &L, const GridDev &g, const SceneDev &s,
   template void launch_advect_adjoint<T>(const Launch &, const GridDev &,   \
                                          Fields<T>, Fields<T>, FieldsMut<T>, \
                                          int);                               \
+  template void launch_viscosity<T>(const Launch &, const GridDev &,        \
+                                    Fields<T>, FieldsMut<T>);                \
   template void launch_loss<T>(const Launch &, const GridDev &, int,        \
                                Fields<T>, FieldsMut<T>, bool,                \
                                const RedScratch &, double *);                \

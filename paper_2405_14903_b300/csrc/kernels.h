@@ -56,6 +56,11 @@ void launch_advect(const Launch &L, const GridDev &g, Fields<T> u,
 template <class T>
 void launch_advect_adjoint(const Launch &L, const GridDev &g, Fields<T> u,
                            Fields<T> gut, FieldsMut<T> gu, int order);
+// Explicit viscosity out = (I - nu h / dx^2 G^T G) in, h = g.dt (also the
+// adjoint map: G^T G is symmetric). in and out must not overlap.
+template <class T>
+void launch_viscosity(const Launch &L, const GridDev &g, Fields<T> in,
+                      FieldsMut<T> out);
 template <class T, class S>
 void launch_rhs(const Launch &L, const GridDev &g, const SceneDev &s,
                 Fields<T> alpha, Fields<T> uh, S *b, const RedScratch &rs,

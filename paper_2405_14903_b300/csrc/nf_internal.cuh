@@ -22,6 +22,7 @@ constexpr int kRedBlocks = 148 * 4;  // blocks of grid-stride reduction kernels
 struct GridDev {
   int nx, ny, nz;
   double dx, dt, rho, c;  // c = dt / (rho dx)
+  double nu;              // kinematic viscosity (0: inviscid)
   int outlet, oj0, ok0, ow, oh;
 
   __host__ __device__ int64_t ncell() const { return (int64_t)nx * ny * nz; }

@@ -42,6 +42,12 @@ def _ragged():
     return dict(I.config_sphere(20, steps=2), grid=g, scene=sc, u0=I.gaussian_faces(g, 0.1, 5))
 
 
+def _viscous(cfg, nu):
+    # explicit viscosity (Eq. viscosity_matrix) with nu h / dx^2 in (0.05, 0.13)
+    cfg["grid"]["nu"] = float(nu)
+    return cfg
+
+
 CONFIGS = {
     "sphere": lambda: I.config_sphere(16, steps=3),
     "plate": lambda: I.config_plate(16, steps=3),
@@ -50,6 +56,10 @@ CONFIGS = {
     "ragged_sphere": _ragged,
     "sphere32": lambda: I.config_sphere(32, steps=2),
     "spheres": lambda: dict(I.config_spheres(24, count=8), steps=2),
+    "sphere_viscous": lambda: _viscous(I.config_sphere(16, steps=3), 0.05),
+    "plate_viscous": lambda: _viscous(I.config_plate(16, steps=3), 0.04),
+    "chamber_sub_viscous": lambda: _viscous(
+        I.config_chamber(24, steps=3, duct_half_cells=3, cfl_max=1.5), 0.02),
 }
 
 
@@ -130,6 +140,32 @@ def test_one_step_stages_match_oracle(nf, prec, name):
         assert np.abs(GP[d][m] - GPr[d][m]).max() <= 1e3 * VEL_TOL[prec] * scale
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
+@pytest.mark.parametrize("nu", [0.03, 0.16])
+def test_viscous_step_matches_oracle_face_by_face(nf, prec, nu):
+    # ragged 20 x 12 x 14 box: U^ = (I - nu dt/dx^2 G^T G) B(U) U compared
+    # face by face (lattice ends at every wall), then the projected velocity;
+    # nu = 0.16 gives nu dt / dx^2 = 0.64, past explicit stability, which
+    # the step computes as written
+    cfg = _ragged()
+    cfg["grid"]["nu"] = nu
+    g = Grid(cfg["grid"])
+    ctx = make_ctx(nf, prec)
+    ep = ctx.episode(cfg["grid"], cfg["scene"])
+    rng = np.random.default_rng(17)
+    U = [0.3 * rng.standard_normal(g.face_shape(d)) for d in range(3)]
+    ep.set_velocity([torch.tensor(u, device="cuda") for u in U], project=False)
+    ep.step(1)
+    U1, tape = S.step(g, cfg["scene"], U, 0, 1e-13)
+    want = advect.viscosity(g, advect.advect(g, U))
+    got = host(ep.advected())
+    tol = 1e-12 if prec == "fp64" else 2e-6
+    for d in range(3):
+        scale = np.abs(want[d]).max()
+        np.testing.assert_allclose(got[d], want[d], rtol=0, atol=tol * scale)
+    assert rel(host(ep.velocity()), U1) <= VEL_TOL[prec]
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_divergence_free_after_step(nf, prec):
     cfg = CONFIGS["plate"]()
@@ -149,7 +185,8 @@ def test_divergence_free_after_step(nf, prec):
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
 @pytest.mark.parametrize("name", ["sphere", "plate", "chamber", "chamber_sub", "ragged_sphere",
-                                  "sphere32"])
+                                  "sphere32", "sphere_viscous", "plate_viscous",
+                                  "chamber_sub_viscous"])
 def test_rollout_loss_and_gradient_match_oracle(nf, prec, name):
     cfg, Jo, gtho, info = oracle_rollout(name)
     ctx = make_ctx(nf, prec, cfg=cfg, checkpoint_every=2)
@@ -265,6 +302,8 @@ def test_invalid_calls_raise(nf):
     g["outlet"] = dict(g["outlet"], w=40)
     with pytest.raises(nf.NFError):
         ctx.episode(g, bad["scene"])                                 # outlet outside
+    with pytest.raises(nf.NFError):
+        ctx.episode(I.make_grid(8, 0.01, nu=-0.1), I.sphere_scene()) # nu < 0
     cfg = CONFIGS["sphere"]()
     ep = ctx.episode(cfg["grid"], cfg["scene"])
     with pytest.raises(nf.NFError):
