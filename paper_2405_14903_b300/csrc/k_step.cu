@@ -7,6 +7,8 @@
 // All kernels are HBM-bound stencils or gathers (no dense contraction), so
 // they are plain CUDA-core code: one thread per face or cell, x fastest so
 // that warps read contiguous rows.
+#include <algorithm>
+
 #include "kernels.h"
 #include "scene.cuh"
 
@@ -395,27 +397,70 @@ __device__ __forceinline__ void face_cells(const GridDev &g, int d, int i,
 // so a face at the end of a lattice row has no neighbour past it (-G^T G is
 // the lattice's graph Laplacian). G^T G is symmetric, so the same kernel maps
 // dJ/dU^ to dJ/dU~ in the adjoint (Sec. 2.3.2, Viscosity and Advection).
+//
+// One thread per (i, j) lattice column of component blockIdx.z marches
+// kViscZ planes (z-chunk blockIdx.y), carrying the values below, at and
+// above the current plane in registers, so each value comes from DRAM once;
+// the x and y neighbours are L1/L2 hits of the same plane. The unrolled
+// loop lets the loads of every plane of the chunk be in flight together.
 // in and out must not overlap.
+constexpr int kViscZ = 8;
+
 template <class T>
-__global__ void k_viscosity(GridDev g, Fields<T> in, FieldsMut<T> out, T kv) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int d;
-  int64_t f;
-  if (!split_face(g, t, d, f)) return;
-  int i, j, k;
-  g.face_ijk(d, f, i, j, k);
+__global__ void __launch_bounds__(kBlock)
+k_viscosity(GridDev g, Fields<T> in, FieldsMut<T> out, T kv) {
+  const int d = blockIdx.z;
   const int nx = g.fnx(d), ny = g.fny(d), nz = g.fnz(d);
-  const int64_t sy = nx, sz = (int64_t)nx * ny;
-  const T *u = comp(in, d);
-  const T c = u[f];
-  T acc = T(0);
-  if (i > 0) acc += u[f - 1] - c;
-  if (i + 1 < nx) acc += u[f + 1] - c;
-  if (j > 0) acc += u[f - sy] - c;
-  if (j + 1 < ny) acc += u[f + sy] - c;
-  if (k > 0) acc += u[f - sz] - c;
-  if (k + 1 < nz) acc += u[f + sz] - c;
-  comp(out, d)[f] = c + kv * acc;
+  const int64_t plane = (int64_t)nx * ny;
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int k0 = blockIdx.y * kViscZ;
+  if (p >= plane || k0 >= nz) return;
+  const int j = (int)((uint32_t)p / (uint32_t)nx);
+  const int i = (int)(p - (int64_t)j * nx);
+  const bool xl = i > 0, xh = i + 1 < nx, yl = j > 0, yh = j + 1 < ny;
+  const T *__restrict__ u = comp(in, d) + p;
+  T *__restrict__ o = comp(out, d) + p;
+  if (k0 + kViscZ < nz) {
+    // a whole chunk with a plane above it: the column's kViscZ + 2 values
+    // are loaded up front (all in flight at once)
+    T v[kViscZ + 2];
+    v[0] = k0 > 0 ? u[(int64_t)(k0 - 1) * plane] : T(0);
+#pragma unroll
+    for (int s = 0; s <= kViscZ; ++s) v[s + 1] = u[(int64_t)(k0 + s) * plane];
+#pragma unroll
+    for (int s = 0; s < kViscZ; ++s) {
+      const int64_t q = (int64_t)(k0 + s) * plane;
+      const T c = v[s + 1];
+      T acc = v[s + 2] - c;
+      if (k0 + s > 0) acc += v[s] - c;
+      if (xl) acc += u[q - 1] - c;
+      if (xh) acc += u[q + 1] - c;
+      if (yl) acc += u[q - nx] - c;
+      if (yh) acc += u[q + nx] - c;
+      o[q] = c + kv * acc;
+    }
+    return;
+  }
+  T below = k0 > 0 ? u[(int64_t)(k0 - 1) * plane] : T(0);
+  T c = u[(int64_t)k0 * plane];
+#pragma unroll
+  for (int s = 0; s < kViscZ; ++s) {
+    const int k = k0 + s;
+    if (k < nz) {
+      const int64_t q = (int64_t)k * plane;
+      const T above = k + 1 < nz ? u[q + plane] : T(0);
+      T acc = T(0);
+      if (xl) acc += u[q - 1] - c;
+      if (xh) acc += u[q + 1] - c;
+      if (yl) acc += u[q - nx] - c;
+      if (yh) acc += u[q + nx] - c;
+      if (k > 0) acc += below - c;
+      if (k + 1 < nz) acc += above - c;
+      o[q] = c + kv * acc;
+      below = c;
+      c = above;
+    }
+  }
 }
 
 // --------------------------------------------------------------- rhs ------
@@ -767,10 +812,14 @@ void launch_advect_adjoint(const Launch &L, const GridDev &g, Fields<T> u,
 template <class T>
 void launch_viscosity(const Launch &L, const GridDev &g, Fields<T> in,
                       FieldsMut<T> out) {
-  const int64_t n = g.nface(0) + g.nface(1) + g.nface(2);
+  // the largest lattice plane (x by y points) and depth over the components
+  const int64_t plane = std::max({(int64_t)(g.nx + 1) * g.ny, (int64_t)g.nx * (g.ny + 1),
+                                  (int64_t)g.nx * g.ny});
+  const dim3 grid((unsigned)((plane + kBlock - 1) / kBlock),
+                  (unsigned)((g.nz + 1 + kViscZ - 1) / kViscZ), 3);
   const double kv = g.nu * g.dt / (g.dx * g.dx);
   ProfScope _ps(L, NF_K_VISCOSITY);
-  k_viscosity<T><<<nblocks(n), kBlock, 0, L.s>>>(g, in, out, T(kv));
+  k_viscosity<T><<<grid, kBlock, 0, L.s>>>(g, in, out, T(kv));
   ++*L.counter;
 }
 
