@@ -414,23 +414,15 @@ k_viscosity(GridDev g, Fields<T> in, FieldsMut<T> out, T kv) {
   const int64_t plane = (int64_t)nx * ny;
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int k0 = blockIdx.y * kViscZ;
-  if (k0 >= nz) return;  // uniform over the block
-  const bool live = p < plane;
-  // every lane of the warp is still here: a warp whose columns all exist
-  // takes the fast path
-  const bool whole = __all_sync(0xffffffffu, live);
-  const int64_t pc = live ? p : plane - 1;
-  const int j = (int)((uint32_t)pc / (uint32_t)nx);
-  const int i = (int)(pc - (int64_t)j * nx);
+  if (p >= plane || k0 >= nz) return;
+  const int j = (int)((uint32_t)p / (uint32_t)nx);
+  const int i = (int)(p - (int64_t)j * nx);
   const bool xl = i > 0, xh = i + 1 < nx, yl = j > 0, yh = j + 1 < ny;
-  const T *__restrict__ u = comp(in, d) + pc;
-  T *__restrict__ o = comp(out, d) + pc;
-  if (whole && k0 + kViscZ < nz) {
+  const T *__restrict__ u = comp(in, d) + p;
+  T *__restrict__ o = comp(out, d) + p;
+  if (k0 + kViscZ < nz) {
     // a whole chunk with a plane above it: the column's kViscZ + 2 values
-    // are loaded up front (all in flight at once); the x neighbours are the
-    // adjacent lanes' values (consecutive lanes hold consecutive columns),
-    // loaded only at the warp's two ends
-    const int lane = threadIdx.x & 31;
+    // are loaded up front (all in flight at once)
     T v[kViscZ + 2];
     v[0] = k0 > 0 ? u[(int64_t)(k0 - 1) * plane] : T(0);
 #pragma unroll
@@ -439,21 +431,16 @@ k_viscosity(GridDev g, Fields<T> in, FieldsMut<T> out, T kv) {
     for (int s = 0; s < kViscZ; ++s) {
       const int64_t q = (int64_t)(k0 + s) * plane;
       const T c = v[s + 1];
-      T left = __shfl_up_sync(0xffffffffu, c, 1);
-      T right = __shfl_down_sync(0xffffffffu, c, 1);
-      if (lane == 0 && xl) left = u[q - 1];
-      if (lane == 31 && xh) right = u[q + 1];
       T acc = v[s + 2] - c;
       if (k0 + s > 0) acc += v[s] - c;
-      if (xl) acc += left - c;
-      if (xh) acc += right - c;
+      if (xl) acc += u[q - 1] - c;
+      if (xh) acc += u[q + 1] - c;
       if (yl) acc += u[q - nx] - c;
       if (yh) acc += u[q + nx] - c;
       o[q] = c + kv * acc;
     }
     return;
   }
-  if (!live) return;
   T below = k0 > 0 ? u[(int64_t)(k0 - 1) * plane] : T(0);
   T c = u[(int64_t)k0 * plane];
 #pragma unroll
