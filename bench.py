@@ -178,8 +178,6 @@ def alg_bytes_per_cell(kclass, nu):
         "apply_dot": 4 + 3 * 4 + 4,            # d, three fraction arrays, q
         "cg_xr": 4 * 4 + 2 * 4,                # x, r, d, q read; x, r written
         "residual64": 8 + 8 + 3 * 4 + 8 + 4,   # b, x (FP64), fractions, r64, r32
-        # three face values per cell read once and written once (FP32)
-        "viscosity": 3 * (4 + 4),
     }.get(kclass)
 
 
@@ -189,7 +187,10 @@ def alg_bytes_per_cell(kclass, nu):
 # V-cycle's mix of the three half-sweep modes (zero start 26.39 MB, six plain
 # 34.78 MB, prolongation folded 35.83 MB; writes stay in L2) at 128^3,
 # profiles/k_mg_smooth_chamber128.md.
-DRAM_BYTES_PER_CELL = {"mg_smooth0": (26.39 + 6 * 34.78 + 35.83) * 1e6 / 8 / 128 ** 3}
+# viscosity: 25.38 MB read + 0.07 MB written per launch (its output stays in
+# L2), profiles/k_viscosity_chamber128.md.
+DRAM_BYTES_PER_CELL = {"mg_smooth0": (26.39 + 6 * 34.78 + 35.83) * 1e6 / 8 / 128 ** 3,
+                       "viscosity": (25.377792 + 0.066304) * 1e6 / 128 ** 3}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -333,7 +334,9 @@ def run_ours(args, rank, world, local_rank):
         va = vb / (vms / 1e3) / 1e9
         out["viscosity_roofline"] = dict(
             bound="hbm", kernel="viscosity", achieved=va, peak=peak, peak_source=src,
-            unit="GB/s", frac=va / peak, traffic=None, launches=visc[0], avg_us=1e3 * vms,
+            unit="GB/s", frac=va / peak,
+            traffic=DRAM_BYTES_PER_CELL["viscosity"] * ncell if n == 128 else None,
+            launches=visc[0], avg_us=1e3 * vms,
             alg_bytes_per_launch=vb,
             timing="CUDA events around every launch, over one step after the timed region")
     tot = sum(v[1] for v in shares.values()) or 1.0
