@@ -30,6 +30,11 @@ class Grid:
         self.rho = float(desc.get("rho", 1.0))
         self.nu = float(desc.get("nu", 0.0))
         self.periodic = bool(desc.get("periodic", False))
+        # face fractions: "supersample" (4x4x4 ramp samples of the face's
+        # control volume) or "corner" (face area from the corner values)
+        self.fractions = desc.get("fractions", "supersample")
+        if self.fractions not in ("supersample", "corner"):
+            raise ValueError(f"unknown fraction rule {self.fractions!r}")
         self.outlet = desc.get("outlet")
         self.c = self.dt / (self.rho * self.dx)
         self.n = (self.nx, self.ny, self.nz)          # cells per axis, (x, y, z)

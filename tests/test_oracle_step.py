@@ -111,14 +111,23 @@ def _viscous(cfg, nu):
     return cfg
 
 
-@pytest.mark.parametrize("name", ["sphere", "plate", "chamber", "sphere_viscous"])
+def _corner(cfg):
+    cfg["grid"]["fractions"] = "corner"
+    return cfg
+
+
+@pytest.mark.parametrize("name", ["sphere", "plate", "chamber", "sphere_viscous",
+                                  "sphere_corner", "plate_corner"])
 def test_rollout_gradient_matches_central_differences(name):
     # sphere_viscous: explicit viscosity with nu dt / dx^2 = 0.072 in the
     # closed box (Eq. viscosity_matrix and its adjoint, Sec. 2.3.2)
     cfg = {"sphere": lambda: I.config_sphere(12, steps=3),
            "plate": lambda: I.config_plate(12, steps=4),
            "chamber": lambda: I.config_chamber(16, steps=4, duct_half_cells=2),
-           "sphere_viscous": lambda: _viscous(I.config_sphere(12, steps=3), 0.05)}[name]()
+           "sphere_viscous": lambda: _viscous(I.config_sphere(12, steps=3), 0.05),
+           # the paper's face-area fractions from corner values (Sec. 2.3.1)
+           "sphere_corner": lambda: _corner(I.config_sphere(12, steps=3)),
+           "plate_corner": lambda: _corner(I.config_plate(12, steps=4))}[name]()
     J, g_adj, _ = S.loss_and_grad(cfg, tol=1e-12)
     g_fd = S.fd_gradient(cfg, h=1e-4, tol=1e-12)
     err = np.linalg.norm(g_adj - g_fd) / np.linalg.norm(g_fd)
