@@ -83,6 +83,9 @@ def parse():
     ap.add_argument("--nu", type=float, default=0.0,
                     help="kinematic viscosity of the chamber (0: the inviscid metric); "
                          "nu > 0 adds explicit viscosity to every step and its adjoint")
+    ap.add_argument("--fractions", default="supersample", choices=["supersample", "corner"],
+                    help="face fractions: 4x4x4 ramp subsamples of the face's control volume, "
+                         "or the face area from the corner values")
     ap.add_argument("--workload", default="rollout", choices=["rollout", "serving", "precision"],
                     help="rollout: the chamber fwd+adjoint metric; serving: the episode mix")
     ap.add_argument("--serve-count", type=int, default=512, help="episodes in the serving mix")
@@ -201,6 +204,7 @@ def run_ours(args, rank, world, local_rank):
     n, T = args.n, args.rollout
     cfg = chamber(n, T, seed=rank)
     cfg["grid"]["nu"] = float(args.nu)
+    cfg["grid"]["fractions"] = args.fractions
     ncell = n ** 3
 
     def barrier():
@@ -289,6 +293,7 @@ def run_ours(args, rank, world, local_rank):
                config=dict(workload=f"pulsing chamber {n}^3, {T} steps dt=0.005, 16x16 outlet, "
                                     "outflow loss; forward rollout + full adjoint",
                            grid=n, rollout_steps=T, checkpoint_every=10, nu=float(args.nu),
+                           fractions=args.fractions,
                            cfl_max=cfg["cfl_max"], substeps_executed=int(stats["fwd"]["steps"]),
                            precision="FP32 MGPCG (V-cycle, CG vectors; BF16 coarse-level "
                                      "fractions), FP32 per-thread dot partials summed in FP64, "
@@ -342,6 +347,9 @@ def run_ours(args, rank, world, local_rank):
     tot = sum(v[1] for v in shares.values()) or 1.0
     out["kernel_shares"] = {k: round(v[1] / tot, 4) for k, v in
                             sorted(shares.items(), key=lambda kv: -kv[1][1]) if v[1] > 0}
+    # average launch time per class in the profiled warm-up step (events
+    # around each launch)
+    out["kernel_avg_us"] = {k: round(1e3 * v[1] / v[0], 2) for k, v in shares.items() if v[0]}
     if not args.no_extras:
         out["e2e"] = run_e2e(args, torch, cfg, dev, ep)
         out["fp64_plain"] = run_plain(args, P, torch, dev)

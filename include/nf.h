@@ -158,7 +158,18 @@ typedef struct nf_grid {
      values are accepted and computed as written. Costs one extra face
      field per episode and one stencil pass each way per step.            */
   double nu;
+  /* face fraction rule: NF_FRACTIONS_SUPERSAMPLE (0) = the fluid share of the
+     face's dx^3 control volume from 4x4x4 ramp subsamples; NF_FRACTIONS_CORNER
+     (1) = the paper's rule (Sec. 2.3.1, Projection): the fluid share of the
+     face's area, from phi at its four corners, zero crossings on its edges
+     by linear interpolation, and the area of the polygon through the fluid
+     corners (phi >= 0) and the crossings in walking order (connected fluid
+     where only two diagonal corners are fluid).                          */
+  int fractions;
 } nf_grid;
+
+#define NF_FRACTIONS_SUPERSAMPLE 0
+#define NF_FRACTIONS_CORNER 1
 
 typedef struct nf_scene {
   int kind;               /* NF_SCENE_*                                       */
@@ -208,8 +219,8 @@ int nf_synchronize(nf_ctx *ctx);
 
 /* Create an episode: a grid, a scene with parameters theta, zero velocity,
    step counter 0. NF_E_INVALID for a grid with fewer than 4 cells on an
-   axis, dx, dt <= 0, nu < 0 or not finite, or an outlet patch off the
-   high-x wall. Admission: NF_E_OOM when its device state would exceed the
+   axis, dx, dt <= 0, nu < 0 or not finite, an unknown fraction rule, or an
+   outlet patch off the high-x wall. Admission: NF_E_OOM when its device state would exceed the
    context's HBM budget. Geometry is evaluated analytically at
    t_{n+1} = (n + 1) dt in every step (Sec. 2.3.1, Projection). */
 int nf_episode_create(nf_ctx *ctx, const nf_grid *g, const nf_scene *s,

@@ -21,6 +21,7 @@ NF_F32, NF_F64 = 0, 1
 NF_MEM_DEVICE, NF_MEM_HOST = 0, 1
 SCENE = {"none": 0, "sphere": 1, "chamber": 2, "plate": 3, "spheres": 4}
 LOSS = {"kinetic_energy": 0, "outflow": 1}
+FRACTIONS = {"supersample": 0, "corner": 1}
 MAX_PARAMS = 8
 CUDA_STREAM_LEGACY = 1   # cudaStreamLegacy: the legacy default stream
 
@@ -50,7 +51,7 @@ class Grid(C.Structure):
                 ("dx", C.c_double), ("dt", C.c_double), ("rho", C.c_double),
                 ("outlet", C.c_int), ("outlet_j0", C.c_int),
                 ("outlet_k0", C.c_int), ("outlet_w", C.c_int),
-                ("outlet_h", C.c_int), ("nu", C.c_double)]
+                ("outlet_h", C.c_int), ("nu", C.c_double), ("fractions", C.c_int)]
 
 
 class Scene(C.Structure):

@@ -53,6 +53,10 @@ def grid_struct(desc):
     if desc.get("periodic", False):
         raise ValueError("the CUDA path implements closed boxes (walls and an outlet patch)")
     g.nu = float(desc.get("nu", 0.0))
+    rule = desc.get("fractions", "supersample")
+    if rule not in L.FRACTIONS:
+        raise ValueError(f"unknown fraction rule {rule!r}")
+    g.fractions = L.FRACTIONS[rule]
     o = desc.get("outlet")
     if o:
         if o["axis"] != 0 or o["side"] != 1:

@@ -326,6 +326,10 @@ int nf_episode_create(nf_ctx *ctx, const nf_grid *g, const nf_scene *s,
               "and fewer than 2^31 faces per component");
     return NF_E_INVALID;
   }
+  if (g->fractions != NF_FRACTIONS_SUPERSAMPLE && g->fractions != NF_FRACTIONS_CORNER) {
+    set_error("nf_episode_create: unknown fraction rule");
+    return NF_E_INVALID;
+  }
   if (!(g->nu >= 0.0) || !std::isfinite(g->nu)) {
     set_error("nf_episode_create: viscosity nu must be finite and >= 0");
     return NF_E_INVALID;

@@ -192,6 +192,7 @@ class EpisodeImpl : public EpisodeBase {
     g.rho = gr.rho > 0 ? gr.rho : 1.0;
     g.c = g.dt / (g.rho * g.dx);
     g.nu = gr.nu;
+    g.frac = gr.fractions;
     g.outlet = gr.outlet;
     g.oj0 = gr.outlet_j0;
     g.ok0 = gr.outlet_k0;

@@ -139,6 +139,71 @@ __device__ __forceinline__ T *comp(FieldsMut<T> &u, int e) {
   return e == 0 ? u.x : (e == 1 ? u.y : u.z);
 }
 
+// ------------------------------------------------ corner (area) fractions --
+// The paper's face fraction (Sec. 2.3.1, Projection), the grid option
+// NF_FRACTIONS_CORNER: phi at the face's four corners, in the cyclic order
+// (0,0), (1,0), (1,1), (0,1) of its tangential axes (d+1)%3 and (d+2)%3; on
+// each edge whose end values differ in sign (phi >= 0 is fluid) the zero
+// crossing by linear interpolation; alpha = the area of the polygon through
+// the fluid corners and the crossings in walking order (shoelace formula),
+// which keeps the fluid connected where only two diagonal corners are fluid.
+
+// Physical position of corner c of face (d; i, j, k).
+__device__ __forceinline__ void face_corner(int d, int i, int j, int k, int c,
+                                            double dx, double p[3]) {
+  face_pos(d, i, j, k, p[0], p[1], p[2]);
+  p[(d + 1) % 3] += (c == 1 || c == 2) ? 0.5 : -0.5;
+  p[(d + 2) % 3] += (c >= 2) ? 0.5 : -0.5;
+  p[0] *= dx;
+  p[1] *= dx;
+  p[2] *= dx;
+}
+
+// alpha from the corner values, and d alpha / d phi_c into da.
+__device__ double corner_area(const double ph[4], double da[4]) {
+  const double cs[4] = {0.0, 1.0, 1.0, 0.0}, ct[4] = {0.0, 0.0, 1.0, 1.0};
+  double vx[8], vy[8], w0[8], w1[8];
+  int ve[8];  // edge (its first corner) of a crossing vertex, -1 for a corner
+  int m = 0;
+  for (int c = 0; c < 4; ++c) {
+    const int n = (c + 1) & 3;
+    const bool fc = ph[c] >= 0.0, fn = ph[n] >= 0.0;
+    da[c] = 0.0;
+    if (fc) {
+      vx[m] = cs[c];
+      vy[m] = ct[c];
+      ve[m] = -1;
+      ++m;
+    }
+    if (fc != fn) {
+      const double den = ph[c] - ph[n], t = ph[c] / den;
+      vx[m] = cs[c] + t * (cs[n] - cs[c]);
+      vy[m] = ct[c] + t * (ct[n] - ct[c]);
+      ve[m] = c;
+      w0[m] = -ph[n] / (den * den);  // dt / dphi_c
+      w1[m] = ph[c] / (den * den);   // dt / dphi_n
+      ++m;
+    }
+  }
+  double area = 0.0;
+  for (int a = 0; a < m; ++a) {
+    const int b = a + 1 < m ? a + 1 : 0;
+    area += 0.5 * (vx[a] * vy[b] - vx[b] * vy[a]);
+  }
+  // dA/dv_a = 1/2 (y_next - y_prev, x_prev - x_next); a crossing moves along
+  // its edge as t changes
+  for (int a = 0; a < m; ++a) {
+    if (ve[a] < 0) continue;
+    const int nx = a + 1 < m ? a + 1 : 0, pv = a > 0 ? a - 1 : m - 1;
+    const int c = ve[a], n = (c + 1) & 3;
+    const double gdt = 0.5 * (vy[nx] - vy[pv]) * (cs[n] - cs[c]) +
+                       0.5 * (vx[pv] - vx[nx]) * (ct[n] - ct[c]);
+    da[c] += gdt * w0[a];
+    da[n] += gdt * w1[a];
+  }
+  return area;
+}
+
 // ---------------------------------------------------------- rasterise -----
 template <class T>
 __device__ __forceinline__ double band_fraction(const GridDev &g,
@@ -151,7 +216,7 @@ __device__ __forceinline__ double band_fraction(const GridDev &g,
 // (subsamples lie within 0.65 dx of the centre and phi is 1-Lipschitz), so
 // only the narrow band evaluates the 64 samples (directly in FP64 for FP64
 // fields, with the narrow-band evaluator of scene.cuh for FP32 fields).
-template <class T>
+template <class T, bool kCorner>
 __global__ void __launch_bounds__(kBlock, 4)
 k_rasterize(GridDev g, SceneDev s, FieldsMut<T> alpha) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -169,13 +234,24 @@ k_rasterize(GridDev g, SceneDev s, FieldsMut<T> alpha) {
   const float pc = scene_phi<float>(s, (i + (d == 0 ? 0.f : 0.5f)) * hf,
                                     (j + (d == 1 ? 0.f : 0.5f)) * hf,
                                     (k + (d == 2 ? 0.f : 0.5f)) * hf);
-  const float margin = 0.8f * hf;
+  // corners lie within 0.71 dx and subsamples within 0.65 dx of the centre
+  const float margin = (kCorner ? 0.75f : 0.8f) * hf;
   if (pc > margin) {
     a[f] = T(1);
     return;
   }
   if (pc < -margin) {
     a[f] = T(0);
+    return;
+  }
+  if (kCorner) {
+    double ph[4], da[4], p[3];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      face_corner(d, i, j, k, c, g.dx, p);
+      ph[c] = scene_phi<double>(s, p[0], p[1], p[2]);
+    }
+    a[f] = T(corner_area(ph, da));
     return;
   }
   double X, Y, Z;
@@ -646,7 +722,7 @@ __global__ void k_adj_gp(GridDev g, Fields<T> alpha, Fields<T> gu, S *gp,
 //   gU^  = alpha (gU + Gy),   gU_s = (1 - alpha)(gU + Gy)
 // and the parameter gradient  sum_f gS_f dalpha_f/dtheta + gU_s,f du_s,f/dtheta
 // (Sec. 2.3.3), with dalpha/dtheta from the subsample ramps (narrow band).
-template <class T, class S>
+template <class T, class S, bool kCorner>
 __global__ void k_adj_face(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
                            const S *P, const S *y, Fields<T> gu,
                            FieldsMut<T> guh, RedScratch rs, double *gtheta) {
@@ -715,6 +791,27 @@ __global__ void k_adj_face(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
       const T us = face_us<T>(g, s, d, i, j, k);
       gS = gU * (Uh - cT * GP - us) + Gy * (Uh - us) - cT * Gy * GP;
       if (gS == T(0)) break;
+      if (kCorner) {
+        // d alpha / d theta = sum_c d alpha / d phi_c d phi_c / d theta,
+        // four corners evaluated by this lane
+        double ph[4], da[4], p[4][3];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          face_corner(d, i, j, k, c, g.dx, p[c]);
+          ph[c] = scene_phi<double>(s, p[c][0], p[c][1], p[c][2]);
+        }
+        corner_area(ph, da);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          if (da[c] == 0.0) continue;
+          double tmp[kMaxParams];
+          scene_dphi(s, p[c][0], p[c][1], p[c][2], tmp);
+#pragma unroll
+          for (int q = 0; q < kMaxParams; ++q)
+            if (q < s.K) acc[q] += gS * (T)(da[c] * tmp[q]);
+        }
+        break;
+      }
       face_pos(d, i, j, k, Xd, Yd, Zd);
       band = true;
     } while (false);
@@ -784,7 +881,10 @@ void launch_rasterize(const Launch &L, const GridDev &g, const SceneDev &s,
                       FieldsMut<T> alpha) {
   const int64_t n = g.nface(0) + g.nface(1) + g.nface(2);
   ProfScope _ps(L, NF_K_RASTERIZE);
-  k_rasterize<T><<<nblocks(n), kBlock, 0, L.s>>>(g, s, alpha);
+  if (g.frac == NF_FRACTIONS_CORNER)
+    k_rasterize<T, true><<<nblocks(n), kBlock, 0, L.s>>>(g, s, alpha);
+  else
+    k_rasterize<T, false><<<nblocks(n), kBlock, 0, L.s>>>(g, s, alpha);
   ++*L.counter;
 }
 
@@ -867,8 +967,12 @@ void launch_adj_face(const Launch &L, const GridDev &g, const SceneDev &s,
                      Fields<T> gu, FieldsMut<T> guh, const RedScratch &rs,
                      double *gtheta) {
   ProfScope _ps(L, NF_K_ADJ_FACE);
-  k_adj_face<T, S><<<kRedBlocks, kBlock, 0, L.s>>>(g, s, alpha, uh, P, y, gu, guh,
-                                                   rs, gtheta);
+  if (g.frac == NF_FRACTIONS_CORNER)
+    k_adj_face<T, S, true><<<kRedBlocks, kBlock, 0, L.s>>>(g, s, alpha, uh, P, y, gu,
+                                                           guh, rs, gtheta);
+  else
+    k_adj_face<T, S, false><<<kRedBlocks, kBlock, 0, L.s>>>(g, s, alpha, uh, P, y, gu,
+                                                            guh, rs, gtheta);
   ++*L.counter;
 }
 

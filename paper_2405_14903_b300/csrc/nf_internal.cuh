@@ -23,6 +23,7 @@ struct GridDev {
   int nx, ny, nz;
   double dx, dt, rho, c;  // c = dt / (rho dx)
   double nu;              // kinematic viscosity (0: inviscid)
+  int frac;               // NF_FRACTIONS_* rule of the face fractions
   int outlet, oj0, ok0, ow, oh;
 
   __host__ __device__ int64_t ncell() const { return (int64_t)nx * ny * nz; }

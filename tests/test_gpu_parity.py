@@ -48,6 +48,12 @@ def _viscous(cfg, nu):
     return cfg
 
 
+def _corner(cfg):
+    # the paper's face-area fractions from corner values (Sec. 2.3.1)
+    cfg["grid"]["fractions"] = "corner"
+    return cfg
+
+
 CONFIGS = {
     "sphere": lambda: I.config_sphere(16, steps=3),
     "plate": lambda: I.config_plate(16, steps=3),
@@ -60,6 +66,13 @@ CONFIGS = {
     "plate_viscous": lambda: _viscous(I.config_plate(16, steps=3), 0.04),
     "chamber_sub_viscous": lambda: _viscous(
         I.config_chamber(24, steps=3, duct_half_cells=3, cfl_max=1.5), 0.02),
+    "sphere_corner": lambda: _corner(I.config_sphere(16, steps=3)),
+    "plate_corner": lambda: _corner(I.config_plate(16, steps=3)),
+    "chamber_corner": lambda: _corner(I.config_chamber(16, steps=3, duct_half_cells=2)),
+    "chamber_sub_corner": lambda: _corner(
+        I.config_chamber(24, steps=3, duct_half_cells=3, cfl_max=1.5)),
+    "spheres_corner": lambda: _corner(dict(I.config_spheres(24, count=8), steps=2)),
+    "ragged_corner": lambda: _corner(_ragged()),
 }
 
 
@@ -85,7 +98,9 @@ def device_u(cfg, dtype=torch.float64):
 # ------------------------------------------------------------ per stage ----
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("name", ["sphere", "plate", "chamber", "spheres"])
+@pytest.mark.parametrize("name", ["sphere", "plate", "chamber", "spheres", "sphere_corner",
+                                  "plate_corner", "chamber_corner", "spheres_corner",
+                                  "ragged_corner"])
 def test_fractions_match_oracle(nf, prec, name):
     cfg = CONFIGS[name]()
     g = Grid(cfg["grid"])
@@ -186,7 +201,8 @@ def test_divergence_free_after_step(nf, prec):
 @pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
 @pytest.mark.parametrize("name", ["sphere", "plate", "chamber", "chamber_sub", "ragged_sphere",
                                   "sphere32", "sphere_viscous", "plate_viscous",
-                                  "chamber_sub_viscous"])
+                                  "chamber_sub_viscous", "sphere_corner", "plate_corner",
+                                  "chamber_sub_corner", "ragged_corner"])
 def test_rollout_loss_and_gradient_match_oracle(nf, prec, name):
     cfg, Jo, gtho, info = oracle_rollout(name)
     ctx = make_ctx(nf, prec, cfg=cfg, checkpoint_every=2)
@@ -304,6 +320,18 @@ def test_invalid_calls_raise(nf):
         ctx.episode(g, bad["scene"])                                 # outlet outside
     with pytest.raises(nf.NFError):
         ctx.episode(I.make_grid(8, 0.01, nu=-0.1), I.sphere_scene()) # nu < 0
+    # an unknown fraction rule, through the C ABI (the binding refuses it first)
+    import ctypes
+    from paper_2405_14903_b300 import _lib as L
+    from paper_2405_14903_b300.api import grid_struct, scene_struct
+    gs = grid_struct(I.make_grid(8, 0.01))
+    gs.fractions = 7
+    ss, _keep = scene_struct(I.sphere_scene())
+    eid = ctypes.c_int64()
+    assert L.lib.nf_episode_create(ctx.handle, ctypes.byref(gs), ctypes.byref(ss),
+                                   ctypes.byref(eid)) == L.NF_E_INVALID
+    with pytest.raises(ValueError):
+        ctx.episode(dict(I.make_grid(8, 0.01), fractions="marching"), I.sphere_scene())
     cfg = CONFIGS["sphere"]()
     ep = ctx.episode(cfg["grid"], cfg["scene"])
     with pytest.raises(nf.NFError):
