@@ -49,8 +49,13 @@ def _viscous(cfg, nu):
 
 
 def _corner(cfg):
-    # the paper's face-area fractions from corner values (Sec. 2.3.1)
+    # the paper's face-area fractions from corner values (Sec. 2.3.1). A
+    # solid surface through grid nodes makes phi = 0 at whole faces' corners,
+    # where the rule's fluid test (phi >= 0) is decided by rounding; the
+    # chamber's duct walls are moved a quarter cell off the nodes
     cfg["grid"]["fractions"] = "corner"
+    if cfg["scene"]["kind"] == "chamber":
+        cfg["scene"] = dict(cfg["scene"], duct_half=cfg["scene"]["duct_half"] + 0.25 * cfg["grid"]["dx"])
     return cfg
 
 
