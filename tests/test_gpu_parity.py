@@ -33,12 +33,12 @@ def host(ts):
     return [t.detach().cpu().numpy() for t in ts]
 
 
-def _ragged():
+def _ragged(radius=0.15):
     # odd-sized, non-cubic box (20 x 12 x 14 cells); the sphere stays clear of
     # the walls (a sphere tangent to a wall leaves near-isolated slivers whose
     # gradient contribution is ill-conditioned)
     g = I.make_grid(20, 0.01, ny=12, nz=14)
-    sc = I.sphere_scene(v=(0.1, 0.05, -0.02), centre=(0.5, 0.3, 0.35), radius=0.15)
+    sc = I.sphere_scene(v=(0.1, 0.05, -0.02), centre=(0.5, 0.3, 0.35), radius=radius)
     return dict(I.config_sphere(20, steps=2), grid=g, scene=sc, u0=I.gaussian_faces(g, 0.1, 5))
 
 
@@ -77,7 +77,9 @@ CONFIGS = {
     "chamber_sub_corner": lambda: _corner(
         I.config_chamber(24, steps=3, duct_half_cells=3, cfl_max=1.5)),
     "spheres_corner": lambda: _corner(dict(I.config_spheres(24, count=8), steps=2)),
-    "ragged_corner": lambda: _corner(_ragged()),
+    # radius 3.074 dx: no grid node on the sphere at any step time (r = 3 dx
+    # about a node centre puts nodes on it at t = 0)
+    "ragged_corner": lambda: _corner(_ragged(radius=0.1537)),
 }
 
 
