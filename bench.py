@@ -196,6 +196,33 @@ DRAM_BYTES_PER_CELL = {"mg_smooth0": (26.39 + 6 * 34.78 + 35.83) * 1e6 / 8 / 128
                        "viscosity": (25.377792 + 0.066304) * 1e6 / 128 ** 3}
 
 
+# ------------------------------------------------------ ranks (replicas) ----
+# Every rank runs its own episode: no data-path collective. The only
+# collectives are the barriers around the timed region and one MAX
+# all-reduce of the timed milliseconds.
+
+def ranks_from_env(env=None):
+    """(world, rank, local_rank) as torchrun sets them (1, 0, 0 alone)."""
+    env = os.environ if env is None else env
+    return (int(env.get("WORLD_SIZE", "1")), int(env.get("RANK", "0")),
+            int(env.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(ms, world, device="cpu"):
+    """The slowest rank's timed milliseconds (the job ends with it)."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world, cells, frames, ms_per_step):
+    """Cell-steps/s of the whole job: every rank advances cells x frames."""
+    return world * cells * frames / (ms_per_step / 1e3)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     torch.cuda.set_device(local_rank)
@@ -280,12 +307,8 @@ def run_ours(args, rank, world, local_rank):
         visc = ctx.profile_read("viscosity")
         ctx.profile(None)
 
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_per_step = float(t.item()) / args.steps
-    value = world * ncell * T / (ms_per_step / 1e3)
+    ms_per_step = max_over_ranks(ms, world, dev) / args.steps
+    value = whole_job_value(world, ncell, T, ms_per_step)
 
     out = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
                warmup=args.warmup, ms_per_step=ms_per_step, higher_is_better=True,
@@ -639,9 +662,7 @@ def main():
     if args.cpu_sample:
         print(_cpu_sample(args.cpu_n))
         return
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local_rank = ranks_from_env()
     if args.impl == "reference":
         out = run_reference(args, rank)
     elif args.workload == "serving":
