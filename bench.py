@@ -483,7 +483,7 @@ def cpu_baseline(args):
 # -------------------------------------------------------------- serving ----
 
 def _serve_episode(kind, n, seed):
-    """Grid, scene and loss of one episode of the mix (configs 1-3 scenes)."""
+    """Grid, scene and loss of one episode of the mix (sphere, chamber or plate)."""
     rng = np.random.default_rng(seed)
     if kind == "sphere":
         cfg = I.config_sphere(n)
@@ -534,8 +534,8 @@ def _serve_run(P, plan, slots, budget):
 
 
 def run_serving(args):
-    """Config 5: Poisson arrivals of episodes (grid sizes 32..192, scenes of
-    configs 1-3), each issuing one-frame step requests of which a seeded 30 %
+    """Serving mix: Poisson arrivals of episodes (grid sizes 32..192, sphere,
+    chamber and plate scenes), each issuing one-frame step requests of which a seeded 30 %
     carry the adjoint, then closing; the same schedule served with `slots`
     concurrent slots and one episode at a time."""
     import torch
@@ -575,7 +575,7 @@ SOLVER_CLASSES = ("residual64", "axpy64", "cg_init", "apply_dot", "cg_xr", "cg_r
 
 
 def run_precision(args):
-    """Config 4: one projection of a divergent N(0, 1) velocity around 64 static
+    """Precision sweep: one projection of a divergent N(0, 1) velocity around 64 static
     spheres at 256^3, to relative residual 1e-8, by FP64 MGPCG, FP32 MGPCG and
     MIXED (FP32 CG, BF16-coarse V-cycle, FP64 refinement). The velocity error
     is measured against FP64 MGPCG to 1e-12 (the oracle's unpreconditioned CG
@@ -626,7 +626,7 @@ def run_precision(args):
                               achieved_gbs=it_bytes * st["iters"] / (st["solve_ms"] / 1e3) / 1e9,
                               velocity_rel_err=err,
                               converged=st["rel_residual"] <= 1e-8)
-    return dict(metric="single projection at 256^3 to rel res 1e-8 (config 4)",
+    return dict(metric="single projection at 256^3 to rel res 1e-8 (64 static spheres)",
                 value=variants["mixed"]["solve_kernel_ms"], unit="ms", n_gpus=1, steps=1,
                 warmup=1, ms_per_step=variants["mixed"]["projection_ms"], higher_is_better=False,
                 scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",

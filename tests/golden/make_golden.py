@@ -2,7 +2,8 @@
 
 Run from the repository root: ``python tests/golden/make_golden.py``. The
 values are the FP64 oracle's loss and parameter gradient of small seeded
-rollouts (configs 1-3 of the workload generator at reduced size). The paper
+rollouts (the sphere, chamber and plate scenes of the workload generator at
+reduced size). The paper
 prints no worked numeric example for this path, so no stored value here is
 the paper's; these guard the oracle against unintended change, and any
 regeneration must name, in its commit message, the passage that justifies
