@@ -17,6 +17,8 @@ What it computes (each module cites the passage it follows):
                  update and the projection adjoint (Eqs. projection_matrix,
                  u_next_matrix; Sec. 2.3.2, 2.3.3).
 * ``step``       step, rollout, losses, BPTT and central finite differences.
+* ``bezier``     polar-Bezier closed curves, their signed distance and radius
+                 gradient, extrusion of key cross-sections, CSG (App. A).
 
 Everything is float64 NumPy written for reading, not speed. Every function
 is pinned by the ``-m "not gpu"`` tests against results fixed by the
@@ -25,5 +27,5 @@ volume fractions of planes, exact shifts, invariants, Taylor-Green decay,
 finite differences); see ``tests/test_oracle_*.py``.
 """
 
-from . import advect, geometry, mac, project, rasterize, step  # noqa: F401
+from . import advect, bezier, geometry, mac, project, rasterize, step  # noqa: F401
 from .mac import Grid  # noqa: F401

@@ -1,0 +1,211 @@
+"""Pins of the oracle's polar-Bezier shapes, extrusion and CSG (no GPU).
+
+Appendix A: N cubic segments around a centre, inner control points at
+2 pi / (3N) from the ends of each segment's angular range, endpoints at the
+midpoint of the two control points around them; key cross-sections along z
+interpolated by the polynomial through the keys; CSG union/intersection.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import bezier as B
+
+C0 = (0.5, 0.45)
+
+
+def _random_shape(seed, N=5):
+    rng = np.random.default_rng(seed)
+    return rng.uniform(0.18, 0.34, N), rng.uniform(0.18, 0.34, N)
+
+
+@pytest.mark.parametrize("N", [3, 4, 6, 9])
+def test_equal_radii_endpoints_and_segment_midpoints_in_closed_form(N):
+    # equal radii rho: every endpoint is the midpoint of two control points
+    # at radius rho, 4 pi / (3N) apart, so at radius rho cos(2 pi / (3N));
+    # the segment's midpoint B(1/2) = (e0 + 3 p0 + 3 p1 + e1) / 8 lies on the
+    # bisector at radius (2 rho cos(2pi/3N) cos(pi/N) + 6 rho cos(pi/3N)) / 8
+    rho = 0.27
+    C = B.control_points(C0, [rho] * N, [rho] * N)
+    c = np.asarray(C0)
+    k = np.cos(2 * np.pi / (3 * N))
+    for i in range(N):
+        e = C[i, 0] - c
+        assert abs(np.linalg.norm(e) - rho * k) <= 1e-15
+        dang = (np.arctan2(e[1], e[0]) - 2 * np.pi * i / N + np.pi) % (2 * np.pi) - np.pi
+        assert abs(dang) <= 1e-12
+        m = B.bezier(C[i], 0.5) - c
+        want = (2 * rho * k * np.cos(np.pi / N) + 6 * rho * np.cos(np.pi / (3 * N))) / 8
+        assert abs(np.linalg.norm(m) - want) <= 1e-15
+    # closed and G1: each endpoint is shared and lies on its control line
+    for i in range(N):
+        n = (i + 1) % N
+        assert np.array_equal(C[i, 3], C[n, 0])
+        a, b = C[i, 2] - C[i, 3], C[n, 1] - C[n, 0]
+        assert abs(a[0] * b[1] - a[1] * b[0]) <= 1e-15
+
+
+def test_distance_matches_dense_sampling_of_the_curve():
+    r1, r2 = _random_shape(1)
+    C = B.control_points(C0, r1, r2)
+    s = np.linspace(0.0, 1.0, 200001)
+    pts = np.concatenate([B.bezier(C[i], s) for i in range(len(C))])
+    rng = np.random.default_rng(2)
+    for x in rng.uniform(0.0, 1.0, size=(40, 2)):
+        want = np.min(np.linalg.norm(pts - x, axis=-1))
+        assert abs(abs(B.shape2d_sdf(C0, r1, r2, x)) - want) <= 1e-9
+
+
+def _winding(poly, x):
+    v = poly - x
+    ang = np.arctan2(v[:, 1], v[:, 0])
+    d = np.diff(np.concatenate([ang, ang[:1]]))
+    d = (d + np.pi) % (2 * np.pi) - np.pi
+    return int(round(d.sum() / (2 * np.pi)))
+
+
+def test_sign_matches_the_winding_number_of_a_dense_polygon():
+    r1, r2 = _random_shape(3)
+    C = B.control_points(C0, r1, r2)
+    s = np.linspace(0.0, 1.0, 400, endpoint=False)
+    poly = np.concatenate([B.bezier(C[i], s) for i in range(len(C))])
+    rng = np.random.default_rng(4)
+    n_in = 0
+    for x in rng.uniform(0.0, 1.0, size=(300, 2)):
+        d = B.shape2d_sdf(C0, r1, r2, x)
+        if abs(d) < 1e-3:
+            continue
+        inside = _winding(poly, x) != 0
+        assert (d < 0) == inside
+        n_in += inside
+    assert n_in > 20
+
+
+def _green_area(C):
+    # area enclosed by the closed piecewise cubic: 1/2 sum of the integral of
+    # x y' - y x' over each segment, exact by 4-point Gauss-Legendre (degree 5)
+    g, w = np.polynomial.legendre.leggauss(4)
+    s, w = 0.5 * (g + 1.0), 0.5 * w
+    tot = 0.0
+    for P in C:
+        pts = B.bezier(P, s)
+        e0, p0, p1, e1 = P
+        d = (3 * (1 - s) ** 2)[:, None] * (p0 - e0) + (6 * (1 - s) * s)[:, None] * (p1 - p0) \
+            + (3 * s ** 2)[:, None] * (e1 - p1)
+        tot += 0.5 * np.sum(w * (pts[:, 0] * d[:, 1] - pts[:, 1] * d[:, 0]))
+    return tot
+
+
+def test_area_by_signs_converges_to_the_enclosed_area():
+    r1, r2 = _random_shape(5)
+    C = B.control_points(C0, r1, r2)
+    exact = _green_area(C)
+    m = 100
+    g = (np.arange(m) + 0.5) / m
+    inside = sum(B.shape2d_sdf(C0, r1, r2, (x, y)) < 0 for x in g for y in g)
+    assert abs(inside / m ** 2 - exact) <= 0.01 * exact
+
+
+def test_radius_gradient_matches_finite_differences():
+    r1, r2 = _random_shape(6)
+    N = len(r1)
+    rng = np.random.default_rng(7)
+    h = 1e-6
+    checked = 0
+    for x in rng.uniform(0.05, 0.95, size=(30, 2)):
+        C = B.control_points(C0, r1, r2)
+        ds = sorted(B.closest_on_segment(C[i], x)[0] for i in range(N))
+        if ds[1] - ds[0] < 1e-3:        # near the medial axis: not differentiable
+            continue
+        _, g = B.shape2d_sdf(C0, r1, r2, x, with_grad=True)
+        for j in range(2 * N):
+            a1, a2, b1, b2 = r1.copy(), r2.copy(), r1.copy(), r2.copy()
+            (a1 if j % 2 == 0 else a2)[j // 2] += h
+            (b1 if j % 2 == 0 else b2)[j // 2] -= h
+            fd = (B.shape2d_sdf(C0, a1, a2, x) - B.shape2d_sdf(C0, b1, b2, x)) / (2 * h)
+            assert abs(fd - g[j]) <= 1e-7
+        checked += 1
+    assert checked > 20
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5])
+def test_key_interpolation_passes_through_keys_and_reproduces_polynomials(n):
+    for k in range(n):
+        u = k / (n - 1) if n > 1 else 0.3
+        np.testing.assert_allclose(B.lagrange_weights(n, u), np.eye(n)[k] if n > 1 else [1.0],
+                                   atol=1e-12)
+    # any polynomial of degree < n is reproduced at every u
+    rng = np.random.default_rng(n)
+    coef = rng.standard_normal(n)
+    uk = np.arange(n) / max(n - 1, 1)
+    vals = np.polyval(coef[::-1], uk)
+    for u in rng.uniform(0.0, 1.0, size=5):
+        assert abs(B.lagrange_weights(n, u) @ vals - np.polyval(coef[::-1], u)) <= 1e-11
+
+
+def _prism(N=5, seed=8, keys=1):
+    r1, r2 = _random_shape(seed, N)
+    return dict(z0=0.3, z1=0.7, keys=[dict(c=C0, rho1=r1, rho2=r2)] * keys)
+
+
+def test_extrusion_of_equal_keys_is_a_capped_prism():
+    sh = _prism(keys=3)
+    k = sh["keys"][0]
+    # inside the slab, far from the caps: the cross-section's own distance
+    for xy in [(0.5, 0.45), (0.9, 0.1), (0.62, 0.4)]:
+        d2 = B.shape2d_sdf(k["c"], k["rho1"], k["rho2"], xy)
+        assert abs(B.extrude_sdf(sh, (*xy, 0.5)) - (d2 if d2 > -0.2 else -0.2)) <= 1e-12 \
+            or d2 < -0.2
+    # straight above the deep interior: the distance to the top cap
+    d2 = B.shape2d_sdf(k["c"], k["rho1"], k["rho2"], C0)
+    assert d2 < -0.1
+    for z in (0.75, 0.9):
+        assert abs(B.extrude_sdf(sh, (*C0, z)) - (z - 0.7)) <= 1e-12
+    # past a side wall and above the cap: the corner distance
+    x = (0.98, 0.45, 0.8)
+    d2 = B.shape2d_sdf(k["c"], k["rho1"], k["rho2"], x[:2])
+    assert abs(B.extrude_sdf(sh, x) - np.hypot(d2, 0.1)) <= 1e-12
+
+
+def test_extrusion_gradient_matches_finite_differences():
+    rng = np.random.default_rng(9)
+    keys = []
+    for _ in range(3):
+        keys.append(dict(c=C0 + rng.uniform(-0.03, 0.03, 2), rho1=rng.uniform(0.2, 0.3, 4),
+                         rho2=rng.uniform(0.2, 0.3, 4)))
+    sh = dict(z0=0.2, z1=0.8, keys=keys)
+    h = 1e-6
+    for x in [(0.6, 0.5, 0.35), (0.3, 0.4, 0.62), (0.55, 0.2, 0.5), (0.5, 0.5, 0.85)]:
+        _, g = B.extrude_sdf(sh, x, with_grad=True)
+        j = 0
+        for k in range(3):
+            for q in range(8):
+                sp = [dict(kk, rho1=np.array(kk["rho1"]), rho2=np.array(kk["rho2"])) for kk in keys]
+                sm = [dict(kk, rho1=np.array(kk["rho1"]), rho2=np.array(kk["rho2"])) for kk in keys]
+                name = "rho1" if q % 2 == 0 else "rho2"
+                sp[k][name][q // 2] += h
+                sm[k][name][q // 2] -= h
+                fd = (B.extrude_sdf(dict(sh, keys=sp), x) - B.extrude_sdf(dict(sh, keys=sm), x)) / (2 * h)
+                assert abs(fd - g[j]) <= 1e-7, (x, k, q)
+                j += 1
+
+
+def test_union_and_intersection_areas():
+    # two shapes: areas by sign counts obey inclusion-exclusion, and a union
+    # of two disjoint shapes has the sum of their enclosed areas
+    a1, a2 = _random_shape(10, 4)
+    m = 48
+    g = (np.arange(m) + 0.5) / m
+    ca, cb, cf = (0.3, 0.5), (0.45, 0.5), (1.3, 0.5)
+    sa = np.array([[B.shape2d_sdf(ca, 0.6 * a1, 0.6 * a2, (x, y)) for y in g] for x in g])
+    sb = np.array([[B.shape2d_sdf(cb, 0.6 * a2, 0.6 * a1, (x, y)) for y in g] for x in g])
+    u, i = B.union(sa, sb), B.intersection(sa, sb)
+    assert (u < 0).sum() + (i < 0).sum() == (sa < 0).sum() + (sb < 0).sum()
+    assert (i < 0).sum() > 0                              # they overlap
+    # the same shape twice, 1 apart along x, sampled on [0, 2] x [0, 1]
+    exact = _green_area(B.control_points(ca, 0.6 * a1, 0.6 * a2))
+    g2 = (np.arange(2 * m) + 0.5) / m
+    near = np.array([[B.shape2d_sdf(ca, 0.6 * a1, 0.6 * a2, (x, y)) for y in g] for x in g2])
+    far = np.array([[B.shape2d_sdf(cf, 0.6 * a1, 0.6 * a2, (x, y)) for y in g] for x in g2])
+    uf = B.union(near, far)
+    assert abs((uf < 0).sum() / m ** 2 - 2 * exact) <= 0.03 * 2 * exact
