@@ -119,6 +119,28 @@ def empty_scene():
     return dict(kind="none", theta=[])
 
 
+def extruded_scene(seed, *, shapes=1, segments=5, keys=2, fluid="outside",
+                   centre=(0.5, 0.5), radius=(0.14, 0.22), z=(0.3, 0.7)):
+    """Static polar-Bezier shapes extruded along z (seeded radii).
+
+    Each shape has ``keys`` key cross-sections of ``segments`` cubic
+    segments; ``theta`` lists every radius, shape by shape, key by key, as
+    rho1_0, rho2_0, rho1_1, ... . ``fluid`` says whether the fluid is outside
+    the shapes (obstacles) or inside them (containers).
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out, theta = [], []
+    for k in range(shapes):
+        cx = centre[0] + 0.12 * (k - (shapes - 1) / 2)
+        ks = []
+        for _ in range(keys):
+            r = rng.uniform(radius[0], radius[1], size=2 * segments)
+            theta += [float(v) for v in r]
+            ks.append(dict(c=[float(cx), float(centre[1])], nseg=int(segments)))
+        out.append(dict(z0=float(z[0]), z1=float(z[1]), keys=ks))
+    return dict(kind="extruded", theta=theta, shapes=out, fluid=str(fluid))
+
+
 def shell_scene(lo, hi, thickness, v):
     """Hollow axis-aligned box shell translating with velocity ``v``.
 

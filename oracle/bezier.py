@@ -23,6 +23,13 @@ even-odd count of the curve's crossings along a ray. The extrusion combines
 the cross-section distance at the point's z with the slab |z - zm| <= h in
 the usual capped form. CSG union and intersection are the min and max of the
 distances (Sec. 2.2).
+
+The scalar functions above are the definition. The many-point functions
+give every point its own interpolated cross-section. They find the
+closest parameter of each segment by Newton steps from the nearest of a few
+samples, and take the side from the outward normal at the closest point.
+This faster evaluation of the same distance serves the rasteriser, and the
+tests hold it to the scalar one.
 """
 
 from __future__ import annotations
@@ -209,3 +216,202 @@ def union(*sdfs):
 def intersection(*sdfs):
     """Intersection of shapes given by distances positive outside: the maximum."""
     return np.maximum.reduce([np.asarray(s, dtype=np.float64) for s in sdfs])
+
+
+# ------------------------------------------------- many points at once ----
+# The same quantities as shape2d_sdf for an array of points: the roots of
+# every point's quintic (and crossing cubic) are the eigenvalues of its
+# companion matrix, computed for all points in one batched call.
+
+def _batched_roots(coef):
+    """Roots (M, n) of the polynomials with ascending coefficients (M, n+1)
+    and a common nonzero leading coefficient."""
+    n = coef.shape[1] - 1
+    comp = np.zeros((coef.shape[0], n, n))
+    comp[:, 1:, :-1] = np.eye(n - 1)
+    comp[:, :, -1] = -coef[:, :-1] / coef[:, -1:]
+    return np.linalg.eigvals(comp)
+
+
+def shape2d_sdf_many(c, rho1, rho2, X, with_grad=False):
+    """shape2d_sdf over points X (M, 2): distances (M,) and optionally the
+    radius gradients (M, 2N)."""
+    X = np.asarray(X, dtype=np.float64)
+    C = control_points(c, rho1, rho2)
+    N = len(C)
+    M = X.shape[0]
+    best_d = np.full(M, np.inf)
+    best_i = np.zeros(M, dtype=int)
+    best_s = np.zeros(M)
+    cross = np.zeros(M, dtype=int)
+    for i in range(N):
+        a = _power(C[i])
+        db = np.array([a[1], 2 * a[2], 3 * a[3]])
+        q = np.zeros((M, 6))
+        for p in range(4):
+            bp = (a[p] - X) if p == 0 else np.broadcast_to(a[p], X.shape)
+            for j in range(3):
+                q[:, p + j] += bp @ db[j]
+        cand = np.concatenate([np.zeros((M, 1)), np.ones((M, 1)), np.full((M, 5), np.nan)], axis=1)
+        if abs(q[0, 5]) > 0.0:
+            r = _batched_roots(q)
+            ok = (np.abs(r.imag) < 1e-9) & (r.real > 0.0) & (r.real < 1.0)
+            cand[:, 2:] = np.where(ok, r.real, np.nan)
+        else:                               # degenerate segment: one point at a time
+            for m in range(M):
+                _, s = closest_on_segment(C[i], X[m])
+                cand[m, 2] = s
+        pts = np.einsum("mkr,rx->mkx", bernstein(np.nan_to_num(cand, nan=0.0)), C[i])
+        dist = np.linalg.norm(pts - X[:, None, :], axis=-1)
+        dist = np.where(np.isnan(cand), np.inf, dist)
+        k = np.argmin(dist, axis=1)
+        dmin = dist[np.arange(M), k]
+        better = dmin < best_d
+        best_d = np.where(better, dmin, best_d)
+        best_i = np.where(better, i, best_i)
+        best_s = np.where(better, cand[np.arange(M), k], best_s)
+        # even-odd crossings of the ray towards +x
+        cy = np.stack([np.full(M, a[0][1]) - X[:, 1], np.full(M, a[1][1]),
+                       np.full(M, a[2][1]), np.full(M, a[3][1])], axis=1)
+        if a[3][1] != 0.0:
+            r = _batched_roots(cy)
+            ok = (np.abs(r.imag) < 1e-12) & (r.real >= 0.0) & (r.real < 1.0)
+            s = np.where(ok, r.real, 0.0)
+            bx = np.einsum("mkr,r->mk", bernstein(s), C[i][:, 0])
+            cross += np.sum(ok & (bx > X[:, :1]), axis=1)
+        else:
+            cross += np.array([_crossings(C[i], X[m]) for m in range(M)])
+    inside = cross % 2 == 1
+    sd = np.where(inside, -best_d, best_d)
+    if not with_grad:
+        return sd
+    # the envelope gradient of shape2d_sdf, for all points at once
+    seg = np.minimum(best_i, N - 1)
+    foot = np.einsum("mr,mrx->mx", bernstein(best_s), C[seg])
+    nrm = np.where(best_d[:, None] > 0.0, (X - foot) / np.where(best_d > 0.0, best_d, 1.0)[:, None], 0.0)
+    base = 2.0 * np.pi * np.arange(N) / N
+    ang = np.empty(2 * N)
+    ang[0::2] = base + 2.0 * np.pi / (3.0 * N)
+    ang[1::2] = base + 4.0 * np.pi / (3.0 * N)
+    U = np.stack([np.cos(ang), np.sin(ang)], axis=-1)          # (2N, 2)
+    nu = nrm @ U.T                                             # (M, 2N)
+    w = bernstein(best_s)                                      # (M, 4)
+    J = control_jacobian(N)
+    grad = np.zeros((M, 2 * N))
+    for r in range(4):
+        grad -= nu * w[:, r:r + 1] * J[seg, r, :]
+    grad = np.where(inside[:, None], -grad, grad)
+    return sd, grad
+
+
+def _controls_per_point(c, r1, r2):
+    """Control polygons (M, N, 4, 2) from per-point centres (M, 2) and radii
+    (M, N): the construction of control_points for every point."""
+    N = r1.shape[1]
+    base = 2.0 * np.pi * np.arange(N) / N
+    a0 = base + 2.0 * np.pi / (3.0 * N)
+    a1 = base + 4.0 * np.pi / (3.0 * N)
+    p0 = c[:, None, :] + r1[..., None] * np.stack([np.cos(a0), np.sin(a0)], axis=-1)
+    p1 = c[:, None, :] + r2[..., None] * np.stack([np.cos(a1), np.sin(a1)], axis=-1)
+    e0 = 0.5 * (np.roll(p1, 1, axis=1) + p0)
+    e1 = np.roll(e0, -1, axis=1)
+    return np.stack([e0, p0, p1, e1], axis=2)
+
+
+def _sdf2d_points(Cp, X, samples=24, newton=5):
+    """Outside-positive distance of each point X[m] to its own closed curve
+    Cp[m], with the closest segment, parameter and the inside flag.
+
+    The closest parameter of each segment starts at the nearest of
+    ``samples`` evenly spaced ones and is refined by Newton steps on
+    (B - x) . B' = 0, kept in [0, 1]. The side comes from the outward normal
+    at the closest point (the curve turns counter-clockwise: radii at
+    increasing polar angles). This is a faster evaluation of the same
+    distance as shape2d_sdf, which checks it."""
+    M, N = Cp.shape[:2]
+    rows = np.arange(M)
+    s0 = np.linspace(0.0, 1.0, samples)
+    Bs = bernstein(s0)                                          # (S, 4)
+    best_d = np.full(M, np.inf)
+    best_i = np.zeros(M, dtype=int)
+    best_s = np.zeros(M)
+    for i in range(N):
+        P = Cp[:, i]                                            # (M, 4, 2)
+        pts = Bs @ P                                            # (M, S, 2)
+        k = np.argmin(np.sum((pts - X[:, None, :]) ** 2, axis=-1), axis=1)
+        sv = s0[k]
+        e0, p0, p1, e1 = (P[:, r] for r in range(4))
+        for _ in range(newton):
+            u = 1.0 - sv
+            B = (u ** 3)[:, None] * e0 + (3 * u * u * sv)[:, None] * p0 \
+                + (3 * u * sv * sv)[:, None] * p1 + (sv ** 3)[:, None] * e1
+            d1 = (3 * u * u)[:, None] * (p0 - e0) + (6 * u * sv)[:, None] * (p1 - p0) \
+                + (3 * sv * sv)[:, None] * (e1 - p1)
+            d2 = (6 * u)[:, None] * (p1 - 2 * p0 + e0) + (6 * sv)[:, None] * (e1 - 2 * p1 + p0)
+            r = B - X
+            f1 = np.sum(r * d1, axis=1)
+            f2 = np.sum(d1 * d1, axis=1) + np.sum(r * d2, axis=1)
+            step = np.where(f2 > 0.0, f1 / np.where(f2 > 0.0, f2, 1.0), 0.0)
+            sv = np.clip(sv - step, 0.0, 1.0)
+        dist = np.linalg.norm((bernstein(sv)[:, None, :] @ P)[:, 0] - X, axis=1)
+        better = dist < best_d
+        best_d = np.where(better, dist, best_d)
+        best_i = np.where(better, i, best_i)
+        best_s = np.where(better, sv, best_s)
+    P = Cp[rows, best_i]
+    u, sv = 1.0 - best_s, best_s
+    foot = np.einsum("mr,mrx->mx", bernstein(best_s), P)
+    tan = (3 * u * u)[:, None] * (P[:, 1] - P[:, 0]) + (6 * u * sv)[:, None] * (P[:, 2] - P[:, 1]) \
+        + (3 * sv * sv)[:, None] * (P[:, 3] - P[:, 2])
+    outward = np.stack([tan[:, 1], -tan[:, 0]], axis=1)         # right of a CCW tangent
+    inside = np.sum((X - foot) * outward, axis=1) < 0.0
+    return np.where(inside, -best_d, best_d), best_d, best_i, best_s, inside
+
+
+def extrude_sdf_many(shape, X, with_grad=False):
+    """extrude_sdf over points X (M, 3): every point gets its own
+    interpolated cross-section."""
+    X = np.asarray(X, dtype=np.float64)
+    keys = shape["keys"]
+    n = len(keys)
+    z0, z1 = float(shape["z0"]), float(shape["z1"])
+    zm, h = 0.5 * (z0 + z1), 0.5 * (z1 - z0)
+    M = X.shape[0]
+    u = np.clip((X[:, 2] - z0) / (z1 - z0), 0.0, 1.0)
+    if n == 1:
+        W = np.ones((M, 1))
+    else:
+        uk = np.arange(n) / (n - 1)
+        coeff = np.linalg.solve(np.vander(uk, n, increasing=True), np.eye(n))
+        W = (u[:, None] ** np.arange(n)) @ coeff               # (M, n)
+    kc = np.array([np.asarray(k["c"], dtype=np.float64) for k in keys])      # (n, 2)
+    k1 = np.array([np.asarray(k["rho1"], dtype=np.float64) for k in keys])   # (n, N)
+    k2 = np.array([np.asarray(k["rho2"], dtype=np.float64) for k in keys])
+    c, r1, r2 = W @ kc, W @ k1, W @ k2
+    Cp = _controls_per_point(c, r1, r2)
+    d, dist, seg, sbest, inside = _sdf2d_points(Cp, X[:, :2])
+    w = np.abs(X[:, 2] - zm) - h
+    nrm = np.hypot(np.maximum(d, 0.0), np.maximum(w, 0.0))
+    out = np.minimum(np.maximum(d, w), 0.0) + nrm
+    if not with_grad:
+        return out
+    N = r1.shape[1]
+    foot = np.einsum("mr,mrx->mx", bernstein(sbest), Cp[np.arange(M), seg])
+    nv = np.where(dist[:, None] > 0.0, (X[:, :2] - foot) / np.where(dist > 0.0, dist, 1.0)[:, None], 0.0)
+    base = 2.0 * np.pi * np.arange(N) / N
+    ang = np.empty(2 * N)
+    ang[0::2] = base + 2.0 * np.pi / (3.0 * N)
+    ang[1::2] = base + 4.0 * np.pi / (3.0 * N)
+    U = np.stack([np.cos(ang), np.sin(ang)], axis=-1)
+    nu = nv @ U.T
+    bw = bernstein(sbest)
+    J = control_jacobian(N)
+    g2 = np.zeros((M, 2 * N))
+    for r in range(4):
+        g2 -= nu * bw[:, r:r + 1] * J[seg, r, :]
+    g2 = np.where(inside[:, None], -g2, g2)
+    both_in = (d <= 0.0) & (w <= 0.0)
+    dd = np.where(both_in, (d >= w).astype(np.float64),
+                  np.maximum(d, 0.0) / np.where(nrm > 0.0, nrm, 1.0))
+    grad = np.concatenate([(dd * W[:, k])[:, None] * g2 for k in range(n)], axis=1)
+    return out, grad

@@ -19,6 +19,8 @@ from __future__ import annotations
 
 import numpy as np
 
+from . import bezier
+
 FAR = 1.0e3   # phi of a scene without solid: every ramp sample saturates to 1
 
 
@@ -121,6 +123,50 @@ def _shell_parts(scene, x, t):
     return x - c, h_out, h_in
 
 
+def _extruded(scene, x, with_grad):
+    """Outside-positive distance to each shape of an ``extruded`` scene (and
+    gradients in theta), theta holding every radius shape by shape, key by
+    key (rho1_0, rho2_0, rho1_1, ...)."""
+    th = np.asarray(scene["theta"], dtype=np.float64)
+    X = x.reshape(-1, 3)
+    dists, grads, j = [], [], 0
+    for sh in scene["shapes"]:
+        keys = []
+        for k in sh["keys"]:
+            n = int(k["nseg"])
+            r = th[j:j + 2 * n]
+            keys.append(dict(c=k["c"], rho1=r[0::2], rho2=r[1::2]))
+            j += 2 * n
+        shape = dict(z0=sh["z0"], z1=sh["z1"], keys=keys)
+        if with_grad:
+            d, g = bezier.extrude_sdf_many(shape, X, with_grad=True)
+            grads.append(g)
+        else:
+            d = bezier.extrude_sdf_many(shape, X)
+        dists.append(d)
+    return dists, grads
+
+
+def _extruded_phi(scene, x, with_grad=False):
+    """phi > 0 in the fluid: outside the union of the shapes (obstacles) or
+    inside it (containers): CSG union is the min of the distances."""
+    dists, grads = _extruded(scene, x, with_grad)
+    D = np.stack(dists)                                   # (shapes, M)
+    a = np.argmin(D, axis=0)
+    sgn = 1.0 if scene["fluid"] == "outside" else -1.0
+    ph = sgn * D[a, np.arange(D.shape[1])]
+    if not with_grad:
+        return ph.reshape(x.shape[:-1])
+    K = len(scene["theta"])
+    G = np.zeros((D.shape[1], K))
+    j = 0
+    for s_, g in enumerate(grads):
+        sel = a == s_
+        G[sel, j:j + g.shape[1]] = sgn * g[sel]
+        j += g.shape[1]
+    return ph.reshape(x.shape[:-1]), G.reshape(x.shape[:-1] + (K,))
+
+
 # ------------------------------------------------------------ dispatch -----
 
 def phi(scene, x, t):
@@ -146,6 +192,8 @@ def phi(scene, x, t):
     if kind == "shell":
         p, ho, hi = _shell_parts(scene, x, t)
         return np.maximum(box_sdf(p, ho), -box_sdf(p, hi))
+    if kind == "extruded":
+        return _extruded_phi(scene, x)
     raise ValueError(kind)
 
 
@@ -192,6 +240,8 @@ def dphi_dtheta(scene, x, t):
         g = np.where((so >= si)[..., None], box_sdf_grad(p, ho),
                      -box_sdf_grad(p, hi))
         return -t * g
+    if kind == "extruded":
+        return _extruded_phi(scene, x, with_grad=True)[1]
     raise ValueError(kind)
 
 

@@ -209,3 +209,87 @@ def test_union_and_intersection_areas():
     far = np.array([[B.shape2d_sdf(cf, 0.6 * a1, 0.6 * a2, (x, y)) for y in g] for x in g2])
     uf = B.union(near, far)
     assert abs((uf < 0).sum() / m ** 2 - 2 * exact) <= 0.03 * 2 * exact
+
+
+def test_batched_evaluation_equals_the_point_by_point_one():
+    r1, r2 = _random_shape(11, 6)
+    rng = np.random.default_rng(12)
+    X = rng.uniform(0.0, 1.0, size=(200, 2))
+    sd, g = B.shape2d_sdf_many(C0, r1, r2, X, with_grad=True)
+    for m in range(len(X)):
+        d1, g1 = B.shape2d_sdf(C0, r1, r2, X[m], with_grad=True)
+        assert abs(sd[m] - d1) <= 1e-12
+        np.testing.assert_allclose(g[m], g1, atol=1e-10)
+    keys = [dict(c=C0, rho1=r1, rho2=r2), dict(c=(0.52, 0.47), rho1=0.9 * r2, rho2=1.1 * r1)]
+    sh = dict(z0=0.25, z1=0.75, keys=keys)
+    X3 = np.concatenate([X[:40], rng.choice([0.1, 0.3, 0.5, 0.8], size=(40, 1))], axis=1)
+    e, ge = B.extrude_sdf_many(sh, X3, with_grad=True)
+    for m in range(len(X3)):
+        e1, ge1 = B.extrude_sdf(sh, X3[m], with_grad=True)
+        assert abs(e[m] - e1) <= 1e-12
+        np.testing.assert_allclose(ge[m], ge1, atol=1e-10)
+
+
+def test_sampled_newton_evaluation_equals_the_exact_one():
+    # the rasteriser's evaluation (samples + Newton, normal side) against the
+    # exact one (quintic roots, even-odd side), near and far from the curve
+    rng = np.random.default_rng(13)
+    keys = [dict(c=C0, rho1=rng.uniform(0.15, 0.3, 5), rho2=rng.uniform(0.15, 0.3, 5)),
+            dict(c=(0.47, 0.5), rho1=rng.uniform(0.15, 0.3, 5), rho2=rng.uniform(0.15, 0.3, 5))]
+    sh = dict(z0=0.2, z1=0.8, keys=keys)
+    X = np.concatenate([rng.uniform(0.0, 1.0, size=(300, 2)), rng.uniform(0.1, 0.9, (300, 1))], 1)
+    # points within 1e-3 of the curve: move random points onto it and off by a little
+    k = keys[0]
+    C = B.control_points(k["c"], k["rho1"], k["rho2"])
+    near = np.array([B.bezier(C[rng.integers(5)], rng.uniform()) for _ in range(100)])
+    near += rng.uniform(-1e-3, 1e-3, near.shape)
+    X = np.concatenate([X, np.concatenate([near, np.full((100, 1), 0.2)], 1)])
+    e, ge = B.extrude_sdf_many(sh, X, with_grad=True)
+    for m in range(len(X)):
+        e1, ge1 = B.extrude_sdf(sh, X[m], with_grad=True)
+        assert abs(e[m] - e1) <= 1e-12, (m, X[m])
+        np.testing.assert_allclose(ge[m], ge1, atol=1e-9)
+
+
+# ------------------------------------------------ the extruded scene ----
+
+def _prism_volume(sc):
+    sh = sc["shapes"][0]
+    th = np.asarray(sc["theta"])
+    return _green_area(B.control_points(sh["keys"][0]["c"], th[0::2], th[1::2])) * (sh["z1"] - sh["z0"])
+
+
+def test_extruded_obstacle_fluid_volume():
+    import nf_inputs as I
+    from oracle import Grid, rasterize
+    sc = I.extruded_scene(3, shapes=1, keys=1)
+    g = Grid(I.make_grid(8, 0.01))
+    a = rasterize.fractions(g, sc, 0.0)
+    # interior x-face control volumes cover [dx/2, 1 - dx/2] along x
+    vol = a[0][:, :, 1:-1].sum() * g.dx ** 3
+    V = _prism_volume(sc)
+    assert abs(vol - ((1.0 - g.dx) - V)) <= 0.015 * V
+
+
+@pytest.mark.parametrize("rule,n", [("corner", 10), ("supersample", 8)])
+def test_extruded_scene_fraction_gradient_matches_finite_differences(rule, n):
+    import nf_inputs as I
+    from oracle import Grid, rasterize
+    sc = I.extruded_scene(4, shapes=2, keys=2)
+    g = Grid(dict(I.make_grid(n, 0.01), fractions=rule))
+    _, dalpha = rasterize.fractions(g, sc, 0.0, with_grad=True)
+    th = np.asarray(sc["theta"])
+    rng = np.random.default_rng(14)
+    w = [rng.standard_normal(g.face_shape(d)) for d in range(3)]
+    h = 1e-6
+    # a radius of each key of the two shapes (one for the slower rule)
+    for k in ((0, 13, 27) if rule == "corner" else (27,)):
+        tp, tm = th.copy(), th.copy()
+        tp[k] += h
+        tm[k] -= h
+        ap = rasterize.fractions(g, dict(sc, theta=list(tp)), 0.0)
+        am = rasterize.fractions(g, dict(sc, theta=list(tm)), 0.0)
+        fd = sum(np.sum(w[d] * (ap[d] - am[d])) for d in range(3)) / (2 * h)
+        an = sum(np.sum(w[d] * dalpha[d][..., k]) for d in range(3))
+        assert abs(fd - an) <= 1e-5 * max(1.0, abs(an)), (k, fd, an)
+        assert abs(an) > 1e-3
