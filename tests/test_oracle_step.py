@@ -134,6 +134,22 @@ def test_rollout_gradient_matches_central_differences(name):
     assert err < 1e-3, (g_adj, g_fd)
 
 
+def test_extruded_obstacle_rollout_gradient_matches_central_differences():
+    # polar-Bezier obstacles (App. A), corner fractions: the adjoint of a
+    # two-step rollout against central differences in two of the radii
+    g = I.make_grid(10, 0.01, nz=10)
+    g["fractions"] = "corner"
+    cfg = dict(name="extruded10", grid=g, scene=I.extruded_scene(4, shapes=2, keys=2),
+               u0=I.gaussian_faces(g, 0.1, 21), project_initial=True, steps=2, tol=1e-12,
+               loss="kinetic_energy")
+    J, g_adj, _ = S.loss_and_grad(cfg, tol=1e-12)
+    which = [0, 27]
+    g_fd = S.fd_gradient(cfg, h=1e-5, tol=1e-12, which=which)
+    for k in which:
+        assert abs(g_adj[k] - g_fd[k]) <= 2e-3 * np.abs(g_fd[which]).max(), (k, g_adj[k], g_fd[k])
+    assert np.abs(g_fd[which]).max() > 0.0
+
+
 def _active_boundary_flux(g, alpha, us):
     """sum over faces with exactly one active neighbour (outlet excluded) of
     (a_high - a_low) u_s: by incompressibility this equals the outflow."""
