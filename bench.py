@@ -377,6 +377,7 @@ def run_ours(args, rank, world, local_rank):
         out["e2e"] = run_e2e(args, torch, cfg, dev, ep)
         out["fp64_plain"] = run_plain(args, P, torch, dev)
         out["cpu_baseline"] = cpu_baseline(args)
+        out["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores(args)
     ep.close()
     ctx.close()
     return out
@@ -478,6 +479,30 @@ def cpu_baseline(args):
                        f"cell-step; a coarser grid needs fewer CG iterations, so this "
                        f"flatters the oracle",
                 seconds=dt)
+
+
+def cpu_baseline_all_cores(args, procs=None):
+    """The same oracle sample run by ``procs`` one-thread interpreters at once
+    (default: one per host CPU, at most 8): independent episodes, as the
+    replicas of the GPU run. value = procs x cells / the slowest sample's
+    time."""
+    n = args.cpu_n
+    P = procs or max(1, min(os.cpu_count() or 1, 8))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
+               MKL_NUM_THREADS="1", NUMEXPR_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", "--cpu-n", str(n)]
+    t0 = time.perf_counter()
+    ps = [subprocess.Popen(cmd, env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                           text=True) for _ in range(P)]
+    outs = [p.communicate(timeout=1800) for p in ps]
+    wall = time.perf_counter() - t0
+    for p, (_, err) in zip(ps, outs):
+        if p.returncode != 0:
+            raise RuntimeError(f"CPU oracle sample failed: {err[-2000:]}")
+    dts = [float(o.strip().splitlines()[-1]) for o, _ in outs]
+    return dict(value=P * n ** 3 / max(dts), unit=UNIT, cores=P, host_cpus=os.cpu_count(),
+                kind="oracle", seconds=max(dts), wall_seconds=wall,
+                sample=f"{P} concurrent one-thread copies of the {n}^3 sample")
 
 
 # -------------------------------------------------------------- serving ----

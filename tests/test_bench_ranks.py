@@ -59,3 +59,14 @@ def test_single_rank_defaults():
     assert bench.ranks_from_env({}) == (1, 0, 0)
     assert bench.max_over_ranks(12.5, 1) == 12.5
     assert bench.whole_job_value(1, 1000, 10, 1000.0) == 10000.0
+
+
+def test_cpu_baseline_one_thread_and_all_cores_on_a_small_sample():
+    import argparse
+    args = argparse.Namespace(cpu_n=10)
+    one = bench.cpu_baseline(args)
+    many = bench.cpu_baseline_all_cores(args, procs=2)
+    assert one["cores"] == 1 and many["cores"] == 2
+    assert one["value"] > 0 and many["value"] > 0
+    # two independent copies: at most twice the one-thread rate, up to timing noise
+    assert many["value"] <= 2.0 * one["value"] * 1.5
