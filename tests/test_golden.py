@@ -11,7 +11,7 @@ import os
 import numpy as np
 import pytest
 
-from tests.golden.make_golden import CASES, compute
+from tests.golden.make_golden import CASES, ORACLE_CASES, compute
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 with open(os.path.join(HERE, "golden", "oracle_small.json")) as f:
@@ -23,7 +23,7 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("name", sorted(CASES) + sorted(ORACLE_CASES))
 def test_oracle_reproduces_stored_values(name):
     got = compute(name)
     ref = GOLDEN[name]
