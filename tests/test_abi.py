@@ -117,3 +117,23 @@ def test_server_rejects_bad_arguments_without_a_device(lib):
     assert lib.nf_server_poll(None, 1, 0, ctypes.byref(r)) == _lib.NF_E_INVALID
     assert lib.nf_server_drain(None, 0) == _lib.NF_E_INVALID
     assert lib.nf_server_destroy(None) == _lib.NF_E_INVALID
+
+
+def test_grid_marshalling_of_viscosity_and_fraction_rule():
+    # host-side marshalling of nf_grid (no device): nu and the fraction rule
+    # reach the struct with the header's codes; what the library cannot run
+    # is refused before any call
+    import nf_inputs as I
+    from paper_2405_14903_b300 import _lib
+    from paper_2405_14903_b300.api import grid_struct
+    src = open(HEADER).read()
+    codes = dict(re.findall(r"#define NF_FRACTIONS_([A-Z]+) (\d+)", src))
+    assert {k.lower(): int(v) for k, v in codes.items()} == _lib.FRACTIONS
+    g = grid_struct(dict(I.make_grid(8, 0.01, nu=0.03), fractions="corner"))
+    assert g.nu == 0.03 and g.fractions == _lib.FRACTIONS["corner"]
+    g = grid_struct(I.make_grid(8, 0.01))
+    assert g.nu == 0.0 and g.fractions == _lib.FRACTIONS["supersample"]
+    with pytest.raises(ValueError):
+        grid_struct(dict(I.make_grid(8, 0.01), fractions="marching"))
+    with pytest.raises(ValueError):
+        grid_struct(I.make_grid(8, 0.01, periodic=True))
