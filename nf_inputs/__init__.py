@@ -141,6 +141,44 @@ def extruded_scene(seed, *, shapes=1, segments=5, keys=2, fluid="outside",
     return dict(kind="extruded", theta=theta, shapes=out, fluid=str(fluid))
 
 
+def _frame(origin, z_dir):
+    """A rigid frame whose local z is the unit vector along ``z_dir``."""
+    z = np.asarray(z_dir, dtype=np.float64)
+    z = z / np.linalg.norm(z)
+    a = np.array([1.0, 0.0, 0.0]) if abs(z[0]) < 0.9 else np.array([0.0, 1.0, 0.0])
+    x = np.cross(a, z)
+    x /= np.linalg.norm(x)
+    y = np.cross(z, x)
+    return dict(origin=[float(v) for v in origin], axes=[list(map(float, r)) for r in (x, y, z)])
+
+
+def heart_scene(seed, *, segments=5):
+    """A heart-like container: the union of a chamber and three tubes (two
+    inlets from the top, one outlet to the side), each an extruded
+    polar-Bezier shape in its own frame, the fluid inside the union.
+
+    theta lists every radius (chamber keys, then each tube's keys)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    shapes, theta = [], []
+
+    def add(frame, z0, z1, centre, radius, keys):
+        ks = []
+        for _ in range(keys):
+            r = rng.uniform(radius[0], radius[1], size=2 * segments)
+            theta.extend(float(v) for v in r)
+            ks.append(dict(c=[float(centre[0]), float(centre[1])], nseg=int(segments)))
+        sh = dict(z0=float(z0), z1=float(z1), keys=ks)
+        if frame is not None:
+            sh["frame"] = frame
+        shapes.append(sh)
+
+    add(None, 0.3, 0.7, (0.5, 0.5), (0.16, 0.22), 3)                   # chamber
+    add(_frame((0.42, 0.5, 0.5), (-0.3, 0.0, 1.0)), 0.0, 0.45, (0.0, 0.0), (0.05, 0.06), 2)
+    add(_frame((0.58, 0.5, 0.5), (0.3, 0.0, 1.0)), 0.0, 0.45, (0.0, 0.0), (0.05, 0.06), 2)
+    add(_frame((0.5, 0.5, 0.45), (0.0, 1.0, 0.0)), 0.0, 0.45, (0.0, 0.0), (0.06, 0.07), 2)
+    return dict(kind="extruded", theta=theta, shapes=shapes, fluid="inside")
+
+
 def shell_scene(lo, hi, thickness, v):
     """Hollow axis-aligned box shell translating with velocity ``v``.
 

@@ -126,11 +126,19 @@ def _shell_parts(scene, x, t):
 def _extruded(scene, x, with_grad):
     """Outside-positive distance to each shape of an ``extruded`` scene (and
     gradients in theta), theta holding every radius shape by shape, key by
-    key (rho1_0, rho2_0, rho1_1, ...)."""
+    key (rho1_0, rho2_0, rho1_1, ...). A shape may carry a rigid local frame
+    ``frame = dict(origin, axes)`` (axes: rows are the local x, y, z in world
+    coordinates, orthonormal); it is extruded along its local z, and a world
+    point x is measured at axes (x - origin), which keeps distances."""
     th = np.asarray(scene["theta"], dtype=np.float64)
-    X = x.reshape(-1, 3)
+    Xw = x.reshape(-1, 3)
     dists, grads, j = [], [], 0
     for sh in scene["shapes"]:
+        fr = sh.get("frame")
+        if fr is None:
+            X = Xw
+        else:
+            X = (Xw - np.asarray(fr["origin"], dtype=np.float64)) @ np.asarray(fr["axes"]).T
         keys = []
         for k in sh["keys"]:
             n = int(k["nseg"])

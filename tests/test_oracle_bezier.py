@@ -293,3 +293,60 @@ def test_extruded_scene_fraction_gradient_matches_finite_differences(rule, n):
         an = sum(np.sum(w[d] * dalpha[d][..., k]) for d in range(3))
         assert abs(fd - an) <= 1e-5 * max(1.0, abs(an)), (k, fd, an)
         assert abs(an) > 1e-3
+
+
+# ------------------------------------------------ shapes in own frames ----
+
+def _one_shape_scene(shape, r, fluid="outside"):
+    return dict(kind="extruded", theta=list(r), shapes=[shape], fluid=fluid)
+
+
+def test_a_framed_shape_is_the_unframed_one_in_local_coordinates():
+    # frame rows: local x = world y, local y = world z, local z = world x
+    # (a cyclic permutation, whose transpose is a different map)
+    from oracle import geometry
+    rng = np.random.default_rng(15)
+    r = rng.uniform(0.1, 0.2, 10)
+    base = dict(z0=0.2, z1=0.8, keys=[dict(c=[0.5, 0.45], nseg=5)])
+    framed = dict(base, frame=dict(origin=[0.0, 0.0, 0.0],
+                                   axes=[[0, 1, 0], [0, 0, 1], [1, 0, 0]]))
+    X = rng.uniform(0.0, 1.0, size=(200, 3))
+    a = geometry.phi(_one_shape_scene(framed, r), X, 0.0)
+    b = geometry.phi(_one_shape_scene(base, r), X[:, [1, 2, 0]], 0.0)
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-13)
+
+
+def test_distance_is_constant_along_a_tilted_tube_axis():
+    import nf_inputs as I
+    from oracle import geometry
+    rng = np.random.default_rng(16)
+    r = rng.uniform(0.05, 0.07, 10)
+    fr = I._frame((0.3, 0.4, 0.2), (1.0, 2.0, 2.0))
+    tube = dict(z0=0.0, z1=0.6, keys=[dict(c=[0.0, 0.0], nseg=5)], frame=fr)
+    d = np.asarray(fr["axes"][2])
+    pts = np.asarray(fr["origin"]) + np.outer(np.linspace(0.15, 0.45, 7), d)
+    ph = geometry.phi(_one_shape_scene(tube, r, fluid="inside"), pts, 0.0)
+    assert np.all(ph > 0.03)
+    assert np.ptp(ph) <= 1e-13
+
+
+def test_heart_scene_fraction_gradient_matches_finite_differences():
+    import nf_inputs as I
+    from oracle import Grid, rasterize
+    sc = I.heart_scene(2)
+    g = Grid(dict(I.make_grid(12, 0.01), fractions="corner"))
+    _, dalpha = rasterize.fractions(g, sc, 0.0, with_grad=True)
+    th = np.asarray(sc["theta"])
+    rng = np.random.default_rng(17)
+    w = [rng.standard_normal(g.face_shape(d)) for d in range(3)]
+    h = 1e-6
+    for k in (3, 30, 75):            # a chamber radius, an inlet's, the outlet's
+        tp, tm = th.copy(), th.copy()
+        tp[k] += h
+        tm[k] -= h
+        ap = rasterize.fractions(g, dict(sc, theta=list(tp)), 0.0)
+        am = rasterize.fractions(g, dict(sc, theta=list(tm)), 0.0)
+        fd = sum(np.sum(w[d] * (ap[d] - am[d])) for d in range(3)) / (2 * h)
+        an = sum(np.sum(w[d] * dalpha[d][..., k]) for d in range(3))
+        assert abs(fd - an) <= 1e-5 * max(1.0, abs(an)), (k, fd, an)
+        assert abs(an) > 1e-4, k
