@@ -137,3 +137,30 @@ def test_grid_marshalling_of_viscosity_and_fraction_rule():
         grid_struct(dict(I.make_grid(8, 0.01), fractions="marching"))
     with pytest.raises(ValueError):
         grid_struct(I.make_grid(8, 0.01, periodic=True))
+
+
+def test_struct_field_offsets_match_the_header(tmp_path):
+    # every field of every ctypes mirror sits at the offset the C compiler
+    # gives the header's field of the same name (catches reordered fields that
+    # keep the total size)
+    from paper_2405_14903_b300 import _lib
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no host C compiler")
+    mirrors = {"nf_config": _lib.Config, "nf_grid": _lib.Grid, "nf_scene": _lib.Scene,
+               "nf_step_stats": _lib.StepStats, "nf_request": _lib.Request,
+               "nf_result": _lib.Result, "nf_server_stats": _lib.ServerStats}
+    lines, want = [], []
+    for cname, cls in mirrors.items():
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({cname}, {fname}));')
+            want.append((cname, fname, getattr(cls, fname).offset))
+    src = tmp_path / "off.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "nf.h"\nint main(void){'
+                   + "".join(lines) + "return 0;}\n")
+    exe = tmp_path / "off"
+    subprocess.check_call([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    assert len(got) == len(want)
+    for g, (cname, fname, off) in zip(got, want):
+        assert g == off, (cname, fname, g, off)
