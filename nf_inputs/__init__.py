@@ -152,21 +152,28 @@ def _frame(origin, z_dir):
     return dict(origin=[float(v) for v in origin], axes=[list(map(float, r)) for r in (x, y, z)])
 
 
-def heart_scene(seed, *, segments=5):
+def heart_scene(seed, *, segments=5, pulse_period=None, outlet=False):
     """A heart-like container: the union of a chamber and three tubes (two
-    inlets from the top, one outlet to the side), each an extruded
-    polar-Bezier shape in its own frame, the fluid inside the union.
+    inlets from the top, one outlet), each an extruded polar-Bezier shape in
+    its own frame, the fluid inside the union.
 
-    theta lists every radius (chamber keys, then each tube's keys)."""
+    Static (default): theta lists every radius (chamber keys, then each
+    tube's keys). With ``pulse_period`` the chamber contracts: its radii are
+    k(t) times seeded base radii, k piecewise linear through 4 knots at t =
+    0, T/3, 2T/3, T, and theta is those 4 knots (seeded near 1). With
+    ``outlet`` the outlet tube runs along +x through the high-x wall (pair it
+    with an outlet patch there); otherwise it ends inside the box.
+    """
     rng = np.random.Generator(np.random.PCG64(seed))
-    shapes, theta = [], []
+    shapes, radii = [], []
 
     def add(frame, z0, z1, centre, radius, keys):
         ks = []
         for _ in range(keys):
             r = rng.uniform(radius[0], radius[1], size=2 * segments)
-            theta.extend(float(v) for v in r)
-            ks.append(dict(c=[float(centre[0]), float(centre[1])], nseg=int(segments)))
+            radii.extend(float(v) for v in r)
+            ks.append(dict(c=[float(centre[0]), float(centre[1])], nseg=int(segments),
+                           rho=[float(v) for v in r]))
         sh = dict(z0=float(z0), z1=float(z1), keys=ks)
         if frame is not None:
             sh["frame"] = frame
@@ -175,8 +182,18 @@ def heart_scene(seed, *, segments=5):
     add(None, 0.3, 0.7, (0.5, 0.5), (0.16, 0.22), 3)                   # chamber
     add(_frame((0.42, 0.5, 0.5), (-0.3, 0.0, 1.0)), 0.0, 0.45, (0.0, 0.0), (0.05, 0.06), 2)
     add(_frame((0.58, 0.5, 0.5), (0.3, 0.0, 1.0)), 0.0, 0.45, (0.0, 0.0), (0.05, 0.06), 2)
-    add(_frame((0.5, 0.5, 0.45), (0.0, 1.0, 0.0)), 0.0, 0.45, (0.0, 0.0), (0.06, 0.07), 2)
-    return dict(kind="extruded", theta=theta, shapes=shapes, fluid="inside")
+    if outlet:
+        add(_frame((0.5, 0.5, 0.5), (1.0, 0.0, 0.0)), 0.0, 0.65, (0.0, 0.0), (0.10, 0.11), 2)
+    else:
+        add(_frame((0.5, 0.5, 0.45), (0.0, 1.0, 0.0)), 0.0, 0.45, (0.0, 0.0), (0.06, 0.07), 2)
+    sc = dict(kind="extruded", shapes=shapes, fluid="inside")
+    if pulse_period is None:
+        sc["theta"] = radii
+    else:
+        sc["theta"] = [float(v) for v in rng.uniform(0.85, 1.0, size=4)]
+        sc["params"] = "pulse"
+        sc["pulse"] = dict(shape=0, period=float(pulse_period))
+    return sc
 
 
 def shell_scene(lo, hi, thickness, v):

@@ -123,56 +123,138 @@ def _shell_parts(scene, x, t):
     return x - c, h_out, h_in
 
 
-def _extruded(scene, x, with_grad):
-    """Outside-positive distance to each shape of an ``extruded`` scene (and
-    gradients in theta), theta holding every radius shape by shape, key by
-    key (rho1_0, rho2_0, rho1_1, ...). A shape may carry a rigid local frame
-    ``frame = dict(origin, axes)`` (axes: rows are the local x, y, z in world
-    coordinates, orthonormal); it is extruded along its local z, and a world
-    point x is measured at axes (x - origin), which keeps distances."""
+def pulse_scale(scene, t):
+    """Contraction of an ``extruded`` scene's pulsing shape: the factor k(t)
+    applied to its radii, piecewise linear through 4 knots (theta) at
+    t = 0, T/3, 2T/3, T; returns k, its rate and their theta-derivatives."""
     th = np.asarray(scene["theta"], dtype=np.float64)
-    Xw = x.reshape(-1, 3)
-    dists, grads, j = [], [], 0
+    seg_len = scene["pulse"]["period"] / 3.0
+    seg = int(min(max(np.floor(t / seg_len), 0), 2))
+    tau = (t - seg * seg_len) / seg_len
+    k = th[seg] * (1.0 - tau) + th[seg + 1] * tau
+    kdot = (th[seg + 1] - th[seg]) / seg_len
+    dk = np.zeros(4)
+    dk[seg], dk[seg + 1] = 1.0 - tau, tau
+    dkdot = np.zeros(4)
+    dkdot[seg], dkdot[seg + 1] = -1.0 / seg_len, 1.0 / seg_len
+    return k, kdot, dk, dkdot
+
+
+def _extruded_radii(scene):
+    """Base radii (2N,) of every key of every shape: theta when the radii are
+    the parameters (``params = "radii"``, the default), else the keys' own."""
+    th = np.asarray(scene["theta"], dtype=np.float64)
+    from_theta = scene.get("params", "radii") == "radii"
+    out, j = [], 0
     for sh in scene["shapes"]:
-        fr = sh.get("frame")
-        if fr is None:
-            X = Xw
-        else:
-            X = (Xw - np.asarray(fr["origin"], dtype=np.float64)) @ np.asarray(fr["axes"]).T
-        keys = []
+        rs = []
         for k in sh["keys"]:
-            n = int(k["nseg"])
-            r = th[j:j + 2 * n]
-            keys.append(dict(c=k["c"], rho1=r[0::2], rho2=r[1::2]))
-            j += 2 * n
+            n2 = 2 * int(k["nseg"])
+            if from_theta:
+                rs.append(th[j:j + n2])
+                j += n2
+            else:
+                rs.append(np.asarray(k["rho"], dtype=np.float64))
+        out.append(rs)
+    return out
+
+
+def _local(sh, Xw):
+    """Points in the shape's frame, and the frame's axes (rows: local x, y, z
+    in world coordinates)."""
+    fr = sh.get("frame")
+    if fr is None:
+        return Xw, np.eye(3)
+    A = np.asarray(fr["axes"], dtype=np.float64)
+    return (Xw - np.asarray(fr["origin"], dtype=np.float64)) @ A.T, A
+
+
+def _extruded(scene, x, t, with_grad):
+    """Outside-positive distance to each shape of an ``extruded`` scene and,
+    with ``with_grad``, its theta-gradient (M, K).
+
+    Shapes: ``dict(z0, z1, keys=[dict(c, nseg[, rho])...][, frame])``. A shape
+    with a rigid frame ``dict(origin, axes)`` (axes orthonormal, rows the
+    local x, y, z in world coordinates) is extruded along its local z and a
+    world point x is measured at axes (x - origin), which keeps distances.
+    theta is either every radius, shape by shape, key by key (rho1_0, rho2_0,
+    rho1_1, ...), or, with ``params = "pulse"``, the 4 knots of the
+    contraction k(t) of shape ``pulse["shape"]``, whose radii are k(t) times
+    its keys' own."""
+    Xw = x.reshape(-1, 3)
+    radii = _extruded_radii(scene)
+    pulse = scene.get("pulse")
+    kt = pulse_scale(scene, t) if pulse else None
+    K = len(scene["theta"])
+    dists, grads, j = [], [], 0
+    for s_, sh in enumerate(scene["shapes"]):
+        X, _ = _local(sh, Xw)
+        scale = kt[0] if (pulse and s_ == pulse["shape"]) else 1.0
+        keys = [dict(c=k["c"], rho1=scale * r[0::2], rho2=scale * r[1::2])
+                for k, r in zip(sh["keys"], radii[s_])]
         shape = dict(z0=sh["z0"], z1=sh["z1"], keys=keys)
-        if with_grad:
-            d, g = bezier.extrude_sdf_many(shape, X, with_grad=True)
-            grads.append(g)
-        else:
-            d = bezier.extrude_sdf_many(shape, X)
+        if not with_grad:
+            dists.append(bezier.extrude_sdf_many(shape, X))
+            continue
+        d, g = bezier.extrude_sdf_many(shape, X, with_grad=True)
+        G = np.zeros((X.shape[0], K))
+        if scene.get("params", "radii") == "radii":
+            G[:, j:j + g.shape[1]] = scale * g
+            j += g.shape[1]
+        elif pulse and s_ == pulse["shape"]:
+            # d d / d k = sum over the scaled radii of g times the base radius
+            G[:, :] = (g @ np.concatenate(radii[s_]))[:, None] * kt[2][None, :]
         dists.append(d)
+        grads.append(G)
     return dists, grads
 
 
-def _extruded_phi(scene, x, with_grad=False):
+def _extruded_phi(scene, x, t, with_grad=False):
     """phi > 0 in the fluid: outside the union of the shapes (obstacles) or
     inside it (containers): CSG union is the min of the distances."""
-    dists, grads = _extruded(scene, x, with_grad)
+    dists, grads = _extruded(scene, x, t, with_grad)
     D = np.stack(dists)                                   # (shapes, M)
     a = np.argmin(D, axis=0)
     sgn = 1.0 if scene["fluid"] == "outside" else -1.0
-    ph = sgn * D[a, np.arange(D.shape[1])]
+    rows = np.arange(D.shape[1])
+    ph = sgn * D[a, rows]
     if not with_grad:
         return ph.reshape(x.shape[:-1])
+    G = sgn * np.stack(grads)[a, rows]                    # (M, K)
     K = len(scene["theta"])
-    G = np.zeros((D.shape[1], K))
-    j = 0
-    for s_, g in enumerate(grads):
-        sel = a == s_
-        G[sel, j:j + g.shape[1]] = sgn * g[sel]
-        j += g.shape[1]
     return ph.reshape(x.shape[:-1]), G.reshape(x.shape[:-1] + (K,))
+
+
+def _extruded_us(scene, x, t, with_grad=False):
+    """Solid velocity: where the pulsing shape is the nearest (the active
+    piece of the union), the velocity of its uniform contraction about the
+    cross-section centre, (kdot / k) (p - c(z)) across its local z; zero
+    elsewhere and on static scenes. With ``with_grad`` also d u_s / d theta."""
+    Xw = x.reshape(-1, 3)
+    K = len(scene["theta"])
+    out = np.zeros(Xw.shape)
+    dout = np.zeros(Xw.shape + (K,))
+    pulse = scene.get("pulse")
+    if pulse:
+        dists, _ = _extruded(scene, x, t, False)
+        act = np.argmin(np.stack(dists), axis=0) == pulse["shape"]
+        sh = scene["shapes"][pulse["shape"]]
+        X, A = _local(sh, Xw)
+        n = len(sh["keys"])
+        z0, z1 = float(sh["z0"]), float(sh["z1"])
+        u = np.clip((X[:, 2] - z0) / (z1 - z0), 0.0, 1.0)
+        W = np.stack([bezier.lagrange_weights(n, uu) for uu in u])      # (M, n)
+        c = W @ np.array([np.asarray(k["c"], dtype=np.float64) for k in sh["keys"]])
+        r = np.zeros(Xw.shape)
+        r[:, :2] = X[:, :2] - c
+        dirw = np.where(act[:, None], r @ A, 0.0)          # back to world axes
+        k, kdot, dk, dkdot = pulse_scale(scene, t)
+        out = (kdot / k) * dirw
+        coef = (dkdot * k - kdot * dk) / (k * k)          # d(kdot / k) / d theta
+        dout = dirw[..., None] * coef
+    if with_grad:
+        return out.reshape(x.shape), dout.reshape(x.shape + (K,))
+    return out.reshape(x.shape)
 
 
 # ------------------------------------------------------------ dispatch -----
@@ -201,7 +283,7 @@ def phi(scene, x, t):
         p, ho, hi = _shell_parts(scene, x, t)
         return np.maximum(box_sdf(p, ho), -box_sdf(p, hi))
     if kind == "extruded":
-        return _extruded_phi(scene, x)
+        return _extruded_phi(scene, x, t)
     raise ValueError(kind)
 
 
@@ -219,6 +301,8 @@ def solid_velocity(scene, x, t):
         r = x - np.asarray(scene["centre"])
         out[..., 0] = -omega * r[..., 1]
         out[..., 1] = omega * r[..., 0]
+    elif kind == "extruded":
+        out = _extruded_us(scene, x, t)
     return out
 
 
@@ -249,7 +333,7 @@ def dphi_dtheta(scene, x, t):
                      -box_sdf_grad(p, hi))
         return -t * g
     if kind == "extruded":
-        return _extruded_phi(scene, x, with_grad=True)[1]
+        return _extruded_phi(scene, x, t, with_grad=True)[1]
     raise ValueError(kind)
 
 
@@ -271,4 +355,6 @@ def dus_dtheta(scene, x, t):
         r = x - np.asarray(scene["centre"])
         out[..., 0, :] = -r[..., 1:2] * domega
         out[..., 1, :] = r[..., 0:1] * domega
+    elif kind == "extruded":
+        out = _extruded_us(scene, x, t, with_grad=True)[1]
     return out

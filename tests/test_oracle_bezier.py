@@ -353,3 +353,63 @@ def test_heart_scene_fraction_gradient_matches_finite_differences():
         an = sum(np.sum(w[d] * dalpha[d][..., k]) for d in range(3))
         assert abs(fd - an) <= 1e-5 * max(1.0, abs(an)), (k, fd, an)
         assert abs(an) > 1e-4, k
+
+
+# ------------------------------------------------------ a pulsing heart ----
+
+def _wall_points(sc, t, z=0.42):
+    """Points on the pulsing chamber's side wall at time t (fluid side of
+    the tubes' junctions: the -x half), where the chamber is the nearest."""
+    from oracle import geometry
+    sh = sc["shapes"][0]
+    k = geometry.pulse_scale(sc, t)[0]
+    n = len(sh["keys"])
+    u = (z - sh["z0"]) / (sh["z1"] - sh["z0"])
+    W = B.lagrange_weights(n, u)
+    base = [np.asarray(kk["rho"]) for kk in sh["keys"]]
+    r = k * sum(W[i] * base[i] for i in range(n))
+    c = sum(W[i] * np.asarray(sh["keys"][i]["c"]) for i in range(n))
+    C = B.control_points(c, r[0::2], r[1::2])
+    pts = [np.append(B.bezier(C[i], s), z) for i in range(len(C)) for s in (0.3, 0.7)]
+    return np.array([p for p in pts if p[0] < 0.45])
+
+
+def test_pulsing_chamber_wall_moves_with_the_solid_velocity():
+    # kinematic condition on the moving wall: d phi / dt + u_s . grad phi = 0
+    import nf_inputs as I
+    from oracle import geometry
+    sc = I.heart_scene(5, pulse_period=0.06)
+    t, h = 0.013, 1e-6
+    X = _wall_points(sc, t)
+    assert len(X) >= 3
+    np.testing.assert_allclose(geometry.phi(sc, X, t), 0.0, atol=1e-12)
+    dphidt = (geometry.phi(sc, X, t + h) - geometry.phi(sc, X, t - h)) / (2 * h)
+    grad = np.stack([(geometry.phi(sc, X + h * e, t) - geometry.phi(sc, X - h * e, t)) / (2 * h)
+                     for e in np.eye(3)], axis=-1)
+    us = geometry.solid_velocity(sc, X, t)
+    kdot = geometry.pulse_scale(sc, t)[1]
+    assert abs(kdot) > 0.1
+    np.testing.assert_allclose(dphidt + np.sum(us * grad, axis=-1), 0.0, atol=1e-6)
+
+
+def test_pulsing_heart_phi_and_velocity_gradients_match_finite_differences():
+    import nf_inputs as I
+    from oracle import geometry
+    sc = I.heart_scene(6, pulse_period=0.06, outlet=True)
+    rng = np.random.default_rng(18)
+    X = np.concatenate([_wall_points(sc, 0.031) + rng.uniform(-0.02, 0.02, (1, 3)),
+                        rng.uniform(0.2, 0.8, size=(40, 3))])
+    t, h = 0.031, 1e-6
+    dphi = geometry.dphi_dtheta(sc, X, t)
+    dus = geometry.dus_dtheta(sc, X, t)
+    th = np.asarray(sc["theta"])
+    for k in range(4):
+        tp, tm = th.copy(), th.copy()
+        tp[k] += h
+        tm[k] -= h
+        sp, sm = dict(sc, theta=list(tp)), dict(sc, theta=list(tm))
+        fd = (geometry.phi(sp, X, t) - geometry.phi(sm, X, t)) / (2 * h)
+        np.testing.assert_allclose(dphi[:, k], fd, atol=1e-7)
+        fdu = (geometry.solid_velocity(sp, X, t) - geometry.solid_velocity(sm, X, t)) / (2 * h)
+        np.testing.assert_allclose(dus[:, :, k], fdu, atol=1e-6)
+    assert np.abs(dphi).max() > 1e-3 and np.abs(dus).max() > 1e-2

@@ -185,6 +185,29 @@ def test_chamber_outflow_equals_geometric_volume_rate_and_its_gradient():
     np.testing.assert_allclose(g_adj, g_geo, rtol=1e-7, atol=1e-9 * np.abs(g_geo).max())
 
 
+def test_pulsing_heart_outflow_equals_geometric_volume_rate_and_its_gradient():
+    # the heart of Sec. 3 as a union of extruded polar-Bezier parts (App. A),
+    # its chamber contracting by k(t) (4 control knots), one opening: the
+    # outlet tube through the high-x patch. As for the chamber, the outflow
+    # is the rate of change of the fluid volume, a function of alpha and u_s
+    n = 12
+    g0 = I.make_grid(n, 0.01, outlet=I.centred_outlet(n, 2))
+    g0["fractions"] = "corner"
+    cfg = dict(name="heart12", grid=g0, scene=I.heart_scene(7, pulse_period=0.06, outlet=True),
+               u0=I.zero_faces(g0), project_initial=False, steps=2, tol=1e-13, loss="outflow")
+    J, g_adj, _ = S.loss_and_grad(cfg, tol=1e-13)
+    g = Grid(cfg["grid"])
+    t = cfg["steps"] * g.dt
+    alpha = rasterize.fractions(g, cfg["scene"], t)
+    us, dus = rasterize.face_solid_velocity(g, cfg["scene"], t, with_grad=True)
+    geo = g.dx ** 2 * _active_boundary_flux(g, alpha, us)
+    assert abs(J) > 0.1
+    assert abs(J - geo) <= 1e-9 * abs(J)
+    g_geo = np.array([g.dx ** 2 * _active_boundary_flux(g, alpha, [dus[d][..., k] for d in range(3)])
+                      for k in range(4)])
+    np.testing.assert_allclose(g_adj, g_geo, rtol=1e-7, atol=1e-9 * np.abs(g_geo).max())
+
+
 def test_substepped_chamber_keeps_the_outflow_identity():
     # CFL sub-stepping (Table 1: more steps than frames): the frame ends at
     # t = frames * dt whatever the split, so the final outflow still equals
