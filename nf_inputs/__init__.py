@@ -28,13 +28,16 @@ SCENE_KINDS = ("none", "sphere", "chamber", "plate", "spheres", "shell")
 
 
 def make_grid(n, dt, *, ny=None, nz=None, nu=0.0, rho=1.0, outlet=None,
-              periodic=False, extent=1.0):
+              periodic=False, extent=1.0, inlet=None):
     """A grid description: ``n`` cells along x over ``[0, extent]``."""
     ny = n if ny is None else ny
     nz = n if nz is None else nz
-    return dict(nx=int(n), ny=int(ny), nz=int(nz), dx=float(extent) / n,
-                dt=float(dt), rho=float(rho), nu=float(nu),
-                periodic=bool(periodic), outlet=outlet)
+    g = dict(nx=int(n), ny=int(ny), nz=int(nz), dx=float(extent) / n,
+             dt=float(dt), rho=float(rho), nu=float(nu),
+             periodic=bool(periodic), outlet=outlet)
+    if inlet is not None:
+        g["inlet"] = inlet
+    return g
 
 
 def face_shape(grid, d):
@@ -53,6 +56,14 @@ def centred_outlet(n, width):
     """A ``width x width`` patch of high-x boundary faces centred in (y, z)."""
     j0 = n // 2 - width // 2
     return dict(axis=0, side=1, j0=j0, k0=j0, w=int(width), h=int(width))
+
+
+def centred_inlet(n, width, speed, side=-1):
+    """A ``width x width`` inflow patch of x-wall faces centred in (y, z),
+    holding the normal velocity ``speed`` (along +x on the low-x wall)."""
+    j0 = n // 2 - width // 2
+    return dict(axis=0, side=int(side), j0=j0, k0=j0, w=int(width), h=int(width),
+                speed=float(speed))
 
 
 def gaussian_faces(grid, sigma, seed):

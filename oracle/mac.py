@@ -36,6 +36,9 @@ class Grid:
         if self.fractions not in ("supersample", "corner"):
             raise ValueError(f"unknown fraction rule {self.fractions!r}")
         self.outlet = desc.get("outlet")
+        # an inflow patch: boundary faces held at a prescribed normal velocity
+        # (a wall, alpha = 0, whose solid velocity is the inflow)
+        self.inlet = desc.get("inlet")
         self.c = self.dt / (self.rho * self.dx)
         self.n = (self.nx, self.ny, self.nz)          # cells per axis, (x, y, z)
 
@@ -113,6 +116,18 @@ def boundary_face_mask(g: Grid, d):
     m[tuple(idx)] = True
     idx[ax] = -1
     m[tuple(idx)] = True
+    return m
+
+
+def inlet_face_mask(g: Grid, d):
+    """True on the boundary faces of the inflow patch (an x wall)."""
+    m = np.zeros(g.face_shape(d), dtype=bool)
+    o = g.inlet
+    if o is None or g.periodic or d != o["axis"]:
+        return m
+    assert o["axis"] == 0, "inflow patches are on an x wall"
+    i = g.nx if o["side"] > 0 else 0
+    m[o["k0"]:o["k0"] + o["h"], o["j0"]:o["j0"] + o["w"], i] = True
     return m
 
 

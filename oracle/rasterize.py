@@ -20,7 +20,10 @@ fluid, that walk keeps the fluid connected across the face (the two solid
 corners are cut off).
 
 Box-boundary faces are walls (alpha = 0, u_s = 0) except the outlet patch,
-which is open (alpha = 1, Appendix B, Eq. bd:dirichlet).
+which is open (alpha = 1, Appendix B, Eq. bd:dirichlet), and an optional
+inflow patch: wall faces (alpha = 0) whose solid velocity is the prescribed
+inflow speed along the wall normal, so the blended update holds them at it
+and the right-hand side carries the inflow.
 """
 
 from __future__ import annotations
@@ -30,7 +33,7 @@ import itertools
 import numpy as np
 
 from . import geometry as geo
-from .mac import Grid, boundary_face_mask, face_positions, outlet_face_mask
+from .mac import Grid, boundary_face_mask, face_positions, inlet_face_mask, outlet_face_mask
 
 
 def subsample_offsets():
@@ -171,6 +174,8 @@ def face_solid_velocity(g: Grid, scene, t, with_grad=False):
         v[wall] = 0.0
         if with_grad:
             dv[wall] = 0.0
+        if g.inlet is not None:
+            v[inlet_face_mask(g, d)] = float(g.inlet["speed"])
         us.append(v)
         dus.append(dv)
     return (us, dus) if with_grad else us

@@ -52,6 +52,8 @@ def grid_struct(desc):
     g.dx, g.dt, g.rho = desc["dx"], desc["dt"], desc.get("rho", 1.0)
     if desc.get("periodic", False):
         raise ValueError("the CUDA path implements closed boxes (walls and an outlet patch)")
+    if desc.get("inlet"):
+        raise ValueError("the CUDA path has no inflow patch (walls and an outlet patch only)")
     g.nu = float(desc.get("nu", 0.0))
     rule = desc.get("fractions", "supersample")
     if rule not in L.FRACTIONS:

@@ -137,6 +137,8 @@ def test_grid_marshalling_of_viscosity_and_fraction_rule():
         grid_struct(dict(I.make_grid(8, 0.01), fractions="marching"))
     with pytest.raises(ValueError):
         grid_struct(I.make_grid(8, 0.01, periodic=True))
+    with pytest.raises(ValueError):
+        grid_struct(I.make_grid(8, 0.01, inlet=I.centred_inlet(8, 2, 0.3)))
 
 
 def test_struct_field_offsets_match_the_header(tmp_path):

@@ -208,6 +208,52 @@ def test_pulsing_heart_outflow_equals_geometric_volume_rate_and_its_gradient():
     np.testing.assert_allclose(g_adj, g_geo, rtol=1e-7, atol=1e-9 * np.abs(g_geo).max())
 
 
+# ------------------------------------------------------- inflow patch ----
+
+def test_uniform_through_flow_is_steady():
+    # the whole low-x wall an inflow at speed V, the whole high-x wall open,
+    # no solid: the uniform field V is divergence free and stays exactly
+    n, V = 8, 0.37
+    g0 = I.make_grid(n, 0.02, inlet=dict(axis=0, side=-1, j0=0, k0=0, w=n, h=n, speed=V),
+                     outlet=dict(axis=0, side=1, j0=0, k0=0, w=n, h=n))
+    g = Grid(g0)
+    U = [np.full(g.face_shape(0), V), np.zeros(g.face_shape(1)), np.zeros(g.face_shape(2))]
+    sc = dict(kind="none", theta=[])
+    for k in range(3):
+        U, _ = S.step(g, sc, U, k, 1e-13)
+    # the y and z walls stay walls (u = 0); x faces carry V everywhere
+    np.testing.assert_allclose(U[0], V, rtol=0, atol=1e-12)
+    for d in (1, 2):
+        np.testing.assert_allclose(U[d], 0.0, rtol=0, atol=1e-12)
+
+
+def test_outflow_equals_inflow_past_a_moving_sphere():
+    # incompressibility: the net flux out is the inflow, since a rigid
+    # motion adds none; both patches 4 x 4 faces
+    n, V = 16, 0.3
+    cfg = I.config_sphere(n, steps=2)
+    cfg["grid"] = I.make_grid(n, 0.01, inlet=I.centred_inlet(n, 4, V),
+                              outlet=I.centred_outlet(n, 4))
+    cfg["u0"] = I.gaussian_faces(cfg["grid"], 0.1, 3)
+    cfg["loss"] = "outflow"
+    g = Grid(cfg["grid"])
+    U, _ = S.rollout(g, cfg["scene"], cfg["u0"], cfg["steps"], 1e-13, True)
+    J, _ = S.outflow(g, U)
+    assert abs(J - V * 16 * g.dx ** 2) <= 1e-10 * J
+
+
+def test_rollout_gradient_with_an_inlet_matches_central_differences():
+    n = 12
+    cfg = I.config_sphere(n, steps=3)
+    cfg["grid"] = I.make_grid(n, 0.01, inlet=I.centred_inlet(n, 4, 0.3),
+                              outlet=I.centred_outlet(n, 4))
+    cfg["u0"] = I.gaussian_faces(cfg["grid"], 0.1, 4)
+    J, g_adj, _ = S.loss_and_grad(cfg, tol=1e-12)
+    g_fd = S.fd_gradient(cfg, h=1e-4, tol=1e-12)
+    err = np.linalg.norm(g_adj - g_fd) / np.linalg.norm(g_fd)
+    assert err < 1e-3, (g_adj, g_fd)
+
+
 def test_substepped_chamber_keeps_the_outflow_identity():
     # CFL sub-stepping (Table 1: more steps than frames): the frame ends at
     # t = frames * dt whatever the split, so the final outflow still equals
