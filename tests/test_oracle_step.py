@@ -254,6 +254,32 @@ def test_rollout_gradient_with_an_inlet_matches_central_differences():
     assert err < 1e-3, (g_adj, g_fd)
 
 
+# ------------------------------------------------- the 2D variant ----
+
+def test_two_dimensional_channel_past_a_cylinder():
+    # a 2D scene as a one-cell slab (nz = 1, closed z walls): uniform inflow
+    # through the whole low-x wall, open high-x wall, a cylinder (an extruded
+    # near-circular polar-Bezier shape through all z). u_z stays zero, the
+    # outflow equals the inflow, and the flow keeps the mirror symmetry of
+    # the cylinder and the data about the centre line y = 1/2
+    n, V = 24, 0.3
+    g0 = I.make_grid(n, 0.005, nz=1, inlet=dict(axis=0, side=-1, j0=0, k0=0, w=n, h=1, speed=V),
+                     outlet=dict(axis=0, side=1, j0=0, k0=0, w=n, h=1))
+    g0["fractions"] = "corner"
+    sc = dict(kind="extruded", theta=[0.08] * 12, fluid="outside",
+              shapes=[dict(z0=-1.0, z1=2.0, keys=[dict(c=[0.35, 0.5], nseg=6)])])
+    g = Grid(g0)
+    U0 = [np.full(g.face_shape(0), V), np.zeros(g.face_shape(1)), np.zeros(g.face_shape(2))]
+    U, _ = S.rollout(g, sc, U0, 3, 1e-13, project_initial=True)
+    assert not np.any(U[2])
+    J, _ = S.outflow(g, U)
+    assert abs(J - V * n * g.dx ** 2) <= 1e-12
+    ux, uy = U[0][0], U[1][0]                  # (y, x) layers of the slab
+    assert np.abs(uy).max() > 0.05             # the cylinder deflects the flow
+    np.testing.assert_allclose(ux, ux[::-1, :], rtol=0, atol=1e-9)
+    np.testing.assert_allclose(uy, -uy[::-1, :], rtol=0, atol=1e-9)
+
+
 def test_substepped_chamber_keeps_the_outflow_identity():
     # CFL sub-stepping (Table 1: more steps than frames): the frame ends at
     # t = frames * dt whatever the split, so the final outflow still equals
