@@ -74,7 +74,7 @@ def parse():
                     help="scale of the coarse-grid correction")
     ap.add_argument("--mg-cluster", type=int, default=0,
                     help="1: coarse levels above an 8^3 local chain on one thread-block cluster")
-    ap.add_argument("--residual-fp64", type=int, default=0,
+    ap.add_argument("--residual-fp64", type=int, default=1,
                     help="1: MIXED refinement residual in FP64 arithmetic (0: split-float)")
     ap.add_argument("--mg-persistent", type=int, default=0,
                     help="1: coarse levels <= 64^3 and the chain in one cooperative kernel")
@@ -319,7 +319,7 @@ def run_ours(args, rank, world, local_rank):
                            fractions=args.fractions,
                            cfl_max=cfg["cfl_max"], substeps_executed=int(stats["fwd"]["steps"]),
                            precision="FP32 MGPCG (V-cycle, CG vectors; BF16 coarse-level "
-                                     "fractions), FP32 per-thread dot partials summed in FP64, "
+                                     "fractions), CG dots in FP64 (FP64 products and sums), "
                                      f"FP64 refinement (x, b FP64) to rel res {args.tol:g}, its "
                                      "residual in "
                                      + ("FP64 arithmetic" if args.residual_fp64 else
@@ -375,7 +375,7 @@ def run_ours(args, rank, world, local_rank):
     out["kernel_avg_us"] = {k: round(1e3 * v[1] / v[0], 2) for k, v in shares.items() if v[0]}
     if not args.no_extras:
         out["e2e"] = run_e2e(args, torch, cfg, dev, ep)
-        out["fp64_plain"] = run_plain(args, P, torch, dev)
+        out["fp64_plain"] = run_plain(args, P, torch, dev, ctx, ep, value)
         out["cpu_baseline"] = cpu_baseline(args)
         out["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores(args)
     ep.close()
@@ -410,38 +410,59 @@ def run_e2e(args, torch, cfg, dev, ep):
                 d2h_bytes_per_step=int(8 + gth.nbytes), ms_per_step=1e3 * dt, steps=k)
 
 
-def run_plain(args, P, torch, dev):
-    """The same GPU's FP64 CG and FP64 MGPCG on a shorter rollout."""
+def _time_rollout(torch, dev, ep, u0, T, warm_T):
+    """Milliseconds (CUDA events) of one forward rollout of T frames plus its
+    adjoint, after one untimed rollout of warm_T frames; solver stats."""
+    def one(frames):
+        ep.set_velocity(u0, project=False)
+        fs = ep.step(frames)
+        J, gU = ep.loss("outflow", want_grad=True)
+        gth, _, bs = ep.backward(gU, want_gU0=False)
+        return fs, bs
+
+    one(warm_T)
+    torch.cuda.synchronize(dev)
+    s = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    fs, bs = one(T)
+    e1.record(s)
+    torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1), fs, bs
+
+
+def run_plain(args, P, torch, dev, ours_ctx, ours_ep, ours_value):
+    """The same GPU's plain FP64 paths on the same scene, like for like.
+
+    FP64 MGPCG runs the metric's own rollout (the same frames, hence the
+    same CFL substeps), so ``value / fp64_mgpcg.value`` compares equal work.
+    FP64 CG is too slow for the full rollout inside a bench run (about ten
+    minutes); it runs the first ``plain_rollout`` frames, and the configured
+    MIXED path is timed on those same frames beside it."""
     res = {}
-    T = args.plain_rollout
-    for solver in ("cg", "mgpcg"):
+    Tp = args.plain_rollout
+    u32 = [torch.zeros(s, dtype=torch.float32, device=dev) for s in ours_ep.face_shapes]
+    ms, fs, bs = _time_rollout(torch, dev, ours_ep, u32, Tp, Tp)
+    mixed_short = dict(value=args.n ** 3 * Tp / (ms / 1e3), unit=UNIT, rollout_steps=Tp,
+                       substeps=int(fs["steps"]), ms_per_rollout=ms,
+                       fwd_iters=fs["iters"], bwd_iters=bs["iters"])
+    for solver, T in (("mgpcg", args.rollout), ("cg", Tp)):
         cfg = chamber(args.n, T, seed=0)
-        ctx = P.Context("fp64", solver, tol=1e-6, max_iters=20000, checkpoint_every=10,
+        ctx = P.Context("fp64", solver, tol=args.tol, max_iters=20000, checkpoint_every=10,
                         cfl_max=cfg["cfl_max"])
         ep = ctx.episode(cfg["grid"], cfg["scene"])
         u0 = [torch.zeros(s, dtype=torch.float64, device=dev) for s in ep.face_shapes]
-
-        def one():
-            ep.set_velocity(u0, project=False)
-            fs = ep.step(T)
-            J, gU = ep.loss("outflow", want_grad=True)
-            gth, _, bs = ep.backward(gU, want_gU0=False)
-            return fs, bs
-
-        one()
-        torch.cuda.synchronize(dev)
-        s = torch.cuda.current_stream(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(s)
-        fs, bs = one()
-        e1.record(s)
-        torch.cuda.synchronize(dev)
-        ms = e0.elapsed_time(e1)
+        ms, fs, bs = _time_rollout(torch, dev, ep, u0, T, 1)
         res[solver] = dict(value=args.n ** 3 * T / (ms / 1e3), unit=UNIT, rollout_steps=T,
                            substeps=int(fs["steps"]), ms_per_rollout=ms,
                            fwd_iters=fs["iters"], bwd_iters=bs["iters"])
         ep.close()
         ctx.close()
+    res["mixed_same_frames_as_cg"] = mixed_short
+    res["speedup_vs_fp64_mgpcg"] = ours_value / res["mgpcg"]["value"]
+    res["speedup_vs_fp64_cg"] = mixed_short["value"] / res["cg"]["value"]
+    res["note"] = ("fp64 mgpcg: the metric's full rollout (same frames and substeps as value); "
+                   f"fp64 cg: the first {Tp} frames, against MIXED on the same {Tp} frames")
     return res
 
 
@@ -456,6 +477,18 @@ def _cpu_sample(n):
     J, gU = S.outflow(g, U)
     S.rollout_backward(g, cfg["scene"], [tape], gU, 1e-6)
     return time.perf_counter() - t0
+
+
+def cpu_model():
+    """The host CPU's model name (from /proc/cpuinfo), or None."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
 
 
 def cpu_baseline(args):
@@ -473,7 +506,7 @@ def cpu_baseline(args):
         raise RuntimeError(f"CPU oracle sample failed: {res.stderr[-2000:]}")
     dt = float(res.stdout.strip().splitlines()[-1])
     return dict(value=n ** 3 / dt, unit=UNIT, cores=1, host_cpus=os.cpu_count(),
-                kind="oracle",
+                cpu_model=cpu_model(), kind="oracle",
                 sample=f"1 step (forward + adjoint) of the same chamber scene on {n}^3 "
                        f"(FP64 NumPy, unpreconditioned CG to 1e-6, one thread), scaled per "
                        f"cell-step; a coarser grid needs fewer CG iterations, so this "
@@ -483,11 +516,10 @@ def cpu_baseline(args):
 
 def cpu_baseline_all_cores(args, procs=None):
     """The same oracle sample run by ``procs`` one-thread interpreters at once
-    (default: one per host CPU, at most 8): independent episodes, as the
-    replicas of the GPU run. value = procs x cells / the slowest sample's
-    time."""
+    (default: one per host CPU): independent episodes, as the replicas of the
+    GPU run. value = procs x cells / the slowest sample's time."""
     n = args.cpu_n
-    P = procs or max(1, min(os.cpu_count() or 1, 8))
+    P = procs or max(1, os.cpu_count() or 1)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
                MKL_NUM_THREADS="1", NUMEXPR_NUM_THREADS="1")
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", "--cpu-n", str(n)]
@@ -501,7 +533,7 @@ def cpu_baseline_all_cores(args, procs=None):
             raise RuntimeError(f"CPU oracle sample failed: {err[-2000:]}")
     dts = [float(o.strip().splitlines()[-1]) for o, _ in outs]
     return dict(value=P * n ** 3 / max(dts), unit=UNIT, cores=P, host_cpus=os.cpu_count(),
-                kind="oracle", seconds=max(dts), wall_seconds=wall,
+                cpu_model=cpu_model(), kind="oracle", seconds=max(dts), wall_seconds=wall,
                 sample=f"{P} concurrent one-thread copies of the {n}^3 sample")
 
 

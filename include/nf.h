@@ -199,7 +199,7 @@ typedef struct nf_step_stats {
    checkpoint_every 10, no budget, cfl_max 0 (no sub-stepping),
    mg_coarsest_sweeps 8, mg_band_sweeps 0, mg_transfer 1 (constant),
    mg_coarse_weight 1.9, mg_smooth_coarse 0, tape_fractions 0,
-   mg_persistent 0, mg_cluster 0, residual_fp64 0. */
+   mg_persistent 0, mg_cluster 0, residual_fp64 1. */
 int nf_config_default(nf_config *cfg);
 
 /* Create a context on cfg->device. *out receives the handle. */
@@ -291,6 +291,15 @@ int nf_get_advected(nf_ctx *ctx, int64_t id, void *const u[3], int dtype,
                     int mem);
 /* Step counter n (the velocity is U^n). */
 int nf_get_step(nf_ctx *ctx, int64_t id, int *n);
+
+/* Diagnostic: *out = sum_i a[i] b[i] over n entries of two device arrays
+   (dtype NF_F32 or NF_F64) of the context's device, computed by the
+   solver's own dot arithmetic (the CG inner products of Eq.
+   projection_matrix's solve): FP32 entries give exact products and
+   compensated per-thread sums, then FP64 block and grid sums in fixed order.
+   Synchronises the context's stream. */
+int nf_dot(nf_ctx *ctx, const void *a, const void *b, int64_t n, int dtype,
+           double *out);
 
 /* Kernel launches issued by this context since creation (a counter of the
    library's own kernels, used to report launches per timed region). */
@@ -436,7 +445,10 @@ int nf_server_destroy(nf_server *srv);
            loss; dt and rho are ignored).
    u       three DEVICE arrays of the current device, component d of shape
            [nz + (d==2)][ny + (d==1)][nx + (d==0)], x fastest, dtype NF_F32
-           or NF_F64. Host pointers are rejected with NF_E_INVALID.
+           or NF_F64. Host pointers, and device pointers of another device,
+           are rejected with NF_E_INVALID. The call cannot check the arrays'
+           sizes: they must hold the grid's face shapes (the Python binding
+           checks shapes and dtypes before the call).
    gU      NULL, or three device arrays of the same shapes and dtype that
            receive dJ/dU.
    J       host double that receives the loss.

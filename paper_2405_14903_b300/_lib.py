@@ -122,6 +122,7 @@ SIGNATURES = [
     ("nf_get_fractions", C.c_int, [_vp, _i64, PP, C.c_int, C.c_int]),
     ("nf_get_advected", C.c_int, [_vp, _i64, PP, C.c_int, C.c_int]),
     ("nf_get_step", C.c_int, [_vp, _i64, _ip]),
+    ("nf_dot", C.c_int, [_vp, _vp, _vp, _i64, C.c_int, C.POINTER(C.c_double)]),
     ("nf_launch_count", C.c_int, [_vp, C.POINTER(_i64)]),
     ("nf_profile", C.c_int, [_vp, C.c_int]),
     ("nf_profile_read", C.c_int, [_vp, C.c_int, C.POINTER(_i64), C.POINTER(C.c_double)]),

@@ -123,16 +123,31 @@ def loss_noalloc(kind, grid, u, gU=None, stream=None):
     dtype) that receives dJ/dU. Runs on torch's current stream (or
     ``stream``) and returns ``J``."""
     arrs = list(u) + (list(gU) if gU is not None else [])
+    if len(u) != 3 or (gU is not None and len(gU) != 3):
+        raise ValueError("u and gU are face triples (three tensors each)")
     if not all(isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous() for t in arrs):
         raise TypeError("u and gU must be contiguous CUDA tensors")
+    g = grid_struct(grid)
+    # the kernel indexes the arrays by the grid's face shapes: a tensor of
+    # another shape, dtype or device would be read or written out of bounds
+    shapes = [(g.nz, g.ny, g.nx + 1), (g.nz, g.ny + 1, g.nx), (g.nz + 1, g.ny, g.nx)]
+    dev = u[0].device
+    for d in range(3):
+        if tuple(u[d].shape) != shapes[d]:
+            raise ValueError(f"u[{d}] has shape {tuple(u[d].shape)}, the grid's face "
+                             f"component {d} is {shapes[d]}")
+        if gU is not None and (tuple(gU[d].shape) != shapes[d] or gU[d].dtype != u[d].dtype):
+            raise ValueError(f"gU[{d}] must match u[{d}] in shape and dtype")
+    if not all(t.device == dev for t in arrs):
+        raise ValueError("u and gU must be on one device")
     p, code, _, keep = _ptrs(u)
     pg = _ptrs(gU)[0] if gU is not None else None
-    if stream is None:
-        stream = torch.cuda.current_stream(keep[0].device).cuda_stream or L.CUDA_STREAM_LEGACY
-    g = grid_struct(grid)
-    J = C.c_double()
-    _check(lib.nf_loss_noalloc(C.byref(g), L.LOSS[kind], p, pg, code, C.byref(J), stream),
-           C.c_void_p())
+    with torch.cuda.device(dev):
+        if stream is None:
+            stream = torch.cuda.current_stream(dev).cuda_stream or L.CUDA_STREAM_LEGACY
+        J = C.c_double()
+        _check(lib.nf_loss_noalloc(C.byref(g), L.LOSS[kind], p, pg, code, C.byref(J), stream),
+               C.c_void_p())
     return J.value
 
 
@@ -141,7 +156,7 @@ def _config(precision="mixed", solver="mgpcg", tol=1e-6, max_iters=500,
             checkpoint_every=10, hbm_budget=0, cfl_max=0.0, mg_coarsest_sweeps=8,
             mg_band_sweeps=0, mg_transfer="constant", mg_coarse_weight=1.9,
             mg_smooth_coarse=0, tape_fractions=False, mg_persistent=False,
-            mg_cluster=False, residual_fp64=False, device=0, stream=0):
+            mg_cluster=False, residual_fp64=True, device=0, stream=0):
     """An ``nf_config`` from keyword arguments (defaults of nf_config_default)."""
     cfg = L.Config()
     _check(lib.nf_config_default(C.byref(cfg)))
@@ -202,6 +217,19 @@ class Context:
 
     def synchronize(self):
         _check(lib.nf_synchronize(self._h), self._h)
+
+    def dot(self, a, b):
+        """``nf_dot``: <a, b> of two CUDA tensors of one dtype by the solver's
+        dot arithmetic (a diagnostic of the CG inner products)."""
+        if not (a.is_cuda and b.is_cuda and a.is_contiguous() and b.is_contiguous()
+                and a.dtype == b.dtype and a.numel() == b.numel()
+                and a.dtype in (torch.float32, torch.float64)):
+            raise ValueError("a and b must be contiguous CUDA tensors of one float dtype and size")
+        out = C.c_double()
+        code = L.NF_F64 if a.dtype == torch.float64 else L.NF_F32
+        _check(lib.nf_dot(self._h, a.data_ptr(), b.data_ptr(), a.numel(), code, C.byref(out)),
+               self._h)
+        return out.value
 
     def launches(self):
         n = C.c_int64()

@@ -12,6 +12,7 @@
 
 #include "ctx.h"
 #include "episode.h"
+#include "kernels.h"
 #include "util.h"
 
 namespace nf {
@@ -205,7 +206,7 @@ int nf_config_default(nf_config *cfg) {
   cfg->tape_fractions = 0;
   cfg->mg_persistent = 0;
   cfg->mg_cluster = 0;
-  cfg->residual_fp64 = 0;
+  cfg->residual_fp64 = 1;
   return NF_OK;
 }
 
@@ -280,6 +281,7 @@ int nf_create(nf_ctx **out, const nf_config *cfg) {
   if (e == cudaSuccess) e = cudaMalloc(&ctx->c.rs.ticket, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemset(ctx->c.rs.ticket, 0, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMallocHost(&ctx->c.pinned, 4096);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->c.dscal, sizeof(double));
   if (e != cudaSuccess) {
     const int rc = nf::cuda_fail(e, "nf_create allocation");
     nf_destroy(ctx);
@@ -297,6 +299,7 @@ int nf_destroy(nf_ctx *ctx) {
   if (ctx->c.rs.partials) cudaFree(ctx->c.rs.partials);
   if (ctx->c.rs.ticket) cudaFree(ctx->c.rs.ticket);
   if (ctx->c.pinned) cudaFreeHost(ctx->c.pinned);
+  if (ctx->c.dscal) cudaFree(ctx->c.dscal);
   if (ctx->c.own_stream && ctx->c.stream) cudaStreamDestroy(ctx->c.stream);
   delete ctx;
   return NF_OK;
@@ -457,6 +460,25 @@ int nf_get_step(nf_ctx *ctx, int64_t id, int *n) {
   EPISODE(ctx, id, e);
   if (!n) return NF_E_INVALID;
   *n = e->step_index();
+  return NF_OK;
+}
+
+int nf_dot(nf_ctx *ctx, const void *a, const void *b, int64_t n, int dtype,
+           double *out) {
+  GUARD(ctx);
+  if (!a || !b || !out || n < 0 || !valid_dtype(dtype)) {
+    set_error("nf_dot: bad arguments");
+    return NF_E_INVALID;
+  }
+  cudaSetDevice(ctx->c.device);
+  nf::Launch L = ctx->c.launch();
+  if (dtype == NF_F64)
+    nf::launch_dot<double>(L, n, (const double *)a, (const double *)b, ctx->c.rs, ctx->c.dscal);
+  else
+    nf::launch_dot<float>(L, n, (const float *)a, (const float *)b, ctx->c.rs, ctx->c.dscal);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return nf::cuda_fail(e, "nf_dot");
+  *out = ctx->c.read_double(ctx->c.dscal);
   return NF_OK;
 }
 

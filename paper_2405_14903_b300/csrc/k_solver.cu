@@ -476,16 +476,44 @@ k_axpy_outer(int64_t n, S *x, const V *e, double inv) {
 }
 
 // ------------------------------------------------------------------ CG -----
-// Dots: each thread accumulates its few grid-stride terms (2M cells over
-// 151k threads: ~14) in the vector type, the block and grid sums are FP64 in
-// fixed order. FP64 arithmetic per element would cost more than the memory
-// traffic on this part, whose FP64 rate is 1/64 of FP32.
+// Dots. Each thread accumulates its few grid-stride terms (2M cells over
+// 151k threads: ~14), then the block and grid sums are FP64 in fixed order.
+// FP32 vectors: every product is kept exactly as a float pair (p, e) with
+// p + e = a b (FMA residual), and the thread's sum is compensated (two-sum,
+// the rounding errors gathered in a second float), so a thread's partial
+// carries about 48 significant bits, the error of an FP64 sum of these few
+// terms, using FP32 instructions only: this part runs FP64 arithmetic (and
+// float-to-double conversion) at 1/64 of the FP32 rate, and an FP64
+// accumulation per element doubled the time of the dot kernels. The error
+// of a partial is below 2^-46 of the sum of its terms' magnitudes. FP64
+// vectors accumulate in FP64.
+template <class V>
+struct DotAcc;
+template <>
+struct DotAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct DotAcc<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);  // a b = p + e exactly
+    const float t = __fadd_rn(s, p);      // two-sum: s + p = t + err exactly
+    const float bp = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(err, e));
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
 template <class V>
 __global__ void __launch_bounds__(kBlock, 4) k_cg_init(int64_t n, const V *r, const V *z, V *d, CGState *st,
                           RedScratch rs) {
   pdl_wait();
-  // per-thread partials in V (a few terms each), block and grid sums in FP64
-  V p0 = V(0), p1 = V(0);
+  DotAcc<V> p0, p1;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   constexpr int U = kIlpStream;
   for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c0 < n;
@@ -504,12 +532,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_cg_init(int64_t n, const V *r, co
       const int64_t c = c0 + u * stride;
       if (c < n) {
         d[c] = zv[u];
-        p0 += rv[u] * zv[u];
-        p1 += rv[u] * rv[u];
+        p0.add(rv[u], zv[u]);
+        p1.add(rv[u], rv[u]);
       }
     }
   }
-  double v[2] = {(double)p0, (double)p1};
+  double v[2] = {p0.value(), p1.value()};
   double tot[2];
   if (grid_sum<2>(v, rs, tot) && threadIdx.x == 0) {
     st->rz = tot[0];
@@ -526,7 +554,7 @@ template <class V>
 __global__ void __launch_bounds__(kBlock, 4) k_cg_continue(int64_t n, const V *r, const V *z, CGState *st,
                               RedScratch rs) {
   pdl_wait();
-  V p0 = V(0), p1 = V(0);
+  DotAcc<V> p0, p1;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   constexpr int U = kIlpStream;
   for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c0 < n;
@@ -544,12 +572,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_cg_continue(int64_t n, const V *r
     for (int u = 0; u < U; ++u) {
       const int64_t c = c0 + u * stride;
       if (c < n) {
-        p0 += rv[u] * zv[u];
-        p1 += rv[u] * rv[u];
+        p0.add(rv[u], zv[u]);
+        p1.add(rv[u], rv[u]);
       }
     }
   }
-  double v[2] = {(double)p0, (double)p1};
+  double v[2] = {p0.value(), p1.value()};
   double tot[2];
   if (grid_sum<2>(v, rs, tot) && threadIdx.x == 0) {
     const double s = st->ratio, rz_old = st->rz * s * s;
@@ -570,7 +598,7 @@ __global__ void k_apply_dot(LevelView<TA> lv, const V *d, V *q, CGState *st,
                             RedScratch rs) {
   pdl_wait();
   const int stop = stop_flag(st);
-  V p = V(0);
+  DotAcc<V> p;
   const RowWalk w;
   const int nrows = lv.ny * lv.nz;
   const V cc = V(lv.c);
@@ -585,11 +613,11 @@ __global__ void k_apply_dot(LevelView<TA> lv, const V *d, V *q, CGState *st,
       const V qc = dg > V(0) ? cc * (dg * g.vc - g.nb()) : V(0);
       if (stop) return;
       q[c] = qc;
-      p += g.vc * qc;
+      p.add(g.vc, qc);
     }
   }
   if (stop) return;  // every thread of every block (none reaches the grid sum)
-  double v[1] = {(double)p};
+  double v[1] = {p.value()};
   double tot[1];
   if (grid_sum<1>(v, rs, tot) && threadIdx.x == 0) {
     st->dq = tot[0];
@@ -607,7 +635,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_cg_xr(int64_t n, V *x, V *r, cons
   pdl_wait();
   const int stop = stop_flag(st);
   const V a = (V)st->alpha;
-  V p = V(0);
+  DotAcc<V> p;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   constexpr int U = kIlpStream;
   for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c0 < n;
@@ -631,12 +659,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_cg_xr(int64_t n, V *x, V *r, cons
         x[c] = xv[u] + a * dv[u];
         const V rc = rv[u] - a * qv[u];
         r[c] = rc;
-        p += rc * rc;
+        p.add(rc, rc);
       }
     }
   }
   if (stop) return;  // every thread of every block (none reaches the grid sum)
-  double v[1] = {(double)p};
+  double v[1] = {p.value()};
   double tot[1];
   if (grid_sum<1>(v, rs, tot) && threadIdx.x == 0) {
     st->rr = tot[0];
@@ -667,7 +695,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_cg_rz(int64_t n, const V *r, cons
                         RedScratch rs) {
   pdl_wait();
   const int stop = stop_flag(st);
-  V p = V(0);
+  DotAcc<V> p;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   constexpr int U = kIlpStream;
   for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c0 < n;
@@ -684,10 +712,10 @@ __global__ void __launch_bounds__(kBlock, 4) k_cg_rz(int64_t n, const V *r, cons
     if (stop) return;
 #pragma unroll
     for (int u = 0; u < U; ++u)
-      if (c0 + u * stride < n) p += rv[u] * zv[u];
+      if (c0 + u * stride < n) p.add(rv[u], zv[u]);
   }
   if (stop) return;  // every thread of every block (none reaches the grid sum)
-  double v[1] = {(double)p};
+  double v[1] = {p.value()};
   double tot[1];
   if (grid_sum<1>(v, rs, tot) && threadIdx.x == 0) {
     if (!(tot[0] > 0.0) || !isfinite(tot[0])) {
@@ -697,6 +725,32 @@ __global__ void __launch_bounds__(kBlock, 4) k_cg_rz(int64_t n, const V *r, cons
       st->rz = tot[0];
     }
   }
+}
+
+template <class V>
+__global__ void __launch_bounds__(kBlock, 4) k_dot(int64_t n, const V *a, const V *b,
+                                                   RedScratch rs, double *out) {
+  DotAcc<V> p;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  constexpr int U = kIlpStream;
+  for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c0 < n;
+       c0 += U * stride) {
+    V av[U], bv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t c = c0 + u * stride;
+      if (c < n) {
+        av[u] = a[c];
+        bv[u] = b[c];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (c0 + u * stride < n) p.add(av[u], bv[u]);
+  }
+  double v[1] = {p.value()};
+  double tot[1];
+  if (grid_sum<1>(v, rs, tot) && threadIdx.x == 0) *out = tot[0];
 }
 
 template <class V>
@@ -2058,6 +2112,12 @@ void launch_cg_rz(const Launch &L, int64_t n, const V *r, const V *z,
   ++*L.counter;
 }
 template <class V>
+void launch_dot(const Launch &L, int64_t n, const V *a, const V *b,
+                const RedScratch &rs, double *out) {
+  k_dot<V><<<kRedBlocks, kBlock, 0, L.s>>>(n, a, b, rs, out);
+  ++*L.counter;
+}
+template <class V>
 void launch_cg_d(const Launch &L, int64_t n, const V *z, V *d, CGState *st,
                  const cudaGraphConditionalHandle *loop) {
   ProfScope _ps(L, NF_K_CG_D);
@@ -2273,7 +2333,9 @@ void launch_mg_coarse_chain(const Launch &L, const CoarseChain<V, TA> &ch,
   template void launch_cg_rz<V>(const Launch &, int64_t, const V *,          \
                                 const V *, CGState *, const RedScratch &);    \
   template void launch_cg_d<V>(const Launch &, int64_t, const V *, V *,      \
-                               CGState *, const cudaGraphConditionalHandle *);
+                               CGState *, const cudaGraphConditionalHandle *);\
+  template void launch_dot<V>(const Launch &, int64_t, const V *, const V *, \
+                              const RedScratch &, double *);
 #define NF_INST_VA(V, TA)                                                      \
   template void launch_apply_dot<V, TA>(const Launch &, const LevelView<TA> &,\
                                         const V *, V *, CGState *,            \

@@ -129,6 +129,11 @@ void launch_cg_xr(const Launch &L, int64_t n, V *x, V *r, const V *d,
 template <class V>
 void launch_cg_rz(const Launch &L, int64_t n, const V *r, const V *z,
                   CGState *st, const RedScratch &rs);
+// *out = <a, b> over n entries, with the dot arithmetic of the CG kernels
+// (per-thread partials, fixed-order FP64 block and grid sums).
+template <class V>
+void launch_dot(const Launch &L, int64_t n, const V *a, const V *b,
+                const RedScratch &rs, double *out);
 // d = z + beta d. With `loop` (the WHILE handle of the device-side CG loop,
 // whose body this launch ends) block 0 also decides whether the loop runs
 // another iteration.

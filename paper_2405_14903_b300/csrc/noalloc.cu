@@ -47,13 +47,17 @@ int invalid(const char *msg) {
   return NF_E_INVALID;
 }
 
-bool on_device(const void *p) {
+// Device (or managed) memory of device `dev`, the device the call runs on:
+// a pointer into another GPU's memory would be dereferenced by this
+// device's kernel.
+bool on_device(const void *p, int dev) {
   cudaPointerAttributes a{};
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();  // clear the sticky-free error of the query
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeDevice) return a.device == dev;
+  return a.type == cudaMemoryTypeManaged;
 }
 
 template <class T>
@@ -108,10 +112,13 @@ extern "C" int nf_loss_noalloc(const nf_grid *gr, int loss_kind,
       (!g.outlet || g.ow < 1 || g.oh < 1 || g.oj0 < 0 || g.ok0 < 0 ||
        g.oj0 + g.ow > g.ny || g.ok0 + g.oh > g.nz))
     return invalid("outflow loss needs an outlet patch inside the high-x wall");
+  int dev = 0;
+  CKC(cudaGetDevice(&dev));
   for (int d = 0; d < 3; ++d) {
-    if (!u[d] || !on_device(u[d])) return invalid("u must be three device arrays");
-    if (gU && (!gU[d] || !on_device(gU[d])))
-      return invalid("gU must be NULL or three device arrays");
+    if (!u[d] || !on_device(u[d], dev))
+      return invalid("u must be three device arrays of the current device");
+    if (gU && (!gU[d] || !on_device(gU[d], dev)))
+      return invalid("gU must be NULL or three device arrays of the current device");
   }
   void *scratch = nullptr;
   CKS(scratch_address(&scratch));

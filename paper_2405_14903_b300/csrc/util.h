@@ -63,6 +63,7 @@ struct Ctx {
   RedScratch rs{};
   int64_t launches = 0;
   void *pinned = nullptr;  // small pinned host buffer for status readback
+  double *dscal = nullptr; // one device double (diagnostic results)
   size_t bytes_in_use = 0;
   Prof prof;
   cudaStream_t capture = nullptr;  // set while a graph is being captured

@@ -68,5 +68,10 @@ def test_cpu_baseline_one_thread_and_all_cores_on_a_small_sample():
     many = bench.cpu_baseline_all_cores(args, procs=2)
     assert one["cores"] == 1 and many["cores"] == 2
     assert one["value"] > 0 and many["value"] > 0
-    # two independent copies: at most twice the one-thread rate, up to timing noise
-    assert many["value"] <= 2.0 * one["value"] * 1.5
+    assert one["kind"] == many["kind"] == "oracle"
+    assert one["host_cpus"] == many["host_cpus"] == os.cpu_count()
+    # value counts every copy's cells over the slowest copy's time (the
+    # structure of the figure, not a timing ratio, which host load can skew)
+    assert many["value"] == pytest.approx(2 * 10 ** 3 / many["seconds"])
+    assert one["value"] == pytest.approx(10 ** 3 / one["seconds"])
+    assert many["wall_seconds"] >= many["seconds"]

@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 from tests.golden.make_golden import CASES, ORACLE_CASES, compute
+from tests.test_gpu_parity import solver_warnings
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 with open(os.path.join(HERE, "golden", "oracle_small.json")) as f:
@@ -43,11 +44,14 @@ def test_cuda_path_matches_stored_values(nf, name, prec, jtol, gtol):
     ctx = nf.Context(prec, "mgpcg", tol={"fp64": 1e-12, "mixed": 1e-10, "fp32": 1e-6}[prec],
                      max_iters=3000, checkpoint_every=2, cfl_max=cfg.get("cfl_max", 0.0))
     ep = ctx.episode(cfg["grid"], cfg["scene"])
-    ep.set_velocity([torch.tensor(x, device="cuda", dtype=torch.float64) for x in cfg["u0"]],
-                    project=cfg["project_initial"])
-    st = ep.step(cfg["steps"])
-    J, gU = ep.loss(cfg["loss"], want_grad=True)
-    gth, _, _ = ep.backward(gU)
+    recording, check = solver_warnings(prec)
+    with recording():
+        s0 = ep.set_velocity([torch.tensor(x, device="cuda", dtype=torch.float64)
+                              for x in cfg["u0"]], project=cfg["project_initial"])
+        st = ep.step(cfg["steps"])
+        J, gU = ep.loss(cfg["loss"], want_grad=True)
+        gth, _, bs = ep.backward(gU)
+    check(s0, st, bs)
     ep.close()
     ctx.close()
     assert st["steps"] + int(cfg["project_initial"]) == ref["steps"]

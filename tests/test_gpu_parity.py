@@ -21,6 +21,41 @@ pytestmark = pytest.mark.gpu
 VEL_TOL = {"fp64": 1e-9, "mixed": 1e-5, "fp32": 1e-5}
 GRAD_TOL = {"fp64": 1e-8, "mixed": 1e-4, "fp32": 1e-4}
 SOLVE_TOL = {"fp64": 1e-12, "mixed": 1e-10, "fp32": 1e-6}
+# Plain FP32 (no FP64 refinement) stalls short of its 1e-6 tolerance on the
+# chamber scenes and at 32^3: its true residual stops falling at the rounding
+# floor of FP32 vectors (1.7e-5 on the 16^3 chamber). Those solves report
+# NF_E_NOT_CONVERGED (a NotConvergedWarning); the tests accept that for FP32
+# alone and hold the residual it did reach to this bound. FP64 and MIXED
+# must converge.
+FP32_REACHED = 1e-4
+
+
+def solver_warnings(prec):
+    """A context manager recording NotConvergedWarnings, and a check to call
+    afterwards with the stats of every call made inside it."""
+    import contextlib
+    import warnings
+
+    from paper_2405_14903_b300.api import NotConvergedWarning
+
+    rec = []
+
+    @contextlib.contextmanager
+    def ctx():
+        with warnings.catch_warnings(record=True) as w:
+            warnings.simplefilter("always", NotConvergedWarning)
+            yield
+        rec.extend(x for x in w if issubclass(x.category, NotConvergedWarning))
+
+    def check(*stats):
+        if prec != "fp32":
+            assert not rec, f"{prec} solve missed its tolerance: {rec[0].message}"
+        else:
+            for st in stats:
+                assert st["rel_residual"] <= FP32_REACHED, st
+        return len(rec)
+
+    return ctx, check
 
 
 def rel(a, b):
@@ -214,10 +249,13 @@ def test_rollout_loss_and_gradient_match_oracle(nf, prec, name):
     cfg, Jo, gtho, info = oracle_rollout(name)
     ctx = make_ctx(nf, prec, cfg=cfg, checkpoint_every=2)
     ep = ctx.episode(cfg["grid"], cfg["scene"])
-    ep.set_velocity(device_u(cfg), project=cfg["project_initial"])
-    ep.step(cfg["steps"])
-    J, gU = ep.loss(cfg["loss"], want_grad=True)
-    gth, gU0, st = ep.backward(gU)
+    recording, check = solver_warnings(prec)
+    with recording():
+        s0 = ep.set_velocity(device_u(cfg), project=cfg["project_initial"])
+        fs = ep.step(cfg["steps"])
+        J, gU = ep.loss(cfg["loss"], want_grad=True)
+        gth, gU0, st = ep.backward(gU)
+    check(s0, fs, st)
     assert abs(J - Jo) <= VEL_TOL[prec] * abs(Jo)
     assert np.linalg.norm(gth - gtho) <= GRAD_TOL[prec] * np.linalg.norm(gtho)
     assert st["steps"] == sum(1 for t in info["tapes"] if t["kind"] == "step")
@@ -368,9 +406,9 @@ def test_hbm_budget_refuses_admission(nf):
     dict(mg_transfer="constant", mg_coarse_weight=1.0, mg_smooth=1),
     dict(mg_transfer="constant", mg_coarse_weight=1.8, mg_coarsest_sweeps=2),
     dict(mg_smooth=2, mg_smooth_coarse=1),
-    dict(residual_fp64=True),
+    dict(residual_fp64=False),
 ], ids=["trilinear", "trilinear_band", "constant_unweighted", "constant_1.8", "coarse_nu1",
-        "residual_fp64"])
+        "residual_split_float"])
 def test_multigrid_variants_match_oracle(nf, prec, variant):
     # the preconditioner changes the iterations, never the solution
     cfg, Jo, gtho, info = oracle_rollout("chamber_sub")
@@ -497,3 +535,24 @@ def test_cluster_coarse_levels_give_the_per_launch_bits(nf, n):
     assert s1["iters"] == s0["iters"] and f1["iters"] == f0["iters"]
     for a, b in zip(u1, u0):
         assert np.array_equal(a, b)
+
+
+# ------------------------------------------------------------------ dots ----
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_solver_dot_error_at_256_cubed(nf, dtype):
+    # the CG inner products at the size of the precision sweep (256^3 cells):
+    # FP32 vectors give exact products and compensated per-thread sums, so
+    # the whole dot is within a few FP64 roundings of the exact value
+    n = 256 ** 3
+    g = torch.Generator(device="cpu").manual_seed(3)
+    a = torch.randn(n, generator=g, dtype=torch.float64).to(dtype)
+    b = (torch.randn(n, generator=g, dtype=torch.float64) + 0.25).to(dtype)
+    ctx = nf.Context("mixed" if dtype == torch.float32 else "fp64")
+    got = ctx.dot(a.cuda(), b.cuda())
+    ctx.close()
+    import math
+    ad, bd = a.double().numpy(), b.double().numpy()
+    exact = math.fsum((ad * bd).tolist())         # products of floats are exact in FP64
+    scale = float(np.abs(ad * bd).sum())
+    assert abs(got - exact) <= 1e-12 * scale, (got, exact, scale)

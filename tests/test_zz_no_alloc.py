@@ -73,5 +73,13 @@ def test_no_alloc_loss_rejects_bad_requests(nf):
     # host arrays are refused by the binding (the C call refuses them too)
     with pytest.raises(TypeError):
         nf.loss_noalloc("kinetic_energy", g, [t.cpu() for t in u])
+    # arrays that do not hold the grid's face shapes, or a gradient triple of
+    # another shape or dtype, are refused by the binding before the C call
+    with pytest.raises(ValueError, match="shape"):
+        nf.loss_noalloc("kinetic_energy", dict(g, nx=9), u)
+    with pytest.raises(ValueError, match="gU"):
+        nf.loss_noalloc("kinetic_energy", g, u, gU=[t.double() for t in u])
+    with pytest.raises(ValueError, match="gU"):
+        nf.loss_noalloc("kinetic_energy", g, u, gU=[t[:-1].contiguous() for t in u])
     # and a valid call still works afterwards: zero field, zero energy
     assert nf.loss_noalloc("kinetic_energy", g, u) == 0.0
