@@ -76,6 +76,9 @@ def parse():
                     help="1: coarse levels above an 8^3 local chain on one thread-block cluster")
     ap.add_argument("--residual-fp64", type=int, default=1,
                     help="1: MIXED refinement residual in FP64 arithmetic (0: split-float)")
+    ap.add_argument("--mg-fused", type=int, default=0,
+                    help="1: finest-level red-black pairs as one shared-memory launch; "
+                         "2: every grid level; 0: one launch per half sweep")
     ap.add_argument("--mg-persistent", type=int, default=0,
                     help="1: coarse levels <= 64^3 and the chain in one cooperative kernel")
     ap.add_argument("--mg-coarsest", type=int, default=4,
@@ -247,7 +250,8 @@ def run_ours(args, rank, world, local_rank):
                     mg_smooth_coarse=args.mg_smooth_coarse, tape_fractions=bool(args.tape_fractions),
                     mg_persistent=bool(args.mg_persistent),
                     mg_cluster=bool(args.mg_cluster),
-                    residual_fp64=bool(args.residual_fp64), device=local_rank)
+                    residual_fp64=bool(args.residual_fp64), mg_fused=args.mg_fused,
+                    device=local_rank)
     ep = ctx.episode(cfg["grid"], cfg["scene"])
     u0 = [torch.zeros(s, dtype=torch.float32, device=dev) for s in ep.face_shapes]
     stats = {}
@@ -333,6 +337,7 @@ def run_ours(args, rank, world, local_rank):
                            mg_persistent=bool(args.mg_persistent),
                            mg_cluster=bool(args.mg_cluster),
                            residual_fp64=bool(args.residual_fp64),
+                           mg_fused=args.mg_fused,
                            l2="inputs larger than L2 (episode state and tape > 1 GB)",
                            parallelism=f"replicas x{world}"),
                gpu_launches=int(launches), iterations=dict(fwd=stats["fwd"], bwd=stats["bwd"]),

@@ -140,6 +140,14 @@ typedef struct nf_config {
                              float transforms: ~48 significant bits, error
                              about 2^-44 max|x|), free of FP64 instructions,
                              which run at 1/64 of the FP32 rate here         */
+  int mg_fused;           /* 1: each red-black sweep pair of the finest level
+                             (red then black before the coarse correction,
+                             black then red after it) is one launch over
+                             shared-memory tiles, reading x, b and the
+                             fractions once per pair (constant transfer, no
+                             band sweeps); 2: the same on every grid level
+                             above the one-block chain; 0: one launch per
+                             half sweep. Same arithmetic, same bits          */
 } nf_config;
 
 typedef struct nf_grid {
@@ -166,6 +174,16 @@ typedef struct nf_grid {
      corners (phi >= 0) and the crossings in walking order (connected fluid
      where only two diagonal corners are fluid).                          */
   int fractions;
+  /* inflow patch (0: none): wall faces of an x wall (inlet_side -1: x = 0,
+     +1: x = nx) over cells j0 .. j0 + w - 1, k0 .. k0 + h - 1 whose normal
+     velocity is held at inlet_speed (along +x). They are wall faces
+     (alpha = 0) whose solid velocity is the inflow: the blended update
+     holds them at it and the right-hand side G^T (I - S) U_s carries the
+     inflow into the projection (the inlets of Sec. 3's heart scene; the
+     inflow boundary of App. D). On the high-x wall it must not overlap the
+     outlet patch.                                                         */
+  int inlet, inlet_side, inlet_j0, inlet_k0, inlet_w, inlet_h;
+  double inlet_speed;
 } nf_grid;
 
 #define NF_FRACTIONS_SUPERSAMPLE 0
@@ -199,7 +217,7 @@ typedef struct nf_step_stats {
    checkpoint_every 10, no budget, cfl_max 0 (no sub-stepping),
    mg_coarsest_sweeps 8, mg_band_sweeps 0, mg_transfer 1 (constant),
    mg_coarse_weight 1.9, mg_smooth_coarse 0, tape_fractions 0,
-   mg_persistent 0, mg_cluster 0, residual_fp64 1. */
+   mg_persistent 0, mg_cluster 0, residual_fp64 1, mg_fused 0. */
 int nf_config_default(nf_config *cfg);
 
 /* Create a context on cfg->device. *out receives the handle. */

@@ -43,7 +43,7 @@ class Config(C.Structure):
                 ("mg_band_sweeps", C.c_int), ("mg_transfer", C.c_int),
                 ("mg_coarse_weight", C.c_double), ("mg_smooth_coarse", C.c_int),
                 ("tape_fractions", C.c_int), ("mg_persistent", C.c_int),
-                ("mg_cluster", C.c_int), ("residual_fp64", C.c_int)]
+                ("mg_cluster", C.c_int), ("residual_fp64", C.c_int), ("mg_fused", C.c_int)]
 
 
 class Grid(C.Structure):
@@ -51,7 +51,10 @@ class Grid(C.Structure):
                 ("dx", C.c_double), ("dt", C.c_double), ("rho", C.c_double),
                 ("outlet", C.c_int), ("outlet_j0", C.c_int),
                 ("outlet_k0", C.c_int), ("outlet_w", C.c_int),
-                ("outlet_h", C.c_int), ("nu", C.c_double), ("fractions", C.c_int)]
+                ("outlet_h", C.c_int), ("nu", C.c_double), ("fractions", C.c_int),
+                ("inlet", C.c_int), ("inlet_side", C.c_int), ("inlet_j0", C.c_int),
+                ("inlet_k0", C.c_int), ("inlet_w", C.c_int), ("inlet_h", C.c_int),
+                ("inlet_speed", C.c_double)]
 
 
 class Scene(C.Structure):

@@ -52,8 +52,13 @@ def grid_struct(desc):
     g.dx, g.dt, g.rho = desc["dx"], desc["dt"], desc.get("rho", 1.0)
     if desc.get("periodic", False):
         raise ValueError("the CUDA path implements closed boxes (walls and an outlet patch)")
-    if desc.get("inlet"):
-        raise ValueError("the CUDA path has no inflow patch (walls and an outlet patch only)")
+    i = desc.get("inlet")
+    if i:
+        if i["axis"] != 0 or i["side"] not in (-1, 1):
+            raise ValueError("inflow patches are on an x wall")
+        g.inlet, g.inlet_side = 1, int(i["side"])
+        g.inlet_j0, g.inlet_k0, g.inlet_w, g.inlet_h = i["j0"], i["k0"], i["w"], i["h"]
+        g.inlet_speed = float(i["speed"])
     g.nu = float(desc.get("nu", 0.0))
     rule = desc.get("fractions", "supersample")
     if rule not in L.FRACTIONS:
@@ -156,7 +161,7 @@ def _config(precision="mixed", solver="mgpcg", tol=1e-6, max_iters=500,
             checkpoint_every=10, hbm_budget=0, cfl_max=0.0, mg_coarsest_sweeps=8,
             mg_band_sweeps=0, mg_transfer="constant", mg_coarse_weight=1.9,
             mg_smooth_coarse=0, tape_fractions=False, mg_persistent=False,
-            mg_cluster=False, residual_fp64=True, device=0, stream=0):
+            mg_cluster=False, residual_fp64=True, mg_fused=0, device=0, stream=0):
     """An ``nf_config`` from keyword arguments (defaults of nf_config_default)."""
     cfg = L.Config()
     _check(lib.nf_config_default(C.byref(cfg)))
@@ -182,6 +187,7 @@ def _config(precision="mixed", solver="mgpcg", tol=1e-6, max_iters=500,
     cfg.mg_persistent = int(bool(mg_persistent))
     cfg.mg_cluster = int(bool(mg_cluster))
     cfg.residual_fp64 = int(bool(residual_fp64))
+    cfg.mg_fused = int(mg_fused)
     return cfg
 
 

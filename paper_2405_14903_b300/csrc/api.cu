@@ -207,6 +207,7 @@ int nf_config_default(nf_config *cfg) {
   cfg->mg_persistent = 0;
   cfg->mg_cluster = 0;
   cfg->residual_fp64 = 1;
+  cfg->mg_fused = 0;
   return NF_OK;
 }
 
@@ -243,6 +244,7 @@ int nf_create(nf_ctx **out, const nf_config *cfg) {
       cfg->mg_smooth_coarse < 0 || (cfg->tape_fractions != 0 && cfg->tape_fractions != 1) ||
       (cfg->mg_persistent != 0 && cfg->mg_persistent != 1) ||
       (cfg->residual_fp64 != 0 && cfg->residual_fp64 != 1) ||
+      cfg->mg_fused < 0 || cfg->mg_fused > 2 ||
       (cfg->mg_cluster != 0 && cfg->mg_cluster != 1)) {
     set_error("nf_create: invalid configuration");
     return NF_E_INVALID;
@@ -342,6 +344,21 @@ int nf_episode_create(nf_ctx *ctx, const nf_grid *g, const nf_scene *s,
                     g->outlet_k0 + g->outlet_h > g->nz)) {
     set_error("nf_episode_create: outlet patch outside the high-x wall");
     return NF_E_INVALID;
+  }
+  if (g->inlet) {
+    const bool inside = (g->inlet_side == 1 || g->inlet_side == -1) && g->inlet_j0 >= 0 &&
+                        g->inlet_k0 >= 0 && g->inlet_w > 0 && g->inlet_h > 0 &&
+                        g->inlet_j0 + g->inlet_w <= g->ny && g->inlet_k0 + g->inlet_h <= g->nz;
+    const bool overlap = g->outlet && g->inlet_side == 1 &&
+                         g->inlet_j0 < g->outlet_j0 + g->outlet_w &&
+                         g->outlet_j0 < g->inlet_j0 + g->inlet_w &&
+                         g->inlet_k0 < g->outlet_k0 + g->outlet_h &&
+                         g->outlet_k0 < g->inlet_k0 + g->inlet_h;
+    if (!inside || overlap || !std::isfinite(g->inlet_speed)) {
+      set_error("nf_episode_create: inflow patch outside an x wall, over the outlet, or "
+                "with a non-finite speed");
+      return NF_E_INVALID;
+    }
   }
   if (s->kind < NF_SCENE_NONE || s->kind > NF_SCENE_SPHERES) {
     set_error("nf_episode_create: unknown scene kind");

@@ -198,6 +198,13 @@ class EpisodeImpl : public EpisodeBase {
     g.ok0 = gr.outlet_k0;
     g.ow = gr.outlet_w;
     g.oh = gr.outlet_h;
+    g.inlet = gr.inlet;
+    g.iside = gr.inlet_side;
+    g.ij0 = gr.inlet_j0;
+    g.ik0 = gr.inlet_k0;
+    g.iw = gr.inlet_w;
+    g.ih = gr.inlet_h;
+    g.ispeed = gr.inlet_speed;
     return g;
   }
 
@@ -558,12 +565,16 @@ class EpisodeImpl : public EpisodeBase {
   // rasterised for scene state sd): uh -> P, u_out.
   int project_faces(const GridDev &g, const SceneDev &sd, const T *uh, S *P,
                     T *u_out, SolveStats *ss) {
+    NvtxRange nv("nf.project");
     Launch L = ctx_->launch();
     CKS(cc_.label<T>(ctx_, g, cview(alpha_)));
     launch_rhs<T, S>(L, g, sd, cview(alpha_), cview(uh), b_, ctx_->rs, dscal_);
     solver_.set_fractions(comp(alpha_, 0), comp(alpha_, 1), comp(alpha_, 2));
     const double bn2 = gauge(b_, ctx_->read_double(dscal_));
-    *ss = solver_.solve(b_, P, bn2);
+    {
+      NvtxRange nvs("nf.solve");
+      *ss = solver_.solve(b_, P, bn2);
+    }
     gauge(P, 0.0);
     launch_update<T, S>(L, g, sd, cview(alpha_), cview(uh), P, mut(u_out));
     return NF_OK;
@@ -572,6 +583,7 @@ class EpisodeImpl : public EpisodeBase {
   // Step m (from ts_[m] - hs_[m] to ts_[m]): u_in -> uh, P, u_out (u_out
   // may alias u_in).
   int forward_step(int m, const T *u_in, T *u_out, T *uh, S *P, SolveStats *ss) {
+    NvtxRange nv("nf.step");
     Launch L = ctx_->launch();
     const GridDev g = grid_h(hs_[m]);
     const SceneDev sd = scene_at(sc_, ts_[m], dsph_);
@@ -580,6 +592,7 @@ class EpisodeImpl : public EpisodeBase {
       // to rasterising them again)
       CKC(cudaMemcpyAsync(alpha_, tapeA_[m], nfaces_ * sizeof(T), cudaMemcpyDeviceToDevice, L.s));
     } else {
+      NvtxRange nvr("nf.rasterize");
       launch_rasterize<T>(L, g, sd, mut(alpha_));
       if (ctx_->cfg.tape_fractions) {
         if ((int)tapeA_.size() <= m) {
@@ -591,6 +604,7 @@ class EpisodeImpl : public EpisodeBase {
         tapeA_ok_[m] = 1;
       }
     }
+    NvtxRange nva("nf.advect");
     if (Ut_) {
       // U~ = B(U) U, then U^ = (I - nu h / dx^2 G^T G) U~ (Sec. 2.3.1)
       launch_advect<T>(L, g, cview(u_in), mut(Ut_), ctx_->cfg.advect_order);
@@ -622,6 +636,7 @@ class EpisodeImpl : public EpisodeBase {
 
   // Recompute segment s from its checkpoint, recording the per-step tape.
   int recompute_segment(int s, nf_step_stats *st) {
+    NvtxRange nv("nf.recompute");
     const int C = std::max(1, ctx_->cfg.checkpoint_every);
     CKS(ensure_segment_buffers(C));
     const int start = s * C, end = std::min(start + C, n_);
@@ -649,6 +664,7 @@ class EpisodeImpl : public EpisodeBase {
   int adjoint_projection(const GridDev &g, const SceneDev &sd, const T *uh,
                          const S *P, double *gth, nf_step_stats *st,
                          bool relabel = true) {
+    NvtxRange nv("nf.adjoint_projection");
     Launch L = ctx_->launch();
     if (relabel)
       CKS(cc_.label<T>(ctx_, g, cview(alpha_)));
@@ -672,6 +688,7 @@ class EpisodeImpl : public EpisodeBase {
 
   // Revert the most recent unreverted step (or the initial projection).
   int revert_one(double *gth, nf_step_stats *st) {
+    NvtxRange nv("nf.backward_step");
     Launch L = ctx_->launch();
     if (n_rev_ == 0) {
       if (!init_proj_ || init_reverted_)
@@ -701,8 +718,11 @@ class EpisodeImpl : public EpisodeBase {
       launch_viscosity<T>(L, g, cview(gUh_), mut(Ut_));
       gUt = Ut_;
     }
-    launch_advect_adjoint<T>(L, g, cview(segU_[k]), cview(gUt), mut(gUb_),
-                             ctx_->cfg.advect_order);
+    {
+      NvtxRange nva("nf.advect_adjoint");
+      launch_advect_adjoint<T>(L, g, cview(segU_[k]), cview(gUt), mut(gUb_),
+                               ctx_->cfg.advect_order);
+    }
     std::swap(gU_, gUb_);
     n_rev_ = m;
     st->steps += 1;

@@ -1003,6 +1003,262 @@ __global__ void k_mg_smooth(LevelView<TA> lv, V *x, const V *b, int color,
   sweep_rows<V, TA, MODE>(lv, x, b, color, f, w.warp, w.nwarps, w.lane, stop);
 }
 
+// ------------------------------------------ fused red-black sweep pair -----
+// One launch applies two half sweeps of a level: colour c1 in mode MODE
+// (zero start, x as stored, or x with the folded constant prolongation),
+// then colour 1 - c1 (x as just updated). Each block owns a TX x TY column
+// of cells and marches up a chunk of planes, ZB planes per step, with the
+// operands staged in shared memory:
+//   - x (other colour of c1) over the tile plus a halo of two cells, read
+//     once from xin (not at all in zero-start mode);
+//   - b and the three fraction arrays over the tile plus one cell;
+//   - in each step the loaded planes are written to shared memory, the next
+//     ZB planes are requested into registers (their latency hides under the
+//     sweeps), the first half sweep runs one plane behind the newest plane
+//     over the tile plus one cell, and the second half sweep one plane
+//     further behind over the tile, storing both colours of its planes.
+// Both half sweeps read only the other colour, so cells of the halo are
+// recomputed by each block that needs them (no exchange between blocks),
+// and the result goes to xout (never xin: a neighbour block still reads
+// the input halo). The per-cell arithmetic is that of sweep_cell, in the
+// same order, so the pair equals two k_mg_smooth launches bit for bit.
+// Loads: x 4 (x halo), b 4 + fractions 3 sizeof(TA) (halo 1); stores: x 4.
+template <class V, class TA, int TX, int TY, int ZB>
+struct RbPair {
+  static constexpr int NT = 256;                   // threads per block
+  static constexpr int XW = TX + 4, XH = TY + 4;   // x region (halo 2)
+  static constexpr int BW = TX + 2, BH = TY + 2;   // b and z-face region (halo 1)
+  static constexpr int AXW = TX + 3;               // x faces: one more column
+  static constexpr int AYH = TY + 3;               // y faces: one more row
+  static constexpr int NX = XW * XH, NB = BW * BH, NAX = AXW * BH, NAY = BW * AYH;
+  static constexpr int DX = ZB + 3;                // planes of x kept
+  static constexpr int DA = ZB + 2;                // planes of b and fractions kept
+  // per-thread register slots of one batch of ZB planes
+  static constexpr int MX = (ZB * NX + NT - 1) / NT;
+  static constexpr int MB = (ZB * NB + NT - 1) / NT;
+  static constexpr int MAX = (ZB * NAX + NT - 1) / NT;
+  static constexpr int MAY = (ZB * NAY + NT - 1) / NT;
+  static constexpr size_t off_b = (size_t)DX * NX * sizeof(V);
+  static constexpr size_t off_ax = off_b + (size_t)DA * NB * sizeof(V);
+  static constexpr size_t off_ay = off_ax + (size_t)DA * NAX * sizeof(TA);
+  static constexpr size_t off_az = off_ay + (size_t)DA * NAY * sizeof(TA);
+  static constexpr size_t bytes = off_az + (size_t)DA * NB * sizeof(TA);
+  static_assert(TX % 2 == 0, "cells are swept in x pairs");
+};
+
+template <class V, class TA, int MODE, int TX, int TY, int ZB>
+__global__ void __launch_bounds__(256, 2)
+k_mg_rb_pair(LevelView<TA> lv, const V *xin, V *xout, const V *b, int c1, int zc,
+             Fold<V> f, const CGState *st) {
+  using C = RbPair<V, TA, TX, TY, ZB>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V *sx = (V *)smem_raw;
+  V *sb = (V *)(smem_raw + C::off_b);
+  TA *sax = (TA *)(smem_raw + C::off_ax);
+  TA *say = (TA *)(smem_raw + C::off_ay);
+  TA *saz = (TA *)(smem_raw + C::off_az);
+  pdl_wait();
+  if (stop_flag(st)) return;  // every thread of the block
+
+  const int nx = lv.nx, ny = lv.ny, nz = lv.nz, nxy = nx * ny;
+  const int nbx = (nx + TX - 1) / TX, nby = (ny + TY - 1) / TY;
+  const int bxi = blockIdx.x % nbx, rest = blockIdx.x / nbx;
+  const int byi = rest % nby, bzi = rest / nby;
+  const int x0 = bxi * TX, y0 = byi * TY, z0 = bzi * zc;
+  const int z1 = min(z0 + zc, nz);
+  const int c2 = c1 ^ 1;
+  const V cc = V(lv.c);
+  // ring slot of plane p (p >= -2 - ZB)
+  auto slx = [](int p) { return (p + 4 * C::DX) % C::DX; };
+  auto sla = [](int p) { return (p + 4 * C::DA) % C::DA; };
+
+  // registers of one batch of planes [p0, p0 + ZB)
+  V rx[C::MX], rb[C::MB];
+  TA rax[C::MAX], ray[C::MAY], raz[C::MB];
+
+  auto fetch = [&](int p0) {
+    if (MODE != kSweepZero) {
+#pragma unroll
+      for (int m = 0; m < C::MX; ++m) {
+        const int e = threadIdx.x + m * C::NT;
+        V v = V(0);
+        if (e < ZB * C::NX) {
+          const int pz = e / C::NX, rem = e - pz * C::NX;
+          const int r = rem / C::XW, col = rem - r * C::XW;
+          const int gi = x0 - 2 + col, gj = y0 - 2 + r, gk = p0 + pz;
+          // only the other colour of the first half sweep is read
+          if (gi >= 0 && gi < nx && gj >= 0 && gj < ny && gk >= 0 && gk < nz &&
+              ((gi + gj + gk) & 1) == c2) {
+            v = xin[gk * nxy + gj * nx + gi];
+            if (MODE == kSweepProlong)
+              v += f.xc[((gk >> 1) * f.cny + (gj >> 1)) * f.cnx + (gi >> 1)] * f.w;
+          }
+        }
+        rx[m] = v;
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < C::MB; ++m) {
+      const int e = threadIdx.x + m * C::NT;
+      V v = V(0);
+      TA a = TA(0.f);
+      if (e < ZB * C::NB) {
+        const int pz = e / C::NB, rem = e - pz * C::NB;
+        const int r = rem / C::BW, col = rem - r * C::BW;
+        const int gi = x0 - 1 + col, gj = y0 - 1 + r, gk = p0 + pz;
+        if (gi >= 0 && gi < nx && gj >= 0 && gj < ny && gk >= 0 && gk <= nz) {
+          if (gk < nz) v = b[gk * nxy + gj * nx + gi];
+          a = lv.az[gk * nxy + gj * nx + gi];
+        }
+      }
+      rb[m] = v;
+      raz[m] = a;
+    }
+#pragma unroll
+    for (int m = 0; m < C::MAX; ++m) {
+      const int e = threadIdx.x + m * C::NT;
+      TA a = TA(0.f);
+      if (e < ZB * C::NAX) {
+        const int pz = e / C::NAX, rem = e - pz * C::NAX;
+        const int r = rem / C::AXW, col = rem - r * C::AXW;
+        const int gi = x0 - 1 + col, gj = y0 - 1 + r, gk = p0 + pz;
+        if (gi >= 0 && gi <= nx && gj >= 0 && gj < ny && gk >= 0 && gk < nz)
+          a = lv.ax[(gk * ny + gj) * (nx + 1) + gi];
+      }
+      rax[m] = a;
+    }
+#pragma unroll
+    for (int m = 0; m < C::MAY; ++m) {
+      const int e = threadIdx.x + m * C::NT;
+      TA a = TA(0.f);
+      if (e < ZB * C::NAY) {
+        const int pz = e / C::NAY, rem = e - pz * C::NAY;
+        const int r = rem / C::BW, col = rem - r * C::BW;
+        const int gi = x0 - 1 + col, gj = y0 - 1 + r, gk = p0 + pz;
+        if (gi >= 0 && gi < nx && gj >= 0 && gj <= ny && gk >= 0 && gk < nz)
+          a = lv.ay[(gk * (ny + 1) + gj) * nx + gi];
+      }
+      ray[m] = a;
+    }
+  };
+
+  auto stage = [&](int p0) {
+    if (MODE != kSweepZero) {
+#pragma unroll
+      for (int m = 0; m < C::MX; ++m) {
+        const int e = threadIdx.x + m * C::NT;
+        if (e < ZB * C::NX) {
+          const int pz = e / C::NX, rem = e - pz * C::NX;
+          sx[slx(p0 + pz) * C::NX + rem] = rx[m];
+        }
+      }
+    } else {
+      // zero start: the other colour is 0 wherever the first half sweep reads it
+      for (int e = threadIdx.x; e < ZB * C::NX; e += C::NT) {
+        const int pz = e / C::NX, rem = e - pz * C::NX;
+        sx[slx(p0 + pz) * C::NX + rem] = V(0);
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < C::MB; ++m) {
+      const int e = threadIdx.x + m * C::NT;
+      if (e < ZB * C::NB) {
+        const int pz = e / C::NB, rem = e - pz * C::NB;
+        sb[sla(p0 + pz) * C::NB + rem] = rb[m];
+        saz[sla(p0 + pz) * C::NB + rem] = raz[m];
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < C::MAX; ++m) {
+      const int e = threadIdx.x + m * C::NT;
+      if (e < ZB * C::NAX) {
+        const int pz = e / C::NAX, rem = e - pz * C::NAX;
+        sax[sla(p0 + pz) * C::NAX + rem] = rax[m];
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < C::MAY; ++m) {
+      const int e = threadIdx.x + m * C::NT;
+      if (e < ZB * C::NAY) {
+        const int pz = e / C::NAY, rem = e - pz * C::NAY;
+        say[sla(p0 + pz) * C::NAY + rem] = ray[m];
+      }
+    }
+  };
+
+  // The 13 operands of cell (gi, gj, q) from shared memory; neighbours
+  // outside the level read the staged zeros (ghost x = 0), as gather7r.
+  auto gather = [&](Nb7<V> &g, V &bc, int gi, int gj, int q) {
+    const int lx = gi - (x0 - 2), ly = gj - (y0 - 2);
+    const int bx = gi - (x0 - 1), by = gj - (y0 - 1);
+    const int a0 = sla(q), a1 = sla(q + 1);
+    g.xm = (V)ld(sax + a0 * C::NAX + by * C::AXW + bx);
+    g.xp = (V)ld(sax + a0 * C::NAX + by * C::AXW + bx + 1);
+    g.ym = (V)ld(say + a0 * C::NAY + by * C::BW + bx);
+    g.yp = (V)ld(say + a0 * C::NAY + (by + 1) * C::BW + bx);
+    g.zm = (V)ld(saz + a0 * C::NB + by * C::BW + bx);
+    g.zp = (V)ld(saz + a1 * C::NB + by * C::BW + bx);
+    const V *xq = sx + slx(q) * C::NX + ly * C::XW + lx;
+    g.vxm = xq[-1];
+    g.vxp = xq[1];
+    g.vym = xq[-C::XW];
+    g.vyp = xq[C::XW];
+    g.vzm = sx[slx(q - 1) * C::NX + ly * C::XW + lx];
+    g.vzp = sx[slx(q + 1) * C::NX + ly * C::XW + lx];
+    bc = sb[a0 * C::NB + by * C::BW + bx];
+  };
+
+  const int s1lo = max(z0 - 1, 0), s1hi = min(z1, nz - 1);  // first half sweep planes
+  fetch(z0 - 2);
+  for (int p0 = z0 - 2; p0 - 2 < z1; p0 += ZB) {
+    __syncthreads();  // the previous step's sweeps are done with the slots reused here
+    stage(p0);
+    __syncthreads();
+    if (p0 + ZB <= z1 + 1) fetch(p0 + ZB);
+    // first half sweep: colour c1 on planes p0 - 1 .. p0 + ZB - 2, tile + 1
+    for (int e = threadIdx.x; e < ZB * C::BH * (C::BW / 2); e += C::NT) {
+      const int pz = e / (C::BH * (C::BW / 2)), rem = e - pz * (C::BH * (C::BW / 2));
+      const int r = rem / (C::BW / 2), m = rem - r * (C::BW / 2);
+      const int q = p0 - 1 + pz, gj = y0 - 1 + r;
+      const int gi = x0 - 1 + 2 * m + ((c1 + x0 + 1 + gj + q) & 1);
+      if (q < s1lo || q > s1hi || gj < 0 || gj >= ny || gi < 0 || gi >= nx) continue;
+      Nb7<V> g;
+      V bc;
+      gather(g, bc, gi, gj, q);
+      const V dg = g.diag();
+      V v;
+      if (MODE == kSweepZero)
+        v = dg > V(0) ? bc / (cc * dg) : V(0);
+      else
+        v = dg > V(0) ? (bc + cc * g.nb()) / (cc * dg) : V(0);
+      sx[slx(q) * C::NX + (gj - (y0 - 2)) * C::XW + (gi - (x0 - 2))] = v;
+    }
+    __syncthreads();
+    // second half sweep: colour c2 on planes p0 - 2 .. p0 + ZB - 3, tile;
+    // each thread stores one cell pair of a row
+    for (int e = threadIdx.x; e < ZB * TY * (TX / 2); e += C::NT) {
+      const int pz = e / (TY * (TX / 2)), rem = e - pz * (TY * (TX / 2));
+      const int r = rem / (TX / 2), m = rem - r * (TX / 2);
+      const int q = p0 - 2 + pz, gj = y0 + r;
+      if (q < z0 || q >= z1 || gj >= ny) continue;
+      const int par = (c2 + x0 + gj + q) & 1;
+      const int gi2 = x0 + 2 * m + par, gi1 = x0 + 2 * m + (par ^ 1);
+      V v = V(0);
+      if (gi2 < nx) {
+        Nb7<V> g;
+        V bc;
+        gather(g, bc, gi2, gj, q);
+        const V dg = g.diag();
+        v = dg > V(0) ? (bc + cc * g.nb()) / (cc * dg) : V(0);
+      }
+      const int row = q * nxy + gj * nx;
+      if (gi1 < nx)
+        xout[row + gi1] = sx[slx(q) * C::NX + (gj - (y0 - 2)) * C::XW + (gi1 - (x0 - 2))];
+      if (gi2 < nx) xout[row + gi2] = v;
+    }
+  }
+}
+
 // Prolongation normaliser of fine cell (i, j, k): 1 / (sum of the trilinear
 // weights of its active coarse cells), 0 if none is active. The V-cycle uses
 // P' = N P and R' = P'^T / 4 = P^T N / 4: near a Neumann (solid) boundary the
@@ -2148,6 +2404,40 @@ void launch_mg_smooth(const Launch &L, const LevelView<TA> &lv, V *x,
     launch_pdl(k_mg_smooth<V, TA, kSweepPlain>, nb, kBlock, 0, L.s, lv, x, b, color, f, st);
   ++*L.counter;
 }
+// Tile shapes of the fused pair: 32 x 8 cells per block, 4 planes per step
+// for FP32 vectors (46 KB of shared memory), 2 for FP64 (62 KB).
+template <class V, class TA, int MODE>
+static void rb_pair_kernel(const Launch &L, const LevelView<TA> &lv, const V *xin, V *xout,
+                           const V *b, int c1, const Fold<V> &f, const CGState *st) {
+  constexpr int TX = 32, TY = 8, ZB = sizeof(V) == 4 ? 4 : 2;
+  using C = RbPair<V, TA, TX, TY, ZB>;
+  auto kernel = k_mg_rb_pair<V, TA, MODE, TX, TY, ZB>;
+  static bool ready = false;  // one attribute call per instantiation
+  if (!ready) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::bytes);
+    ready = true;
+  }
+  const int nbx = (lv.nx + TX - 1) / TX, nby = (lv.ny + TY - 1) / TY;
+  // planes per block: 32, halved (to 8 at least) until there are two blocks
+  // per SM
+  int zc = 32;
+  while (zc > 8 && (int64_t)nbx * nby * ((lv.nz + zc - 1) / zc) < 2 * 148) zc /= 2;
+  const unsigned nb = (unsigned)(nbx * nby * ((lv.nz + zc - 1) / zc));
+  launch_pdl(kernel, nb, (unsigned)C::NT, C::bytes, L.s, lv, xin, xout, b, c1, zc, f, st);
+}
+template <class V, class TA>
+void launch_mg_rb_pair(const Launch &L, const LevelView<TA> &lv, const V *xin, V *xout,
+                       const V *b, int c1, int mode, const Fold<V> &f, const CGState *st,
+                       int kclass) {
+  ProfScope _ps(L, kclass);
+  if (mode == kSweepZero)
+    rb_pair_kernel<V, TA, kSweepZero>(L, lv, xin, xout, b, c1, f, st);
+  else if (mode == kSweepProlong)
+    rb_pair_kernel<V, TA, kSweepProlong>(L, lv, xin, xout, b, c1, f, st);
+  else
+    rb_pair_kernel<V, TA, kSweepPlain>(L, lv, xin, xout, b, c1, f, st);
+  ++*L.counter;
+}
 template <class TA>
 void launch_band_build(const Launch &L, const LevelView<TA> &lv,
                        unsigned char *mark, int *list0, int *list1, int *count) {
@@ -2343,6 +2633,9 @@ void launch_mg_coarse_chain(const Launch &L, const CoarseChain<V, TA> &ch,
   template void launch_mg_smooth<V, TA>(const Launch &, const LevelView<TA> &,\
                                         V *, const V *, int, int,             \
                                         const Fold<V> &, const CGState *, int);\
+  template void launch_mg_rb_pair<V, TA>(const Launch &, const LevelView<TA> &,\
+                                         const V *, V *, const V *, int, int, \
+                                         const Fold<V> &, const CGState *, int);\
   template void launch_band_smooth<V, TA>(const Launch &,                    \
                                           const LevelView<TA> &, V *,         \
                                           const V *, const int *,             \

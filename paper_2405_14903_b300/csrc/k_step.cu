@@ -433,13 +433,15 @@ __global__ void k_advect_adjoint(GridDev g, Fields<T> u, Fields<T> gut,
 }
 
 // ----------------------------------------------------- face helpers -------
-// Solid velocity of a component-d face (0 on the box boundary), evaluated in
+// Solid velocity of a component-d face (0 on the box boundary but for an
+// inflow patch's faces, which carry the inflow speed), evaluated in
 // the field precision T (positions formed in T: no FP64 for FP32 fields).
 template <class T>
 __device__ __forceinline__ T face_us(const GridDev &g, const SceneDev &s,
                                      int d, int i, int j, int k) {
+  // box walls: at rest, except the faces of an inflow patch
+  if (g.boundary(d, i, j, k)) return g.inlet_face(d, i, j, k) ? T(g.ispeed) : T(0);
   if (s.kind == NF_SCENE_NONE || s.kind == NF_SCENE_SPHERES) return T(0);
-  if (g.boundary(d, i, j, k)) return T(0);
   const T h = T(g.dx);
   const T X = (T(i) + (d == 0 ? T(0) : T(0.5))) * h;
   const T Y = (T(j) + (d == 1 ? T(0) : T(0.5))) * h;

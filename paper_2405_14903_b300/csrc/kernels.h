@@ -167,6 +167,14 @@ struct Fold {
 template <class TI, class TO>
 void launch_mg_coarsen(const Launch &L, const LevelView<TI> &fine,
                        int cnx, int cny, int cnz, TO *ax, TO *ay, TO *az);
+// Two half sweeps in one launch: colour c1 in mode kSweep* (fold f), then
+// colour 1 - c1 as stored; reads xin (unused in zero-start mode), writes
+// every cell of xout (xout != xin). Equal, bit for bit, to the two
+// launch_mg_smooth calls on one array.
+template <class V, class TA>
+void launch_mg_rb_pair(const Launch &L, const LevelView<TA> &lv, const V *xin, V *xout,
+                       const V *b, int c1, int mode, const Fold<V> &f, const CGState *st,
+                       int kclass);
 // Red-black half sweep of colour `color`; mode kSweep* with its fold f.
 template <class V, class TA>
 void launch_mg_smooth(const Launch &L, const LevelView<TA> &lv, V *x,

@@ -25,6 +25,8 @@ struct GridDev {
   double nu;              // kinematic viscosity (0: inviscid)
   int frac;               // NF_FRACTIONS_* rule of the face fractions
   int outlet, oj0, ok0, ow, oh;
+  int inlet, iside, ij0, ik0, iw, ih;  // inflow patch on an x wall (side -1 / +1)
+  double ispeed;                       // its normal velocity (along +x)
 
   __host__ __device__ int64_t ncell() const { return (int64_t)nx * ny * nz; }
   __host__ __device__ int fnx(int d) const { return nx + (d == 0); }
@@ -62,6 +64,10 @@ struct GridDev {
     int o = d == 0 ? i : (d == 1 ? j : k);
     int n = d == 0 ? nx : (d == 1 ? ny : nz);
     return o == 0 || o == n;
+  }
+  __host__ __device__ bool inlet_face(int d, int i, int j, int k) const {
+    return inlet && d == 0 && i == (iside > 0 ? nx : 0) && j >= ij0 && j < ij0 + iw &&
+           k >= ik0 && k < ik0 + ih;
   }
   __host__ __device__ bool outlet_face(int d, int i, int j, int k) const {
     return outlet && d == 0 && i == nx && j >= oj0 && j < oj0 + ow &&

@@ -489,6 +489,31 @@ class Solver {
   // Pre-smoothing and restriction of levels lo .. hi-1 (level 0: x = z,
   // b = r), one launch per phase. x starts from zero: the first half sweep
   // reads no x, unless the boundary band sweeps first.
+  // Sweep pairs as fused launches (constant transfer): level 0 with
+  // mg_fused >= 1 (and no band sweeps), the coarser grid levels with
+  // mg_fused = 2. Pair m of a level's 2 nu pairs writes the level's x (z on
+  // level 0) when 2 nu - 1 - m is even and the level's spare vector (r,
+  // unused by the constant transfer) otherwise, and reads pair m - 1's
+  // output, so the last pre-smoothing pair's output is what the restriction
+  // reads and the last pair leaves the result in x.
+  bool fused(int l) const {
+    if (!mg_ || cfg_.mg_transfer != 1 || levels_.size() < 2 || cfg_.mg_fused < 1) return false;
+    return l == 0 ? !band_count_ : cfg_.mg_fused >= 2;
+  }
+  int nu_at(int l) const { return l == 0 ? std::max(1, cfg_.mg_smooth) : nu_coarse(); }
+  V *pair_out(int l, V *z, int m) const {
+    V *x = l == 0 ? z : (V *)levels_[l].x;
+    return ((2 * nu_at(l) - 1 - m) & 1) ? (V *)levels_[l].r : x;
+  }
+  void pair(int l, const V *in, V *out, const V *b, int c1, int mode, const Fold<V> &f,
+            const CGState *st) {
+    Launch L = ctx_->launch();
+    if (l == 0)
+      launch_mg_rb_pair<V, T>(L, view0(), in, out, b, c1, mode, f, st, NF_K_MG_SMOOTH0);
+    else
+      launch_mg_rb_pair<V, TA>(L, viewc(l), in, out, b, c1, mode, f, st, NF_K_MG_SMOOTH);
+  }
+
   void down_levels(int lo, int hi, const V *r, V *z, const CGState *st) {
     Launch L = ctx_->launch();
     for (int l = lo; l < hi; ++l) {
@@ -501,9 +526,17 @@ class Solver {
         band(x, b, 0, st);
       }
       const int nu = l == 0 ? std::max(1, cfg_.mg_smooth) : nu_coarse();
-      for (int s = 0; s < nu; ++s) {
-        smooth(l, x, b, 0, st, s == 0 && !banded ? kSweepZero : kSweepPlain);
-        smooth(l, x, b, 1, st);
+      if (fused(l)) {
+        for (int s = 0; s < nu; ++s) {
+          x = pair_out(l, z, s);
+          pair(l, s == 0 ? nullptr : pair_out(l, z, s - 1), x, b, 0,
+               s == 0 ? kSweepZero : kSweepPlain, Fold<V>{nullptr, 0, 0, V(0)}, st);
+        }
+      } else {
+        for (int s = 0; s < nu; ++s) {
+          smooth(l, x, b, 0, st, s == 0 && !banded ? kSweepZero : kSweepPlain);
+          smooth(l, x, b, 1, st);
+        }
       }
       const Level &C = levels_[l + 1];
       if (cfg_.mg_transfer == 1) {
@@ -536,6 +569,14 @@ class Solver {
       const Level &C = levels_[l + 1];
       const int nu = l == 0 ? std::max(1, cfg_.mg_smooth) : nu_coarse();
       int s = 0;
+      if (fused(l)) {
+        const Fold<V> f{(const V *)C.x, C.nx, C.ny, V(coarse_w())};
+        for (int m = nu; m < 2 * nu; ++m)
+          pair(l, pair_out(l, z, m - 1), pair_out(l, z, m), b, 1,
+               m == nu ? kSweepProlong : kSweepPlain, m == nu ? f : Fold<V>{nullptr, 0, 0, V(0)},
+               st);
+        continue;
+      }
       if (cfg_.mg_transfer == 1) {
         const Fold<V> f{(const V *)C.x, C.nx, C.ny, V(coarse_w())};
         smooth(l, x, b, 1, st, kSweepProlong, f);

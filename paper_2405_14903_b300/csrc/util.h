@@ -4,6 +4,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "nf_internal.cuh"
 
 namespace nf {
@@ -94,6 +96,16 @@ struct Alloc {
   }
   void free_all();
   ~Alloc() { free_all(); }
+};
+
+// A named host range for profilers (NVTX: nsys and ncu group the launches
+// of a phase under it). Header-only; without an attached tool each range
+// costs a pointer test.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
 }  // namespace nf

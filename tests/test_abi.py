@@ -65,7 +65,7 @@ def test_status_strings_and_defaults(lib):
     assert lib.nf_config_default(ctypes.byref(cfg)) == 0
     assert cfg.precision == _lib.PREC["mixed"] and cfg.solver == _lib.SOLVER["mgpcg"]
     assert cfg.checkpoint_every == 10 and abs(cfg.tol - 1e-6) < 1e-18
-    assert cfg.mg_transfer == 1 and cfg.mg_persistent == 0 and cfg.residual_fp64 == 1
+    assert cfg.mg_transfer == 1 and cfg.mg_persistent == 0 and cfg.residual_fp64 == 1 and cfg.mg_fused == 0
     assert cfg.mg_cluster == 0
 
 
@@ -137,8 +137,11 @@ def test_grid_marshalling_of_viscosity_and_fraction_rule():
         grid_struct(dict(I.make_grid(8, 0.01), fractions="marching"))
     with pytest.raises(ValueError):
         grid_struct(I.make_grid(8, 0.01, periodic=True))
+    g = grid_struct(I.make_grid(8, 0.01, inlet=I.centred_inlet(8, 2, 0.3)))
+    assert (g.inlet, g.inlet_side, g.inlet_j0, g.inlet_k0, g.inlet_w, g.inlet_h) == \
+        (1, -1, 3, 3, 2, 2) and g.inlet_speed == 0.3
     with pytest.raises(ValueError):
-        grid_struct(I.make_grid(8, 0.01, inlet=I.centred_inlet(8, 2, 0.3)))
+        grid_struct(I.make_grid(8, 0.01, inlet=dict(I.centred_inlet(8, 2, 0.3), axis=1)))
 
 
 def test_struct_field_offsets_match_the_header(tmp_path):

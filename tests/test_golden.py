@@ -57,3 +57,19 @@ def test_cuda_path_matches_stored_values(nf, name, prec, jtol, gtol):
     assert st["steps"] + int(cfg["project_initial"]) == ref["steps"]
     assert abs(J - ref["loss"]) <= jtol * abs(ref["loss"])
     assert _rel(gth, ref["dJ_dtheta"]) <= gtol
+
+
+# The verification configurations at their stated sizes (stored by
+# make_golden.py --configs, about 20 minutes of host time): the oracle's own
+# adjoint agrees with central differences of its loss (h = 1e-4) within the
+# band set by the kinks of trilinear interpolation and the fraction ramp
+with open(os.path.join(HERE, "golden", "oracle_configs.json")) as f:
+    CONFIGS_STORED = json.load(f)["cases"]
+
+
+@pytest.mark.parametrize("name,band", [("config1_sphere32_s20", 1e-3),
+                                       ("config3_plate64_s16", 1e-2)])
+def test_stored_config_adjoint_matches_its_central_differences(name, band):
+    ref = CONFIGS_STORED[name]
+    assert _rel(ref["dJ_dtheta"], ref["dJ_dtheta_fd"]) <= band
+    assert ref["fd_h"] == 1e-4

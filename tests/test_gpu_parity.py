@@ -94,6 +94,17 @@ def _corner(cfg):
     return cfg
 
 
+def _inlet(n=16, steps=3, V=0.3):
+    # an inflow patch on the low-x wall and an outlet on the high-x wall,
+    # a moving sphere between them; kinetic-energy loss (with a prescribed
+    # inflow the outflow is fixed by the geometry)
+    cfg = I.config_sphere(n, steps=steps)
+    cfg["grid"] = I.make_grid(n, 0.01, inlet=I.centred_inlet(n, 4, V),
+                              outlet=I.centred_outlet(n, 4))
+    cfg["u0"] = I.gaussian_faces(cfg["grid"], 0.1, 4)
+    return cfg
+
+
 CONFIGS = {
     "sphere": lambda: I.config_sphere(16, steps=3),
     "plate": lambda: I.config_plate(16, steps=3),
@@ -115,6 +126,8 @@ CONFIGS = {
     # radius 3.074 dx: no grid node on the sphere at any step time (r = 3 dx
     # about a node centre puts nodes on it at t = 0)
     "ragged_corner": lambda: _corner(_ragged(radius=0.1537)),
+    "sphere_inlet": _inlet,
+    "sphere_inlet_corner": lambda: _corner(_inlet()),
 }
 
 
@@ -174,7 +187,8 @@ def test_initial_projection_matches_oracle(nf, prec, solver, name):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("name", ["sphere", "plate", "chamber", "ragged_sphere"])
+@pytest.mark.parametrize("name", ["sphere", "plate", "chamber", "ragged_sphere",
+                                  "sphere_inlet"])
 def test_one_step_stages_match_oracle(nf, prec, name):
     cfg = CONFIGS[name]()
     g = Grid(cfg["grid"])
@@ -224,6 +238,26 @@ def test_viscous_step_matches_oracle_face_by_face(nf, prec, nu):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_inflow_patch_outflow_equals_inflow(nf, prec="mixed"):
+    # incompressibility with one inflow and one outflow patch: the net flux
+    # out equals the prescribed inflow (a rigid sphere adds none), on the
+    # GPU as in the oracle's pin
+    cfg = _inlet(16, steps=2, V=0.3)
+    g = Grid(cfg["grid"])
+    ctx = make_ctx(nf, prec, tol=1e-10)
+    ep = ctx.episode(cfg["grid"], cfg["scene"])
+    ep.set_velocity(device_u(cfg), project=True)
+    ep.step(2)
+    J = ep.loss("outflow")
+    assert abs(J - 0.3 * 16 * g.dx ** 2) <= 1e-6 * J
+    # the inlet faces hold the inflow speed exactly
+    U = host(ep.velocity())
+    i0 = cfg["grid"]["inlet"]
+    patch = U[0][i0["k0"]:i0["k0"] + 4, i0["j0"]:i0["j0"] + 4, 0]
+    np.testing.assert_allclose(patch, 0.3, rtol=0, atol=1e-7)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_divergence_free_after_step(nf, prec):
     cfg = CONFIGS["plate"]()
     g = Grid(cfg["grid"])
@@ -244,7 +278,8 @@ def test_divergence_free_after_step(nf, prec):
 @pytest.mark.parametrize("name", ["sphere", "plate", "chamber", "chamber_sub", "ragged_sphere",
                                   "sphere32", "sphere_viscous", "plate_viscous",
                                   "chamber_sub_viscous", "sphere_corner", "plate_corner",
-                                  "chamber_sub_corner", "ragged_corner"])
+                                  "chamber_sub_corner", "ragged_corner", "sphere_inlet",
+                                  "sphere_inlet_corner"])
 def test_rollout_loss_and_gradient_match_oracle(nf, prec, name):
     cfg, Jo, gtho, info = oracle_rollout(name)
     ctx = make_ctx(nf, prec, cfg=cfg, checkpoint_every=2)
@@ -387,6 +422,29 @@ def test_invalid_calls_raise(nf):
     assert e.value.status == 7
     with pytest.raises(nf.NFError):
         ep.loss("outflow")                                           # no outlet
+
+
+def test_non_finite_velocity_reports_diverged_and_the_context_recovers(nf):
+    # a poisoned input (NaN in one fluid face) made on the host: the
+    # projection's residual turns non-finite and the call returns
+    # NF_E_DIVERGED instead of iterating; a step from it does the same
+    cfg = CONFIGS["sphere"]()
+    ctx = make_ctx(nf, "mixed")
+    u = device_u(cfg)
+    u[0][3, 4, 5] = float("nan")                 # fluid: far from the sphere
+    ep = ctx.episode(cfg["grid"], cfg["scene"])
+    with pytest.raises(nf.NFError) as e:
+        ep.set_velocity(u, project=True)
+    assert e.value.status == 4
+    ep2 = ctx.episode(cfg["grid"], cfg["scene"])
+    ep2.set_velocity(u, project=False)
+    with pytest.raises(nf.NFError) as e:
+        ep2.step(1)
+    assert e.value.status == 4
+    ep3 = ctx.episode(cfg["grid"], cfg["scene"])
+    ep3.set_velocity(device_u(cfg), project=True)
+    ep3.step(1)
+    assert all(np.isfinite(x).all() for x in host(ep3.velocity()))
 
 
 def test_hbm_budget_refuses_admission(nf):
@@ -556,3 +614,40 @@ def test_solver_dot_error_at_256_cubed(nf, dtype):
     exact = math.fsum((ad * bd).tolist())         # products of floats are exact in FP64
     scale = float(np.abs(ad * bd).sum())
     assert abs(got - exact) <= 1e-12 * scale, (got, exact, scale)
+
+
+# ------------------------------------------------- fused sweep pairs ----
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
+@pytest.mark.parametrize("name", ["chamber_sub", "ragged_sphere", "sphere32", "plate64"])
+def test_fused_sweep_pairs_give_the_per_launch_bits(nf, prec, name):
+    # the red-black pairs as one shared-memory launch each (finest level;
+    # every grid level) against one launch per half sweep: the same arithmetic in the same
+    # order, so the rollout, its adjoint and the iteration counts agree
+    # exactly (ragged sizes, several tiles and z chunks, block edges)
+    cfg = I.config_plate(64, steps=2) if name == "plate64" else CONFIGS[name]()
+    out = []
+    for fused in (0, 1, 2):
+        ctx = make_ctx(nf, prec, cfg=cfg, checkpoint_every=2, mg_fused=fused)
+        ep = ctx.episode(cfg["grid"], cfg["scene"])
+        recording, _ = solver_warnings(prec)
+        with recording():
+            ep.set_velocity(device_u(cfg), project=cfg["project_initial"])
+            fs = ep.step(cfg["steps"])
+            J, gU = ep.loss(cfg["loss"], want_grad=True)
+            gth, _, bs = ep.backward(gU, want_gU0=False)
+        out.append((host(ep.velocity()), J, gth, fs["iters"], bs["iters"]))
+        ep.close()
+        ctx.close()
+    u0, J0, g0, i0, b0 = out[0]
+    for u1, J1, g1, i1, b1 in out[1:]:
+        assert i0 == i1
+        assert J0 == J1
+        for a, b in zip(u0, u1):
+            assert np.array_equal(a, b)
+        # the adjoint's advection scatter uses float atomics, so its
+        # right-hand sides (and then an adjoint solve's iteration count, by
+        # one) vary from run to run at rounding level, fused or not
+        assert abs(b1 - b0) <= 2
+        tol = 1e-10 if prec == "fp64" else 1e-5
+        assert np.linalg.norm(g1 - g0) <= tol * np.linalg.norm(g0)
