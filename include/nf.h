@@ -69,6 +69,9 @@ extern "C" {
                               Fourier coefficients theta, union a duct    */
 #define NF_SCENE_PLATE 3   /* plate rotating about z, 4 angle knots theta   */
 #define NF_SCENE_SPHERES 4 /* static spheres, no parameters                */
+#define NF_SCENE_EXTRUDED 5 /* polar-Bezier shapes extruded along z, CSG
+                               union (App. A, Sec. 2.2; the heart of Sec. 3
+                               as a union of four): table in nf_scene      */
 
 #define NF_LOSS_KINETIC 0 /* J = 1/2 sum_faces u^2 dx^3                     */
 #define NF_LOSS_OUTFLOW 1 /* J = sum over outlet faces of u_x dx^2         */
@@ -151,7 +154,11 @@ typedef struct nf_config {
 } nf_config;
 
 typedef struct nf_grid {
-  int nx, ny, nz;         /* cells per axis (each >= 4)                       */
+  int nx, ny, nz;         /* cells per axis: nx, ny >= 4; nz >= 4, or nz = 1
+                             for the 2D variant of App. D as a one-cell slab
+                             between closed z walls (its multigrid has one
+                             level: the preconditioner is symmetric
+                             Gauss-Seidel)                                  */
   double dx;              /* cell edge                                        */
   double dt;              /* time step                                        */
   double rho;             /* density (1 in every shipped scene)               */
@@ -199,6 +206,21 @@ typedef struct nf_scene {
   double consts[16];
   const double *spheres;  /* SPHERES: nspheres x (cx, cy, cz, r), host memory */
   int nspheres;
+  /* EXTRUDED: consts[0] shapes (1..4), consts[1] fluid inside the union (1)
+     or outside it (0), consts[2] theta mode: 0 = every radius of the table
+     in table order (K = their count <= NF_MAX_PARAMS; the table's own radii
+     are ignored), 1 = the 4 knots (at t = 0, T/3, 2T/3, T) of a piecewise-
+     linear contraction k(t) scaling the radii of shape consts[3], period
+     T = consts[4] (its wall moves with the contraction's velocity about the
+     cross-section centre), 2 = no parameters. `shapes` is a host table of
+     `nshape_values` doubles, copied at creation: per shape
+       n keys (1..4), N segments (1..8), z0 < z1, has frame (0/1),
+       frame origin (3), frame axes (9, row r = the shape's local axis r in
+       world coordinates, orthonormal),
+     then per key: centre (x, y) in the local frame, radii rho1_0, rho2_0,
+     rho1_1, ... (2N). Key sections are evenly spaced in z0..z1.          */
+  const double *shapes;
+  int nshape_values;
 } nf_scene;
 
 typedef struct nf_step_stats {
@@ -236,8 +258,8 @@ int nf_synchronize(nf_ctx *ctx);
 /* ---------------------------------------------------------------- episode */
 
 /* Create an episode: a grid, a scene with parameters theta, zero velocity,
-   step counter 0. NF_E_INVALID for a grid with fewer than 4 cells on an
-   axis, dx, dt <= 0, nu < 0 or not finite, an unknown fraction rule, or an
+   step counter 0. NF_E_INVALID for a grid with fewer than 4 cells in x or y,
+   nz not 1 or >= 4, dx, dt <= 0, nu < 0 or not finite, an unknown fraction rule, or an
    outlet patch off the high-x wall. Admission: NF_E_OOM when its device state would exceed the
    context's HBM budget. Geometry is evaluated analytically at
    t_{n+1} = (n + 1) dt in every step (Sec. 2.3.1, Projection). */
@@ -307,6 +329,19 @@ int nf_get_fractions(nf_ctx *ctx, int64_t id, void *const a[3], int dtype,
    when nu > 0 (3 face arrays). */
 int nf_get_advected(nf_ctx *ctx, int64_t id, void *const u[3], int dtype,
                     int mem);
+/* Resume: the episode's state (velocity, frame clock, theta) as host bytes.
+   nf_episode_export with buf = NULL sets *bytes to the size needed; with a
+   host buffer of *bytes >= that size it writes the state and sets *bytes.
+   nf_episode_import loads such bytes into an episode of the same grid,
+   scene kind and precision (NF_E_INVALID otherwise, or for a buffer that is
+   not an exported state): velocity, theta and the frame clock are restored,
+   so the next nf_step continues the rollout at the saved time; the tape
+   starts anew (nf_backward reaches back to the import, as after
+   nf_set_velocity). Both synchronise the context's stream. Not a step of
+   the method: a service for checkpointing and resuming served episodes. */
+int nf_episode_export(nf_ctx *ctx, int64_t id, void *buf, size_t *bytes);
+int nf_episode_import(nf_ctx *ctx, int64_t id, const void *buf, size_t bytes);
+
 /* Step counter n (the velocity is U^n). */
 int nf_get_step(nf_ctx *ctx, int64_t id, int *n);
 

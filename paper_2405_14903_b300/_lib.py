@@ -19,7 +19,7 @@ PREC = {"fp64": 0, "fp32": 1, "mixed": 2}
 SOLVER = {"cg": 0, "mgpcg": 1}
 NF_F32, NF_F64 = 0, 1
 NF_MEM_DEVICE, NF_MEM_HOST = 0, 1
-SCENE = {"none": 0, "sphere": 1, "chamber": 2, "plate": 3, "spheres": 4}
+SCENE = {"none": 0, "sphere": 1, "chamber": 2, "plate": 3, "spheres": 4, "extruded": 5}
 LOSS = {"kinetic_energy": 0, "outflow": 1}
 FRACTIONS = {"supersample": 0, "corner": 1}
 MAX_PARAMS = 8
@@ -61,7 +61,8 @@ class Scene(C.Structure):
     _fields_ = [("kind", C.c_int), ("K", C.c_int),
                 ("theta", C.c_double * MAX_PARAMS),
                 ("consts", C.c_double * 16),
-                ("spheres", C.POINTER(C.c_double)), ("nspheres", C.c_int)]
+                ("spheres", C.POINTER(C.c_double)), ("nspheres", C.c_int),
+                ("shapes", C.POINTER(C.c_double)), ("nshape_values", C.c_int)]
 
 
 class StepStats(C.Structure):
@@ -125,6 +126,8 @@ SIGNATURES = [
     ("nf_get_fractions", C.c_int, [_vp, _i64, PP, C.c_int, C.c_int]),
     ("nf_get_advected", C.c_int, [_vp, _i64, PP, C.c_int, C.c_int]),
     ("nf_get_step", C.c_int, [_vp, _i64, _ip]),
+    ("nf_episode_export", C.c_int, [_vp, _i64, _vp, C.POINTER(C.c_size_t)]),
+    ("nf_episode_import", C.c_int, [_vp, _i64, _vp, C.c_size_t]),
     ("nf_dot", C.c_int, [_vp, _vp, _vp, _i64, C.c_int, C.POINTER(C.c_double)]),
     ("nf_launch_count", C.c_int, [_vp, C.POINTER(_i64)]),
     ("nf_profile", C.c_int, [_vp, C.c_int]),

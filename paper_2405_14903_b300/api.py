@@ -94,9 +94,44 @@ def scene_struct(sc):
         keep = np.ascontiguousarray(np.asarray(sc["spheres"], dtype=np.float64).reshape(-1, 4))
         s.spheres = keep.ctypes.data_as(C.POINTER(C.c_double))
         s.nspheres = keep.shape[0]
+    elif kind == "extruded":
+        keep = extruded_table(sc)
+        s.shapes = keep.ctypes.data_as(C.POINTER(C.c_double))
+        s.nshape_values = keep.size
+        mode = {"radii": 0, "pulse": 1}.get(sc.get("params", "radii"), 2)
+        pulse = sc.get("pulse") or {}
+        consts = [len(sc["shapes"]), 1.0 if sc["fluid"] == "inside" else 0.0, mode,
+                  pulse.get("shape", 0), pulse.get("period", 0.0)]
     for k, v in enumerate(consts):
         s.consts[k] = v
     return s, keep
+
+
+def extruded_table(sc):
+    """The shape table of an ``extruded`` scene description (the layout of
+    nf_scene.shapes in nf.h): per shape n keys, N segments, z0, z1, the
+    frame (flag, origin, axes), then every key's centre and radii (theta's
+    in radii mode, else the key's own)."""
+    th = list(sc.get("theta", []))
+    radii_mode = sc.get("params", "radii") == "radii"
+    out, j = [], 0
+    for sh in sc["shapes"]:
+        keys = sh["keys"]
+        N = int(keys[0]["nseg"])
+        if any(int(k["nseg"]) != N for k in keys):
+            raise ValueError("every key of a shape has the same number of segments")
+        fr = sh.get("frame")
+        out += [len(keys), N, float(sh["z0"]), float(sh["z1"]), 1.0 if fr else 0.0]
+        out += list(fr["origin"]) if fr else [0.0, 0.0, 0.0]
+        out += [float(v) for row in fr["axes"] for v in row] if fr else [1.0, 0, 0, 0, 1.0, 0, 0, 0, 1.0]
+        for k in keys:
+            out += [float(k["c"][0]), float(k["c"][1])]
+            if radii_mode:
+                out += th[j:j + 2 * N]
+                j += 2 * N
+            else:
+                out += [float(v) for v in k["rho"]]
+    return np.ascontiguousarray(np.asarray(out, dtype=np.float64))
 
 
 def _ptrs(arrs):
@@ -379,6 +414,19 @@ class Episode:
             ptr, mem = out.data_ptr(), L.NF_MEM_DEVICE
         _check(lib.nf_get_pressure(self._c, self.id, ptr, code, mem), self._c)
         return out
+
+    def export_state(self):
+        """``nf_episode_export``: the resumable state as bytes."""
+        n = C.c_size_t()
+        _check(lib.nf_episode_export(self._c, self.id, None, C.byref(n)), self._c)
+        buf = C.create_string_buffer(n.value)
+        _check(lib.nf_episode_export(self._c, self.id, buf, C.byref(n)), self._c)
+        return buf.raw[:n.value]
+
+    def import_state(self, state):
+        """``nf_episode_import``: continue from bytes of :meth:`export_state`."""
+        data = bytes(state)
+        _check(lib.nf_episode_import(self._c, self.id, data, len(data)), self._c)
 
     def step_index(self):
         n = C.c_int()

@@ -325,10 +325,11 @@ int nf_episode_create(nf_ctx *ctx, const nf_grid *g, const nf_scene *s,
   const int64_t max_faces = std::max({(int64_t)(g->nx + 1) * g->ny * g->nz,
                                       (int64_t)g->nx * (g->ny + 1) * g->nz,
                                       (int64_t)g->nx * g->ny * (g->nz + 1)});
-  if (g->nx < 4 || g->ny < 4 || g->nz < 4 || !(g->dx > 0) || !(g->dt > 0) ||
+  // nz = 1: the 2D variant as a one-cell slab between closed z walls
+  if (g->nx < 4 || g->ny < 4 || (g->nz < 4 && g->nz != 1) || !(g->dx > 0) || !(g->dt > 0) ||
       max_faces > (int64_t)INT32_MAX) {
-    set_error("nf_episode_create: grid must have >= 4 cells per axis, dx > 0, dt > 0 "
-              "and fewer than 2^31 faces per component");
+    set_error("nf_episode_create: grid must have >= 4 cells in x and y, nz >= 4 or nz = 1 "
+              "(a 2D slab), dx > 0, dt > 0 and fewer than 2^31 faces per component");
     return NF_E_INVALID;
   }
   if (g->fractions != NF_FRACTIONS_SUPERSAMPLE && g->fractions != NF_FRACTIONS_CORNER) {
@@ -360,12 +361,19 @@ int nf_episode_create(nf_ctx *ctx, const nf_grid *g, const nf_scene *s,
       return NF_E_INVALID;
     }
   }
-  if (s->kind < NF_SCENE_NONE || s->kind > NF_SCENE_SPHERES) {
+  if (s->kind < NF_SCENE_NONE || s->kind > NF_SCENE_EXTRUDED) {
     set_error("nf_episode_create: unknown scene kind");
     return NF_E_INVALID;
   }
+  if (s->kind == NF_SCENE_EXTRUDED) {
+    const std::string why = nf::bz_check(*s);
+    if (!why.empty()) {
+      set_error("nf_episode_create: extruded scene: " + why);
+      return NF_E_INVALID;
+    }
+  }
   const int want = s->kind == NF_SCENE_SPHERE ? 3 : s->kind == NF_SCENE_CHAMBER ? 8
-                   : s->kind == NF_SCENE_PLATE ? 4 : 0;
+                   : s->kind == NF_SCENE_PLATE ? 4 : s->kind == NF_SCENE_EXTRUDED ? s->K : 0;
   if (s->K != want) {
     set_error("nf_episode_create: scene expects " + std::to_string(want) + " parameters");
     return NF_E_INVALID;
@@ -471,6 +479,17 @@ int nf_get_pressure(nf_ctx *ctx, int64_t id, void *p, int dtype, int mem) {
   EPISODE(ctx, id, e);
   if (!p || !valid_dtype(dtype) || !valid_mem(mem)) return NF_E_INVALID;
   return e->get_pressure(p, dtype, mem);
+}
+
+int nf_episode_export(nf_ctx *ctx, int64_t id, void *buf, size_t *bytes) {
+  EPISODE(ctx, id, e);
+  if (!bytes) return NF_E_INVALID;
+  return e->export_state(buf, bytes);
+}
+
+int nf_episode_import(nf_ctx *ctx, int64_t id, const void *buf, size_t bytes) {
+  EPISODE(ctx, id, e);
+  return e->import_state(buf, bytes);
 }
 
 int nf_get_step(nf_ctx *ctx, int64_t id, int *n) {

@@ -36,25 +36,129 @@ namespace nf {
 
 // ------------------------------------------------------------- scenes -----
 
-static int scene_K(int kind) {
-  switch (kind) {
+static int scene_K(const nf_scene &sc) {
+  switch (sc.kind) {
     case NF_SCENE_SPHERE:
       return 3;
     case NF_SCENE_CHAMBER:
       return 8;
     case NF_SCENE_PLATE:
       return 4;
+    case NF_SCENE_EXTRUDED:
+      return sc.K;
     default:
       return 0;
   }
 }
 
+// ------------------------------------------------ extruded shapes (host) ---
+// Caller's table (nf.h): per shape 17 header values, then n keys of 2 + 2N.
+std::string bz_check(const nf_scene &s) {
+  const int ns = (int)s.consts[0], mode = (int)s.consts[2];
+  if (ns < 1 || ns > kBzMaxShapes) return "1 to 4 shapes";
+  if (!s.shapes || s.nshape_values <= 0) return "shape table missing";
+  if (mode < kBzRadii || mode > kBzFixed) return "unknown theta mode";
+  int o = 0, radii = 0;
+  for (int sh = 0; sh < ns; ++sh) {
+    if (o + 17 > s.nshape_values) return "shape table too short";
+    const double *h = s.shapes + o;
+    const int n = (int)h[0], N = (int)h[1];
+    if (n < 1 || n > kBzMaxKeys || N < 1 || N > kBzMaxSeg || h[0] != n || h[1] != N)
+      return "1 to 4 keys and 1 to 8 segments per shape";
+    if (!(h[3] > h[2])) return "z1 must exceed z0";
+    for (int v = 2; v < 17; ++v)
+      if (!std::isfinite(h[v])) return "non-finite shape header";
+    o += 17 + n * (2 + 2 * N);
+    radii += n * 2 * N;
+    if (o > s.nshape_values) return "shape table too short";
+  }
+  if (o != s.nshape_values) return "shape table size does not match its shapes";
+  for (int v = 0; v < o; ++v)
+    if (!std::isfinite(s.shapes[v])) return "non-finite shape table entry";
+  const int want = mode == kBzRadii ? radii : (mode == kBzPulse ? 4 : 0);
+  if (mode == kBzRadii && radii > NF_MAX_PARAMS) return "more radii than NF_MAX_PARAMS";
+  if (s.K != want) return "K does not match the theta mode";
+  if (mode == kBzPulse &&
+      ((int)s.consts[3] < 0 || (int)s.consts[3] >= ns || !(s.consts[4] > 0.0)))
+    return "pulse shape index or period invalid";
+  return std::string();
+}
+
+// Device table of scene.cuh: header with the inverse Vandermonde
+// coefficients of the key interpolation and the segments' unit vectors,
+// keys with the radii (theta's in radii mode).
+void bz_build(const nf_scene &s, const std::vector<double> &src, BzInfo &out) {
+  out.n = (int)s.consts[0];
+  out.inside = s.consts[1] != 0.0 ? 1 : 0;
+  out.mode = (int)s.consts[2];
+  out.pulse = (int)s.consts[3];
+  out.period = s.consts[4];
+  out.table.clear();
+  int o = 0, th = 0;
+  out.radii = 0;
+  for (int sh = 0; sh < out.n; ++sh) {
+    const double *h = src.data() + o;
+    const int n = (int)h[0], N = (int)h[1];
+    out.off[sh] = (int)out.table.size();
+    out.theta0[sh] = th;
+    for (int v = 0; v < 17; ++v) out.table.push_back(h[v]);
+    // coeff = V^-1, V[k][m] = u_k^m, u_k = k / (n - 1): W = powers(u) coeff
+    double V[kBzMaxKeys][2 * kBzMaxKeys] = {};
+    for (int k = 0; k < n; ++k) {
+      const double uk = n > 1 ? (double)k / (double)(n - 1) : 0.0;
+      double p = 1.0;
+      for (int m = 0; m < n; ++m) {
+        V[k][m] = p;
+        p *= uk;
+      }
+      V[k][n + k] = 1.0;
+    }
+    for (int c = 0; c < n; ++c) {  // Gauss-Jordan with partial pivoting
+      int piv = c;
+      for (int r = c + 1; r < n; ++r)
+        if (std::fabs(V[r][c]) > std::fabs(V[piv][c])) piv = r;
+      for (int m = 0; m < 2 * n; ++m) std::swap(V[c][m], V[piv][m]);
+      const double inv = 1.0 / V[c][c];
+      for (int m = 0; m < 2 * n; ++m) V[c][m] *= inv;
+      for (int r = 0; r < n; ++r) {
+        if (r == c) continue;
+        const double f = V[r][c];
+        for (int m = 0; m < 2 * n; ++m) V[r][m] -= f * V[c][m];
+      }
+    }
+    // the inverse: coeff[m][k] = (V^-1)[m][k], rows m of the right half
+    for (int m = 0; m < kBzMaxKeys; ++m)
+      for (int k = 0; k < kBzMaxKeys; ++k)
+        out.table.push_back(m < n && k < n ? V[m][n + k] : 0.0);
+    for (int i = 0; i < N; ++i) {
+      const double base = 2.0 * M_PI * i / N;
+      const double a0 = base + 2.0 * M_PI / (3.0 * N), a1 = base + 4.0 * M_PI / (3.0 * N);
+      out.table.push_back(std::cos(a0));
+      out.table.push_back(std::sin(a0));
+      out.table.push_back(std::cos(a1));
+      out.table.push_back(std::sin(a1));
+    }
+    const double *kb = h + 17;
+    for (int k = 0; k < n; ++k) {
+      out.table.push_back(kb[k * (2 + 2 * N)]);
+      out.table.push_back(kb[k * (2 + 2 * N) + 1]);
+      for (int j = 0; j < 2 * N; ++j)
+        out.table.push_back(out.mode == kBzRadii ? s.theta[th + j]
+                                                 : kb[k * (2 + 2 * N) + 2 + j]);
+      th += 2 * N;
+    }
+    out.radii += n * 2 * N;
+    o += 17 + n * (2 + 2 * N);
+  }
+}
+
 // Scene state at time t (host, double precision).
-static SceneDev scene_at(const nf_scene &sc, double t, const double *d_spheres) {
+static SceneDev scene_at(const nf_scene &sc, double t, const double *d_spheres,
+                         const BzInfo *bz = nullptr) {
   SceneDev s;
   std::memset(&s, 0, sizeof(s));
   s.kind = sc.kind;
-  s.K = scene_K(sc.kind);
+  s.K = scene_K(sc);
   s.t = t;
   const double *c = sc.consts;
   const double *th = sc.theta;
@@ -127,6 +231,33 @@ static SceneDev scene_at(const nf_scene &sc, double t, const double *d_spheres) 
       s.spheres = d_spheres;
       s.nspheres = sc.nspheres;
       break;
+    case NF_SCENE_EXTRUDED: {
+      s.bz = bz->dev;
+      s.bz_n = bz->n;
+      s.bz_inside = bz->inside;
+      s.bz_mode = bz->mode;
+      s.bz_pulse = bz->pulse;
+      for (int a = 0; a < kBzMaxShapes; ++a) {
+        s.bz_off[a] = bz->off[a];
+        s.bz_theta0[a] = bz->theta0[a];
+      }
+      s.bz_k = 1.0;
+      if (bz->mode == kBzPulse) {
+        // k(t) piecewise linear through the 4 knots at 0, T/3, 2T/3, T
+        const double L = bz->period / 3.0;
+        int seg = (int)std::floor(t / L);
+        seg = std::max(0, std::min(2, seg));
+        const double tau = (t - seg * L) / L;
+        s.bz_k = th[seg] * (1.0 - tau) + th[seg + 1] * tau;
+        s.bz_kdot = (th[seg + 1] - th[seg]) / L;
+        for (int k = 0; k < 4; ++k) s.bz_dk[k] = s.bz_dkdot[k] = 0.0;
+        s.bz_dk[seg] = 1.0 - tau;
+        s.bz_dk[seg + 1] = tau;
+        s.bz_dkdot[seg] = -1.0 / L;
+        s.bz_dkdot[seg + 1] = 1.0 / L;
+      }
+      break;
+    }
     default:
       break;
   }
@@ -178,8 +309,9 @@ class EpisodeImpl : public EpisodeBase {
   EpisodeImpl(Ctx *ctx, const nf_grid &gr, const nf_scene &sc)
       : ctx_(ctx), g_(make_grid(gr)), sc_(sc), solver_(ctx, make_grid(gr), ctx->cfg) {
     A_.stream = ctx->stream;
-    sc_.K = scene_K(sc.kind);
+    sc_.K = scene_K(sc);
     sc_.spheres = nullptr;
+    sc_.shapes = nullptr;  // kept in bz_src_ by init
   }
 
   static GridDev make_grid(const nf_grid &gr) {
@@ -231,6 +363,10 @@ class EpisodeImpl : public EpisodeBase {
                           cudaMemcpyHostToDevice, ctx_->stream));
       CKC(cudaStreamSynchronize(ctx_->stream));  // the host list is the caller's
     }
+    if (sc.kind == NF_SCENE_EXTRUDED) {
+      bz_src_.assign(sc.shapes, sc.shapes + sc.nshape_values);
+      CKS(upload_bz());
+    }
     CKS(solver_.init(A_));
     CKS(cc_.init(A_, ncell_));
     solver_.set_projector(&cc_);
@@ -239,7 +375,7 @@ class EpisodeImpl : public EpisodeBase {
     CKC(cudaMemsetAsync(P_, 0, ncell_ * sizeof(S), L.s));
     CKC(cudaMemsetAsync(Uh_, 0, nfaces_ * sizeof(T), L.s));
     // fractions of the initial geometry (t = 0) so queries are meaningful
-    launch_rasterize<T>(L, g_, scene_at(sc_, 0.0, dsph_), mut(alpha_));
+    launch_rasterize<T>(L, g_, scene_at(sc_, 0.0, dsph_, &bz_), mut(alpha_));
     return check_launch();
   }
 
@@ -250,6 +386,18 @@ class EpisodeImpl : public EpisodeBase {
     if (K != sc_.K) return invalid("set_params: expected %d parameters", sc_.K);
     for (int k = 0; k < K; ++k) sc_.theta[k] = theta[k];
     clear_tape();
+    if (sc_.kind == NF_SCENE_EXTRUDED) CKS(upload_bz());  // radii mode: new radii
+    return NF_OK;
+  }
+
+  // The extruded scene's device table from the kept caller table and theta.
+  int upload_bz() {
+    bz_build(sc_, bz_src_, bz_);
+    const size_t bytes = bz_.table.size() * sizeof(double);
+    if (!bz_dev_) CKS(A_.get(&bz_dev_, bytes));
+    CKC(cudaMemcpyAsync(bz_dev_, bz_.table.data(), bytes, cudaMemcpyHostToDevice, ctx_->stream));
+    CKC(cudaStreamSynchronize(ctx_->stream));  // bz_.table is rebuilt by the next call
+    bz_.dev = bz_dev_;
     return NF_OK;
   }
 
@@ -267,7 +415,7 @@ class EpisodeImpl : public EpisodeBase {
       }
       Launch L = ctx_->launch();
       CKC(cudaMemcpyAsync(Uinit_, U_, nfaces_ * sizeof(T), cudaMemcpyDeviceToDevice, L.s));
-      const SceneDev sd = scene_at(sc_, 0.0, dsph_);
+      const SceneDev sd = scene_at(sc_, 0.0, dsph_, &bz_);
       launch_rasterize<T>(L, g_, sd, mut(alpha_));
       SolveStats ss;
       CKS(project_faces(g_, sd, Uinit_, Pinit_, U_, &ss));
@@ -423,6 +571,65 @@ class EpisodeImpl : public EpisodeBase {
 
   int get_pressure(void *dst, int dtype, int mem) override {
     return copy_out_t<S>(dst, P_, ncell_, dtype, mem);
+  }
+
+  // Resume format: a header (magic, version, field size, grid, frame
+  // clock, theta) and the face velocity in the episode's field type.
+  struct StateHeader {
+    char magic[8];
+    int32_t version, field_bytes, nx, ny, nz, K, kind, pad;
+    int64_t frames;
+    double dx, dt, theta[NF_MAX_PARAMS];
+  };
+  static constexpr char kMagic[8] = {'N', 'F', 'E', 'P', 'I', 'S', 'O', '1'};
+
+  int export_state(void *buf, size_t *bytes) override {
+    const size_t need = sizeof(StateHeader) + nfaces_ * sizeof(T);
+    if (!buf) {
+      *bytes = need;
+      return NF_OK;
+    }
+    if (*bytes < need) return invalid("episode_export: buffer of %zu bytes is too small", *bytes);
+    StateHeader h{};
+    std::memcpy(h.magic, kMagic, 8);
+    h.version = 1;
+    h.field_bytes = (int32_t)sizeof(T);
+    h.nx = g_.nx;
+    h.ny = g_.ny;
+    h.nz = g_.nz;
+    h.K = sc_.K;
+    h.kind = sc_.kind;
+    h.frames = frames_;
+    h.dx = g_.dx;
+    h.dt = g_.dt;
+    for (int k = 0; k < NF_MAX_PARAMS; ++k) h.theta[k] = sc_.theta[k];
+    std::memcpy(buf, &h, sizeof(h));
+    CKC(cudaMemcpyAsync((char *)buf + sizeof(h), U_, nfaces_ * sizeof(T), cudaMemcpyDeviceToHost,
+                        ctx_->stream));
+    CKC(cudaStreamSynchronize(ctx_->stream));
+    *bytes = need;
+    return NF_OK;
+  }
+
+  int import_state(const void *buf, size_t bytes) override {
+    StateHeader h{};
+    if (!buf || bytes < sizeof(h)) return invalid("episode_import: buffer too short%s", "");
+    std::memcpy(&h, buf, sizeof(h));
+    if (std::memcmp(h.magic, kMagic, 8) != 0 || h.version != 1)
+      return invalid("episode_import: not an exported episode state%s", "");
+    if (h.field_bytes != (int32_t)sizeof(T) || h.nx != g_.nx || h.ny != g_.ny || h.nz != g_.nz ||
+        h.K != sc_.K || h.kind != sc_.kind || h.dx != g_.dx || h.dt != g_.dt || h.frames < 0)
+      return invalid("episode_import: state of another grid, scene or precision%s", "");
+    if (bytes != sizeof(h) + nfaces_ * sizeof(T))
+      return invalid("episode_import: size does not match the grid%s", "");
+    CKC(cudaMemcpyAsync(U_, (const char *)buf + sizeof(h), nfaces_ * sizeof(T),
+                        cudaMemcpyHostToDevice, ctx_->stream));
+    CKC(cudaStreamSynchronize(ctx_->stream));  // the caller's buffer is borrowed
+    for (int k = 0; k < sc_.K; ++k) sc_.theta[k] = h.theta[k];
+    clear_tape();
+    if (sc_.kind == NF_SCENE_EXTRUDED) CKS(upload_bz());
+    frames_ = (int)h.frames;  // the clock resumes; the tape starts here
+    return NF_OK;
   }
 
  private:
@@ -586,7 +793,7 @@ class EpisodeImpl : public EpisodeBase {
     NvtxRange nv("nf.step");
     Launch L = ctx_->launch();
     const GridDev g = grid_h(hs_[m]);
-    const SceneDev sd = scene_at(sc_, ts_[m], dsph_);
+    const SceneDev sd = scene_at(sc_, ts_[m], dsph_, &bz_);
     if (m < (int)tapeA_.size() && tapeA_[m] && tapeA_ok_[m]) {
       // recomputed step: the fractions kept by the first pass (bit-identical
       // to rasterising them again)
@@ -693,7 +900,7 @@ class EpisodeImpl : public EpisodeBase {
     if (n_rev_ == 0) {
       if (!init_proj_ || init_reverted_)
         return state_err("backward_step: nothing left to revert");
-      const SceneDev sd = scene_at(sc_, 0.0, dsph_);
+      const SceneDev sd = scene_at(sc_, 0.0, dsph_, &bz_);
       launch_rasterize<T>(L, g_, sd, mut(alpha_));
       const int rc = adjoint_projection(g_, sd, Uinit_, Pinit_, gth, st);
       CKC(cudaMemcpyAsync(gU_, gUh_, nfaces_ * sizeof(T), cudaMemcpyDeviceToDevice, L.s));
@@ -706,7 +913,7 @@ class EpisodeImpl : public EpisodeBase {
     if (seg_start_ != s * C) CKS(recompute_segment(s, st));
     const int k = m - seg_start_;
     const GridDev g = grid_h(hs_[m]);
-    const SceneDev sd = scene_at(sc_, ts_[m], dsph_);
+    const SceneDev sd = scene_at(sc_, ts_[m], dsph_, &bz_);
     // the step's fractions, kept by the recompute (the solver's captured
     // graphs read alpha_, so they are copied back rather than pointed to)
     CKC(cudaMemcpyAsync(alpha_, segA_[k], nfaces_ * sizeof(T), cudaMemcpyDeviceToDevice, L.s));
@@ -743,6 +950,9 @@ class EpisodeImpl : public EpisodeBase {
   void *stage_ = nullptr;
   double *dscal_ = nullptr;  // [0] norms, [1] loss, [8..16) dJ/dtheta
   double *dsph_ = nullptr;
+  std::vector<double> bz_src_;  // the caller's shape table (extruded scenes)
+  BzInfo bz_;
+  double *bz_dev_ = nullptr;
   // tape
   int n_ = 0, n_rev_ = 0, frames_ = 0;
   std::vector<double> ts_, hs_;  // end time and length of every step

@@ -2,6 +2,9 @@
 // rollout tape. Precision-specific implementations live in episode.cu.
 #pragma once
 
+#include <string>
+#include <vector>
+
 #include "util.h"
 
 namespace nf {
@@ -30,7 +33,24 @@ class EpisodeBase {
   virtual int get_pressure(void *dst, int dtype, int mem) = 0;
   virtual int step_index() const = 0;
   virtual size_t bytes() const = 0;
+  // Resumable state (velocity, frame clock, theta) to / from host bytes.
+  virtual int export_state(void *buf, size_t *bytes) = 0;
+  virtual int import_state(const void *buf, size_t bytes) = 0;
 };
+
+// Extruded polar-Bezier scenes: the device table of scene.cuh built from
+// the caller's table (nf.h, NF_SCENE_EXTRUDED) and theta, and the per-shape
+// offsets. bz_check validates a scene (empty string when valid).
+struct BzInfo {
+  int n = 0, inside = 0, mode = 0, pulse = 0;
+  double period = 0.0;
+  int off[4] = {0, 0, 0, 0}, theta0[4] = {0, 0, 0, 0};
+  int radii = 0;                 // radii in the table (all shapes and keys)
+  const double *dev = nullptr;   // device copy of `table`
+  std::vector<double> table;
+};
+std::string bz_check(const nf_scene &s);
+void bz_build(const nf_scene &s, const std::vector<double> &src, BzInfo &out);
 
 // Creates an episode in the precision of ctx->cfg. Returns a status.
 int create_episode(Ctx *ctx, const nf_grid *g, const nf_scene *s,

@@ -54,6 +54,12 @@ __device__ __forceinline__ void face_pos(int d, int i, int j, int k, double &X,
 template <class R>
 __device__ __forceinline__ void axis_w(int base, R o, int n, int &i0, R &fr,
                                        R &slope) {
+  if (n == 1) {  // a one-point lattice (the 2D slab's z axis): constant
+    i0 = 0;
+    fr = R(0);
+    slope = R(0);
+    return;
+  }
   const R fl = floor(o);
   const int i = base + (int)fl;
   const R f = o - fl;
@@ -103,18 +109,20 @@ __device__ __forceinline__ R trilerp(const GridDev &g, const T *U, int e,
   axis_w<R>(bj, oy, ny, j0, fy, sy);
   axis_w<R>(bk, oz, nz, k0, fz, sz);
   const int64_t base = ((int64_t)k0 * ny + j0) * nx + i0;
-  const int64_t sy1 = nx, sz1 = (int64_t)nx * ny;
-  const R c000 = (R)U[base], c100 = (R)U[base + 1];
-  const R c010 = (R)U[base + sy1], c110 = (R)U[base + sy1 + 1];
-  const R c001 = (R)U[base + sz1], c101 = (R)U[base + sz1 + 1];
-  const R c011 = (R)U[base + sz1 + sy1], c111 = (R)U[base + sz1 + sy1 + 1];
+  // steps to the upper corner along each axis (0 on a one-point axis, whose
+  // upper corner has weight 0: its load stays in bounds)
+  const int64_t sx1 = nx > 1 ? 1 : 0, sy1 = ny > 1 ? nx : 0, sz1 = nz > 1 ? (int64_t)nx * ny : 0;
+  const R c000 = (R)U[base], c100 = (R)U[base + sx1];
+  const R c010 = (R)U[base + sy1], c110 = (R)U[base + sy1 + sx1];
+  const R c001 = (R)U[base + sz1], c101 = (R)U[base + sz1 + sx1];
+  const R c011 = (R)U[base + sz1 + sy1], c111 = (R)U[base + sz1 + sy1 + sx1];
   const R gx = R(1) - fx, gy = R(1) - fy, gz = R(1) - fz;
   const R v = gz * (gy * (gx * c000 + fx * c100) + fy * (gx * c010 + fx * c110)) +
               fz * (gy * (gx * c001 + fx * c101) + fy * (gx * c011 + fx * c111));
   if (kStencil) {
-    const int64_t id[8] = {base,           base + 1,       base + sy1,
-                           base + sy1 + 1, base + sz1,     base + sz1 + 1,
-                           base + sz1 + sy1, base + sz1 + sy1 + 1};
+    const int64_t id[8] = {base,             base + sx1,       base + sy1,
+                           base + sy1 + sx1, base + sz1,       base + sz1 + sx1,
+                           base + sz1 + sy1, base + sz1 + sy1 + sx1};
     const R wx[2] = {gx, fx}, wy[2] = {gy, fy}, wz[2] = {gz, fz};
     const R ddx[2] = {-sx, sx}, ddy[2] = {-sy, sy}, ddz[2] = {-sz, sz};
 #pragma unroll

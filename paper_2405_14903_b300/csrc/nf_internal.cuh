@@ -102,7 +102,18 @@ struct SceneDev {
   // static spheres (device array of nspheres x 4 doubles)
   const double *spheres;
   int nspheres;
+  // extruded polar-Bezier shapes (App. A): device table (layout in
+  // scene.cuh, bz_*), shape count, fluid inside (1) or outside (0) their
+  // union, theta mode (kBzRadii, kBzPulse, kBzFixed), the pulsing shape and
+  // its contraction k(t), rate and their theta derivatives
+  const double *bz;
+  int bz_n, bz_inside, bz_mode, bz_pulse;
+  int bz_off[4];       // table offset of each shape
+  int bz_theta0[4];    // first theta index of each shape's radii (kBzRadii)
+  double bz_k, bz_kdot, bz_dk[4], bz_dkdot[4];
 };
+constexpr int kBzRadii = 0, kBzPulse = 1, kBzFixed = 2;
+constexpr int kBzMaxShapes = 4, kBzMaxKeys = 4, kBzMaxSeg = 8;
 
 // ------------------------------------------------------------ launches ----
 struct Prof;  // CUDA-event timing of one kernel class (util.h)

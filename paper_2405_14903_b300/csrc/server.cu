@@ -30,6 +30,7 @@ struct Job {
   int64_t ticket = 0;
   nf_request req{};
   std::vector<double> spheres;  // owned copy of an OPEN's sphere list
+  std::vector<double> shapes;   // owned copy of an OPEN's shape table
   double submit_ms = 0.0;
 };
 
@@ -173,6 +174,7 @@ void nf_server::work(int s) {
     if (job.req.kind == NF_REQ_OPEN) {
       nf_scene sc = job.req.scene;
       sc.spheres = job.spheres.empty() ? nullptr : job.spheres.data();
+      sc.shapes = job.shapes.empty() ? nullptr : job.shapes.data();
       res.status = nf_episode_create(slot.ctx, &job.req.grid, &sc, &id);
       created = res.status == NF_OK;
     } else if (failed || !created) {
@@ -272,6 +274,15 @@ extern "C" int nf_server_submit(nf_server *srv, const nf_request *req, int64_t *
     job.spheres.assign(req->scene.spheres, req->scene.spheres + 4 * req->scene.nspheres);
   }
   job.req.scene.spheres = nullptr;
+  if (req->kind == NF_REQ_OPEN && req->scene.kind == NF_SCENE_EXTRUDED &&
+      req->scene.nshape_values > 0) {
+    if (!req->scene.shapes) {
+      nf::set_error("nf_server_submit: extruded scene without a shape table");
+      return NF_E_INVALID;
+    }
+    job.shapes.assign(req->scene.shapes, req->scene.shapes + req->scene.nshape_values);
+  }
+  job.req.scene.shapes = nullptr;
   std::lock_guard<std::mutex> lk(srv->mu);
   if (srv->stop) return NF_E_STATE;
   job.ticket = srv->next_ticket++;

@@ -105,6 +105,56 @@ def _inlet(n=16, steps=3, V=0.3):
     return cfg
 
 
+def _slab(n=24, steps=3, V=0.3):
+    # the 2D variant (App. D) as a one-cell slab between closed z walls:
+    # uniform inflow through the whole low-x wall, the high-x wall open, a
+    # moving disc (a sphere through the slab) in the channel
+    g = I.make_grid(n, 0.005, nz=1,
+                    inlet=dict(axis=0, side=-1, j0=0, k0=0, w=n, h=1, speed=V),
+                    outlet=dict(axis=0, side=1, j0=0, k0=0, w=n, h=1))
+    sc = I.sphere_scene(v=(0.1, 0.02, 0.0), centre=(0.35, 0.5, 0.5 * g["dx"]), radius=0.12)
+    u0 = [np.full(I.face_shape(g, 0), V), np.zeros(I.face_shape(g, 1)),
+          np.zeros(I.face_shape(g, 2))]
+    return dict(name="slab", grid=g, scene=sc, u0=u0, project_initial=True, steps=steps,
+                tol=1e-10, loss="kinetic_energy")
+
+
+def _extruded(n=12):
+    # an extruded polar-Bezier obstacle (App. A): one shape, one key section
+    # of four segments, theta = its 8 radii
+    g = I.make_grid(n, 0.01)
+    return dict(name="extruded", grid=g, scene=I.extruded_scene(4, shapes=1, segments=4, keys=1),
+                u0=I.gaussian_faces(g, 0.1, 21), project_initial=True, steps=2, tol=1e-12,
+                loss="kinetic_energy")
+
+
+def _extruded_fixed(n=12):
+    # two shapes with two key sections each, CSG union, radii fixed (K = 0),
+    # the paper's face-area fractions
+    g = I.make_grid(n, 0.01)
+    g["fractions"] = "corner"
+    sc = I.extruded_scene(5, shapes=2, segments=5, keys=2)
+    th, j = sc["theta"], 0
+    for shp in sc["shapes"]:
+        for k in shp["keys"]:
+            k["rho"] = th[j:j + 2 * k["nseg"]]
+            j += 2 * k["nseg"]
+    sc = dict(sc, theta=[], params="fixed")
+    return dict(name="extruded_fixed", grid=g, scene=sc, u0=I.gaussian_faces(g, 0.1, 22),
+                project_initial=True, steps=2, tol=1e-12, loss="kinetic_energy")
+
+
+def _heart(n=12, fractions="corner"):
+    # the heart of Sec. 3: a chamber and three tubes, each an extruded
+    # polar-Bezier part in its own frame, fluid inside their union; the
+    # chamber contracts by k(t) (theta = 4 knots); the outlet tube runs
+    # through the high-x patch
+    g = I.make_grid(n, 0.01, outlet=I.centred_outlet(n, 2))
+    g["fractions"] = fractions
+    return dict(name="heart", grid=g, scene=I.heart_scene(7, pulse_period=0.06, outlet=True),
+                u0=I.zero_faces(g), project_initial=False, steps=2, tol=1e-13, loss="outflow")
+
+
 CONFIGS = {
     "sphere": lambda: I.config_sphere(16, steps=3),
     "plate": lambda: I.config_plate(16, steps=3),
@@ -127,6 +177,13 @@ CONFIGS = {
     # about a node centre puts nodes on it at t = 0)
     "ragged_corner": lambda: _corner(_ragged(radius=0.1537)),
     "sphere_inlet": _inlet,
+    "slab": _slab,
+    "extruded": _extruded,
+    "extruded_corner": lambda: _corner(_extruded()),
+    "extruded_fixed": _extruded_fixed,
+    "heart": _heart,
+    "heart_super": lambda: _heart(fractions="supersample"),
+    "slab_corner": lambda: _corner(_slab()),
     "sphere_inlet_corner": lambda: _corner(_inlet()),
 }
 
@@ -155,7 +212,8 @@ def device_u(cfg, dtype=torch.float64):
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("name", ["sphere", "plate", "chamber", "spheres", "sphere_corner",
                                   "plate_corner", "chamber_corner", "spheres_corner",
-                                  "ragged_corner"])
+                                  "ragged_corner", "extruded", "extruded_corner",
+                                  "extruded_fixed", "heart", "heart_super"])
 def test_fractions_match_oracle(nf, prec, name):
     cfg = CONFIGS[name]()
     g = Grid(cfg["grid"])
@@ -188,7 +246,7 @@ def test_initial_projection_matches_oracle(nf, prec, solver, name):
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("name", ["sphere", "plate", "chamber", "ragged_sphere",
-                                  "sphere_inlet"])
+                                  "sphere_inlet", "slab"])
 def test_one_step_stages_match_oracle(nf, prec, name):
     cfg = CONFIGS[name]()
     g = Grid(cfg["grid"])
@@ -207,6 +265,8 @@ def test_one_step_stages_match_oracle(nf, prec, name):
     GPr = mac.grad(g, tape["P"])
     for d in range(3):
         m = tape["alpha"][d] > 0
+        if not m.any():
+            continue          # the slab's z faces are all walls
         scale = np.abs(GPr[d][m]).max()
         assert np.abs(GP[d][m] - GPr[d][m]).max() <= 1e3 * VEL_TOL[prec] * scale
 
@@ -238,13 +298,13 @@ def test_viscous_step_matches_oracle_face_by_face(nf, prec, nu):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_inflow_patch_outflow_equals_inflow(nf, prec="mixed"):
+def test_inflow_patch_outflow_equals_inflow(nf, prec):
     # incompressibility with one inflow and one outflow patch: the net flux
     # out equals the prescribed inflow (a rigid sphere adds none), on the
     # GPU as in the oracle's pin
     cfg = _inlet(16, steps=2, V=0.3)
     g = Grid(cfg["grid"])
-    ctx = make_ctx(nf, prec, tol=1e-10)
+    ctx = make_ctx(nf, prec)
     ep = ctx.episode(cfg["grid"], cfg["scene"])
     ep.set_velocity(device_u(cfg), project=True)
     ep.step(2)
@@ -255,6 +315,24 @@ def test_inflow_patch_outflow_equals_inflow(nf, prec="mixed"):
     i0 = cfg["grid"]["inlet"]
     patch = U[0][i0["k0"]:i0["k0"] + 4, i0["j0"]:i0["j0"] + 4, 0]
     np.testing.assert_allclose(patch, 0.3, rtol=0, atol=1e-7)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_slab_keeps_the_flow_planar_and_the_outflow_equal_to_the_inflow(nf, prec):
+    # one-cell slab: u_z stays exactly zero (its faces are the z walls), and
+    # with inflow over the whole low-x wall and the high-x wall open the net
+    # outflow equals the inflow
+    cfg = _slab(24, steps=4)
+    g = Grid(cfg["grid"])
+    ctx = make_ctx(nf, prec)
+    ep = ctx.episode(cfg["grid"], cfg["scene"])
+    ep.set_velocity(device_u(cfg), project=True)
+    ep.step(cfg["steps"])
+    U = host(ep.velocity())
+    assert not np.any(U[2])
+    assert np.abs(U[1]).max() > 1e-3               # the disc deflects the flow
+    J = ep.loss("outflow")
+    assert abs(J - 0.3 * 24 * g.dx ** 2) <= 1e-6 * J
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
@@ -279,7 +357,8 @@ def test_divergence_free_after_step(nf, prec):
                                   "sphere32", "sphere_viscous", "plate_viscous",
                                   "chamber_sub_viscous", "sphere_corner", "plate_corner",
                                   "chamber_sub_corner", "ragged_corner", "sphere_inlet",
-                                  "sphere_inlet_corner"])
+                                  "sphere_inlet_corner", "slab", "slab_corner", "extruded",
+                                  "extruded_corner", "extruded_fixed", "heart"])
 def test_rollout_loss_and_gradient_match_oracle(nf, prec, name):
     cfg, Jo, gtho, info = oracle_rollout(name)
     ctx = make_ctx(nf, prec, cfg=cfg, checkpoint_every=2)
@@ -295,7 +374,7 @@ def test_rollout_loss_and_gradient_match_oracle(nf, prec, name):
     assert np.linalg.norm(gth - gtho) <= GRAD_TOL[prec] * np.linalg.norm(gtho)
     assert st["steps"] == sum(1 for t in info["tapes"] if t["kind"] == "step")
     scale = max(np.abs(x).max() for x in host(gU))
-    if name.startswith("chamber"):
+    if name.startswith(("chamber", "heart")):
         # the outflow is a function of the geometry alone: dJ/dU^0 vanishes
         # up to solver tolerance (oracle and GPU both)
         assert max(np.abs(x).max() for x in host(gU0)) <= 1e-3 * scale
@@ -651,3 +730,36 @@ def test_fused_sweep_pairs_give_the_per_launch_bits(nf, prec, name):
         assert abs(b1 - b0) <= 2
         tol = 1e-10 if prec == "fp64" else 1e-5
         assert np.linalg.norm(g1 - g0) <= tol * np.linalg.norm(g0)
+
+
+# --------------------------------------------------------------- resume ----
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_exported_episode_resumes_bit_for_bit(nf, prec):
+    # an episode exported after 3 frames and imported into a fresh one
+    # continues exactly as the original: the forward step is deterministic
+    # and the frame clock (the geometry's time) is restored
+    cfg = I.config_chamber(16, steps=5, duct_half_cells=2, cfl_max=1.0)
+    ctx = make_ctx(nf, prec, cfg=cfg)
+    a = ctx.episode(cfg["grid"], cfg["scene"])
+    a.set_velocity(device_u(cfg), project=False)
+    a.step(3)
+    state = a.export_state()
+    a.step(2)
+    b = ctx.episode(cfg["grid"], cfg["scene"])
+    b.set_params(np.zeros(8))                          # overwritten by the import
+    b.import_state(state)
+    b.step(2)
+    for x, y in zip(host(a.velocity()), host(b.velocity())):
+        assert np.array_equal(x, y)
+    # the tape starts at the import: the adjoint reaches back two frames
+    J, gU = b.loss("outflow", want_grad=True)
+    _, _, st = b.backward(gU, want_gU0=False)
+    assert st["steps"] == b.step_index()
+    # refused: another grid, a truncated or foreign buffer
+    c = ctx.episode(I.make_grid(8, 0.005, outlet=I.centred_outlet(8, 2)),
+                    I.config_chamber(8, duct_half_cells=1)["scene"])
+    for bad in (state, state[:-8], b"x" * len(state)):
+        with pytest.raises(nf.NFError) as e:
+            (c if bad is state else b).import_state(bad)
+        assert e.value.status == 1
