@@ -141,15 +141,44 @@ __global__ void k_cc_compress(int64_t n, int *lab) {
   }
 }
 
-// ground[root] = 1 for components with an open (outlet) face; counts the
-// floating roots into *nfloat.
-__global__ void k_cc_ground(GridDev g, const int *lab, int *ground) {
-  if (!g.outlet) return;
-  const int64_t n = (int64_t)g.ow * g.oh;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+// ground[root] = 1 for components with an open box face: a face of the box
+// boundary with alpha > 0 (walls and inflow patches have alpha = 0, outlet
+// faces 1). For one episode this is the outlet patch; for episodes stacked
+// along z (a batched solve) it finds every member's own outlet.
+template <class T>
+__global__ void k_cc_ground_open(GridDev g, Fields<T> a, const int *lab, int *ground) {
+  const int64_t nxw = 2 * (int64_t)g.ny * g.nz, nyw = 2 * (int64_t)g.nx * g.nz,
+                nzw = 2 * (int64_t)g.nx * g.ny;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nxw + nyw + nzw;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const int j = g.oj0 + (int)(t % g.ow), k = g.ok0 + (int)(t / g.ow);
-    const int r = lab[g.cell(g.nx - 1, j, k)];
+    int i, j, k;
+    T af;
+    if (t < nxw) {
+      const int hi = (int)(t & 1);
+      const int64_t q = t >> 1;
+      j = (int)(q % g.ny);
+      k = (int)(q / g.ny);
+      af = a.x[g.face(0, hi ? g.nx : 0, j, k)];
+      i = hi ? g.nx - 1 : 0;
+    } else if (t < nxw + nyw) {
+      const int64_t u = t - nxw;
+      const int hi = (int)(u & 1);
+      const int64_t q = u >> 1;
+      i = (int)(q % g.nx);
+      k = (int)(q / g.nx);
+      af = a.y[g.face(1, i, hi ? g.ny : 0, k)];
+      j = hi ? g.ny - 1 : 0;
+    } else {
+      const int64_t u = t - nxw - nyw;
+      const int hi = (int)(u & 1);
+      const int64_t q = u >> 1;
+      i = (int)(q % g.nx);
+      j = (int)(q / g.nx);
+      af = a.z[g.face(2, i, j, hi ? g.nz : 0)];
+      k = hi ? g.nz - 1 : 0;
+    }
+    if (!(af > T(0))) continue;
+    const int r = lab[g.cell(i, j, k)];
     if (r >= 0) ground[r] = 1;
   }
 }
@@ -340,7 +369,8 @@ int Components::label(Ctx *ctx, const GridDev &g, Fields<T> alpha) {
   cudaMemsetAsync((int *)scal + 1, 0, sizeof(int), L.s);
   {
     ProfScope _ps(L, NF_K_GAUGE);
-    k_cc_ground<<<cc_blocks((int64_t)g.ow * g.oh + 1), kBlock, 0, L.s>>>(g, lab, ground);
+    const int64_t nw = 2 * ((int64_t)g.ny * g.nz + (int64_t)g.nx * g.nz + (int64_t)g.nx * g.ny);
+    k_cc_ground_open<T><<<cc_blocks(nw), kBlock, 0, L.s>>>(g, alpha, lab, ground);
     k_cc_count<<<cc_blocks(n), kBlock, 0, L.s>>>(n, lab, ground, (int *)scal + 1, fslot);
     *L.counter += 2;
   }
