@@ -97,6 +97,10 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=2,
                     help="step requests per episode (one frame each)")
     ap.add_argument("--serve-slots", type=int, default=8, help="concurrent worker slots")
+    ap.add_argument("--serve-batch", type=int, default=1,
+                    help="most same-size episodes stepped as one batch (1: no batching)")
+    ap.add_argument("--serve-summary-count", type=int, default=48,
+                    help="episodes of the compact serving run in the default bench line")
     ap.add_argument("--serve-budget-gb", type=float, default=150.0, help="admission budget")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-n", type=int, default=64,
@@ -383,6 +387,7 @@ def run_ours(args, rank, world, local_rank):
         out["fp64_plain"] = run_plain(args, P, torch, dev, ctx, ep, value)
         out["cpu_baseline"] = cpu_baseline(args)
         out["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores(args)
+        out["serving"] = serving_summary(args)
     ep.close()
     ctx.close()
     return out
@@ -559,9 +564,9 @@ def _serve_episode(kind, n, seed):
     return cfg["grid"], cfg["scene"], "kinetic_energy"
 
 
-def _serve_run(P, plan, slots, budget):
+def _serve_run(P, plan, slots, budget, batch=8):
     srv = P.Server(slots=slots, hbm_budget=budget, precision="mixed", tol=1e-6,
-                   max_iters=1000, cfl_max=8.0, checkpoint_every=10)
+                   max_iters=1000, cfl_max=8.0, checkpoint_every=10, batch=batch)
     tickets = []
     t0 = time.perf_counter()
     for ep in plan:
@@ -585,6 +590,7 @@ def _serve_run(P, plan, slots, budget):
             cell_frames += ep["cells"]
     srv.close_server()
     every = lat["step"] + lat["step_adjoint"]
+    batches = (int(stats["batches"]), int(stats["batched_requests"]))
     pct = lambda v, q: float(np.percentile(v, q)) if v else None  # noqa: E731
     return dict(value=cell_frames / wall, unit="cell-frames/s", wall_s=wall,
                 requests=len(every), failed=failed,
@@ -592,7 +598,47 @@ def _serve_run(P, plan, slots, budget):
                 step_p50_ms=pct(lat["step"], 50), step_p99_ms=pct(lat["step"], 99),
                 adjoint_p50_ms=pct(lat["step_adjoint"], 50),
                 adjoint_p99_ms=pct(lat["step_adjoint"], 99),
-                slots=slots, bytes_peak=int(stats["bytes_peak"]))
+                slots=slots, batch=batch, batches=batches[0], batched_requests=batches[1],
+                bytes_peak=int(stats["bytes_peak"]))
+
+
+def _serve_plan(count, rate, seed=0, requests=2, sizes=(32, 64, 96, 128, 192)):
+    mix = I.serving_mix(seed=seed, count=count, rate_per_ms=rate, sizes=sizes)
+    rng = np.random.default_rng(12345)
+    plan = []
+    for key, m in enumerate(mix):
+        grid, scene, loss = _serve_episode(m["scene_kind"], m["n"], m["seed"])
+        plan.append(dict(key=key, arrival_ms=m["arrival_ms"], grid=grid, scene=scene, loss=loss,
+                         cells=m["n"] ** 3,
+                         adjoint=[bool(x) for x in rng.uniform(size=requests) < 0.3]))
+    return plan
+
+
+def serving_summary(args):
+    """A compact serving run for the default bench line: episodes of the mix
+    (grids 32..192^3, three scene kinds, 30 % of one-frame requests with the
+    adjoint) arriving faster than the device serves them (saturating), served
+    four ways on the same schedule: 8 slots (the default: no cross-episode
+    batching), 8 slots with batched steps, one slot with batched steps, one
+    episode at a time; for the full size mix and for its small grids (32 and
+    64^3) alone."""
+    import paper_2405_14903_b300 as P
+    budget = int(args.serve_budget_gb * 1e9)
+    keys = ("value", "unit", "p50_ms", "p99_ms", "wall_s", "requests", "failed", "batches",
+            "batched_requests")
+    out = {}
+    for mix, sizes in (("mix", (32, 64, 96, 128, 192)), ("small", (32, 64))):
+        plan = _serve_plan(args.serve_summary_count, rate=5.0, sizes=sizes)
+        res = {}
+        for name, slots, batch in (("slots", 8, 1), ("batched", 8, 8), ("batched_one_slot", 1, 8),
+                                   ("one_at_a_time", 1, 1)):
+            r = _serve_run(P, plan, slots, budget, batch=batch)
+            res[name] = {k: r[k] for k in keys}
+        res["workload"] = (f"{args.serve_summary_count} episodes arriving at 5/ms (saturating), "
+                           f"grids {'/'.join(str(n) for n in sizes)}^3, sphere/chamber/plate, "
+                           "2 one-frame requests each, 30 % with adjoint, MIXED MGPCG 1e-6")
+        out[mix] = res
+    return out
 
 
 def run_serving(args):
@@ -603,17 +649,11 @@ def run_serving(args):
     import torch
     import paper_2405_14903_b300 as P
     torch.cuda.set_device(0)
-    mix = I.serving_mix(seed=0, count=args.serve_count, rate_per_ms=args.serve_rate)
-    rng = np.random.default_rng(12345)
-    plan = []
-    for key, m in enumerate(mix):
-        grid, scene, loss = _serve_episode(m["scene_kind"], m["n"], m["seed"])
-        plan.append(dict(key=key, arrival_ms=m["arrival_ms"], grid=grid, scene=scene, loss=loss,
-                         cells=m["n"] ** 3,
-                         adjoint=[bool(x) for x in rng.uniform(size=args.serve_requests) < 0.3]))
+    plan = _serve_plan(args.serve_count, args.serve_rate, requests=args.serve_requests)
     budget = int(args.serve_budget_gb * 1e9)
-    ours = _serve_run(P, plan, args.serve_slots, budget)
-    one = _serve_run(P, plan, 1, budget)
+    ours = _serve_run(P, plan, args.serve_slots, budget, batch=args.serve_batch)
+    unbatched = _serve_run(P, plan, args.serve_slots, budget, batch=1)
+    one = _serve_run(P, plan, 1, budget, batch=1)
     return dict(metric="served cell-frames/s, serving mix (p50/p99 request latency)",
                 value=ours["value"], unit="cell-frames/s", n_gpus=1, steps=1, warmup=0,
                 ms_per_step=1e3 * ours["wall_s"], higher_is_better=True, scaling="weak",
@@ -624,7 +664,7 @@ def run_serving(args):
                                      "per episode, 30 % with adjoint, MIXED MGPCG 1e-6",
                             slots=args.serve_slots, budget_gb=args.serve_budget_gb),
                 p50_ms=ours["p50_ms"], p99_ms=ours["p99_ms"], served=ours,
-                one_episode_at_a_time=one)
+                slots_without_batching=unbatched, one_episode_at_a_time=one)
 
 
 # ------------------------------------------------------------ precision ----

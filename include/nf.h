@@ -151,6 +151,13 @@ typedef struct nf_config {
                              band sweeps); 2: the same on every grid level
                              above the one-block chain; 0: one launch per
                              half sweep. Same arithmetic, same bits          */
+  int recompute_overlap;  /* 1: during nf_backward (and the serving adjoint),
+                             the next checkpoint segment is recomputed on a
+                             second stream by a helper thread while the
+                             current one is reverted (the same kernels on the
+                             same data: the same results); 0: sequential.
+                             Costs one more segment of tape, a solver
+                             hierarchy and a host thread per episode          */
 } nf_config;
 
 typedef struct nf_grid {
@@ -239,7 +246,8 @@ typedef struct nf_step_stats {
    checkpoint_every 10, no budget, cfl_max 0 (no sub-stepping),
    mg_coarsest_sweeps 8, mg_band_sweeps 0, mg_transfer 1 (constant),
    mg_coarse_weight 1.9, mg_smooth_coarse 0, tape_fractions 0,
-   mg_persistent 0, mg_cluster 0, residual_fp64 1, mg_fused 0. */
+   mg_persistent 0, mg_cluster 0, residual_fp64 1, mg_fused 0,
+   recompute_overlap 1. */
 int nf_config_default(nf_config *cfg);
 
 /* Create a context on cfg->device. *out receives the handle. */
@@ -329,6 +337,31 @@ int nf_get_fractions(nf_ctx *ctx, int64_t id, void *const a[3], int dtype,
    when nu > 0 (3 face arrays). */
 int nf_get_advected(nf_ctx *ctx, int64_t id, void *const u[3], int dtype,
                     int mem);
+/* Advance n episodes (distinct ids, 1 <= n <= 64) of this context by
+   nframes frames each (nf_step), solving every substep's projections as
+   one stacked system: the members' boxes stacked along z with their closed
+   z walls between them, so the stacked operator is block diagonal and each
+   solver launch (smoothing, restriction, coarse chain, CG updates, dots,
+   FP64 residual) serves every member. Members must share nx, ny, nz and
+   their multigrid depth (NF_E_INVALID otherwise); scenes, dt, viscosity,
+   fraction rule and openings may differ. With CFL sub-stepping each member
+   takes its own substeps; a substep's batch holds the members that have
+   it. Each member's right-hand side enters the stack scaled by a power of
+   two to norm in [1/2, 2) (undone on its pressure, exactly), and the
+   stacked solve stops when ||r|| <= tol min_e ||b_e||, which keeps every
+   member's relative residual within tol; a member's result differs
+   from its solve alone within that tolerance (one Krylov process serves all
+   members). st (n entries, may be NULL) receives each member's statistics
+   (the shared solves counted for each) and status (n entries, may be NULL)
+   each member's status: a member whose right-hand side turns non-finite
+   leaves the batch with NF_E_DIVERGED while the others go on. The call
+   returns the worst member status. The tape of each member is
+   recorded as by nf_step, so nf_backward works per member afterwards. The
+   stacked solver's device memory is cached in the context per (cells,
+   members) and is not counted in the HBM budget. */
+int nf_step_batch(nf_ctx *ctx, const int64_t *ids, int n, int nframes, nf_step_stats *st,
+                  int *status);
+
 /* Resume: the episode's state (velocity, frame clock, theta) as host bytes.
    nf_episode_export with buf = NULL sets *bytes to the size needed; with a
    host buffer of *bytes >= that size it writes the state and sets *bytes.
@@ -462,6 +495,8 @@ typedef struct nf_server_stats {
   int64_t submitted, completed, open_waiting, episodes;
   size_t bytes_reserved, bytes_peak, budget;
   int slots;
+  int64_t batches;          /* batched steps run (2 or more members)        */
+  int64_t batched_requests; /* requests served inside those batches         */
 } nf_server_stats;
 
 /* cfg: precision, solver and tolerances of every episode (its device and
@@ -478,6 +513,25 @@ int nf_server_poll(nf_server *srv, int64_t ticket, int wait_ms, nf_result *out);
 /* Wait until every submitted request has completed (wait_ms as in poll). */
 int nf_server_drain(nf_server *srv, int wait_ms);
 int nf_server_stats_get(nf_server *srv, nf_server_stats *out);
+/* Batching: a slot that takes a STEP or STEP_ADJOINT request also takes
+   the queued step requests of other episodes of the same slot with the same
+   cell counts and frame count (each the oldest queued request of its
+   episode), up to max_members in all, and runs their forward frames with
+   nf_step_batch (every projection of a substep solved for all of them in
+   one stacked solve); STEP_ADJOINT members then run their backward pass
+   alone. Admission places an episode on a slot that already holds
+   episodes of its cell counts when that slot is within two requests of the
+   least loaded. Results: each member's forward differs from its solve alone
+   within the solver tolerance. Only episodes of at most max_cells cells
+   batch (and get the slot preference): small grids, whose solver launches
+   are latency-bound, gain from sharing launches, while large ones fill the
+   device alone and lose concurrency to the lockstep. max_members 1 turns
+   batching off, the default: on this GPU the slots' concurrent streams
+   already overlap small episodes' launches, and the batch's lockstep
+   (slot affinity, the slowest member's substeps and iterations) measured
+   slower in the serving mixes; batching pays where few streams serve many
+   small episodes. */
+int nf_server_set_batching(nf_server *srv, int max_members, int64_t max_cells);
 /* Stops the workers after their current request, destroys all episodes. */
 int nf_server_destroy(nf_server *srv);
 

@@ -43,7 +43,8 @@ class Config(C.Structure):
                 ("mg_band_sweeps", C.c_int), ("mg_transfer", C.c_int),
                 ("mg_coarse_weight", C.c_double), ("mg_smooth_coarse", C.c_int),
                 ("tape_fractions", C.c_int), ("mg_persistent", C.c_int),
-                ("mg_cluster", C.c_int), ("residual_fp64", C.c_int), ("mg_fused", C.c_int)]
+                ("mg_cluster", C.c_int), ("residual_fp64", C.c_int), ("mg_fused", C.c_int),
+                ("recompute_overlap", C.c_int)]
 
 
 class Grid(C.Structure):
@@ -91,7 +92,8 @@ class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64),
                 ("open_waiting", C.c_int64), ("episodes", C.c_int64),
                 ("bytes_reserved", C.c_size_t), ("bytes_peak", C.c_size_t),
-                ("budget", C.c_size_t), ("slots", C.c_int)]
+                ("budget", C.c_size_t), ("slots", C.c_int),
+                ("batches", C.c_int64), ("batched_requests", C.c_int64)]
 
 
 REQ = {"open": 0, "step": 1, "step_adjoint": 2, "close": 3}
@@ -138,6 +140,9 @@ SIGNATURES = [
     ("nf_server_drain", C.c_int, [_vp, C.c_int]),
     ("nf_server_stats_get", C.c_int, [_vp, C.POINTER(ServerStats)]),
     ("nf_server_destroy", C.c_int, [_vp]),
+    ("nf_server_set_batching", C.c_int, [_vp, C.c_int, _i64]),
+    ("nf_step_batch", C.c_int, [_vp, C.POINTER(_i64), C.c_int, C.c_int, C.POINTER(StepStats),
+                                C.POINTER(C.c_int)]),
 ]
 
 

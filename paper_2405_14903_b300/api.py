@@ -196,7 +196,8 @@ def _config(precision="mixed", solver="mgpcg", tol=1e-6, max_iters=500,
             checkpoint_every=10, hbm_budget=0, cfl_max=0.0, mg_coarsest_sweeps=8,
             mg_band_sweeps=0, mg_transfer="constant", mg_coarse_weight=1.9,
             mg_smooth_coarse=0, tape_fractions=False, mg_persistent=False,
-            mg_cluster=False, residual_fp64=True, mg_fused=0, device=0, stream=0):
+            mg_cluster=False, residual_fp64=True, mg_fused=0, recompute_overlap=True, device=0,
+            stream=0):
     """An ``nf_config`` from keyword arguments (defaults of nf_config_default)."""
     cfg = L.Config()
     _check(lib.nf_config_default(C.byref(cfg)))
@@ -223,6 +224,7 @@ def _config(precision="mixed", solver="mgpcg", tol=1e-6, max_iters=500,
     cfg.mg_cluster = int(bool(mg_cluster))
     cfg.residual_fp64 = int(bool(residual_fp64))
     cfg.mg_fused = int(mg_fused)
+    cfg.recompute_overlap = int(bool(recompute_overlap))
     return cfg
 
 
@@ -290,6 +292,19 @@ class Context:
 
     def episode(self, grid_desc, scene):
         return Episode(self, grid_desc, scene)
+
+    def step_batch(self, episodes, frames=1):
+        """``nf_step_batch``: advance same-size episodes of this context
+        together, each substep's projections solved as one stacked system;
+        returns each member's statistics with its ``status``."""
+        n = len(episodes)
+        ids = (C.c_int64 * n)(*[e.id for e in episodes])
+        st = (L.StepStats * n)()
+        stat = (C.c_int * n)()
+        rc = lib.nf_step_batch(self._h, ids, n, int(frames), st, stat)
+        if rc in (L.NF_E_INVALID, L.NF_E_CUDA, L.NF_E_OOM):
+            _check(rc, self._h)
+        return [dict(x.as_dict(), status=int(c)) for x, c in zip(st, stat)]
 
 
 class Episode:
@@ -443,13 +458,14 @@ class Server:
     timeout). Keyword arguments configure every episode like ``Context``.
     """
 
-    def __init__(self, slots=4, hbm_budget=0, device=0, **cfg_kw):
+    def __init__(self, slots=4, hbm_budget=0, device=0, batch=1, batch_cells=64 ** 3, **cfg_kw):
         cfg = _config(device=device, stream=0, **cfg_kw)
         h = C.c_void_p()
         _check(lib.nf_server_create(C.byref(cfg), int(slots), int(hbm_budget), C.byref(h)),
                C.c_void_p())
         self._h = h
         self._keep = {}
+        _check(lib.nf_server_set_batching(h, int(batch), int(batch_cells)), C.c_void_p())
 
     def _submit(self, req):
         t = C.c_int64()

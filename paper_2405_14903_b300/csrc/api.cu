@@ -9,6 +9,7 @@
 #include <memory>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "ctx.h"
 #include "episode.h"
@@ -208,6 +209,7 @@ int nf_config_default(nf_config *cfg) {
   cfg->mg_cluster = 0;
   cfg->residual_fp64 = 1;
   cfg->mg_fused = 0;
+  cfg->recompute_overlap = 1;
   return NF_OK;
 }
 
@@ -245,6 +247,7 @@ int nf_create(nf_ctx **out, const nf_config *cfg) {
       (cfg->mg_persistent != 0 && cfg->mg_persistent != 1) ||
       (cfg->residual_fp64 != 0 && cfg->residual_fp64 != 1) ||
       cfg->mg_fused < 0 || cfg->mg_fused > 2 ||
+      (cfg->recompute_overlap != 0 && cfg->recompute_overlap != 1) ||
       (cfg->mg_cluster != 0 && cfg->mg_cluster != 1)) {
     set_error("nf_create: invalid configuration");
     return NF_E_INVALID;
@@ -298,6 +301,7 @@ int nf_destroy(nf_ctx *ctx) {
   cudaSetDevice(ctx->c.device);
   if (ctx->c.stream) cudaStreamSynchronize(ctx->c.stream);
   ctx->eps.clear();
+  ctx->batches.clear();  // frees on the context's stream, before it goes
   if (ctx->c.rs.partials) cudaFree(ctx->c.rs.partials);
   if (ctx->c.rs.ticket) cudaFree(ctx->c.rs.ticket);
   if (ctx->c.pinned) cudaFreeHost(ctx->c.pinned);
@@ -479,6 +483,39 @@ int nf_get_pressure(nf_ctx *ctx, int64_t id, void *p, int dtype, int mem) {
   EPISODE(ctx, id, e);
   if (!p || !valid_dtype(dtype) || !valid_mem(mem)) return NF_E_INVALID;
   return e->get_pressure(p, dtype, mem);
+}
+
+int nf_step_batch(nf_ctx *ctx, const int64_t *ids, int n, int nframes, nf_step_stats *st,
+                  int *status) {
+  GUARD(ctx);
+  if (!ids || n < 1 || n > 64 || nframes < 0) {
+    set_error("nf_step_batch: need 1 to 64 episode ids and nframes >= 0");
+    return NF_E_INVALID;
+  }
+  std::vector<nf::EpisodeBase *> eps(n);
+  for (int i = 0; i < n; ++i) {
+    auto it = ctx->eps.find(ids[i]);
+    if (it == ctx->eps.end()) {
+      set_error("nf_step_batch: unknown episode id");
+      return NF_E_INVALID;
+    }
+    for (int j = 0; j < i; ++j)
+      if (ids[j] == ids[i]) {
+        set_error("nf_step_batch: an episode appears twice");
+        return NF_E_INVALID;
+      }
+    eps[i] = it->second.get();
+  }
+  if (n == 1) {
+    const int rc = eps[0]->step(nframes, st);
+    if (status) status[0] = rc;
+    return rc;
+  }
+  if (!eps[0]->batchable_with(eps.data(), n)) {
+    set_error("nf_step_batch: members must share their cell counts and multigrid depth");
+    return NF_E_INVALID;
+  }
+  return nf::step_batch(&ctx->c, ctx->batches, eps.data(), n, nframes, st, status);
 }
 
 int nf_episode_export(nf_ctx *ctx, int64_t id, void *buf, size_t *bytes) {

@@ -11,5 +11,6 @@
 struct nf_ctx {
   nf::Ctx c;
   std::map<int64_t, std::unique_ptr<nf::EpisodeBase>> eps;
+  nf::BatchCache batches;  // stacked solvers of nf_step_batch
   int64_t next_id = 1;
 };

@@ -25,6 +25,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <thread>
 #include <vector>
 
 #include "components.h"
@@ -291,6 +292,21 @@ __global__ void k_cast(int64_t n, const A *in, B *out) {
     out[i] = (B)in[i];
 }
 
+// out = f in (f a power of two: exact).
+template <class A>
+__global__ void k_scaled_copy(int64_t n, const A *in, A *out, double f) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (A)((double)in[i] * f);
+}
+template <class A>
+static void scaled_copy(const Launch &L, int64_t n, const A *in, A *out, double f) {
+  unsigned nb = nblocks(n);
+  if (nb > 148u * 32u) nb = 148u * 32u;
+  k_scaled_copy<A><<<nb, kBlock, 0, L.s>>>(n, in, out, f);
+  ++*L.counter;
+}
+
 template <class A, class B>
 static void cast(const Launch &L, int64_t n, const A *in, B *out) {
   unsigned nb = nblocks(n);
@@ -418,7 +434,8 @@ class EpisodeImpl : public EpisodeBase {
       const SceneDev sd = scene_at(sc_, 0.0, dsph_, &bz_);
       launch_rasterize<T>(L, g_, sd, mut(alpha_));
       SolveStats ss;
-      CKS(project_faces(g_, sd, Uinit_, Pinit_, U_, &ss));
+      Eng e = eng();
+      CKS(project_faces(e, g_, sd, Uinit_, Pinit_, U_, &ss));
       CKC(cudaMemcpyAsync(Uh_, Uinit_, nfaces_ * sizeof(T), cudaMemcpyDeviceToDevice, L.s));
       CKC(cudaMemcpyAsync(P_, Pinit_, ncell_ * sizeof(S), cudaMemcpyDeviceToDevice, L.s));
       acc_stats(&s, ss);
@@ -442,28 +459,11 @@ class EpisodeImpl : public EpisodeBase {
         if (!std::isfinite(umax)) return diverged("step: non-finite velocity");
         m = std::max(1, (int)std::ceil(umax * g_.dt / (g_.dx * cfl)));
       }
-      const int f = frames_;
       for (int sub = 0; sub < m; ++sub) {
-        // t = (f + (sub + 1) / m) dt, exact for m = 1
-        const double h = g_.dt / m;
-        const double t1 = (double)(f * (int64_t)m + sub + 1) * h;
-        const int C = std::max(1, ctx_->cfg.checkpoint_every);
-        if (n_ % C == 0) {
-          const int idx = n_ / C;
-          while ((int)ckpt_.size() <= idx) {
-            T *p = nullptr;
-            CKS(faces(&p));
-            ckpt_.push_back(p);
-          }
-          CKC(cudaMemcpyAsync(ckpt_[idx], U_, nfaces_ * sizeof(T),
-                              cudaMemcpyDeviceToDevice, ctx_->stream));
-        }
-        ts_.resize(n_ + 1);
-        hs_.resize(n_ + 1);
-        ts_[n_] = t1;
-        hs_[n_] = h;
+        CKS(begin_substep(sub, m));
         SolveStats ss;
-        CKS(forward_step(n_, U_, U_, Uh_, P_, &ss));
+        Eng e = eng();
+        CKS(forward_step(e, n_, U_, U_, Uh_, P_, &ss));
         acc_stats(&s, ss);
         s.steps += 1;
         if (ss.status != NF_OK && worst == NF_OK) worst = ss.status;
@@ -471,10 +471,7 @@ class EpisodeImpl : public EpisodeBase {
           worst = NF_E_DIVERGED;
           break;
         }
-        ++n_;
-        n_rev_ = n_;
-        init_reverted_ = false;  // a later backward covers the whole history
-        seg_start_ = -1;  // a new step invalidates the cached segment
+        end_substep();
       }
       ++frames_;
     }
@@ -547,10 +544,23 @@ class EpisodeImpl : public EpisodeBase {
     nf_step_stats s{};
     double gth[kMaxParams] = {0};
     int worst = NF_OK;
+    overlap_now_ = overlap_ok();
     while (n_rev_ > 0 || (init_proj_ && !init_reverted_)) {
       const int rc = revert_one(gth, &s);
-      if (rc != NF_OK && rc != NF_E_NOT_CONVERGED) return rc;
+      if (rc != NF_OK && rc != NF_E_NOT_CONVERGED) {
+        overlap_now_ = false;
+        if (helper_seg_ >= 0) {  // a helper still running: wait, drop its segment
+          helper_seg_ = -1;
+          if (helper_->th.joinable()) helper_->th.join();
+        }
+        return rc;
+      }
       if (rc != NF_OK && worst == NF_OK) worst = rc;
+    }
+    overlap_now_ = false;
+    if (helper_seg_ >= 0) {
+      helper_seg_ = -1;
+      if (helper_->th.joinable()) helper_->th.join();
     }
     if (g_theta)
       for (int k = 0; k < sc_.K; ++k) g_theta[k] = gth[k];
@@ -767,102 +777,329 @@ class EpisodeImpl : public EpisodeBase {
   // Zero mean on every floating component; returns ||v||^2 afterwards.
   double gauge(S *v, double n2) { return cc_.gauge<S>(ctx_, ncell_, v, n2); }
 
+  // What one forward step works with: a context (stream, reduction
+  // scratch), fraction and right-hand-side scratch, components, a solver.
+  // The episode's own engine serves every call; a second one (its own
+  // stream) lets the backward pass recompute the next segment while it
+  // reverts the current one.
+  struct Eng {
+    Ctx *ctx;
+    T *alpha;
+    S *b;
+    Components *cc;
+    Solver<T, S, V, TA> *solver;
+    T *Ut;
+    double *dscal;
+  };
+  Eng eng() { return Eng{ctx_, alpha_, b_, &cc_, &solver_, Ut_, dscal_}; }
+
   // ----------------------------------------------------------- forward ----
-  // Right-hand side, solve and blended update for fractions alpha_ (already
+  // Right-hand side, solve and blended update for fractions e.alpha (already
   // rasterised for scene state sd): uh -> P, u_out.
-  int project_faces(const GridDev &g, const SceneDev &sd, const T *uh, S *P,
+  int project_faces(Eng &e, const GridDev &g, const SceneDev &sd, const T *uh, S *P,
                     T *u_out, SolveStats *ss) {
     NvtxRange nv("nf.project");
-    Launch L = ctx_->launch();
-    CKS(cc_.label<T>(ctx_, g, cview(alpha_)));
-    launch_rhs<T, S>(L, g, sd, cview(alpha_), cview(uh), b_, ctx_->rs, dscal_);
-    solver_.set_fractions(comp(alpha_, 0), comp(alpha_, 1), comp(alpha_, 2));
-    const double bn2 = gauge(b_, ctx_->read_double(dscal_));
+    Launch L = e.ctx->launch();
+    CKS(e.cc->template label<T>(e.ctx, g, cview(e.alpha)));
+    launch_rhs<T, S>(L, g, sd, cview(e.alpha), cview(uh), e.b, e.ctx->rs, e.dscal);
+    e.solver->set_fractions(comp(e.alpha, 0), comp(e.alpha, 1), comp(e.alpha, 2));
+    const double bn2 = e.cc->template gauge<S>(e.ctx, ncell_, e.b, e.ctx->read_double(e.dscal));
     {
       NvtxRange nvs("nf.solve");
-      *ss = solver_.solve(b_, P, bn2);
+      *ss = e.solver->solve(e.b, P, bn2);
     }
-    gauge(P, 0.0);
-    launch_update<T, S>(L, g, sd, cview(alpha_), cview(uh), P, mut(u_out));
+    e.cc->template gauge<S>(e.ctx, ncell_, P, 0.0);
+    launch_update<T, S>(L, g, sd, cview(e.alpha), cview(uh), P, mut(u_out));
     return NF_OK;
+  }
+
+  // Substep sub of m of the current frame: its time and length on the
+  // tape, and a checkpoint of U every checkpoint_every steps.
+  int begin_substep(int sub, int m) {
+    // t = (f + (sub + 1) / m) dt, exact for m = 1
+    const double h = g_.dt / m;
+    const double t1 = (double)(frames_ * (int64_t)m + sub + 1) * h;
+    const int C = std::max(1, ctx_->cfg.checkpoint_every);
+    if (n_ % C == 0) {
+      const int idx = n_ / C;
+      while ((int)ckpt_.size() <= idx) {
+        T *p = nullptr;
+        CKS(faces(&p));
+        ckpt_.push_back(p);
+      }
+      CKC(cudaMemcpyAsync(ckpt_[idx], U_, nfaces_ * sizeof(T), cudaMemcpyDeviceToDevice,
+                          ctx_->stream));
+    }
+    ts_.resize(n_ + 1);
+    hs_.resize(n_ + 1);
+    ts_[n_] = t1;
+    hs_[n_] = h;
+    return NF_OK;
+  }
+  void end_substep() {
+    ++n_;
+    n_rev_ = n_;
+    init_reverted_ = false;  // a later backward covers the whole history
+    seg_start_ = -1;         // a new step invalidates the cached segment
   }
 
   // Step m (from ts_[m] - hs_[m] to ts_[m]): u_in -> uh, P, u_out (u_out
   // may alias u_in).
-  int forward_step(int m, const T *u_in, T *u_out, T *uh, S *P, SolveStats *ss) {
+  int forward_step(Eng &e, int m, const T *u_in, T *u_out, T *uh, S *P, SolveStats *ss) {
     NvtxRange nv("nf.step");
-    Launch L = ctx_->launch();
     const GridDev g = grid_h(hs_[m]);
     const SceneDev sd = scene_at(sc_, ts_[m], dsph_, &bz_);
+    CKS(geometry_and_advect(e, m, g, sd, u_in, uh));
+    return project_faces(e, g, sd, uh, P, u_out, ss);
+  }
+
+  // Step m up to the projection: fractions at its end time (taped or
+  // rasterised), then U^ from u_in by advection and viscosity.
+  int geometry_and_advect(Eng &e, int m, const GridDev &g, const SceneDev &sd, const T *u_in,
+                          T *uh) {
+    Launch L = e.ctx->launch();
     if (m < (int)tapeA_.size() && tapeA_[m] && tapeA_ok_[m]) {
       // recomputed step: the fractions kept by the first pass (bit-identical
       // to rasterising them again)
-      CKC(cudaMemcpyAsync(alpha_, tapeA_[m], nfaces_ * sizeof(T), cudaMemcpyDeviceToDevice, L.s));
+      CKC(cudaMemcpyAsync(e.alpha, tapeA_[m], nfaces_ * sizeof(T), cudaMemcpyDeviceToDevice, L.s));
     } else {
       NvtxRange nvr("nf.rasterize");
-      launch_rasterize<T>(L, g, sd, mut(alpha_));
-      if (ctx_->cfg.tape_fractions) {
+      launch_rasterize<T>(L, g, sd, mut(e.alpha));
+      if (e.ctx == ctx_ && ctx_->cfg.tape_fractions) {  // (the first pass only)
         if ((int)tapeA_.size() <= m) {
           tapeA_.resize(m + 1, nullptr);
           tapeA_ok_.resize(m + 1, 0);
         }
         if (!tapeA_[m]) CKS(faces(&tapeA_[m]));
-        CKC(cudaMemcpyAsync(tapeA_[m], alpha_, nfaces_ * sizeof(T), cudaMemcpyDeviceToDevice, L.s));
+        CKC(cudaMemcpyAsync(tapeA_[m], e.alpha, nfaces_ * sizeof(T), cudaMemcpyDeviceToDevice, L.s));
         tapeA_ok_[m] = 1;
       }
     }
     NvtxRange nva("nf.advect");
-    if (Ut_) {
+    if (e.Ut) {
       // U~ = B(U) U, then U^ = (I - nu h / dx^2 G^T G) U~ (Sec. 2.3.1)
-      launch_advect<T>(L, g, cview(u_in), mut(Ut_), ctx_->cfg.advect_order);
-      launch_viscosity<T>(L, g, cview(Ut_), mut(uh));
+      launch_advect<T>(L, g, cview(u_in), mut(e.Ut), ctx_->cfg.advect_order);
+      launch_viscosity<T>(L, g, cview(e.Ut), mut(uh));
     } else {
       launch_advect<T>(L, g, cview(u_in), mut(uh), ctx_->cfg.advect_order);
     }
-    return project_faces(g, sd, uh, P, u_out, ss);
+    return NF_OK;
   }
 
+ public:
+  // ------------------------------------------------ batched substeps -----
+  // nf_step_batch: the members' substeps run up to the right-hand side on
+  // their own, the projections of one substep as one stacked solve, then
+  // each member's blended update.
+  int batch_before(int sub, int m, GridDev *g, SceneDev *sd, double *bn2) {
+    CKS(begin_substep(sub, m));
+    *g = grid_h(hs_[n_]);
+    *sd = scene_at(sc_, ts_[n_], dsph_, &bz_);
+    Eng e = eng();
+    CKS(geometry_and_advect(e, n_, *g, *sd, U_, Uh_));
+    Launch L = ctx_->launch();
+    launch_rhs<T, S>(L, *g, *sd, cview(alpha_), cview(Uh_), b_, ctx_->rs, dscal_);
+    *bn2 = ctx_->read_double(dscal_);
+    return check_launch();
+  }
+  int batch_after(const GridDev &g, const SceneDev &sd) {
+    Launch L = ctx_->launch();
+    launch_update<T, S>(L, g, sd, cview(alpha_), cview(Uh_), P_, mut(U_));
+    end_substep();
+    return check_launch();
+  }
+  void batch_end_frame() { ++frames_; }
+  int substeps_now(int *m) {
+    *m = 1;
+    if (ctx_->cfg.cfl_max > 0.0) {
+      const double umax = max_speed();
+      if (!std::isfinite(umax)) return diverged("step: non-finite velocity");
+      *m = std::max(1, (int)std::ceil(umax * g_.dt / (g_.dx * ctx_->cfg.cfl_max)));
+    }
+    return NF_OK;
+  }
+  const GridDev &grid() const { return g_; }
+  bool batchable_with(EpisodeBase *const *eps, int n) const override {
+    for (int i = 0; i < n; ++i) {
+      const auto *o = static_cast<const EpisodeImpl *>(eps[i]);
+      if (o->g_.nx != g_.nx || o->g_.ny != g_.ny || o->g_.nz != g_.nz ||
+          o->solver_.levels() != solver_.levels())
+        return false;
+    }
+    return true;
+  }
+  const T *alpha() const { return alpha_; }
+  const S *rhs() const { return b_; }
+  S *pressure_buf() { return P_; }
+  int levels() const { return solver_.levels(); }
+  void acc(nf_step_stats *s, const SolveStats &ss) { acc_stats(s, ss); }
+
+ private:
+
   // ---------------------------------------------------------- backward ----
-  int ensure_segment_buffers(int C) {
-    while ((int)segU_.size() < C) {
+  // A recomputed segment: per step the velocity entering it, U^, the
+  // fractions, the pressure and whether a component floats.
+  struct Seg {
+    std::vector<T *> U, Uh, A;
+    std::vector<S *> P;
+    std::vector<int> Float;
+    T *tmpU = nullptr;
+    int start = -1;  // first step held (-1: none)
+  };
+
+  int ensure_segment_buffers(Seg &sg, int C) {
+    while ((int)sg.U.size() < C) {
       T *a = nullptr, *b = nullptr, *f = nullptr;
       S *p = nullptr;
       CKS(faces(&a));
       CKS(faces(&b));
       CKS(faces(&f));
       CKS(A_.get(&p, ncell_ * sizeof(S)));
-      segU_.push_back(a);
-      segUh_.push_back(b);
-      segA_.push_back(f);
-      segP_.push_back(p);
-      segFloat_.push_back(-1);
+      sg.U.push_back(a);
+      sg.Uh.push_back(b);
+      sg.A.push_back(f);
+      sg.P.push_back(p);
+      sg.Float.push_back(-1);
     }
-    if (!tmpU_) CKS(faces(&tmpU_));
+    if (!sg.tmpU) CKS(faces(&sg.tmpU));
     return NF_OK;
   }
 
-  // Recompute segment s from its checkpoint, recording the per-step tape.
-  int recompute_segment(int s, nf_step_stats *st) {
+  // Recompute segment s from its checkpoint with engine e into sg.
+  int recompute_into(Eng &e, Seg &sg, int s, nf_step_stats *st) {
     NvtxRange nv("nf.recompute");
     const int C = std::max(1, ctx_->cfg.checkpoint_every);
-    CKS(ensure_segment_buffers(C));
     const int start = s * C, end = std::min(start + C, n_);
-    CKC(cudaMemcpyAsync(segU_[0], ckpt_[s], nfaces_ * sizeof(T),
-                        cudaMemcpyDeviceToDevice, ctx_->stream));
+    CKC(cudaMemcpyAsync(sg.U[0], ckpt_[s], nfaces_ * sizeof(T), cudaMemcpyDeviceToDevice,
+                        e.ctx->stream));
     for (int m = start; m < end; ++m) {
       const int k = m - start;
-      T *out = (k + 1 < end - start) ? segU_[k + 1] : tmpU_;
+      T *out = (k + 1 < end - start) ? sg.U[k + 1] : sg.tmpU;
       SolveStats ss;
-      CKS(forward_step(m, segU_[k], out, segUh_[k], segP_[k], &ss));
+      CKS(forward_step(e, m, sg.U[k], out, sg.Uh[k], sg.P[k], &ss));
       // keep the step's fractions for its adjoint (saves a rasterisation)
       // and whether any component floats (if none, the adjoint needs no
       // labels: its gauge is the identity)
-      CKC(cudaMemcpyAsync(segA_[k], alpha_, nfaces_ * sizeof(T),
-                          cudaMemcpyDeviceToDevice, ctx_->stream));
-      segFloat_[k] = cc_.nfloat;
+      CKC(cudaMemcpyAsync(sg.A[k], e.alpha, nfaces_ * sizeof(T), cudaMemcpyDeviceToDevice,
+                          e.ctx->stream));
+      sg.Float[k] = e.cc->nfloat;
       acc_stats(st, ss);
     }
-    seg_start_ = start;
+    sg.start = start;
+    return NF_OK;
+  }
+
+  // Segment s on the episode's own engine.
+  int recompute_segment(int s, nf_step_stats *st) {
+    CKS(ensure_segment_buffers(seg_, std::max(1, ctx_->cfg.checkpoint_every)));
+    Eng e = eng();
+    CKS(recompute_into(e, seg_, s, st));
+    seg_start_ = seg_.start;
+    return NF_OK;
+  }
+
+  // ------------------------------------------- overlapped recompute -----
+  // While the backward pass reverts segment s on the context's stream, a
+  // helper thread recomputes segment s - 1 on a stream of its own, with its
+  // own solver, components and scratch, into a second segment set; the two
+  // are swapped at the segment boundary. Both are latency-bound chains of
+  // small launches, so their kernels fill each other's gaps. Results are
+  // those of the sequential order (the same kernels on the same data).
+  struct Helper {
+    Ctx ctx;
+    std::unique_ptr<Solver<T, S, V, TA>> solver;
+    Components cc;
+    T *alpha = nullptr, *Ut = nullptr;
+    S *b = nullptr;
+    double *dscal = nullptr;
+    Seg seg;
+    std::thread th;
+    int rc = NF_OK;
+    nf_step_stats st{};
+    bool ready = false;
+    ~Helper() {
+      if (th.joinable()) th.join();
+      if (ctx.stream) cudaStreamDestroy(ctx.stream);
+      if (ctx.rs.partials) cudaFree(ctx.rs.partials);
+      if (ctx.rs.ticket) cudaFree(ctx.rs.ticket);
+      if (ctx.pinned) cudaFreeHost(ctx.pinned);
+    }
+  };
+
+  bool overlap_ok() const {
+    if (!ctx_->cfg.recompute_overlap || ctx_->prof.kclass != -2) return false;
+    // the taped fractions must cover every step (a recompute that rasterises
+    // would write the tape from the helper thread)
+    if (ctx_->cfg.tape_fractions)
+      for (int m = 0; m < n_; ++m)
+        if (m >= (int)tapeA_.size() || !tapeA_[m] || !tapeA_ok_[m]) return false;
+    return true;
+  }
+
+  int helper_init() {
+    if (helper_) return NF_OK;
+    auto h = std::make_unique<Helper>();
+    h->ctx.device = ctx_->device;
+    h->ctx.cfg = ctx_->cfg;
+    h->ctx.prof.kclass = -2;
+    CKC(cudaStreamCreateWithFlags(&h->ctx.stream, cudaStreamNonBlocking));
+    CKC(cudaMalloc(&h->ctx.rs.partials, sizeof(double) * kRedBlocks * kMaxWidth));
+    CKC(cudaMalloc(&h->ctx.rs.ticket, sizeof(unsigned int)));
+    CKC(cudaMemset(h->ctx.rs.ticket, 0, sizeof(unsigned int)));
+    CKC(cudaMallocHost(&h->ctx.pinned, 4096));
+    CKS(faces(&h->alpha));
+    if (g_.nu > 0.0) CKS(faces(&h->Ut));
+    CKS(A_.get(&h->b, ncell_ * sizeof(S)));
+    CKS(A_.get(&h->dscal, 64 * sizeof(double)));
+    h->solver = std::make_unique<Solver<T, S, V, TA>>(&h->ctx, g_, ctx_->cfg);
+    CKS(h->solver->init(A_));
+    CKS(h->cc.init(A_, ncell_));
+    h->solver->set_projector(&h->cc);
+    CKS(ensure_segment_buffers(h->seg, std::max(1, ctx_->cfg.checkpoint_every)));
+    CKC(cudaStreamSynchronize(ctx_->stream));  // allocations are ordered on this stream
+    helper_ = std::move(h);
+    return NF_OK;
+  }
+
+  // Start recomputing segment s on the helper (context stream's work so far
+  // comes first: the checkpoints and buffers it reads).
+  int helper_start(int s) {
+    Helper &h = *helper_;
+    cudaEvent_t ev;
+    CKC(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CKC(cudaEventRecord(ev, ctx_->stream));
+    CKC(cudaStreamWaitEvent(h.ctx.stream, ev, 0));
+    CKC(cudaEventDestroy(ev));
+    h.rc = NF_OK;
+    h.st = nf_step_stats{};
+    h.ready = false;
+    const int dev = ctx_->device;
+    h.th = std::thread([this, &h, s, dev] {
+      cudaSetDevice(dev);
+      Eng e{&h.ctx, h.alpha, h.b, &h.cc, h.solver.get(), h.Ut, h.dscal};
+      int rc = recompute_into(e, h.seg, s, &h.st);
+      const cudaError_t ce = cudaStreamSynchronize(h.ctx.stream);
+      if (rc == NF_OK && ce != cudaSuccess) rc = cuda_fail(ce, "recompute helper");
+      h.rc = rc;
+    });
+    return NF_OK;
+  }
+
+  // Wait for the helper; on success its segment becomes the current one.
+  int helper_join(nf_step_stats *st) {
+    Helper &h = *helper_;
+    if (!h.th.joinable()) return NF_OK;
+    h.th.join();
+    ctx_->launches += h.ctx.launches;
+    h.ctx.launches = 0;
+    if (h.rc != NF_OK && h.rc != NF_E_NOT_CONVERGED) return h.rc;
+    st->solves += h.st.solves;
+    st->iters += h.st.iters;
+    st->outer += h.st.outer;
+    st->max_iters = std::max(st->max_iters, h.st.max_iters);
+    st->rel_residual = std::max(st->rel_residual, h.st.rel_residual);
+    std::swap(seg_, h.seg);
+    seg_start_ = seg_.start;
     return NF_OK;
   }
 
@@ -910,14 +1147,24 @@ class EpisodeImpl : public EpisodeBase {
     const int m = n_rev_ - 1;
     const int C = std::max(1, ctx_->cfg.checkpoint_every);
     const int s = m / C;
+    if (seg_start_ != s * C && helper_ && helper_seg_ == s) {
+      helper_seg_ = -1;
+      CKS(helper_join(st));
+    }
     if (seg_start_ != s * C) CKS(recompute_segment(s, st));
+    // the segment before this one, on the helper, while this one is reverted
+    if (overlap_now_ && s >= 1 && helper_seg_ < 0) {
+      CKS(helper_init());
+      CKS(helper_start(s - 1));
+      helper_seg_ = s - 1;
+    }
     const int k = m - seg_start_;
     const GridDev g = grid_h(hs_[m]);
     const SceneDev sd = scene_at(sc_, ts_[m], dsph_, &bz_);
     // the step's fractions, kept by the recompute (the solver's captured
     // graphs read alpha_, so they are copied back rather than pointed to)
-    CKC(cudaMemcpyAsync(alpha_, segA_[k], nfaces_ * sizeof(T), cudaMemcpyDeviceToDevice, L.s));
-    const int rc = adjoint_projection(g, sd, segUh_[k], segP_[k], gth, st, segFloat_[k] != 0);
+    CKC(cudaMemcpyAsync(alpha_, seg_.A[k], nfaces_ * sizeof(T), cudaMemcpyDeviceToDevice, L.s));
+    const int rc = adjoint_projection(g, sd, seg_.Uh[k], seg_.P[k], gth, st, seg_.Float[k] != 0);
     const T *gUt = gUh_;
     if (Ut_) {
       // dJ/dU~ = (I - nu h / dx^2 G^T G) dJ/dU^ (Sec. 2.3.2; the map is
@@ -927,7 +1174,7 @@ class EpisodeImpl : public EpisodeBase {
     }
     {
       NvtxRange nva("nf.advect_adjoint");
-      launch_advect_adjoint<T>(L, g, cview(segU_[k]), cview(gUt), mut(gUb_),
+      launch_advect_adjoint<T>(L, g, cview(seg_.U[k]), cview(gUt), mut(gUb_),
                                ctx_->cfg.advect_order);
     }
     std::swap(gU_, gUb_);
@@ -944,7 +1191,7 @@ class EpisodeImpl : public EpisodeBase {
   Alloc A_;
   int64_t nfaces_ = 0, ncell_ = 0;
   T *U_ = nullptr, *Uh_ = nullptr, *alpha_ = nullptr;
-  T *gU_ = nullptr, *gUb_ = nullptr, *gUh_ = nullptr, *tmpU_ = nullptr;
+  T *gU_ = nullptr, *gUb_ = nullptr, *gUh_ = nullptr;
   T *Ut_ = nullptr;  // viscous grids only: U~ (forward), dJ/dU~ (adjoint)
   S *P_ = nullptr, *b_ = nullptr, *gP_ = nullptr, *y_ = nullptr;
   void *stage_ = nullptr;
@@ -961,9 +1208,10 @@ class EpisodeImpl : public EpisodeBase {
   S *Pinit_ = nullptr;
   std::vector<T *> ckpt_;
   int seg_start_ = -1;
-  std::vector<T *> segU_, segUh_, segA_;
-  std::vector<S *> segP_;
-  std::vector<int> segFloat_;  // floating components of each segment step
+  Seg seg_;                          // the segment the backward pass reverts
+  std::unique_ptr<Helper> helper_;   // overlapped recompute (backward)
+  int helper_seg_ = -1;              // segment the helper is recomputing
+  bool overlap_now_ = false;         // inside a whole-rollout backward pass
   std::vector<T *> tapeA_;     // fractions of every step (tape_fractions)
   std::vector<char> tapeA_ok_; // tapeA_[m] holds step m of the current tape
 };
@@ -980,6 +1228,195 @@ size_t episode_base_bytes(const nf_config &cfg, const nf_grid &g) {
   b += nc * s + 5 * nc * v;                      // solver vectors
   b += (nc * (2 * v + 3 * t)) * 2 / 7 + nc * v;  // hierarchy (approx.)
   return b;
+}
+
+// ------------------------------------------------------ batched solve -----
+// B same-size episodes stacked along z into one grid of nx x ny x (B nz)
+// cells. Each member keeps its own closed z walls (alpha = 0 on the planes
+// between members), so the stacked operator is block diagonal: one solve
+// of the stack is B independent projections, and every kernel of the
+// solver (smoothing, restriction, the coarse chain, the CG updates and dots,
+// the FP64 residual) runs once for all members. The stacked hierarchy is
+// capped at the members' own level count, so coarse cells never straddle
+// two members. Members' CG iterates share their step lengths (one Krylov
+// process): the result of each member differs from its solve alone within
+// the solver tolerance, which the stopping rule keeps for every member.
+template <class T, class S, class V, class TA>
+struct BatchProj : BatchBase {
+  Ctx *ctx;
+  GridDev gs;  // stacked grid, unit operator scale
+  GridDev ge;  // one member's grid
+  int B;
+  Alloc A;
+  Solver<T, S, V, TA> solver;
+  Components cc;
+  T *alpha = nullptr;
+  S *b = nullptr, *P = nullptr;
+  std::vector<double> scale_;  // each member's right-hand-side scale
+
+  static GridDev stacked(const GridDev &g, int B) {
+    GridDev s = g;
+    s.nz = g.nz * B;
+    s.c = 1.0;
+    s.outlet = 0;  // open faces are found from the fractions
+    s.inlet = 0;
+    return s;
+  }
+  BatchProj(Ctx *c, const GridDev &g, int nb)
+      : ctx(c), gs(stacked(g, nb)), ge(g), B(nb), solver(c, stacked(g, nb), c->cfg),
+        scale_(nb, 1.0) {
+    A.stream = c->stream;
+  }
+  ~BatchProj() override { A.free_all(); }
+  size_t bytes() const override { return A.bytes; }
+
+  int init(int levels) {
+    const int64_t nf = gs.nface(0) + gs.nface(1) + gs.nface(2);
+    CKS(A.get(&alpha, nf * sizeof(T)));
+    CKS(A.get(&b, gs.ncell() * sizeof(S)));
+    CKS(A.get(&P, gs.ncell() * sizeof(S)));
+    solver.set_max_levels(levels);
+    CKS(solver.init(A));
+    CKS(cc.init(A, gs.ncell()));
+    solver.set_projector(&cc);
+    return NF_OK;
+  }
+
+  // Gather the members' fractions and right-hand sides (slot e of the
+  // stack; a null member leaves its slot empty: no active cell), solve,
+  // scatter the pressures. bn2[e] = ||b_e||^2 of each member.
+  template <class E>
+  SolveStats solve(E *const *mem, const double *bn2) {
+    Launch L = ctx->launch();
+    const int64_t fx = ge.nface(0), fy = ge.nface(1), nc = ge.ncell();
+    const int64_t zplane = (int64_t)ge.nx * ge.ny;
+    T *ax = alpha, *ay = alpha + gs.nface(0), *az = alpha + gs.nface(0) + gs.nface(1);
+    double total = 0.0, tmin = 0.0;
+    for (int e = 0; e < B; ++e) {
+      if (!mem[e]) {
+        cudaMemsetAsync(ax + e * fx, 0, fx * sizeof(T), L.s);
+        cudaMemsetAsync(ay + e * fy, 0, fy * sizeof(T), L.s);
+        cudaMemsetAsync(az + e * nc, 0, nc * sizeof(T), L.s);
+        cudaMemsetAsync(b + e * nc, 0, nc * sizeof(S), L.s);
+        continue;
+      }
+      const T *a = mem[e]->alpha();
+      cudaMemcpyAsync(ax + e * fx, a, fx * sizeof(T), cudaMemcpyDeviceToDevice, L.s);
+      cudaMemcpyAsync(ay + e * fy, a + fx, fy * sizeof(T), cudaMemcpyDeviceToDevice, L.s);
+      // z faces: the member's planes 0 .. nz - 1 (its top wall is the next
+      // member's bottom wall, alpha = 0 in both)
+      cudaMemcpyAsync(az + e * nc, a + fx + fy, nc * sizeof(T), cudaMemcpyDeviceToDevice, L.s);
+      // each member's right-hand side scaled by a power of two to norm in
+      // [1/2, 2) (exact, undone on its pressure): the stacked stopping rule
+      // then asks every member for about the same relative residual
+      const double sb = bn2[e] > 0.0 ? std::ldexp(1.0, -std::ilogb(std::sqrt(bn2[e]))) : 1.0;
+      scale_[e] = sb;
+      scaled_copy<S>(L, nc, mem[e]->rhs(), b + e * nc, sb);
+      const double n2 = bn2[e] * sb * sb;
+      total += n2;
+      if (n2 > 0.0 && (tmin == 0.0 || n2 < tmin)) tmin = n2;
+    }
+    cudaMemsetAsync(az + (int64_t)B * nc, 0, zplane * sizeof(T), L.s);  // the stack's top wall
+    SolveStats ss;
+    if (cc.label<T>(ctx, gs, Fields<T>{ax, ay, az}) != NF_OK) {
+      ss.status = NF_E_CUDA;
+      return ss;
+    }
+    solver.set_fractions(ax, ay, az);
+    const double bn = cc.gauge<S>(ctx, gs.ncell(), b, total);
+    ss = solver.solve(b, P, bn, tmin);
+    cc.gauge<S>(ctx, gs.ncell(), P, 0.0);
+    for (int e = 0; e < B; ++e)
+      if (mem[e]) scaled_copy<S>(L, nc, P + e * nc, mem[e]->pressure_buf(), 1.0 / scale_[e]);
+    return ss;
+  }
+};
+
+template <class T, class S, class V, class TA>
+static int step_batch_t(Ctx *ctx, BatchCache &cache, EpisodeBase *const *base, int n,
+                        int nframes, nf_step_stats *st, int *stat) {
+  using E = EpisodeImpl<T, S, V, TA>;
+  std::vector<E *> eps(n);
+  for (int i = 0; i < n; ++i) eps[i] = static_cast<E *>(base[i]);
+  const GridDev &g0 = eps[0]->grid();
+  const std::array<int, 4> key = {g0.nx, g0.ny, g0.nz, n};
+  auto it = cache.find(key);
+  if (it == cache.end()) {
+    auto *bp = new BatchProj<T, S, V, TA>(ctx, g0, n);
+    const int rc = bp->init(eps[0]->levels());
+    if (rc != NF_OK) {
+      delete bp;
+      return rc;
+    }
+    it = cache.emplace(key, std::unique_ptr<BatchBase>(bp)).first;
+  }
+  auto *bp = static_cast<BatchProj<T, S, V, TA> *>(it->second.get());
+  std::vector<nf_step_stats> s(n);
+  std::vector<int> status(n, NF_OK), m(n);
+  std::vector<GridDev> gh(n);
+  std::vector<SceneDev> sd(n);
+  std::vector<double> bn2(n);
+  std::vector<E *> mem(n);
+  for (int f = 0; f < nframes; ++f) {
+    int M = 0;
+    for (int i = 0; i < n; ++i) {
+      m[i] = 0;
+      if (status[i] == NF_E_DIVERGED) continue;
+      const int rc = eps[i]->substeps_now(&m[i]);
+      if (rc != NF_OK) {
+        status[i] = rc;
+        m[i] = 0;
+      }
+      M = std::max(M, m[i]);
+    }
+    for (int sub = 0; sub < M; ++sub) {
+      for (int i = 0; i < n; ++i) {
+        mem[i] = nullptr;
+        if (sub >= m[i]) continue;
+        CKS(eps[i]->batch_before(sub, m[i], &gh[i], &sd[i], &bn2[i]));
+        if (!std::isfinite(bn2[i])) {  // this member diverged: out of the batch
+          status[i] = NF_E_DIVERGED;
+          m[i] = 0;
+          continue;
+        }
+        mem[i] = eps[i];
+      }
+      const SolveStats ss = bp->solve(mem.data(), bn2.data());
+      for (int i = 0; i < n; ++i) {
+        if (!mem[i]) continue;
+        eps[i]->acc(&s[i], ss);
+        s[i].steps += 1;
+        if (ss.status != NF_OK && status[i] == NF_OK) status[i] = ss.status;
+        CKS(eps[i]->batch_after(gh[i], sd[i]));
+      }
+    }
+    for (int i = 0; i < n; ++i)
+      if (status[i] != NF_E_DIVERGED) eps[i]->batch_end_frame();
+  }
+  int worst = NF_OK;
+  for (int i = 0; i < n; ++i) {
+    if (st) st[i] = s[i];
+    if (stat) stat[i] = status[i];
+    if (status[i] != NF_OK && worst == NF_OK) worst = status[i];
+    if (status[i] == NF_E_DIVERGED) worst = NF_E_DIVERGED;
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "batched step");
+  return worst;
+}
+
+int step_batch(Ctx *ctx, BatchCache &cache, EpisodeBase *const *eps, int n, int nframes,
+               nf_step_stats *st, int *status) {
+  switch (ctx->cfg.precision) {
+    case NF_PREC_FP64:
+      return step_batch_t<double, double, double, double>(ctx, cache, eps, n, nframes, st,
+                                                          status);
+    case NF_PREC_FP32:
+      return step_batch_t<float, float, float, float>(ctx, cache, eps, n, nframes, st, status);
+    default:
+      return step_batch_t<float, double, float, __nv_bfloat16>(ctx, cache, eps, n, nframes, st,
+                                                               status);
+  }
 }
 
 template <class T, class S, class V, class TA>

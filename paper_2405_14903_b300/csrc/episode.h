@@ -2,6 +2,9 @@
 // rollout tape. Precision-specific implementations live in episode.cu.
 #pragma once
 
+#include <array>
+#include <map>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -36,6 +39,8 @@ class EpisodeBase {
   // Resumable state (velocity, frame clock, theta) to / from host bytes.
   virtual int export_state(void *buf, size_t *bytes) = 0;
   virtual int import_state(const void *buf, size_t bytes) = 0;
+  // Can these n episodes (this one among them) be stepped as one batch?
+  virtual bool batchable_with(EpisodeBase *const *eps, int n) const = 0;
 };
 
 // Extruded polar-Bezier scenes: the device table of scene.cuh built from
@@ -51,6 +56,21 @@ struct BzInfo {
 };
 std::string bz_check(const nf_scene &s);
 void bz_build(const nf_scene &s, const std::vector<double> &src, BzInfo &out);
+
+// Stacked projections of a batch of same-size episodes (nf_step_batch),
+// cached per context by (nx, ny, nz, members).
+struct BatchBase {
+  virtual ~BatchBase() {}
+  virtual size_t bytes() const = 0;
+};
+using BatchCache = std::map<std::array<int, 4>, std::unique_ptr<BatchBase>>;
+
+// Advances n episodes of one context (same cell counts) by nframes frames
+// each; every substep's projections are solved as one stacked system.
+// st and status (n entries each, may be null) receive each member's
+// statistics and status.
+int step_batch(Ctx *ctx, BatchCache &cache, EpisodeBase *const *eps, int n, int nframes,
+               nf_step_stats *st, int *status);
 
 // Creates an episode in the precision of ctx->cfg. Returns a status.
 int create_episode(Ctx *ctx, const nf_grid *g, const nf_scene *s,

@@ -2325,6 +2325,20 @@ void launch_residual_outer(const Launch &L, const LevelView<T> &lv, const S *b,
   ++*L.counter;
 }
 template <class S, class V>
+__global__ void __launch_bounds__(kBlock, 8) k_scale_rhs(int64_t n, const S *b, V *rin,
+                                                         double scale) {
+  pdl_wait();
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x)
+    rin[c] = (V)((double)b[c] * scale);
+}
+template <class S, class V>
+void launch_scale_rhs(const Launch &L, int64_t n, const S *b, V *rin, double scale) {
+  ProfScope _ps(L, NF_K_RESIDUAL64);
+  launch_pdl(k_scale_rhs<S, V>, gs_blocks(n), kBlock, 0, L.s, n, b, rin, scale);
+  ++*L.counter;
+}
+template <class S, class V>
 void launch_axpy_outer(const Launch &L, int64_t n, S *x, const V *e, double inv) {
   ProfScope _ps(L, NF_K_AXPY64);
   launch_pdl(k_axpy_outer<S, V>, gs_blocks(n), kBlock, 0, L.s, n, x, e, inv);
@@ -2692,6 +2706,9 @@ template void launch_mg_coarsen<double, double>(const Launch &, const LevelView<
 template void launch_residual_outer<double, float, float>(const Launch &, const LevelView<float> &, const double *, const double *, float *, double, int, bool, const RedScratch &, double *);
 template void launch_residual_outer<float, float, float>(const Launch &, const LevelView<float> &, const float *, const float *, float *, double, int, bool, const RedScratch &, double *);
 template void launch_residual_outer<double, double, double>(const Launch &, const LevelView<double> &, const double *, const double *, double *, double, int, bool, const RedScratch &, double *);
+template void launch_scale_rhs<double, float>(const Launch &, int64_t, const double *, float *, double);
+template void launch_scale_rhs<float, float>(const Launch &, int64_t, const float *, float *, double);
+template void launch_scale_rhs<double, double>(const Launch &, int64_t, const double *, double *, double);
 template void launch_axpy_outer<double, float>(const Launch &, int64_t, double *, const float *, double);
 template void launch_axpy_outer<float, float>(const Launch &, int64_t, float *, const float *, double);
 template void launch_axpy_outer<double, double>(const Launch &, int64_t, double *, const double *, double);

@@ -319,8 +319,10 @@ __device__ __forceinline__ double band_fraction(const GridDev &g,
 // ------------------------------------------------------------- advect -----
 // Positions are carried as (integer lattice base, small fractional offset)
 // so that the interpolation weights keep full precision at every grid size.
+// r = dt / dx is formed on the host (an FP64 division per thread occupied
+// the FP64 pipe, 1/64 of the FP32 rate here, for 45 % of the kernel).
 template <class T>
-__global__ void k_advect(GridDev g, Fields<T> u, FieldsMut<T> out, int order) {
+__global__ void k_advect(GridDev g, Fields<T> u, FieldsMut<T> out, int order, T rdt) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int d;
   int64_t f;
@@ -328,7 +330,7 @@ __global__ void k_advect(GridDev g, Fields<T> u, FieldsMut<T> out, int order) {
   int i, j, k;
   g.face_ijk(d, f, i, j, k);
   typedef T R;
-  const R r = R(g.dt / g.dx);
+  const R r = rdt;
   R v0[3];
 #pragma unroll
   for (int e = 0; e < 3; ++e)
@@ -361,7 +363,7 @@ __global__ void k_advect(GridDev g, Fields<T> u, FieldsMut<T> out, int order) {
 // summation order (not the set of terms) scheduling dependent.
 template <class T>
 __global__ void k_advect_adjoint(GridDev g, Fields<T> u, Fields<T> gut,
-                                 FieldsMut<T> gu, int order) {
+                                 FieldsMut<T> gu, int order, T rdt) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int d;
   int64_t f;
@@ -371,7 +373,7 @@ __global__ void k_advect_adjoint(GridDev g, Fields<T> u, Fields<T> gut,
   int i, j, k;
   g.face_ijk(d, f, i, j, k);
   typedef T R;
-  const R r = R(g.dt / g.dx);
+  const R r = rdt;
   Interp<R> st;
   R v0[3], v1[3], dm[3], db[3];
 #pragma unroll
@@ -573,12 +575,13 @@ __global__ void k_rhs(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
         const int64_t fx = g.face(0, I[side], j, k), fy = g.face(1, i, J[side], k),
                       fz = g.face(2, i, j, K[side]);
         const T ax = alpha.x[fx], ay = alpha.y[fy], az = alpha.z[fz];
-        acc += sg * (double)(ax * uh.x[fx] +
-                             (T(1) - ax) * face_us<T>(g, s, 0, I[side], j, k));
-        acc += sg * (double)(ay * uh.y[fy] +
-                             (T(1) - ay) * face_us<T>(g, s, 1, i, J[side], k));
-        acc += sg * (double)(az * uh.z[fz] +
-                             (T(1) - az) * face_us<T>(g, s, 2, i, j, K[side]));
+        // the solid velocity only where it has weight (fluid faces skip the scene)
+        const T usx = ax < T(1) ? face_us<T>(g, s, 0, I[side], j, k) : T(0);
+        const T usy = ay < T(1) ? face_us<T>(g, s, 1, i, J[side], k) : T(0);
+        const T usz = az < T(1) ? face_us<T>(g, s, 2, i, j, K[side]) : T(0);
+        acc += sg * (double)(ax * uh.x[fx] + (T(1) - ax) * usx);
+        acc += sg * (double)(ay * uh.y[fy] + (T(1) - ay) * usy);
+        acc += sg * (double)(az * uh.z[fz] + (T(1) - az) * usz);
       }
       acc *= inv_c;
     }
@@ -593,7 +596,7 @@ __global__ void k_rhs(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
 // U = alpha (U^ - c G P) + (1 - alpha) U_s, with ghost P = 0 outside.
 template <class T, class S>
 __global__ void k_update(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
-                         const S *P, FieldsMut<T> u) {
+                         const S *P, FieldsMut<T> u, T cT) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int d;
   int64_t f;
@@ -604,9 +607,11 @@ __global__ void k_update(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
   face_cells(g, d, i, j, k, cL, cR);
   const S pR = cR >= 0 ? P[cR] : S(0);
   const S pL = cL >= 0 ? P[cL] : S(0);
-  const T gp = T(g.c) * (T)(pR - pL);
+  const T gp = cT * (T)(pR - pL);
   const T a = comp(alpha, d)[f];
-  comp(u, d)[f] = a * (comp(uh, d)[f] - gp) + (T(1) - a) * face_us<T>(g, s, d, i, j, k);
+  // the solid velocity only where it has weight (fluid faces skip the scene)
+  const T us = a < T(1) ? face_us<T>(g, s, d, i, j, k) : T(0);
+  comp(u, d)[f] = a * (comp(uh, d)[f] - gp) + (T(1) - a) * us;
 }
 
 // -------------------------------------------------------------- losses ----
@@ -903,7 +908,7 @@ void launch_advect(const Launch &L, const GridDev &g, Fields<T> u,
                    FieldsMut<T> out, int order) {
   const int64_t n = g.nface(0) + g.nface(1) + g.nface(2);
   ProfScope _ps(L, NF_K_ADVECT);
-  k_advect<T><<<nblocks(n), kBlock, 0, L.s>>>(g, u, out, order);
+  k_advect<T><<<nblocks(n), kBlock, 0, L.s>>>(g, u, out, order, (T)(g.dt / g.dx));
   ++*L.counter;
 }
 
@@ -915,7 +920,7 @@ void launch_advect_adjoint(const Launch &L, const GridDev &g, Fields<T> u,
   cudaMemsetAsync(gu.y, 0, g.nface(1) * sizeof(T), L.s);
   cudaMemsetAsync(gu.z, 0, g.nface(2) * sizeof(T), L.s);
   ProfScope _ps(L, NF_K_ADJ_ADVECT);
-  k_advect_adjoint<T><<<nblocks(n), kBlock, 0, L.s>>>(g, u, gut, gu, order);
+  k_advect_adjoint<T><<<nblocks(n), kBlock, 0, L.s>>>(g, u, gut, gu, order, (T)(g.dt / g.dx));
   ++*L.counter;
 }
 
@@ -947,7 +952,7 @@ void launch_update(const Launch &L, const GridDev &g, const SceneDev &s,
                    Fields<T> alpha, Fields<T> uh, const S *P, FieldsMut<T> u) {
   const int64_t n = g.nface(0) + g.nface(1) + g.nface(2);
   ProfScope _ps(L, NF_K_UPDATE);
-  k_update<T, S><<<nblocks(n), kBlock, 0, L.s>>>(g, s, alpha, uh, P, u);
+  k_update<T, S><<<nblocks(n), kBlock, 0, L.s>>>(g, s, alpha, uh, P, u, (T)g.c);
   ++*L.counter;
 }
 

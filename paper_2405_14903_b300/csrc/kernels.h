@@ -99,6 +99,10 @@ void launch_residual_outer(const Launch &L, const LevelView<T> &lv,
 // x += inv * e (V -> S); inv undoes the scale of the inner system.
 template <class S, class V>
 void launch_axpy_outer(const Launch &L, int64_t n, S *x, const V *e, double inv);
+// rin = scale * b (S -> V): the residual of the zero start, b - A 0 = b,
+// rounded as the residual kernel rounds its output.
+template <class S, class V>
+void launch_scale_rhs(const Launch &L, int64_t n, const S *b, V *rin, double scale);
 
 // d = z, <r, z>, <r, r>; stop when <r, r> <= st->tol^2 <r0, r0>.
 template <class V>

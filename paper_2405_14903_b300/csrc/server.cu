@@ -36,6 +36,7 @@ struct Job {
 
 struct EpisodeRec {
   int slot = -1;           // -1 until admitted
+  int nx = 0, ny = 0, nz = 0;  // cell counts (batching: same-size members)
   int64_t id = 0;          // episode id inside the slot's nf_ctx
   bool created = false;
   bool failed = false;
@@ -66,6 +67,12 @@ struct nf_server {
   std::mutex mu;
   std::condition_variable done_cv;
   int64_t next_ticket = 1, submitted = 0, completed = 0;
+  int64_t batches = 0, batched_requests = 0;
+  int batch_max = 1;       // most episodes stepped as one batch (1: none)
+  int64_t batch_cells = 64 * 64 * 64;  // only episodes of at most this many cells batch
+  bool batchable(const EpisodeRec &r) const {
+    return batch_max > 1 && (int64_t)r.nx * r.ny * r.nz <= batch_cells;
+  }
   bool stop = false;
   Clock::time_point t0 = Clock::now();
 
@@ -84,12 +91,27 @@ struct nf_server {
     return nf::episode_base_bytes(cfg, g) + (C + 2) * (3 * nf * t + nc * s);
   }
 
-  // The slot with the fewest queued or running requests.
-  int pick_slot() const {
+  // The slot with the fewest queued or running requests; with batching, a
+  // slot that already holds episodes of the same cell counts when it is
+  // within two requests of the least loaded (their steps can then share
+  // launches).
+  int pick_slot(const EpisodeRec &rec) const {
     int best = 0;
     for (int s = 1; s < (int)slots.size(); ++s)
       if (slots[s]->pending < slots[best]->pending) best = s;
-    return best;
+    if (!batchable(rec)) return best;
+    std::vector<int> same(slots.size(), 0);
+    for (const auto &kv : eps) {
+      const EpisodeRec &o = kv.second;
+      if (&o != &rec && o.slot >= 0 && o.nx == rec.nx && o.ny == rec.ny && o.nz == rec.nz)
+        same[o.slot] += 1;
+    }
+    int pick = -1;
+    for (int s = 0; s < (int)slots.size(); ++s)
+      if (same[s] > 0 && slots[s]->pending <= slots[best]->pending + 2 &&
+          (pick < 0 || slots[s]->pending < slots[pick]->pending))
+        pick = s;
+    return pick >= 0 ? pick : best;
   }
 
   void enqueue(int s, Job &&job) {
@@ -101,7 +123,7 @@ struct nf_server {
   bool fits(size_t bytes) const { return budget == 0 || reserved + bytes <= budget; }
 
   void admit(int64_t key, EpisodeRec &rec) {
-    rec.slot = pick_slot();
+    rec.slot = pick_slot(rec);
     rec.reserved = rec.estimate;
     reserved += rec.reserved;
     peak = std::max(peak, reserved);
@@ -143,89 +165,226 @@ struct nf_server {
   }
 
   void work(int s);
+  // Under the lock: queued step requests of the same slot that can run as
+  // one batch with `first` (same cell counts and frames, distinct episodes,
+  // each the oldest queued request of its episode, or the first after the
+  // episode's own queued OPEN, which then runs first: `opens`).
+  void gather_batch(Slot &slot, const Job &first, std::vector<Job> &group,
+                    std::vector<Job> &opens);
+  // Under the lock: bookkeeping of a finished request.
+  void complete(Slot &slot, const Job &job, nf_result &res, int64_t id, bool created,
+                size_t bytes);
 };
+
+void nf_server::gather_batch(Slot &slot, const Job &first_job, std::vector<Job> &group,
+                             std::vector<Job> &opens) {
+  // (group grows below: keep copies, not a reference into it)
+  const int64_t first = first_job.req.episode;
+  const int frames = first_job.req.frames;
+  auto f = eps.find(first);
+  if (f == eps.end() || !batchable(f->second) || !f->second.created || f->second.failed) return;
+  const int nx = f->second.nx, ny = f->second.ny, nz = f->second.nz;
+  std::set<int64_t> seen = {first};
+  std::map<int64_t, size_t> open_at;  // episodes whose only queued job so far is their OPEN
+  std::vector<size_t> take_open, take_step;
+  for (size_t i = 0; i < slot.queue.size() && (int)(group.size() + take_step.size()) < batch_max;
+       ++i) {
+    const Job &q = slot.queue[i];
+    const int64_t key = q.req.episode;
+    if (seen.count(key)) continue;
+    auto e = eps.find(key);
+    const bool same = e != eps.end() && !e->second.failed && e->second.nx == nx &&
+                      e->second.ny == ny && e->second.nz == nz;
+    const auto o = open_at.find(key);
+    if (q.req.kind == NF_REQ_OPEN && same && !e->second.created && o == open_at.end()) {
+      open_at[key] = i;  // its first step may join, the OPEN run just before the batch
+      continue;
+    }
+    const bool step = (q.req.kind == NF_REQ_STEP || q.req.kind == NF_REQ_STEP_ADJOINT) &&
+                      q.req.frames == frames;
+    if (step && same && (e->second.created || o != open_at.end())) {
+      if (o != open_at.end()) take_open.push_back(o->second);
+      take_step.push_back(i);
+    }
+    seen.insert(key);  // later requests of this episode wait for this one
+  }
+  std::vector<size_t> all(take_open);
+  all.insert(all.end(), take_step.begin(), take_step.end());
+  for (size_t i : take_open) opens.push_back(std::move(slot.queue[i]));
+  for (size_t i : take_step) group.push_back(std::move(slot.queue[i]));
+  std::sort(all.begin(), all.end());
+  for (auto it = all.rbegin(); it != all.rend(); ++it)
+    slot.queue.erase(slot.queue.begin() + (std::ptrdiff_t)*it);
+}
+
+void nf_server::complete(Slot &slot, const Job &job, nf_result &res, int64_t id, bool created,
+                         size_t bytes) {
+  slot.pending -= 1;
+  auto it = eps.find(job.req.episode);
+  if (it != eps.end()) {
+    EpisodeRec &rec = it->second;
+    if (job.req.kind == NF_REQ_OPEN) {
+      rec.id = id;
+      rec.created = created;
+      rec.failed = !created;
+      if (rec.failed) {  // nothing stays resident: release the reservation
+        reserved -= std::min(reserved, rec.reserved);
+        rec.reserved = 0;
+      }
+    }
+    if (job.req.kind == NF_REQ_CLOSE) {
+      // memory returns to the budget
+      reserved -= std::min(reserved, rec.reserved);
+      eps.erase(it);
+    } else if (bytes > rec.reserved) {
+      reserved += bytes - rec.reserved;
+      rec.reserved = bytes;
+      peak = std::max(peak, reserved);
+    }
+    admit_waiting();
+  }
+  finish(job.ticket, res);
+}
 
 void nf_server::work(int s) {
   cudaSetDevice(device);
   Slot &slot = *slots[s];
   for (;;) {
-    Job job;
-    int64_t id = 0;
-    bool created = false, failed = false;
+    std::vector<Job> group, opens;
+    std::vector<int64_t> ids;
+    std::vector<char> created, failed;
     {
       std::unique_lock<std::mutex> lk(mu);
       slot.cv.wait(lk, [&] { return stop || !slot.queue.empty(); });
       if (slot.queue.empty()) return;  // stop requested and nothing left
-      job = std::move(slot.queue.front());
+      group.push_back(std::move(slot.queue.front()));
       slot.queue.pop_front();
-      auto it = eps.find(job.req.episode);
-      if (it != eps.end()) {
-        id = it->second.id;
-        created = it->second.created;
-        failed = it->second.failed;
-      }
+      if (group[0].req.kind == NF_REQ_STEP || group[0].req.kind == NF_REQ_STEP_ADJOINT)
+        gather_batch(slot, group[0], group, opens);
     }
-    nf_result res{};
-    res.kind = job.req.kind;
-    res.episode = job.req.episode;
-    res.submit_ms = job.submit_ms;
-    res.start_ms = now_ms();
-    size_t bytes = 0;
-    if (job.req.kind == NF_REQ_OPEN) {
+    // the OPENs of batch members whose episode was not created yet run first
+    // (each request of an episode still runs in its submission order)
+    for (Job &job : opens) {
+      nf_result r{};
+      r.kind = job.req.kind;
+      r.episode = job.req.episode;
+      r.submit_ms = job.submit_ms;
+      r.start_ms = now_ms();
       nf_scene sc = job.req.scene;
       sc.spheres = job.spheres.empty() ? nullptr : job.spheres.data();
       sc.shapes = job.shapes.empty() ? nullptr : job.shapes.data();
-      res.status = nf_episode_create(slot.ctx, &job.req.grid, &sc, &id);
-      created = res.status == NF_OK;
-    } else if (failed || !created) {
-      res.status = NF_E_STATE;
-    } else if (job.req.kind == NF_REQ_STEP || job.req.kind == NF_REQ_STEP_ADJOINT) {
-      res.status = nf_step(slot.ctx, id, job.req.frames, &res.fwd);
-      if (job.req.kind == NF_REQ_STEP_ADJOINT &&
-          (res.status == NF_OK || res.status == NF_E_NOT_CONVERGED)) {
-        auto e = slot.ctx->eps.find(id);
-        const int rc = e == slot.ctx->eps.end()
-                           ? NF_E_STATE
-                           : e->second->loss_backward(job.req.loss_kind, &res.loss,
-                                                      res.g_theta, &res.bwd);
-        if (rc != NF_OK && res.status == NF_OK) res.status = rc;
-      }
-    } else if (job.req.kind == NF_REQ_CLOSE) {
-      res.status = nf_episode_destroy(slot.ctx, id);
-    } else {
-      res.status = NF_E_INVALID;
+      int64_t id = 0;
+      r.status = nf_episode_create(slot.ctx, &job.req.grid, &sc, &id);
+      size_t bytes = 0;
+      if (r.status == NF_OK) nf_episode_bytes(slot.ctx, id, &bytes);
+      nf_synchronize(slot.ctx);
+      r.end_ms = now_ms();
+      r.episode_bytes = bytes;
+      std::lock_guard<std::mutex> lk(mu);
+      complete(slot, job, r, id, r.status == NF_OK, bytes);
     }
-    if (job.req.kind != NF_REQ_CLOSE && created) nf_episode_bytes(slot.ctx, id, &bytes);
-    nf_synchronize(slot.ctx);
-    res.end_ms = now_ms();
-    res.episode_bytes = bytes;
     {
       std::lock_guard<std::mutex> lk(mu);
-      slot.pending -= 1;
-      auto it = eps.find(job.req.episode);
-      if (it != eps.end()) {
-        EpisodeRec &rec = it->second;
-        if (job.req.kind == NF_REQ_OPEN) {
-          rec.id = id;
-          rec.created = created;
-          rec.failed = !created;
-          if (rec.failed) {  // nothing stays resident: release the reservation
-            reserved -= std::min(reserved, rec.reserved);
-            rec.reserved = 0;
-          }
-        }
-        if (job.req.kind == NF_REQ_CLOSE) {
-          // memory returns to the budget
-          reserved -= std::min(reserved, rec.reserved);
-          eps.erase(it);
-        } else if (bytes > rec.reserved) {
-          reserved += bytes - rec.reserved;
-          rec.reserved = bytes;
-          peak = std::max(peak, reserved);
-        }
-        admit_waiting();
+      for (const Job &job : group) {
+        auto it = eps.find(job.req.episode);
+        ids.push_back(it != eps.end() ? it->second.id : 0);
+        created.push_back(it != eps.end() && it->second.created);
+        failed.push_back(it != eps.end() && it->second.failed);
       }
-      finish(job.ticket, res);
+    }
+    const int n = (int)group.size();
+    std::vector<nf_result> res(n);
+    for (int i = 0; i < n; ++i) {
+      res[i].kind = group[i].req.kind;
+      res[i].episode = group[i].req.episode;
+      res[i].submit_ms = group[i].submit_ms;
+      res[i].start_ms = now_ms();
+    }
+    if (n > 1) {
+      // one batch: the members' forward frames with every projection solved
+      // for all of them at once, then each STEP_ADJOINT member's backward.
+      // Members whose episode failed to open are left out.
+      std::vector<int> run;
+      std::vector<int64_t> rid;
+      for (int i = 0; i < n; ++i)
+        if (created[i] && !failed[i]) {
+          run.push_back(i);
+          rid.push_back(ids[i]);
+        }
+      const int m = (int)run.size();
+      std::vector<nf_step_stats> st(n), mst(std::max(m, 1));
+      std::vector<int> stat(n, NF_E_STATE), mstat(std::max(m, 1), NF_E_STATE);
+      int rc = m > 0 ? nf_step_batch(slot.ctx, rid.data(), m, group[0].req.frames, mst.data(),
+                                     mstat.data())
+                     : NF_OK;
+      if (rc == NF_E_INVALID)  // not batchable after all: one at a time
+        for (int k = 0; k < m; ++k) {
+          mstat[k] = nf_step(slot.ctx, rid[k], group[run[k]].req.frames, &mst[k]);
+          rc = NF_OK;
+        }
+      for (int k = 0; k < m; ++k) {
+        stat[run[k]] = rc == NF_E_CUDA || rc == NF_E_OOM ? rc : mstat[k];
+        st[run[k]] = mst[k];
+      }
+      for (int i = 0; i < n; ++i) {
+        res[i].status = stat[i];
+        res[i].fwd = st[i];
+        if (group[i].req.kind == NF_REQ_STEP_ADJOINT &&
+            (res[i].status == NF_OK || res[i].status == NF_E_NOT_CONVERGED)) {
+          auto e = slot.ctx->eps.find(ids[i]);
+          const int rb = e == slot.ctx->eps.end()
+                             ? NF_E_STATE
+                             : e->second->loss_backward(group[i].req.loss_kind, &res[i].loss,
+                                                        res[i].g_theta, &res[i].bwd);
+          if (rb != NF_OK && res[i].status == NF_OK) res[i].status = rb;
+        }
+      }
+    } else {
+      Job &job = group[0];
+      int64_t &id = ids[0];
+      nf_result &r = res[0];
+      if (job.req.kind == NF_REQ_OPEN) {
+        nf_scene sc = job.req.scene;
+        sc.spheres = job.spheres.empty() ? nullptr : job.spheres.data();
+        sc.shapes = job.shapes.empty() ? nullptr : job.shapes.data();
+        r.status = nf_episode_create(slot.ctx, &job.req.grid, &sc, &id);
+        created[0] = r.status == NF_OK;
+      } else if (failed[0] || !created[0]) {
+        r.status = NF_E_STATE;
+      } else if (job.req.kind == NF_REQ_STEP || job.req.kind == NF_REQ_STEP_ADJOINT) {
+        r.status = nf_step(slot.ctx, id, job.req.frames, &r.fwd);
+        if (job.req.kind == NF_REQ_STEP_ADJOINT &&
+            (r.status == NF_OK || r.status == NF_E_NOT_CONVERGED)) {
+          auto e = slot.ctx->eps.find(id);
+          const int rc = e == slot.ctx->eps.end()
+                             ? NF_E_STATE
+                             : e->second->loss_backward(job.req.loss_kind, &r.loss, r.g_theta,
+                                                        &r.bwd);
+          if (rc != NF_OK && r.status == NF_OK) r.status = rc;
+        }
+      } else if (job.req.kind == NF_REQ_CLOSE) {
+        r.status = nf_episode_destroy(slot.ctx, id);
+      } else {
+        r.status = NF_E_INVALID;
+      }
+    }
+    std::vector<size_t> bytes(n, 0);
+    for (int i = 0; i < n; ++i)
+      if (group[i].req.kind != NF_REQ_CLOSE && created[i])
+        nf_episode_bytes(slot.ctx, ids[i], &bytes[i]);
+    nf_synchronize(slot.ctx);
+    const double end = now_ms();
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      if (n > 1) {
+        batches += 1;
+        batched_requests += n;
+      }
+      for (int i = 0; i < n; ++i) {
+        res[i].end_ms = end;
+        res[i].episode_bytes = bytes[i];
+        complete(slot, group[i], res[i], ids[i], created[i] != 0, bytes[i]);
+      }
     }
   }
 }
@@ -299,6 +458,9 @@ extern "C" int nf_server_submit(nf_server *srv, const nf_request *req, int64_t *
     }
     EpisodeRec rec;
     rec.estimate = srv->estimate(req->grid);
+    rec.nx = req->grid.nx;
+    rec.ny = req->grid.ny;
+    rec.nz = req->grid.nz;
     if (srv->budget && rec.estimate > srv->budget) {
       srv->finish(job.ticket, srv->immediate(job, NF_E_OOM));
       return NF_OK;
@@ -361,9 +523,19 @@ extern "C" int nf_server_drain(nf_server *srv, int wait_ms) {
              : NF_E_TIMEOUT;
 }
 
+extern "C" int nf_server_set_batching(nf_server *srv, int max_members, int64_t max_cells) {
+  if (!srv || max_members < 1 || max_members > 64 || max_cells < 0) return NF_E_INVALID;
+  std::lock_guard<std::mutex> lk(srv->mu);
+  srv->batch_max = max_members;
+  srv->batch_cells = max_cells;
+  return NF_OK;
+}
+
 extern "C" int nf_server_stats_get(nf_server *srv, nf_server_stats *out) {
   if (!srv || !out) return NF_E_INVALID;
   std::lock_guard<std::mutex> lk(srv->mu);
+  out->batches = srv->batches;
+  out->batched_requests = srv->batched_requests;
   out->submitted = srv->submitted;
   out->completed = srv->completed;
   out->open_waiting = (int64_t)srv->open_wait.size();

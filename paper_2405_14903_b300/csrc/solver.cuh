@@ -55,6 +55,10 @@ class Solver {
     stall_ = stall && std::strcmp(stall, "1") == 0 ? 1 : 0;
   }
 
+  // At most this many multigrid levels (a batched solve keeps every level
+  // of the stacked grid aligned with its members' own levels).
+  void set_max_levels(int n) { max_levels_ = std::max(1, std::min(n, kMaxLevels)); }
+
   // Allocates the hierarchy. Returns NF_OK or an error status.
   int init(Alloc &A) {
     n_ = g_.ncell();
@@ -74,7 +78,7 @@ class Solver {
     if (mg_) {
       const int mn = std::max(2, cfg_.mg_coarsest);
       while (nx % 2 == 0 && ny % 2 == 0 && nz % 2 == 0 && nx / 2 >= mn &&
-             ny / 2 >= mn && nz / 2 >= mn && (int)levels_.size() < kMaxLevels) {
+             ny / 2 >= mn && nz / 2 >= mn && (int)levels_.size() < max_levels_) {
         nx /= 2;
         ny /= 2;
         nz /= 2;
@@ -218,7 +222,10 @@ class Solver {
   }
 
   // Solve A x = b (x overwritten). bnorm2 is ||b||^2 already on the host.
-  SolveStats solve(const S *b, S *x, double bnorm2) {
+  // The tolerance is relative to tol_norm2 when given (> 0), else to
+  // bnorm2: a batched solve of stacked, decoupled systems stops when
+  // ||r|| <= tol min_e ||b_e||, which bounds every member's own residual.
+  SolveStats solve(const S *b, S *x, double bnorm2, double tol_norm2 = 0.0) {
     SolveStats out;
     Launch L = ctx_->launch();
     cudaMemsetAsync(x, 0, n_ * sizeof(S), L.s);
@@ -236,8 +243,11 @@ class Solver {
     // would otherwise underflow in the V-typed dots
     double scale = unit_scale(std::sqrt(bnorm2));
     es_ = std::max(-900, std::min(900, -std::ilogb(std::sqrt(bnorm2))));
-    double rn2 = residual(b, x, scale);  // r = b - A 0
-    out.rel = std::sqrt(rn2 / bnorm2);
+    const double tn2 = tol_norm2 > 0.0 ? tol_norm2 : bnorm2;
+    // r = b - A 0 = b: the scaled right-hand side, no stencil evaluation
+    launch_scale_rhs<S, V>(L, n_, b, (V *)rin_, scale);
+    double rn2 = bnorm2;
+    out.rel = std::sqrt(rn2 / tn2);
     int total = 0;
     double prev_scale = scale;
     bool can_cont = false;
@@ -270,7 +280,7 @@ class Solver {
       const double pred = std::max(std::sqrt(rr_in) / scale, 1e-7 * rn);
       scale = unit_scale(pred);
       rn2 = residual(b, x, scale);
-      out.rel = std::sqrt(rn2 / bnorm2);
+      out.rel = std::sqrt(rn2 / tn2);
       // the next pass may keep the search direction only while the
       // recurrence residual still tracks the true one (it drifts below it
       // once V rounding stalls the true residual)
@@ -302,6 +312,7 @@ class Solver {
     void *pn = nullptr;  // prolongation normaliser (levels with a coarser one)
   };
   static constexpr int kMaxOuter = 12;
+  int max_levels_ = kMaxLevels;
   static constexpr int kChainCells = 16 * 16 * 16;
   static constexpr int64_t kMidCells = 64 * 64 * 64;
   static constexpr int64_t kClusterCells = 32 * 32 * 32;

@@ -65,7 +65,7 @@ def test_status_strings_and_defaults(lib):
     assert lib.nf_config_default(ctypes.byref(cfg)) == 0
     assert cfg.precision == _lib.PREC["mixed"] and cfg.solver == _lib.SOLVER["mgpcg"]
     assert cfg.checkpoint_every == 10 and abs(cfg.tol - 1e-6) < 1e-18
-    assert cfg.mg_transfer == 1 and cfg.mg_persistent == 0 and cfg.residual_fp64 == 1 and cfg.mg_fused == 0
+    assert cfg.mg_transfer == 1 and cfg.mg_persistent == 0 and cfg.residual_fp64 == 1 and cfg.mg_fused == 0 and cfg.recompute_overlap == 1
     assert cfg.mg_cluster == 0
 
 

@@ -763,3 +763,34 @@ def test_exported_episode_resumes_bit_for_bit(nf, prec):
         with pytest.raises(nf.NFError) as e:
             (c if bad is state else b).import_state(bad)
         assert e.value.status == 1
+
+
+# ------------------------------------------------ overlapped recompute ----
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["chamber_sub", "plate", "sphere_viscous"])
+def test_overlapped_recompute_gives_the_sequential_gradient(nf, prec, name):
+    # the backward pass recomputing the next checkpoint segment on a second
+    # stream (helper thread) while it reverts the current one: the same
+    # kernels on the same data, so the loss is bitwise equal and the
+    # gradient equal to rounding (float-atomic scatter in the advection
+    # adjoint); many segments (checkpoint every 2 steps)
+    cfg, Jo, gtho, info = oracle_rollout(name)
+    out = []
+    for overlap in (False, True):
+        ctx = make_ctx(nf, prec, cfg=cfg, checkpoint_every=2, recompute_overlap=overlap)
+        ep = ctx.episode(cfg["grid"], cfg["scene"])
+        ep.set_velocity(device_u(cfg), project=cfg["project_initial"])
+        fs = ep.step(cfg["steps"])
+        J, gU = ep.loss(cfg["loss"], want_grad=True)
+        gth, gU0, bs = ep.backward(gU)
+        out.append((J, gth, host(gU0), bs))
+        ep.close()
+        ctx.close()
+    (J0, g0, u0, b0), (J1, g1, u1, b1) = out
+    assert J0 == J1
+    assert b1["steps"] == b0["steps"] and b1["solves"] == b0["solves"]
+    tol = 1e-10 if prec == "fp64" else 1e-5
+    assert np.linalg.norm(g1 - g0) <= tol * np.linalg.norm(g0)
+    assert rel(u1, u0) <= tol
+    assert np.linalg.norm(g1 - gtho) <= GRAD_TOL[prec] * np.linalg.norm(gtho)
