@@ -213,7 +213,7 @@ __device__ double corner_area(const double ph[4], double da[4]) {
 }
 
 // ---------------------------------------------------------- rasterise -----
-template <class T>
+template <class T, bool kBz>
 __device__ __forceinline__ double band_fraction(const GridDev &g,
                                                 const SceneDev &s, double x,
                                                 double y, double z);
@@ -224,7 +224,8 @@ __device__ __forceinline__ double band_fraction(const GridDev &g,
 // (subsamples lie within 0.65 dx of the centre and phi is 1-Lipschitz), so
 // only the narrow band evaluates the 64 samples (directly in FP64 for FP64
 // fields, with the narrow-band evaluator of scene.cuh for FP32 fields).
-template <class T, bool kCorner>
+// kBz: the scene may be polar-Bezier shapes (else that case is compiled out).
+template <class T, bool kCorner, bool kBz>
 __global__ void __launch_bounds__(kBlock, 4)
 k_rasterize(GridDev g, SceneDev s, FieldsMut<T> alpha) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -239,7 +240,7 @@ k_rasterize(GridDev g, SceneDev s, FieldsMut<T> alpha) {
     return;
   }
   const float hf = (float)g.dx;
-  const float pc = scene_phi<float>(s, (i + (d == 0 ? 0.f : 0.5f)) * hf,
+  const float pc = scene_phi<float, kBz>(s, (i + (d == 0 ? 0.f : 0.5f)) * hf,
                                     (j + (d == 1 ? 0.f : 0.5f)) * hf,
                                     (k + (d == 2 ? 0.f : 0.5f)) * hf);
   // corners lie within 0.71 dx and subsamples within 0.65 dx of the centre
@@ -257,19 +258,19 @@ k_rasterize(GridDev g, SceneDev s, FieldsMut<T> alpha) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       face_corner(d, i, j, k, c, g.dx, p);
-      ph[c] = scene_phi<double>(s, p[0], p[1], p[2]);
+      ph[c] = scene_phi<double, kBz>(s, p[0], p[1], p[2]);
     }
     a[f] = T(corner_area(ph, da));
     return;
   }
   double X, Y, Z;
   face_pos(d, i, j, k, X, Y, Z);
-  a[f] = T(band_fraction<T>(g, s, X * g.dx, Y * g.dx, Z * g.dx));
+  a[f] = T(band_fraction<T, kBz>(g, s, X * g.dx, Y * g.dx, Z * g.dx));
 }
 
 // alpha of a band face: the 64-sample ramp average. FP64 fields evaluate
 // phi directly in FP64; FP32 fields use the narrow-band evaluator.
-template <class T>
+template <class T, bool kBz>
 __device__ __forceinline__ double band_fraction(const GridDev &g,
                                                 const SceneDev &s, double x,
                                                 double y, double z) {
@@ -307,7 +308,7 @@ __device__ __forceinline__ double band_fraction(const GridDev &g,
       const double yy = y + ((b + 0.5) * 0.25 - 0.5) * g.dx;
       for (int q = 0; q < 4; ++q) {
         const double xx = x + ((q + 0.5) * 0.25 - 0.5) * g.dx;
-        const double hv = 0.5 + scene_phi<double>(s, xx, yy, zz) * inv_w;
+        const double hv = 0.5 + scene_phi<double, kBz>(s, xx, yy, zz) * inv_w;
         acc += fmin(fmax(hv, 0.0), 1.0);
       }
     }
@@ -319,6 +320,30 @@ __device__ __forceinline__ double band_fraction(const GridDev &g,
 // ------------------------------------------------------------- advect -----
 // Positions are carried as (integer lattice base, small fractional offset)
 // so that the interpolation weights keep full precision at every grid size.
+// Component e of the velocity at the centre of face (d; i, j, k): the
+// clamped trilinear interpolant there, whose weights are 1/2 or 1 (a face
+// of component d sits half a cell off component e's lattice along d and e):
+// the face's own value for e = d, else the mean of the two e-faces across
+// it along e, averaged over the two cells beside it along d (one at the
+// box walls, where the interpolant clamps).
+template <class T>
+__device__ __forceinline__ T face_velocity(const GridDev &g, const T *U, int e, int d, int i,
+                                           int j, int k) {
+  const int nx = g.nx + (e == 0), ny = g.ny + (e == 1);
+  if (e == d) return U[((int64_t)k * ny + j) * nx + i];
+  const int nd = d == 0 ? g.nx : (d == 1 ? g.ny : g.nz);  // e's points along d
+  const int id = d == 0 ? i : (d == 1 ? j : k);
+  const int64_t se = e == 0 ? 1 : (e == 1 ? (int64_t)nx : (int64_t)nx * ny);
+  const int64_t sd = d == 0 ? 1 : (d == 1 ? (int64_t)nx : (int64_t)nx * ny);
+  // lattice point (i, j, k) of component e with the d index moved to id - 1
+  const int64_t base = ((int64_t)k * ny + j) * nx + i - sd;
+  const int lo = id > 0 ? -1 : 0;            // d neighbours, clamped at the walls
+  const int hi = id < nd ? 0 : -1;
+  const T a = T(0.5) * (U[base + (lo + 1) * sd] + U[base + (lo + 1) * sd + se]);
+  const T b = T(0.5) * (U[base + (hi + 1) * sd] + U[base + (hi + 1) * sd + se]);
+  return T(0.5) * (a + b);
+}
+
 // r = dt / dx is formed on the host (an FP64 division per thread occupied
 // the FP64 pipe, 1/64 of the FP32 rate here, for 45 % of the kernel).
 template <class T>
@@ -333,9 +358,7 @@ __global__ void k_advect(GridDev g, Fields<T> u, FieldsMut<T> out, int order, T 
   const R r = rdt;
   R v0[3];
 #pragma unroll
-  for (int e = 0; e < 3; ++e)
-    v0[e] = trilerp<T, R, false>(g, comp(u, e), e, i, j, k, R(lat_off(d, e, 0)),
-                                 R(lat_off(d, e, 1)), R(lat_off(d, e, 2)));
+  for (int e = 0; e < 3; ++e) v0[e] = face_velocity<T>(g, comp(u, e), e, d, i, j, k);
   R db[3];
   if (order == 1) {
 #pragma unroll
@@ -446,7 +469,7 @@ __global__ void k_advect_adjoint(GridDev g, Fields<T> u, Fields<T> gut,
 // Solid velocity of a component-d face (0 on the box boundary but for an
 // inflow patch's faces, which carry the inflow speed), evaluated in
 // the field precision T (positions formed in T: no FP64 for FP32 fields).
-template <class T>
+template <class T, bool kBz>
 __device__ __forceinline__ T face_us(const GridDev &g, const SceneDev &s,
                                      int d, int i, int j, int k) {
   // box walls: at rest, except the faces of an inflow patch
@@ -456,7 +479,7 @@ __device__ __forceinline__ T face_us(const GridDev &g, const SceneDev &s,
   const T X = (T(i) + (d == 0 ? T(0) : T(0.5))) * h;
   const T Y = (T(j) + (d == 1 ? T(0) : T(0.5))) * h;
   const T Z = (T(k) + (d == 2 ? T(0) : T(0.5))) * h;
-  return scene_us<T>(s, d, X, Y, Z);
+  return scene_us<T, kBz>(s, d, X, Y, Z);
 }
 
 // Sum of the six face fractions of cell (i, j, k).
@@ -556,7 +579,7 @@ k_viscosity(GridDev g, Fields<T> in, FieldsMut<T> out, T kv) {
 // G^T v at a cell is v(low face) - v(high face), summed over the axes. The
 // division by c = dt / (rho dx) lets the solver use the unit-scale operator
 // G^T S G, whose coefficients do not depend on the step length.
-template <class T, class S>
+template <class T, class S, bool kBz>
 __global__ void k_rhs(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
                       S *b, RedScratch rs, double *bnorm2) {
   const double inv_c = 1.0 / g.c;
@@ -576,9 +599,9 @@ __global__ void k_rhs(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
                       fz = g.face(2, i, j, K[side]);
         const T ax = alpha.x[fx], ay = alpha.y[fy], az = alpha.z[fz];
         // the solid velocity only where it has weight (fluid faces skip the scene)
-        const T usx = ax < T(1) ? face_us<T>(g, s, 0, I[side], j, k) : T(0);
-        const T usy = ay < T(1) ? face_us<T>(g, s, 1, i, J[side], k) : T(0);
-        const T usz = az < T(1) ? face_us<T>(g, s, 2, i, j, K[side]) : T(0);
+        const T usx = ax < T(1) ? face_us<T, kBz>(g, s, 0, I[side], j, k) : T(0);
+        const T usy = ay < T(1) ? face_us<T, kBz>(g, s, 1, i, J[side], k) : T(0);
+        const T usz = az < T(1) ? face_us<T, kBz>(g, s, 2, i, j, K[side]) : T(0);
         acc += sg * (double)(ax * uh.x[fx] + (T(1) - ax) * usx);
         acc += sg * (double)(ay * uh.y[fy] + (T(1) - ay) * usy);
         acc += sg * (double)(az * uh.z[fz] + (T(1) - az) * usz);
@@ -594,7 +617,7 @@ __global__ void k_rhs(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
 
 // ------------------------------------------------------------- update -----
 // U = alpha (U^ - c G P) + (1 - alpha) U_s, with ghost P = 0 outside.
-template <class T, class S>
+template <class T, class S, bool kBz>
 __global__ void k_update(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
                          const S *P, FieldsMut<T> u, T cT) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -610,7 +633,7 @@ __global__ void k_update(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
   const T gp = cT * (T)(pR - pL);
   const T a = comp(alpha, d)[f];
   // the solid velocity only where it has weight (fluid faces skip the scene)
-  const T us = a < T(1) ? face_us<T>(g, s, d, i, j, k) : T(0);
+  const T us = a < T(1) ? face_us<T, kBz>(g, s, d, i, j, k) : T(0);
   comp(u, d)[f] = a * (comp(uh, d)[f] - gp) + (T(1) - a) * us;
 }
 
@@ -661,7 +684,7 @@ __global__ void k_loss_outflow(GridDev g, Fields<T> u, FieldsMut<T> gu,
 // fields; initialised once per face by one lane) or directly in FP64; out
 // receives this lane's part of sum_samples (4 / dx) d phi / d theta, to be
 // summed over the warp.
-template <class T>
+template <class T, bool kBz>
 __device__ __forceinline__ void band_dalpha_lanes(const GridDev &g, const SceneDev &s,
                                                   const LocalSdf *L, double x, double y,
                                                   double z, int lane, T *out) {
@@ -693,10 +716,10 @@ __device__ __forceinline__ void band_dalpha_lanes(const GridDev &g, const SceneD
     const double xx = x + (((sm & 3) + 0.5) * 0.25 - 0.5) * g.dx;
     const double yy = y + ((((sm >> 2) & 3) + 0.5) * 0.25 - 0.5) * g.dx;
     const double zz = z + (((sm >> 4) + 0.5) * 0.25 - 0.5) * g.dx;
-    const double hv = 0.5 + scene_phi<double>(s, xx, yy, zz) * inv_w;
+    const double hv = 0.5 + scene_phi<double, kBz>(s, xx, yy, zz) * inv_w;
     if (hv > 0.0 && hv < 1.0) {
       double tmp[kMaxParams];
-      scene_dphi(s, xx, yy, zz, tmp);
+      scene_dphi<kBz>(s, xx, yy, zz, tmp);
 #pragma unroll
       for (int p = 0; p < kMaxParams; ++p)
         if (p < s.K) out[p] += (T)(inv_w * tmp[p]);
@@ -737,7 +760,7 @@ __global__ void k_adj_gp(GridDev g, Fields<T> alpha, Fields<T> gu, S *gp,
 //   gU^  = alpha (gU + Gy),   gU_s = (1 - alpha)(gU + Gy)
 // and the parameter gradient  sum_f gS_f dalpha_f/dtheta + gU_s,f du_s,f/dtheta
 // (Sec. 2.3.3), with dalpha/dtheta from the subsample ramps (narrow band).
-template <class T, class S, bool kCorner>
+template <class T, class S, bool kCorner, bool kBz>
 __global__ void k_adj_face(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
                            const S *P, const S *y, Fields<T> gu,
                            FieldsMut<T> guh, RedScratch rs, double *gtheta) {
@@ -785,13 +808,13 @@ __global__ void k_adj_face(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
       if (gUs != T(0) && s.kind != NF_SCENE_SPHERES) {
         if (sizeof(T) == 4) {
           float tmp[kMaxParams];
-          scene_dus_f(s, d, (float)X, (float)Y, (float)Z, tmp);
+          scene_dus_f<kBz>(s, d, (float)X, (float)Y, (float)Z, tmp);
 #pragma unroll
           for (int q = 0; q < kMaxParams; ++q)
             if (q < s.K) acc[q] += gUs * (T)tmp[q];
         } else {
           double tmp[kMaxParams];
-          scene_dus(s, d, (double)X, (double)Y, (double)Z, tmp);
+          scene_dus<kBz>(s, d, (double)X, (double)Y, (double)Z, tmp);
 #pragma unroll
           for (int q = 0; q < kMaxParams; ++q)
             if (q < s.K) acc[q] += gUs * (T)tmp[q];
@@ -799,11 +822,11 @@ __global__ void k_adj_face(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
       }
       // fraction term: d alpha / d theta vanishes off the narrow band (the
       // rasteriser's own test)
-      const float pc = scene_phi<float>(s, (float)X, (float)Y, (float)Z);
+      const float pc = scene_phi<float, kBz>(s, (float)X, (float)Y, (float)Z);
       if (pc > margin || pc < -margin) break;
       const T GP = (T)((cR >= 0 ? P[cR] : S(0)) - (cL >= 0 ? P[cL] : S(0)));
       const T Uh = comp(uh, d)[f];
-      const T us = face_us<T>(g, s, d, i, j, k);
+      const T us = face_us<T, kBz>(g, s, d, i, j, k);
       gS = gU * (Uh - cT * GP - us) + Gy * (Uh - us) - cT * Gy * GP;
       if (gS == T(0)) break;
       if (kCorner) {
@@ -813,14 +836,14 @@ __global__ void k_adj_face(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           face_corner(d, i, j, k, c, g.dx, p[c]);
-          ph[c] = scene_phi<double>(s, p[c][0], p[c][1], p[c][2]);
+          ph[c] = scene_phi<double, kBz>(s, p[c][0], p[c][1], p[c][2]);
         }
         corner_area(ph, da);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           if (da[c] == 0.0) continue;
           double tmp[kMaxParams];
-          scene_dphi(s, p[c][0], p[c][1], p[c][2], tmp);
+          scene_dphi<kBz>(s, p[c][0], p[c][1], p[c][2], tmp);
 #pragma unroll
           for (int q = 0; q < kMaxParams; ++q)
             if (q < s.K) acc[q] += gS * (T)(da[c] * tmp[q]);
@@ -844,7 +867,7 @@ __global__ void k_adj_face(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
       if (sizeof(T) == 4 && lane == 0) L->init(s, bx, by, bz, g.dx);
       __syncwarp();
       T part[kMaxParams];
-      band_dalpha_lanes<T>(g, s, L, bx, by, bz, lane, part);
+      band_dalpha_lanes<T, kBz>(g, s, L, bx, by, bz, lane, part);
 #pragma unroll
       for (int q = 0; q < kMaxParams; ++q) {
         T v = part[q];
@@ -896,10 +919,15 @@ void launch_rasterize(const Launch &L, const GridDev &g, const SceneDev &s,
                       FieldsMut<T> alpha) {
   const int64_t n = g.nface(0) + g.nface(1) + g.nface(2);
   ProfScope _ps(L, NF_K_RASTERIZE);
-  if (g.frac == NF_FRACTIONS_CORNER)
-    k_rasterize<T, true><<<nblocks(n), kBlock, 0, L.s>>>(g, s, alpha);
+  const bool corner = g.frac == NF_FRACTIONS_CORNER, bz = s.kind == NF_SCENE_EXTRUDED;
+  if (corner && bz)
+    k_rasterize<T, true, true><<<nblocks(n), kBlock, 0, L.s>>>(g, s, alpha);
+  else if (corner)
+    k_rasterize<T, true, false><<<nblocks(n), kBlock, 0, L.s>>>(g, s, alpha);
+  else if (bz)
+    k_rasterize<T, false, true><<<nblocks(n), kBlock, 0, L.s>>>(g, s, alpha);
   else
-    k_rasterize<T, false><<<nblocks(n), kBlock, 0, L.s>>>(g, s, alpha);
+    k_rasterize<T, false, false><<<nblocks(n), kBlock, 0, L.s>>>(g, s, alpha);
   ++*L.counter;
 }
 
@@ -943,7 +971,10 @@ void launch_rhs(const Launch &L, const GridDev &g, const SceneDev &s,
                 Fields<T> alpha, Fields<T> uh, S *b, const RedScratch &rs,
                 double *bnorm2) {
   ProfScope _ps(L, NF_K_RHS);
-  k_rhs<T, S><<<kRedBlocks, kBlock, 0, L.s>>>(g, s, alpha, uh, b, rs, bnorm2);
+  if (s.kind == NF_SCENE_EXTRUDED)
+    k_rhs<T, S, true><<<kRedBlocks, kBlock, 0, L.s>>>(g, s, alpha, uh, b, rs, bnorm2);
+  else
+    k_rhs<T, S, false><<<kRedBlocks, kBlock, 0, L.s>>>(g, s, alpha, uh, b, rs, bnorm2);
   ++*L.counter;
 }
 
@@ -952,7 +983,10 @@ void launch_update(const Launch &L, const GridDev &g, const SceneDev &s,
                    Fields<T> alpha, Fields<T> uh, const S *P, FieldsMut<T> u) {
   const int64_t n = g.nface(0) + g.nface(1) + g.nface(2);
   ProfScope _ps(L, NF_K_UPDATE);
-  k_update<T, S><<<nblocks(n), kBlock, 0, L.s>>>(g, s, alpha, uh, P, u, (T)g.c);
+  if (s.kind == NF_SCENE_EXTRUDED)
+    k_update<T, S, true><<<nblocks(n), kBlock, 0, L.s>>>(g, s, alpha, uh, P, u, (T)g.c);
+  else
+    k_update<T, S, false><<<nblocks(n), kBlock, 0, L.s>>>(g, s, alpha, uh, P, u, (T)g.c);
   ++*L.counter;
 }
 
@@ -982,12 +1016,19 @@ void launch_adj_face(const Launch &L, const GridDev &g, const SceneDev &s,
                      Fields<T> gu, FieldsMut<T> guh, const RedScratch &rs,
                      double *gtheta) {
   ProfScope _ps(L, NF_K_ADJ_FACE);
-  if (g.frac == NF_FRACTIONS_CORNER)
-    k_adj_face<T, S, true><<<kRedBlocks, kBlock, 0, L.s>>>(g, s, alpha, uh, P, y, gu,
-                                                           guh, rs, gtheta);
+  const bool corner = g.frac == NF_FRACTIONS_CORNER, bz = s.kind == NF_SCENE_EXTRUDED;
+  if (corner && bz)
+    k_adj_face<T, S, true, true><<<kRedBlocks, kBlock, 0, L.s>>>(g, s, alpha, uh, P, y, gu,
+                                                                 guh, rs, gtheta);
+  else if (corner)
+    k_adj_face<T, S, true, false><<<kRedBlocks, kBlock, 0, L.s>>>(g, s, alpha, uh, P, y, gu,
+                                                                  guh, rs, gtheta);
+  else if (bz)
+    k_adj_face<T, S, false, true><<<kRedBlocks, kBlock, 0, L.s>>>(g, s, alpha, uh, P, y, gu,
+                                                                  guh, rs, gtheta);
   else
-    k_adj_face<T, S, false><<<kRedBlocks, kBlock, 0, L.s>>>(g, s, alpha, uh, P, y, gu,
-                                                            guh, rs, gtheta);
+    k_adj_face<T, S, false, false><<<kRedBlocks, kBlock, 0, L.s>>>(g, s, alpha, uh, P, y, gu,
+                                                                   guh, rs, gtheta);
   ++*L.counter;
 }
 

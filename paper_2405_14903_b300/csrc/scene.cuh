@@ -376,8 +376,10 @@ __device__ inline double bz_us(const SceneDev &s, int d, double x, double y, dou
   return (s.bz_kdot / s.bz_k) * dir;
 }
 
-// Fluid-positive level set phi(x) of the scene at its time.
-template <class R>
+// Fluid-positive level set phi(x) of the scene at its time. kBz = false
+// compiles the polar-Bezier case out (kernels launched for the other scene
+// kinds then keep their own register budget).
+template <class R, bool kBz = true>
 __device__ __forceinline__ R scene_phi(const SceneDev &s, R x, R y, R z) {
   switch (s.kind) {
     case NF_SCENE_SPHERE: {
@@ -408,7 +410,8 @@ __device__ __forceinline__ R scene_phi(const SceneDev &s, R x, R y, R z) {
                         P<R>(s.ph[1], s.f_ph[1]), P<R>(s.ph[2], s.f_ph[2]));
     }
     case NF_SCENE_EXTRUDED:
-      return R(bz_phi(s, (double)x, (double)y, (double)z, nullptr, nullptr));
+      if constexpr (kBz) return R(bz_phi(s, (double)x, (double)y, (double)z, nullptr, nullptr));
+      return R(1.0e3);
     default:
       return R(1.0e3);
   }
@@ -427,7 +430,7 @@ __device__ __forceinline__ bool chamber_ell_active(const SceneDev &s, R x, R y,
 }
 
 // Component d of the solid velocity at x, in precision R.
-template <class R>
+template <class R, bool kBz = true>
 __device__ __forceinline__ R scene_us(const SceneDev &s, int d, R x, R y,
                                       R z) {
   switch (s.kind) {
@@ -444,13 +447,15 @@ __device__ __forceinline__ R scene_us(const SceneDev &s, int d, R x, R y,
       return R(0);
     }
     case NF_SCENE_EXTRUDED:
-      return R(bz_us(s, d, (double)x, (double)y, (double)z, nullptr));
+      if constexpr (kBz) return R(bz_us(s, d, (double)x, (double)y, (double)z, nullptr));
+      return R(0);
     default:
       return R(0);
   }
 }
 
 // d phi / d theta at x (K values).
+template <bool kBz = true>
 __device__ __forceinline__ void scene_dphi(const SceneDev &s, double x,
                                            double y, double z, double *out) {
   switch (s.kind) {
@@ -478,8 +483,11 @@ __device__ __forceinline__ void scene_dphi(const SceneDev &s, double x,
       return;
     }
     case NF_SCENE_EXTRUDED:
-      bz_dphi(s, x, y, z, out);
-      return;
+      if constexpr (kBz) {
+        bz_dphi(s, x, y, z, out);
+        return;
+      }
+      [[fallthrough]];
     default:
 #pragma unroll
       for (int k = 0; k < kMaxParams; ++k) out[k] = 0.0;
@@ -487,6 +495,7 @@ __device__ __forceinline__ void scene_dphi(const SceneDev &s, double x,
 }
 
 // d u_s,d / d theta at x (K values), FP32 (selector and factors only).
+template <bool kBz = true>
 __device__ __forceinline__ void scene_dus_f(const SceneDev &s, int d, float x,
                                             float y, float z, float *out) {
   switch (s.kind) {
@@ -504,12 +513,14 @@ __device__ __forceinline__ void scene_dus_f(const SceneDev &s, int d, float x,
       for (int k = 0; k < 4; ++k) out[k] = f * s.f_pdomega[k];
       return;
     }
-    case NF_SCENE_EXTRUDED: {
-      double tmp[kMaxParams];
-      bz_us(s, d, (double)x, (double)y, (double)z, tmp);
-      for (int k = 0; k < kMaxParams; ++k) out[k] = (float)tmp[k];
-      return;
-    }
+    case NF_SCENE_EXTRUDED:
+      if constexpr (kBz) {
+        double tmp[kMaxParams];
+        bz_us(s, d, (double)x, (double)y, (double)z, tmp);
+        for (int k = 0; k < kMaxParams; ++k) out[k] = (float)tmp[k];
+        return;
+      }
+      [[fallthrough]];
     default:
 #pragma unroll
       for (int k = 0; k < kMaxParams; ++k) out[k] = 0.f;
@@ -517,6 +528,7 @@ __device__ __forceinline__ void scene_dus_f(const SceneDev &s, int d, float x,
 }
 
 // d u_s,d / d theta at x (K values).
+template <bool kBz = true>
 __device__ __forceinline__ void scene_dus(const SceneDev &s, int d, double x,
                                           double y, double z, double *out) {
   switch (s.kind) {
@@ -535,8 +547,11 @@ __device__ __forceinline__ void scene_dus(const SceneDev &s, int d, double x,
       return;
     }
     case NF_SCENE_EXTRUDED:
-      bz_us(s, d, x, y, z, out);
-      return;
+      if constexpr (kBz) {
+        bz_us(s, d, x, y, z, out);
+        return;
+      }
+      [[fallthrough]];
     default:
 #pragma unroll
       for (int k = 0; k < kMaxParams; ++k) out[k] = 0.0;
