@@ -239,6 +239,7 @@ class Context:
         cfg = _config(precision=precision, solver=solver, device=device, stream=stream, **kw)
         self.precision = precision
         self.device = device
+        self.config = cfg  # the nf_config the context was created with
         self._h = C.c_void_p()
         _check(lib.nf_create(C.byref(self._h), C.byref(cfg)))
         self.field_dtype = torch.float64 if precision == "fp64" else torch.float32

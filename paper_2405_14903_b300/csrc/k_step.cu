@@ -213,107 +213,133 @@ __device__ double corner_area(const double ph[4], double da[4]) {
 }
 
 // ---------------------------------------------------------- rasterise -----
+// alpha of a band face centred at (x, y, z), by the 32 lanes of a warp
+// together: lane l takes subsamples l and l + 32 (x fastest, then y, z),
+// the warp sums them. FP32 fields use the face's narrow-band evaluator L
+// unless it overflowed, FP64 fields evaluate phi directly in FP64. Every lane
+// returns the face's value.
 template <class T, bool kBz>
-__device__ __forceinline__ double band_fraction(const GridDev &g,
-                                                const SceneDev &s, double x,
-                                                double y, double z);
+__device__ __forceinline__ double band_fraction_warp(const GridDev &g, const SceneDev &s,
+                                                     const LocalSdf *L, double x, double y,
+                                                     double z, int lane) {
+  constexpr unsigned kAll = 0xffffffffu;
+  if (sizeof(T) == 4 && !L->overflow) {
+    // saturated samples are counted exactly; only the samples inside the
+    // ramp are summed in FP32
+    const float inv_w = (float)(4.0 / g.dx), h = (float)g.dx;
+    int full = 0;
+    float part = 0.f;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int sm = lane + 32 * half;
+      const float ox = (((sm & 3) + 0.5f) * 0.25f - 0.5f) * h;
+      const float oy = ((((sm >> 2) & 3) + 0.5f) * 0.25f - 0.5f) * h;
+      const float oz = (((sm >> 4) + 0.5f) * 0.25f - 0.5f) * h;
+      const float hv = 0.5f + L->phi(ox, oy, oz) * inv_w;
+      if (hv >= 1.f)
+        ++full;
+      else if (hv > 0.f)
+        part += hv;
+    }
+    full = __reduce_add_sync(kAll, full);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kAll, part, o);
+    return ((double)full + (double)part) * (1.0 / 64.0);
+  }
+  const double inv_w = 4.0 / g.dx;
+  double acc = 0.0;
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    const int sm = lane + 32 * half;
+    const double xx = x + (((sm & 3) + 0.5) * 0.25 - 0.5) * g.dx;
+    const double yy = y + ((((sm >> 2) & 3) + 0.5) * 0.25 - 0.5) * g.dx;
+    const double zz = z + (((sm >> 4) + 0.5) * 0.25 - 0.5) * g.dx;
+    const double hv = 0.5 + scene_phi<double, kBz>(s, xx, yy, zz) * inv_w;
+    acc += fmin(fmax(hv, 0.0), 1.0);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kAll, acc, o);
+  return acc * (1.0 / 64.0);
+}
+
+// Threads per block of the rasteriser: one narrow-band evaluator slot in
+// shared memory per thread.
+constexpr int kRastBlock = 128;
 
 // alpha_f = (1/64) sum over 4x4x4 cell-centred subsamples of the face's
 // dx^3 control volume of H(phi), H = clamp(1/2 + phi / (dx/4), 0, 1).
 // Faces whose centre is farther than 0.8 dx from the interface are saturated
 // (subsamples lie within 0.65 dx of the centre and phi is 1-Lipschitz), so
-// only the narrow band evaluates the 64 samples (directly in FP64 for FP64
-// fields, with the narrow-band evaluator of scene.cuh for FP32 fields).
-// kBz: the scene may be polar-Bezier shapes (else that case is compiled out).
+// only the narrow band evaluates the 64 samples. Each lane classifies its own
+// face and, for a band face, sets up its narrow-band evaluator (the FP64
+// centre terms, all band lanes at once); the band faces of a warp (sparse:
+// one lane per band face would leave the others idle through 64 samples)
+// are then summed one after another by the whole warp. kBz: the scene may
+// be polar-Bezier shapes (else that case is compiled out).
 template <class T, bool kCorner, bool kBz>
-__global__ void __launch_bounds__(kBlock, 4)
+__global__ void __launch_bounds__(kRastBlock, 8)
 k_rasterize(GridDev g, SceneDev s, FieldsMut<T> alpha) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int d;
-  int64_t f;
-  if (!split_face(g, t, d, f)) return;
-  int i, j, k;
-  g.face_ijk(d, f, i, j, k);
-  T *a = comp(alpha, d);
-  if (g.boundary(d, i, j, k)) {
-    a[f] = g.outlet_face(d, i, j, k) ? T(1) : T(0);
-    return;
-  }
-  const float hf = (float)g.dx;
-  const float pc = scene_phi<float, kBz>(s, (i + (d == 0 ? 0.f : 0.5f)) * hf,
-                                    (j + (d == 1 ? 0.f : 0.5f)) * hf,
-                                    (k + (d == 2 ? 0.f : 0.5f)) * hf);
-  // corners lie within 0.71 dx and subsamples within 0.65 dx of the centre
-  const float margin = (kCorner ? 0.75f : 0.8f) * hf;
-  if (pc > margin) {
-    a[f] = T(1);
-    return;
-  }
-  if (pc < -margin) {
-    a[f] = T(0);
-    return;
-  }
-  if (kCorner) {
-    double ph[4], da[4], p[3];
+  const int lane = threadIdx.x & 31;
+  __shared__ LocalSdf sdf[kCorner ? 1 : kRastBlock];
+  bool band = false;
+  double X = 0.0, Y = 0.0, Z = 0.0;
+  T *a = alpha.x;
+  int64_t f = 0;
+  do {
+    int d;
+    if (!split_face(g, t, d, f)) break;
+    int i, j, k;
+    g.face_ijk(d, f, i, j, k);
+    a = comp(alpha, d);
+    if (g.boundary(d, i, j, k)) {
+      a[f] = g.outlet_face(d, i, j, k) ? T(1) : T(0);
+      break;
+    }
+    const float hf = (float)g.dx;
+    const float pc = scene_phi<float, kBz>(s, (i + (d == 0 ? 0.f : 0.5f)) * hf,
+                                           (j + (d == 1 ? 0.f : 0.5f)) * hf,
+                                           (k + (d == 2 ? 0.f : 0.5f)) * hf);
+    // corners lie within 0.71 dx and subsamples within 0.65 dx of the centre
+    const float margin = (kCorner ? 0.75f : 0.8f) * hf;
+    if (pc > margin) {
+      a[f] = T(1);
+      break;
+    }
+    if (pc < -margin) {
+      a[f] = T(0);
+      break;
+    }
+    if (kCorner) {
+      double ph[4], da[4], p[3];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      face_corner(d, i, j, k, c, g.dx, p);
-      ph[c] = scene_phi<double, kBz>(s, p[0], p[1], p[2]);
-    }
-    a[f] = T(corner_area(ph, da));
-    return;
-  }
-  double X, Y, Z;
-  face_pos(d, i, j, k, X, Y, Z);
-  a[f] = T(band_fraction<T, kBz>(g, s, X * g.dx, Y * g.dx, Z * g.dx));
-}
-
-// alpha of a band face: the 64-sample ramp average. FP64 fields evaluate
-// phi directly in FP64; FP32 fields use the narrow-band evaluator.
-template <class T, bool kBz>
-__device__ __forceinline__ double band_fraction(const GridDev &g,
-                                                const SceneDev &s, double x,
-                                                double y, double z) {
-  if (sizeof(T) == 4) {
-    LocalSdf L;
-    L.init(s, x, y, z, g.dx);
-    if (!L.overflow) {
-      // saturated samples are counted exactly; only the few samples inside
-      // the ramp are summed in FP32
-      const float inv_w = (float)(4.0 / g.dx), h = (float)g.dx;
-      int full = 0;
-      float part = 0.f;
       for (int c = 0; c < 4; ++c) {
-        const float oz = ((c + 0.5f) * 0.25f - 0.5f) * h;
-        for (int b = 0; b < 4; ++b) {
-          const float oy = ((b + 0.5f) * 0.25f - 0.5f) * h;
-          for (int q = 0; q < 4; ++q) {
-            const float ox = ((q + 0.5f) * 0.25f - 0.5f) * h;
-            const float hv = 0.5f + L.phi(ox, oy, oz) * inv_w;
-            if (hv >= 1.f)
-              ++full;
-            else if (hv > 0.f)
-              part += hv;
-          }
-        }
+        face_corner(d, i, j, k, c, g.dx, p);
+        ph[c] = scene_phi<double, kBz>(s, p[0], p[1], p[2]);
       }
-      return ((double)full + (double)part) * (1.0 / 64.0);
+      a[f] = T(corner_area(ph, da));
+      break;
     }
+    face_pos(d, i, j, k, X, Y, Z);
+    X *= g.dx;
+    Y *= g.dx;
+    Z *= g.dx;
+    if (sizeof(T) == 4) sdf[threadIdx.x].init(s, X, Y, Z, g.dx);
+    band = true;
+  } while (false);
+  if (kCorner) return;
+  __syncwarp();  // the band lanes' evaluators are visible to the whole warp
+  unsigned todo = __ballot_sync(0xffffffffu, band);
+  while (todo) {
+    const int src = __ffs(todo) - 1;
+    todo &= todo - 1;
+    const double bx = __shfl_sync(0xffffffffu, X, src);
+    const double by = __shfl_sync(0xffffffffu, Y, src);
+    const double bz = __shfl_sync(0xffffffffu, Z, src);
+    const double v = band_fraction_warp<T, kBz>(g, s, &sdf[(threadIdx.x & ~31) + src], bx, by,
+                                                bz, lane);
+    if (lane == src) a[f] = T(v);
   }
-  const double inv_w = 4.0 / g.dx;
-  double acc = 0.0;
-  for (int c = 0; c < 4; ++c) {
-    const double zz = z + ((c + 0.5) * 0.25 - 0.5) * g.dx;
-    for (int b = 0; b < 4; ++b) {
-      const double yy = y + ((b + 0.5) * 0.25 - 0.5) * g.dx;
-      for (int q = 0; q < 4; ++q) {
-        const double xx = x + ((q + 0.5) * 0.25 - 0.5) * g.dx;
-        const double hv = 0.5 + scene_phi<double, kBz>(s, xx, yy, zz) * inv_w;
-        acc += fmin(fmax(hv, 0.0), 1.0);
-      }
-    }
-  }
-  return acc * (1.0 / 64.0);
 }
 
 
@@ -760,10 +786,14 @@ __global__ void k_adj_gp(GridDev g, Fields<T> alpha, Fields<T> gu, S *gp,
 //   gU^  = alpha (gU + Gy),   gU_s = (1 - alpha)(gU + Gy)
 // and the parameter gradient  sum_f gS_f dalpha_f/dtheta + gU_s,f du_s,f/dtheta
 // (Sec. 2.3.3), with dalpha/dtheta from the subsample ramps (narrow band).
+// Threads per block of k_adj_face: one narrow-band evaluator slot in shared
+// memory per thread.
+constexpr int kAdjBlock = 128;
+
 template <class T, class S, bool kCorner, bool kBz>
-__global__ void k_adj_face(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
-                           const S *P, const S *y, Fields<T> gu,
-                           FieldsMut<T> guh, RedScratch rs, double *gtheta) {
+__global__ void __launch_bounds__(kAdjBlock, 4)
+k_adj_face(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh, const S *P, const S *y,
+           Fields<T> gu, FieldsMut<T> guh, RedScratch rs, double *gtheta) {
   // per-thread partial sums in the field precision (each thread adds a few
   // dozen faces), block and grid sums in FP64
   T acc[kMaxParams];
@@ -775,11 +805,13 @@ __global__ void k_adj_face(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  __shared__ LocalSdf sdf[kBlock / 32];
+  __shared__ LocalSdf sdf[kCorner ? 1 : kAdjBlock];
   // Each warp takes 32 consecutive faces at a time: every lane does its own
-  // face's per-face work; then the whole warp evaluates the 64-sample
-  // derivative of each band face of the chunk in turn (band faces are
-  // sparse, so one lane per band face would leave the others idle).
+  // face's per-face work, a band face's lane also the FP64 centre terms of
+  // its narrow-band evaluator (all band lanes at once); then the whole warp
+  // evaluates the 64-sample derivative of each band face of the chunk in
+  // turn (band faces are sparse, so one lane per band face would leave the
+  // others idle).
   for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
     const int64_t t = base + lane;
     bool band = false;
@@ -851,8 +883,10 @@ __global__ void k_adj_face(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
         break;
       }
       face_pos(d, i, j, k, Xd, Yd, Zd);
+      if (sizeof(T) == 4) sdf[threadIdx.x].init(s, Xd * g.dx, Yd * g.dx, Zd * g.dx, g.dx);
       band = true;
     } while (false);
+    __syncwarp();  // the band lanes' evaluators are visible to the whole warp
     unsigned todo = __ballot_sync(0xffffffffu, band);
     while (todo) {
       const int src = __ffs(todo) - 1;
@@ -861,11 +895,7 @@ __global__ void k_adj_face(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
       const double by = __shfl_sync(0xffffffffu, Yd, src) * g.dx;
       const double bz = __shfl_sync(0xffffffffu, Zd, src) * g.dx;
       const T gSb = __shfl_sync(0xffffffffu, gS, src);
-      // the face's FP64 centre evaluation, once, shared through the warp's
-      // slot (FP64 work scales with the lanes that run it)
-      LocalSdf *L = &sdf[threadIdx.x >> 5];
-      if (sizeof(T) == 4 && lane == 0) L->init(s, bx, by, bz, g.dx);
-      __syncwarp();
+      const LocalSdf *L = &sdf[(threadIdx.x & ~31) + src];
       T part[kMaxParams];
       band_dalpha_lanes<T, kBz>(g, s, L, bx, by, bz, lane, part);
 #pragma unroll
@@ -875,8 +905,8 @@ __global__ void k_adj_face(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0 && q < s.K) acc[q] += gSb * (v * T(1.0 / 64.0));
       }
-      __syncwarp();  // the slot is rewritten for the next band face
     }
+    __syncwarp();  // the slots are rewritten for the next chunk
   }
   double dacc[kMaxParams];
 #pragma unroll
@@ -920,14 +950,15 @@ void launch_rasterize(const Launch &L, const GridDev &g, const SceneDev &s,
   const int64_t n = g.nface(0) + g.nface(1) + g.nface(2);
   ProfScope _ps(L, NF_K_RASTERIZE);
   const bool corner = g.frac == NF_FRACTIONS_CORNER, bz = s.kind == NF_SCENE_EXTRUDED;
+  const unsigned nb = nblocks(n, kRastBlock);
   if (corner && bz)
-    k_rasterize<T, true, true><<<nblocks(n), kBlock, 0, L.s>>>(g, s, alpha);
+    k_rasterize<T, true, true><<<nb, kRastBlock, 0, L.s>>>(g, s, alpha);
   else if (corner)
-    k_rasterize<T, true, false><<<nblocks(n), kBlock, 0, L.s>>>(g, s, alpha);
+    k_rasterize<T, true, false><<<nb, kRastBlock, 0, L.s>>>(g, s, alpha);
   else if (bz)
-    k_rasterize<T, false, true><<<nblocks(n), kBlock, 0, L.s>>>(g, s, alpha);
+    k_rasterize<T, false, true><<<nb, kRastBlock, 0, L.s>>>(g, s, alpha);
   else
-    k_rasterize<T, false, false><<<nblocks(n), kBlock, 0, L.s>>>(g, s, alpha);
+    k_rasterize<T, false, false><<<nb, kRastBlock, 0, L.s>>>(g, s, alpha);
   ++*L.counter;
 }
 
@@ -1018,16 +1049,16 @@ void launch_adj_face(const Launch &L, const GridDev &g, const SceneDev &s,
   ProfScope _ps(L, NF_K_ADJ_FACE);
   const bool corner = g.frac == NF_FRACTIONS_CORNER, bz = s.kind == NF_SCENE_EXTRUDED;
   if (corner && bz)
-    k_adj_face<T, S, true, true><<<kRedBlocks, kBlock, 0, L.s>>>(g, s, alpha, uh, P, y, gu,
+    k_adj_face<T, S, true, true><<<kRedBlocks, kAdjBlock, 0, L.s>>>(g, s, alpha, uh, P, y, gu,
                                                                  guh, rs, gtheta);
   else if (corner)
-    k_adj_face<T, S, true, false><<<kRedBlocks, kBlock, 0, L.s>>>(g, s, alpha, uh, P, y, gu,
+    k_adj_face<T, S, true, false><<<kRedBlocks, kAdjBlock, 0, L.s>>>(g, s, alpha, uh, P, y, gu,
                                                                   guh, rs, gtheta);
   else if (bz)
-    k_adj_face<T, S, false, true><<<kRedBlocks, kBlock, 0, L.s>>>(g, s, alpha, uh, P, y, gu,
+    k_adj_face<T, S, false, true><<<kRedBlocks, kAdjBlock, 0, L.s>>>(g, s, alpha, uh, P, y, gu,
                                                                   guh, rs, gtheta);
   else
-    k_adj_face<T, S, false, false><<<kRedBlocks, kBlock, 0, L.s>>>(g, s, alpha, uh, P, y, gu,
+    k_adj_face<T, S, false, false><<<kRedBlocks, kAdjBlock, 0, L.s>>>(g, s, alpha, uh, P, y, gu,
                                                                    guh, rs, gtheta);
   ++*L.counter;
 }

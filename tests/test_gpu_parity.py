@@ -726,8 +726,10 @@ def test_fused_sweep_pairs_give_the_per_launch_bits(nf, prec, name):
             assert np.array_equal(a, b)
         # the adjoint's advection scatter uses float atomics, so its
         # right-hand sides (and then an adjoint solve's iteration count, by
-        # one) vary from run to run at rounding level, fused or not
-        assert abs(b1 - b0) <= 2
+        # one) vary from run to run at rounding level, fused or not; plain
+        # FP32 solves end where their residual stalls at the rounding floor,
+        # which moves the count by a few iterations over the rollout
+        assert abs(b1 - b0) <= (2 if prec != "fp32" else max(6, b0 // 20))
         tol = 1e-10 if prec == "fp64" else 1e-5
         assert np.linalg.norm(g1 - g0) <= tol * np.linalg.norm(g0)
 
@@ -794,3 +796,4 @@ def test_overlapped_recompute_gives_the_sequential_gradient(nf, prec, name):
     assert np.linalg.norm(g1 - g0) <= tol * np.linalg.norm(g0)
     assert rel(u1, u0) <= tol
     assert np.linalg.norm(g1 - gtho) <= GRAD_TOL[prec] * np.linalg.norm(gtho)
+
