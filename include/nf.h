@@ -387,6 +387,19 @@ int nf_get_step(nf_ctx *ctx, int64_t id, int *n);
 int nf_dot(nf_ctx *ctx, const void *a, const void *b, int64_t n, int dtype,
            double *out);
 
+/* Diagnostic: the face kernels widen FP32 values to FP64 and round FP64
+   values to FP32 by integer operations on the bits (the conversion
+   instructions issue on the FP64 pipe, at 1/64 of the FP32 rate on this
+   part). This runs those routines on the n host values in[] (copied to the
+   context's device and back) beside the conversion instructions:
+   out_f[i] = the integer FP64 -> FP32 rounding of in[i], out_d[i] = the
+   integer FP32 -> FP64 widening of (float)in[i], and *mismatches = the
+   number of i where either differs from the instruction's result (bitwise;
+   NaN against NaN counts as equal). Host arrays of n entries, owned by the
+   caller; n in [0, 2^24]. Synchronises the context's stream. */
+int nf_check_conversions(nf_ctx *ctx, const double *in, int64_t n, float *out_f,
+                         double *out_d, int64_t *mismatches);
+
 /* Kernel launches issued by this context since creation (a counter of the
    library's own kernels, used to report launches per timed region). */
 int nf_launch_count(nf_ctx *ctx, int64_t *count);

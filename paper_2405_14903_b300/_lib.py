@@ -131,6 +131,7 @@ SIGNATURES = [
     ("nf_episode_export", C.c_int, [_vp, _i64, _vp, C.POINTER(C.c_size_t)]),
     ("nf_episode_import", C.c_int, [_vp, _i64, _vp, C.c_size_t]),
     ("nf_dot", C.c_int, [_vp, _vp, _vp, _i64, C.c_int, C.POINTER(C.c_double)]),
+    ("nf_check_conversions", C.c_int, [_vp, _vp, _i64, _vp, _vp, C.POINTER(_i64)]),
     ("nf_launch_count", C.c_int, [_vp, C.POINTER(_i64)]),
     ("nf_profile", C.c_int, [_vp, C.c_int]),
     ("nf_profile_read", C.c_int, [_vp, C.c_int, C.POINTER(_i64), C.POINTER(C.c_double)]),

@@ -275,6 +275,20 @@ class Context:
                self._h)
         return out.value
 
+    def check_conversions(self, values):
+        """``nf_check_conversions``: the library's integer-bit FP64 -> FP32
+        rounding and FP32 -> FP64 widening on the device, beside the
+        conversion instructions. Returns (rounded float32 array, widened
+        float64 array, number of mismatching entries)."""
+        v = np.ascontiguousarray(np.asarray(values, dtype=np.float64))
+        n = v.size
+        out_f = np.empty(n, np.float32)
+        out_d = np.empty(n, np.float64)
+        m = C.c_int64()
+        _check(lib.nf_check_conversions(self._h, v.ctypes.data, n, out_f.ctypes.data,
+                                        out_d.ctypes.data, C.byref(m)), self._h)
+        return out_f, out_d, m.value
+
     def launches(self):
         n = C.c_int64()
         _check(lib.nf_launch_count(self._h, C.byref(n)), self._h)

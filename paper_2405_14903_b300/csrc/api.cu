@@ -555,6 +555,42 @@ int nf_dot(nf_ctx *ctx, const void *a, const void *b, int64_t n, int dtype,
   return NF_OK;
 }
 
+int nf_check_conversions(nf_ctx *ctx, const double *in, int64_t n, float *out_f,
+                         double *out_d, int64_t *mismatches) {
+  GUARD(ctx);
+  if (n < 0 || n > ((int64_t)1 << 24) || !mismatches || (n > 0 && (!in || !out_f || !out_d))) {
+    set_error("nf_check_conversions: bad arguments");
+    return NF_E_INVALID;
+  }
+  cudaSetDevice(ctx->c.device);
+  *mismatches = 0;
+  if (n == 0) return NF_OK;
+  void *dev = nullptr;
+  const size_t bytes = (size_t)n * (sizeof(double) + sizeof(float) + sizeof(double)) + 16;
+  cudaError_t e = cudaMalloc(&dev, bytes);
+  if (e != cudaSuccess) return nf::cuda_fail(e, "nf_check_conversions");
+  double *din = (double *)dev;
+  double *dd = din + n;
+  unsigned long long *dm = (unsigned long long *)(dd + n);
+  float *df = (float *)(dm + 1);
+  const cudaStream_t st = ctx->c.stream;
+  e = cudaMemcpyAsync(din, in, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dm, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) {
+    nf::launch_check_conversions(ctx->c.launch(), din, n, df, dd, dm);
+    e = cudaGetLastError();
+  }
+  unsigned long long m = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out_f, df, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out_d, dd, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&m, dm, sizeof(m), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(dev);
+  if (e != cudaSuccess) return nf::cuda_fail(e, "nf_check_conversions");
+  *mismatches = (int64_t)m;
+  return NF_OK;
+}
+
 int nf_launch_count(nf_ctx *ctx, int64_t *count) {
   if (!ctx || !count) return NF_E_INVALID;
   *count = ctx->c.launches;

@@ -353,6 +353,7 @@ class EpisodeImpl : public EpisodeBase {
     g.iw = gr.inlet_w;
     g.ih = gr.inlet_h;
     g.ispeed = gr.inlet_speed;
+    g.set_derived();
     return g;
   }
 
@@ -693,6 +694,7 @@ class EpisodeImpl : public EpisodeBase {
     GridDev g = g_;
     g.dt = h;
     g.c = h / (g_.rho * g_.dx);
+    g.set_derived();
     return g;
   }
   int check_launch() {
@@ -1260,6 +1262,7 @@ struct BatchProj : BatchBase {
     s.c = 1.0;
     s.outlet = 0;  // open faces are found from the fractions
     s.inlet = 0;
+    s.set_derived();
     return s;
   }
   BatchProj(Ctx *c, const GridDev &g, int nb)

@@ -293,18 +293,29 @@ struct RowWalk {
   }
 };
 
+// A fraction widened to the arithmetic type R (FP32 fractions into the FP64
+// outer residual by f2d: that kernel is bound by the FP64 pipe).
+template <class R, class TA>
+__device__ __forceinline__ R widen(const TA *p) {
+  return (R)ld(p);
+}
+template <>
+__device__ __forceinline__ double widen<double, float>(const float *p) {
+  return f2d(*p);
+}
+
 template <class R, class TA, class X>
 __device__ __forceinline__ void gather7r(Nb7<R> &g, const LevelView<TA> &lv,
                                          const X *x, int i, int j, int k, int c,
                                          int row) {
   const int nx = lv.nx, nxy = lv.nx * lv.ny;
   const int fy = c + k * nx;
-  g.xm = (R)ld(lv.ax + c + row);
-  g.xp = (R)ld(lv.ax + c + row + 1);
-  g.ym = (R)ld(lv.ay + fy);
-  g.yp = (R)ld(lv.ay + fy + nx);
-  g.zm = (R)ld(lv.az + c);
-  g.zp = (R)ld(lv.az + c + nxy);
+  g.xm = widen<R>(lv.ax + c + row);
+  g.xp = widen<R>(lv.ax + c + row + 1);
+  g.ym = widen<R>(lv.ay + fy);
+  g.yp = widen<R>(lv.ay + fy + nx);
+  g.zm = widen<R>(lv.az + c);
+  g.zp = widen<R>(lv.az + c + nxy);
   g.vxm = i > 0 ? (R)x[c - 1] : R(0);
   g.vxp = i < nx - 1 ? (R)x[c + 1] : R(0);
   g.vym = j > 0 ? (R)x[c - nx] : R(0);

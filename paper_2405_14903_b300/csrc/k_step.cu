@@ -63,23 +63,14 @@ __device__ __forceinline__ void axis_w(int base, R o, int n, int &i0, R &fr,
   const R fl = floor(o);
   const int i = base + (int)fl;
   const R f = o - fl;
-  if (i < 0) {
-    i0 = 0;
-    fr = R(0);
-    slope = R(0);
-  } else if (i > n - 1 || (i == n - 1 && f > R(0))) {
-    i0 = n - 2;
-    fr = R(1);
-    slope = R(0);
-  } else if (i == n - 1) {  // exactly on the last point
-    i0 = n - 2;
-    fr = R(1);
-    slope = R(1);
-  } else {
-    i0 = i;
-    fr = f;
-    slope = R(1);
-  }
+  // below the lattice: the first point, slope 0; at or past the last point:
+  // the last interval at weight 1, slope 0 past it and 1 exactly on it;
+  // inside: the interval's own weight (selects, no branches)
+  const bool below = i < 0, top = i >= n - 1;
+  const bool past = i > n - 1 || (i == n - 1 && f > R(0));
+  i0 = below ? 0 : (top ? n - 2 : i);
+  fr = below ? R(0) : (top ? R(1) : f);
+  slope = (below || past) ? R(0) : R(1);
 }
 
 // Lattice offsets (h_d - s_e) of a component-d face in component e's lattice.
@@ -91,13 +82,14 @@ __device__ __forceinline__ float lat_off(int d, int e, int a) {
 
 template <class R>
 struct Interp {
-  int64_t idx[8];
+  int idx[8];
   R w[8];
   R dw[3][8];
 };
 
 // Trilinear interpolation of component e at base + o (grid units, e's
 // lattice coordinates). Optionally records corners and weight derivatives.
+// Indices are 32-bit: an episode has fewer than 2^31 faces per component.
 template <class T, class R, bool kStencil>
 __device__ __forceinline__ R trilerp(const GridDev &g, const T *U, int e,
                                      int bi, int bj, int bk, R ox, R oy, R oz,
@@ -108,10 +100,10 @@ __device__ __forceinline__ R trilerp(const GridDev &g, const T *U, int e,
   axis_w<R>(bi, ox, nx, i0, fx, sx);
   axis_w<R>(bj, oy, ny, j0, fy, sy);
   axis_w<R>(bk, oz, nz, k0, fz, sz);
-  const int64_t base = ((int64_t)k0 * ny + j0) * nx + i0;
+  const int base = (k0 * ny + j0) * nx + i0;
   // steps to the upper corner along each axis (0 on a one-point axis, whose
   // upper corner has weight 0: its load stays in bounds)
-  const int64_t sx1 = nx > 1 ? 1 : 0, sy1 = ny > 1 ? nx : 0, sz1 = nz > 1 ? (int64_t)nx * ny : 0;
+  const int sx1 = nx > 1 ? 1 : 0, sy1 = ny > 1 ? nx : 0, sz1 = nz > 1 ? nx * ny : 0;
   const R c000 = (R)U[base], c100 = (R)U[base + sx1];
   const R c010 = (R)U[base + sy1], c110 = (R)U[base + sy1 + sx1];
   const R c001 = (R)U[base + sz1], c101 = (R)U[base + sz1 + sx1];
@@ -120,7 +112,7 @@ __device__ __forceinline__ R trilerp(const GridDev &g, const T *U, int e,
   const R v = gz * (gy * (gx * c000 + fx * c100) + fy * (gx * c010 + fx * c110)) +
               fz * (gy * (gx * c001 + fx * c101) + fy * (gx * c011 + fx * c111));
   if (kStencil) {
-    const int64_t id[8] = {base,             base + sx1,       base + sy1,
+    const int id[8] = {base,             base + sx1,       base + sy1,
                            base + sy1 + sx1, base + sz1,       base + sz1 + sx1,
                            base + sz1 + sy1, base + sz1 + sy1 + sx1};
     const R wx[2] = {gx, fx}, wy[2] = {gy, fy}, wz[2] = {gz, fz};
@@ -226,7 +218,7 @@ __device__ __forceinline__ double band_fraction_warp(const GridDev &g, const Sce
   if (sizeof(T) == 4 && !L->overflow) {
     // saturated samples are counted exactly; only the samples inside the
     // ramp are summed in FP32
-    const float inv_w = (float)(4.0 / g.dx), h = (float)g.dx;
+    const float inv_w = g.finvw, h = g.fdx;
     int full = 0;
     float part = 0.f;
 #pragma unroll
@@ -246,7 +238,7 @@ __device__ __forceinline__ double band_fraction_warp(const GridDev &g, const Sce
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kAll, part, o);
     return ((double)full + (double)part) * (1.0 / 64.0);
   }
-  const double inv_w = 4.0 / g.dx;
+  const double inv_w = g.invw;
   double acc = 0.0;
 #pragma unroll
   for (int half = 0; half < 2; ++half) {
@@ -296,7 +288,7 @@ k_rasterize(GridDev g, SceneDev s, FieldsMut<T> alpha) {
       a[f] = g.outlet_face(d, i, j, k) ? T(1) : T(0);
       break;
     }
-    const float hf = (float)g.dx;
+    const float hf = g.fdx;
     const float pc = scene_phi<float, kBz>(s, (i + (d == 0 ? 0.f : 0.5f)) * hf,
                                            (j + (d == 1 ? 0.f : 0.5f)) * hf,
                                            (k + (d == 2 ? 0.f : 0.5f)) * hf);
@@ -356,13 +348,13 @@ template <class T>
 __device__ __forceinline__ T face_velocity(const GridDev &g, const T *U, int e, int d, int i,
                                            int j, int k) {
   const int nx = g.nx + (e == 0), ny = g.ny + (e == 1);
-  if (e == d) return U[((int64_t)k * ny + j) * nx + i];
+  if (e == d) return U[(k * ny + j) * nx + i];
   const int nd = d == 0 ? g.nx : (d == 1 ? g.ny : g.nz);  // e's points along d
   const int id = d == 0 ? i : (d == 1 ? j : k);
-  const int64_t se = e == 0 ? 1 : (e == 1 ? (int64_t)nx : (int64_t)nx * ny);
-  const int64_t sd = d == 0 ? 1 : (d == 1 ? (int64_t)nx : (int64_t)nx * ny);
+  const int se = e == 0 ? 1 : (e == 1 ? nx : nx * ny);
+  const int sd = d == 0 ? 1 : (d == 1 ? nx : nx * ny);
   // lattice point (i, j, k) of component e with the d index moved to id - 1
-  const int64_t base = ((int64_t)k * ny + j) * nx + i - sd;
+  const int base = (k * ny + j) * nx + i - sd;
   const int lo = id > 0 ? -1 : 0;            // d neighbours, clamped at the walls
   const int hi = id < nd ? 0 : -1;
   const T a = T(0.5) * (U[base + (lo + 1) * sd] + U[base + (lo + 1) * sd + se]);
@@ -501,7 +493,7 @@ __device__ __forceinline__ T face_us(const GridDev &g, const SceneDev &s,
   // box walls: at rest, except the faces of an inflow patch
   if (g.boundary(d, i, j, k)) return g.inlet_face(d, i, j, k) ? T(g.ispeed) : T(0);
   if (s.kind == NF_SCENE_NONE || s.kind == NF_SCENE_SPHERES) return T(0);
-  const T h = T(g.dx);
+  const T h = sizeof(T) == 4 ? T(g.fdx) : T(g.dx);
   const T X = (T(i) + (d == 0 ? T(0) : T(0.5))) * h;
   const T Y = (T(j) + (d == 1 ? T(0) : T(0.5))) * h;
   const T Z = (T(k) + (d == 2 ? T(0) : T(0.5))) * h;
@@ -608,7 +600,7 @@ k_viscosity(GridDev g, Fields<T> in, FieldsMut<T> out, T kv) {
 template <class T, class S, bool kBz>
 __global__ void k_rhs(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
                       S *b, RedScratch rs, double *bnorm2) {
-  const double inv_c = 1.0 / g.c;
+  const double inv_c = g.invc;
   double v[1] = {0.0};
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
        c < g.ncell(); c += (int64_t)gridDim.x * blockDim.x) {
@@ -656,7 +648,7 @@ __global__ void k_update(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
   face_cells(g, d, i, j, k, cL, cR);
   const S pR = cR >= 0 ? P[cR] : S(0);
   const S pL = cL >= 0 ? P[cL] : S(0);
-  const T gp = cT * (T)(pR - pL);
+  const T gp = cT * narrow<T>(pR - pL);
   const T a = comp(alpha, d)[f];
   // the solid velocity only where it has weight (fluid faces skip the scene)
   const T us = a < T(1) ? face_us<T, kBz>(g, s, d, i, j, k) : T(0);
@@ -717,7 +709,7 @@ __device__ __forceinline__ void band_dalpha_lanes(const GridDev &g, const SceneD
 #pragma unroll
   for (int q = 0; q < kMaxParams; ++q) out[q] = T(0);
   if (sizeof(T) == 4 && !L->overflow) {
-    const float inv_w = (float)(4.0 / g.dx), h = (float)g.dx;
+    const float inv_w = g.finvw, h = g.fdx;
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
       const int sm = lane + 32 * half;
@@ -735,7 +727,7 @@ __device__ __forceinline__ void band_dalpha_lanes(const GridDev &g, const SceneD
     }
     return;
   }
-  const double inv_w = 4.0 / g.dx;
+  const double inv_w = g.invw;
 #pragma unroll
   for (int half = 0; half < 2; ++half) {
     const int sm = lane + 32 * half;
@@ -800,8 +792,8 @@ k_adj_face(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh, const S *P, con
 #pragma unroll
   for (int q = 0; q < kMaxParams; ++q) acc[q] = T(0);
   const int64_t n = g.nface(0) + g.nface(1) + g.nface(2);
-  const T cT = T(g.c), h = T(g.dx);
-  const float margin = 0.8f * (float)g.dx;
+  const T cT = sizeof(T) == 4 ? T(g.fc) : T(g.c), h = sizeof(T) == 4 ? T(g.fdx) : T(g.dx);
+  const float margin = 0.8f * g.fdx;
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;

@@ -306,4 +306,8 @@ size_t mg_chain_smem_bytes(const CoarseChain<V, TA> &ch);
 template <class V, class TA>
 int prepare_mg_chain(int smem_limit);
 
+// The integer-bit conversions beside the conversion instructions (a check).
+void launch_check_conversions(const Launch &L, const double *in, int64_t n, float *out_f,
+                              double *out_d, unsigned long long *mismatches);
+
 }  // namespace nf

@@ -27,6 +27,20 @@ struct GridDev {
   int outlet, oj0, ok0, ow, oh;
   int inlet, iside, ij0, ik0, iw, ih;  // inflow patch on an x wall (side -1 / +1)
   double ispeed;                       // its normal velocity (along +x)
+  // Derived on the host by set_derived(): a division or an FP32/FP64
+  // conversion per thread would occupy the FP64 pipe, which runs at 1/64 of
+  // the FP32 rate on this part.
+  double invc;           // 1 / c
+  double invw;           // 4 / dx, the slope of the fraction ramp
+  float fdx, finvw, fc;  // dx, 4 / dx and c rounded to FP32
+
+  void set_derived() {
+    invc = c != 0.0 ? 1.0 / c : 0.0;
+    invw = 4.0 / dx;
+    fdx = (float)dx;
+    finvw = (float)invw;
+    fc = (float)c;
+  }
 
   __host__ __device__ int64_t ncell() const { return (int64_t)nx * ny * nz; }
   __host__ __device__ int fnx(int d) const { return nx + (d == 0); }
@@ -220,6 +234,44 @@ __device__ inline bool grid_sum(double (&v)[W], const RedScratch &rs,
 }
 
 // ---------------------------------------------------------- conversions ----
+// float -> double by integer operations on the bits (exact): a conversion
+// between FP32 and FP64 issues on the FP64 pipe, which runs at 1/64 of the
+// FP32 rate on this part. Zero and normal values take the integer path;
+// subnormal, infinite and NaN values the conversion instruction.
+__device__ __forceinline__ double f2d(float v) {
+  const unsigned u = __float_as_uint(v), a = u & 0x7fffffffu, e = a >> 23;
+  if (a != 0u && (e == 0u || e == 0xffu)) return (double)v;
+  const unsigned sign = u & 0x80000000u;
+  const unsigned hi = a == 0u ? sign : (sign | ((e + 896u) << 20) | ((a & 0x7fffffu) >> 3));
+  const unsigned lo = a == 0u ? 0u : (u << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// double -> float, rounded to nearest even, by integer operations on the
+// bits (the same result as the conversion instruction). Zero takes the
+// integer path; values outside the normal FP32 range, infinities and NaN the
+// conversion instruction.
+__device__ __forceinline__ float d2f(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const unsigned hi = (unsigned)(u >> 32), sign = hi & 0x80000000u;
+  if ((u << 1) == 0ull) return __uint_as_float(sign);
+  const int ef = (int)((hi >> 20) & 0x7ffu) - 896;  // FP32 biased exponent
+  if (ef <= 0 || ef >= 255) return (float)v;
+  const unsigned long long m = u & 0xfffffffffffffull;
+  const unsigned keep = (unsigned)(m >> 29), rem = (unsigned)(m & 0x1fffffffull);
+  unsigned f = sign | ((unsigned)ef << 23) | keep;
+  f += (rem > 0x10000000u || (rem == 0x10000000u && (keep & 1u))) ? 1u : 0u;  // may carry
+  return __uint_as_float(f);                                                // into the exponent
+}
+// A value of precision S in the field precision T.
+template <class T, class S>
+__device__ __forceinline__ T narrow(S v) {
+  return (T)v;
+}
+template <>
+__device__ __forceinline__ float narrow<float, double>(double v) {
+  return d2f(v);
+}
 __device__ __forceinline__ float ld(const float *p) { return *p; }
 __device__ __forceinline__ double ld(const double *p) { return *p; }
 __device__ __forceinline__ float ld(const __nv_bfloat16 *p) {

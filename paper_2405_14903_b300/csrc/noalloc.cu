@@ -105,6 +105,7 @@ extern "C" int nf_loss_noalloc(const nf_grid *gr, int loss_kind,
   g.ok0 = gr->outlet_k0;
   g.ow = gr->outlet_w;
   g.oh = gr->outlet_h;
+  g.set_derived();
   for (int d = 0; d < 3; ++d)
     if (g.nface(d) > NF_NOALLOC_MAX_FACES)
       return invalid("grid too large: a face component exceeds NF_NOALLOC_MAX_FACES entries");

@@ -797,3 +797,47 @@ def test_overlapped_recompute_gives_the_sequential_gradient(nf, prec, name):
     assert rel(u1, u0) <= tol
     assert np.linalg.norm(g1 - gtho) <= GRAD_TOL[prec] * np.linalg.norm(gtho)
 
+
+
+# ---------------------------------------------- integer-bit conversions ----
+
+def _conversion_cases():
+    rng = np.random.default_rng(11)
+    f32 = np.finfo(np.float32)
+    # doubles over and beyond the FP32 range, both signs
+    e = rng.integers(-160, 140, 20000)
+    v = [rng.uniform(1.0, 2.0, e.size) * np.ldexp(1.0, e) * rng.choice([-1.0, 1.0], e.size)]
+    # exact ties between neighbouring floats (round half to even) and their neighbours
+    f = rng.uniform(-1e4, 1e4, 5000).astype(np.float32)
+    up = np.nextafter(f, np.float32(np.inf))
+    mid = (f.astype(np.float64) + up.astype(np.float64)) / 2.0
+    v += [mid, np.nextafter(mid, np.inf), np.nextafter(mid, -np.inf), f.astype(np.float64)]
+    # range edges: largest float and the tie above it, smallest normal and subnormals
+    top = float(f32.max)
+    v.append(np.array([0.0, -0.0, np.inf, -np.inf, np.nan, top, -top,
+                       top * (1.0 + 2.0 ** -25), top * (1.0 + 2.0 ** -24),
+                       float(f32.tiny), float(f32.tiny) * 0.5, float(f32.tiny) * (1 - 2 ** -24),
+                       2.0 ** -149, 2.0 ** -150, 2.0 ** -151, 1.0, -1.0, 0.5, 3.0 ** 0.5,
+                       np.finfo(np.float64).tiny, np.finfo(np.float64).max]))
+    # fractions as the kernels see them: multiples of 1/64 and random values in [0, 1]
+    v += [np.arange(65) / 64.0, rng.uniform(0.0, 1.0, 5000)]
+    return np.concatenate(v)
+
+
+def test_integer_bit_conversions_match_the_instructions(nf):
+    # the face kernels' FP64 -> FP32 rounding and FP32 -> FP64 widening by
+    # integer operations (the conversion instructions run on the slow FP64
+    # pipe) against the instructions on the device and against NumPy's
+    # round-to-nearest-even casts
+    vals = _conversion_cases()
+    ctx = nf.Context("mixed", "mgpcg")
+    out_f, out_d, bad = ctx.check_conversions(vals)
+    ctx.close()
+    assert bad == 0
+    with np.errstate(over="ignore"):
+        ref_f = vals.astype(np.float32)
+    nan = np.isnan(ref_f)
+    assert np.array_equal(np.isnan(out_f), nan)
+    assert np.array_equal(out_f[~nan].view(np.uint32), ref_f[~nan].view(np.uint32))
+    ref_d = ref_f.astype(np.float64)
+    assert np.array_equal(out_d[~nan].view(np.uint64), ref_d[~nan].view(np.uint64))
