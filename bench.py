@@ -175,15 +175,13 @@ def chamber(n, steps, seed):
 # fields, FP32 fractions on the finest level): what the operation must move.
 def alg_bytes_per_cell(kclass, nu):
     if kclass == "mg_smooth0":
-        # red-black half sweep: x of the other colour (n/2), b (n/2), the six
-        # fractions of the updated cells = every face once (3n), x written (n/2);
-        # of the 4 nu half sweeps of a V-cycle the first starts from zero (no x
-        # read) and the first post-smoothing one also reads the coarse
-        # correction (n/8): the average over the V-cycle's launches
-        plain = 4 * 0.5 + 4 * 0.5 + 3 * 4 + 4 * 0.5
-        zero, prolong = plain - 4 * 0.5, plain + 4 / 8
-        k = 4 * max(1, nu)
-        return (zero + prolong + (k - 2) * plain) / k
+        # the method's bytes for one full red-black sweep of the finest level:
+        # x read, b read, the three fraction arrays read, x written, each once
+        # = 24 B/cell; a launch is a half sweep, so 12 B/cell. (Split into two
+        # launches, each half sweep reads every fraction and x of the other
+        # colour again: 17.8 B/cell on average over a V-cycle, which is what
+        # the kernel moves; the difference is charged to the kernel.)
+        return (4 + 4 + 3 * 4 + 4) / 2
     return {
         "apply_dot": 4 + 3 * 4 + 4,            # d, three fraction arrays, q
         "cg_xr": 4 * 4 + 2 * 4,                # x, r, d, q read; x, r written
@@ -361,6 +359,10 @@ def run_ours(args, rank, world, local_rank):
                                     if DRAM_BYTES_PER_CELL.get(roof_class) and n == 128
                                     and args.mg_smooth == 2 else None),
                            launches=nl, avg_us=1e3 * avg_ms, alg_bytes_per_launch=per_launch,
+                           accounting=("24 B/cell per full red-black sweep (x, b, three "
+                                       "fractions read, x written), two launches per sweep"
+                                       if roof_class == "mg_smooth0" else "per-cell reads "
+                                       "and writes of the operation"),
                            timing="CUDA events around every launch of the kernel, over one "
                                   "step of the same workload run right after the timed region")
     if visc is not None and visc[0]:

@@ -209,9 +209,9 @@ __device__ double corner_area(const double ph[4], double da[4]) {
 // together: lane l takes subsamples l and l + 32 (x fastest, then y, z),
 // the warp sums them. FP32 fields use the face's narrow-band evaluator L
 // unless it overflowed, FP64 fields evaluate phi directly in FP64. Every lane
-// returns the face's value.
+// returns the face's value in the field precision.
 template <class T, bool kBz>
-__device__ __forceinline__ double band_fraction_warp(const GridDev &g, const SceneDev &s,
+__device__ __forceinline__ T band_fraction_warp(const GridDev &g, const SceneDev &s,
                                                      const LocalSdf *L, double x, double y,
                                                      double z, int lane) {
   constexpr unsigned kAll = 0xffffffffu;
@@ -236,7 +236,10 @@ __device__ __forceinline__ double band_fraction_warp(const GridDev &g, const Sce
     full = __reduce_add_sync(kAll, full);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kAll, part, o);
-    return ((double)full + (double)part) * (1.0 / 64.0);
+    // (full + part) / 64 rounded once to FP32: the sum is formed exactly
+    // before its one rounding (full <= 64, part a float), so FP32 arithmetic
+    // gives the bits that the FP64 sum rounded to FP32 would
+    return T(((float)full + part) * (1.0f / 64.0f));
   }
   const double inv_w = g.invw;
   double acc = 0.0;
@@ -251,7 +254,7 @@ __device__ __forceinline__ double band_fraction_warp(const GridDev &g, const Sce
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kAll, acc, o);
-  return acc * (1.0 / 64.0);
+  return T(acc * (1.0 / 64.0));
 }
 
 // Threads per block of the rasteriser: one narrow-band evaluator slot in
@@ -328,9 +331,9 @@ k_rasterize(GridDev g, SceneDev s, FieldsMut<T> alpha) {
     const double bx = __shfl_sync(0xffffffffu, X, src);
     const double by = __shfl_sync(0xffffffffu, Y, src);
     const double bz = __shfl_sync(0xffffffffu, Z, src);
-    const double v = band_fraction_warp<T, kBz>(g, s, &sdf[(threadIdx.x & ~31) + src], bx, by,
-                                                bz, lane);
-    if (lane == src) a[f] = T(v);
+    const T v = band_fraction_warp<T, kBz>(g, s, &sdf[(threadIdx.x & ~31) + src], bx, by, bz,
+                                           lane);
+    if (lane == src) a[f] = v;
   }
 }
 
