@@ -583,7 +583,7 @@ int nf_server_destroy(nf_server *srv);
    work. The ticket is cleared (cudaMemsetAsync on `stream`) at every call.
    The first call on each device looks up the array's device address
    (cudaGetSymbolAddress with that device current, checked: NF_E_CUDA on
-   failure) and caches it; make that first call before any stream capture.
+   failure) and caches it.
    Calls that overlap in time on one device (other streams, other threads)
    share the scratch and race: serialise them. Results equal nf_loss's for
    the same velocity (same kernel, same summation order). */
