@@ -93,25 +93,47 @@ k_cc_tile(GridDev g, Fields<T> a, int *lab) {
 }
 
 // Union across tile borders: the faces from a tile's last layer to the next
-// tile, in the forest of tile roots.
+// tile, in the forest of tile roots. The lanes of a warp hold consecutive
+// cells, and across a tile border plane the neighbouring lanes' cells mostly
+// carry the same pair of tile labels: a lane whose pair (its label, its
+// neighbour's label, as read) equals the previous lane's leaves the union to
+// that lane (the two unions join the same two sets, since labels only ever
+// point at ancestors). That cuts the contended unions on the tile roots by
+// up to the tile width; the labels that result are the same (a component's
+// root is its smallest cell index whatever the order of the unions).
 template <class T>
 __global__ void k_cc_merge(GridDev g, Fields<T> a, int *lab) {
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < g.ncell();
-       c += (int64_t)gridDim.x * blockDim.x) {
-    int i, j, k;
-    g.cell_ijk(c, i, j, k);
-    const bool bx = (i % kCcTile) == kCcTile - 1, by = (j % kCcTile) == kCcTile - 1,
-               bz = (k % kCcTile) == kCcTile - 1;
-    if (!(bx || by || bz)) continue;
-    if (((const volatile int *)lab)[c] < 0) continue;
+  const int lane = threadIdx.x & 31;
+  const int64_t n = g.ncell();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) - lane; base < n;
+       base += stride) {
+    const int64_t c = base + lane;
+    int i = 0, j = 0, k = 0;
+    bool bx = false, by = false, bz = false, live = false;
+    if (c < n) {
+      g.cell_ijk(c, i, j, k);
+      bx = (i % kCcTile) == kCcTile - 1;
+      by = (j % kCcTile) == kCcTile - 1;
+      bz = (k % kCcTile) == kCcTile - 1;
+      live = (bx || by || bz) && ((const volatile int *)lab)[c] >= 0;
+    }
     for (int d = 0; d < 3; ++d) {
-      if (!(d == 0 ? bx : (d == 1 ? by : bz))) continue;
-      const int ni = i + (d == 0), nj = j + (d == 1), nk = k + (d == 2);
-      if (ni >= g.nx || nj >= g.ny || nk >= g.nz) continue;
-      const T af = d == 0 ? a.x[g.face(0, ni, j, k)]
-                          : (d == 1 ? a.y[g.face(1, i, nj, k)] : a.z[g.face(2, i, j, nk)]);
-      if (!(af > T(0))) continue;
-      cc_union(lab, (int)c, (int)g.cell(ni, nj, nk));
+      int la = -1, lb = -1;
+      if (live && (d == 0 ? bx : (d == 1 ? by : bz))) {
+        const int ni = i + (d == 0), nj = j + (d == 1), nk = k + (d == 2);
+        if (ni < g.nx && nj < g.ny && nk < g.nz) {
+          const T af = d == 0 ? a.x[g.face(0, ni, j, k)]
+                              : (d == 1 ? a.y[g.face(1, i, nj, k)] : a.z[g.face(2, i, j, nk)]);
+          if (af > T(0)) {
+            la = ((const volatile int *)lab)[c];
+            lb = ((const volatile int *)lab)[g.cell(ni, nj, nk)];
+          }
+        }
+      }
+      const int pa = __shfl_up_sync(0xffffffffu, la, 1), pb = __shfl_up_sync(0xffffffffu, lb, 1);
+      const bool dup = lane > 0 && pa == la && pb == lb;
+      if (la >= 0 && lb >= 0 && la != lb && !dup) cc_union(lab, la, lb);
     }
   }
 }
