@@ -303,6 +303,9 @@ template <>
 __device__ __forceinline__ double widen<double, float>(const float *p) {
   return f2d(*p);
 }
+// A V value widened to FP64 (FP32 by f2d).
+__device__ __forceinline__ double widen_v(float v) { return f2d(v); }
+__device__ __forceinline__ double widen_v(double v) { return v; }
 
 template <class R, class TA, class X>
 __device__ __forceinline__ void gather7r(Nb7<R> &g, const LevelView<TA> &lv,
@@ -481,7 +484,7 @@ k_axpy_outer(int64_t n, S *x, const V *e, double inv) {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int64_t c = c0 + u * stride;
-      if (c < n) x[c] = (S)((double)xv[u] + inv * (double)ev[u]);
+      if (c < n) x[c] = (S)((double)xv[u] + inv * widen_v(ev[u]));
     }
   }
 }
