@@ -860,20 +860,38 @@ class EpisodeImpl : public EpisodeBase {
   int geometry_and_advect(Eng &e, int m, const GridDev &g, const SceneDev &sd, const T *u_in,
                           T *uh) {
     Launch L = e.ctx->launch();
+    bool joined = true;
     if (m < (int)tapeA_.size() && tapeA_[m] && tapeA_ok_[m]) {
       // recomputed step: the fractions kept by the first pass (bit-identical
       // to rasterising them again)
       CKC(cudaMemcpyAsync(e.alpha, tapeA_[m], nfaces_ * sizeof(T), cudaMemcpyDeviceToDevice, L.s));
     } else {
       NvtxRange nvr("nf.rasterize");
-      launch_rasterize<T>(L, g, sd, mut(e.alpha));
-      if (e.ctx == ctx_ && ctx_->cfg.tape_fractions) {  // (the first pass only)
+      const bool tape = e.ctx == ctx_ && ctx_->cfg.tape_fractions;  // (the first pass only)
+      if (tape) {
         if ((int)tapeA_.size() <= m) {
           tapeA_.resize(m + 1, nullptr);
           tapeA_ok_.resize(m + 1, 0);
         }
         if (!tapeA_[m]) CKS(faces(&tapeA_[m]));
-        CKC(cudaMemcpyAsync(tapeA_[m], e.alpha, nfaces_ * sizeof(T), cudaMemcpyDeviceToDevice, L.s));
+      }
+      // The fractions (and their tape copy) go to a side stream and overlap
+      // the advection below, which does not read them: both kernels are
+      // latency-bound and leave most of the GPU idle. The context stream
+      // waits for them before the projection. The episode's own engine only,
+      // and not while kernel classes are being timed.
+      Launch Lr = L;
+      if (e.ctx == ctx_ && ctx_->prof.kclass == -2 && L.s == ctx_->stream) {
+        CKS(side_.ensure());
+        CKC(cudaEventRecord(side_.fork, L.s));
+        CKC(cudaStreamWaitEvent(side_.s, side_.fork, 0));
+        Lr = Launch{side_.s, L.counter, nullptr};
+        joined = false;
+      }
+      launch_rasterize<T>(Lr, g, sd, mut(e.alpha));
+      if (tape) {
+        CKC(cudaMemcpyAsync(tapeA_[m], e.alpha, nfaces_ * sizeof(T), cudaMemcpyDeviceToDevice,
+                            Lr.s));
         tapeA_ok_[m] = 1;
       }
     }
@@ -884,6 +902,10 @@ class EpisodeImpl : public EpisodeBase {
       launch_viscosity<T>(L, g, cview(e.Ut), mut(uh));
     } else {
       launch_advect<T>(L, g, cview(u_in), mut(uh), ctx_->cfg.advect_order);
+    }
+    if (!joined) {
+      CKC(cudaEventRecord(side_.join, side_.s));
+      CKC(cudaStreamWaitEvent(L.s, side_.join, 0));
     }
     return NF_OK;
   }
@@ -1212,6 +1234,25 @@ class EpisodeImpl : public EpisodeBase {
   int seg_start_ = -1;
   Seg seg_;                          // the segment the backward pass reverts
   std::unique_ptr<Helper> helper_;   // overlapped recompute (backward)
+  // A second stream of the episode and its fork / join events (the
+  // forward's rasterisation beside the advection), made on first use.
+  struct Side {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    int ensure() {
+      if (s) return NF_OK;
+      CKC(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+      CKC(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+      CKC(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+      return NF_OK;
+    }
+    ~Side() {
+      if (fork) cudaEventDestroy(fork);
+      if (join) cudaEventDestroy(join);
+      if (s) cudaStreamDestroy(s);
+    }
+  };
+  Side side_;
   int helper_seg_ = -1;              // segment the helper is recomputing
   bool overlap_now_ = false;         // inside a whole-rollout backward pass
   std::vector<T *> tapeA_;     // fractions of every step (tape_fractions)
