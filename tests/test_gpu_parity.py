@@ -624,15 +624,19 @@ def test_expired_device_waits_report_timeout_and_the_context_recovers(nf, monkey
 # default, in replayed batches of graphs while profiling, and as direct
 # launches with NF_GRAPHS=0. The kernels and their order are the same (the
 # other paths only add launches that return at once), so a forward rollout
-# gives the same bits and iteration counts on all three.
+# gives the same bits and iteration counts on all three. The forward's
+# rasterisation runs on a side stream beside the advection except while
+# profiling, so the comparison also checks that fork and join order it.
 
-def test_launch_paths_give_the_same_bits(nf, monkeypatch):
-    cfg = CONFIGS["chamber_sub"]()
+@pytest.mark.parametrize("name,tape", [("chamber_sub", False), ("chamber_sub", True),
+                                       ("plate", True), ("sphere32", False)])
+def test_launch_paths_give_the_same_bits(nf, monkeypatch, name, tape):
+    cfg = CONFIGS[name]()
 
     def run(profile=False, graphs=True):
         if not graphs:
             monkeypatch.setenv("NF_GRAPHS", "0")
-        ctx = make_ctx(nf, "mixed", cfg=cfg)
+        ctx = make_ctx(nf, "mixed", cfg=cfg, tape_fractions=tape)
         if profile:
             ctx.profile("all")
         ep = ctx.episode(cfg["grid"], cfg["scene"])
