@@ -599,10 +599,12 @@ k_viscosity(GridDev g, Fields<T> in, FieldsMut<T> out, T kv) {
 // b = G^T (S U^ + (I - S) U_s) / c on active cells (sum alpha > 0), else 0.
 // G^T v at a cell is v(low face) - v(high face), summed over the axes. The
 // division by c = dt / (rho dx) lets the solver use the unit-scale operator
-// G^T S G, whose coefficients do not depend on the step length.
+// G^T S G, whose coefficients do not depend on the step length. Four blocks
+// per SM (at most 64 registers) keep the kRedBlocks grid to one wave.
 template <class T, class S, bool kBz>
-__global__ void k_rhs(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
-                      S *b, RedScratch rs, double *bnorm2) {
+__global__ void __launch_bounds__(kBlock, 4)
+k_rhs(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh, S *b, RedScratch rs,
+      double *bnorm2) {
   const double inv_c = g.invc;
   double v[1] = {0.0};
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
