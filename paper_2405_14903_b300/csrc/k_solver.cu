@@ -219,16 +219,6 @@ __device__ __forceinline__ int stop_flag(const CGState *st) {
   return st != nullptr ? *(volatile const int *)&st->done : 0;
 }
 
-// Programmatic dependent launch: kernels launched by launch_pdl may start
-// while their predecessor in the stream finishes. Each such kernel first
-// waits until the predecessor has completed and its writes are visible,
-// then lets its own successor's blocks be scheduled (they wait the same
-// way). Without the launch attribute both instructions are no-ops.
-__device__ __forceinline__ void pdl_wait() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
 // ------------------------------------------------------------- ILP ------
 // Grid-stride kernels walk cells in batches of ILP cells per thread (cells
 // c0, c0 + stride, ...): every load of a batch is issued before its results
@@ -2295,23 +2285,7 @@ k_mg_mid(MidSpan<V, TA> m, CoarseChain<V, TA> ch, const CGState *st) {
 }
 
 // ------------------------------------------------------------ launchers ---
-// Launch with programmatic dependent launch allowed (the kernel calls
-// pdl_wait() before reading anything its predecessor wrote).
-template <class... P, class... A>
-static void launch_pdl(void (*kernel)(P...), unsigned grid, unsigned block, size_t smem,
-                       cudaStream_t s, A... args) {
-  cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, kernel, (P)args...);
-}
+
 // Grid-stride streaming kernels: at most one wave (148 SMs x 8 blocks of
 // kBlock threads; their launch bounds keep 8 blocks resident), so every
 // block pays its start-up latency once.

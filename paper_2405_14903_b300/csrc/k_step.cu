@@ -369,6 +369,7 @@ __device__ __forceinline__ T face_velocity(const GridDev &g, const T *U, int e, 
 // the FP64 pipe, 1/64 of the FP32 rate here, for 45 % of the kernel).
 template <class T>
 __global__ void k_advect(GridDev g, Fields<T> u, FieldsMut<T> out, int order, T rdt) {
+  pdl_wait();
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int d;
   int64_t f;
@@ -408,6 +409,7 @@ __global__ void k_advect(GridDev g, Fields<T> u, FieldsMut<T> out, int order, T 
 template <class T>
 __global__ void k_advect_adjoint(GridDev g, Fields<T> u, Fields<T> gut,
                                  FieldsMut<T> gu, int order, T rdt) {
+  pdl_wait();
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int d;
   int64_t f;
@@ -605,6 +607,7 @@ template <class T, class S, bool kBz>
 __global__ void __launch_bounds__(kBlock, 4)
 k_rhs(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh, S *b, RedScratch rs,
       double *bnorm2) {
+  pdl_wait();
   const double inv_c = g.invc;
   double v[1] = {0.0};
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -643,6 +646,7 @@ k_rhs(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh, S *b, RedScratch rs,
 template <class T, class S, bool kBz>
 __global__ void k_update(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh,
                          const S *P, FieldsMut<T> u, T cT) {
+  pdl_wait();
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int d;
   int64_t f;
@@ -755,6 +759,7 @@ __device__ __forceinline__ void band_dalpha_lanes(const GridDev &g, const SceneD
 template <class T, class S>
 __global__ void k_adj_gp(GridDev g, Fields<T> alpha, Fields<T> gu, S *gp,
                          RedScratch rs, double *norm2) {
+  pdl_wait();
   double v[1] = {0.0};
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
        c < g.ncell(); c += (int64_t)gridDim.x * blockDim.x) {
@@ -791,6 +796,7 @@ template <class T, class S, bool kCorner, bool kBz>
 __global__ void __launch_bounds__(kAdjBlock, 4)
 k_adj_face(GridDev g, SceneDev s, Fields<T> alpha, Fields<T> uh, const S *P, const S *y,
            Fields<T> gu, FieldsMut<T> guh, RedScratch rs, double *gtheta) {
+  pdl_wait();
   // per-thread partial sums in the field precision (each thread adds a few
   // dozen faces), block and grid sums in FP64
   T acc[kMaxParams];
@@ -964,7 +970,7 @@ void launch_advect(const Launch &L, const GridDev &g, Fields<T> u,
                    FieldsMut<T> out, int order) {
   const int64_t n = g.nface(0) + g.nface(1) + g.nface(2);
   ProfScope _ps(L, NF_K_ADVECT);
-  k_advect<T><<<nblocks(n), kBlock, 0, L.s>>>(g, u, out, order, (T)(g.dt / g.dx));
+  launch_pdl(k_advect<T>, nblocks(n), kBlock, 0, L.s, g, u, out, order, (T)(g.dt / g.dx));
   ++*L.counter;
 }
 
@@ -976,7 +982,8 @@ void launch_advect_adjoint(const Launch &L, const GridDev &g, Fields<T> u,
   cudaMemsetAsync(gu.y, 0, g.nface(1) * sizeof(T), L.s);
   cudaMemsetAsync(gu.z, 0, g.nface(2) * sizeof(T), L.s);
   ProfScope _ps(L, NF_K_ADJ_ADVECT);
-  k_advect_adjoint<T><<<nblocks(n), kBlock, 0, L.s>>>(g, u, gut, gu, order, (T)(g.dt / g.dx));
+  launch_pdl(k_advect_adjoint<T>, nblocks(n), kBlock, 0, L.s, g, u, gut, gu, order,
+             (T)(g.dt / g.dx));
   ++*L.counter;
 }
 
@@ -1000,9 +1007,9 @@ void launch_rhs(const Launch &L, const GridDev &g, const SceneDev &s,
                 double *bnorm2) {
   ProfScope _ps(L, NF_K_RHS);
   if (s.kind == NF_SCENE_EXTRUDED)
-    k_rhs<T, S, true><<<kRedBlocks, kBlock, 0, L.s>>>(g, s, alpha, uh, b, rs, bnorm2);
+    launch_pdl(k_rhs<T, S, true>, kRedBlocks, kBlock, 0, L.s, g, s, alpha, uh, b, rs, bnorm2);
   else
-    k_rhs<T, S, false><<<kRedBlocks, kBlock, 0, L.s>>>(g, s, alpha, uh, b, rs, bnorm2);
+    launch_pdl(k_rhs<T, S, false>, kRedBlocks, kBlock, 0, L.s, g, s, alpha, uh, b, rs, bnorm2);
   ++*L.counter;
 }
 
@@ -1012,9 +1019,9 @@ void launch_update(const Launch &L, const GridDev &g, const SceneDev &s,
   const int64_t n = g.nface(0) + g.nface(1) + g.nface(2);
   ProfScope _ps(L, NF_K_UPDATE);
   if (s.kind == NF_SCENE_EXTRUDED)
-    k_update<T, S, true><<<nblocks(n), kBlock, 0, L.s>>>(g, s, alpha, uh, P, u, (T)g.c);
+    launch_pdl(k_update<T, S, true>, nblocks(n), kBlock, 0, L.s, g, s, alpha, uh, P, u, (T)g.c);
   else
-    k_update<T, S, false><<<nblocks(n), kBlock, 0, L.s>>>(g, s, alpha, uh, P, u, (T)g.c);
+    launch_pdl(k_update<T, S, false>, nblocks(n), kBlock, 0, L.s, g, s, alpha, uh, P, u, (T)g.c);
   ++*L.counter;
 }
 
@@ -1034,7 +1041,7 @@ template <class T, class S>
 void launch_adj_gp(const Launch &L, const GridDev &g, Fields<T> alpha,
                    Fields<T> gu, S *gp, const RedScratch &rs, double *norm2) {
   ProfScope _ps(L, NF_K_ADJ_GP);
-  k_adj_gp<T, S><<<kRedBlocks, kBlock, 0, L.s>>>(g, alpha, gu, gp, rs, norm2);
+  launch_pdl(k_adj_gp<T, S>, kRedBlocks, kBlock, 0, L.s, g, alpha, gu, gp, rs, norm2);
   ++*L.counter;
 }
 
@@ -1046,17 +1053,17 @@ void launch_adj_face(const Launch &L, const GridDev &g, const SceneDev &s,
   ProfScope _ps(L, NF_K_ADJ_FACE);
   const bool corner = g.frac == NF_FRACTIONS_CORNER, bz = s.kind == NF_SCENE_EXTRUDED;
   if (corner && bz)
-    k_adj_face<T, S, true, true><<<kRedBlocks, kAdjBlock, 0, L.s>>>(g, s, alpha, uh, P, y, gu,
-                                                                 guh, rs, gtheta);
+    launch_pdl(k_adj_face<T, S, true, true>, kRedBlocks, kAdjBlock, 0, L.s, g, s, alpha, uh, P, y,
+               gu, guh, rs, gtheta);
   else if (corner)
-    k_adj_face<T, S, true, false><<<kRedBlocks, kAdjBlock, 0, L.s>>>(g, s, alpha, uh, P, y, gu,
-                                                                  guh, rs, gtheta);
+    launch_pdl(k_adj_face<T, S, true, false>, kRedBlocks, kAdjBlock, 0, L.s, g, s, alpha, uh, P, y,
+               gu, guh, rs, gtheta);
   else if (bz)
-    k_adj_face<T, S, false, true><<<kRedBlocks, kAdjBlock, 0, L.s>>>(g, s, alpha, uh, P, y, gu,
-                                                                  guh, rs, gtheta);
+    launch_pdl(k_adj_face<T, S, false, true>, kRedBlocks, kAdjBlock, 0, L.s, g, s, alpha, uh, P, y,
+               gu, guh, rs, gtheta);
   else
-    k_adj_face<T, S, false, false><<<kRedBlocks, kAdjBlock, 0, L.s>>>(g, s, alpha, uh, P, y, gu,
-                                                                   guh, rs, gtheta);
+    launch_pdl(k_adj_face<T, S, false, false>, kRedBlocks, kAdjBlock, 0, L.s, g, s, alpha, uh, P,
+               y, gu, guh, rs, gtheta);
   ++*L.counter;
 }
 

@@ -153,6 +153,34 @@ struct ProfScope {
   }
 };
 
+// Programmatic dependent launch: kernels launched by launch_pdl may start
+// while their predecessor in the stream finishes. Each such kernel first
+// waits until the predecessor has completed and its writes are visible,
+// then lets its own successor's blocks be scheduled (they wait the same
+// way). Without the launch attribute both instructions are no-ops.
+__device__ __forceinline__ void pdl_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launch with programmatic dependent launch allowed (the kernel calls
+// pdl_wait() before reading anything its predecessor wrote).
+template <class... P, class... A>
+inline void launch_pdl(void (*kernel)(P...), unsigned grid, unsigned block, size_t smem,
+                       cudaStream_t s, A... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, (P)args...);
+}
+
 inline unsigned nblocks(int64_t n, int b = kBlock) {
   return (unsigned)((n + b - 1) / b);
 }
