@@ -75,3 +75,15 @@ def test_cpu_baseline_one_thread_and_all_cores_on_a_small_sample():
     assert many["value"] == pytest.approx(2 * 10 ** 3 / many["seconds"])
     assert one["value"] == pytest.approx(10 ** 3 / one["seconds"])
     assert many["wall_seconds"] >= many["seconds"]
+
+
+def test_smoother_roofline_counts_the_methods_full_sweep_bytes():
+    # a full red-black sweep of the finest level must read x, b and the three
+    # fraction arrays and write x once (FP32: 24 B/cell); a launch is a half
+    # sweep, so it is charged 12 B/cell whatever the kernel itself re-reads
+    assert bench.alg_bytes_per_cell("mg_smooth0", 2) == 12.0
+    assert bench.alg_bytes_per_cell("mg_smooth0", 3) == 12.0
+    # the other classes: their operands read and written once
+    assert bench.alg_bytes_per_cell("apply_dot", 2) == 20
+    assert bench.alg_bytes_per_cell("cg_xr", 2) == 24
+    assert bench.alg_bytes_per_cell("unknown", 2) is None
