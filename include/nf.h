@@ -48,6 +48,7 @@ extern "C" {
 #define NF_E_TIMEOUT 5       /* a bounded device wait expired              */
 #define NF_E_CUDA 6          /* a CUDA runtime call failed                 */
 #define NF_E_STATE 7         /* call invalid in the episode's state        */
+#define NF_E_CANCELED 8      /* a served request dropped by NF_REQ_CANCEL   */
 
 /* ----------------------------------------------------------------- enums */
 #define NF_PREC_FP64 0   /* FP64 fields, vectors and multigrid            */
@@ -472,6 +473,13 @@ int nf_profile_read(nf_ctx *ctx, int kclass, int64_t *launches, double *ms);
                           the episode's whole rollout (nf_backward).
      NF_REQ_CLOSE         destroy the episode; its memory returns to the
                           budget and admits waiting OPENs (FIFO).
+     NF_REQ_CANCEL        cancel the episode at once: its requests that have
+                          not started complete with NF_E_CANCELED, the one
+                          running (if any) completes normally, then the
+                          episode closes (the cancel's own result reports
+                          NF_REQ_CLOSE once it has); an episode never
+                          created is dropped with its reservation, and the
+                          cancel completes at once with NF_OK.
    Budget: an OPEN reserves episode_estimate = the episode's base state plus
    its rollout tape for checkpoint_every steps; after every request the
    reservation follows the episode's actual bytes where they are larger.
@@ -483,6 +491,7 @@ typedef struct nf_server nf_server;
 #define NF_REQ_STEP 1
 #define NF_REQ_STEP_ADJOINT 2
 #define NF_REQ_CLOSE 3
+#define NF_REQ_CANCEL 4
 
 typedef struct nf_request {
   int kind;               /* NF_REQ_*                                         */

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "libnf.so")
 
 NF_OK, NF_E_INVALID, NF_E_OOM, NF_E_NOT_CONVERGED = 0, 1, 2, 3
 NF_E_DIVERGED, NF_E_TIMEOUT, NF_E_CUDA, NF_E_STATE = 4, 5, 6, 7
+NF_E_CANCELED = 8
 PREC = {"fp64": 0, "fp32": 1, "mixed": 2}
 SOLVER = {"cg": 0, "mgpcg": 1}
 NF_F32, NF_F64 = 0, 1
@@ -96,7 +97,7 @@ class ServerStats(C.Structure):
                 ("batches", C.c_int64), ("batched_requests", C.c_int64)]
 
 
-REQ = {"open": 0, "step": 1, "step_adjoint": 2, "close": 3}
+REQ = {"open": 0, "step": 1, "step_adjoint": 2, "close": 3, "cancel": 4}
 
 P3 = C.c_void_p * 3          # a (x, y, z) triple of array pointers
 PP = C.POINTER(C.c_void_p)   # how a triple (or NULL) is passed

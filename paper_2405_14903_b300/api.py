@@ -512,6 +512,14 @@ class Server:
         req.episode = int(key)
         return self._submit(req)
 
+    def cancel(self, key):
+        """NF_REQ_CANCEL: the episode's requests that have not started
+        complete with NF_E_CANCELED, then it closes."""
+        req = L.Request()
+        req.kind = L.REQ["cancel"]
+        req.episode = int(key)
+        return self._submit(req)
+
     def poll(self, ticket, wait_ms=-1):
         r = L.Result()
         st = lib.nf_server_poll(self._h, int(ticket), int(wait_ms), C.byref(r))

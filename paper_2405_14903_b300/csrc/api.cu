@@ -223,6 +223,7 @@ const char *nf_status_string(int s) {
     case NF_E_TIMEOUT: return "bounded device wait expired";
     case NF_E_CUDA: return "CUDA runtime error";
     case NF_E_STATE: return "call invalid in the current state";
+    case NF_E_CANCELED: return "request cancelled before it started";
     default: return "unknown status";
   }
 }

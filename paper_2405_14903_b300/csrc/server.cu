@@ -473,6 +473,47 @@ extern "C" int nf_server_submit(nf_server *srv, const nf_request *req, int64_t *
       srv->open_wait.push_back(key);
     return NF_OK;
   }
+  if (req->kind == NF_REQ_CANCEL) {
+    if (it == srv->eps.end()) {
+      srv->finish(job.ticket, srv->immediate(job, NF_E_INVALID));
+      return NF_OK;
+    }
+    EpisodeRec &rec = it->second;
+    // the episode's requests that have not started complete as cancelled
+    bool open_dropped = false;
+    auto drop = [&](std::deque<Job> &q, Slot *slot) {
+      for (auto j = q.begin(); j != q.end();) {
+        if (j->req.episode != key) {
+          ++j;
+          continue;
+        }
+        if (j->req.kind == NF_REQ_OPEN) open_dropped = true;
+        srv->finish(j->ticket, srv->immediate(*j, NF_E_CANCELED));
+        if (slot) slot->pending -= 1;
+        j = q.erase(j);
+      }
+    };
+    if (rec.slot < 0) {  // not admitted: nothing reserved, nothing on a slot
+      drop(rec.waiting, nullptr);
+      srv->eps.erase(it);  // (its key leaves the admission queue)
+      srv->admit_waiting();
+      srv->finish(job.ticket, srv->immediate(job, NF_OK));
+      return NF_OK;
+    }
+    Slot *sl = srv->slots[rec.slot].get();
+    drop(sl->queue, sl);
+    if (open_dropped) {  // never created: its reservation returns
+      srv->reserved -= std::min(srv->reserved, rec.reserved);
+      srv->eps.erase(it);
+      srv->admit_waiting();
+      srv->finish(job.ticket, srv->immediate(job, NF_OK));
+      return NF_OK;
+    }
+    // created (or being created): it closes after its running request
+    job.req.kind = NF_REQ_CLOSE;
+    srv->enqueue(rec.slot, std::move(job));
+    return NF_OK;
+  }
   if (req->kind != NF_REQ_STEP && req->kind != NF_REQ_STEP_ADJOINT &&
       req->kind != NF_REQ_CLOSE) {
     srv->finish(job.ticket, srv->immediate(job, NF_E_INVALID));

@@ -285,3 +285,49 @@ def test_served_batches_match_alone_within_tolerance(nf):
         assert abs(m["loss"] - a["loss"]) <= 1e-6 * abs(a["loss"])
         g_a = np.asarray(a["g_theta"])
         assert np.linalg.norm(m["g_theta"] - g_a) <= 1e-4 * np.linalg.norm(g_a)
+
+
+def test_cancel_drops_the_queued_requests_and_closes_the_episode(nf):
+    # one slot: the episode's OPEN runs while its queued steps wait; a cancel
+    # completes every step that has not started with NF_E_CANCELED (those
+    # that ran before it complete normally: a prefix), then closes the
+    # episode, whose memory returns; later requests for the key are invalid
+    ep = _episodes()[0]
+    srv = nf.Server(slots=1, **CFG)
+    t_open = srv.open(ep["key"], ep["grid"], ep["scene"])
+    steps = [srv.step(ep["key"], frames=1) for _ in range(6)]
+    t_cancel = srv.cancel(ep["key"])
+    assert srv.drain(wait_ms=300000)
+    assert srv.poll(t_open)["status"] == 0
+    status = [srv.poll(t)["status"] for t in steps]
+    ran = status.index(8) if 8 in status else len(status)
+    assert all(s == 0 for s in status[:ran]) and all(s == 8 for s in status[ran:]), status
+    assert srv.poll(t_cancel)["status"] == 0
+    st = srv.stats()
+    assert st["episodes"] == 0 and st["bytes_reserved"] == 0
+    assert srv.poll(srv.step(ep["key"]), wait_ms=60000)["status"] == 1
+    srv.close_server()
+
+
+def test_cancel_of_an_episode_waiting_for_memory(nf):
+    # a budget that holds one episode: the second OPEN waits; cancelling it
+    # completes the OPEN and its step with NF_E_CANCELED at once, reserves
+    # nothing, and leaves the first episode's requests untouched
+    eps = _episodes()[3:5]                         # two 24^3 episodes
+    probe = nf.Server(slots=1, **CFG)
+    probe.poll(probe.open(1, eps[0]["grid"], eps[0]["scene"]))
+    budget = int(probe.stats()["bytes_reserved"] * 1.5)
+    probe.close_server()
+    srv = nf.Server(slots=2, hbm_budget=budget, **CFG)
+    a = _script(srv, eps[0])
+    b_open = srv.open(eps[1]["key"], eps[1]["grid"], eps[1]["scene"])
+    b_step = srv.step(eps[1]["key"], frames=1)
+    waiting = srv.stats()["open_waiting"]
+    b_cancel = srv.cancel(eps[1]["key"])
+    assert srv.poll(b_cancel, wait_ms=60000)["status"] == 0
+    assert srv.drain(wait_ms=300000)
+    assert waiting >= 1
+    assert srv.poll(b_open)["status"] == 8 and srv.poll(b_step)["status"] == 8
+    assert all(r["status"] == 0 for r in _collect(srv, a))
+    assert srv.stats()["bytes_reserved"] == 0
+    srv.close_server()
